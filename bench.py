@@ -1,0 +1,307 @@
+"""Benchmark: NLL + gradient evaluations of the 4D B0 -> K*0 mu mu model, 1M events, FP64.
+
+One step = one pass of the hot path for a new parameter point: host hoisting of the
+parameter-only terms, the fused CUDA kernel (event loads, density, log, gradient sums,
+warp/block/grid reduction), the copy of the sums to the host and the host assembly of
+NLL and gradient (nll_eval_grad through the C ABI).  Inputs are resident in HBM; the L2
+is flushed (512 MiB write) between timed steps.  value = events per second per
+NLL+gradient evaluation, whole job (all ranks).
+
+Also reported: e2e (the same metric with the events copied from pinned host memory and
+the basis rebuilt every step), the roofline of the fused kernel, the oracle timed on the
+host cores (cpu_baseline), and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank evaluates its own 1M-event sample (weak scaling, no collective
+on the data path); the step time is the maximum over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2505_12414_gb300 import synth  # noqa: E402
+
+N_EVENTS = 1_000_000
+WORKLOAD = "kstar4d_1M"
+METRIC = "events/s per NLL+grad eval (4D, 1M ev, FP64)"
+
+# Algorithmic FP64 work per event of the fused 4D NLL+gradient with the precomputed
+# angular basis (paper Sec. 2.4.1 hoisting and Sec. 2.4.2 event precompute), in FP64
+# flops (add/mul = 1, FMA = 2):
+#   mass exponent (d, q, arg)                      1 + 2 + 2      =  5
+#   angular dot product A (8 FMA)                                  = 16
+#   Chebyshev factors (6 FMA) and products (4 mul)                 = 16
+#   mixture s = A E, P = s + C                                     =  2
+#   gradient sums: R E, R s, sum R s, R s d, sum, FMA              =  7
+#                  8 angular FMA                                   = 16
+#                  R C, sum, FMA                                   =  4
+#                  u1..u3 (3 mul) and 6 FMA                        = 15
+#   running product of P (1 mul)                                   =  1
+#  => 82 flops of arithmetic, plus one exponential and one reciprocal per event charged
+#  at the cost of CUDA's own exp() and 1.0/x measured on GB300 in DFMA issue slots
+#  (2 flops each): c_exp and c_rcp below (calibration in profiles/fp64_calibration.md).
+ARITH_FLOPS_4D = 82.0
+C_EXP_DFMA = 12.0   # calibrated: DFMA-equivalent issue slots of CUDA exp() on GB300
+C_RCP_DFMA = 8.0    # calibrated: DFMA-equivalent issue slots of CUDA 1.0/x on GB300
+FLOPS_PER_EVENT = ARITH_FLOPS_4D + 2.0 * (C_EXP_DFMA + C_RCP_DFMA)
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no FP64 entry in MEASURED_PEAKS.json)
+# DRAM traffic of one fused-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# one ncu capture); None until measured for the current kernel.
+KERNEL_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def thetas(k):
+    scale = np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    return [synth.perturb(synth.TRUTH_4D, scale, seed=synth.BASE_SEED + 17, k=i, frac=0.3) for i in range(k)]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smmax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(cols, seconds=10.0, sample=100_000):
+    """The oracle, as it stands, on the host cores: events/s per NLL+grad evaluation."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0))
+    sub = [c[:sample] for c in cols]
+    th = thetas(3)
+    oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[0], nthreads=cores)
+    t0 = time.perf_counter()
+    evals = 0
+    while True:
+        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[evals % 3], nthreads=cores)
+        evals += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": evals * sample / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+            "sample": "%d NLL+grad evals of the first %d events of the 4D 1M-event sample, %d threads" %
+                      (evals, sample, cores)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    cols = synth.kstar4d(N_EVENTS, stream=0)
+    cores = len(os.sched_getaffinity(0))
+    sample = 200_000
+    sub = [c[:sample] for c in cols]
+    th = thetas(args.warmup + args.steps)
+    for i in range(args.warmup):
+        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[i], nthreads=cores)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[args.warmup + i], nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = args.steps * sample / dt
+    desc = "%d events of the 4D 1M-event sample per step, oracle (C, FP64, Kahan), %d threads" % (sample, cores)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "sample_events": sample},
+            "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2505_12414_gb300 as g
+
+    g.load()
+    stream = torch.cuda.current_stream(dev)
+
+    cols = synth.kstar4d(N_EVENTS, stream=rank)
+    model = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=local, stream=stream.cuda_stream)
+    model.load(cols, precompute=True)
+    th = thetas(args.warmup + args.steps)
+    model.eval_grad(th[0])
+    g.nll_autotune(model.handle)
+    launch = g.nll_get_launch(model.handle)
+    g.nll_set_profiling(model.handle, True)
+
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for i in range(args.warmup):
+        flush.zero_()
+        model.eval_grad(th[i])
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        model.eval_grad(th[args.warmup + i])
+        ends[i].record(stream)
+        kernel_ms.append(g.nll_last_kernel_ms(model.handle))
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * N_EVENTS / (ms_per_step * 1e-3)
+
+    # end to end through the public API: pinned host columns copied every step
+    pinned = []
+    for c in cols:
+        t = torch.empty(len(c), dtype=torch.float64, pin_memory=True)
+        t.numpy()[:] = c
+        pinned.append(t.numpy())
+    e2e_ms = []
+    g.nll_set_profiling(model.handle, False)
+    for i in range(args.e2e_steps + 2):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        model.load(pinned, precompute=True)
+        model.eval_grad(th[i % len(th)])
+        s1.record(stream)
+        s1.synchronize()
+        if i >= 2:
+            e2e_ms.append(s0.elapsed_time(s1))
+    e2e_step = statistics.median(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+
+    kms = statistics.median(kernel_ms)
+    achieved = FLOPS_PER_EVENT * N_EVENTS / (kms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": KERNEL_TRAFFIC_BYTES,
+                "kernel": "fused_nll_kernel<4D, precompute, grad>", "kernel_ms": kms,
+                "peak_source": "nominal FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
+                "flops_per_event": FLOPS_PER_EVENT}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(cols)
+        k_acc = 21
+        line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "model": "B0->K*0mumu 4D, 18 params",
+                           "variant": {1: "precompute", 2: "direct"}.get(launch["variant"]),
+                           "blocks_per_sm": launch["blocks_per_sm"], "threads": launch["threads"],
+                           "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas/weak"},
+                "e2e": {"value": world * N_EVENTS / (e2e_step * 1e-3), "unit": "events/s",
+                        "h2d_bytes_per_step": 4 * 8 * N_EVENTS, "d2h_bytes_per_step": 8 * (k_acc + 3),
+                        "ms_per_step": e2e_step},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * gbnll.h -- C ABI of the GB300 (sm_103a) unbinned maximum-likelihood hot path.
+ *
+ * The library evaluates, for a fixed data sample and a parameter vector theta,
+ *     NLL(theta) = - sum_i w_i ln P(x_i | theta)                (paper Sec. 2.1, Eq. 1)
+ * and its analytic gradient dNLL/dtheta (Sec. 2.1 and Sec. 2.2 ask for analytic first
+ * derivatives for gradient-based minimisers), in IEEE FP64 on the GPU, and minimises it
+ * with a host quasi-Newton minimiser (Sec. 2.1: the minimiser runs on the host and the
+ * accelerator evaluates the likelihood).  w_i = 1 unless weights are loaded.
+ *
+ * Models (fixed parameter order):
+ *   NLL_MODEL_MASS1D (Sec. 2.4.1, Eq. 2; Sec. 3.2): observable m on [ma, mb];
+ *     P = fsig G(m; mu, sigma) + (1 - fsig) E(m; alpha), each normalised on [ma, mb];
+ *     theta = [mu, sigma, alpha, fsig].
+ *   NLL_MODEL_KSTARMUMU4D: observables (m, cos theta_l, cos theta_K, phi) on
+ *     [ma, mb] x [-1, 1] x [-1, 1] x [-pi, pi];
+ *     P = fsig G(m) A(angles) + (1 - fsig) E(m) prod_j C_j(x_j) / Nc_j, with A the
+ *     angular rate of Sec. 2.4.2 Eq. 3 and C_j = 1 + c1_j x + c2_j (2x^2 - 1) in
+ *     x = cos theta_l, cos theta_K, phi/pi (the paper's angular benchmark has no mass
+ *     dimension or background; this product background is the library's 4D model);
+ *     theta = [mu, sigma, FL, S3, S4, S5, AFB, S7, S8, S9, alpha,
+ *              c1_ctl, c2_ctl, c1_ctk, c2_ctk, c1_phi, c2_phi, fsig].
+ *
+ * Conventions for every call:
+ *   - Every function returns an nll_status; none aborts or throws.  nll_last_error()
+ *     gives the text of the model's most recent error.
+ *   - Pointers passed in are borrowed for the duration of the call only.  The library
+ *     owns all device memory it allocates (event copies, reduction buffers) and frees
+ *     it in nll_destroy().
+ *   - A model is bound to one device and one CUDA stream.  Calls on one model are
+ *     serialised on that stream and block the calling host thread until their results
+ *     are on the host.  A model is not thread-safe; different models are independent.
+ *   - Arrays of doubles are IEEE binary64.  Event columns are structure-of-arrays.
+ */
+#ifndef GBNLL_H
+#define GBNLL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nll_model nll_model; /* opaque; owned by the library */
+
+typedef enum {
+    NLL_OK = 0,
+    NLL_ERR_ARG = 1,              /* invalid argument, size, range or parameter value     */
+    NLL_ERR_CUDA = 2,             /* a CUDA runtime call failed                           */
+    NLL_ERR_OOM = 3,              /* device or pinned host allocation failed              */
+    NLL_ERR_NONPOSITIVE_PDF = 4,  /* some P_i <= 0 or not finite; *nll_out = +inf         */
+    NLL_ERR_NOT_CONVERGED = 5,    /* minimiser stopped before its convergence test passed */
+    NLL_ERR_TIMEOUT = 6,          /* a bounded device-side wait ran out                   */
+    NLL_ERR_STATE = 7             /* call out of order (e.g. evaluate before loading)     */
+} nll_status;
+
+typedef enum { NLL_MODEL_MASS1D = 1, NLL_MODEL_KSTARMUMU4D = 2 } nll_model_kind;
+
+/* Kernel variants for the 4D model's angular part (paper Sec. 2.4.2):
+ *   NLL_VARIANT_AUTO       precomputed basis when loaded with precompute, else direct;
+ *   NLL_VARIANT_PRECOMPUTE event-only angular terms built once at load and read per eval;
+ *   NLL_VARIANT_DIRECT     angular terms recomputed from the angles at every eval. */
+typedef enum { NLL_VARIANT_AUTO = 0, NLL_VARIANT_PRECOMPUTE = 1, NLL_VARIANT_DIRECT = 2 } nll_variant;
+
+/*
+ * nll_create_model -- create a model of `kind` on CUDA device `device`.
+ *   obs_ranges   host array: [ma, mb] for MASS1D; [ma, mb, -1, 1, -1, 1, -pi, pi] for
+ *                KSTARMUMU4D (the angular ranges must be exactly these; ma < mb finite).
+ *                Paper Sec. 2.4.1 normalises over a fixed observable range.
+ *   cuda_stream  a cudaStream_t cast to uintptr_t on which every launch and copy of this
+ *                model is issued; 0 = the library creates and owns a non-blocking stream.
+ *   out          receives the model handle (NULL on error).
+ * Errors: NLL_ERR_ARG (kind, ranges), NLL_ERR_CUDA (device), NLL_ERR_OOM.
+ */
+int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t cuda_stream, nll_model** out);
+
+/*
+ * nll_load_events -- copy a data sample into the model (replacing any previous one).
+ *   columns      ndim pointers (1 for MASS1D: m; 4 for 4D: m, ctl, ctk, phi), each to
+ *                n_events doubles.  Host pointers if on_device == 0, device pointers on
+ *                the model's device if on_device == 1.  The library copies them into its
+ *                own 256-byte-aligned SoA store (padded to a tile multiple).
+ *   weights      n_events per-event weights w_i (same memory space), or NULL for w_i = 1.
+ *   precompute   4D only: 1 = build the event-only angular basis once here (paper
+ *                Sec. 2.4.2 event-dependent precompute), 0 = keep only the raw angles.
+ * Events outside the observable ranges, or non-finite values/weights, are rejected with
+ * NLL_ERR_ARG and the model keeps no sample.  n_events may be 0 (NLL = 0, gradient 0).
+ */
+int nll_load_events(nll_model* m, const double* const* columns, const double* weights, int64_t n_events,
+                    int on_device, int precompute);
+
+/*
+ * nll_eval -- NLL(theta) (paper Eq. 1) for the loaded sample.
+ *   theta        host array of n_params = nll_num_params(m) doubles, in the model's order.
+ *                sigma > 0, 0 <= fsig <= 1, all finite; 4D: 2 - (2/3) c2_j > 0.
+ *   nll_out      host double.
+ * Returns NLL_ERR_NONPOSITIVE_PDF with *nll_out = +inf if some P_i <= 0 or is not finite.
+ */
+int nll_eval(nll_model* m, const double* theta, int n_params, double* nll_out);
+
+/*
+ * nll_eval_grad -- NLL(theta) and its gradient in one fused pass over the events.
+ *   grad_out     host array of n_params doubles, dNLL/dtheta_k in the model's order.
+ * Requires 0 < fsig < 1 (the fsig derivative divides the component sums by fsig and
+ * 1 - fsig); otherwise as nll_eval.
+ */
+int nll_eval_grad(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out);
+
+/* Minimiser options and result (paper Sec. 2.1: Migrad-style variable-metric minimiser
+ * on the host; Sec. 3.1: uncertainties from the inverse Hessian, HESSE). */
+typedef struct {
+    double tol_edm; /* stop when EDM = g^T V g / 2 < tol_edm (e.g. 1e-8; <= 0 -> 1e-8)       */
+    int max_iter;   /* quasi-Newton iterations (<= 0 -> 500)                                  */
+    int strategy;   /* 0: start from diag(step^2); 1: start from a finite-difference Hessian  */
+    int hessian;    /* 0: covariance from the quasi-Newton matrix; 1: finite-difference
+                       Hessian of the analytic gradient at the minimum plus Newton polish     */
+} fit_options;
+
+#define FIT_MAXPAR 32
+typedef struct {
+    double theta[FIT_MAXPAR];               /* fitted parameters (fixed ones unchanged)       */
+    double err[FIT_MAXPAR];                 /* sqrt(diag(cov)); 0 for fixed parameters        */
+    double cov[FIT_MAXPAR * FIT_MAXPAR];    /* covariance, row-major n_params x n_params      */
+    double nll, edm;                        /* objective and estimated distance to minimum    */
+    int n_eval, n_iter, status;             /* evaluations, iterations, nll_status of the fit */
+} fit_result;
+
+/*
+ * fit_minimise -- minimise the model's NLL with the library's quasi-Newton (BFGS)
+ * minimiser, evaluating NLL and gradient on the GPU at each step.
+ *   theta0, lo, hi, step  host arrays of n_params: start point, bounds (lo < hi bounds the
+ *                parameter through a smooth sine transform; lo >= hi means unbounded), and
+ *                initial step sizes (> 0).  fixed[k] != 0 keeps parameter k at theta0[k].
+ *   opt          options (NULL -> defaults); out: result (always filled as far as reached).
+ * Returns NLL_OK on convergence, NLL_ERR_NOT_CONVERGED, or an evaluation error.
+ */
+int fit_minimise(nll_model* m, const double* theta0, const double* lo, const double* hi, const double* step,
+                 const int* fixed, int n_params, const fit_options* opt, fit_result* out);
+
+/*
+ * fit_minimise_fcn -- the same minimiser on a caller-supplied objective (host callback).
+ *   fcn(user, theta, nll_out, grad_out) must fill *nll_out and grad_out[n_params] and
+ *   return 0 on success, non-zero to reject the point.  No GPU is involved.
+ */
+typedef int (*fit_fcn)(void* user, const double* theta, double* nll_out, double* grad_out);
+int fit_minimise_fcn(fit_fcn fcn, void* user, const double* theta0, const double* lo, const double* hi,
+                     const double* step, const int* fixed, int n_params, const fit_options* opt,
+                     fit_result* out);
+
+/* Number of parameters of the model (4 or 18) and the name of parameter i. */
+int nll_num_params(const nll_model* m);
+const char* nll_param_name(const nll_model* m, int i);
+
+/* Text of the most recent error on this model ("" if none).  Valid until the next call. */
+const char* nll_last_error(const nll_model* m);
+
+/* Free the model and all its device and host buffers.  NULL is accepted. */
+void nll_destroy(nll_model* m);
+
+/*
+ * Launch configuration and measurement.
+ *   nll_set_launch  blocks per SM (1..32) and threads per block (64..1024, multiple of 64)
+ *                   of the fused kernel, and the 4D variant (nll_variant).  0 keeps a value.
+ *   nll_autotune    times the candidate launch shapes (and both 4D variants when the basis is
+ *                   loaded) on the loaded sample and keeps the fastest; blocks the host.
+ *   nll_set_profiling / nll_last_kernel_ms   when profiling is on, each evaluation records
+ *                   CUDA events on the model's stream around its fused kernel; the last
+ *                   kernel duration in milliseconds is returned.
+ *   nll_get_launch  reports blocks per SM, threads per block, variant and the SM count.
+ */
+int nll_set_launch(nll_model* m, int blocks_per_sm, int threads_per_block, int variant);
+int nll_get_launch(const nll_model* m, int* blocks_per_sm, int* threads_per_block, int* variant, int* sm_count);
+int nll_autotune(nll_model* m);
+int nll_set_profiling(nll_model* m, int on);
+int nll_last_kernel_ms(const nll_model* m, double* ms);
+
+/*
+ * nll_precomputed_basis -- copy the event-only angular basis built at load (4D,
+ * precompute = 1) to `out` (host, row-major [n_events][13]): for each event
+ *   h0, hFL, h_S3, h_S4, h_S5, h_AFB, h_S7, h_S8, h_S9, T2(ctl), T2(ctk), phi/pi, T2(phi/pi)
+ * where A = h0 + FL hFL + sum_k S_k h_k (paper Sec. 2.4.2, Eq. 3 regrouped by parameter)
+ * and T2(x) = 2x^2 - 1.  NLL_ERR_STATE if no basis was built.
+ */
+int nll_precomputed_basis(nll_model* m, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBNLL_H */

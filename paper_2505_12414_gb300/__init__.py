@@ -1,0 +1,331 @@
+"""Python binding of libgbnll: the GB300 unbinned-NLL hot path (arXiv 2505.12414).
+
+Argument marshalling only.  Every evaluation runs in the CUDA library's kernels; there is
+no CPU fallback: if the library is not built, or no CUDA device is present, the calls
+raise.  Function names match the C ABI in include/gbnll.h.
+
+Inputs may be numpy arrays (host memory, copied by the library) or CUDA torch tensors
+(device memory on the model's device, copied device-to-device).  Streams: pass
+``torch.cuda.current_stream().cuda_stream`` (or 0 for a library-owned stream).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libgbnll.so")
+
+NLL_OK = 0
+NLL_ERR_ARG = 1
+NLL_ERR_CUDA = 2
+NLL_ERR_OOM = 3
+NLL_ERR_NONPOSITIVE_PDF = 4
+NLL_ERR_NOT_CONVERGED = 5
+NLL_ERR_TIMEOUT = 6
+NLL_ERR_STATE = 7
+
+NLL_MODEL_MASS1D = 1
+NLL_MODEL_KSTARMUMU4D = 2
+
+NLL_VARIANT_AUTO = 0
+NLL_VARIANT_PRECOMPUTE = 1
+NLL_VARIANT_DIRECT = 2
+
+FIT_MAXPAR = 32
+
+_lib = None
+
+
+class NLLError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("gbnll status %d: %s" % (status, message))
+        self.status = status
+
+
+class fit_options(ctypes.Structure):
+    _fields_ = [("tol_edm", ctypes.c_double), ("max_iter", ctypes.c_int), ("strategy", ctypes.c_int),
+                ("hessian", ctypes.c_int)]
+
+
+class fit_result(ctypes.Structure):
+    _fields_ = [("theta", ctypes.c_double * FIT_MAXPAR), ("err", ctypes.c_double * FIT_MAXPAR),
+                ("cov", ctypes.c_double * (FIT_MAXPAR * FIT_MAXPAR)), ("nll", ctypes.c_double),
+                ("edm", ctypes.c_double), ("n_eval", ctypes.c_int), ("n_iter", ctypes.c_int),
+                ("status", ctypes.c_int)]
+
+
+FIT_FCN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path=None):
+    """Load libgbnll.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError("libgbnll.so is not built (%s); run __graft_entry__.build()" % p)
+    L = ctypes.CDLL(p)
+    vp = ctypes.c_void_p
+    L.nll_create_model.argtypes = [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.nll_load_events.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+    L.nll_eval.argtypes = [vp, _DP, ctypes.c_int, _DP]
+    L.nll_eval_grad.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP]
+    L.fit_minimise.argtypes = [vp, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                               ctypes.POINTER(fit_options), ctypes.POINTER(fit_result)]
+    L.fit_minimise_fcn.argtypes = [FIT_FCN, vp, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                   ctypes.POINTER(fit_options), ctypes.POINTER(fit_result)]
+    L.nll_num_params.argtypes = [vp]
+    L.nll_param_name.argtypes = [vp, ctypes.c_int]
+    L.nll_param_name.restype = ctypes.c_char_p
+    L.nll_last_error.argtypes = [vp]
+    L.nll_last_error.restype = ctypes.c_char_p
+    L.nll_destroy.argtypes = [vp]
+    L.nll_destroy.restype = None
+    L.nll_set_launch.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.nll_get_launch.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.nll_autotune.argtypes = [vp]
+    L.nll_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.nll_last_kernel_ms.argtypes = [vp, _DP]
+    L.nll_precomputed_basis.argtypes = [vp, _DP]
+    _lib = L
+    return L
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _p(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _is_cuda_tensor(x):
+    return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and bool(x.is_cuda)
+
+
+def _check(model, st):
+    if st != NLL_OK:
+        msg = load().nll_last_error(model).decode() if model else ""
+        raise NLLError(st, msg)
+
+
+def _err(model):
+    return load().nll_last_error(model).decode()
+
+
+# ------------------------------------------------------------------------------------
+# functions with the C ABI's names
+# ------------------------------------------------------------------------------------
+def nll_create_model(kind, obs_ranges, device=0, stream=0):
+    """Create a model; returns an opaque handle (int)."""
+    L = load()
+    r = _f64(obs_ranges)
+    h = ctypes.c_void_p()
+    st = L.nll_create_model(int(kind), _p(r), int(device), int(stream or 0), ctypes.byref(h))
+    if st != NLL_OK:
+        raise NLLError(st, "nll_create_model failed")
+    return h.value
+
+
+def nll_load_events(model, columns, weights=None, precompute=True):
+    """Copy events (numpy arrays on the host, or CUDA tensors) into the model."""
+    L = load()
+    cols = list(columns)
+    on_device = _is_cuda_tensor(cols[0])
+    keep = []
+    if on_device:
+        import torch
+
+        cols = [c.to(torch.float64).contiguous() for c in cols]
+        keep.extend(cols)
+        ptrs = [c.data_ptr() for c in cols]
+        n = int(cols[0].numel())
+        wp = None
+        if weights is not None:
+            w = weights.to(torch.float64).contiguous()
+            keep.append(w)
+            wp = w.data_ptr()
+    else:
+        cols = [_f64(c) for c in cols]
+        keep.extend(cols)
+        ptrs = [c.ctypes.data for c in cols]
+        n = len(cols[0])
+        wp = None
+        if weights is not None:
+            w = _f64(weights)
+            keep.append(w)
+            wp = w.ctypes.data
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    st = L.nll_load_events(model, arr, wp, n, 1 if on_device else 0, 1 if precompute else 0)
+    _check(model, st)
+
+
+def nll_eval(model, theta, check=True):
+    """NLL at theta.  With check=False returns (nll, status) instead of raising."""
+    L = load()
+    th = _f64(theta)
+    out = ctypes.c_double()
+    st = L.nll_eval(model, _p(th), len(th), ctypes.byref(out))
+    if not check:
+        return out.value, st
+    _check(model, st)
+    return out.value
+
+
+def nll_eval_grad(model, theta, check=True):
+    """(NLL, gradient ndarray) at theta.  With check=False also returns the status."""
+    L = load()
+    th = _f64(theta)
+    out = ctypes.c_double()
+    g = np.zeros(len(th))
+    st = L.nll_eval_grad(model, _p(th), len(th), ctypes.byref(out), _p(g))
+    if not check:
+        return out.value, g, st
+    _check(model, st)
+    return out.value, g
+
+
+def _fit_args(theta0, lo, hi, step, fixed):
+    th = _f64(theta0)
+    n = len(th)
+    lo = _f64(lo if lo is not None else np.zeros(n))
+    hi = _f64(hi if hi is not None else np.zeros(n))
+    step = _f64(step if step is not None else np.maximum(1e-3 * np.abs(th), 1e-3))
+    fx = np.ascontiguousarray(np.asarray(fixed if fixed is not None else np.zeros(n), dtype=np.int32))
+    return th, lo, hi, step, fx
+
+
+def _result_dict(res, n):
+    cov = np.ctypeslib.as_array(res.cov)[: FIT_MAXPAR * FIT_MAXPAR].reshape(FIT_MAXPAR, FIT_MAXPAR)
+    cov = cov.reshape(-1)[: n * n].reshape(n, n).copy()
+    return dict(theta=np.array(res.theta[:n]), err=np.array(res.err[:n]), cov=cov, nll=res.nll, edm=res.edm,
+                n_eval=res.n_eval, n_iter=res.n_iter, status=res.status)
+
+
+def fit_minimise(model, theta0, lo=None, hi=None, step=None, fixed=None, tol_edm=1e-8, max_iter=500,
+                 strategy=1, hessian=1):
+    """Minimise the model's NLL on the GPU; returns a dict (theta, err, cov, nll, edm, ...)."""
+    L = load()
+    th, lo, hi, step, fx = _fit_args(theta0, lo, hi, step, fixed)
+    opt = fit_options(tol_edm, max_iter, strategy, hessian)
+    res = fit_result()
+    L.fit_minimise(model, _p(th), _p(lo), _p(hi), _p(step), fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                   len(th), ctypes.byref(opt), ctypes.byref(res))
+    return _result_dict(res, len(th))
+
+
+def fit_minimise_fcn(fcn, theta0, lo=None, hi=None, step=None, fixed=None, tol_edm=1e-8, max_iter=500,
+                     strategy=1, hessian=1):
+    """The library's minimiser on a Python objective fcn(theta) -> (f, grad)."""
+    L = load()
+    th, lo, hi, step, fx = _fit_args(theta0, lo, hi, step, fixed)
+    n = len(th)
+
+    def cb(user, tp, fp, gp):
+        try:
+            t = np.ctypeslib.as_array(tp, shape=(n,)).copy()
+            f, g = fcn(t)
+            fp[0] = float(f)
+            for k in range(n):
+                gp[k] = float(g[k])
+            return 0
+        except Exception:
+            return 1
+
+    cfun = FIT_FCN(cb)
+    opt = fit_options(tol_edm, max_iter, strategy, hessian)
+    res = fit_result()
+    L.fit_minimise_fcn(cfun, None, _p(th), _p(lo), _p(hi), _p(step),
+                       fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n, ctypes.byref(opt), ctypes.byref(res))
+    return _result_dict(res, n)
+
+
+def nll_num_params(model):
+    return load().nll_num_params(model)
+
+
+def nll_param_name(model, i):
+    return load().nll_param_name(model, int(i)).decode()
+
+
+def nll_last_error(model):
+    return _err(model)
+
+
+def nll_destroy(model):
+    if model:
+        load().nll_destroy(model)
+
+
+def nll_set_launch(model, blocks_per_sm=0, threads_per_block=0, variant=0):
+    _check(model, load().nll_set_launch(model, int(blocks_per_sm), int(threads_per_block), int(variant)))
+
+
+def nll_get_launch(model):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(model, load().nll_get_launch(model, *[ctypes.byref(x) for x in v]))
+    return dict(blocks_per_sm=v[0].value, threads=v[1].value, variant=v[2].value, sm_count=v[3].value)
+
+
+def nll_autotune(model):
+    _check(model, load().nll_autotune(model))
+
+
+def nll_set_profiling(model, on=True):
+    _check(model, load().nll_set_profiling(model, 1 if on else 0))
+
+
+def nll_last_kernel_ms(model):
+    out = ctypes.c_double()
+    _check(model, load().nll_last_kernel_ms(model, ctypes.byref(out)))
+    return out.value
+
+
+def nll_precomputed_basis(model, n_events):
+    out = np.zeros((int(n_events), 13))
+    _check(model, load().nll_precomputed_basis(model, _p(out)))
+    return out
+
+
+class Model:
+    """Owning wrapper around a model handle."""
+
+    def __init__(self, kind, obs_ranges, device=0, stream=0):
+        self.kind = kind
+        self.handle = nll_create_model(kind, obs_ranges, device, stream)
+
+    def load(self, columns, weights=None, precompute=True):
+        nll_load_events(self.handle, columns, weights, precompute)
+        return self
+
+    def eval(self, theta):
+        return nll_eval(self.handle, theta)
+
+    def eval_grad(self, theta):
+        return nll_eval_grad(self.handle, theta)
+
+    def fit(self, theta0, **kw):
+        return fit_minimise(self.handle, theta0, **kw)
+
+    @property
+    def num_params(self):
+        return nll_num_params(self.handle)
+
+    def param_names(self):
+        return [nll_param_name(self.handle, i) for i in range(self.num_params)]
+
+    def close(self):
+        if self.handle:
+            nll_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

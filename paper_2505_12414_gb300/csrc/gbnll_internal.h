@@ -1,0 +1,97 @@
+// gbnll_internal.h -- structures shared by the CUDA kernels (kernels.cu) and the host
+// runtime (runtime.cu).  Not part of the public C ABI (include/gbnll.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gbnll {
+
+constexpr int kMass1D = 1;
+constexpr int kKstar4D = 2;
+
+// Angular-part variants of the 4D kernel (paper Sec. 2.4.2).
+constexpr int kVarPrecompute = 1;  // read the event-only basis built at load
+constexpr int kVarDirect = 2;      // recompute the basis from the angles per evaluation
+
+// Columns of the structure-of-arrays event store.  Every column holds n_pad doubles and
+// starts on a 256-byte boundary.
+enum Col : int {
+    kColM = 0,     // mass
+    kColCtl = 1,   // cos theta_l          (4D)
+    kColCtk = 2,   // cos theta_K          (4D)
+    kColPhi = 3,   // phi                  (4D)
+    kColH0 = 4,    // basis: h0, hFL, h_S3 .. h_S9  (9 columns, 4D precompute)
+    kColT2l = 13,  // 2 ctl^2 - 1
+    kColT2k = 14,  // 2 ctk^2 - 1
+    kColXp = 15,   // phi / pi
+    kColT2p = 16,  // 2 (phi/pi)^2 - 1
+    kNumCols = 17
+};
+
+// Accumulator slots of the fused kernels.  Every slot is an FP64 sum over events
+// (slot 0 = sum of w ln Ptilde; the last slot counts invalid densities).
+//   mass model : lnp, R s, R s d, R s d^2, R, R d, bad
+//   4D model   : lnp, R s, R s d, R s d^2, R E h_k (8: FL, S3..S9), R C, R C d,
+//                R C/C1 {x1, T2(x1)}, R C/C2 {x2, T2(x2)}, R C/C3 {x3, T2(x3)}, bad
+//   NLL only   : lnp, bad
+// with d = m - mu, E the Gaussian factor, R = w / Ptilde, s = A E, C the background
+// factor (see kernels.cu for the factorisation).
+constexpr int kAcc1D = 7;
+constexpr int kAcc4D = 21;
+constexpr int kAccNll = 2;
+constexpr int kAccMax = 21;
+
+// Per-launch constant block: every parameter-only term the per-event work needs
+// (paper Sec. 2.4.1: terms that depend on the parameters only are computed once per
+// parameter point on the host and passed to the kernel).
+struct KConst {
+    double mu;         // Gaussian mean
+    double neg_b0;     // -1/(2 sigma^2)
+    double neg_alpha;  // -alpha
+    double k0;         // ln b1 - alpha (mu - ma); exponent = d (neg_b0 d + neg_alpha) + k0
+    double b2;         // mass model: background constant (1-f) / Ntilde2
+    double ang[8];     // FL, S3, S4, S5, AFB, S7, S8, S9
+    double cq[9];      // background factors: C_j = cq[3j] + cq[3j+1] x_j + cq[3j+2] T2(x_j)
+};
+
+struct KArgs {
+    const double* col[kNumCols];  // device column pointers (unused ones NULL)
+    const double* w;              // weights or NULL
+    int64_t n;                    // events
+    KConst c;
+    double* partials;             // [kAccMax][max_blocks] per-block sums
+    unsigned int* ticket;         // grid-completion counter, 0 between launches
+    double* out;                  // [kAccMax] final sums
+};
+
+// Load-time statistics: sum w, sum w (m - ma), count of events outside the ranges.
+struct SArgs {
+    const double* col[4];
+    const double* w;
+    int64_t n;
+    int ndim;
+    double lo[4], hi[4];
+    double* partials;
+    unsigned int* ticket;
+    double* out;  // [3]
+};
+
+struct BArgs {  // basis precompute
+    const double* ctl;
+    const double* ctk;
+    const double* phi;
+    double* out[13];  // h0, hFL, h_S3..h_S9, T2l, T2k, xp, T2p
+    int64_t n;
+};
+
+// Launchers (kernels.cu).  They return the launch's cudaError_t.
+cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,
+                         cudaStream_t stream, const KArgs& a);
+cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a);
+cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BArgs& a);
+cudaError_t upload_exp2_table_values(const double* host256);  // 2^(j/256) into device symbol
+                                                              // (current device)
+int num_acc(int kind, bool grad);
+
+}  // namespace gbnll

@@ -1,0 +1,443 @@
+// kernels.cu -- fused FP64 NLL + gradient kernels for sm_103a.
+//
+// Hot path of the unbinned maximum-likelihood fit (paper Sec. 2.1, Eq. 1): for every
+// event, evaluate the normalised density with the parameter-only terms hoisted into a
+// per-launch constant block (paper Sec. 2.4.1) and, for the 4D model, optionally the
+// event-only angular basis read from memory (paper Sec. 2.4.2); take the logarithm;
+// accumulate the few per-event sums from which the host assembles the gradient; reduce
+// warp -> block -> grid in a fixed order.
+//
+// GB300 specifics that shape the code:
+//  * FP64 throughput is scarce (about 1.2 TFLOP/s against about 7 TB/s of HBM), so the
+//    per-event work is arranged to minimise FP64 instructions:
+//      - the density is factored as P = exp(alpha (m - ma)) * Ptilde,
+//        Ptilde = A(angles) exp(-b0 d^2 - alpha d + k0) + C(background), so one
+//        exponential per event serves both mixture components;
+//      - for unweighted samples sum_i ln Ptilde_i is taken as the logarithm of a running
+//        product whose binary exponent is split off with integer instructions each event
+//        (one logarithm per thread instead of one per event); sum_i alpha (m_i - ma) is
+//        a constant of the sample, computed once at load;
+//      - the exponential is a table-driven implementation (P. T. P. Tang, ACM TOMS 15
+//        (1989) 144) with a 256-entry table of 2^(j/256) held in shared memory and a
+//        degree-4 Taylor polynomial; the reciprocal 1/Ptilde starts from the hardware
+//        approximation rcp.approx.ftz.f64 and takes one cubically convergent correction
+//        y (1 + e + e^2), e = 1 - x y;
+//      - validity checks and the exponent bookkeeping use the integer pipe only.
+//  * Events are SoA FP64 columns read with 128-bit (double2) coalesced loads; each
+//    thread handles two consecutive events per iteration of a grid-stride loop.
+//  * The grid is a small multiple of the SM count; block partial sums are written to a
+//    scratch buffer and the last block to finish (atomic ticket) reduces them in a fixed
+//    order, so results are bitwise reproducible for a given launch shape.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gbnll_internal.h"
+
+namespace gbnll {
+
+__device__ double g_exp2tab[256];  // 2^(j/256), correctly rounded, uploaded once per device
+
+// ----------------------------------------------------------------------------------
+// FP64 building blocks
+// ----------------------------------------------------------------------------------
+
+// exp(x) after Tang's table-driven method: x = (256 q + j) ln2/256 + r, |r| <= ln2/512,
+// exp(x) = 2^q 2^(j/256) exp(r), exp(r) - 1 = r (1 + r/2 + r^2/6 + r^3/24) (truncation
+// below 0.35 ulp).  The reduction constant ln2/256 is split so that k * L_hi is exact.
+// |x| >= 707 returns 0 (x < 0) or +inf (x > 0, also NaN); results below 2^-1020 are
+// flushed to zero.  9 FP64 instructions on the fast path.
+__device__ __forceinline__ double fexp(double x, const double* __restrict__ tab)
+{
+    const double kInvL = 0x1.71547652b82fep+8;   // 256/ln2
+    const double kMagic = 0x1.8p52;              // 1.5 * 2^52: rounds to an integer in the low word
+    const double kLhi = 0x1.62e42ff000000p-9;    // ln2/256, 29 significant bits
+    const double kLlo = -0x1.718432a1b0e26p-43;  // ln2/256 - kLhi
+    double kd = fma(x, kInvL, kMagic);
+    int k = __double2loint(kd);
+    double kf = kd - kMagic;
+    double r = fma(kf, -kLhi, x);
+    r = fma(kf, -kLlo, r);
+    double t = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+    t = fma(t, r, 0.5);
+    t = fma(t, r, 1.0);
+    double p = t * r;
+    double T = tab[k & 255];
+    double y = fma(T, p, T);
+    int hi = __double2hiint(y) + ((k >> 8) << 20);
+    y = __hiloint2double(hi, __double2loint(y));
+    int xhi = __double2hiint(x);
+    if ((xhi & 0x7fffffff) >= 0x40861800) y = (xhi < 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
+    return y;
+}
+
+// 1/x from the hardware approximation plus one cubic correction: with e = 1 - x y0,
+// 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...).  3 FP64 instructions + 1 MUFU.
+__device__ __forceinline__ double frcp(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    double t = fma(e, e, e);
+    return fma(y, t, y);
+}
+
+// 1 if x is not a positive normal finite double (integer pipe only).
+__device__ __forceinline__ int not_positive_normal(double x)
+{
+    return (unsigned)(__double2hiint(x) - 0x00100000) >= 0x7fe00000u;
+}
+
+// Running product with the binary exponent split off: value = m * 2^e, m in [1, 2).
+struct LogProd {
+    double m;
+    int e;
+};
+
+__device__ __forceinline__ void logprod_mul(LogProd& lp, double x)
+{
+    double q = lp.m * x;
+    int hi = __double2hiint(q);
+    lp.e += (hi >> 20) - 1023;
+    lp.m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(q));
+}
+
+__device__ __forceinline__ double logprod_value(const LogProd& lp)
+{
+    const double kLn2hi = 0x1.62e42ff000000p-1, kLn2lo = -0x1.718432a1b0e26p-35;
+    double e = (double)lp.e;
+    return fma(e, kLn2hi, fma(e, kLn2lo, log(lp.m)));
+}
+
+// ----------------------------------------------------------------------------------
+// Angular basis (paper Sec. 2.4.2, Eq. 3 regrouped by parameter):
+//   A = h0 + FL hFL + S3 h3 + S4 h4 + S5 h5 + AFB h6 + S7 h7 + S8 h8 + S9 h9,
+//   h0 = c sin^2 tK (3/4 + cos 2tl / 4), hFL = c cos^2 tK (1 - cos 2tl) - h0, ...
+// with c = 9/(32 pi).  Also the Chebyshev inputs T2(ctl), T2(ctk), phi/pi, T2(phi/pi).
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi, double h[9], double& t2l,
+                                              double& t2k, double& xp, double& t2p)
+{
+    const double c = 0x1.6eb167b830193p-4;  // 9/(32 pi)
+    const double kInvPi = 0x1.45f306dc9c883p-2;
+    double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);
+    double sl = sqrt(sl2), sk = sqrt(sk2);
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    t2l = fma(2.0 * ctl, ctl, -1.0);
+    t2k = fma(2.0 * ctk, ctk, -1.0);
+    double c2p = fma(2.0 * cp, cp, -1.0);  // cos 2phi
+    double s2p = 2.0 * sp * cp;            // sin 2phi
+    double h0 = c * sk2 * fma(0.25, t2l, 0.75);
+    double a = c * sk2 * sl2;              // c sin^2 tK sin^2 tl
+    double b = 2.0 * c * sk * ctk * sl;    // c sin 2tK sin tl
+    h[0] = h0;
+    h[1] = c * (ctk * ctk) * (1.0 - t2l) - h0;
+    h[2] = a * c2p;                // S3
+    h[3] = 2.0 * b * ctl * cp;     // S4: c sin 2tK sin 2tl cos phi
+    h[4] = b * cp;                 // S5
+    h[5] = (4.0 / 3.0) * c * sk2 * ctl;  // AFB
+    h[6] = b * sp;                 // S7
+    h[7] = 2.0 * b * ctl * sp;     // S8
+    h[8] = a * s2p;                // S9
+    xp = phi * kInvPi;
+    t2p = fma(2.0 * xp, xp, -1.0);
+}
+
+// ----------------------------------------------------------------------------------
+// Per-event bodies.  acc[] slots as documented in gbnll_internal.h.
+// ----------------------------------------------------------------------------------
+template <bool W, bool GRAD>
+__device__ __forceinline__ void event_mass(const KConst& c, double m, double w, double* acc, LogProd& lp,
+                                           int& bad, const double* tab)
+{
+    double d = m - c.mu;
+    double E = fexp(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
+    double P = E + c.b2;
+    bad |= not_positive_normal(P);
+    if (W)
+        acc[0] = fma(w, log(P), acc[0]);
+    else
+        logprod_mul(lp, P);
+    if (GRAD) {
+        double R = frcp(P);
+        if (W) R *= w;
+        double rs = R * E;
+        acc[1] += rs;
+        double rsd = rs * d;
+        acc[2] += rsd;
+        acc[3] = fma(rsd, d, acc[3]);
+        acc[4] += R;
+        acc[5] = fma(R, d, acc[5]);
+    }
+}
+
+template <bool W, bool GRAD>
+__device__ __forceinline__ void event_4d(const KConst& c, double m, const double h[9], double xl, double t2l,
+                                         double xk, double t2k, double xp, double t2p, double w, double* acc,
+                                         LogProd& lp, int& bad, const double* tab)
+{
+    double d = m - c.mu;
+    double E = fexp(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
+    double A = fma(c.ang[0], h[1], h[0]);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) A = fma(c.ang[k], h[k + 1], A);
+    double C1 = fma(c.cq[1], xl, fma(c.cq[2], t2l, c.cq[0]));
+    double C2 = fma(c.cq[4], xk, fma(c.cq[5], t2k, c.cq[3]));
+    double C3 = fma(c.cq[7], xp, fma(c.cq[8], t2p, c.cq[6]));
+    double C12 = C1 * C2;
+    double C = C12 * C3;
+    double s = A * E;
+    double P = s + C;
+    bad |= not_positive_normal(P);
+    if (W)
+        acc[0] = fma(w, log(P), acc[0]);
+    else
+        logprod_mul(lp, P);
+    if (GRAD) {
+        double R = frcp(P);
+        if (W) R *= w;
+        double rE = R * E;
+        double rs = rE * A;
+        acc[1] += rs;
+        double rsd = rs * d;
+        acc[2] += rsd;
+        acc[3] = fma(rsd, d, acc[3]);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[4 + k] = fma(rE, h[k + 1], acc[4 + k]);
+        double re = R * C;
+        acc[12] += re;
+        acc[13] = fma(re, d, acc[13]);
+        double u1 = R * (C2 * C3);
+        double u2 = R * (C1 * C3);
+        double u3 = R * C12;
+        acc[14] = fma(u1, xl, acc[14]);
+        acc[15] = fma(u1, t2l, acc[15]);
+        acc[16] = fma(u2, xk, acc[16]);
+        acc[17] = fma(u2, t2k, acc[17]);
+        acc[18] = fma(u3, xp, acc[18]);
+        acc[19] = fma(u3, t2p, acc[19]);
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// Fixed-order reductions
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Reduce K per-thread values over the block (result valid in threads 0..K-1 as `res`).
+template <int K>
+__device__ __forceinline__ double block_reduce(const double (&v)[K], double* smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) smem[warp * K + k] = s;
+    }
+    __syncthreads();
+    double res = 0.0;
+    if (threadIdx.x < K) {
+        for (int w = 0; w < nwarps; ++w) res += smem[w * K + threadIdx.x];
+    }
+    __syncthreads();
+    return res;
+}
+
+// Block partials -> scratch; the last block to arrive sums them in block order (with
+// Neumaier compensation) into out[0..K).  Returns nothing; resets the ticket.
+template <int K>
+__device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, double* partials,
+                                            unsigned int* ticket, double* out)
+{
+    __shared__ int s_last;
+    const int nb = gridDim.x;
+    double bsum = block_reduce<K>(v, smem);
+    if (threadIdx.x < K) partials[threadIdx.x * nb + blockIdx.x] = bsum;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1));
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // each thread sums a fixed strided subset of blocks for every slot, then a fixed tree
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] += __ldcg(partials + k * nb + b);
+    }
+    double tot = block_reduce<K>(acc, smem);
+    if (threadIdx.x < K) out[threadIdx.x] = tot;
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// ----------------------------------------------------------------------------------
+// The fused kernel
+// ----------------------------------------------------------------------------------
+template <int KIND, int VAR, bool W, bool GRAD>
+__global__ void __launch_bounds__(256) fused_nll_kernel(const KArgs a)
+{
+    constexpr int K = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
+    __shared__ double s_tab[256];
+    __shared__ double s_red[8 * K];
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) s_tab[j] = g_exp2tab[j];
+    __syncthreads();
+
+    double acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = 0.0;
+    LogProd lp{1.0, 0};
+    int bad = 0;
+
+    const int64_t n = a.n;
+    const int64_t npairs = (n + 1) >> 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const KConst& c = a.c;
+
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += stride) {
+        const int64_t i0 = 2 * p;
+        const bool second = (i0 + 1) < n;
+        double2 m2 = __ldg(reinterpret_cast<const double2*>(a.col[kColM]) + p);
+        double2 w2 = make_double2(1.0, 1.0);
+        if (W) w2 = __ldg(reinterpret_cast<const double2*>(a.w) + p);
+        if (KIND == kMass1D) {
+            event_mass<W, GRAD>(c, m2.x, w2.x, acc, lp, bad, s_tab);
+            if (second) event_mass<W, GRAD>(c, m2.y, w2.y, acc, lp, bad, s_tab);
+        } else {
+            double hx[9], hy[9];
+            double t2lx, t2ly, t2kx, t2ky, xpx, xpy, t2px, t2py;
+            double2 l2 = __ldg(reinterpret_cast<const double2*>(a.col[kColCtl]) + p);
+            double2 k2 = __ldg(reinterpret_cast<const double2*>(a.col[kColCtk]) + p);
+            if (VAR == kVarPrecompute) {
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    double2 v = __ldg(reinterpret_cast<const double2*>(a.col[kColH0 + j]) + p);
+                    hx[j] = v.x;
+                    hy[j] = v.y;
+                }
+                double2 v;
+                v = __ldg(reinterpret_cast<const double2*>(a.col[kColT2l]) + p);
+                t2lx = v.x;
+                t2ly = v.y;
+                v = __ldg(reinterpret_cast<const double2*>(a.col[kColT2k]) + p);
+                t2kx = v.x;
+                t2ky = v.y;
+                v = __ldg(reinterpret_cast<const double2*>(a.col[kColXp]) + p);
+                xpx = v.x;
+                xpy = v.y;
+                v = __ldg(reinterpret_cast<const double2*>(a.col[kColT2p]) + p);
+                t2px = v.x;
+                t2py = v.y;
+            } else {
+                double2 f2 = __ldg(reinterpret_cast<const double2*>(a.col[kColPhi]) + p);
+                angular_basis(l2.x, k2.x, f2.x, hx, t2lx, t2kx, xpx, t2px);
+                angular_basis(l2.y, k2.y, f2.y, hy, t2ly, t2ky, xpy, t2py);
+            }
+            event_4d<W, GRAD>(c, m2.x, hx, l2.x, t2lx, k2.x, t2kx, xpx, t2px, w2.x, acc, lp, bad, s_tab);
+            if (second)
+                event_4d<W, GRAD>(c, m2.y, hy, l2.y, t2ly, k2.y, t2ky, xpy, t2py, w2.y, acc, lp, bad, s_tab);
+        }
+    }
+    if (!W) acc[0] = logprod_value(lp);
+    acc[K - 1] = (double)bad;
+    grid_reduce<K>(acc, s_red, a.partials, a.ticket, a.out);
+}
+
+// ----------------------------------------------------------------------------------
+// Load-time statistics and range validation: sum w, sum w (m - ma), events outside.
+// ----------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) stats_kernel(const SArgs a)
+{
+    __shared__ double s_red[8 * 3];
+    double v[3] = {0.0, 0.0, 0.0};
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        double w = a.w ? a.w[i] : 1.0;
+        bool outside = !(w >= 0.0 && w <= 1.0e300);  // also catches NaN
+        for (int d = 0; d < a.ndim; ++d) {
+            double x = a.col[d][i];
+            outside |= !(x >= a.lo[d] && x <= a.hi[d]);
+        }
+        double m = a.col[0][i];
+        v[0] += w;
+        v[1] = fma(w, m - a.lo[0], v[1]);
+        v[2] += outside ? 1.0 : 0.0;
+    }
+    grid_reduce<3>(v, s_red, a.partials, a.ticket, a.out);
+}
+
+// ----------------------------------------------------------------------------------
+// Event-only precompute of the angular basis (paper Sec. 2.4.2), once per sample.
+// ----------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) basis_kernel(const BArgs a)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        double h[9], t2l, t2k, xp, t2p;
+        angular_basis(a.ctl[i], a.ctk[i], a.phi[i], h, t2l, t2k, xp, t2p);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) a.out[j][i] = h[j];
+        a.out[9][i] = t2l;
+        a.out[10][i] = t2k;
+        a.out[11][i] = xp;
+        a.out[12][i] = t2p;
+    }
+}
+
+// ----------------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------------
+int num_acc(int kind, bool grad) { return !grad ? kAccNll : (kind == kMass1D ? kAcc1D : kAcc4D); }
+
+template <int KIND, int VAR>
+static cudaError_t launch_kv(bool weighted, bool grad, int blocks, int threads, cudaStream_t s, const KArgs& a)
+{
+    if (weighted) {
+        if (grad)
+            fused_nll_kernel<KIND, VAR, true, true><<<blocks, threads, 0, s>>>(a);
+        else
+            fused_nll_kernel<KIND, VAR, true, false><<<blocks, threads, 0, s>>>(a);
+    } else {
+        if (grad)
+            fused_nll_kernel<KIND, VAR, false, true><<<blocks, threads, 0, s>>>(a);
+        else
+            fused_nll_kernel<KIND, VAR, false, false><<<blocks, threads, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,
+                         cudaStream_t stream, const KArgs& a)
+{
+    if (threads > 256 || threads < 32 || (threads & 31)) return cudaErrorInvalidValue;
+    if (kind == kMass1D) return launch_kv<kMass1D, kVarPrecompute>(weighted, grad, blocks, threads, stream, a);
+    if (variant == kVarDirect) return launch_kv<kKstar4D, kVarDirect>(weighted, grad, blocks, threads, stream, a);
+    return launch_kv<kKstar4D, kVarPrecompute>(weighted, grad, blocks, threads, stream, a);
+}
+
+cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a)
+{
+    stats_kernel<<<blocks, threads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BArgs& a)
+{
+    basis_kernel<<<blocks, threads, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t upload_exp2_table_values(const double* host256)
+{
+    return cudaMemcpyToSymbol(g_exp2tab, host256, 256 * sizeof(double));
+}
+
+}  // namespace gbnll

@@ -1,0 +1,20 @@
+// minimise.h -- host quasi-Newton minimiser used by fit_minimise / fit_minimise_fcn.
+#pragma once
+
+#include <functional>
+
+#include "../../include/gbnll.h"
+
+namespace gbnll {
+
+// Objective: fills f and g (full external parameter vector) at theta; returns an
+// nll_status (NLL_OK on success; any other value rejects the point).
+using Objective = std::function<int(const double* theta, double* f, double* g)>;
+
+int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double* lo, const double* hi,
+                  const double* step, const int* fixed, const fit_options* opt, fit_result* out);
+
+// Dense symmetric positive-definite inverse by Cholesky; false if not positive definite.
+bool spd_inverse(int n, const double* a, double* inv);
+
+}  // namespace gbnll

@@ -1,0 +1,662 @@
+// runtime.cu -- host side of the C ABI declared in include/gbnll.h.
+//
+// Per minimiser step (paper Sec. 2.1 and 2.4.1) an evaluation
+//   1. validates theta and computes the parameter-only terms on the host (normalisations,
+//      their logarithms and derivatives) into the per-launch constant block,
+//   2. launches one fused kernel that evaluates every event, its log-density and the
+//      per-event gradient sums and reduces them on the device,
+//   3. copies the handful of sums back and assembles NLL and gradient on the host.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gbnll.h"
+#include "gbnll_internal.h"
+#include "minimise.h"
+
+using namespace gbnll;
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+const char* kNames1D[4] = {"mu", "sigma", "alpha", "fsig"};
+const char* kNames4D[18] = {"mu",     "sigma",  "FL",     "S3",     "S4",     "S5",
+                            "AFB",    "S7",     "S8",     "S9",     "alpha",  "c1_ctl",
+                            "c2_ctl", "c1_ctk", "c2_ctk", "c1_phi", "c2_phi", "fsig"};
+
+// Host-side derivative constants for the gradient assembly.
+struct Hoist {
+    KConst k;
+    double mu, sigma, alpha, f, ma;
+    double b0, b2;
+    double dlnN1_dmu, dlnN1_dsig, dlnN2t_dal;
+    double dlnNc_dc2[3];
+};
+
+std::mutex g_table_mutex;
+bool g_table_ready[64];
+
+int ensure_exp2_table(int device)
+{
+    std::lock_guard<std::mutex> lock(g_table_mutex);
+    if (device < 0 || device >= 64) return NLL_ERR_ARG;
+    if (g_table_ready[device]) return NLL_OK;
+    double tab[256];
+    for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
+    if (upload_exp2_table_values(tab) != cudaSuccess) return NLL_ERR_CUDA;
+    g_table_ready[device] = true;
+    return NLL_OK;
+}
+
+}  // namespace
+
+struct nll_model {
+    int kind = 0;
+    int ndim = 0;
+    int npar = 0;
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double ranges[8] = {0};
+
+    // event store
+    int64_t n = 0, n_pad = 0;
+    bool loaded = false, weighted = false, has_basis = false;
+    int ncols = 0;           // event columns allocated before the weights
+    double* d_ev = nullptr;  // kNumCols columns of n_pad doubles (only the used ones allocated)
+    double* d_w = nullptr;
+    size_t ev_bytes = 0;     // bytes used by the current sample
+    size_t ev_capacity = 0;  // bytes allocated at d_ev
+    double sum_w = 0.0, sum_wdm = 0.0;
+
+    // reduction scratch and results
+    int max_blocks = 0;
+    double* d_partials = nullptr;
+    unsigned int* d_ticket = nullptr;
+    double* d_out = nullptr;
+    double* h_out = nullptr;  // pinned
+
+    // launch shape
+    int bps = 2, threads = 256, variant = 0;
+
+    // profiling
+    bool profiling = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double last_ms = -1.0;
+
+    // last valid constant block (for autotuning)
+    bool have_last = false;
+    Hoist last;
+
+    std::string err;
+};
+
+namespace {
+
+int fail(nll_model* m, int status, const char* fmt, ...)
+{
+    if (m) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        m->err = buf;
+    }
+    return status;
+}
+
+int cuda_fail(nll_model* m, cudaError_t e, const char* what)
+{
+    return fail(m, e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+const double* colptr(const nll_model* m, int c) { return m->d_ev ? m->d_ev + (size_t)c * m->n_pad : nullptr; }
+
+// N1 = 1/2 [erf(za) - erf(zb)] with za = (mu-ma)/(sqrt2 sigma), zb = (mu-mb)/(sqrt2 sigma)
+// (paper Eq. 2); evaluated with erfc on the side where both arguments share a sign.
+double gauss_norm(double za, double zb)
+{
+    if (zb > 0.0) return 0.5 * (erfc(zb) - erfc(za));
+    if (za < 0.0) return 0.5 * (erfc(-za) - erfc(-zb));
+    return 0.5 * (erf(za) - erf(zb));
+}
+
+// Parameter-only terms (paper Sec. 2.4.1).  The density is written as
+//   P(x) = exp(alpha (m - ma)) * Ptilde,
+//   Ptilde = A(angles) exp(-b0 d^2 - alpha d + k0) + b2 prod_j Cbar_j(x_j),
+// d = m - mu, b0 = 1/(2 sigma^2), k0 = ln b1 - alpha (mu - ma),
+// b1 = fsig / (sqrt(2 pi) sigma N1), b2 = (1 - fsig) / (Ntilde2 prod_j Nc_j),
+// Ntilde2 = exp(-alpha ma) N2 = expm1(alpha (mb - ma)) / alpha  (mb - ma at alpha = 0),
+// Cbar_j = 1 + c1_j x_j + c2_j (2 x_j^2 - 1), Nc_j = (2 - 2/3 c2_j) (times pi for phi).
+int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
+{
+    memset(&H, 0, sizeof H);
+    for (int k = 0; k < m->npar; ++k)
+        if (!isfinite(th[k])) return fail(m, NLL_ERR_ARG, "parameter %d (%s) is not finite", k,
+                                           m->kind == kMass1D ? kNames1D[k] : kNames4D[k]);
+    const double ma = m->ranges[0], mb = m->ranges[1], D = mb - ma;
+    double mu = th[0], sigma = th[1];
+    double alpha = m->kind == kMass1D ? th[2] : th[10];
+    double f = m->kind == kMass1D ? th[3] : th[17];
+    if (!(sigma > 0.0)) return fail(m, NLL_ERR_ARG, "sigma must be > 0 (got %g)", sigma);
+    if (grad ? !(f > 0.0 && f < 1.0) : !(f >= 0.0 && f <= 1.0))
+        return fail(m, NLL_ERR_ARG, "fsig must be in %s (got %g)", grad ? "(0, 1)" : "[0, 1]", f);
+    double za = (mu - ma) / (sqrt(2.0) * sigma), zb = (mu - mb) / (sqrt(2.0) * sigma);
+    double N1 = gauss_norm(za, zb);
+    if (!(N1 > 1e-300)) return fail(m, NLL_ERR_ARG, "Gaussian normalisation underflows (mu=%g sigma=%g)", mu, sigma);
+    double ea = exp(-za * za), eb = exp(-zb * zb);
+    H.dlnN1_dmu = (ea - eb) / (sqrt(2.0 * kPi) * sigma * N1);
+    H.dlnN1_dsig = -(za * ea - zb * eb) / (sqrt(kPi) * sigma * N1);
+    double t = alpha * D;
+    double Nt2;
+    if (alpha == 0.0) {
+        Nt2 = D;
+        H.dlnN2t_dal = 0.5 * D;
+    } else {
+        Nt2 = expm1(t) / alpha;
+        // d ln Ntilde2 / d alpha = D (1/(1 - e^-t) - 1/t)
+        if (fabs(t) > 1e-3)
+            H.dlnN2t_dal = D * (-1.0 / expm1(-t) - 1.0 / t);
+        else
+            H.dlnN2t_dal = D * (0.5 + t / 12.0 - t * t * t / 720.0 + t * t * t * t * t / 30240.0);
+    }
+    double b0 = 1.0 / (2.0 * sigma * sigma);
+    double lnb1 = (f > 0.0) ? log(f) - 0.5 * log(2.0 * kPi) - log(sigma) - log(N1) : -INFINITY;
+    double b2 = (1.0 - f) / Nt2;
+    if (m->kind == kKstar4D) {
+        for (int j = 0; j < 3; ++j) {
+            double c2 = th[12 + 2 * j];
+            double nc = 2.0 - (2.0 / 3.0) * c2;
+            if (!(nc > 0.0)) return fail(m, NLL_ERR_ARG, "Chebyshev normalisation %d is not positive", j);
+            H.dlnNc_dc2[j] = (-2.0 / 3.0) / nc;
+            b2 /= nc * (j == 2 ? kPi : 1.0);
+        }
+    }
+    // exponent range of the per-event exponential: -b0 d^2 - alpha (m - ma) + ln b1 <= |alpha| D + ln b1
+    if (fabs(alpha) * D + std::max(lnb1, 0.0) > 700.0)
+        return fail(m, NLL_ERR_ARG, "parameter point outside the exponent range (|alpha|(mb-ma)=%g, ln b1=%g)",
+                    fabs(alpha) * D, lnb1);
+    H.mu = mu;
+    H.sigma = sigma;
+    H.alpha = alpha;
+    H.f = f;
+    H.ma = ma;
+    H.b0 = b0;
+    H.b2 = b2;
+    KConst& k = H.k;
+    k.mu = mu;
+    k.neg_b0 = -b0;
+    k.neg_alpha = -alpha;
+    k.k0 = lnb1 - alpha * (mu - ma);
+    k.b2 = b2;
+    if (m->kind == kKstar4D) {
+        for (int j = 0; j < 8; ++j) k.ang[j] = th[2 + j];
+        k.cq[0] = b2;
+        k.cq[1] = b2 * th[11];
+        k.cq[2] = b2 * th[12];
+        k.cq[3] = 1.0;
+        k.cq[4] = th[13];
+        k.cq[5] = th[14];
+        k.cq[6] = 1.0;
+        k.cq[7] = th[15];
+        k.cq[8] = th[16];
+    }
+    return NLL_OK;
+}
+
+int launch_blocks(const nll_model* m, int bps, int threads)
+{
+    int64_t npairs = (m->n + 1) / 2;
+    int64_t need = (npairs + threads - 1) / threads;
+    int64_t b = std::min<int64_t>((int64_t)m->sm_count * bps, std::max<int64_t>(need, 1));
+    return (int)std::min<int64_t>(b, m->max_blocks);
+}
+
+int effective_variant(const nll_model* m)
+{
+    if (m->kind != kKstar4D) return kVarPrecompute;
+    if (m->variant == NLL_VARIANT_DIRECT) return kVarDirect;
+    if (m->variant == NLL_VARIANT_PRECOMPUTE) return m->has_basis ? kVarPrecompute : -1;
+    return m->has_basis ? kVarPrecompute : kVarDirect;
+}
+
+int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int variant, bool record)
+{
+    KArgs a;
+    memset(&a, 0, sizeof a);
+    for (int c = 0; c < kNumCols; ++c) a.col[c] = c < m->ncols ? colptr(m, c) : nullptr;
+    a.w = m->weighted ? m->d_w : nullptr;
+    a.n = m->n;
+    a.c = H.k;
+    a.partials = m->d_partials;
+    a.ticket = m->d_ticket;
+    a.out = m->d_out;
+    int blocks = launch_blocks(m, bps, threads);
+    cudaError_t e;
+    if (record && m->profiling) cudaEventRecord(m->ev0, m->stream);
+    e = launch_fused(m->kind, variant, m->weighted, grad, blocks, threads, m->stream, a);
+    if (e != cudaSuccess) return cuda_fail(m, e, "fused kernel launch");
+    if (record && m->profiling) cudaEventRecord(m->ev1, m->stream);
+    return NLL_OK;
+}
+
+int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out)
+{
+    if (!m) return NLL_ERR_ARG;
+    const bool grad = grad_out != nullptr;
+    if (!theta || !nll_out) return fail(m, NLL_ERR_ARG, "null theta or output");
+    if (n_params != m->npar) return fail(m, NLL_ERR_ARG, "expected %d parameters, got %d", m->npar, n_params);
+    if (!m->loaded) return fail(m, NLL_ERR_STATE, "no events loaded");
+    Hoist H;
+    int st = hoist(m, theta, grad, H);
+    if (st != NLL_OK) return st;
+    m->last = H;
+    m->have_last = true;
+    const int K = num_acc(m->kind, grad);
+    double S[kAccMax] = {0};
+    if (m->n > 0) {
+        int var = effective_variant(m);
+        if (var < 0) return fail(m, NLL_ERR_STATE, "precompute variant requested but no basis was built");
+        if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
+        st = run_fused(m, H, grad, m->bps, m->threads, var, true);
+        if (st != NLL_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(m->h_out, m->d_out, K * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_fail(m, e, "evaluation");
+        if (m->profiling) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, m->ev0, m->ev1) == cudaSuccess) m->last_ms = ms;
+        }
+        memcpy(S, m->h_out, K * sizeof(double));
+    }
+    double bad = S[K - 1];
+    if (bad != 0.0 || !isfinite(S[0])) {
+        *nll_out = INFINITY;
+        if (grad)
+            for (int k = 0; k < m->npar; ++k) grad_out[k] = NAN;
+        return fail(m, NLL_ERR_NONPOSITIVE_PDF, "density not positive for %.0f thread(s) of events", bad);
+    }
+    // ln L = alpha sum w (m - ma) + sum w ln Ptilde
+    double lnL = H.alpha * m->sum_wdm + S[0];
+    *nll_out = -lnL;
+    if (!grad) return NLL_OK;
+    const double two_b0 = 2.0 * H.b0, dma = H.mu - H.ma;
+    std::vector<double> dL(m->npar, 0.0);
+    // mass shape: d ln s / d mu = 2 b0 d - dlnN1/dmu ; d ln s / d sigma = 2 b0 d^2 / sigma - 1/sigma - dlnN1/dsigma
+    dL[0] = two_b0 * S[2] - H.dlnN1_dmu * S[1];
+    dL[1] = two_b0 / H.sigma * S[3] - (1.0 / H.sigma + H.dlnN1_dsig) * S[1];
+    if (m->kind == kMass1D) {
+        double sre = H.b2 * S[4], sred = H.b2 * S[5];
+        dL[2] = sred + dma * sre - H.dlnN2t_dal * sre;
+        dL[3] = S[1] / H.f - sre / (1.0 - H.f);
+    } else {
+        for (int k = 0; k < 8; ++k) dL[2 + k] = S[4 + k];
+        double sre = S[12], sred = S[13];
+        dL[10] = sred + dma * sre - H.dlnN2t_dal * sre;
+        dL[11] = H.b2 * S[14];
+        dL[12] = H.b2 * S[15] - H.dlnNc_dc2[0] * sre;
+        dL[13] = S[16];
+        dL[14] = S[17] - H.dlnNc_dc2[1] * sre;
+        dL[15] = S[18];
+        dL[16] = S[19] - H.dlnNc_dc2[2] * sre;
+        dL[17] = S[1] / H.f - sre / (1.0 - H.f);
+    }
+    for (int k = 0; k < m->npar; ++k) grad_out[k] = -dL[k];
+    return NLL_OK;
+}
+
+// forget the sample; the allocation is kept for reuse unless `release`
+void reset_events(nll_model* m, bool release)
+{
+    if (release && m->d_ev) {
+        cudaFree(m->d_ev);
+        m->d_ev = nullptr;
+        m->ev_capacity = 0;
+    }
+    m->d_w = nullptr;
+    m->loaded = m->weighted = m->has_basis = false;
+    m->n = m->n_pad = 0;
+    m->ncols = 0;
+}
+
+void free_events(nll_model* m) { reset_events(m, true); }
+
+int run_stats(nll_model* m, const double* const* cols, const double* w, int64_t n, double out[3])
+{
+    SArgs s;
+    memset(&s, 0, sizeof s);
+    for (int d = 0; d < m->ndim; ++d) {
+        s.col[d] = cols[d];
+        s.lo[d] = m->ranges[2 * d];
+        s.hi[d] = m->ranges[2 * d + 1];
+    }
+    s.w = w;
+    s.n = n;
+    s.ndim = m->ndim;
+    s.partials = m->d_partials;
+    s.ticket = m->d_ticket;
+    s.out = m->d_out;
+    int blocks = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), (int64_t)m->sm_count * 2);
+    blocks = std::min(blocks, m->max_blocks);
+    cudaError_t e = launch_stats(blocks, 256, m->stream, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_out, m->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return cuda_fail(m, e, "load statistics");
+    memcpy(out, m->h_out, 3 * sizeof(double));
+    return NLL_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t cuda_stream, nll_model** out)
+{
+    if (!out) return NLL_ERR_ARG;
+    *out = nullptr;
+    if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges) return NLL_ERR_ARG;
+    double ma = obs_ranges[0], mb = obs_ranges[1];
+    if (!(isfinite(ma) && isfinite(mb) && ma < mb)) return NLL_ERR_ARG;
+    if (kind == NLL_MODEL_KSTARMUMU4D) {
+        const double want[6] = {-1.0, 1.0, -1.0, 1.0, -kPi, kPi};
+        for (int i = 0; i < 6; ++i)
+            if (fabs(obs_ranges[2 + i] - want[i]) > 1e-12) return NLL_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
+    nll_model* m = new nll_model();
+    m->kind = kind;
+    m->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
+    m->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
+    m->device = device;
+    memcpy(m->ranges, obs_ranges, sizeof(double) * 2 * m->ndim);
+    if (kind == NLL_MODEL_KSTARMUMU4D) {
+        m->ranges[6] = -kPi;
+        m->ranges[7] = kPi;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete m;
+        return NLL_ERR_CUDA;
+    }
+    m->sm_count = prop.multiProcessorCount;
+    m->max_blocks = m->sm_count * 32;
+    int st = ensure_exp2_table(device);
+    if (st != NLL_OK) {
+        delete m;
+        return st;
+    }
+    cudaError_t e = cudaSuccess;
+    if (cuda_stream) {
+        m->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
+        m->own_stream = true;
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_partials, sizeof(double) * kAccMax * m->max_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_ticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(m->d_ticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_out, sizeof(double) * kAccMax);
+    if (e == cudaSuccess) e = cudaMallocHost(&m->h_out, sizeof(double) * kAccMax);
+    if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
+    if (e != cudaSuccess) {
+        int code = e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA;
+        nll_destroy(m);
+        return code;
+    }
+    *out = m;
+    return NLL_OK;
+}
+
+void nll_destroy(nll_model* m)
+{
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    free_events(m);
+    if (m->d_partials) cudaFree(m->d_partials);
+    if (m->d_ticket) cudaFree(m->d_ticket);
+    if (m->d_out) cudaFree(m->d_out);
+    if (m->h_out) cudaFreeHost(m->h_out);
+    if (m->ev0) cudaEventDestroy(m->ev0);
+    if (m->ev1) cudaEventDestroy(m->ev1);
+    if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
+    delete m;
+}
+
+int nll_load_events(nll_model* m, const double* const* columns, const double* weights, int64_t n_events,
+                    int on_device, int precompute)
+{
+    if (!m) return NLL_ERR_ARG;
+    if (n_events < 0 || (n_events > 0 && !columns)) return fail(m, NLL_ERR_ARG, "bad event count or columns");
+    for (int d = 0; d < m->ndim && n_events > 0; ++d)
+        if (!columns[d]) return fail(m, NLL_ERR_ARG, "column %d is NULL", d);
+    if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
+    cudaStreamSynchronize(m->stream);
+    reset_events(m, false);
+    const bool basis = (m->kind == kKstar4D) && precompute;
+    const int64_t n_pad = std::max<int64_t>((n_events + 63) / 64 * 64, 64);
+    // columns: mass model m [+ w]; 4D: m, ctl, ctk, phi [+ basis 13] [+ w]
+    int ncols = m->kind == kMass1D ? 1 : (basis ? kNumCols : 4);
+    int nalloc = ncols + (weights ? 1 : 0);
+    size_t bytes = sizeof(double) * (size_t)n_pad * nalloc;
+    cudaError_t e = cudaSuccess;
+    if (bytes > m->ev_capacity) {
+        reset_events(m, true);
+        e = cudaMalloc(&m->d_ev, bytes);
+        if (e != cudaSuccess) {
+            m->d_ev = nullptr;
+            return cuda_fail(m, e, "event store allocation");
+        }
+        m->ev_capacity = bytes;
+    }
+    m->ev_bytes = bytes;
+    m->n_pad = n_pad;
+    m->ncols = ncols;
+    if (n_events < n_pad) {  // zero the padding tail of every column
+        for (int c = 0; c < nalloc && e == cudaSuccess; ++c)
+            e = cudaMemsetAsync(m->d_ev + (size_t)c * n_pad + n_events, 0,
+                                sizeof(double) * (size_t)(n_pad - n_events), m->stream);
+    }
+    cudaMemcpyKind kindc = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int d = 0; d < m->ndim && e == cudaSuccess && n_events > 0; ++d)
+        e = cudaMemcpyAsync(m->d_ev + (size_t)d * n_pad, columns[d], sizeof(double) * n_events, kindc, m->stream);
+    if (weights) {
+        m->d_w = m->d_ev + (size_t)ncols * n_pad;
+        if (e == cudaSuccess && n_events > 0)
+            e = cudaMemcpyAsync(m->d_w, weights, sizeof(double) * n_events, kindc, m->stream);
+    }
+    if (e != cudaSuccess) {
+        free_events(m);
+        return cuda_fail(m, e, "event copy");
+    }
+    m->n = n_events;
+    m->weighted = weights != nullptr;
+    double stats[3] = {0.0, 0.0, 0.0};
+    if (n_events > 0) {
+        const double* dcols[4];
+        for (int d = 0; d < m->ndim; ++d) dcols[d] = m->d_ev + (size_t)d * n_pad;
+        int st = run_stats(m, dcols, m->d_w, n_events, stats);
+        if (st != NLL_OK) {
+            free_events(m);
+            return st;
+        }
+        if (stats[2] != 0.0) {
+            free_events(m);
+            return fail(m, NLL_ERR_ARG, "%.0f event(s) outside the observable ranges or with invalid weights",
+                        stats[2]);
+        }
+    }
+    m->sum_w = stats[0];
+    m->sum_wdm = stats[1];
+    if (basis && n_events > 0) {
+        BArgs b;
+        b.ctl = colptr(m, kColCtl);
+        b.ctk = colptr(m, kColCtk);
+        b.phi = colptr(m, kColPhi);
+        for (int j = 0; j < 13; ++j) b.out[j] = m->d_ev + (size_t)(kColH0 + j) * n_pad;
+        b.n = n_events;
+        int blocks = (int)std::min<int64_t>((n_events + 255) / 256, (int64_t)m->sm_count * 8);
+        e = launch_basis(std::max(blocks, 1), 256, m->stream, b);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) {
+            free_events(m);
+            return cuda_fail(m, e, "basis precompute");
+        }
+    }
+    m->has_basis = basis;
+    m->loaded = true;
+    m->err.clear();
+    return NLL_OK;
+}
+
+int nll_eval(nll_model* m, const double* theta, int n_params, double* nll_out)
+{
+    return eval_impl(m, theta, n_params, nll_out, nullptr);
+}
+
+int nll_eval_grad(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out)
+{
+    if (m && !grad_out) return fail(m, NLL_ERR_ARG, "null gradient output");
+    return eval_impl(m, theta, n_params, nll_out, grad_out);
+}
+
+int fit_minimise(nll_model* m, const double* theta0, const double* lo, const double* hi, const double* step,
+                 const int* fixed, int n_params, const fit_options* opt, fit_result* out)
+{
+    if (!m || !out) return NLL_ERR_ARG;
+    if (n_params != m->npar) return fail(m, NLL_ERR_ARG, "expected %d parameters", m->npar);
+    Objective obj = [m, n_params](const double* th, double* f, double* g) {
+        return nll_eval_grad(m, th, n_params, f, g);
+    };
+    return bfgs_minimise(obj, n_params, theta0, lo, hi, step, fixed, opt, out);
+}
+
+int nll_num_params(const nll_model* m) { return m ? m->npar : -1; }
+
+const char* nll_param_name(const nll_model* m, int i)
+{
+    if (!m || i < 0 || i >= m->npar) return "";
+    return m->kind == kMass1D ? kNames1D[i] : kNames4D[i];
+}
+
+const char* nll_last_error(const nll_model* m) { return m ? m->err.c_str() : "null model"; }
+
+int nll_set_launch(nll_model* m, int blocks_per_sm, int threads_per_block, int variant)
+{
+    if (!m) return NLL_ERR_ARG;
+    if (blocks_per_sm < 0 || blocks_per_sm > 32) return fail(m, NLL_ERR_ARG, "blocks_per_sm out of range");
+    if (threads_per_block != 0 &&
+        (threads_per_block < 64 || threads_per_block > 256 || (threads_per_block % 64) != 0))
+        return fail(m, NLL_ERR_ARG, "threads_per_block must be 64, 128, 192 or 256");
+    if (variant < 0 || variant > 2) return fail(m, NLL_ERR_ARG, "unknown variant");
+    if (blocks_per_sm) m->bps = blocks_per_sm;
+    if (threads_per_block) m->threads = threads_per_block;
+    if (variant) m->variant = variant;
+    return NLL_OK;
+}
+
+int nll_get_launch(const nll_model* m, int* blocks_per_sm, int* threads_per_block, int* variant, int* sm_count)
+{
+    if (!m) return NLL_ERR_ARG;
+    if (blocks_per_sm) *blocks_per_sm = m->bps;
+    if (threads_per_block) *threads_per_block = m->threads;
+    if (variant) *variant = effective_variant(m);
+    if (sm_count) *sm_count = m->sm_count;
+    return NLL_OK;
+}
+
+int nll_autotune(nll_model* m)
+{
+    if (!m) return NLL_ERR_ARG;
+    if (!m->loaded || !m->have_last || m->n == 0)
+        return fail(m, NLL_ERR_STATE, "autotune needs loaded events and one prior evaluation");
+    if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
+    const int shapes[][2] = {{1, 256}, {2, 256}, {3, 256}, {4, 256}, {6, 256}, {8, 256},
+                             {2, 128}, {4, 128}, {6, 128}, {8, 128}, {12, 128}, {16, 128}};
+    std::vector<int> variants;
+    if (m->kind == kKstar4D && m->has_basis && m->variant == NLL_VARIANT_AUTO) {
+        variants.push_back(kVarPrecompute);
+        variants.push_back(kVarDirect);
+    } else {
+        variants.push_back(effective_variant(m));
+    }
+    bool grad = m->last.f > 0.0 && m->last.f < 1.0;
+    float best = 1e30f;
+    int best_bps = m->bps, best_thr = m->threads, best_var = variants[0];
+    for (int var : variants)
+        for (auto& sh : shapes) {
+            float tot = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                cudaEventRecord(m->ev0, m->stream);
+                int st = run_fused(m, m->last, grad, sh[0], sh[1], var, false);
+                if (st != NLL_OK) return st;
+                cudaEventRecord(m->ev1, m->stream);
+                cudaError_t e = cudaEventSynchronize(m->ev1);
+                if (e != cudaSuccess) return cuda_fail(m, e, "autotune");
+                float ms;
+                cudaEventElapsedTime(&ms, m->ev0, m->ev1);
+                if (rep > 0) tot += ms;  // first launch of a shape is a warm-up
+            }
+            if (tot < best) {
+                best = tot;
+                best_bps = sh[0];
+                best_thr = sh[1];
+                best_var = var;
+            }
+        }
+    m->bps = best_bps;
+    m->threads = best_thr;
+    if (variants.size() > 1) m->variant = best_var == kVarDirect ? NLL_VARIANT_DIRECT : NLL_VARIANT_PRECOMPUTE;
+    return NLL_OK;
+}
+
+int nll_set_profiling(nll_model* m, int on)
+{
+    if (!m) return NLL_ERR_ARG;
+    m->profiling = on != 0;
+    m->last_ms = -1.0;
+    return NLL_OK;
+}
+
+int nll_last_kernel_ms(const nll_model* m, double* ms)
+{
+    if (!m || !ms) return NLL_ERR_ARG;
+    if (m->last_ms < 0.0) return NLL_ERR_STATE;
+    *ms = m->last_ms;
+    return NLL_OK;
+}
+
+int nll_precomputed_basis(nll_model* m, double* out)
+{
+    if (!m || !out) return NLL_ERR_ARG;
+    if (!m->has_basis) return fail(m, NLL_ERR_STATE, "no precomputed basis");
+    if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
+    std::vector<double> col((size_t)m->n);
+    for (int j = 0; j < 13; ++j) {
+        cudaError_t e = cudaMemcpyAsync(col.data(), colptr(m, kColH0 + j), sizeof(double) * m->n,
+                                        cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_fail(m, e, "basis copy");
+        for (int64_t i = 0; i < m->n; ++i) out[i * 13 + j] = col[i];
+    }
+    return NLL_OK;
+}
+
+}  // extern "C"

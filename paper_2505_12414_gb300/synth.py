@@ -44,6 +44,7 @@ RANGES_1D_GEV = np.array([5.0, 7.0])
 TRUTH_1D_GEV = np.array([5.28, 0.06, -1.0, 0.3])
 
 _M64 = (1 << 64) - 1
+_BATCH = 1 << 23  # largest candidate batch of the accept-reject loops
 _GAMMA = 0x9E3779B97F4A7C15
 
 
@@ -84,7 +85,7 @@ class Stream:
 def _gauss_trunc(rs: Stream, n: int, mu: float, sigma: float, lo: float, hi: float) -> np.ndarray:
     out = np.empty(0)
     while len(out) < n:
-        k = max(2 * (n - len(out)), 64)
+        k = min(max(2 * (n - len(out)), 64), _BATCH)
         u1, u2 = rs.uniform(k), rs.uniform(k)
         z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)  # Box-Muller
         m = mu + sigma * z
@@ -104,7 +105,7 @@ def _cheb_trunc(rs: Stream, n: int, c1: float, c2: float) -> np.ndarray:
     bound = 1.0 + abs(c1) + abs(c2)
     out = np.empty(0)
     while len(out) < n:
-        k = max(2 * (n - len(out)), 64)
+        k = min(max(2 * (n - len(out)), 64), _BATCH)
         x = 2.0 * rs.uniform(k) - 1.0
         y = bound * rs.uniform(k)
         dens = 1.0 + c1 * x + c2 * (2.0 * x * x - 1.0)
@@ -134,7 +135,7 @@ def _angles_signal(rs: Stream, n: int, ang) -> tuple:
     acc = [np.empty(0)] * 3
     have = 0
     while have < n:
-        k = max(12 * (n - have), 256)
+        k = min(max(12 * (n - have), 256), _BATCH)
         ctl = 2.0 * rs.uniform(k) - 1.0
         ctk = 2.0 * rs.uniform(k) - 1.0
         phi = math.pi * (2.0 * rs.uniform(k) - 1.0)

@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER_DIR = os.path.join(ROOT, "include")
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(HEADER_DIR)):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(HEADER_DIR, fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char|double|int64_t)\s*\**\s*(\w+)\s*\(", text, re.M):
+            names.append(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2505_12414_gb300 import build
+
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("nll_create_model", "nll_load_events", "nll_eval", "nll_eval_grad", "fit_minimise"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_library_targets_sm_103a():
+    from paper_2505_12414_gb300 import build
+
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
+    lib.nll_num_params.argtypes = [ctypes.c_void_p]
+    assert lib.nll_num_params(None) == -1
+    lib.nll_destroy.argtypes = [ctypes.c_void_p]
+    lib.nll_destroy(None)  # accepted
+    h = ctypes.c_void_p()
+    r = (ctypes.c_double * 2)(5170.0, 5970.0)
+    lib.nll_create_model.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_size_t,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    assert lib.nll_create_model(7, r, 0, 0, ctypes.byref(h)) == 1  # unknown kind -> NLL_ERR_ARG
+    bad = (ctypes.c_double * 2)(5970.0, 5170.0)
+    assert lib.nll_create_model(1, bad, 0, 0, ctypes.byref(h)) == 1
+    assert h.value is None
