@@ -49,15 +49,16 @@ METRIC = "events/s per NLL+grad eval (4D, 1M ev, FP64)"
 #                  u1..u3 (3 mul) and 6 FMA                        = 15
 #   running product of P (1 mul)                                   =  1
 #  => 82 flops of arithmetic, plus one exponential and one reciprocal per event charged
-#  at the cost of CUDA's own exp() and 1.0/x measured on GB300 in DFMA issue slots
-#  (2 flops each): c_exp and c_rcp below (calibration in profiles/fp64_calibration.md).
+#  at the cost of CUDA's own exp() and 1.0/x on GB300, in DFMA issue slots of 2 flops:
+#  16.0 and 4.7 slots, measured once with nll_calibrate_fp64 (exp: 1.5996e1 slots; division:
+#  5.688 slots including one DADD) and frozen here (profiles/fp64_calibration.md).
 ARITH_FLOPS_4D = 82.0
-C_EXP_DFMA = 12.0   # calibrated: DFMA-equivalent issue slots of CUDA exp() on GB300
-C_RCP_DFMA = 8.0    # calibrated: DFMA-equivalent issue slots of CUDA 1.0/x on GB300
+C_EXP_DFMA = 16.0
+C_RCP_DFMA = 4.7
 FLOPS_PER_EVENT = ARITH_FLOPS_4D + 2.0 * (C_EXP_DFMA + C_RCP_DFMA)
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (no FP64 entry in MEASURED_PEAKS.json)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, for context; the roofline peak is measured live
 # DRAM traffic of one fused-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum,
-# one ncu capture); None until measured for the current kernel.
+# one ncu capture of the same launch shape); None until measured for the current kernel.
 KERNEL_TRAFFIC_BYTES = None
 
 
@@ -69,6 +70,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the launch shape given below")
+    ap.add_argument("--bps", type=int, default=2, help="blocks per SM without autotuning")
+    ap.add_argument("--threads", type=int, default=128, help="threads per block without autotuning")
     return ap.parse_args()
 
 
@@ -203,8 +207,13 @@ def run_ours(args):
     model.load(cols, precompute=True)
     th = thetas(args.warmup + args.steps)
     model.eval_grad(th[0])
-    g.nll_autotune(model.handle)
+    if args.no_autotune:
+        g.nll_set_launch(model.handle, args.bps, args.threads, 0)
+    else:
+        g.nll_autotune(model.handle)
     launch = g.nll_get_launch(model.handle)
+    rates = g.nll_calibrate_fp64(local)
+    peak = 2.0 * rates["dfma"] / 1e12
     g.nll_set_profiling(model.handle, True)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -249,7 +258,7 @@ def run_ours(args):
         pinned.append(t.numpy())
     e2e_ms = []
     g.nll_set_profiling(model.handle, False)
-    for i in range(args.e2e_steps + 2):
+    for i in range(args.e2e_steps + 2 if args.e2e_steps > 0 else 0):
         flush.zero_()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
@@ -259,7 +268,7 @@ def run_ours(args):
         s1.synchronize()
         if i >= 2:
             e2e_ms.append(s0.elapsed_time(s1))
-    e2e_step = statistics.median(e2e_ms)
+    e2e_step = statistics.median(e2e_ms) if e2e_ms else float("nan")
     if world > 1:
         t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -267,11 +276,14 @@ def run_ours(args):
 
     kms = statistics.median(kernel_ms)
     achieved = FLOPS_PER_EVENT * N_EVENTS / (kms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": KERNEL_TRAFFIC_BYTES,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": KERNEL_TRAFFIC_BYTES,
                 "kernel": "fused_nll_kernel<4D, precompute, grad>", "kernel_ms": kms,
-                "peak_source": "nominal FP64 1.25 TFLOP/s (no FP64 entry in MEASURED_PEAKS.json)",
-                "flops_per_event": FLOPS_PER_EVENT}
+                "peak_source": "measured: 2 x DFMA/s of nll_calibrate_fp64 in this run (nominal %.2f)"
+                               % FP64_NOMINAL_TFLOPS,
+                "flops_per_event": FLOPS_PER_EVENT,
+                "calibration": {"dfma_per_s": rates["dfma"], "cuda_exp_slots": rates["dfma"] / rates["cuda_exp"],
+                                "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}
 
     if rank == 0:
         cpu = None

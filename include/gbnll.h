@@ -69,7 +69,9 @@ typedef enum { NLL_VARIANT_AUTO = 0, NLL_VARIANT_PRECOMPUTE = 1, NLL_VARIANT_DIR
  *                KSTARMUMU4D (the angular ranges must be exactly these; ma < mb finite).
  *                Paper Sec. 2.4.1 normalises over a fixed observable range.
  *   cuda_stream  a cudaStream_t cast to uintptr_t on which every launch and copy of this
- *                model is issued; 0 = the library creates and owns a non-blocking stream.
+ *                model is issued; 0 is CUDA's default (legacy) stream, as everywhere in CUDA
+ *                (torch's default stream also has handle 0).  The stream is borrowed: the
+ *                caller keeps it alive until nll_destroy().
  *   out          receives the model handle (NULL on error).
  * Errors: NLL_ERR_ARG (kind, ranges), NLL_ERR_CUDA (device), NLL_ERR_OOM.
  */
@@ -183,6 +185,18 @@ int nll_last_kernel_ms(const nll_model* m, double* ms);
  * and T2(x) = 2x^2 - 1.  NLL_ERR_STATE if no basis was built.
  */
 int nll_precomputed_basis(nll_model* m, double* out);
+
+/*
+ * nll_calibrate_fp64 -- diagnostic: FP64 throughput of device `device`, measured with
+ * independent dependency chains over 8 blocks of 256 threads per SM (about 0.1 s).
+ *   rates        host array of 6 doubles, operations per second of:
+ *                [0] DFMA, [1] CUDA exp(), [2] CUDA 1.0/x (plus one DADD), [3] CUDA log()
+ *                (plus one DADD), [4] the library's table exp, [5] the library's reciprocal
+ *                (plus one DADD).  2 * rates[0] is the FP64 roofline in flop/s; rates[0] /
+ *                rates[i] is the cost of operation i in DFMA issue slots.
+ * The fused kernels are FP64-issue bound (see DESIGN), so this is their roofline.
+ */
+int nll_calibrate_fp64(int device, double* rates);
 
 #ifdef __cplusplus
 }

@@ -6,7 +6,7 @@ raise.  Function names match the C ABI in include/gbnll.h.
 
 Inputs may be numpy arrays (host memory, copied by the library) or CUDA torch tensors
 (device memory on the model's device, copied device-to-device).  Streams: pass
-``torch.cuda.current_stream().cuda_stream`` (or 0 for a library-owned stream).
+``torch.cuda.current_stream().cuda_stream`` (0, CUDA's default stream, is the default).
 """
 import ctypes
 import os
@@ -92,6 +92,7 @@ def load(path=None):
     L.nll_set_profiling.argtypes = [vp, ctypes.c_int]
     L.nll_last_kernel_ms.argtypes = [vp, _DP]
     L.nll_precomputed_basis.argtypes = [vp, _DP]
+    L.nll_calibrate_fp64.argtypes = [ctypes.c_int, _DP]
     _lib = L
     return L
 
@@ -290,6 +291,16 @@ def nll_precomputed_basis(model, n_events):
     out = np.zeros((int(n_events), 13))
     _check(model, load().nll_precomputed_basis(model, _p(out)))
     return out
+
+
+def nll_calibrate_fp64(device=0):
+    """FP64 throughput of the device: dict of operations/s (see include/gbnll.h)."""
+    r = np.zeros(6)
+    st = load().nll_calibrate_fp64(int(device), _p(r))
+    if st != NLL_OK:
+        raise NLLError(st, "nll_calibrate_fp64 failed")
+    keys = ["dfma", "cuda_exp", "cuda_div_plus_dadd", "cuda_log_plus_dadd", "lib_exp", "lib_rcp_plus_dadd"]
+    return dict(zip(keys, r.tolist()))
 
 
 class Model:

@@ -1,0 +1,94 @@
+// calibrate.cu -- FP64 throughput calibration on the current GPU (diagnostic entry point).
+//
+// The fused kernels are bound by the FP64 pipe, so their roofline is the FP64 issue rate.
+// nll_calibrate_fp64 measures it with independent DFMA chains, and measures CUDA's own
+// exp(), log() and 1.0/x and this library's fexp / frcp in the same way, so that the cost
+// of a transcendental can be expressed in DFMA issue slots on the running GPU.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "../../include/gbnll.h"
+#include "fp64_math.cuh"
+
+namespace {
+
+constexpr int kChains = 8;
+
+__device__ double g_cal_tab[256];
+
+template <int OP>
+__global__ void __launch_bounds__(256) cal_kernel(double* out, int iters, double a)
+{
+    __shared__ double s_tab[256];
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) s_tab[j] = g_cal_tab[j];
+    __syncthreads();
+    const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 0.5 + 1e-3 * (c + (gid & 7));
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) {
+            if (OP == 0) x[c] = fma(x[c], a, 0.25);            // DFMA
+            if (OP == 1) x[c] = exp(-x[c]);                    // CUDA exp
+            if (OP == 2) x[c] = 1.0 / (x[c] + 1.0);            // CUDA division (+1 DADD)
+            if (OP == 3) x[c] = log(x[c] + 3.0);               // CUDA log (+1 DADD)
+            if (OP == 4) x[c] = gbnll::fexp(-x[c], s_tab);     // library exp
+            if (OP == 5) x[c] = gbnll::frcp(x[c] + 1.0);       // library reciprocal (+1 DADD)
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    out[gid] = s;
+}
+
+template <int OP>
+cudaError_t time_op(double* out, int blocks, int iters, double a, float* ms)
+{
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    cal_kernel<OP><<<blocks, 256>>>(out, iters, a);  // warm-up
+    cudaEventRecord(e0);
+    for (int r = 0; r < 3; ++r) cal_kernel<OP><<<blocks, 256>>>(out, iters, a);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventElapsedTime(ms, e0, e1);
+    *ms /= 3.0f;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+}  // namespace
+
+extern "C" int nll_calibrate_fp64(int device, double* rates)
+{
+    if (!rates) return NLL_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return NLL_ERR_CUDA;
+    double tab[256];
+    for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
+    if (cudaMemcpyToSymbol(g_cal_tab, tab, sizeof tab) != cudaSuccess) return NLL_ERR_CUDA;
+    const int blocks = p.multiProcessorCount * 8;
+    double* out = nullptr;
+    if (cudaMalloc(&out, sizeof(double) * blocks * 256) != cudaSuccess) return NLL_ERR_OOM;
+    const int it_fast = 4096, it_slow = 256;
+    float ms[6] = {0};
+    cudaError_t e = time_op<0>(out, blocks, it_fast, 0.999999, &ms[0]);
+    if (e == cudaSuccess) e = time_op<1>(out, blocks, it_slow, 0.0, &ms[1]);
+    if (e == cudaSuccess) e = time_op<2>(out, blocks, it_slow, 0.0, &ms[2]);
+    if (e == cudaSuccess) e = time_op<3>(out, blocks, it_slow, 0.0, &ms[3]);
+    if (e == cudaSuccess) e = time_op<4>(out, blocks, it_slow, 0.0, &ms[4]);
+    if (e == cudaSuccess) e = time_op<5>(out, blocks, it_slow, 0.0, &ms[5]);
+    cudaFree(out);
+    if (e != cudaSuccess) return NLL_ERR_CUDA;
+    const double per = (double)blocks * 256 * kChains;
+    const int iters[6] = {it_fast, it_slow, it_slow, it_slow, it_slow, it_slow};
+    for (int i = 0; i < 6; ++i) rates[i] = per * iters[i] / (ms[i] * 1e-3);
+    return NLL_OK;
+}

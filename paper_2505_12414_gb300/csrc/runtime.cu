@@ -402,12 +402,8 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
         return st;
     }
     cudaError_t e = cudaSuccess;
-    if (cuda_stream) {
-        m->stream = (cudaStream_t)cuda_stream;
-    } else {
-        e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking);
-        m->own_stream = true;
-    }
+    m->stream = (cudaStream_t)cuda_stream;  // 0: CUDA's default stream
+    m->own_stream = false;
     if (e == cudaSuccess) e = cudaMalloc(&m->d_partials, sizeof(double) * kAccMax * m->max_blocks);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(m->d_ticket, 0, sizeof(unsigned int));
