@@ -56,7 +56,10 @@ ARITH_FLOPS_4D = 82.0
 C_EXP_DFMA = 16.0
 C_RCP_DFMA = 4.7
 FLOPS_PER_EVENT = ARITH_FLOPS_4D + 2.0 * (C_EXP_DFMA + C_RCP_DFMA)
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, for context; the roofline peak is measured live
+# FP64 peak from the recipe's unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+# = 1.26 TFLOP/s, the nominal 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry).  ncu's
+# FP64-pipe peak is the same 2 DFMA/clk/SM.
+FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of one fused-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum,
 # one ncu capture of the same launch shape); None until measured for the current kernel.
 KERNEL_TRAFFIC_BYTES = None
@@ -213,7 +216,7 @@ def run_ours(args):
         g.nll_autotune(model.handle)
     launch = g.nll_get_launch(model.handle)
     rates = g.nll_calibrate_fp64(local)
-    peak = 2.0 * rates["dfma"] / 1e12
+    peak = FP64_PEAK_TFLOPS
     g.nll_set_profiling(model.handle, True)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -279,8 +282,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": KERNEL_TRAFFIC_BYTES,
                 "kernel": "fused_nll_kernel<4D, precompute, grad>", "kernel_ms": kms,
-                "peak_source": "measured: 2 x DFMA/s of nll_calibrate_fp64 in this run (nominal %.2f)"
-                               % FP64_NOMINAL_TFLOPS,
+                "peak_source": "recipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
                 "flops_per_event": FLOPS_PER_EVENT,
                 "calibration": {"dfma_per_s": rates["dfma"], "cuda_exp_slots": rates["dfma"] / rates["cuda_exp"],
                                 "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}

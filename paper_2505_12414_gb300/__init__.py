@@ -93,6 +93,7 @@ def load(path=None):
     L.nll_last_kernel_ms.argtypes = [vp, _DP]
     L.nll_precomputed_basis.argtypes = [vp, _DP]
     L.nll_calibrate_fp64.argtypes = [ctypes.c_int, _DP]
+    L.nll_diag_math.argtypes = [ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int64]
     _lib = L
     return L
 
@@ -301,6 +302,16 @@ def nll_calibrate_fp64(device=0):
         raise NLLError(st, "nll_calibrate_fp64 failed")
     keys = ["dfma", "cuda_exp", "cuda_div_plus_dadd", "cuda_log_plus_dadd", "lib_exp", "lib_rcp_plus_dadd"]
     return dict(zip(keys, r.tolist()))
+
+
+def nll_diag_math(fn, x, device=0):
+    """Evaluate the library's device exp (fn=0) or reciprocal (fn=1) on host array x."""
+    xa = _f64(x)
+    y = np.zeros_like(xa)
+    st = load().nll_diag_math(int(device), int(fn), _p(xa), _p(y), len(xa))
+    if st != NLL_OK:
+        raise NLLError(st, "nll_diag_math failed")
+    return y
 
 
 class Model:

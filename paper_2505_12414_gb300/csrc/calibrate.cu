@@ -14,13 +14,13 @@ namespace {
 
 constexpr int kChains = 8;
 
-__device__ double g_cal_tab[256];
+__device__ double g_cal_tab[gbnll::kExpTable];
 
 template <int OP>
 __global__ void __launch_bounds__(256) cal_kernel(double* out, int iters, double a)
 {
-    __shared__ double s_tab[256];
-    for (int j = threadIdx.x; j < 256; j += blockDim.x) s_tab[j] = g_cal_tab[j];
+    __shared__ double s_tab[gbnll::kExpTable];
+    for (int j = threadIdx.x; j < gbnll::kExpTable; j += blockDim.x) s_tab[j] = g_cal_tab[j];
     __syncthreads();
     const int gid = blockIdx.x * blockDim.x + threadIdx.x;
     double x[kChains];
@@ -63,7 +63,48 @@ cudaError_t time_op(double* out, int blocks, int iters, double a, float* ms)
     return e;
 }
 
+cudaError_t upload_table()
+{
+    static double tab[gbnll::kExpTable];
+    for (int j = 0; j < gbnll::kExpTable; ++j)
+        tab[j] = (double)exp2l((long double)j / (long double)gbnll::kExpTable);
+    return cudaMemcpyToSymbol(g_cal_tab, tab, sizeof tab);
+}
+
+__global__ void __launch_bounds__(256) diag_kernel(int fn, const double* x, double* y, int64_t n)
+{
+    __shared__ double s_tab[gbnll::kExpTable];
+    for (int j = threadIdx.x; j < gbnll::kExpTable; j += blockDim.x) s_tab[j] = g_cal_tab[j];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fn == 0 ? gbnll::fexp(x[i], s_tab) : gbnll::frcp(x[i]);
+}
+
 }  // namespace
+
+extern "C" int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n)
+{
+    if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!x || !y))) return NLL_ERR_ARG;
+    if (n == 0) return NLL_OK;
+    if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
+    if (upload_table() != cudaSuccess) return NLL_ERR_CUDA;
+    double *dx = nullptr, *dy = nullptr;
+    if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess) return NLL_ERR_OOM;
+    if (cudaMalloc(&dy, sizeof(double) * n) != cudaSuccess) {
+        cudaFree(dx);
+        return NLL_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+        diag_kernel<<<blocks, 256>>>(fn, dx, dy, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dy);
+    return e == cudaSuccess ? NLL_OK : NLL_ERR_CUDA;
+}
 
 extern "C" int nll_calibrate_fp64(int device, double* rates)
 {
@@ -71,9 +112,7 @@ extern "C" int nll_calibrate_fp64(int device, double* rates)
     if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
     cudaDeviceProp p;
     if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return NLL_ERR_CUDA;
-    double tab[256];
-    for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
-    if (cudaMemcpyToSymbol(g_cal_tab, tab, sizeof tab) != cudaSuccess) return NLL_ERR_CUDA;
+    if (upload_table() != cudaSuccess) return NLL_ERR_CUDA;
     const int blocks = p.multiProcessorCount * 8;
     double* out = nullptr;
     if (cudaMalloc(&out, sizeof(double) * blocks * 256) != cudaSuccess) return NLL_ERR_OOM;

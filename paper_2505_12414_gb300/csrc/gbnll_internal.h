@@ -90,8 +90,9 @@ cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int bl
                          cudaStream_t stream, const KArgs& a);
 cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a);
 cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BArgs& a);
-cudaError_t upload_exp2_table_values(const double* host256);  // 2^(j/256) into device symbol
-                                                              // (current device)
+cudaError_t upload_exp2_table_values(const double* host_table);  // 2^(j/N), N = exp2_table_size(),
+                                                                 // into the current device
+int exp2_table_size();
 int num_acc(int kind, bool grad);
 
 }  // namespace gbnll

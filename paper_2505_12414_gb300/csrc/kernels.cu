@@ -18,13 +18,17 @@
 //        (one logarithm per thread instead of one per event); sum_i alpha (m_i - ma) is
 //        a constant of the sample, computed once at load;
 //      - the exponential is a table-driven implementation (P. T. P. Tang, ACM TOMS 15
-//        (1989) 144) with a 256-entry table of 2^(j/256) held in shared memory and a
-//        degree-4 Taylor polynomial; the reciprocal 1/Ptilde starts from the hardware
+//        (1989) 144) with a 1024-entry table of 2^(j/1024) held in shared memory and an
+//        economised cubic (8 FP64 instructions); the reciprocal 1/Ptilde starts from the hardware
 //        approximation rcp.approx.ftz.f64 and takes one cubically convergent correction
 //        y (1 + e + e^2), e = 1 - x y;
 //      - validity checks and the exponent bookkeeping use the integer pipe only.
 //  * Events are SoA FP64 columns read with 128-bit (double2) coalesced loads; each
-//    thread handles two consecutive events per iteration of a grid-stride loop.
+//    thread handles two consecutive events per iteration of a grid-stride loop, in one
+//    basic block (the ragged tail masks the second event arithmetically, no branch), so
+//    the two events' dependency chains interleave in the FP64 pipe.
+//  * Warp reductions halve the slot count per shuffle level (31 FP64 adds per warp for
+//    up to 32 slots) instead of a shuffle tree per slot.
 //  * The grid is a small multiple of the SM count; block partial sums are written to a
 //    scratch buffer and the last block to finish (atomic ticket) reduces them in a fixed
 //    order, so results are bitwise reproducible for a given launch shape.
@@ -38,7 +42,7 @@
 
 namespace gbnll {
 
-__device__ double g_exp2tab[256];  // 2^(j/256), correctly rounded, uploaded once per device
+__device__ double g_exp2tab[kExpTable];  // 2^(j/N), correctly rounded, uploaded once per device
 
 // ----------------------------------------------------------------------------------
 // Angular basis (paper Sec. 2.4.2, Eq. 3 regrouped by parameter):
@@ -76,23 +80,27 @@ __device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi
 }
 
 // ----------------------------------------------------------------------------------
-// Per-event bodies.  acc[] slots as documented in gbnll_internal.h.
+// Per-event bodies.  acc[] slots as documented in gbnll_internal.h.  `valid` == false
+// turns the event into an exact no-op (factor 1 in the product, R = 0 in every sum), so
+// both events of a pair run in one basic block and their dependency chains interleave.
 // ----------------------------------------------------------------------------------
 template <bool W, bool GRAD>
-__device__ __forceinline__ void event_mass(const KConst& c, double m, double w, double* acc, LogProd& lp,
-                                           int& bad, const double* tab)
+__device__ __forceinline__ void event_mass(const KConst& c, double m, double w, bool valid, double* acc,
+                                           LogProd& lp, int& bad, const double* tab)
 {
     double d = m - c.mu;
     double E = fexp(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
     double P = E + c.b2;
-    bad |= not_positive_normal(P);
+    bad |= valid ? not_positive_normal(P) : 0;
+    P = valid ? P : 1.0;
     if (W)
-        acc[0] = fma(w, log(P), acc[0]);
+        acc[0] = fma(valid ? w : 0.0, log(P), acc[0]);
     else
         logprod_mul(lp, P);
     if (GRAD) {
         double R = frcp(P);
         if (W) R *= w;
+        R = valid ? R : 0.0;
         double rs = R * E;
         acc[1] += rs;
         double rsd = rs * d;
@@ -105,8 +113,8 @@ __device__ __forceinline__ void event_mass(const KConst& c, double m, double w, 
 
 template <bool W, bool GRAD>
 __device__ __forceinline__ void event_4d(const KConst& c, double m, const double h[9], double xl, double t2l,
-                                         double xk, double t2k, double xp, double t2p, double w, double* acc,
-                                         LogProd& lp, int& bad, const double* tab)
+                                         double xk, double t2k, double xp, double t2p, double w, bool valid,
+                                         double* acc, LogProd& lp, int& bad, const double* tab)
 {
     double d = m - c.mu;
     double E = fexp(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
@@ -120,14 +128,16 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
     double C = C12 * C3;
     double s = A * E;
     double P = s + C;
-    bad |= not_positive_normal(P);
+    bad |= valid ? not_positive_normal(P) : 0;
+    P = valid ? P : 1.0;
     if (W)
-        acc[0] = fma(w, log(P), acc[0]);
+        acc[0] = fma(valid ? w : 0.0, log(P), acc[0]);
     else
         logprod_mul(lp, P);
     if (GRAD) {
         double R = frcp(P);
         if (W) R *= w;
+        R = valid ? R : 0.0;
         double rE = R * E;
         double rs = rE * A;
         acc[1] += rs;
@@ -136,12 +146,14 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
         acc[3] = fma(rsd, d, acc[3]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) acc[4 + k] = fma(rE, h[k + 1], acc[4 + k]);
-        double re = R * C;
+        // R C/C_j for the three background factors, and R C
+        double u3 = R * C12;
+        double rc3 = R * C3;
+        double u1 = rc3 * C2;
+        double u2 = rc3 * C1;
+        double re = u3 * C3;
         acc[12] += re;
         acc[13] = fma(re, d, acc[13]);
-        double u1 = R * (C2 * C3);
-        double u2 = R * (C1 * C3);
-        double u3 = R * C12;
         acc[14] = fma(u1, xl, acc[14]);
         acc[15] = fma(u1, t2l, acc[15]);
         acc[16] = fma(u2, xk, acc[16]);
@@ -154,23 +166,39 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
 // ----------------------------------------------------------------------------------
 // Fixed-order reductions
 // ----------------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v)
+
+// Warp reduction of K slots by recursive halving: at level s each lane keeps half of its
+// slots, sends the other half to lane ^ s and adds what it receives, so the warp spends
+// 16 + 8 + 4 + 2 + 1 = 31 FP64 additions instead of 5 K.  On return lane l holds the
+// warp total of slot l (l < K).  The pairing is fixed, so the result is deterministic.
+template <int K>
+__device__ __forceinline__ double warp_reduce_slots(const double (&in)[K])
 {
+    static_assert(K <= 32, "at most 32 slots");
+    const int lane = threadIdx.x & 31;
+    double v[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
+    for (int k = 0; k < 32; ++k) v[k] = k < K ? in[k] : 0.0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            double send = upper ? v[i] : v[i + s];
+            double keep = upper ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
 }
 
-// Reduce K per-thread values over the block (result valid in threads 0..K-1 as `res`).
+// Reduce K per-thread values over the block; the result is valid in threads 0..K-1.
 template <int K>
 __device__ __forceinline__ double block_reduce(const double (&v)[K], double* smem)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        double s = warp_sum(v[k]);
-        if (lane == 0) smem[warp * K + k] = s;
-    }
+    double s = warp_reduce_slots<K>(v);
+    if (lane < K) smem[warp * K + lane] = s;
     __syncthreads();
     double res = 0.0;
     if (threadIdx.x < K) {
@@ -180,8 +208,8 @@ __device__ __forceinline__ double block_reduce(const double (&v)[K], double* sme
     return res;
 }
 
-// Block partials -> scratch; the last block to arrive sums them in block order (with
-// Neumaier compensation) into out[0..K).  Returns nothing; resets the ticket.
+// Block partials -> scratch; the last block to arrive sums them in block order into
+// out[0..K).  Resets the ticket for the next launch.
 template <int K>
 __device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, double* partials,
                                             unsigned int* ticket, double* out)
@@ -212,19 +240,24 @@ __device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, 
 // ----------------------------------------------------------------------------------
 // The fused kernel
 // ----------------------------------------------------------------------------------
+__device__ __forceinline__ double2 ld2(const double* col, int64_t p)
+{
+    return __ldg(reinterpret_cast<const double2*>(col) + p);
+}
+
 template <int KIND, int VAR, bool W, bool GRAD>
 __global__ void __launch_bounds__(256) fused_nll_kernel(const KArgs a)
 {
     constexpr int K = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
-    __shared__ double s_tab[256];
+    __shared__ double s_tab[kExpTable];
     __shared__ double s_red[8 * K];
-    for (int j = threadIdx.x; j < 256; j += blockDim.x) s_tab[j] = g_exp2tab[j];
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_tab[j] = g_exp2tab[j];
     __syncthreads();
 
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    LogProd lp{1.0, 0};
+    LogProd lpx{1.0, 0}, lpy{1.0, 0};
     int bad = 0;
 
     const int64_t n = a.n;
@@ -233,50 +266,47 @@ __global__ void __launch_bounds__(256) fused_nll_kernel(const KArgs a)
     const KConst& c = a.c;
 
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += stride) {
-        const int64_t i0 = 2 * p;
-        const bool second = (i0 + 1) < n;
-        double2 m2 = __ldg(reinterpret_cast<const double2*>(a.col[kColM]) + p);
+        const bool second = (2 * p + 1) < n;
+        double2 m2 = ld2(a.col[kColM], p);
         double2 w2 = make_double2(1.0, 1.0);
-        if (W) w2 = __ldg(reinterpret_cast<const double2*>(a.w) + p);
+        if (W) w2 = ld2(a.w, p);
         if (KIND == kMass1D) {
-            event_mass<W, GRAD>(c, m2.x, w2.x, acc, lp, bad, s_tab);
-            if (second) event_mass<W, GRAD>(c, m2.y, w2.y, acc, lp, bad, s_tab);
+            event_mass<W, GRAD>(c, m2.x, w2.x, true, acc, lpx, bad, s_tab);
+            event_mass<W, GRAD>(c, m2.y, w2.y, second, acc, lpy, bad, s_tab);
         } else {
             double hx[9], hy[9];
             double t2lx, t2ly, t2kx, t2ky, xpx, xpy, t2px, t2py;
-            double2 l2 = __ldg(reinterpret_cast<const double2*>(a.col[kColCtl]) + p);
-            double2 k2 = __ldg(reinterpret_cast<const double2*>(a.col[kColCtk]) + p);
+            double2 l2 = ld2(a.col[kColCtl], p);
+            double2 k2 = ld2(a.col[kColCtk], p);
             if (VAR == kVarPrecompute) {
 #pragma unroll
                 for (int j = 0; j < 9; ++j) {
-                    double2 v = __ldg(reinterpret_cast<const double2*>(a.col[kColH0 + j]) + p);
+                    double2 v = ld2(a.col[kColH0 + j], p);
                     hx[j] = v.x;
                     hy[j] = v.y;
                 }
-                double2 v;
-                v = __ldg(reinterpret_cast<const double2*>(a.col[kColT2l]) + p);
+                double2 v = ld2(a.col[kColT2l], p);
                 t2lx = v.x;
                 t2ly = v.y;
-                v = __ldg(reinterpret_cast<const double2*>(a.col[kColT2k]) + p);
+                v = ld2(a.col[kColT2k], p);
                 t2kx = v.x;
                 t2ky = v.y;
-                v = __ldg(reinterpret_cast<const double2*>(a.col[kColXp]) + p);
+                v = ld2(a.col[kColXp], p);
                 xpx = v.x;
                 xpy = v.y;
-                v = __ldg(reinterpret_cast<const double2*>(a.col[kColT2p]) + p);
+                v = ld2(a.col[kColT2p], p);
                 t2px = v.x;
                 t2py = v.y;
             } else {
-                double2 f2 = __ldg(reinterpret_cast<const double2*>(a.col[kColPhi]) + p);
+                double2 f2 = ld2(a.col[kColPhi], p);
                 angular_basis(l2.x, k2.x, f2.x, hx, t2lx, t2kx, xpx, t2px);
                 angular_basis(l2.y, k2.y, f2.y, hy, t2ly, t2ky, xpy, t2py);
             }
-            event_4d<W, GRAD>(c, m2.x, hx, l2.x, t2lx, k2.x, t2kx, xpx, t2px, w2.x, acc, lp, bad, s_tab);
-            if (second)
-                event_4d<W, GRAD>(c, m2.y, hy, l2.y, t2ly, k2.y, t2ky, xpy, t2py, w2.y, acc, lp, bad, s_tab);
+            event_4d<W, GRAD>(c, m2.x, hx, l2.x, t2lx, k2.x, t2kx, xpx, t2px, w2.x, true, acc, lpx, bad, s_tab);
+            event_4d<W, GRAD>(c, m2.y, hy, l2.y, t2ly, k2.y, t2ky, xpy, t2py, w2.y, second, acc, lpy, bad, s_tab);
         }
     }
-    if (!W) acc[0] = logprod_value(lp);
+    if (!W) acc[0] = logprod_value(lpx) + logprod_value(lpy);
     acc[K - 1] = (double)bad;
     grid_reduce<K>(acc, s_red, a.partials, a.ticket, a.out);
 }
@@ -365,9 +395,11 @@ cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BAr
     return cudaGetLastError();
 }
 
-cudaError_t upload_exp2_table_values(const double* host256)
+cudaError_t upload_exp2_table_values(const double* host_table)
 {
-    return cudaMemcpyToSymbol(g_exp2tab, host256, 256 * sizeof(double));
+    return cudaMemcpyToSymbol(g_exp2tab, host_table, kExpTable * sizeof(double));
 }
+
+int exp2_table_size() { return kExpTable; }
 
 }  // namespace gbnll

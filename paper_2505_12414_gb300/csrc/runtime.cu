@@ -49,9 +49,10 @@ int ensure_exp2_table(int device)
     std::lock_guard<std::mutex> lock(g_table_mutex);
     if (device < 0 || device >= 64) return NLL_ERR_ARG;
     if (g_table_ready[device]) return NLL_OK;
-    double tab[256];
-    for (int j = 0; j < 256; ++j) tab[j] = (double)exp2l((long double)j / 256.0L);
-    if (upload_exp2_table_values(tab) != cudaSuccess) return NLL_ERR_CUDA;
+    const int N = exp2_table_size();
+    std::vector<double> tab(N);
+    for (int j = 0; j < N; ++j) tab[j] = (double)exp2l((long double)j / (long double)N);
+    if (upload_exp2_table_values(tab.data()) != cudaSuccess) return NLL_ERR_CUDA;
     g_table_ready[device] = true;
     return NLL_OK;
 }
