@@ -94,5 +94,6 @@ cudaError_t upload_exp2_table_values(const double* host_table);  // 2^(j/N), N =
                                                                  // into the current device
 int exp2_table_size();
 int num_acc(int kind, bool grad);
+int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads);  // resident blocks/SM
 
 }  // namespace gbnll

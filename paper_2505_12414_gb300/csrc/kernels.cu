@@ -245,12 +245,87 @@ __device__ __forceinline__ double2 ld2(const double* col, int64_t p)
     return __ldg(reinterpret_cast<const double2*>(col) + p);
 }
 
+// Inputs of one pair of consecutive events (one 128-bit load per column).
+struct PairIn {
+    double2 m, w, l, k, f;
+    double2 h[9];
+    double2 t2l, t2k, xp, t2p;
+};
+
+template <int KIND, int VAR, bool W>
+__device__ __forceinline__ void load_pair(const KArgs& a, int64_t p, PairIn& in)
+{
+    in.m = ld2(a.col[kColM], p);
+    if (W) in.w = ld2(a.w, p);
+    if (KIND == kKstar4D) {
+        in.l = ld2(a.col[kColCtl], p);
+        in.k = ld2(a.col[kColCtk], p);
+        if (VAR == kVarPrecompute) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) in.h[j] = ld2(a.col[kColH0 + j], p);
+            in.t2l = ld2(a.col[kColT2l], p);
+            in.t2k = ld2(a.col[kColT2k], p);
+            in.xp = ld2(a.col[kColXp], p);
+            in.t2p = ld2(a.col[kColT2p], p);
+        } else {
+            in.f = ld2(a.col[kColPhi], p);
+        }
+    }
+}
+
 template <int KIND, int VAR, bool W, bool GRAD>
-__global__ void __launch_bounds__(256) fused_nll_kernel(const KArgs a)
+__device__ __forceinline__ void process_pair(const KConst& c, const PairIn& in, bool second, double* acc,
+                                             LogProd& lpx, LogProd& lpy, int& bad, const double* tab)
+{
+    const double wx = W ? in.w.x : 1.0, wy = W ? in.w.y : 1.0;
+    if (KIND == kMass1D) {
+        event_mass<W, GRAD>(c, in.m.x, wx, true, acc, lpx, bad, tab);
+        event_mass<W, GRAD>(c, in.m.y, wy, second, acc, lpy, bad, tab);
+    } else {
+        double hx[9], hy[9];
+        double t2lx, t2ly, t2kx, t2ky, xpx, xpy, t2px, t2py;
+        if (VAR == kVarPrecompute) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                hx[j] = in.h[j].x;
+                hy[j] = in.h[j].y;
+            }
+            t2lx = in.t2l.x;
+            t2ly = in.t2l.y;
+            t2kx = in.t2k.x;
+            t2ky = in.t2k.y;
+            xpx = in.xp.x;
+            xpy = in.xp.y;
+            t2px = in.t2p.x;
+            t2py = in.t2p.y;
+        } else {
+            angular_basis(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px);
+            angular_basis(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py);
+        }
+        event_4d<W, GRAD>(c, in.m.x, hx, in.l.x, t2lx, in.k.x, t2kx, xpx, t2px, wx, true, acc, lpx, bad, tab);
+        event_4d<W, GRAD>(c, in.m.y, hy, in.l.y, t2ly, in.k.y, t2ky, xpy, t2py, wy, second, acc, lpy, bad, tab);
+    }
+}
+
+// Work split: block b owns the contiguous pair range [b P / B, (b+1) P / B) (P pairs, B
+// blocks), which its threads walk with a block-sized stride (coalesced).  Every block,
+// hence every SM, gets the same work to within one pair.
+template <int KIND, int VAR, bool W, bool GRAD>
+__global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 {
     constexpr int K = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
     __shared__ double s_tab[kExpTable];
     __shared__ double s_red[8 * K];
+
+    const int64_t n = a.n;
+    const int64_t npairs = (n + 1) >> 1;
+    const int64_t begin = npairs * blockIdx.x / gridDim.x;
+    const int64_t end = npairs * (blockIdx.x + 1) / gridDim.x;
+    int64_t p = begin + threadIdx.x;
+
+    // the first pair's loads are in flight while the block stages the exp table
+    PairIn in;
+    if (p < end) load_pair<KIND, VAR, W>(a, p, in);
     for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_tab[j] = g_exp2tab[j];
     __syncthreads();
 
@@ -259,52 +334,12 @@ __global__ void __launch_bounds__(256) fused_nll_kernel(const KArgs a)
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
     LogProd lpx{1.0, 0}, lpy{1.0, 0};
     int bad = 0;
-
-    const int64_t n = a.n;
-    const int64_t npairs = (n + 1) >> 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const KConst& c = a.c;
 
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += stride) {
-        const bool second = (2 * p + 1) < n;
-        double2 m2 = ld2(a.col[kColM], p);
-        double2 w2 = make_double2(1.0, 1.0);
-        if (W) w2 = ld2(a.w, p);
-        if (KIND == kMass1D) {
-            event_mass<W, GRAD>(c, m2.x, w2.x, true, acc, lpx, bad, s_tab);
-            event_mass<W, GRAD>(c, m2.y, w2.y, second, acc, lpy, bad, s_tab);
-        } else {
-            double hx[9], hy[9];
-            double t2lx, t2ly, t2kx, t2ky, xpx, xpy, t2px, t2py;
-            double2 l2 = ld2(a.col[kColCtl], p);
-            double2 k2 = ld2(a.col[kColCtk], p);
-            if (VAR == kVarPrecompute) {
-#pragma unroll
-                for (int j = 0; j < 9; ++j) {
-                    double2 v = ld2(a.col[kColH0 + j], p);
-                    hx[j] = v.x;
-                    hy[j] = v.y;
-                }
-                double2 v = ld2(a.col[kColT2l], p);
-                t2lx = v.x;
-                t2ly = v.y;
-                v = ld2(a.col[kColT2k], p);
-                t2kx = v.x;
-                t2ky = v.y;
-                v = ld2(a.col[kColXp], p);
-                xpx = v.x;
-                xpy = v.y;
-                v = ld2(a.col[kColT2p], p);
-                t2px = v.x;
-                t2py = v.y;
-            } else {
-                double2 f2 = ld2(a.col[kColPhi], p);
-                angular_basis(l2.x, k2.x, f2.x, hx, t2lx, t2kx, xpx, t2px);
-                angular_basis(l2.y, k2.y, f2.y, hy, t2ly, t2ky, xpy, t2py);
-            }
-            event_4d<W, GRAD>(c, m2.x, hx, l2.x, t2lx, k2.x, t2kx, xpx, t2px, w2.x, true, acc, lpx, bad, s_tab);
-            event_4d<W, GRAD>(c, m2.y, hy, l2.y, t2ly, k2.y, t2ky, xpy, t2py, w2.y, second, acc, lpy, bad, s_tab);
-        }
+    while (p < end) {
+        process_pair<KIND, VAR, W, GRAD>(c, in, (2 * p + 1) < n, acc, lpx, lpy, bad, s_tab);
+        p += blockDim.x;
+        if (p < end) load_pair<KIND, VAR, W>(a, p, in);
     }
     if (!W) acc[0] = logprod_value(lpx) + logprod_value(lpy);
     acc[K - 1] = (double)bad;
@@ -356,6 +391,31 @@ __global__ void __launch_bounds__(256) basis_kernel(const BArgs a)
 // launchers
 // ----------------------------------------------------------------------------------
 int num_acc(int kind, bool grad) { return !grad ? kAccNll : (kind == kMass1D ? kAcc1D : kAcc4D); }
+
+template <int KIND, int VAR>
+static int occ_kv(bool weighted, bool grad, int threads)
+{
+    int nb = 0;
+    if (weighted) {
+        if (grad)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, true, true>, threads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, true, false>, threads, 0);
+    } else {
+        if (grad)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, false, true>, threads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, false, false>, threads, 0);
+    }
+    return nb;
+}
+
+int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads)
+{
+    if (kind == kMass1D) return occ_kv<kMass1D, kVarPrecompute>(weighted, grad, threads);
+    if (variant == kVarDirect) return occ_kv<kKstar4D, kVarDirect>(weighted, grad, threads);
+    return occ_kv<kKstar4D, kVarPrecompute>(weighted, grad, threads);
+}
 
 template <int KIND, int VAR>
 static cudaError_t launch_kv(bool weighted, bool grad, int blocks, int threads, cudaStream_t s, const KArgs& a)

@@ -585,8 +585,16 @@ int nll_autotune(nll_model* m)
     if (!m->loaded || !m->have_last || m->n == 0)
         return fail(m, NLL_ERR_STATE, "autotune needs loaded events and one prior evaluation");
     if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
-    const int shapes[][2] = {{1, 256}, {2, 256}, {3, 256}, {4, 256}, {6, 256}, {8, 256},
-                             {2, 128}, {4, 128}, {6, 128}, {8, 128}, {12, 128}, {16, 128}};
+    // candidate shapes: for each block size, 1x and 2x the resident blocks per SM
+    std::vector<std::pair<int, int>> shapes;
+    bool grad_ok = m->last.f > 0.0 && m->last.f < 1.0;
+    for (int thr : {64, 128, 192, 256}) {
+        int occ = fused_occupancy(m->kind, effective_variant(m) < 0 ? kVarDirect : effective_variant(m), m->weighted,
+                                  grad_ok, thr);
+        if (occ <= 0) continue;
+        for (int mult : {1, 2})
+            if (occ * mult <= 32) shapes.push_back({occ * mult, thr});
+    }
     std::vector<int> variants;
     if (m->kind == kKstar4D && m->has_basis && m->variant == NLL_VARIANT_AUTO) {
         variants.push_back(kVarPrecompute);
@@ -594,7 +602,7 @@ int nll_autotune(nll_model* m)
     } else {
         variants.push_back(effective_variant(m));
     }
-    bool grad = m->last.f > 0.0 && m->last.f < 1.0;
+    bool grad = grad_ok;
     float best = 1e30f;
     int best_bps = m->bps, best_thr = m->threads, best_var = variants[0];
     for (int var : variants)
@@ -602,7 +610,7 @@ int nll_autotune(nll_model* m)
             float tot = 0.f;
             for (int rep = 0; rep < 4; ++rep) {
                 cudaEventRecord(m->ev0, m->stream);
-                int st = run_fused(m, m->last, grad, sh[0], sh[1], var, false);
+                int st = run_fused(m, m->last, grad, sh.first, sh.second, var, false);
                 if (st != NLL_OK) return st;
                 cudaEventRecord(m->ev1, m->stream);
                 cudaError_t e = cudaEventSynchronize(m->ev1);
@@ -613,8 +621,8 @@ int nll_autotune(nll_model* m)
             }
             if (tot < best) {
                 best = tot;
-                best_bps = sh[0];
-                best_thr = sh[1];
+                best_bps = sh.first;
+                best_thr = sh.second;
                 best_var = var;
             }
         }
