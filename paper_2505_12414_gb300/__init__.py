@@ -94,6 +94,8 @@ def load(path=None):
     L.nll_precomputed_basis.argtypes = [vp, _DP]
     L.nll_calibrate_fp64.argtypes = [ctypes.c_int, _DP]
     L.nll_diag_math.argtypes = [ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int64]
+    L.nll_eval_grad_4d_noalloc.argtypes = [_DP, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64,
+                                           _DP, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _DP, _DP]
     _lib = L
     return L
 
@@ -312,6 +314,46 @@ def nll_diag_math(fn, x, device=0):
     if st != NLL_OK:
         raise NLLError(st, "nll_diag_math failed")
     return y
+
+
+NLL_NOALLOC_MAX_BLOCKS = 1024
+
+
+def nll_eval_grad_4d_noalloc(obs_ranges, dev_columns, theta, dev_weights=None, blocks=0, stream=0, check=True):
+    """4D NLL and gradient on caller-owned device buffers (CUDA tensors or raw pointers),
+    without any device allocation by the library.  Returns (nll, grad[, status])."""
+    L = load()
+    r = _f64(obs_ranges)
+    ptrs = [c.data_ptr() if hasattr(c, "data_ptr") else int(c) for c in dev_columns]
+    arr = (ctypes.c_void_p * 4)(*ptrs)
+    n = int(dev_columns[0].numel()) if hasattr(dev_columns[0], "numel") else None
+    return _noalloc_call(L, r, arr, dev_weights, n, theta, blocks, stream, check)
+
+
+def _noalloc_call(L, r, arr, dev_weights, n, theta, blocks, stream, check):
+    th = _f64(theta)
+    wp = None
+    if dev_weights is not None:
+        wp = dev_weights.data_ptr() if hasattr(dev_weights, "data_ptr") else int(dev_weights)
+    out = ctypes.c_double()
+    g = np.zeros(len(th))
+    st = L.nll_eval_grad_4d_noalloc(_p(r), arr, wp, int(n), _p(th), len(th), int(blocks), int(stream or 0),
+                                    ctypes.byref(out), _p(g))
+    if not check:
+        return out.value, g, st
+    if st != NLL_OK:
+        raise NLLError(st, "nll_eval_grad_4d_noalloc failed")
+    return out.value, g
+
+
+def nll_eval_grad_4d_noalloc_n(obs_ranges, dev_columns, n_events, theta, dev_weights=None, blocks=0, stream=0,
+                               check=True):
+    """As nll_eval_grad_4d_noalloc with an explicit event count (buffers may be longer)."""
+    L = load()
+    r = _f64(obs_ranges)
+    ptrs = [c.data_ptr() if hasattr(c, "data_ptr") else int(c) for c in dev_columns]
+    arr = (ctypes.c_void_p * 4)(*ptrs)
+    return _noalloc_call(L, r, arr, dev_weights, n_events, theta, blocks, stream, check)
 
 
 class Model:

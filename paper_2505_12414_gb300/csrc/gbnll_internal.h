@@ -94,6 +94,17 @@ cudaError_t upload_exp2_table_values(const double* host_table);  // 2^(j/N), N =
                                                                  // into the current device
 int exp2_table_size();
 int num_acc(int kind, bool grad);
+
+// Static device scratch of nll_eval_grad_4d_noalloc (kernels.cu).
+constexpr int kNoAllocMaxBlocks = 1024;
+struct NoAllocScratch {
+    double* partials;      // [kAccMax][max_blocks]
+    double* out;           // [32]
+    unsigned int* ticket;  // grid-completion counter
+    int max_blocks;
+};
+// Device addresses of the scratch on `device` (which must be current); set up once per device.
+cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out);
 int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads);  // resident blocks/SM
 
 }  // namespace gbnll

@@ -37,6 +37,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fp64_math.cuh"
 #include "gbnll_internal.h"
 
@@ -461,5 +463,34 @@ cudaError_t upload_exp2_table_values(const double* host_table)
 }
 
 int exp2_table_size() { return kExpTable; }
+
+// ----------------------------------------------------------------------------------
+// Static scratch for callers that cannot allocate device memory (nll_eval_grad_4d_noalloc).
+// One array per process and device, zero at module load, holding the block partials
+// ([kAccMax][kNoAllocMaxBlocks]), the final sums (32 slots) and the grid ticket.
+// ----------------------------------------------------------------------------------
+constexpr int kNoAllocDoubles = kAccMax * kNoAllocMaxBlocks + 64;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out)
+{
+    static std::mutex mu;
+    static double* base[64] = {nullptr};
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!base[device]) {
+        // host code only sees a stand-in for the symbol: look up its device address, with
+        // `device` current, once per device
+        double* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        base[device] = ptr;
+    }
+    out->partials = base[device];
+    out->out = base[device] + (size_t)kAccMax * kNoAllocMaxBlocks;
+    out->ticket = reinterpret_cast<unsigned int*>(out->out + 32);
+    out->max_blocks = kNoAllocMaxBlocks;
+    return cudaSuccess;
+}
 
 }  // namespace gbnll
