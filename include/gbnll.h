@@ -201,9 +201,9 @@ int nll_calibrate_fp64(int device, double* rates);
 /*
  * nll_diag_math -- diagnostic: evaluate the library's device FP64 building blocks on n
  * host inputs x, writing host outputs y (fn 0: the table-driven exponential used by the
- * kernels, after Tang's method; fn 1: the reciprocal, hardware approximation plus one
- * cubic correction).  For accuracy tests against the host's libm; allocates temporary
- * device buffers.
+ * kernels, after Tang's method, which takes its argument pre-scaled: y = exp(x ln2/1024);
+ * fn 1: the reciprocal, hardware approximation plus one cubic correction).  For accuracy
+ * tests against the host's libm; allocates temporary device buffers.
  */
 int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
 

@@ -362,16 +362,32 @@ class Model:
     def __init__(self, kind, obs_ranges, device=0, stream=0):
         self.kind = kind
         self.handle = nll_create_model(kind, obs_ranges, device, stream)
+        n = nll_num_params(self.handle)
+        # preallocated argument buffers for the repeated-evaluation path
+        self._n = n
+        self._th = np.zeros(n)
+        self._g = np.zeros(n)
+        self._out = ctypes.c_double()
+        self._thp = self._th.ctypes.data_as(_DP)
+        self._gp = self._g.ctypes.data_as(_DP)
+        self._outp = ctypes.byref(self._out)
 
     def load(self, columns, weights=None, precompute=True):
         nll_load_events(self.handle, columns, weights, precompute)
         return self
 
     def eval(self, theta):
-        return nll_eval(self.handle, theta)
+        self._th[:] = theta
+        st = load().nll_eval(self.handle, self._thp, self._n, self._outp)
+        _check(self.handle, st)
+        return self._out.value
 
     def eval_grad(self, theta):
-        return nll_eval_grad(self.handle, theta)
+        """(NLL, gradient); the gradient array is a fresh copy."""
+        self._th[:] = theta
+        st = load().nll_eval_grad(self.handle, self._thp, self._n, self._outp, self._gp)
+        _check(self.handle, st)
+        return self._out.value, self._g.copy()
 
     def fit(self, theta0, **kw):
         return fit_minimise(self.handle, theta0, **kw)

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) cal_kernel(double* out, int iters, double
             if (OP == 1) x[c] = exp(-x[c]);                    // CUDA exp
             if (OP == 2) x[c] = 1.0 / (x[c] + 1.0);            // CUDA division (+1 DADD)
             if (OP == 3) x[c] = log(x[c] + 3.0);               // CUDA log (+1 DADD)
-            if (OP == 4) x[c] = gbnll::fexp(-x[c], s_tab);     // library exp
+            if (OP == 4) x[c] = gbnll::fexp_scaled(-x[c], s_tab);  // library exp
             if (OP == 5) x[c] = gbnll::frcp(x[c] + 1.0);       // library reciprocal (+1 DADD)
         }
     }
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) diag_kernel(int fn, const double* x, doub
     for (int j = threadIdx.x; j < gbnll::kExpTable; j += blockDim.x) s_tab[j] = g_cal_tab[j];
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = fn == 0 ? gbnll::fexp(x[i], s_tab) : gbnll::frcp(x[i]);
+        y[i] = fn == 0 ? gbnll::fexp_scaled(x[i], s_tab) : gbnll::frcp(x[i]);
 }
 
 }  // namespace

@@ -9,38 +9,38 @@ namespace gbnll {
 constexpr int kExpTableBits = 10;
 constexpr int kExpTable = 1 << kExpTableBits;
 
-// exp(x) after Tang's table-driven method (P. T. P. Tang, ACM TOMS 15 (1989) 144):
-//   x = (N q + j) ln2/N + r,  |r| <= ln2/(2N),  exp(x) = 2^q 2^(j/N) exp(r),  N = 1024.
-// exp(r) - 1 is a cubic obtained by Chebyshev economisation of the degree-4 Taylor
-// polynomial on [-ln2/2N, ln2/2N] (the r^4 term is replaced by its best lower-degree
-// approximation): c0 + r (1 + r (c2 + r c3)), c0 = -h^4/192, c2 = 1/2 + h^2/24, c3 = 1/6,
-// h = ln2/2N; truncation error below 0.62 ulp of 1.  The reduction constant ln2/N is split
-// so that k * L_hi is exact for |k| < 2^24.
-// |x| >= 707 returns 0 (x < 0) or +inf (x > 0, and NaN); results below 2^-1016 are flushed.
-// 8 FP64 instructions on the fast path.
-__device__ __forceinline__ double fexp(double x, const double* __restrict__ tab)
+// Scale of the exponential's argument: fexp_scaled(x * kExpArgScale) = exp(x).
+constexpr double kExpArgScale = 0x1.71547652b82fep+10;  // N/ln2, N = 1024
+
+// exp(xs / S), S = N/ln2, after Tang's table-driven method (P. T. P. Tang, ACM TOMS 15
+// (1989) 144), N = 1024.  The argument arrives pre-scaled (the kernels fold S into the
+// hoisted constants), so the reduction is exact without a split constant:
+//   xs = N q + j + r,  |r| <= 1/2,  exp(xs / S) = 2^q 2^(j/N) exp(r ln2/N).
+// exp(r ln2/N) - 1 is a cubic in r obtained by Chebyshev economisation of the degree-4
+// Taylor polynomial on [-ln2/2N, ln2/2N] (the r^4 term replaced by its best lower-degree
+// approximation), with the powers of ln2/N folded into the coefficients; truncation error
+// below 0.62 ulp of 1.  |xs| >= 1.04e6 (|x| >= 704) returns 0 (xs < 0) or +inf (xs > 0,
+// and NaN).  7 FP64 instructions on the fast path.
+__device__ __forceinline__ double fexp_scaled(double xs, const double* __restrict__ tab)
 {
-    const double kInvL = 0x1.71547652b82fep+10;  // N/ln2
-    const double kMagic = 0x1.8p52;              // 1.5 * 2^52: rounds to an integer in the low word
-    const double kLhi = 0x1.62e42ff000000p-11;   // ln2/N, 29 significant bits
-    const double kLlo = -0x1.718432a1b0e26p-45;  // ln2/N - kLhi
-    const double c0 = -0x1.3b2ab6fba4e77p-54;
-    const double c2 = 0x1.00000028ffa80p-1;
-    const double c3 = 0x1.5555555555555p-3;
-    double kd = fma(x, kInvL, kMagic);
+    const double kMagic = 0x1.8p52;  // 1.5 * 2^52: xs + kMagic rounds xs to an integer
+    const double C1 = 0x1.62e42fefa39efp-11;  // ln2/N
+    const double C2 = 0x1.ebfbe046f706bp-23;  // (1/2 + h^2/24) (ln2/N)^2, h = ln2/2N
+    const double C3 = 0x1.c6b08d704a0c0p-35;  // (1/6) (ln2/N)^3
+    const double C0 = -0x1.3b2ab6fba4e77p-54;  // -h^4/192
+    double kd = xs + kMagic;
     int k = __double2loint(kd);
     double kf = kd - kMagic;
-    double r = fma(kf, -kLhi, x);
-    r = fma(kf, -kLlo, r);
+    double r = xs - kf;  // exact
     double T = tab[k & (kExpTable - 1)];
-    double p = fma(r, c3, c2);
-    p = fma(p, r, 1.0);
-    p = fma(p, r, c0);
+    double p = fma(r, C3, C2);
+    p = fma(p, r, C1);
+    p = fma(p, r, C0);
     double y = fma(T, p, T);
     int hi = __double2hiint(y) + ((k >> kExpTableBits) << 20);
     y = __hiloint2double(hi, __double2loint(y));
-    int xhi = __double2hiint(x);
-    if ((xhi & 0x7fffffff) >= 0x40861800) y = (xhi < 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
+    int xhi = __double2hiint(xs);
+    if ((xhi & 0x7fffffff) >= 0x412fbd00) y = (xhi < 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
     return y;
 }
 

@@ -47,9 +47,9 @@ constexpr int kAccMax = 21;
 // parameter point on the host and passed to the kernel).
 struct KConst {
     double mu;         // Gaussian mean
-    double neg_b0;     // -1/(2 sigma^2)
-    double neg_alpha;  // -alpha
-    double k0;         // ln b1 - alpha (mu - ma); exponent = d (neg_b0 d + neg_alpha) + k0
+    double neg_b0;     // -S/(2 sigma^2)          (S = N/ln2, the exponential's argument scale)
+    double neg_alpha;  // -S alpha
+    double k0;         // S (ln b1 - alpha (mu - ma)); scaled exponent = d (neg_b0 d + neg_alpha) + k0
     double b2;         // mass model: background constant (1-f) / Ntilde2
     double ang[8];     // FL, S3, S4, S5, AFB, S7, S8, S9
     double cq[9];      // background factors: C_j = cq[3j] + cq[3j+1] x_j + cq[3j+2] T2(x_j)

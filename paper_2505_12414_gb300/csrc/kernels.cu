@@ -19,7 +19,8 @@
 //        a constant of the sample, computed once at load;
 //      - the exponential is a table-driven implementation (P. T. P. Tang, ACM TOMS 15
 //        (1989) 144) with a 1024-entry table of 2^(j/1024) held in shared memory and an
-//        economised cubic (8 FP64 instructions); the reciprocal 1/Ptilde starts from the hardware
+//        economised cubic; the hoisted constants carry the argument scale 1024/ln2, so the
+//        reduction is exact and costs 7 FP64 instructions; the reciprocal 1/Ptilde starts from the hardware
 //        approximation rcp.approx.ftz.f64 and takes one cubically convergent correction
 //        y (1 + e + e^2), e = 1 - x y;
 //      - validity checks and the exponent bookkeeping use the integer pipe only.
@@ -91,7 +92,7 @@ __device__ __forceinline__ void event_mass(const KConst& c, double m, double w, 
                                            LogProd& lp, int& bad, const double* tab)
 {
     double d = m - c.mu;
-    double E = fexp(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
+    double E = fexp_scaled(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
     double P = E + c.b2;
     bad |= valid ? not_positive_normal(P) : 0;
     P = valid ? P : 1.0;
@@ -119,7 +120,7 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
                                          double* acc, LogProd& lp, int& bad, const double* tab)
 {
     double d = m - c.mu;
-    double E = fexp(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
+    double E = fexp_scaled(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
     double A = fma(c.ang[0], h[1], h[0]);
 #pragma unroll
     for (int k = 1; k < 8; ++k) A = fma(c.ang[k], h[k + 1], A);
@@ -128,8 +129,7 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
     double C3 = fma(c.cq[7], xp, fma(c.cq[8], t2p, c.cq[6]));
     double C12 = C1 * C2;
     double C = C12 * C3;
-    double s = A * E;
-    double P = s + C;
+    double P = fma(A, E, C);
     bad |= valid ? not_positive_normal(P) : 0;
     P = valid ? P : 1.0;
     if (W)

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/gbnll.h"
+#include "fp64_math.cuh"
 #include "gbnll_internal.h"
 #include "minimise.h"
 
@@ -83,8 +84,8 @@ struct nll_model {
     int max_blocks = 0;
     double* d_partials = nullptr;
     unsigned int* d_ticket = nullptr;
-    double* d_out = nullptr;
-    double* h_out = nullptr;  // pinned
+    double* d_out = nullptr;  // device alias of h_out
+    double* h_out = nullptr;  // mapped pinned host memory, written by the kernels
 
     // launch shape
     int bps = 2, threads = 256, variant = 0;
@@ -196,10 +197,11 @@ int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
     H.b0 = b0;
     H.b2 = b2;
     KConst& k = H.k;
+    const double S = kExpArgScale;  // the kernels' exponential takes its argument times S
     k.mu = mu;
-    k.neg_b0 = -b0;
-    k.neg_alpha = -alpha;
-    k.k0 = lnb1 - alpha * (mu - ma);
+    k.neg_b0 = -b0 * S;
+    k.neg_alpha = -alpha * S;
+    k.k0 = (lnb1 - alpha * (mu - ma)) * S;
     k.b2 = b2;
     if (m->kind == kKstar4D) {
         for (int j = 0; j < 8; ++j) k.ang[j] = th[2 + j];
@@ -272,8 +274,7 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
         st = run_fused(m, H, grad, m->bps, m->threads, var, true);
         if (st != NLL_OK) return st;
-        cudaError_t e = cudaMemcpyAsync(m->h_out, m->d_out, K * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        cudaError_t e = cudaStreamSynchronize(m->stream);
         if (e != cudaSuccess) return cuda_fail(m, e, "evaluation");
         if (m->profiling) {
             float ms = 0.f;
@@ -351,7 +352,6 @@ int run_stats(nll_model* m, const double* const* cols, const double* w, int64_t 
     int blocks = (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), (int64_t)m->sm_count * 2);
     blocks = std::min(blocks, m->max_blocks);
     cudaError_t e = launch_stats(blocks, 256, m->stream, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_out, m->d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, m->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
     if (e != cudaSuccess) return cuda_fail(m, e, "load statistics");
     memcpy(out, m->h_out, 3 * sizeof(double));
@@ -408,8 +408,9 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
     if (e == cudaSuccess) e = cudaMalloc(&m->d_partials, sizeof(double) * kAccMax * m->max_blocks);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(m->d_ticket, 0, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_out, sizeof(double) * kAccMax);
-    if (e == cudaSuccess) e = cudaMallocHost(&m->h_out, sizeof(double) * kAccMax);
+    // results land in mapped pinned host memory: the grid's last block writes them there
+    if (e == cudaSuccess) e = cudaHostAlloc(&m->h_out, sizeof(double) * kAccMax, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_out, m->h_out, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
     if (e != cudaSuccess) {
@@ -429,8 +430,7 @@ void nll_destroy(nll_model* m)
     free_events(m);
     if (m->d_partials) cudaFree(m->d_partials);
     if (m->d_ticket) cudaFree(m->d_ticket);
-    if (m->d_out) cudaFree(m->d_out);
-    if (m->h_out) cudaFreeHost(m->h_out);
+    if (m->h_out) cudaFreeHost(m->h_out);  // d_out is its device alias
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);

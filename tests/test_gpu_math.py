@@ -12,18 +12,23 @@ def ulp_err(a, ref):
 
 
 def test_table_exponential_accuracy(gpu_lib):
+    # the kernels' exponential takes its argument pre-scaled by S = 1024/ln2
+    S = 1024.0 / np.log(2.0)
     rs = synth.Stream(21, 0)
-    x = np.concatenate([
-        (2 * rs.uniform(200000) - 1) * 706.0,          # the whole fast range
-        (2 * rs.uniform(200000) - 1) * 40.0,           # the range the likelihood uses
-        (2 * rs.uniform(50000) - 1) * 1e-3,            # near zero
-        np.array([0.0, -0.0, 1e-300, -1e-300, 5e-324, 706.9, -706.9, np.log(2.0), -np.log(2.0)]),
+    xs = np.concatenate([
+        (2 * rs.uniform(200000) - 1) * 703.0 * S,       # the whole fast range
+        (2 * rs.uniform(200000) - 1) * 40.0 * S,        # the range the likelihood uses
+        (2 * rs.uniform(50000) - 1) * 2.0,              # a few table steps around zero
+        np.array([0.0, -0.0, 0.5, -0.5, 1023.5, -1024.5, 1e-300, 703.9 * S, -703.9 * S]),
     ])
-    y = gpu_lib.nll_diag_math(0, x)
-    ref = np.exp(x)
-    assert ulp_err(y, ref).max() <= 2.0
-    # the saturated range: 0 below -707, +inf above 707
-    big = np.array([-707.0, -800.0, -1e300, -np.inf, 707.0, 1e300, np.inf])
+    y = gpu_lib.nll_diag_math(0, xs)
+    # reference exp(xs ln2 / 1024) in extended precision (x87 80-bit here, binary128 on Arm)
+    ln2 = np.log(np.longdouble(2.0))
+    ref = np.exp(xs.astype(np.longdouble) * (ln2 / np.longdouble(1024.0)))
+    err = np.abs(y.astype(np.longdouble) - ref) / np.spacing(ref.astype(np.float64)).astype(np.longdouble)
+    assert float(err.max()) <= 2.0, float(err.max())
+    # the saturated range: 0 below -1.04e6 (|x| >= 704), +inf above
+    big = np.array([-1.04e6, -2e6, -1e300, -np.inf, 1.04e6, 1e300, np.inf])
     yb = gpu_lib.nll_diag_math(0, big)
     assert np.all(yb[:4] == 0.0) and np.all(np.isinf(yb[4:]))
 
