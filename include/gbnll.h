@@ -207,6 +207,76 @@ int nll_calibrate_fp64(int device, double* rates);
  */
 int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
 
+/* ------------------------------------------------------------------------------------
+ * Batched pseudo-experiments (paper Sec. 2.5 and Sec. 3.1: fit validation and coverage
+ * studies generate and fit many toys; Sec. 1: O(1e5) toys for coverage corrections).
+ * A batch holds many independent samples of one model, of uneven sizes (CSR layout), on
+ * one device.  Each minimiser step of every toy is one step of a device-resident loop:
+ *   prepare  -- hoist the parameter-only terms of every active toy's trial point(s) on the
+ *               device (Sec. 2.4.1), one work item per (toy, point);
+ *   evaluate -- one persistent kernel: blocks pull work units (item x event tile) from a
+ *               device counter and write each unit's sums (the fused NLL+gradient pass of
+ *               nll_eval_grad);
+ *   update   -- one warp per toy sums its units in tile order, assembles NLL and gradient and
+ *               advances that toy's minimiser (BFGS, Armijo line search, sine-transform bounds,
+ *               finite-difference Hessian of the analytic gradient at the minimum).
+ * The three launches are captured once in a CUDA graph and the graph is replayed until every
+ * toy has finished.  Schedules: tile_events = 0 gives one work unit per toy and point
+ * (CTA-per-toy); tile_events > 0 splits every toy into tiles of that many events whose sums
+ * are combined in tile order (split-toy).  Results are deterministic for a given schedule.
+ * ------------------------------------------------------------------------------------ */
+typedef struct nll_batch nll_batch; /* opaque; owned by the library */
+
+/* Create a batch of `kind` on `device`, ranges as nll_create_model.  The batch runs on a
+ * stream of its own (graph capture needs one); every call first waits for the work queued on
+ * `cuda_stream` (0 = CUDA's default stream) and returns when its results are on the host. */
+int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t cuda_stream, nll_batch** out);
+
+/*
+ * nll_batch_load -- copy n_toys samples into the batch.
+ *   offsets      host int64 array of n_toys + 1 entries; toy t owns events
+ *                [offsets[t], offsets[t+1]) of the columns (non-decreasing, offsets[0] = 0).
+ *   columns      ndim host pointers (as nll_load_events), offsets[n_toys] doubles each.
+ *   weights      host per-event weights or NULL.
+ *   precompute   4D only: build the event-only angular basis (paper Sec. 2.4.2).
+ * Events outside the ranges are rejected (NLL_ERR_ARG).  Toys may be empty.
+ */
+int nll_batch_load(nll_batch* b, const int64_t* offsets, int n_toys, const double* const* columns,
+                   const double* weights, int precompute);
+
+/*
+ * nll_batch_eval_grad -- one evaluation of every toy at its own parameter point.
+ *   thetas       host [n_toys][npar]; nll_out host [n_toys]; grad_out host [n_toys][npar].
+ *   status_out   host [n_toys] nll_status per toy (NULL allowed).
+ * Returns NLL_OK if every toy evaluated, else the first failing toy's status.
+ */
+int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, double* grad_out, int* status_out);
+
+/*
+ * nll_batch_fit -- minimise every toy's NLL on the device (see above).
+ *   theta0       host [n_toys][npar] start points, or [npar] shared by all toys if
+ *                shared_start != 0; lo, hi, step, fixed as fit_minimise (shared by all toys).
+ *   opt          tol_edm, max_iter, strategy (1: start from a finite-difference Hessian),
+ *                hessian (1: finite-difference Hessian of the analytic gradient at the minimum
+ *                for the covariance; 0: covariance from the BFGS matrix).
+ *   results      host array of n_toys fit_result.
+ *   steps_out    number of graph replays (device steps) used, or NULL.
+ * Returns NLL_OK when every toy converged, else NLL_ERR_NOT_CONVERGED (see results[].status).
+ */
+int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
+                  const double* step, const int* fixed, const fit_options* opt, fit_result* results,
+                  int* steps_out);
+
+/* Schedule: tile_events = 0 (CTA-per-toy) or > 0 (split-toy, multiple of 2);
+ * blocks_per_sm of the persistent evaluation kernel (0 keeps the value). */
+int nll_batch_set_schedule(nll_batch* b, int tile_events, int blocks_per_sm);
+int nll_batch_get_schedule(const nll_batch* b, int* tile_events, int* blocks_per_sm);
+/* Time both schedules (and tile sizes) on the loaded toys and keep the fastest. */
+int nll_batch_autotune(nll_batch* b);
+int nll_batch_num_toys(const nll_batch* b);
+const char* nll_batch_last_error(const nll_batch* b);
+void nll_batch_destroy(nll_batch* b);
+
 /*
  * nll_eval_grad_4d_noalloc -- NLL and gradient of the 4D model for a sample that stays in
  * the caller's device memory, without allocating any device memory.  The paper has no

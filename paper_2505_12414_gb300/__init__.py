@@ -94,6 +94,19 @@ def load(path=None):
     L.nll_precomputed_basis.argtypes = [vp, _DP]
     L.nll_calibrate_fp64.argtypes = [ctypes.c_int, _DP]
     L.nll_diag_math.argtypes = [ctypes.c_int, ctypes.c_int, _DP, _DP, ctypes.c_int64]
+    L.nll_batch_create.argtypes = [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.nll_batch_load.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.c_int]
+    L.nll_batch_eval_grad.argtypes = [vp, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int)]
+    L.nll_batch_fit.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(fit_options), ctypes.POINTER(fit_result), ctypes.POINTER(ctypes.c_int)]
+    L.nll_batch_set_schedule.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.nll_batch_get_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.nll_batch_autotune.argtypes = [vp]
+    L.nll_batch_num_toys.argtypes = [vp]
+    L.nll_batch_last_error.argtypes = [vp]
+    L.nll_batch_last_error.restype = ctypes.c_char_p
+    L.nll_batch_destroy.argtypes = [vp]
+    L.nll_batch_destroy.restype = None
     L.nll_eval_grad_4d_noalloc.argtypes = [_DP, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64,
                                            _DP, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _DP, _DP]
     _lib = L
@@ -402,6 +415,98 @@ class Model:
     def close(self):
         if self.handle:
             nll_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------
+# batched pseudo-experiments
+# ------------------------------------------------------------------------------------
+def _bcheck(handle, st):
+    if st != NLL_OK:
+        raise NLLError(st, load().nll_batch_last_error(handle).decode())
+
+
+class Batch:
+    """Many toys of one model (CSR samples); batched evaluation and device-resident fits."""
+
+    def __init__(self, kind, obs_ranges, device=0, stream=0):
+        L = load()
+        r = _f64(obs_ranges)
+        h = ctypes.c_void_p()
+        st = L.nll_batch_create(int(kind), _p(r), int(device), int(stream or 0), ctypes.byref(h))
+        if st != NLL_OK:
+            raise NLLError(st, "nll_batch_create failed")
+        self.handle = h.value
+        self.kind = kind
+        self.npar = 4 if kind == NLL_MODEL_MASS1D else 18
+        self.n_toys = 0
+
+    def load(self, offsets, columns, weights=None, precompute=True):
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        cols = [_f64(c) for c in columns]
+        ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+        w = _f64(weights) if weights is not None else None
+        st = load().nll_batch_load(self.handle, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(off) - 1,
+                                   ptrs, w.ctypes.data if w is not None else None, 1 if precompute else 0)
+        _bcheck(self.handle, st)
+        self.n_toys = len(off) - 1
+        return self
+
+    def eval_grad(self, thetas):
+        """(nll[n], grad[n, npar], status[n]) at one parameter point per toy."""
+        th = _f64(np.broadcast_to(np.asarray(thetas, dtype=np.float64), (self.n_toys, self.npar)))
+        nll = np.zeros(self.n_toys)
+        g = np.zeros((self.n_toys, self.npar))
+        stv = np.zeros(self.n_toys, dtype=np.int32)
+        load().nll_batch_eval_grad(self.handle, _p(th), _p(nll), _p(g), stv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return nll, g, stv
+
+    def fit(self, theta0, lo=None, hi=None, step=None, fixed=None, tol_edm=1e-8, max_iter=500, strategy=1,
+            hessian=1):
+        """Fit every toy on the device; returns a dict of per-toy arrays and 'steps'."""
+        t0 = np.asarray(theta0, dtype=np.float64)
+        shared = 1 if t0.ndim == 1 else 0
+        th, lo, hi, step, fx = _fit_args(t0.reshape(-1)[: self.npar] if shared else t0[0], lo, hi, step, fixed)
+        th = _f64(t0)
+        opt = fit_options(tol_edm, max_iter, strategy, hessian)
+        res = (fit_result * max(self.n_toys, 1))()
+        steps = ctypes.c_int()
+        st = load().nll_batch_fit(self.handle, _p(th), shared, _p(lo), _p(hi), _p(step),
+                                  fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt), res,
+                                  ctypes.byref(steps))
+        if st not in (NLL_OK, NLL_ERR_NOT_CONVERGED):
+            _bcheck(self.handle, st)
+        n = self.npar
+        out = dict(theta=np.array([r.theta[:n] for r in res[: self.n_toys]]),
+                   err=np.array([r.err[:n] for r in res[: self.n_toys]]),
+                   nll=np.array([r.nll for r in res[: self.n_toys]]),
+                   edm=np.array([r.edm for r in res[: self.n_toys]]),
+                   n_eval=np.array([r.n_eval for r in res[: self.n_toys]]),
+                   n_iter=np.array([r.n_iter for r in res[: self.n_toys]]),
+                   status=np.array([r.status for r in res[: self.n_toys]]), steps=steps.value)
+        out["cov"] = np.array([np.ctypeslib.as_array(r.cov)[: n * n].reshape(n, n) for r in res[: self.n_toys]])
+        return out
+
+    def set_schedule(self, tile_events=0, blocks_per_sm=0):
+        _bcheck(self.handle, load().nll_batch_set_schedule(self.handle, int(tile_events), int(blocks_per_sm)))
+
+    def get_schedule(self):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _bcheck(self.handle, load().nll_batch_get_schedule(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return dict(tile_events=a.value, blocks_per_sm=b.value)
+
+    def autotune(self):
+        _bcheck(self.handle, load().nll_batch_autotune(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().nll_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

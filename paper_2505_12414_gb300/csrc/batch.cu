@@ -1,0 +1,1315 @@
+// batch.cu -- batched pseudo-experiments: many independent fits of one model, each toy
+// with its own sample (CSR, uneven sizes), evaluated and minimised on the device.
+//
+// The paper validates fits with pseudo-experiments and uses them for coverage corrections
+// (Sec. 1, Sec. 2.5, Sec. 3.1); its toy study runs generate -> fit -> HESSE one toy at a time
+// with the minimiser on the host.  Here one device step advances every active toy:
+//   batch_prepare  (thread per toy)  parameter-only terms of each toy's trial point(s)
+//                                    (Sec. 2.4.1 hoisting, computed on the device), one work
+//                                    item per (toy, point) and one work unit per event tile;
+//   batch_eval     (persistent)      blocks pull units from a device counter and run the
+//                                    fused per-event NLL+gradient pass of the single-sample
+//                                    kernel over the unit's tile, writing the unit's sums;
+//   batch_update   (warp per toy)    sums the units of each item in tile order, assembles
+//                                    NLL and gradient and advances the toy's minimiser:
+//                                    BFGS on sine-transformed bounded parameters with an
+//                                    Armijo line search, optionally started from and finished
+//                                    with a finite-difference Hessian of the analytic gradient
+//                                    (all stencil points of all toys in one step).
+// The three launches (plus a counter reset) are captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/gbnll.h"
+#include "fp64_math.cuh"
+#include "gbnll_internal.h"
+#include "nll_device.cuh"
+
+namespace gbnll {
+namespace {
+
+constexpr int kNP = 18;                 // largest parameter count
+constexpr int kMaxSlots = 2 * kNP + 1;  // trial point + stencil points per toy and step
+constexpr int kEvalThreads = 128;
+constexpr int kUpdWarps = 4;
+const double kPiH = 3.14159265358979323846;
+
+__device__ double g_btab[kExpTable];
+
+enum Phase : int { kPhInit = 0, kPhSearch = 1, kPhHess = 2, kPhDone = 3 };
+
+// Derivative constants of one parameter point (device copy of the host Hoist fields).
+struct DConst {
+    double mu, sigma, alpha, f, ma, b0, b2, dlnN1_dmu, dlnN1_dsig, dlnN2t_dal, dlnNc[3];
+    int ok;
+};
+
+// Minimiser state of one toy (device).
+struct ToyFit {
+    int phase, iter, n_eval, status, first;
+    double f, ft, edm, alpha, gp;
+    double x[kNP], g[kNP], p[kNP], xt[kNP], sint[kNP], hstep[kNP];
+    double th[kNP];    // external parameters of the accepted point (all npar)
+    double gext[kNP];  // external gradient (free components) at the accepted point
+    double V[kNP * kNP];
+    double gsten[2 * kNP][kNP];
+    double cov[kNP * kNP];
+    double err[kNP];
+    int item[kMaxSlots];
+};
+
+struct FitConfig {
+    int kind, npar, nf, strategy, hessian, max_iter;
+    double tol_edm;
+    double ranges[8];
+    int idx[kNP];
+    int bounded[kNP];
+    double lo[kNP], hi[kNP];
+};
+
+struct BatchDev {
+    int n_toys, tile_pairs;        // tile_pairs = 0: one unit per item
+    const int64_t* ev_begin;       // per toy, even
+    const int64_t* ev_end;         // per toy, exclusive
+    const double* sum_wdm;         // per toy: sum w (m - ma)
+    KArgs cols;                    // column pointers and weights
+    ToyFit* fits;
+    int* counters;                 // [0] items, [1] units, [2] next unit
+    int* n_active;                 // toys not yet done (mapped host memory)
+    int* item_toy;
+    int* item_u0;
+    int* item_nt;
+    KConst* item_kc;
+    DConst* item_dc;
+    int* unit_item;
+    int* unit_tile;
+    double* unit_sums;             // [max_units][kAccMax]
+    int max_items, max_units;
+    FitConfig cfg;
+};
+
+// ---------------------------------------------------------------------------------
+// device-side parameter-only terms and gradient assembly (same formulas as runtime.cu)
+// ---------------------------------------------------------------------------------
+__device__ double dev_gauss_norm(double za, double zb)
+{
+    if (zb > 0.0) return 0.5 * (erfc(zb) - erfc(za));
+    if (za < 0.0) return 0.5 * (erfc(-za) - erfc(-zb));
+    return 0.5 * (erf(za) - erf(zb));
+}
+
+__device__ bool dev_hoist(int kind, const double* ranges, const double* th, KConst& k, DConst& H)
+{
+    const int npar = kind == kMass1D ? 4 : 18;
+    for (int i = 0; i < npar; ++i)
+        if (!isfinite(th[i])) return false;
+    const double ma = ranges[0], mb = ranges[1], D = mb - ma;
+    double mu = th[0], sigma = th[1];
+    double alpha = kind == kMass1D ? th[2] : th[10];
+    double f = kind == kMass1D ? th[3] : th[17];
+    if (!(sigma > 0.0) || !(f > 0.0 && f < 1.0)) return false;
+    double za = (mu - ma) / (sqrt(2.0) * sigma), zb = (mu - mb) / (sqrt(2.0) * sigma);
+    double N1 = dev_gauss_norm(za, zb);
+    if (!(N1 > 1e-300)) return false;
+    double ea = exp(-za * za), eb = exp(-zb * zb);
+    H.dlnN1_dmu = (ea - eb) / (sqrt(2.0 * kPiH) * sigma * N1);
+    H.dlnN1_dsig = -(za * ea - zb * eb) / (sqrt(kPiH) * sigma * N1);
+    double t = alpha * D, Nt2;
+    if (alpha == 0.0) {
+        Nt2 = D;
+        H.dlnN2t_dal = 0.5 * D;
+    } else {
+        Nt2 = expm1(t) / alpha;
+        if (fabs(t) > 1e-3)
+            H.dlnN2t_dal = D * (-1.0 / expm1(-t) - 1.0 / t);
+        else
+            H.dlnN2t_dal = D * (0.5 + t / 12.0 - t * t * t / 720.0 + t * t * t * t * t / 30240.0);
+    }
+    double b0 = 1.0 / (2.0 * sigma * sigma);
+    double lnb1 = log(f) - 0.5 * log(2.0 * kPiH) - log(sigma) - log(N1);
+    double b2 = (1.0 - f) / Nt2;
+    if (kind == kKstar4D) {
+        for (int j = 0; j < 3; ++j) {
+            double nc = 2.0 - (2.0 / 3.0) * th[12 + 2 * j];
+            if (!(nc > 0.0)) return false;
+            H.dlnNc[j] = (-2.0 / 3.0) / nc;
+            b2 /= nc * (j == 2 ? kPiH : 1.0);
+        }
+    }
+    if (fabs(alpha) * D + fmax(lnb1, 0.0) > 700.0) return false;
+    H.mu = mu;
+    H.sigma = sigma;
+    H.alpha = alpha;
+    H.f = f;
+    H.ma = ma;
+    H.b0 = b0;
+    H.b2 = b2;
+    const double S = kExpArgScale;
+    k.mu = mu;
+    k.neg_b0 = -b0 * S;
+    k.neg_alpha = -alpha * S;
+    k.k0 = (lnb1 - alpha * (mu - ma)) * S;
+    k.b2 = b2;
+    if (kind == kKstar4D) {
+        for (int j = 0; j < 8; ++j) k.ang[j] = th[2 + j];
+        k.cq[0] = b2;
+        k.cq[1] = b2 * th[11];
+        k.cq[2] = b2 * th[12];
+        k.cq[3] = 1.0;
+        k.cq[4] = th[13];
+        k.cq[5] = th[14];
+        k.cq[6] = 1.0;
+        k.cq[7] = th[15];
+        k.cq[8] = th[16];
+    }
+    H.ok = 1;
+    return true;
+}
+
+// NLL and full external gradient from the sums S; false if the density was not positive.
+__device__ bool dev_assemble(int kind, const DConst& H, double sum_wdm, const double* S, double& nll, double* g)
+{
+    const int K = kind == kMass1D ? kAcc1D : kAcc4D;
+    if (S[K - 1] != 0.0 || !isfinite(S[0])) return false;
+    nll = -(H.alpha * sum_wdm + S[0]);
+    const double two_b0 = 2.0 * H.b0, dma = H.mu - H.ma;
+    double dL[kNP];
+    dL[0] = two_b0 * S[2] - H.dlnN1_dmu * S[1];
+    dL[1] = two_b0 / H.sigma * S[3] - (1.0 / H.sigma + H.dlnN1_dsig) * S[1];
+    int npar;
+    if (kind == kMass1D) {
+        double sre = H.b2 * S[4], sred = H.b2 * S[5];
+        dL[2] = sred + dma * sre - H.dlnN2t_dal * sre;
+        dL[3] = S[1] / H.f - sre / (1.0 - H.f);
+        npar = 4;
+    } else {
+        for (int k = 0; k < 8; ++k) dL[2 + k] = S[4 + k];
+        double sre = S[12], sred = S[13];
+        dL[10] = sred + dma * sre - H.dlnN2t_dal * sre;
+        dL[11] = H.b2 * S[14];
+        dL[12] = H.b2 * S[15] - H.dlnNc[0] * sre;
+        dL[13] = S[16];
+        dL[14] = S[17] - H.dlnNc[1] * sre;
+        dL[15] = S[18];
+        dL[16] = S[19] - H.dlnNc[2] * sre;
+        dL[17] = S[1] / H.f - sre / (1.0 - H.f);
+        npar = 18;
+    }
+    for (int k = 0; k < npar; ++k) g[k] = -dL[k];
+    return isfinite(nll);
+}
+
+// ---------------------------------------------------------------------------------
+// sine transform of bounded parameters (Minuit manual)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double to_ext(const FitConfig& c, int i, double x)
+{
+    int k = c.idx[i];
+    return c.bounded[k] ? c.lo[k] + (c.hi[k] - c.lo[k]) * 0.5 * (sin(x) + 1.0) : x;
+}
+
+__device__ __forceinline__ double jac(const FitConfig& c, int i, double x)
+{
+    int k = c.idx[i];
+    return c.bounded[k] ? (c.hi[k] - c.lo[k]) * 0.5 * cos(x) : 1.0;
+}
+
+// ---------------------------------------------------------------------------------
+// prepare: one thread per toy
+// ---------------------------------------------------------------------------------
+__device__ void emit_item(const BatchDev& b, int toy, int slot, const double* th, int64_t npairs)
+{
+    ToyFit& F = b.fits[toy];
+    int nt = 0;
+    if (npairs > 0) nt = b.tile_pairs ? (int)((npairs + b.tile_pairs - 1) / b.tile_pairs) : 1;
+    KConst kc;
+    DConst dc;
+    memset(&kc, 0, sizeof kc);
+    memset(&dc, 0, sizeof dc);
+    bool ok = dev_hoist(b.cfg.kind, b.cfg.ranges, th, kc, dc);
+    if (!ok) nt = 0;
+    int it = atomicAdd(&b.counters[0], 1);
+    if (it >= b.max_items) {  // cannot happen with the host's sizing; keep the toy consistent
+        F.item[slot] = -1;
+        return;
+    }
+    int u0 = nt ? atomicAdd(&b.counters[1], nt) : 0;
+    if (u0 + nt > b.max_units) {
+        nt = 0;
+        dc.ok = 0;
+    }
+    b.item_toy[it] = toy;
+    b.item_u0[it] = u0;
+    b.item_nt[it] = nt;
+    b.item_kc[it] = kc;
+    b.item_dc[it] = dc;
+    for (int j = 0; j < nt; ++j) {
+        b.unit_item[u0 + j] = it;
+        b.unit_tile[u0 + j] = j;
+    }
+    F.item[slot] = it;
+}
+
+__global__ void batch_prepare(BatchDev b)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= b.n_toys) return;
+    ToyFit& F = b.fits[t];
+    for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
+    if (F.phase == kPhDone) return;
+    const FitConfig& c = b.cfg;
+    const int64_t npairs = (b.ev_end[t] - b.ev_begin[t] + 1) / 2;
+    double th[kNP];
+    for (int k = 0; k < c.npar; ++k) th[k] = F.th[k];
+    if (F.phase == kPhInit || F.phase == kPhSearch) {
+        for (int i = 0; i < c.nf; ++i) th[c.idx[i]] = to_ext(c, i, F.xt[i]);
+        emit_item(b, t, 0, th, npairs);
+        if (F.phase == kPhInit && c.strategy) {
+            // stencil in internal coordinates around the start point
+            for (int j = 0; j < c.nf; ++j)
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    for (int i = 0; i < c.nf; ++i) th[c.idx[i]] = to_ext(c, i, F.xt[i]);
+                    double h = 0.1 * F.sint[j];
+                    th[c.idx[j]] = to_ext(c, j, F.xt[j] + (sgn ? -h : h));
+                    emit_item(b, t, 1 + 2 * j + sgn, th, npairs);
+                }
+        }
+    } else if (F.phase == kPhHess) {
+        // stencil in external coordinates around the minimum
+        for (int j = 0; j < c.nf; ++j)
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                for (int k = 0; k < c.npar; ++k) th[k] = F.th[k];
+                th[c.idx[j]] += sgn ? -F.hstep[j] : F.hstep[j];
+                emit_item(b, t, 1 + 2 * j + sgn, th, npairs);
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// evaluate: persistent blocks over work units
+// ---------------------------------------------------------------------------------
+template <int KIND, int VAR, bool W>
+__global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
+{
+    constexpr int K = KIND == kMass1D ? kAcc1D : kAcc4D;
+    __shared__ double s_tab[kExpTable];
+    __shared__ double s_red[(kEvalThreads / 32) * K];
+    __shared__ int s_u;
+    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_tab[j] = g_btab[j];
+    __syncthreads();
+    const int nunits = min(b.counters[1], b.max_units);
+    while (true) {
+        if (threadIdx.x == 0) s_u = atomicAdd(&b.counters[2], 1);
+        __syncthreads();
+        const int u = s_u;
+        __syncthreads();
+        if (u >= nunits) break;
+        const int item = b.unit_item[u], tile = b.unit_tile[u];
+        const int toy = b.item_toy[item];
+        const KConst c = b.item_kc[item];
+        const int64_t ev_end = b.ev_end[toy];
+        const int64_t p_first = b.ev_begin[toy] / 2, p_last = (ev_end + 1) / 2;
+        int64_t pb = p_first, pe = p_last;
+        if (b.tile_pairs) {
+            pb = p_first + (int64_t)tile * b.tile_pairs;
+            pe = min(pb + (int64_t)b.tile_pairs, p_last);
+        }
+        double acc[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[k] = 0.0;
+        LogProd lpx{1.0, 0}, lpy{1.0, 0};
+        int bad = 0;
+        for (int64_t p = pb + threadIdx.x; p < pe; p += blockDim.x) {
+            PairIn in;
+            load_pair<KIND, VAR, W>(b.cols, p, in);
+            process_pair<KIND, VAR, W, true>(c, in, (2 * p + 1) < ev_end, acc, lpx, lpy, bad, s_tab);
+        }
+        if (!W) {
+            double lw = logprod_value(logprod_warp(logprod_combine(lpx, lpy)));
+            acc[0] = (threadIdx.x & 31) == 0 ? lw : 0.0;
+        }
+        acc[K - 1] = (double)bad;
+        double r = block_reduce<K>(acc, s_red);
+        if (threadIdx.x < K) b.unit_sums[(size_t)u * kAccMax + threadIdx.x] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// update: one warp per toy
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ double wsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// inverse of the symmetric positive-definite n x n matrix A (row-major, smem) into Out by a
+// warp: Cholesky A = L L^T (right-looking, lane i owns row i), M = L^-1 (lane j owns column j),
+// Out = M^T M.  Returns false (all lanes) if A is not positive definite.
+__device__ bool warp_spd_inverse(int n, double* A, double* L, double* M, double* Out)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < n * n; i += 32)
+        if (i + lane < n * n) L[i + lane] = 0.0;
+    __syncwarp();
+    bool ok = true;
+    for (int k = 0; k < n; ++k) {
+        double d = A[k * n + k];
+        if (!(d > 0.0) || !isfinite(d)) ok = false;
+        double lkk = sqrt(fmax(d, 1e-300));
+        if (lane == k) L[k * n + k] = lkk;
+        if (lane > k && lane < n) L[lane * n + k] = A[lane * n + k] / lkk;
+        __syncwarp();
+        if (lane > k && lane < n)
+            for (int j = k + 1; j <= lane; ++j) A[lane * n + j] -= L[lane * n + k] * L[j * n + k];
+        __syncwarp();
+    }
+    if (!ok) return false;
+    if (lane < n) {
+        const int j = lane;
+        for (int i = 0; i < n; ++i) M[i * n + j] = 0.0;
+        for (int i = j; i < n; ++i) {
+            double s = (i == j) ? 1.0 : 0.0;
+            for (int k = j; k < i; ++k) s -= L[i * n + k] * M[k * n + j];
+            M[i * n + j] = s / L[i * n + i];
+        }
+    }
+    __syncwarp();
+    if (lane < n) {
+        const int i = lane;
+        for (int j = 0; j < n; ++j) {
+            double s = 0.0;
+            for (int k = max(i, j); k < n; ++k) s += M[k * n + i] * M[k * n + j];
+            Out[i * n + j] = s;
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
+{
+    constexpr int K = KIND == kMass1D ? kAcc1D : kAcc4D;
+    __shared__ double s_S[kUpdWarps][32];
+    __shared__ double s_g[kUpdWarps][kNP];
+    __shared__ double s_mat[kUpdWarps][4][kNP * kNP];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kUpdWarps + wib;
+    if (t >= b.n_toys) return;
+    ToyFit& F = b.fits[t];
+    if (F.phase == kPhDone) return;
+    const FitConfig& c = b.cfg;
+    const int nf = c.nf;
+    const bool mine = lane < nf;
+
+    // assemble every evaluated slot: f_s and the free components of the external gradient
+    double f0 = INFINITY, g0 = 0.0;  // slot 0 (lane-uniform f0; lane i holds component i)
+    bool ok0 = false, sten_ok = true;
+    int nslots = 0;
+    for (int s = 0; s < kMaxSlots; ++s) {
+        const int it = F.item[s];
+        if (it < 0) continue;
+        ++nslots;
+        const int u0 = b.item_u0[it], nt = b.item_nt[it];
+        double v = 0.0;
+        if (lane < K)
+            for (int j = 0; j < nt; ++j) v += b.unit_sums[(size_t)(u0 + j) * kAccMax + lane];
+        s_S[wib][lane] = v;
+        __syncwarp();
+        double fv = INFINITY;
+        int okv = 0;
+        if (lane == 0) {
+            const DConst dc = b.item_dc[it];
+            double gfull[kNP];
+            if (dc.ok && dev_assemble(c.kind, dc, b.sum_wdm[t], s_S[wib], fv, gfull)) {
+                okv = 1;
+                for (int i = 0; i < nf; ++i) s_g[wib][i] = gfull[c.idx[i]];
+            }
+        }
+        __syncwarp();
+        fv = __shfl_sync(0xffffffffu, fv, 0);
+        okv = __shfl_sync(0xffffffffu, okv, 0);
+        double gi = (mine && okv) ? s_g[wib][lane] : 0.0;
+        __syncwarp();
+        if (s == 0) {
+            f0 = fv;
+            ok0 = okv;
+            g0 = gi;
+        } else {
+            if (!okv) sten_ok = false;
+            if (mine) F.gsten[s - 1][lane] = gi;
+        }
+    }
+    if (lane == 0) F.n_eval += nslots;
+
+    double* A = s_mat[wib][0];
+    double* Lm = s_mat[wib][1];
+    double* Mm = s_mat[wib][2];
+    double* Out = s_mat[wib][3];
+    const double c1 = 1e-4;
+    bool finish = false;      // reached the convergence test (go to the Hessian or done)
+    int done_status = -1;     // >= 0: toy ends with this status
+
+    if (F.phase == kPhInit) {
+        if (!ok0) {
+            done_status = NLL_ERR_NONPOSITIVE_PDF;
+        } else {
+            const double xi = mine ? F.xt[lane] : 0.0;
+            const double Ji = mine ? jac(c, lane, xi) : 0.0;
+            double gi = g0 * Ji;
+            if (mine) {
+                F.x[lane] = xi;
+                F.g[lane] = gi;
+                F.gext[lane] = g0;
+                F.th[c.idx[lane]] = to_ext(c, lane, xi);
+            }
+            if (lane == 0) F.f = f0;
+            // initial inverse Hessian: diag(step^2), or the inverse of the stencil Hessian
+            bool have = false;
+            if (c.strategy && sten_ok) {
+                for (int j = 0; j < nf; ++j) {
+                    double h = 0.1 * F.sint[j];
+                    if (mine) {
+                        // internal gradient at x +- h e_j: the Jacobian changes only in component j
+                        double Jp = lane == j ? jac(c, lane, xi + h) : Ji;
+                        double Jm = lane == j ? jac(c, lane, xi - h) : Ji;
+                        A[lane * nf + j] = (F.gsten[2 * j][lane] * Jp - F.gsten[2 * j + 1][lane] * Jm) / (2.0 * h);
+                    }
+                }
+                __syncwarp();
+                if (mine)
+                    for (int j = 0; j < lane; ++j) {
+                        double sym = 0.5 * (A[lane * nf + j] + A[j * nf + lane]);
+                        A[lane * nf + j] = sym;
+                    }
+                __syncwarp();
+                if (mine)
+                    for (int j = lane + 1; j < nf; ++j) A[lane * nf + j] = A[j * nf + lane];
+                __syncwarp();
+                have = warp_spd_inverse(nf, A, Lm, Mm, Out);
+                if (have && mine)
+                    for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = Out[lane * nf + j];
+            }
+            if (!have && mine)
+                for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? F.sint[lane] * F.sint[lane] : 0.0;
+            if (lane == 0) F.first = have ? 0 : 1;
+            __syncwarp();
+            // direction
+            double vg = 0.0;
+            if (mine)
+                for (int j = 0; j < nf; ++j) vg += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, gi, j);
+            else
+                for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, gi, j);
+            double edm = 0.5 * wsum(mine ? gi * vg : 0.0);
+            double pi = -vg;
+            double gp = wsum(mine ? gi * pi : 0.0);
+            if (lane == 0) {
+                F.edm = edm;
+                F.gp = gp;
+                F.alpha = 1.0;
+                F.iter = 1;
+            }
+            if (mine) {
+                F.p[lane] = pi;
+                F.xt[lane] = xi + pi;
+            }
+            if (edm < c.tol_edm) finish = true;
+            else if (lane == 0) F.phase = kPhSearch;
+        }
+    } else if (F.phase == kPhSearch) {
+        const double f = F.f, alpha = F.alpha, gp = F.gp;
+        const bool accept = ok0 && f0 <= f + c1 * alpha * gp;
+        if (accept) {
+            const double xt = mine ? F.xt[lane] : 0.0, x = mine ? F.x[lane] : 0.0, gi_old = mine ? F.g[lane] : 0.0;
+            const double gt = mine ? g0 * jac(c, lane, xt) : 0.0;
+            const double si = xt - x, yi = gt - gi_old;
+            const double ys = wsum(yi * si), yy = wsum(yi * yi), ss = wsum(si * si);
+            if (ys > 1e-300 && ys > 1e-12 * sqrt(yy * ss)) {
+                if (F.first && mine)
+                    for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? ys / yy : 0.0;
+                __syncwarp();
+                double vy = 0.0;
+                if (mine)
+                    for (int j = 0; j < nf; ++j) vy += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, yi, j);
+                else
+                    for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, yi, j);
+                const double yvy = wsum(mine ? yi * vy : 0.0);
+                const double rho = 1.0 / ys;
+                __syncwarp();
+                for (int j = 0; j < nf; ++j) {
+                    const double sj = __shfl_sync(0xffffffffu, si, j), vyj = __shfl_sync(0xffffffffu, vy, j);
+                    if (mine) F.V[lane * nf + j] += rho * ((1.0 + rho * yvy) * si * sj - vy * sj - si * vyj);
+                }
+                if (lane == 0) F.first = 0;
+            }
+            __syncwarp();
+            if (mine) {
+                F.x[lane] = xt;
+                F.g[lane] = gt;
+                F.gext[lane] = g0;
+                F.th[c.idx[lane]] = to_ext(c, lane, xt);
+            }
+            if (lane == 0) F.f = f0;
+            __syncwarp();
+            double vg = 0.0;
+            if (mine)
+                for (int j = 0; j < nf; ++j) vg += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, gt, j);
+            else
+                for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, gt, j);
+            const double edm = 0.5 * wsum(mine ? gt * vg : 0.0);
+            if (lane == 0) F.edm = edm;
+            if (edm < c.tol_edm) {
+                finish = true;
+            } else if (F.iter >= c.max_iter) {
+                done_status = NLL_ERR_NOT_CONVERGED;
+            } else {
+                double pi = -vg;
+                double gpn = wsum(mine ? gt * pi : 0.0);
+                if (!(gpn < 0.0)) {  // not a descent direction: restart from the diagonal
+                    if (mine)
+                        for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? F.sint[lane] * F.sint[lane] : 0.0;
+                    pi = mine ? -F.sint[lane] * F.sint[lane] * gt : 0.0;
+                    gpn = wsum(mine ? gt * pi : 0.0);
+                }
+                if (mine) {
+                    F.p[lane] = pi;
+                    F.xt[lane] = xt + pi;
+                }
+                if (lane == 0) {
+                    F.gp = gpn;
+                    F.alpha = 1.0;
+                    F.iter += 1;
+                }
+            }
+        } else {
+            double anew;
+            if (ok0 && isfinite(f0)) {
+                const double denom = 2.0 * (f0 - f - gp * alpha);
+                anew = denom > 0.0 ? -gp * alpha * alpha / denom : 0.5 * alpha;
+                anew = fmin(fmax(anew, 0.1 * alpha), 0.5 * alpha);
+            } else {
+                anew = 0.25 * alpha;
+            }
+            if (anew < 1e-12) {
+                done_status = F.edm < 100.0 * c.tol_edm ? NLL_OK : NLL_ERR_NOT_CONVERGED;
+                finish = done_status == NLL_OK;
+                if (finish) done_status = -1;
+            } else {
+                if (mine) F.xt[lane] = F.x[lane] + anew * F.p[lane];
+                if (lane == 0) F.alpha = anew;
+            }
+        }
+    } else if (F.phase == kPhHess) {
+        bool have = false;
+        if (sten_ok) {
+            for (int j = 0; j < nf; ++j)
+                if (mine) A[lane * nf + j] = (F.gsten[2 * j][lane] - F.gsten[2 * j + 1][lane]) / (2.0 * F.hstep[j]);
+            __syncwarp();
+            if (mine)
+                for (int j = 0; j < lane; ++j) A[lane * nf + j] = 0.5 * (A[lane * nf + j] + A[j * nf + lane]);
+            __syncwarp();
+            if (mine)
+                for (int j = lane + 1; j < nf; ++j) A[lane * nf + j] = A[j * nf + lane];
+            __syncwarp();
+            have = warp_spd_inverse(nf, A, Lm, Mm, Out);
+        }
+        if (have) {
+            if (mine)
+                for (int j = 0; j < nf; ++j) F.cov[lane * nf + j] = Out[lane * nf + j];
+            __syncwarp();
+            const double ge = mine ? F.gext[lane] : 0.0;
+            double cg = 0.0;
+            if (mine)
+                for (int j = 0; j < nf; ++j) cg += F.cov[lane * nf + j] * __shfl_sync(0xffffffffu, ge, j);
+            else
+                for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, ge, j);
+            const double edm = 0.5 * wsum(mine ? ge * cg : 0.0);
+            if (lane == 0) F.edm = edm;
+        }
+        // (without a positive-definite Hessian the BFGS covariance set before stays)
+        if (mine) F.err[lane] = sqrt(fmax(F.cov[lane * nf + lane], 0.0));
+        done_status = NLL_OK;
+    }
+
+    if (finish) {
+        // covariance from the BFGS matrix in external coordinates, C = J V J
+        const double Ji = mine ? jac(c, lane, F.x[lane]) : 0.0;
+        for (int j = 0; j < nf; ++j) {
+            const double Jj = __shfl_sync(0xffffffffu, Ji, j);
+            if (mine) F.cov[lane * nf + j] = Ji * F.V[lane * nf + j] * Jj;
+        }
+        __syncwarp();
+        if (mine) F.err[lane] = sqrt(fmax(F.cov[lane * nf + lane], 0.0));
+        if (c.hessian) {
+            if (mine) {
+                double sd = F.err[lane];
+                if (!(sd > 0.0)) sd = F.sint[lane];
+                F.hstep[lane] = 1e-3 * sd;
+            }
+            if (lane == 0) F.phase = kPhHess;
+        } else {
+            done_status = NLL_OK;
+        }
+    }
+    if (done_status >= 0 && lane == 0) {
+        F.status = done_status;
+        F.phase = kPhDone;
+        atomicSub(b.n_active, 1);
+    }
+}
+
+template <int KIND, int VAR, bool W>
+cudaError_t launch_eval_t(int blocks, cudaStream_t s, const BatchDev& b)
+{
+    batch_eval<KIND, VAR, W><<<blocks, kEvalThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval(int kind, int var, bool w, int blocks, cudaStream_t s, const BatchDev& b)
+{
+    if (kind == kMass1D) return w ? launch_eval_t<kMass1D, kVarPrecompute, true>(blocks, s, b)
+                                  : launch_eval_t<kMass1D, kVarPrecompute, false>(blocks, s, b);
+    if (var == kVarDirect) return w ? launch_eval_t<kKstar4D, kVarDirect, true>(blocks, s, b)
+                                    : launch_eval_t<kKstar4D, kVarDirect, false>(blocks, s, b);
+    return w ? launch_eval_t<kKstar4D, kVarPrecompute, true>(blocks, s, b)
+             : launch_eval_t<kKstar4D, kVarPrecompute, false>(blocks, s, b);
+}
+
+std::mutex g_btab_mutex;
+bool g_btab_ready[64];
+
+cudaError_t ensure_btab(int device)
+{
+    std::lock_guard<std::mutex> lock(g_btab_mutex);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (g_btab_ready[device]) return cudaSuccess;
+    std::vector<double> tab(kExpTable);
+    for (int j = 0; j < kExpTable; ++j) tab[j] = (double)exp2l((long double)j / (long double)kExpTable);
+    cudaError_t e = cudaMemcpyToSymbol(g_btab, tab.data(), sizeof(double) * kExpTable);
+    if (e == cudaSuccess) g_btab_ready[device] = true;
+    return e;
+}
+
+}  // namespace
+}  // namespace gbnll
+
+using namespace gbnll;
+
+// ------------------------------------------------------------------------------------
+// host runtime
+// ------------------------------------------------------------------------------------
+struct nll_batch {
+    int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
+    cudaStream_t user_stream = nullptr;  // caller's stream (0 = default)
+    cudaStream_t stream = nullptr;       // the batch's own stream (graph capture needs one)
+    double ranges[8] = {0};
+    int n_toys = 0;
+    int64_t n_pad = 0;                   // padded events per column
+    int ncols = 0;
+    bool weighted = false, has_basis = false, loaded = false;
+    double* d_ev = nullptr;
+    double* d_w = nullptr;
+    std::vector<int64_t> begin, end;     // padded positions per toy
+    std::vector<double> sum_wdm;
+    int64_t* d_begin = nullptr;
+    int64_t* d_end = nullptr;
+    double* d_sum_wdm = nullptr;
+    // work arrays
+    int max_items = 0, max_units = 0;
+    int* d_counters = nullptr;
+    int* h_active = nullptr;  // mapped
+    int* d_active = nullptr;
+    int* d_item_toy = nullptr;
+    int* d_item_u0 = nullptr;
+    int* d_item_nt = nullptr;
+    KConst* d_item_kc = nullptr;
+    DConst* d_item_dc = nullptr;
+    int* d_unit_item = nullptr;
+    int* d_unit_tile = nullptr;
+    double* d_unit_sums = nullptr;
+    ToyFit* d_fits = nullptr;
+    // schedule
+    int tile_events = 0, bps = 2;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int bfail(nll_batch* b, int status, const char* fmt, ...)
+{
+    if (b) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        b->err = buf;
+    }
+    return status;
+}
+
+int bcuda(nll_batch* b, cudaError_t e, const char* what)
+{
+    return bfail(b, e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA, "%s: %s", what,
+                 cudaGetErrorString(e));
+}
+
+void free_work(nll_batch* b)
+{
+    void* ptrs[] = {b->d_ev, b->d_begin, b->d_end, b->d_sum_wdm, b->d_item_toy, b->d_item_u0, b->d_item_nt,
+                    b->d_item_kc, b->d_item_dc, b->d_unit_item, b->d_unit_tile, b->d_unit_sums, b->d_fits};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b->d_ev = nullptr;
+    b->d_w = nullptr;
+    b->d_begin = b->d_end = nullptr;
+    b->d_sum_wdm = nullptr;
+    b->d_item_toy = b->d_item_u0 = b->d_item_nt = nullptr;
+    b->d_item_kc = nullptr;
+    b->d_item_dc = nullptr;
+    b->d_unit_item = b->d_unit_tile = nullptr;
+    b->d_unit_sums = nullptr;
+    b->d_fits = nullptr;
+    b->loaded = false;
+}
+
+int tile_pairs_of(const nll_batch* b) { return b->tile_events > 0 ? b->tile_events / 2 : 0; }
+
+// work already queued on the caller's stream completes before the batch's own stream runs
+cudaError_t follow_user_stream(nll_batch* b)
+{
+    cudaError_t e = cudaEventRecord(b->ev0, b->user_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev0, 0);
+    return e;
+}
+
+BatchDev make_dev(nll_batch* b)
+{
+    BatchDev d;
+    memset(&d, 0, sizeof d);
+    d.n_toys = b->n_toys;
+    d.tile_pairs = tile_pairs_of(b);
+    d.ev_begin = b->d_begin;
+    d.ev_end = b->d_end;
+    d.sum_wdm = b->d_sum_wdm;
+    for (int c = 0; c < kNumCols; ++c) d.cols.col[c] = c < b->ncols ? b->d_ev + (size_t)c * b->n_pad : nullptr;
+    d.cols.w = b->weighted ? b->d_w : nullptr;
+    d.fits = b->d_fits;
+    d.counters = b->d_counters;
+    d.n_active = b->d_active;
+    d.item_toy = b->d_item_toy;
+    d.item_u0 = b->d_item_u0;
+    d.item_nt = b->d_item_nt;
+    d.item_kc = b->d_item_kc;
+    d.item_dc = b->d_item_dc;
+    d.unit_item = b->d_unit_item;
+    d.unit_tile = b->d_unit_tile;
+    d.unit_sums = b->d_unit_sums;
+    d.max_items = b->max_items;
+    d.max_units = b->max_units;
+    d.cfg.kind = b->kind;
+    d.cfg.npar = b->npar;
+    for (int i = 0; i < 8; ++i) d.cfg.ranges[i] = b->ranges[i];
+    return d;
+}
+
+int variant_of(const nll_batch* b) { return (b->kind == kKstar4D && !b->has_basis) ? kVarDirect : kVarPrecompute; }
+
+// host-hoisted evaluation of every toy at thetas (one item per toy); fills nll, grad, status
+int eval_all(nll_batch* b, const double* thetas, double* nll_out, double* grad_out, int* status_out, float* ms)
+{
+    const int n = b->n_toys, np = b->npar;
+    const int tp = tile_pairs_of(b);
+    std::vector<KConst> kc(n);
+    std::vector<Hoist> hs(n);
+    std::vector<int> item_toy(n), item_u0(n), item_nt(n), unit_item, unit_tile;
+    std::vector<int> st(n, NLL_OK);
+    int nunits = 0;
+    for (int t = 0; t < n; ++t) {
+        std::string e;
+        memset(&kc[t], 0, sizeof(KConst));
+        int s = hoist_core(b->kind, b->ranges, thetas + (size_t)t * np, true, hs[t], &e);
+        int64_t npairs = (b->end[t] - b->begin[t] + 1) / 2;
+        int nt = npairs > 0 ? (tp ? (int)((npairs + tp - 1) / tp) : 1) : 0;
+        if (s != NLL_OK) {
+            st[t] = s;
+            nt = 0;
+        } else {
+            kc[t] = hs[t].k;
+        }
+        item_toy[t] = t;
+        item_u0[t] = nunits;
+        item_nt[t] = nt;
+        for (int j = 0; j < nt; ++j) {
+            unit_item.push_back(t);
+            unit_tile.push_back(j);
+        }
+        nunits += nt;
+    }
+    if (nunits > b->max_units || n > b->max_items) return bfail(b, NLL_ERR_ARG, "work arrays too small");
+    int counters[3] = {n, nunits, 0};
+    cudaError_t e = cudaMemcpyAsync(b->d_item_kc, kc.data(), sizeof(KConst) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_item_toy, item_toy.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_item_u0, item_u0.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_item_nt, item_nt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nunits)
+        e = cudaMemcpyAsync(b->d_unit_item, unit_item.data(), sizeof(int) * nunits, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && nunits)
+        e = cudaMemcpyAsync(b->d_unit_tile, unit_tile.data(), sizeof(int) * nunits, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_counters, counters, sizeof counters, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch upload");
+    BatchDev d = make_dev(b);
+    int blocks = std::max(1, std::min(b->sm_count * b->bps, nunits));
+    if (ms) cudaEventRecord(b->ev0, b->stream);
+    if (nunits) e = launch_eval(b->kind, variant_of(b), b->weighted, blocks, b->stream, d);
+    if (ms) cudaEventRecord(b->ev1, b->stream);
+    std::vector<double> sums((size_t)std::max(nunits, 1) * kAccMax);
+    if (e == cudaSuccess && nunits)
+        e = cudaMemcpyAsync(sums.data(), b->d_unit_sums, sizeof(double) * kAccMax * nunits, cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "batch evaluation");
+    if (ms) cudaEventElapsedTime(ms, b->ev0, b->ev1);
+    const int K = num_acc(b->kind, true);
+    int first_bad = NLL_OK;
+    for (int t = 0; t < n; ++t) {
+        double* g = grad_out ? grad_out + (size_t)t * np : nullptr;
+        if (st[t] == NLL_OK) {
+            double S[kAccMax] = {0};
+            for (int j = 0; j < item_nt[t]; ++j)
+                for (int k = 0; k < K; ++k) S[k] += sums[(size_t)(item_u0[t] + j) * kAccMax + k];
+            if (S[K - 1] != 0.0 || !isfinite(S[0])) {
+                st[t] = NLL_ERR_NONPOSITIVE_PDF;
+            } else {
+                double gg[18];
+                assemble_core(b->kind, hs[t], b->sum_wdm[t], S, &nll_out[t], gg);
+                if (g)
+                    for (int k = 0; k < np; ++k) g[k] = gg[k];
+            }
+        }
+        if (st[t] != NLL_OK) {
+            nll_out[t] = INFINITY;
+            if (g)
+                for (int k = 0; k < np; ++k) g[k] = NAN;
+            if (first_bad == NLL_OK) first_bad = st[t];
+        }
+        if (status_out) status_out[t] = st[t];
+    }
+    return first_bad;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t cuda_stream, nll_batch** out)
+{
+    if (!out) return NLL_ERR_ARG;
+    *out = nullptr;
+    if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges) return NLL_ERR_ARG;
+    if (!(isfinite(obs_ranges[0]) && isfinite(obs_ranges[1]) && obs_ranges[0] < obs_ranges[1])) return NLL_ERR_ARG;
+    if (kind == NLL_MODEL_KSTARMUMU4D) {
+        const double want[6] = {-1.0, 1.0, -1.0, 1.0, -kPiH, kPiH};
+        for (int i = 0; i < 6; ++i)
+            if (fabs(obs_ranges[2 + i] - want[i]) > 1e-12) return NLL_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
+    nll_batch* b = new nll_batch();
+    b->kind = kind;
+    b->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
+    b->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
+    b->device = device;
+    b->user_stream = (cudaStream_t)cuda_stream;
+    memcpy(b->ranges, obs_ranges, sizeof(double) * 2 * b->ndim);
+    if (kind == NLL_MODEL_KSTARMUMU4D) {
+        b->ranges[6] = -kPiH;
+        b->ranges[7] = kPiH;
+    }
+    cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaError_t e = ensure_btab(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_active, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_active, b->h_active, 0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e != cudaSuccess) {
+        nll_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA;
+    }
+    *out = b;
+    return NLL_OK;
+}
+
+void nll_batch_destroy(nll_batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    free_work(b);
+    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->h_active) cudaFreeHost(b->h_active);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int nll_batch_load(nll_batch* b, const int64_t* offsets, int n_toys, const double* const* columns,
+                   const double* weights, int precompute)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (n_toys < 0 || !offsets || offsets[0] != 0) return bfail(b, NLL_ERR_ARG, "bad offsets");
+    for (int t = 0; t < n_toys; ++t)
+        if (offsets[t + 1] < offsets[t]) return bfail(b, NLL_ERR_ARG, "offsets must not decrease");
+    const int64_t total = offsets[n_toys];
+    if (total > 0 && !columns) return bfail(b, NLL_ERR_ARG, "null columns");
+    for (int d = 0; d < b->ndim && total > 0; ++d)
+        if (!columns[d]) return bfail(b, NLL_ERR_ARG, "column %d is NULL", d);
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
+    if (follow_user_stream(b) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "stream ordering failed");
+    cudaStreamSynchronize(b->stream);
+    free_work(b);
+    // padded positions: every toy starts on an even event index (pairs of events per load)
+    b->n_toys = n_toys;
+    b->begin.assign(n_toys, 0);
+    b->end.assign(n_toys, 0);
+    b->sum_wdm.assign(n_toys, 0.0);
+    int64_t pos = 0;
+    for (int t = 0; t < n_toys; ++t) {
+        pos = (pos + 1) & ~int64_t(1);
+        b->begin[t] = pos;
+        pos += offsets[t + 1] - offsets[t];
+        b->end[t] = pos;
+    }
+    const int64_t n_pad = std::max<int64_t>((pos + 63) / 64 * 64, 64);
+    // validate on the host, and sum w (m - ma) per toy (fixed order)
+    for (int t = 0; t < n_toys; ++t) {
+        double s = 0.0;
+        for (int64_t i = offsets[t]; i < offsets[t + 1]; ++i) {
+            double w = weights ? weights[i] : 1.0;
+            if (!(w >= 0.0 && w <= 1e300)) return bfail(b, NLL_ERR_ARG, "invalid weight at event %lld", (long long)i);
+            for (int d = 0; d < b->ndim; ++d) {
+                double x = columns[d][i];
+                if (!(x >= b->ranges[2 * d] && x <= b->ranges[2 * d + 1]))
+                    return bfail(b, NLL_ERR_ARG, "event %lld outside the observable ranges", (long long)i);
+            }
+            s += w * (columns[0][i] - b->ranges[0]);
+        }
+        b->sum_wdm[t] = s;
+    }
+    const bool basis = b->kind == kKstar4D && precompute;
+    b->ncols = b->kind == kMass1D ? 1 : (basis ? kNumCols : 4);
+    const int nalloc = b->ncols + (weights ? 1 : 0);
+    b->n_pad = n_pad;
+    cudaError_t e = cudaMalloc(&b->d_ev, sizeof(double) * n_pad * nalloc);
+    if (e != cudaSuccess) {
+        b->d_ev = nullptr;
+        return bcuda(b, e, "batch event store");
+    }
+    e = cudaMemsetAsync(b->d_ev, 0, sizeof(double) * n_pad * nalloc, b->stream);
+    // host staging in the padded layout, one copy per column
+    std::vector<double> stage(n_pad);
+    auto put = [&](const double* src, double* dst) {
+        std::fill(stage.begin(), stage.end(), 0.0);
+        for (int t = 0; t < n_toys; ++t)
+            memcpy(stage.data() + b->begin[t], src + offsets[t], sizeof(double) * (offsets[t + 1] - offsets[t]));
+        cudaError_t e2 = cudaMemcpyAsync(dst, stage.data(), sizeof(double) * n_pad, cudaMemcpyHostToDevice, b->stream);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(b->stream);
+        return e2;
+    };
+    for (int d = 0; d < b->ndim && e == cudaSuccess && total > 0; ++d) e = put(columns[d], b->d_ev + (size_t)d * n_pad);
+    b->weighted = weights != nullptr;
+    if (weights) {
+        b->d_w = b->d_ev + (size_t)b->ncols * n_pad;
+        if (e == cudaSuccess && total > 0) e = put(weights, b->d_w);
+    }
+    if (e != cudaSuccess) {
+        free_work(b);
+        return bcuda(b, e, "batch copy");
+    }
+    if (basis && total > 0) {
+        BArgs ba;
+        ba.ctl = b->d_ev + (size_t)kColCtl * n_pad;
+        ba.ctk = b->d_ev + (size_t)kColCtk * n_pad;
+        ba.phi = b->d_ev + (size_t)kColPhi * n_pad;
+        for (int j = 0; j < 13; ++j) ba.out[j] = b->d_ev + (size_t)(kColH0 + j) * n_pad;
+        ba.n = pos;
+        int blocks = (int)std::min<int64_t>((pos + 255) / 256, (int64_t)b->sm_count * 8);
+        e = launch_basis(std::max(blocks, 1), 256, b->stream, ba);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            free_work(b);
+            return bcuda(b, e, "batch basis precompute");
+        }
+    }
+    b->has_basis = basis;
+    // per-toy arrays and work arrays sized for the largest step (every toy with a full stencil)
+    int64_t tiles_max = 0;
+    const int64_t min_tile_pairs = 64;  // smallest split-toy tile the schedule accepts
+    for (int t = 0; t < n_toys; ++t) {
+        int64_t np = (b->end[t] - b->begin[t] + 1) / 2;
+        tiles_max += np ? (np + min_tile_pairs - 1) / min_tile_pairs : 0;
+    }
+    int64_t max_items = (int64_t)std::max(n_toys, 1) * (2 * b->npar + 1);
+    int64_t max_units = std::max<int64_t>(tiles_max, 1) * (2 * b->npar + 1);
+    if (max_units > (1ll << 30)) return bfail(b, NLL_ERR_ARG, "too many work units");
+    b->max_items = (int)max_items;
+    b->max_units = (int)max_units;
+    e = cudaMalloc(&b->d_begin, sizeof(int64_t) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_end, sizeof(int64_t) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sum_wdm, sizeof(double) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_toy, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_u0, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_nt, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_kc, sizeof(KConst) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_dc, sizeof(DConst) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_item, sizeof(int) * max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_tile, sizeof(int) * max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_sums, sizeof(double) * kAccMax * max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_fits, sizeof(ToyFit) * std::max(n_toys, 1));
+    // every index the kernels can read is valid from the start
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_toy, 0, sizeof(int) * max_items, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_u0, 0, sizeof(int) * max_items, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_nt, 0, sizeof(int) * max_items, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_unit_item, 0, sizeof(int) * max_units, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_unit_tile, 0, sizeof(int) * max_units, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 4, b->stream);
+    if (e == cudaSuccess && n_toys) {
+        e = cudaMemcpyAsync(b->d_begin, b->begin.data(), sizeof(int64_t) * n_toys, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_end, b->end.data(), sizeof(int64_t) * n_toys, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_sum_wdm, b->sum_wdm.data(), sizeof(double) * n_toys, cudaMemcpyHostToDevice,
+                                b->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        free_work(b);
+        return bcuda(b, e, "batch work arrays");
+    }
+    b->loaded = true;
+    b->err.clear();
+    return NLL_OK;
+}
+
+int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, double* grad_out, int* status_out)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (!b->loaded) return bfail(b, NLL_ERR_STATE, "no toys loaded");
+    if (!thetas || !nll_out || !grad_out) return bfail(b, NLL_ERR_ARG, "null argument");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
+    if (b->n_toys == 0) return NLL_OK;
+    if (follow_user_stream(b) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "stream ordering failed");
+    return eval_all(b, thetas, nll_out, grad_out, status_out, nullptr);
+}
+
+int nll_batch_set_schedule(nll_batch* b, int tile_events, int blocks_per_sm)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
+        return bfail(b, NLL_ERR_ARG, "tile_events must be 0 or an even number >= 128");
+    if (blocks_per_sm < 0 || blocks_per_sm > 32) return bfail(b, NLL_ERR_ARG, "blocks_per_sm out of range");
+    b->tile_events = tile_events;
+    if (blocks_per_sm) b->bps = blocks_per_sm;
+    return NLL_OK;
+}
+
+int nll_batch_get_schedule(const nll_batch* b, int* tile_events, int* blocks_per_sm)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (tile_events) *tile_events = b->tile_events;
+    if (blocks_per_sm) *blocks_per_sm = b->bps;
+    return NLL_OK;
+}
+
+int nll_batch_num_toys(const nll_batch* b) { return b ? b->n_toys : -1; }
+
+const char* nll_batch_last_error(const nll_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+int nll_batch_autotune(nll_batch* b)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (!b->loaded || b->n_toys == 0) return bfail(b, NLL_ERR_STATE, "no toys loaded");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
+    // evaluate every toy at a valid interior point of the model: the mean of the ranges is
+    // not one, so use the first toy's sample-independent default (mid-window Gaussian)
+    const int np = b->npar;
+    std::vector<double> th((size_t)b->n_toys * np);
+    double base[18];
+    const double ma = b->ranges[0], mb = b->ranges[1];
+    if (b->kind == kMass1D) {
+        const double v[4] = {0.5 * (ma + mb), 0.05 * (mb - ma), 0.0, 0.5};
+        memcpy(base, v, sizeof v);
+    } else {
+        const double v[18] = {0.5 * (ma + mb), 0.05 * (mb - ma), 0.6, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0.5};
+        memcpy(base, v, sizeof v);
+    }
+    for (int t = 0; t < b->n_toys; ++t) memcpy(&th[(size_t)t * np], base, sizeof(double) * np);
+    std::vector<double> nll(b->n_toys), g((size_t)b->n_toys * np);
+    const int tiles[] = {0, 256, 512, 1024, 2048, 4096};
+    const int bpss[] = {1, 2, 4};
+    float best = 1e30f;
+    int bt = b->tile_events, bb = b->bps;
+    for (int tile : tiles)
+        for (int bps : bpss) {
+            b->tile_events = tile;
+            b->bps = bps;
+            float tot = 0.f;
+            for (int rep = 0; rep < 3; ++rep) {
+                float ms = 0.f;
+                eval_all(b, th.data(), nll.data(), g.data(), nullptr, &ms);
+                if (rep > 0) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                bt = tile;
+                bb = bps;
+            }
+        }
+    b->tile_events = bt;
+    b->bps = bb;
+    return NLL_OK;
+}
+
+int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
+                  const double* step, const int* fixed, const fit_options* opt_in, fit_result* results, int* steps_out)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (!b->loaded) return bfail(b, NLL_ERR_STATE, "no toys loaded");
+    if (!theta0 || !results) return bfail(b, NLL_ERR_ARG, "null argument");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
+    fit_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        memset(&opt, 0, sizeof opt);
+    if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
+    if (opt.max_iter <= 0) opt.max_iter = 500;
+    const int n = b->n_toys, np = b->npar;
+    if (n == 0) return NLL_OK;
+    BatchDev d = make_dev(b);
+    FitConfig& c = d.cfg;
+    c.strategy = opt.strategy >= 1;
+    c.hessian = opt.hessian >= 1;
+    c.max_iter = opt.max_iter;
+    c.tol_edm = opt.tol_edm;
+    int nf = 0;
+    std::vector<double> sint;
+    for (int k = 0; k < np; ++k) {
+        c.bounded[k] = 0;
+        c.lo[k] = c.hi[k] = 0.0;
+        if (lo && hi && lo[k] < hi[k] && isfinite(lo[k]) && isfinite(hi[k])) {
+            c.bounded[k] = 1;
+            c.lo[k] = lo[k];
+            c.hi[k] = hi[k];
+        }
+        if (fixed && fixed[k]) continue;
+        c.idx[nf++] = k;
+    }
+    c.nf = nf;
+    // initial states
+    std::vector<ToyFit> fits(n);
+    for (int t = 0; t < n; ++t) {
+        ToyFit& F = fits[t];
+        memset(&F, 0, sizeof F);
+        const double* th0 = shared_start ? theta0 : theta0 + (size_t)t * np;
+        for (int k = 0; k < np; ++k) F.th[k] = th0[k];
+        for (int i = 0; i < nf; ++i) {
+            const int k = c.idx[i];
+            double x = th0[k];
+            double J = 1.0;
+            if (c.bounded[k]) {
+                double u = 2.0 * (x - c.lo[k]) / (c.hi[k] - c.lo[k]) - 1.0;
+                u = std::min(std::max(u, -1.0 + 1e-10), 1.0 - 1e-10);
+                x = asin(u);
+                J = (c.hi[k] - c.lo[k]) * 0.5 * cos(x);
+            }
+            F.xt[i] = x;
+            double s0 = step && step[k] > 0.0 ? step[k] : std::max(1e-3 * fabs(th0[k]), 1e-3);
+            double si = s0 / std::max(fabs(J), 1e-8);
+            if (c.bounded[k]) si = std::min(si, 0.5);
+            F.sint[i] = si;
+        }
+        F.phase = kPhInit;
+        F.status = NLL_ERR_NOT_CONVERGED;
+        for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
+    }
+    *b->h_active = n;
+    cudaError_t e = follow_user_stream(b);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_fits, fits.data(), sizeof(ToyFit) * n, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "fit state upload");
+
+    // one device step = counter reset, prepare, evaluate, update; captured once
+    const int eval_blocks = b->sm_count * b->bps;
+    const int prep_blocks = (n + 127) / 128;
+    const int upd_blocks = (n + kUpdWarps - 1) / kUpdWarps;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 3, b->stream);
+        batch_prepare<<<prep_blocks, 128, 0, b->stream>>>(d);
+        launch_eval(b->kind, variant_of(b), b->weighted, eval_blocks, b->stream, d);
+        if (b->kind == kMass1D)
+            batch_update<kMass1D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
+        else
+            batch_update<kKstar4D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
+        e = cudaStreamEndCapture(b->stream, &graph);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return bcuda(b, e, "fit graph");
+    }
+    const int max_steps = opt.max_iter * 40 + 8;  // every line-search trial is one step
+    int steps = 0;
+    while (steps < max_steps) {
+        const int burst = steps < 8 ? 1 : 4;  // poll often at first, then every few steps
+        for (int r = 0; r < burst && e == cudaSuccess; ++r, ++steps) e = cudaGraphLaunch(exec, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) break;
+        if (*(volatile int*)b->h_active <= 0) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bcuda(b, e, "fit loop");
+    if (steps_out) *steps_out = steps;
+    e = cudaMemcpyAsync(fits.data(), b->d_fits, sizeof(ToyFit) * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "fit state download");
+    int all = NLL_OK;
+    for (int t = 0; t < n; ++t) {
+        const ToyFit& F = fits[t];
+        fit_result& r = results[t];
+        memset(&r, 0, sizeof r);
+        for (int k = 0; k < np; ++k) r.theta[k] = F.th[k];
+        for (int i = 0; i < nf; ++i) {
+            r.err[c.idx[i]] = F.err[i];
+            for (int j = 0; j < nf; ++j) r.cov[c.idx[i] * np + c.idx[j]] = F.cov[i * nf + j];
+        }
+        r.nll = F.f;
+        r.edm = F.edm;
+        r.n_eval = F.n_eval;
+        r.n_iter = F.iter;
+        r.status = F.phase == kPhDone ? F.status : NLL_ERR_NOT_CONVERGED;
+        if (r.status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
+    }
+    return all;
+}
+
+}  // extern "C"

@@ -75,6 +75,25 @@ __device__ __forceinline__ void logprod_mul(LogProd& lp, double x)
     lp.m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(q));
 }
 
+// Product of two running products (exact exponent bookkeeping, one rounding).
+__device__ __forceinline__ LogProd logprod_combine(const LogProd& a, const LogProd& b)
+{
+    LogProd r{a.m, a.e + b.e};
+    logprod_mul(r, b.m);
+    return r;
+}
+
+// Product over the warp (butterfly, every lane ends with the same value).
+__device__ __forceinline__ LogProd logprod_warp(LogProd lp)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        LogProd other{__shfl_xor_sync(0xffffffffu, lp.m, o), __shfl_xor_sync(0xffffffffu, lp.e, o)};
+        lp = logprod_combine(lp, other);
+    }
+    return lp;
+}
+
 __device__ __forceinline__ double logprod_value(const LogProd& lp)
 {
     const double kLn2hi = 0x1.62e42ff000000p-1, kLn2lo = -0x1.718432a1b0e26p-35;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace gbnll {
 
 constexpr int kMass1D = 1;
@@ -84,6 +86,18 @@ struct BArgs {  // basis precompute
     double* out[13];  // h0, hFL, h_S3..h_S9, T2l, T2k, xp, T2p
     int64_t n;
 };
+
+// Host-side parameter-only terms of one parameter point (runtime.cu): the kernel constant
+// block and the derivative constants of the gradient assembly.
+struct Hoist {
+    KConst k;
+    double mu, sigma, alpha, f, ma;
+    double b0, b2;
+    double dlnN1_dmu, dlnN1_dsig, dlnN2t_dal;
+    double dlnNc_dc2[3];
+};
+int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hoist& H, std::string* err);
+void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, double* nll_out, double* grad_out);
 
 // Launchers (kernels.cu).  They return the launch's cudaError_t.
 cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,

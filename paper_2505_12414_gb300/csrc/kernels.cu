@@ -42,272 +42,11 @@
 
 #include "fp64_math.cuh"
 #include "gbnll_internal.h"
+#include "nll_device.cuh"
 
 namespace gbnll {
 
 __device__ double g_exp2tab[kExpTable];  // 2^(j/N), correctly rounded, uploaded once per device
-
-// ----------------------------------------------------------------------------------
-// Angular basis (paper Sec. 2.4.2, Eq. 3 regrouped by parameter):
-//   A = h0 + FL hFL + S3 h3 + S4 h4 + S5 h5 + AFB h6 + S7 h7 + S8 h8 + S9 h9,
-//   h0 = c sin^2 tK (3/4 + cos 2tl / 4), hFL = c cos^2 tK (1 - cos 2tl) - h0, ...
-// with c = 9/(32 pi).  Also the Chebyshev inputs T2(ctl), T2(ctk), phi/pi, T2(phi/pi).
-// ----------------------------------------------------------------------------------
-__device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi, double h[9], double& t2l,
-                                              double& t2k, double& xp, double& t2p)
-{
-    const double c = 0x1.6eb167b830193p-4;  // 9/(32 pi)
-    const double kInvPi = 0x1.45f306dc9c883p-2;
-    double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);
-    double sl = sqrt(sl2), sk = sqrt(sk2);
-    double sp, cp;
-    sincos(phi, &sp, &cp);
-    t2l = fma(2.0 * ctl, ctl, -1.0);
-    t2k = fma(2.0 * ctk, ctk, -1.0);
-    double c2p = fma(2.0 * cp, cp, -1.0);  // cos 2phi
-    double s2p = 2.0 * sp * cp;            // sin 2phi
-    double h0 = c * sk2 * fma(0.25, t2l, 0.75);
-    double a = c * sk2 * sl2;              // c sin^2 tK sin^2 tl
-    double b = 2.0 * c * sk * ctk * sl;    // c sin 2tK sin tl
-    h[0] = h0;
-    h[1] = c * (ctk * ctk) * (1.0 - t2l) - h0;
-    h[2] = a * c2p;                // S3
-    h[3] = 2.0 * b * ctl * cp;     // S4: c sin 2tK sin 2tl cos phi
-    h[4] = b * cp;                 // S5
-    h[5] = (4.0 / 3.0) * c * sk2 * ctl;  // AFB
-    h[6] = b * sp;                 // S7
-    h[7] = 2.0 * b * ctl * sp;     // S8
-    h[8] = a * s2p;                // S9
-    xp = phi * kInvPi;
-    t2p = fma(2.0 * xp, xp, -1.0);
-}
-
-// ----------------------------------------------------------------------------------
-// Per-event bodies.  acc[] slots as documented in gbnll_internal.h.  `valid` == false
-// turns the event into an exact no-op (factor 1 in the product, R = 0 in every sum), so
-// both events of a pair run in one basic block and their dependency chains interleave.
-// ----------------------------------------------------------------------------------
-template <bool W, bool GRAD>
-__device__ __forceinline__ void event_mass(const KConst& c, double m, double w, bool valid, double* acc,
-                                           LogProd& lp, int& bad, const double* tab)
-{
-    double d = m - c.mu;
-    double E = fexp_scaled(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
-    double P = E + c.b2;
-    bad |= valid ? not_positive_normal(P) : 0;
-    P = valid ? P : 1.0;
-    if (W)
-        acc[0] = fma(valid ? w : 0.0, log(P), acc[0]);
-    else
-        logprod_mul(lp, P);
-    if (GRAD) {
-        double R = frcp(P);
-        if (W) R *= w;
-        R = valid ? R : 0.0;
-        double rs = R * E;
-        acc[1] += rs;
-        double rsd = rs * d;
-        acc[2] += rsd;
-        acc[3] = fma(rsd, d, acc[3]);
-        acc[4] += R;
-        acc[5] = fma(R, d, acc[5]);
-    }
-}
-
-template <bool W, bool GRAD>
-__device__ __forceinline__ void event_4d(const KConst& c, double m, const double h[9], double xl, double t2l,
-                                         double xk, double t2k, double xp, double t2p, double w, bool valid,
-                                         double* acc, LogProd& lp, int& bad, const double* tab)
-{
-    double d = m - c.mu;
-    double E = fexp_scaled(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
-    double A = fma(c.ang[0], h[1], h[0]);
-#pragma unroll
-    for (int k = 1; k < 8; ++k) A = fma(c.ang[k], h[k + 1], A);
-    double C1 = fma(c.cq[1], xl, fma(c.cq[2], t2l, c.cq[0]));
-    double C2 = fma(c.cq[4], xk, fma(c.cq[5], t2k, c.cq[3]));
-    double C3 = fma(c.cq[7], xp, fma(c.cq[8], t2p, c.cq[6]));
-    double C12 = C1 * C2;
-    double C = C12 * C3;
-    double P = fma(A, E, C);
-    bad |= valid ? not_positive_normal(P) : 0;
-    P = valid ? P : 1.0;
-    if (W)
-        acc[0] = fma(valid ? w : 0.0, log(P), acc[0]);
-    else
-        logprod_mul(lp, P);
-    if (GRAD) {
-        double R = frcp(P);
-        if (W) R *= w;
-        R = valid ? R : 0.0;
-        double rE = R * E;
-        double rs = rE * A;
-        acc[1] += rs;
-        double rsd = rs * d;
-        acc[2] += rsd;
-        acc[3] = fma(rsd, d, acc[3]);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc[4 + k] = fma(rE, h[k + 1], acc[4 + k]);
-        // R C/C_j for the three background factors, and R C
-        double u3 = R * C12;
-        double rc3 = R * C3;
-        double u1 = rc3 * C2;
-        double u2 = rc3 * C1;
-        double re = u3 * C3;
-        acc[12] += re;
-        acc[13] = fma(re, d, acc[13]);
-        acc[14] = fma(u1, xl, acc[14]);
-        acc[15] = fma(u1, t2l, acc[15]);
-        acc[16] = fma(u2, xk, acc[16]);
-        acc[17] = fma(u2, t2k, acc[17]);
-        acc[18] = fma(u3, xp, acc[18]);
-        acc[19] = fma(u3, t2p, acc[19]);
-    }
-}
-
-// ----------------------------------------------------------------------------------
-// Fixed-order reductions
-// ----------------------------------------------------------------------------------
-
-// Warp reduction of K slots by recursive halving: at level s each lane keeps half of its
-// slots, sends the other half to lane ^ s and adds what it receives, so the warp spends
-// 16 + 8 + 4 + 2 + 1 = 31 FP64 additions instead of 5 K.  On return lane l holds the
-// warp total of slot l (l < K).  The pairing is fixed, so the result is deterministic.
-template <int K>
-__device__ __forceinline__ double warp_reduce_slots(const double (&in)[K])
-{
-    static_assert(K <= 32, "at most 32 slots");
-    const int lane = threadIdx.x & 31;
-    double v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = k < K ? in[k] : 0.0;
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool upper = (lane & s) != 0;
-#pragma unroll
-        for (int i = 0; i < s; ++i) {
-            double send = upper ? v[i] : v[i + s];
-            double keep = upper ? v[i + s] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-        }
-    }
-    return v[0];
-}
-
-// Reduce K per-thread values over the block; the result is valid in threads 0..K-1.
-template <int K>
-__device__ __forceinline__ double block_reduce(const double (&v)[K], double* smem)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    double s = warp_reduce_slots<K>(v);
-    if (lane < K) smem[warp * K + lane] = s;
-    __syncthreads();
-    double res = 0.0;
-    if (threadIdx.x < K) {
-        for (int w = 0; w < nwarps; ++w) res += smem[w * K + threadIdx.x];
-    }
-    __syncthreads();
-    return res;
-}
-
-// Block partials -> scratch; the last block to arrive sums them in block order into
-// out[0..K).  Resets the ticket for the next launch.
-template <int K>
-__device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, double* partials,
-                                            unsigned int* ticket, double* out)
-{
-    __shared__ int s_last;
-    const int nb = gridDim.x;
-    double bsum = block_reduce<K>(v, smem);
-    if (threadIdx.x < K) partials[threadIdx.x * nb + blockIdx.x] = bsum;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // each thread sums a fixed strided subset of blocks for every slot, then a fixed tree
-    double acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) acc[k] += __ldcg(partials + k * nb + b);
-    }
-    double tot = block_reduce<K>(acc, smem);
-    if (threadIdx.x < K) out[threadIdx.x] = tot;
-    if (threadIdx.x == 0) *ticket = 0u;
-}
-
-// ----------------------------------------------------------------------------------
-// The fused kernel
-// ----------------------------------------------------------------------------------
-__device__ __forceinline__ double2 ld2(const double* col, int64_t p)
-{
-    return __ldg(reinterpret_cast<const double2*>(col) + p);
-}
-
-// Inputs of one pair of consecutive events (one 128-bit load per column).
-struct PairIn {
-    double2 m, w, l, k, f;
-    double2 h[9];
-    double2 t2l, t2k, xp, t2p;
-};
-
-template <int KIND, int VAR, bool W>
-__device__ __forceinline__ void load_pair(const KArgs& a, int64_t p, PairIn& in)
-{
-    in.m = ld2(a.col[kColM], p);
-    if (W) in.w = ld2(a.w, p);
-    if (KIND == kKstar4D) {
-        in.l = ld2(a.col[kColCtl], p);
-        in.k = ld2(a.col[kColCtk], p);
-        if (VAR == kVarPrecompute) {
-#pragma unroll
-            for (int j = 0; j < 9; ++j) in.h[j] = ld2(a.col[kColH0 + j], p);
-            in.t2l = ld2(a.col[kColT2l], p);
-            in.t2k = ld2(a.col[kColT2k], p);
-            in.xp = ld2(a.col[kColXp], p);
-            in.t2p = ld2(a.col[kColT2p], p);
-        } else {
-            in.f = ld2(a.col[kColPhi], p);
-        }
-    }
-}
-
-template <int KIND, int VAR, bool W, bool GRAD>
-__device__ __forceinline__ void process_pair(const KConst& c, const PairIn& in, bool second, double* acc,
-                                             LogProd& lpx, LogProd& lpy, int& bad, const double* tab)
-{
-    const double wx = W ? in.w.x : 1.0, wy = W ? in.w.y : 1.0;
-    if (KIND == kMass1D) {
-        event_mass<W, GRAD>(c, in.m.x, wx, true, acc, lpx, bad, tab);
-        event_mass<W, GRAD>(c, in.m.y, wy, second, acc, lpy, bad, tab);
-    } else {
-        double hx[9], hy[9];
-        double t2lx, t2ly, t2kx, t2ky, xpx, xpy, t2px, t2py;
-        if (VAR == kVarPrecompute) {
-#pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                hx[j] = in.h[j].x;
-                hy[j] = in.h[j].y;
-            }
-            t2lx = in.t2l.x;
-            t2ly = in.t2l.y;
-            t2kx = in.t2k.x;
-            t2ky = in.t2k.y;
-            xpx = in.xp.x;
-            xpy = in.xp.y;
-            t2px = in.t2p.x;
-            t2py = in.t2p.y;
-        } else {
-            angular_basis(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px);
-            angular_basis(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py);
-        }
-        event_4d<W, GRAD>(c, in.m.x, hx, in.l.x, t2lx, in.k.x, t2kx, xpx, t2px, wx, true, acc, lpx, bad, tab);
-        event_4d<W, GRAD>(c, in.m.y, hy, in.l.y, t2ly, in.k.y, t2ky, xpy, t2py, wy, second, acc, lpy, bad, tab);
-    }
-}
 
 // Work split: block b owns the contiguous pair range [b P / B, (b+1) P / B) (P pairs, B
 // blocks), which its threads walk with a block-sized stride (coalesced).  Every block,
@@ -343,7 +82,11 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
         p += blockDim.x;
         if (p < end) load_pair<KIND, VAR, W>(a, p, in);
     }
-    if (!W) acc[0] = logprod_value(lpx) + logprod_value(lpy);
+    if (!W) {
+        // one logarithm per warp: multiply the running products across the warp first
+        double lw = logprod_value(logprod_warp(logprod_combine(lpx, lpy)));
+        acc[0] = (threadIdx.x & 31) == 0 ? lw : 0.0;
+    }
     acc[K - 1] = (double)bad;
     grid_reduce<K>(acc, s_red, a.partials, a.ticket, a.out);
 }

@@ -33,15 +33,6 @@ const char* kNames4D[18] = {"mu",     "sigma",  "FL",     "S3",     "S4",     "S
                             "AFB",    "S7",     "S8",     "S9",     "alpha",  "c1_ctl",
                             "c2_ctl", "c1_ctk", "c2_ctk", "c1_phi", "c2_phi", "fsig"};
 
-// Host-side derivative constants for the gradient assembly.
-struct Hoist {
-    KConst k;
-    double mu, sigma, alpha, f, ma;
-    double b0, b2;
-    double dlnN1_dmu, dlnN1_dsig, dlnN2t_dal;
-    double dlnNc_dc2[3];
-};
-
 std::mutex g_table_mutex;
 bool g_table_ready[64];
 
@@ -117,6 +108,19 @@ int fail(nll_model* m, int status, const char* fmt, ...)
     return status;
 }
 
+int fail_text(std::string* err, int status, const char* fmt, ...)
+{
+    if (err) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        *err = buf;
+    }
+    return status;
+}
+
 int cuda_fail(nll_model* m, cudaError_t e, const char* what)
 {
     return fail(m, e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA, "%s: %s", what,
@@ -141,22 +145,26 @@ double gauss_norm(double za, double zb)
 // b1 = fsig / (sqrt(2 pi) sigma N1), b2 = (1 - fsig) / (Ntilde2 prod_j Nc_j),
 // Ntilde2 = exp(-alpha ma) N2 = expm1(alpha (mb - ma)) / alpha  (mb - ma at alpha = 0),
 // Cbar_j = 1 + c1_j x_j + c2_j (2 x_j^2 - 1), Nc_j = (2 - 2/3 c2_j) (times pi for phi).
-int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
+}  // namespace
+
+namespace gbnll {
+int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hoist& H, std::string* err)
 {
     memset(&H, 0, sizeof H);
-    for (int k = 0; k < m->npar; ++k)
-        if (!isfinite(th[k])) return fail(m, NLL_ERR_ARG, "parameter %d (%s) is not finite", k,
-                                           m->kind == kMass1D ? kNames1D[k] : kNames4D[k]);
-    const double ma = m->ranges[0], mb = m->ranges[1], D = mb - ma;
+    const int npar = kind == kMass1D ? 4 : 18;
+    for (int k = 0; k < npar; ++k)
+        if (!isfinite(th[k])) return fail_text(err, NLL_ERR_ARG, "parameter %d (%s) is not finite", k,
+                                           kind == kMass1D ? kNames1D[k] : kNames4D[k]);
+    const double ma = ranges[0], mb = ranges[1], D = mb - ma;
     double mu = th[0], sigma = th[1];
-    double alpha = m->kind == kMass1D ? th[2] : th[10];
-    double f = m->kind == kMass1D ? th[3] : th[17];
-    if (!(sigma > 0.0)) return fail(m, NLL_ERR_ARG, "sigma must be > 0 (got %g)", sigma);
+    double alpha = kind == kMass1D ? th[2] : th[10];
+    double f = kind == kMass1D ? th[3] : th[17];
+    if (!(sigma > 0.0)) return fail_text(err, NLL_ERR_ARG, "sigma must be > 0 (got %g)", sigma);
     if (grad ? !(f > 0.0 && f < 1.0) : !(f >= 0.0 && f <= 1.0))
-        return fail(m, NLL_ERR_ARG, "fsig must be in %s (got %g)", grad ? "(0, 1)" : "[0, 1]", f);
+        return fail_text(err, NLL_ERR_ARG, "fsig must be in %s (got %g)", grad ? "(0, 1)" : "[0, 1]", f);
     double za = (mu - ma) / (sqrt(2.0) * sigma), zb = (mu - mb) / (sqrt(2.0) * sigma);
     double N1 = gauss_norm(za, zb);
-    if (!(N1 > 1e-300)) return fail(m, NLL_ERR_ARG, "Gaussian normalisation underflows (mu=%g sigma=%g)", mu, sigma);
+    if (!(N1 > 1e-300)) return fail_text(err, NLL_ERR_ARG, "Gaussian normalisation underflows (mu=%g sigma=%g)", mu, sigma);
     double ea = exp(-za * za), eb = exp(-zb * zb);
     H.dlnN1_dmu = (ea - eb) / (sqrt(2.0 * kPi) * sigma * N1);
     H.dlnN1_dsig = -(za * ea - zb * eb) / (sqrt(kPi) * sigma * N1);
@@ -176,18 +184,18 @@ int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
     double b0 = 1.0 / (2.0 * sigma * sigma);
     double lnb1 = (f > 0.0) ? log(f) - 0.5 * log(2.0 * kPi) - log(sigma) - log(N1) : -INFINITY;
     double b2 = (1.0 - f) / Nt2;
-    if (m->kind == kKstar4D) {
+    if (kind == kKstar4D) {
         for (int j = 0; j < 3; ++j) {
             double c2 = th[12 + 2 * j];
             double nc = 2.0 - (2.0 / 3.0) * c2;
-            if (!(nc > 0.0)) return fail(m, NLL_ERR_ARG, "Chebyshev normalisation %d is not positive", j);
+            if (!(nc > 0.0)) return fail_text(err, NLL_ERR_ARG, "Chebyshev normalisation %d is not positive", j);
             H.dlnNc_dc2[j] = (-2.0 / 3.0) / nc;
             b2 /= nc * (j == 2 ? kPi : 1.0);
         }
     }
     // exponent range of the per-event exponential: -b0 d^2 - alpha (m - ma) + ln b1 <= |alpha| D + ln b1
     if (fabs(alpha) * D + std::max(lnb1, 0.0) > 700.0)
-        return fail(m, NLL_ERR_ARG, "parameter point outside the exponent range (|alpha|(mb-ma)=%g, ln b1=%g)",
+        return fail_text(err, NLL_ERR_ARG, "parameter point outside the exponent range (|alpha|(mb-ma)=%g, ln b1=%g)",
                     fabs(alpha) * D, lnb1);
     H.mu = mu;
     H.sigma = sigma;
@@ -203,7 +211,7 @@ int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
     k.neg_alpha = -alpha * S;
     k.k0 = (lnb1 - alpha * (mu - ma)) * S;
     k.b2 = b2;
-    if (m->kind == kKstar4D) {
+    if (kind == kKstar4D) {
         for (int j = 0; j < 8; ++j) k.ang[j] = th[2 + j];
         k.cq[0] = b2;
         k.cq[1] = b2 * th[11];
@@ -216,6 +224,15 @@ int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
         k.cq[8] = th[16];
     }
     return NLL_OK;
+}
+
+}  // namespace gbnll
+
+namespace {
+
+int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
+{
+    return hoist_core(m->kind, m->ranges, th, grad, H, &m->err);
 }
 
 int launch_blocks(const nll_model* m, int bps, int threads)
@@ -254,6 +271,46 @@ int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int
     return NLL_OK;
 }
 
+}  // namespace
+
+namespace gbnll {
+// NLL and gradient from the kernel sums S (slots of gbnll_internal.h) and the constants.
+void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, double* nll_out, double* grad_out)
+{
+    const bool grad = grad_out != nullptr;
+    const int npar = kind == kMass1D ? 4 : 18;
+    // ln L = alpha sum w (m - ma) + sum w ln Ptilde
+    double lnL = H.alpha * sum_wdm + S[0];
+    *nll_out = -lnL;
+    if (!grad) return;
+    const double two_b0 = 2.0 * H.b0, dma = H.mu - H.ma;
+    double dL[18] = {0};
+    // mass shape: d ln s / d mu = 2 b0 d - dlnN1/dmu ; d ln s / d sigma = 2 b0 d^2 / sigma - 1/sigma - dlnN1/dsigma
+    dL[0] = two_b0 * S[2] - H.dlnN1_dmu * S[1];
+    dL[1] = two_b0 / H.sigma * S[3] - (1.0 / H.sigma + H.dlnN1_dsig) * S[1];
+    if (kind == kMass1D) {
+        double sre = H.b2 * S[4], sred = H.b2 * S[5];
+        dL[2] = sred + dma * sre - H.dlnN2t_dal * sre;
+        dL[3] = S[1] / H.f - sre / (1.0 - H.f);
+    } else {
+        for (int k = 0; k < 8; ++k) dL[2 + k] = S[4 + k];
+        double sre = S[12], sred = S[13];
+        dL[10] = sred + dma * sre - H.dlnN2t_dal * sre;
+        dL[11] = H.b2 * S[14];
+        dL[12] = H.b2 * S[15] - H.dlnNc_dc2[0] * sre;
+        dL[13] = S[16];
+        dL[14] = S[17] - H.dlnNc_dc2[1] * sre;
+        dL[15] = S[18];
+        dL[16] = S[19] - H.dlnNc_dc2[2] * sre;
+        dL[17] = S[1] / H.f - sre / (1.0 - H.f);
+    }
+    for (int k = 0; k < npar; ++k) grad_out[k] = -dL[k];
+}
+
+}  // namespace gbnll
+
+namespace {
+
 int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out)
 {
     if (!m) return NLL_ERR_ARG;
@@ -289,32 +346,7 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
             for (int k = 0; k < m->npar; ++k) grad_out[k] = NAN;
         return fail(m, NLL_ERR_NONPOSITIVE_PDF, "density not positive for %.0f thread(s) of events", bad);
     }
-    // ln L = alpha sum w (m - ma) + sum w ln Ptilde
-    double lnL = H.alpha * m->sum_wdm + S[0];
-    *nll_out = -lnL;
-    if (!grad) return NLL_OK;
-    const double two_b0 = 2.0 * H.b0, dma = H.mu - H.ma;
-    std::vector<double> dL(m->npar, 0.0);
-    // mass shape: d ln s / d mu = 2 b0 d - dlnN1/dmu ; d ln s / d sigma = 2 b0 d^2 / sigma - 1/sigma - dlnN1/dsigma
-    dL[0] = two_b0 * S[2] - H.dlnN1_dmu * S[1];
-    dL[1] = two_b0 / H.sigma * S[3] - (1.0 / H.sigma + H.dlnN1_dsig) * S[1];
-    if (m->kind == kMass1D) {
-        double sre = H.b2 * S[4], sred = H.b2 * S[5];
-        dL[2] = sred + dma * sre - H.dlnN2t_dal * sre;
-        dL[3] = S[1] / H.f - sre / (1.0 - H.f);
-    } else {
-        for (int k = 0; k < 8; ++k) dL[2 + k] = S[4 + k];
-        double sre = S[12], sred = S[13];
-        dL[10] = sred + dma * sre - H.dlnN2t_dal * sre;
-        dL[11] = H.b2 * S[14];
-        dL[12] = H.b2 * S[15] - H.dlnNc_dc2[0] * sre;
-        dL[13] = S[16];
-        dL[14] = S[17] - H.dlnNc_dc2[1] * sre;
-        dL[15] = S[18];
-        dL[16] = S[19] - H.dlnNc_dc2[2] * sre;
-        dL[17] = S[1] / H.f - sre / (1.0 - H.f);
-    }
-    for (int k = 0; k < m->npar; ++k) grad_out[k] = -dL[k];
+    assemble_core(m->kind, H, m->sum_wdm, S, nll_out, grad ? grad_out : nullptr);
     return NLL_OK;
 }
 

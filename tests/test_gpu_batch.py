@@ -1,0 +1,144 @@
+"""Batched pseudo-experiments on the GPU: per-toy parity with the oracle, device-resident fits
+against one-at-a-time fits, schedules, and pulls (paper Sec. 2.5, Sec. 3.1)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import fit as ofit
+from paper_2505_12414_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+M1, M4 = oracle.MASS1D, oracle.KSTAR4D
+RAGGED = [0, 1, 2, 3, 5, 64, 65, 127, 1001, 2000, 2001, 4096, 0, 7]
+
+
+def ragged_toys(kind, sizes, stream0, weighted=False):
+    cols = None
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    parts = []
+    for t, n in enumerate(sizes):
+        parts.append(synth.mass1d(n, stream=stream0 + t) if kind == M1 else synth.kstar4d(n, stream=stream0 + t))
+    ndim = 1 if kind == M1 else 4
+    cols = [np.concatenate([p[d] for p in parts]) if len(parts) else np.zeros(0) for d in range(ndim)]
+    w = synth.weights(int(off[-1]), stream=stream0 + 999) if weighted else None
+    return off, cols, w
+
+
+def ranges_of(kind):
+    return synth.RANGES_1D if kind == M1 else synth.RANGES_4D
+
+
+def truth_of(kind):
+    return synth.TRUTH_1D if kind == M1 else synth.TRUTH_4D
+
+
+def scale_of(kind):
+    if kind == M1:
+        return np.array([2.0, 1.0, 2e-4, 0.02])
+    return np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+
+
+@pytest.mark.parametrize("kind,precompute,weighted",
+                         [(M1, True, False), (M1, True, True), (M4, True, False), (M4, False, True)])
+@pytest.mark.parametrize("tile", [0, 128, 512])
+def test_batch_eval_parity(gpu_lib, kind, precompute, weighted, tile):
+    off, cols, w = ragged_toys(kind, RAGGED, 7000, weighted)
+    b = gpu_lib.Batch(kind, ranges_of(kind))
+    b.load(off, cols, w, precompute=precompute)
+    b.set_schedule(tile, 2)
+    thetas = np.array([synth.perturb(truth_of(kind), scale_of(kind), k=t) for t in range(len(RAGGED))])
+    nll, g, st = b.eval_grad(thetas)
+    assert np.all(st == 0)
+    for t in range(len(RAGGED)):
+        sl = slice(off[t], off[t + 1])
+        ct = [c[sl] for c in cols]
+        wt = w[sl] if w is not None else None
+        if off[t + 1] == off[t]:
+            assert nll[t] == 0.0 and np.all(g[t] == 0.0)
+            continue
+        rn, rg, rs, rst = oracle.nll_grad(kind, ranges_of(kind), ct, thetas[t], w=wt)
+        assert rst == 0
+        lp = np.log(oracle.pdf(kind, ranges_of(kind), thetas[t], ct))
+        nscale = np.sum(np.abs(lp if wt is None else wt * lp))
+        assert abs(nll[t] - rn) <= 1e-12 * nscale, (t, nll[t], rn)
+        assert np.all(np.abs(g[t] - rg) <= 1e-9 * np.abs(rg) + 1e-13 * rs), (t, g[t], rg)
+    b.close()
+
+
+def _bounds(kind):
+    n = 4 if kind == M1 else 18
+    lo, hi = np.zeros(n), np.zeros(n)
+    lo[-1], hi[-1] = 0.0, 1.0
+    return lo, hi
+
+
+@pytest.mark.parametrize("kind,nev,ntoy", [(M1, 3000, 8), (M4, 3000, 4)])
+def test_batch_fits_match_single_fits(gpu_lib, kind, nev, ntoy):
+    off, cols, _ = ragged_toys(kind, [nev] * ntoy, 8000)
+    lo, hi = _bounds(kind)
+    step = scale_of(kind)
+    start = truth_of(kind) + 0.5 * step
+    b = gpu_lib.Batch(kind, ranges_of(kind)).load(off, cols)
+    r = b.fit(start, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=1, hessian=1)
+    assert np.all(r["status"] == 0), r["status"]
+    for t in range(ntoy):
+        sl = slice(off[t], off[t + 1])
+        m = gpu_lib.Model(kind, ranges_of(kind))
+        m.load([c[sl] for c in cols])
+        s = m.fit(start, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=1, hessian=1)
+        m.close()
+        assert s["status"] == 0
+        pull = (r["theta"][t] - s["theta"]) / s["err"]
+        assert np.max(np.abs(pull)) < 1e-6, (t, pull)
+        np.testing.assert_allclose(r["err"][t], s["err"], rtol=1e-3)
+    b.close()
+
+
+def test_batch_schedules_agree(gpu_lib):
+    off, cols, _ = ragged_toys(M4, [1500, 2500, 900, 3100], 8100)
+    lo, hi = _bounds(M4)
+    step = scale_of(M4)
+    res = []
+    for tile in (0, 256):
+        b = gpu_lib.Batch(M4, synth.RANGES_4D).load(off, cols)
+        b.set_schedule(tile, 2)
+        res.append(b.fit(synth.TRUTH_4D, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=1, hessian=1))
+        b.close()
+    assert np.all(res[0]["status"] == 0) and np.all(res[1]["status"] == 0)
+    pull = (res[0]["theta"] - res[1]["theta"]) / res[0]["err"]
+    assert np.max(np.abs(pull)) < 1e-6
+
+
+def test_batch_autotune_and_oracle_newton_fit(gpu_lib):
+    off, cols, _ = ragged_toys(M1, [5000, 20000, 1000], 8200)
+    b = gpu_lib.Batch(M1, synth.RANGES_1D).load(off, cols)
+    b.autotune()
+    sch = b.get_schedule()
+    assert sch["tile_events"] in (0, 256, 512, 1024, 2048, 4096)
+    lo, hi = _bounds(M1)
+    r = b.fit(synth.TRUTH_1D, lo=lo, hi=hi, step=scale_of(M1), tol_edm=1e-14, strategy=1, hessian=1)
+    for t in range(3):
+        sl = slice(off[t], off[t + 1])
+        ref = ofit.fit(M1, synth.RANGES_1D, [cols[0][sl]], synth.TRUTH_1D, tol_edm=1e-18, h0=scale_of(M1) * 1e-2)
+        pull = (r["theta"][t] - ref["theta"]) / ref["err"]
+        assert np.max(np.abs(pull)) < 1e-6, pull
+    b.close()
+
+
+@pytest.mark.slow
+def test_batch_pulls_mass_model(gpu_lib):
+    ntoy, nev = 1000, 1000
+    off, cols = synth.toys1d(ntoy, nev, fixed_size=True)
+    lo, hi = _bounds(M1)
+    b = gpu_lib.Batch(M1, synth.RANGES_1D).load(off, cols)
+    r = b.fit(synth.TRUTH_1D, lo=lo, hi=hi, step=scale_of(M1), tol_edm=1e-10, strategy=1, hessian=1)
+    assert np.all(r["status"] == 0)
+    pulls = (r["theta"] - synth.TRUTH_1D) / r["err"]
+    mean, width = pulls.mean(axis=0), pulls.std(axis=0)
+    assert np.all(np.abs(mean) < 4.0 / math.sqrt(ntoy) + 0.02), mean
+    assert np.all(np.abs(width - 1.0) < 4.0 / math.sqrt(2 * ntoy) + 0.02), width
+    b.close()
