@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the launch shape given below")
     ap.add_argument("--bps", type=int, default=2, help="blocks per SM without autotuning")
     ap.add_argument("--threads", type=int, default=128, help="threads per block without autotuning")
+    ap.add_argument("--toys", type=int, default=1000, help="batched 4D toys (0 skips the toy-fit measurement)")
+    ap.add_argument("--seq-toys", type=int, default=20, help="toys fitted one at a time for comparison")
+    ap.add_argument("--requests", type=int, default=30, help="served fits (0 skips the serving measurement)")
+    ap.add_argument("--rate", type=float, default=50.0, help="Poisson arrival rate of served fits per second")
     return ap.parse_args()
 
 
@@ -159,6 +163,98 @@ def cpu_baseline(cols, seconds=10.0, sample=100_000):
     return {"value": evals * sample / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
             "sample": "%d NLL+grad evals of the first %d events of the 4D 1M-event sample, %d threads" %
                       (evals, sample, cores)}
+
+
+def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
+    """Batched device-resident fits of n_toys 4D toys (Poisson(2000) events, generated from
+    truth) against the plain one-fit-at-a-time GPU path; fits/s by wall clock of the
+    synchronous calls (generation excluded, the same fitted results at tolerance 1e-8)."""
+    off, cols = synth.toys4d(n_toys, 2000.0, seed=synth.BASE_SEED + seed_stream)
+    lo, hi = np.zeros(18), np.zeros(18)
+    hi[17] = 1.0
+    step = np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    opts = dict(lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=1, hessian=1)
+    b = g.Batch(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device).load(off, cols)
+    b.autotune()
+    sched = b.get_schedule()
+    b.fit(synth.TRUTH_4D, **opts)  # warm-up (graph instantiation, caches)
+    t0 = time.perf_counter()
+    r = b.fit(synth.TRUTH_4D, **opts)
+    dt = time.perf_counter() - t0
+    b.close()
+    m = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device)
+    seq_t = 0.0
+    agree = []
+    for t in range(min(n_seq, n_toys) + 1):
+        sl = slice(off[t], off[t + 1])
+        t1 = time.perf_counter()
+        m.load([c[sl] for c in cols])
+        s = m.fit(synth.TRUTH_4D, **opts)
+        if t > 0:  # the first fit is a warm-up
+            seq_t += time.perf_counter() - t1
+            if s["status"] == 0 and r["status"][t] == 0:
+                agree.append(float(np.max(np.abs(r["theta"][t] - s["theta"]) / s["err"])))
+    m.close()
+    n_seq_done = min(n_seq, n_toys)
+    return {"n_toys": n_toys, "mean_events": 2000, "batched_fits_per_s": n_toys / dt, "batched_wall_s": dt,
+            "device_steps": r["steps"], "converged": int(np.sum(r["status"] == 0)),
+            "mean_evals_per_fit": float(np.mean(r["n_eval"])), "schedule": sched,
+            "sequential_fits_per_s": n_seq_done / seq_t if seq_t > 0 else None, "sequential_sample": n_seq_done,
+            "max_abs_diff_over_sigma_vs_sequential": max(agree) if agree else None,
+            "speedup_vs_sequential": (n_toys / dt) / (n_seq_done / seq_t) if seq_t > 0 else None}
+
+
+def serving(g, device, n_req, rate, seed_stream=0):
+    """Poisson-arrival stream of full fits mixing the mass and 4D models, event counts
+    log-uniform in [1e3, 1e6]: continuous batching (nll_server_*) against the plain
+    one-fit-at-a-time GPU path on the same requests and arrival times."""
+    from paper_2505_12414_gb300.serve import Request, latency_summary, serve, serve_sequential
+
+    rs = synth.Stream(synth.BASE_SEED + 4242 + seed_stream, 0)
+    sizes = np.exp(np.log(1e3) + (np.log(1e6) - np.log(1e3)) * rs.uniform(n_req)).astype(int)
+    gaps = -np.log(rs.uniform(n_req)) / rate
+    arrivals = np.cumsum(gaps) - gaps[0]
+    kinds = [g.NLL_MODEL_MASS1D if u < 0.5 else g.NLL_MODEL_KSTARMUMU4D for u in rs.uniform(n_req)]
+    step = {g.NLL_MODEL_MASS1D: np.array([2.0, 1.0, 2e-4, 0.02]),
+            g.NLL_MODEL_KSTARMUMU4D: np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])}
+    truth = {g.NLL_MODEL_MASS1D: synth.TRUTH_1D, g.NLL_MODEL_KSTARMUMU4D: synth.TRUTH_4D}
+    ranges = {g.NLL_MODEL_MASS1D: synth.RANGES_1D, g.NLL_MODEL_KSTARMUMU4D: synth.RANGES_4D}
+    opts = {}
+    for k in step:
+        lo, hi = np.zeros(len(step[k])), np.zeros(len(step[k]))
+        hi[-1] = 1.0
+        opts[k] = dict(lo=lo, hi=hi, step=step[k], tol_edm=1e-8, strategy=1, hessian=1)
+    cols = []
+    for i in range(n_req):
+        gen = synth.mass1d if kinds[i] == g.NLL_MODEL_MASS1D else synth.kstar4d
+        cols.append(gen(int(sizes[i]), stream=700000 + 1000 * seed_stream + i))
+
+    def requests():
+        return [Request(i, kinds[i], cols[i], truth[kinds[i]] + 0.3 * step[kinds[i]], float(arrivals[i]))
+                for i in range(n_req)]
+
+    servers = {g.NLL_MODEL_MASS1D: g.Server(g.NLL_MODEL_MASS1D, synth.RANGES_1D, 16, 4_000_000, 4096,
+                                            device=device, **opts[g.NLL_MODEL_MASS1D]),
+               g.NLL_MODEL_KSTARMUMU4D: g.Server(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, 16, 8_000_000, 4096,
+                                                 device=device, **opts[g.NLL_MODEL_KSTARMUMU4D])}
+    serve(servers, requests()[:2], realtime=False)  # warm-up
+    served = serve(servers, requests(), realtime=True)
+    for srv in servers.values():
+        srv.close()
+    models = {k: g.Model(k, ranges[k], device=device) for k in step}
+    serve_sequential(models, requests()[:2], opts)  # warm-up
+    seq = serve_sequential(models, requests(), opts)
+    for m in models.values():
+        m.close()
+    diffs = [float(np.max(np.abs(a.result["theta"] - b.result["theta"]) / b.result["err"]))
+             for a, b in zip(served, seq) if a.result["status"] == 0 and b.result["status"] == 0]
+    out = {"requests": n_req, "rate_per_s": rate, "events_log_uniform": [1000, 1000000],
+           "served": latency_summary(served), "sequential": latency_summary(seq),
+           "converged": int(sum(r.result["status"] == 0 for r in served)),
+           "max_abs_diff_over_sigma_vs_sequential": max(diffs) if diffs else None}
+    if out["served"]["fits_per_s"] and out["sequential"]["fits_per_s"]:
+        out["speedup_fits_per_s"] = out["served"]["fits_per_s"] / out["sequential"]["fits_per_s"]
+    return out
 
 
 def run_reference(args):
@@ -287,6 +383,13 @@ def run_ours(args):
                 "calibration": {"dfma_per_s": rates["dfma"], "cuda_exp_slots": rates["dfma"] / rates["cuda_exp"],
                                 "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}
 
+    toys = None
+    if args.toys > 0:
+        toys = toy_fits(g, local, args.toys, args.seq_toys, seed_stream=rank)
+    served = None
+    if args.requests > 0:
+        served = serving(g, local, args.requests, args.rate, seed_stream=rank)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -302,7 +405,8 @@ def run_ours(args):
                 "e2e": {"value": world * N_EVENTS / (e2e_step * 1e-3), "unit": "events/s",
                         "h2d_bytes_per_step": 4 * 8 * N_EVENTS, "d2h_bytes_per_step": 8 * (k_acc + 3),
                         "ms_per_step": e2e_step},
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
+                "toy_fits": toys, "serving": served}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:

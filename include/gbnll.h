@@ -277,6 +277,57 @@ int nll_batch_num_toys(const nll_batch* b);
 const char* nll_batch_last_error(const nll_batch* b);
 void nll_batch_destroy(nll_batch* b);
 
+/* ------------------------------------------------------------------------------------
+ * Serving: continuous batching of independent fits of one model kind.  A server owns
+ * `max_slots` fit slots and an event pool of `pool_events` events on the device (the HBM
+ * budget).  A submitted fit is admitted into a free slot if the pool has a free range for
+ * its events; every nll_server_step advances all busy slots by one device step of the
+ * batched machinery above (one CUDA graph replay); finished fits are collected with
+ * nll_server_poll, which frees their slot and pool range for the next admissions.  A fit's
+ * result does not depend on which other fits share the steps (each fit's sums are reduced
+ * in its own fixed order).
+ * ------------------------------------------------------------------------------------ */
+typedef struct nll_server nll_server; /* opaque; owned by the library */
+
+/*
+ * nll_server_create -- kind, obs_ranges and device as nll_create_model.
+ *   max_slots    concurrent fits (>= 1).     pool_events  device event capacity (>= 1).
+ *   tile_events  split-toy tile size (even, >= 128; 0 = 4096).
+ *   lo, hi, step, fixed, opt   minimiser settings shared by every fit (as fit_minimise).
+ * The server runs on its own CUDA stream.
+ */
+int nll_server_create(int kind, const double* obs_ranges, int device, int max_slots, int64_t pool_events,
+                      int tile_events, const double* lo, const double* hi, const double* step, const int* fixed,
+                      const fit_options* opt, nll_server** out);
+
+/*
+ * nll_server_submit -- admit one fit: n_events events (host SoA columns; weights must be NULL,
+ * a server serves unweighted fits) and its start point theta0 (host, npar doubles).  On
+ * success *request_id identifies the fit and its events are on the device.
+ * Returns NLL_ERR_STATE (nothing admitted) when no slot or no pool range is free: the
+ * caller keeps the request queued and retries after nll_server_poll returned finished fits.
+ * Returns NLL_ERR_ARG for events outside the ranges or more events than the whole pool.
+ */
+int nll_server_submit(nll_server* s, const double* const* columns, const double* weights, int64_t n_events,
+                      const double* theta0, int64_t* request_id);
+
+/* Queue n_steps device steps (graph replays) advancing every busy slot; returns without
+ * waiting, so steps of servers on different streams overlap on the device.  nll_server_sync
+ * waits for them (nll_server_poll and nll_server_submit also wait first). */
+int nll_server_step(nll_server* s, int n_steps);
+int nll_server_sync(nll_server* s);
+
+/*
+ * nll_server_poll -- collect up to max_results finished fits: ids_out[i] and results[i]
+ * (host arrays); *n_out receives the count.  Their slots and pool ranges are released.
+ */
+int nll_server_poll(nll_server* s, int64_t* ids_out, fit_result* results, int max_results, int* n_out);
+
+/* Busy slots, free slots and free pool events (any output may be NULL). */
+int nll_server_status(const nll_server* s, int* busy, int* free_slots, int64_t* free_events);
+const char* nll_server_last_error(const nll_server* s);
+void nll_server_destroy(nll_server* s);
+
 /*
  * nll_eval_grad_4d_noalloc -- NLL and gradient of the 4D model for a sample that stays in
  * the caller's device memory, without allocating any device memory.  The paper has no

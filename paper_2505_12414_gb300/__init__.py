@@ -107,6 +107,20 @@ def load(path=None):
     L.nll_batch_last_error.restype = ctypes.c_char_p
     L.nll_batch_destroy.argtypes = [vp]
     L.nll_batch_destroy.restype = None
+    L.nll_server_create.argtypes = [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                    _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(fit_options),
+                                    ctypes.POINTER(vp)]
+    L.nll_server_submit.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.c_int64, _DP, ctypes.POINTER(ctypes.c_int64)]
+    L.nll_server_step.argtypes = [vp, ctypes.c_int]
+    L.nll_server_sync.argtypes = [vp]
+    L.nll_server_poll.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(fit_result), ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int)]
+    L.nll_server_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int64)]
+    L.nll_server_last_error.argtypes = [vp]
+    L.nll_server_last_error.restype = ctypes.c_char_p
+    L.nll_server_destroy.argtypes = [vp]
+    L.nll_server_destroy.restype = None
     L.nll_eval_grad_4d_noalloc.argtypes = [_DP, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64,
                                            _DP, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _DP, _DP]
     _lib = L
@@ -507,6 +521,77 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             load().nll_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------------------
+# serving
+# ------------------------------------------------------------------------------------
+def _scheck(handle, st):
+    if st != NLL_OK:
+        raise NLLError(st, load().nll_server_last_error(handle).decode())
+
+
+class Server:
+    """Continuous batching of fits of one model kind (see nll_server_* in include/gbnll.h)."""
+
+    def __init__(self, kind, obs_ranges, max_slots, pool_events, tile_events=4096, lo=None, hi=None, step=None,
+                 fixed=None, tol_edm=1e-8, max_iter=500, strategy=1, hessian=1, device=0):
+        L = load()
+        self.kind = kind
+        self.npar = 4 if kind == NLL_MODEL_MASS1D else 18
+        self.ndim = 1 if kind == NLL_MODEL_MASS1D else 4
+        th, lo, hi, step, fx = _fit_args(np.zeros(self.npar), lo, hi, step, fixed)
+        opt = fit_options(tol_edm, max_iter, strategy, hessian)
+        h = ctypes.c_void_p()
+        st = L.nll_server_create(int(kind), _p(_f64(obs_ranges)), int(device), int(max_slots), int(pool_events),
+                                 int(tile_events), _p(lo), _p(hi), _p(step),
+                                 fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt), ctypes.byref(h))
+        if st != NLL_OK:
+            raise NLLError(st, "nll_server_create failed")
+        self.handle = h.value
+        self.max_slots = max_slots
+        self._res = (fit_result * max_slots)()
+        self._ids = (ctypes.c_int64 * max_slots)()
+
+    def submit(self, columns, theta0):
+        """Admit a fit; returns its id, or None when no slot or pool range is free."""
+        cols = [_f64(c) for c in columns]
+        ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+        th = _f64(theta0)
+        rid = ctypes.c_int64()
+        st = load().nll_server_submit(self.handle, ptrs, None, len(cols[0]), _p(th), ctypes.byref(rid))
+        if st == NLL_ERR_STATE:
+            return None
+        _scheck(self.handle, st)
+        return rid.value
+
+    def step(self, n=1):
+        _scheck(self.handle, load().nll_server_step(self.handle, int(n)))
+
+    def sync(self):
+        _scheck(self.handle, load().nll_server_sync(self.handle))
+
+    def poll(self):
+        """Finished fits as a list of (id, result dict)."""
+        n = ctypes.c_int()
+        _scheck(self.handle, load().nll_server_poll(self.handle, self._ids, self._res, self.max_slots, ctypes.byref(n)))
+        return [(self._ids[i], _result_dict(self._res[i], self.npar)) for i in range(n.value)]
+
+    def status(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _scheck(self.handle, load().nll_server_status(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return dict(busy=a.value, free_slots=b.value, free_events=c.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().nll_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

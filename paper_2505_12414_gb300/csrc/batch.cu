@@ -84,6 +84,7 @@ struct BatchDev {
     ToyFit* fits;
     int* counters;                 // [0] items, [1] units, [2] next unit
     int* n_active;                 // toys not yet done (mapped host memory)
+    int* done_flags;               // per toy, set to 1 when it finishes (mapped), or NULL
     int* item_toy;
     int* item_u0;
     int* item_nt;
@@ -665,6 +666,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
         F.status = done_status;
         F.phase = kPhDone;
         atomicSub(b.n_active, 1);
+        if (b.done_flags) b.done_flags[t] = 1;
     }
 }
 
@@ -907,6 +909,73 @@ int eval_all(nll_batch* b, const double* thetas, double* nll_out, double* grad_o
         if (status_out) status_out[t] = st[t];
     }
     return first_bad;
+}
+
+
+// minimiser settings shared by all toys
+void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
+                  const fit_options& opt)
+{
+    c.strategy = opt.strategy >= 1;
+    c.hessian = opt.hessian >= 1;
+    c.max_iter = opt.max_iter;
+    c.tol_edm = opt.tol_edm;
+    int nf = 0;
+    for (int k = 0; k < np; ++k) {
+        c.bounded[k] = 0;
+        c.lo[k] = c.hi[k] = 0.0;
+        if (lo && hi && lo[k] < hi[k] && isfinite(lo[k]) && isfinite(hi[k])) {
+            c.bounded[k] = 1;
+            c.lo[k] = lo[k];
+            c.hi[k] = hi[k];
+        }
+        if (fixed && fixed[k]) continue;
+        c.idx[nf++] = k;
+    }
+    c.nf = nf;
+}
+
+// initial minimiser state of one toy at th0 (internal coordinates and steps)
+void init_fit(ToyFit& F, const FitConfig& c, const double* th0, const double* step)
+{
+    memset(&F, 0, sizeof F);
+    for (int k = 0; k < c.npar; ++k) F.th[k] = th0[k];
+    for (int i = 0; i < c.nf; ++i) {
+        const int k = c.idx[i];
+        double x = th0[k];
+        double J = 1.0;
+        if (c.bounded[k]) {
+            double u = 2.0 * (x - c.lo[k]) / (c.hi[k] - c.lo[k]) - 1.0;
+            u = std::min(std::max(u, -1.0 + 1e-10), 1.0 - 1e-10);
+            x = asin(u);
+            J = (c.hi[k] - c.lo[k]) * 0.5 * cos(x);
+        }
+        F.xt[i] = x;
+        double s0 = step && step[k] > 0.0 ? step[k] : std::max(1e-3 * fabs(th0[k]), 1e-3);
+        double si = s0 / std::max(fabs(J), 1e-8);
+        if (c.bounded[k]) si = std::min(si, 0.5);
+        F.sint[i] = si;
+    }
+    F.phase = kPhInit;
+    F.status = NLL_ERR_NOT_CONVERGED;
+    for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
+}
+
+// fit_result of one finished toy
+void fill_result(const ToyFit& F, const FitConfig& c, fit_result& r)
+{
+    const int np = c.npar, nf = c.nf;
+    memset(&r, 0, sizeof r);
+    for (int k = 0; k < np; ++k) r.theta[k] = F.th[k];
+    for (int i = 0; i < nf; ++i) {
+        r.err[c.idx[i]] = F.err[i];
+        for (int j = 0; j < nf; ++j) r.cov[c.idx[i] * np + c.idx[j]] = F.cov[i * nf + j];
+    }
+    r.nll = F.f;
+    r.edm = F.edm;
+    r.n_eval = F.n_eval;
+    r.n_iter = F.iter;
+    r.status = F.phase == kPhDone ? F.status : NLL_ERR_NOT_CONVERGED;
 }
 
 }  // namespace
@@ -1203,51 +1272,10 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     if (n == 0) return NLL_OK;
     BatchDev d = make_dev(b);
     FitConfig& c = d.cfg;
-    c.strategy = opt.strategy >= 1;
-    c.hessian = opt.hessian >= 1;
-    c.max_iter = opt.max_iter;
-    c.tol_edm = opt.tol_edm;
-    int nf = 0;
-    std::vector<double> sint;
-    for (int k = 0; k < np; ++k) {
-        c.bounded[k] = 0;
-        c.lo[k] = c.hi[k] = 0.0;
-        if (lo && hi && lo[k] < hi[k] && isfinite(lo[k]) && isfinite(hi[k])) {
-            c.bounded[k] = 1;
-            c.lo[k] = lo[k];
-            c.hi[k] = hi[k];
-        }
-        if (fixed && fixed[k]) continue;
-        c.idx[nf++] = k;
-    }
-    c.nf = nf;
-    // initial states
+    setup_config(c, np, lo, hi, step, fixed, opt);
+    const int nf = c.nf;
     std::vector<ToyFit> fits(n);
-    for (int t = 0; t < n; ++t) {
-        ToyFit& F = fits[t];
-        memset(&F, 0, sizeof F);
-        const double* th0 = shared_start ? theta0 : theta0 + (size_t)t * np;
-        for (int k = 0; k < np; ++k) F.th[k] = th0[k];
-        for (int i = 0; i < nf; ++i) {
-            const int k = c.idx[i];
-            double x = th0[k];
-            double J = 1.0;
-            if (c.bounded[k]) {
-                double u = 2.0 * (x - c.lo[k]) / (c.hi[k] - c.lo[k]) - 1.0;
-                u = std::min(std::max(u, -1.0 + 1e-10), 1.0 - 1e-10);
-                x = asin(u);
-                J = (c.hi[k] - c.lo[k]) * 0.5 * cos(x);
-            }
-            F.xt[i] = x;
-            double s0 = step && step[k] > 0.0 ? step[k] : std::max(1e-3 * fabs(th0[k]), 1e-3);
-            double si = s0 / std::max(fabs(J), 1e-8);
-            if (c.bounded[k]) si = std::min(si, 0.5);
-            F.sint[i] = si;
-        }
-        F.phase = kPhInit;
-        F.status = NLL_ERR_NOT_CONVERGED;
-        for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
-    }
+    for (int t = 0; t < n; ++t) init_fit(fits[t], c, shared_start ? theta0 : theta0 + (size_t)t * np, step);
     *b->h_active = n;
     cudaError_t e = follow_user_stream(b);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_fits, fits.data(), sizeof(ToyFit) * n, cudaMemcpyHostToDevice, b->stream);
@@ -1294,22 +1322,411 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     if (e != cudaSuccess) return bcuda(b, e, "fit state download");
     int all = NLL_OK;
     for (int t = 0; t < n; ++t) {
-        const ToyFit& F = fits[t];
-        fit_result& r = results[t];
-        memset(&r, 0, sizeof r);
-        for (int k = 0; k < np; ++k) r.theta[k] = F.th[k];
-        for (int i = 0; i < nf; ++i) {
-            r.err[c.idx[i]] = F.err[i];
-            for (int j = 0; j < nf; ++j) r.cov[c.idx[i] * np + c.idx[j]] = F.cov[i * nf + j];
-        }
-        r.nll = F.f;
-        r.edm = F.edm;
-        r.n_eval = F.n_eval;
-        r.n_iter = F.iter;
-        r.status = F.phase == kPhDone ? F.status : NLL_ERR_NOT_CONVERGED;
-        if (r.status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
+        fill_result(fits[t], c, results[t]);
+        if (results[t].status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
     }
     return all;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// serving: continuous batching of fits into fixed slots over a device event pool
+// ------------------------------------------------------------------------------------
+struct nll_server {
+    int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
+    cudaStream_t stream = nullptr;
+    double ranges[8] = {0};
+    int max_slots = 0;
+    int64_t pool_events = 0, n_pad = 0;
+    int ncols = 0, tile_events = 4096;
+    double* d_ev = nullptr;
+    std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end) in pool events, sorted
+    std::vector<char> busy;
+    std::vector<int64_t> slot_id, slot_begin, slot_len;
+    int64_t next_id = 1;
+    FitConfig cfg;
+    std::vector<double> step;
+    // device work arrays
+    int64_t* d_begin = nullptr;
+    int64_t* d_end = nullptr;
+    double* d_sum_wdm = nullptr;
+    ToyFit* d_fits = nullptr;
+    int* d_counters = nullptr;
+    int* h_active = nullptr;
+    int* d_active = nullptr;
+    int* h_done = nullptr;
+    int* d_done = nullptr;
+    int* d_item_toy = nullptr;
+    int* d_item_u0 = nullptr;
+    int* d_item_nt = nullptr;
+    KConst* d_item_kc = nullptr;
+    DConst* d_item_dc = nullptr;
+    int* d_unit_item = nullptr;
+    int* d_unit_tile = nullptr;
+    double* d_unit_sums = nullptr;
+    int max_items = 0, max_units = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int sfail(nll_server* s, int status, const char* fmt, ...)
+{
+    if (s) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        s->err = buf;
+    }
+    return status;
+}
+
+void server_free(nll_server* s)
+{
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    void* ptrs[] = {s->d_ev, s->d_begin, s->d_end, s->d_sum_wdm, s->d_fits, s->d_counters, s->d_item_toy,
+                    s->d_item_u0, s->d_item_nt, s->d_item_kc, s->d_item_dc, s->d_unit_item, s->d_unit_tile,
+                    s->d_unit_sums};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (s->h_active) cudaFreeHost(s->h_active);
+    if (s->h_done) cudaFreeHost(s->h_done);
+    if (s->stream) cudaStreamDestroy(s->stream);
+}
+
+// first-fit allocation of `len` (even) pool events starting on an even event
+bool pool_alloc(nll_server* s, int64_t len, int64_t* begin)
+{
+    for (size_t i = 0; i < s->free_ranges.size(); ++i) {
+        auto& r = s->free_ranges[i];
+        if (r.second - r.first >= len) {
+            *begin = r.first;
+            r.first += len;
+            if (r.first == r.second) s->free_ranges.erase(s->free_ranges.begin() + i);
+            return true;
+        }
+    }
+    return false;
+}
+
+void pool_release(nll_server* s, int64_t begin, int64_t len)
+{
+    auto& fr = s->free_ranges;
+    auto it = std::lower_bound(fr.begin(), fr.end(), std::make_pair(begin, begin + len));
+    it = fr.insert(it, {begin, begin + len});
+    // merge with neighbours
+    size_t i = it - fr.begin();
+    if (i + 1 < fr.size() && fr[i].second == fr[i + 1].first) {
+        fr[i].second = fr[i + 1].second;
+        fr.erase(fr.begin() + i + 1);
+    }
+    if (i > 0 && fr[i - 1].second == fr[i].first) {
+        fr[i - 1].second = fr[i].second;
+        fr.erase(fr.begin() + i);
+    }
+}
+
+BatchDev server_dev(nll_server* s)
+{
+    BatchDev d;
+    memset(&d, 0, sizeof d);
+    d.n_toys = s->max_slots;
+    d.tile_pairs = s->tile_events / 2;
+    d.ev_begin = s->d_begin;
+    d.ev_end = s->d_end;
+    d.sum_wdm = s->d_sum_wdm;
+    for (int c = 0; c < kNumCols; ++c) d.cols.col[c] = c < s->ncols ? s->d_ev + (size_t)c * s->n_pad : nullptr;
+    d.cols.w = nullptr;
+    d.fits = s->d_fits;
+    d.counters = s->d_counters;
+    d.n_active = s->d_active;
+    d.done_flags = s->d_done;
+    d.item_toy = s->d_item_toy;
+    d.item_u0 = s->d_item_u0;
+    d.item_nt = s->d_item_nt;
+    d.item_kc = s->d_item_kc;
+    d.item_dc = s->d_item_dc;
+    d.unit_item = s->d_unit_item;
+    d.unit_tile = s->d_unit_tile;
+    d.unit_sums = s->d_unit_sums;
+    d.max_items = s->max_items;
+    d.max_units = s->max_units;
+    d.cfg = s->cfg;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nll_server_create(int kind, const double* obs_ranges, int device, int max_slots, int64_t pool_events,
+                      int tile_events, const double* lo, const double* hi, const double* step, const int* fixed,
+                      const fit_options* opt_in, nll_server** out)
+{
+    if (!out) return NLL_ERR_ARG;
+    *out = nullptr;
+    if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges || max_slots < 1 ||
+        pool_events < 1 || tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
+        return NLL_ERR_ARG;
+    if (!(isfinite(obs_ranges[0]) && isfinite(obs_ranges[1]) && obs_ranges[0] < obs_ranges[1])) return NLL_ERR_ARG;
+    if (kind == NLL_MODEL_KSTARMUMU4D) {
+        const double want[6] = {-1.0, 1.0, -1.0, 1.0, -kPiH, kPiH};
+        for (int i = 0; i < 6; ++i)
+            if (fabs(obs_ranges[2 + i] - want[i]) > 1e-12) return NLL_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
+    nll_server* s = new nll_server();
+    s->kind = kind;
+    s->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
+    s->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
+    s->device = device;
+    s->max_slots = max_slots;
+    s->tile_events = tile_events ? tile_events : 4096;
+    memcpy(s->ranges, obs_ranges, sizeof(double) * 2 * s->ndim);
+    if (kind == NLL_MODEL_KSTARMUMU4D) {
+        s->ranges[6] = -kPiH;
+        s->ranges[7] = kPiH;
+    }
+    cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, device);
+    fit_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        memset(&opt, 0, sizeof opt);
+    if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
+    if (opt.max_iter <= 0) opt.max_iter = 500;
+    memset(&s->cfg, 0, sizeof s->cfg);
+    s->cfg.kind = kind;
+    s->cfg.npar = s->npar;
+    for (int i = 0; i < 8; ++i) s->cfg.ranges[i] = s->ranges[i];
+    setup_config(s->cfg, s->npar, lo, hi, step, fixed, opt);
+    s->step.assign(s->npar, 0.0);
+    for (int k = 0; k < s->npar; ++k) s->step[k] = step ? step[k] : 0.0;
+    // pool: padded so a range of even length starting on an even event can end anywhere
+    s->pool_events = (pool_events + 1) & ~int64_t(1);
+    s->n_pad = std::max<int64_t>((s->pool_events + 63) / 64 * 64, 64);
+    s->ncols = kind == kMass1D ? 1 : kNumCols;
+    s->free_ranges.push_back({0, s->pool_events});
+    s->busy.assign(max_slots, 0);
+    s->slot_id.assign(max_slots, 0);
+    s->slot_begin.assign(max_slots, 0);
+    s->slot_len.assign(max_slots, 0);
+    const int64_t tp = s->tile_events / 2;
+    s->max_items = max_slots * (2 * s->npar + 1);
+    int64_t mu = (s->pool_events / 2 / tp + max_slots + 1) * (2 * (int64_t)s->npar + 1);
+    if (mu > (1ll << 30)) {
+        delete s;
+        return NLL_ERR_ARG;
+    }
+    s->max_units = (int)mu;
+    cudaError_t e = ensure_btab(device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_ev, sizeof(double) * s->n_pad * s->ncols);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ev, 0, sizeof(double) * s->n_pad * s->ncols, s->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_begin, sizeof(int64_t) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_end, sizeof(int64_t) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sum_wdm, sizeof(double) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_fits, sizeof(ToyFit) * max_slots);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, sizeof(int) * 4);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_active, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_active, s->h_active, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_done, sizeof(int) * max_slots, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_done, s->h_done, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_toy, sizeof(int) * s->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_u0, sizeof(int) * s->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_nt, sizeof(int) * s->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_kc, sizeof(KConst) * s->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_dc, sizeof(DConst) * s->max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_item, sizeof(int) * s->max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_tile, sizeof(int) * s->max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_sums, sizeof(double) * kAccMax * s->max_units);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_toy, 0, sizeof(int) * s->max_items, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_u0, 0, sizeof(int) * s->max_items, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_nt, 0, sizeof(int) * s->max_items, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_unit_item, 0, sizeof(int) * s->max_units, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_unit_tile, 0, sizeof(int) * s->max_units, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_begin, 0, sizeof(int64_t) * max_slots, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_end, 0, sizeof(int64_t) * max_slots, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_sum_wdm, 0, sizeof(double) * max_slots, s->stream);
+    if (e == cudaSuccess) {
+        // every slot starts finished (empty); the prepare kernel skips finished slots
+        std::vector<ToyFit> idle(max_slots);
+        for (auto& F : idle) {
+            memset(&F, 0, sizeof F);
+            F.phase = kPhDone;
+            for (int q = 0; q < kMaxSlots; ++q) F.item[q] = -1;
+        }
+        e = cudaMemcpyAsync(s->d_fits, idle.data(), sizeof(ToyFit) * max_slots, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+    if (e == cudaSuccess) {
+        memset(s->h_done, 0, sizeof(int) * max_slots);
+        *s->h_active = 0;
+        BatchDev d = server_dev(s);
+        const int eval_blocks = s->sm_count * 2;
+        e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(s->d_counters, 0, sizeof(int) * 3, s->stream);
+            batch_prepare<<<(max_slots + 127) / 128, 128, 0, s->stream>>>(d);
+            launch_eval(kind, kVarPrecompute, false, eval_blocks, s->stream, d);
+            if (kind == kMass1D)
+                batch_update<kMass1D><<<(max_slots + kUpdWarps - 1) / kUpdWarps, kUpdWarps * 32, 0, s->stream>>>(d);
+            else
+                batch_update<kKstar4D><<<(max_slots + kUpdWarps - 1) / kUpdWarps, kUpdWarps * 32, 0, s->stream>>>(d);
+            e = cudaStreamEndCapture(s->stream, &s->graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->exec, s->graph, 0);
+    }
+    if (e != cudaSuccess) {
+        server_free(s);
+        delete s;
+        return e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA;
+    }
+    *out = s;
+    return NLL_OK;
+}
+
+void nll_server_destroy(nll_server* s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    server_free(s);
+    delete s;
+}
+
+const char* nll_server_last_error(const nll_server* s) { return s ? s->err.c_str() : "null server"; }
+
+int nll_server_status(const nll_server* s, int* busy, int* free_slots, int64_t* free_events)
+{
+    if (!s) return NLL_ERR_ARG;
+    int nb = 0;
+    for (char c : s->busy) nb += c ? 1 : 0;
+    int64_t fe = 0;
+    for (auto& r : s->free_ranges) fe += r.second - r.first;
+    if (busy) *busy = nb;
+    if (free_slots) *free_slots = s->max_slots - nb;
+    if (free_events) *free_events = fe;
+    return NLL_OK;
+}
+
+int nll_server_sync(nll_server* s)
+{
+    if (!s) return NLL_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    return e == cudaSuccess ? NLL_OK : sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
+}
+
+int nll_server_step(nll_server* s, int n_steps)
+{
+    if (!s || n_steps < 0) return NLL_ERR_ARG;
+    if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
+    for (int i = 0; i < n_steps; ++i) {
+        cudaError_t e = cudaGraphLaunch(s->exec, s->stream);
+        if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server step: %s", cudaGetErrorString(e));
+    }
+    return NLL_OK;
+}
+
+int nll_server_submit(nll_server* s, const double* const* columns, const double* weights, int64_t n_events,
+                      const double* theta0, int64_t* request_id)
+{
+    if (!s || !theta0 || !request_id || n_events < 0) return NLL_ERR_ARG;
+    if (weights) return sfail(s, NLL_ERR_ARG, "a server serves unweighted fits");
+    if (n_events > 0 && !columns) return sfail(s, NLL_ERR_ARG, "null columns");
+    for (int d = 0; d < s->ndim && n_events > 0; ++d)
+        if (!columns[d]) return sfail(s, NLL_ERR_ARG, "column %d is NULL", d);
+    for (int k = 0; k < s->npar; ++k)
+        if (!isfinite(theta0[k])) return sfail(s, NLL_ERR_ARG, "start point not finite");
+    const int64_t len = std::max<int64_t>((n_events + 1) & ~int64_t(1), 2);
+    if (len > s->pool_events) return sfail(s, NLL_ERR_ARG, "more events than the whole pool");
+    // validate events and sum (m - ma) on the host
+    double sum = 0.0;
+    for (int64_t i = 0; i < n_events; ++i) {
+        for (int d = 0; d < s->ndim; ++d) {
+            double x = columns[d][i];
+            if (!(x >= s->ranges[2 * d] && x <= s->ranges[2 * d + 1]))
+                return sfail(s, NLL_ERR_ARG, "event %lld outside the observable ranges", (long long)i);
+        }
+        sum += columns[0][i] - s->ranges[0];
+    }
+    if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
+    cudaError_t e = cudaStreamSynchronize(s->stream);  // no step may run while a slot is rewritten
+    if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
+    int slot = -1;
+    for (int i = 0; i < s->max_slots; ++i)
+        if (!s->busy[i]) {
+            slot = i;
+            break;
+        }
+    int64_t begin = 0;
+    if (slot < 0 || !pool_alloc(s, len, &begin)) return sfail(s, NLL_ERR_STATE, "no free slot or pool range");
+    // events into the pool range (and the angular basis for the 4D model)
+    for (int d = 0; d < s->ndim && e == cudaSuccess && n_events > 0; ++d)
+        e = cudaMemcpyAsync(s->d_ev + (size_t)d * s->n_pad + begin, columns[d], sizeof(double) * n_events,
+                            cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess && s->kind == kKstar4D && n_events > 0) {
+        BArgs ba;
+        ba.ctl = s->d_ev + (size_t)kColCtl * s->n_pad + begin;
+        ba.ctk = s->d_ev + (size_t)kColCtk * s->n_pad + begin;
+        ba.phi = s->d_ev + (size_t)kColPhi * s->n_pad + begin;
+        for (int j = 0; j < 13; ++j) ba.out[j] = s->d_ev + (size_t)(kColH0 + j) * s->n_pad + begin;
+        ba.n = n_events;
+        int blocks = (int)std::min<int64_t>((n_events + 255) / 256, (int64_t)s->sm_count * 8);
+        e = launch_basis(std::max(blocks, 1), 256, s->stream, ba);
+    }
+    ToyFit F;
+    init_fit(F, s->cfg, theta0, s->step.data());
+    const int64_t end = begin + n_events;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_fits + slot, &F, sizeof F, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_begin + slot, &begin, sizeof begin, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_end + slot, &end, sizeof end, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_sum_wdm + slot, &sum, sizeof sum, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        pool_release(s, begin, len);
+        return sfail(s, NLL_ERR_CUDA, "admission: %s", cudaGetErrorString(e));
+    }
+    s->h_done[slot] = 0;
+    __atomic_add_fetch(s->h_active, 1, __ATOMIC_SEQ_CST);
+    s->busy[slot] = 1;
+    s->slot_id[slot] = s->next_id;
+    s->slot_begin[slot] = begin;
+    s->slot_len[slot] = len;
+    *request_id = s->next_id++;
+    return NLL_OK;
+}
+
+int nll_server_poll(nll_server* s, int64_t* ids_out, fit_result* results, int max_results, int* n_out)
+{
+    if (!s || !n_out || max_results < 0 || (max_results > 0 && (!ids_out || !results))) return NLL_ERR_ARG;
+    *n_out = 0;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
+    int n = 0;
+    for (int i = 0; i < s->max_slots && n < max_results; ++i) {
+        if (!s->busy[i] || !((volatile int*)s->h_done)[i]) continue;
+        ToyFit F;
+        e = cudaMemcpyAsync(&F, s->d_fits + i, sizeof F, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "result copy: %s", cudaGetErrorString(e));
+        fill_result(F, s->cfg, results[n]);
+        ids_out[n] = s->slot_id[i];
+        ++n;
+        s->busy[i] = 0;
+        s->h_done[i] = 0;
+        pool_release(s, s->slot_begin[i], s->slot_len[i]);
+    }
+    *n_out = n;
+    return NLL_OK;
 }
 
 }  // extern "C"

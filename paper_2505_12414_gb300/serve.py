@@ -1,0 +1,87 @@
+"""Request loop for serving fits with continuous batching.
+
+Requests (model kind, events, start point, arrival time) are admitted into the servers of
+their model kind as slots and pool memory free up; every loop iteration queues a few device
+steps on each busy server (servers run on their own CUDA streams, so their steps overlap on
+the device), then collects finished fits.  The loop only schedules: all fitting runs in the
+library (nll_server_*).
+"""
+import collections
+import time
+
+import numpy as np
+
+
+class Request:
+    __slots__ = ("rid", "kind", "columns", "theta0", "arrival", "admitted", "done", "result")
+
+    def __init__(self, rid, kind, columns, theta0, arrival):
+        self.rid = rid
+        self.kind = kind
+        self.columns = columns
+        self.theta0 = theta0
+        self.arrival = arrival
+        self.admitted = None
+        self.done = None
+        self.result = None
+
+
+def serve(servers, requests, steps_per_iter=2, realtime=True):
+    """Run `requests` (sorted by arrival, seconds from start) through `servers` {kind: Server}.
+
+    With realtime=True requests become visible at their arrival times on the wall clock;
+    otherwise all are queued at once.  Returns the requests with admitted/done times and
+    results filled in."""
+    pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
+    queues = {k: collections.deque() for k in servers}
+    inflight = {k: {} for k in servers}
+    left = len(requests)
+    t0 = time.perf_counter()
+    while left:
+        now = time.perf_counter() - t0
+        while pending and (not realtime or pending[0].arrival <= now):
+            r = pending.popleft()
+            queues[r.kind].append(r)
+        for k, srv in servers.items():
+            q = queues[k]
+            while q:
+                rid = srv.submit(q[0].columns, q[0].theta0)
+                if rid is None:
+                    break
+                r = q.popleft()
+                r.admitted = time.perf_counter() - t0
+                inflight[k][rid] = r
+        busy = [k for k in servers if inflight[k]]
+        for k in busy:
+            servers[k].step(steps_per_iter)
+        for k in busy:
+            for rid, res in servers[k].poll():
+                r = inflight[k].pop(rid)
+                r.done = time.perf_counter() - t0
+                r.result = res
+                left -= 1
+        if not busy and pending and realtime:
+            time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
+    return requests
+
+
+def serve_sequential(models, requests, fit_kwargs):
+    """The plain path: one fit at a time in arrival order on the GPU ({kind: Model})."""
+    t0 = time.perf_counter()
+    for r in sorted(requests, key=lambda r: r.arrival):
+        now = time.perf_counter() - t0
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        r.admitted = time.perf_counter() - t0
+        m = models[r.kind]
+        m.load(r.columns)
+        r.result = m.fit(r.theta0, **fit_kwargs[r.kind])
+        r.done = time.perf_counter() - t0
+    return requests
+
+
+def latency_summary(requests):
+    lat = np.array([r.done - r.arrival for r in requests])
+    span = max(r.done for r in requests) - min(r.arrival for r in requests)
+    return {"n": len(requests), "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "fits_per_s": len(requests) / span if span > 0 else None}

@@ -1,0 +1,58 @@
+"""The torch.autograd.Function around the fused kernel: backward is the kernel's analytic
+gradient, agrees with central finite differences of forward, and with the oracle at 1e7
+weighted events."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_12414_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_backward_matches_kernel_gradient_and_finite_differences(gpu_lib):
+    import torch
+
+    from paper_2505_12414_gb300 import autograd
+
+    cols = synth.kstar4d(20000, stream=31)
+    m = gpu_lib.Model(gpu_lib.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D).load(cols)
+    th0 = synth.TRUTH_4D + 0.01
+    theta = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    y = autograd.nll(m, theta)
+    y.backward()
+    nll, g = m.eval_grad(th0)
+    assert y.item() == nll
+    assert np.array_equal(theta.grad.numpy(), g)
+    _, _, s, _ = oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, cols, th0)
+    for k in range(18):
+        h = 1e-6 * max(abs(th0[k]), 1e-2)
+        tp, tm = th0.copy(), th0.copy()
+        tp[k] += h
+        tm[k] -= h
+        with torch.no_grad():
+            fd = (autograd.nll(m, torch.tensor(tp)).item() - autograd.nll(m, torch.tensor(tm)).item()) / (2 * h)
+        assert abs(fd - g[k]) <= 1e-6 * abs(g[k]) + 1e-7 * s[k], (k, fd, g[k])
+    m.close()
+
+
+@pytest.mark.slow
+def test_backward_against_oracle_10M_weighted(gpu_lib):
+    import torch
+
+    from paper_2505_12414_gb300 import autograd
+
+    n = 10_000_000
+    cols = synth.kstar4d(n, stream=4)
+    w = synth.weights(n, stream=1000007)
+    m = gpu_lib.Model(gpu_lib.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D).load(cols, w)
+    th = synth.TRUTH_4D - 0.005
+    theta = torch.tensor(th, dtype=torch.float64, device="cuda", requires_grad=True)
+    y = autograd.nll(m, theta)
+    (2.0 * y).backward()
+    rn, rg, rs, st = oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, cols, th, w=w, nthreads=16)
+    assert st == 0
+    assert abs(y.item() - rn) <= 1e-12 * abs(rn)
+    g = theta.grad.cpu().numpy() / 2.0
+    assert np.all(np.abs(g - rg) <= 1e-9 * np.abs(rg) + 1e-13 * rs)
+    m.close()

@@ -1,0 +1,97 @@
+"""Serving with continuous batching: each fit gives the same result alone and in the mix,
+admission respects the pool budget, and served fits match one-at-a-time fits."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2505_12414_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+M1, M4 = oracle.MASS1D, oracle.KSTAR4D
+
+
+def opts(kind):
+    n = 4 if kind == M1 else 18
+    lo, hi = np.zeros(n), np.zeros(n)
+    hi[-1] = 1.0
+    step = np.array([2.0, 1.0, 2e-4, 0.02]) if kind == M1 else np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    return dict(lo=lo, hi=hi, step=step, tol_edm=1e-12, strategy=1, hessian=1)
+
+
+def make_requests(n, stream0):
+    from paper_2505_12414_gb300.serve import Request
+
+    rs = synth.Stream(stream0, 1)
+    sizes = np.exp(np.log(1000) + (np.log(8000) - np.log(1000)) * rs.uniform(n)).astype(int)
+    reqs = []
+    for i in range(n):
+        kind = M1 if i % 2 == 0 else M4
+        cols = synth.mass1d(int(sizes[i]), stream=stream0 + i) if kind == M1 else synth.kstar4d(int(sizes[i]), stream=stream0 + i)
+        th0 = (synth.TRUTH_1D if kind == M1 else synth.TRUTH_4D) + 0.3 * opts(kind)["step"]
+        reqs.append(Request(i, kind, cols, th0, 0.0))
+    return reqs
+
+
+def servers(g, slots, pool):
+    return {k: g.Server(k, synth.RANGES_1D if k == M1 else synth.RANGES_4D, slots, pool, 1024, **opts(k))
+            for k in (M1, M4)}
+
+
+def test_results_are_the_same_alone_and_in_the_mix(gpu_lib):
+    from paper_2505_12414_gb300.serve import serve
+
+    mix = make_requests(10, 9100)
+    srv = servers(gpu_lib, 8, 200000)
+    serve(srv, mix, realtime=False)
+    for s in srv.values():
+        s.close()
+    alone = make_requests(10, 9100)
+    for r in alone:
+        srv = servers(gpu_lib, 1, 20000)
+        serve(srv, [r], realtime=False)
+        for s in srv.values():
+            s.close()
+    for a, b in zip(mix, alone):
+        assert a.result["status"] == 0 and b.result["status"] == 0
+        assert np.array_equal(a.result["theta"], b.result["theta"]), (a.rid, a.result["theta"] - b.result["theta"])
+        assert np.array_equal(a.result["err"], b.result["err"])
+        assert a.result["nll"] == b.result["nll"]
+
+
+def test_admission_by_pool_budget(gpu_lib):
+    s = gpu_lib.Server(M1, synth.RANGES_1D, 4, 5000, 1024, **opts(M1))
+    c1, c2 = synth.mass1d(3000, stream=1), synth.mass1d(3000, stream=2)
+    id1 = s.submit(c1, synth.TRUTH_1D)
+    assert id1 is not None
+    assert s.submit(c2, synth.TRUTH_1D) is None  # 3000 + 3000 events exceed the 5000-event pool
+    st = s.status()
+    assert st["busy"] == 1 and st["free_slots"] == 3 and st["free_events"] == 2000
+    done = []
+    for _ in range(500):
+        s.step(4)
+        done += s.poll()
+        if done:
+            break
+    assert [d[0] for d in done] == [id1] and done[0][1]["status"] == 0
+    assert s.submit(c2, synth.TRUTH_1D) is not None
+    s.close()
+
+
+def test_served_fits_match_model_fits(gpu_lib):
+    from paper_2505_12414_gb300.serve import serve
+
+    reqs = make_requests(4, 9200)
+    srv = servers(gpu_lib, 4, 100000)
+    serve(srv, reqs, realtime=False)
+    for r in reqs:
+        m = gpu_lib.Model(r.kind, synth.RANGES_1D if r.kind == M1 else synth.RANGES_4D)
+        m.load(r.columns)
+        o = dict(opts(r.kind))
+        o["tol_edm"] = 1e-14
+        ref = m.fit(r.theta0, **o)
+        m.close()
+        pull = (r.result["theta"] - ref["theta"]) / ref["err"]
+        assert np.max(np.abs(pull)) < 1e-4, pull  # served fits stop at EDM 1e-12
+    for s in srv.values():
+        s.close()
