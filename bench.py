@@ -79,15 +79,16 @@ def parse():
     ap.add_argument("--toys", type=int, default=1000, help="batched 4D toys (0 skips the toy-fit measurement)")
     ap.add_argument("--seq-toys", type=int, default=20, help="toys fitted one at a time for comparison")
     ap.add_argument("--requests", type=int, default=30, help="served fits (0 skips the serving measurement)")
-    ap.add_argument("--rate", type=float, default=50.0, help="Poisson arrival rate of served fits per second")
+    ap.add_argument("--study-toys", type=int, default=100, help="toys per size in the paper-style toy study (0 skips)")
+    ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0],
+                    help="Poisson arrival rates of served fits per second (one measurement each)")
     return ap.parse_args()
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2505_12414_gb300 import dist as gd
+
+    return gd.env()
 
 
 def thetas(k):
@@ -112,7 +113,7 @@ class ClockSampler:
             self.f = tempfile.TemporaryFile(mode="w+")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -257,6 +258,38 @@ def serving(g, device, n_req, rate, seed_stream=0):
     return out
 
 
+def toy_study(g, device, n_toys):
+    """The paper's pseudo-experiment study on its own mass-fit configuration (Sec. 3.2, GeV
+    units: [5, 7], fsig 0.3, mu 5.28, sigma 0.06, alpha -1): per N in 1e3..1e6, n_toys toys are
+    generated on the device, fitted from the generation values, and their uncertainties taken
+    from the Hessian; ms per pseudo-experiment by wall clock of the synchronous calls."""
+    lo, hi = np.zeros(4), np.zeros(4)
+    hi[3] = 1.0
+    step = np.array([0.005, 0.005, 0.05, 0.02])
+    out = {}
+    for n in (1000, 10000, 100000, 1000000):
+        b = g.Batch(g.NLL_MODEL_MASS1D, synth.RANGES_1D_GEV, device=device)
+        b.generate(synth.TRUTH_1D_GEV, [n] * n_toys, seed=synth.BASE_SEED)  # warm-up
+        b.autotune()
+        b.fit(synth.TRUTH_1D_GEV, lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=1, hessian=1)
+        t0 = time.perf_counter()
+        b.generate(synth.TRUTH_1D_GEV, [n] * n_toys, seed=synth.BASE_SEED + 1)
+        t1 = time.perf_counter()
+        r = b.fit(synth.TRUTH_1D_GEV, lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=1, hessian=1)
+        t2 = time.perf_counter()
+        sched = b.get_schedule()
+        b.close()
+        pulls = (r["theta"] - synth.TRUTH_1D_GEV) / r["err"]
+        out[str(n)] = {"schedule": sched, "ms_per_toy": 1e3 * (t2 - t0) / n_toys, "generation_ms_per_toy": 1e3 * (t1 - t0) / n_toys,
+                       "fit_ms_per_toy": 1e3 * (t2 - t1) / n_toys, "converged": int(np.sum(r["status"] == 0)),
+                       "mean_evals": float(np.mean(r["n_eval"])), "pull_mean": pulls.mean(axis=0).round(3).tolist(),
+                       "pull_width": pulls.std(axis=0).round(3).tolist()}
+    out["toys_per_size"] = n_toys
+    out["paper_context_ms_per_toy"] = {"MoreFit OpenCL GPU analytic, Titan V": {"1000": 1.24, "10000": 1.62,
+                                                                                  "100000": 4.06, "1000000": 19.7}}
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -301,7 +334,9 @@ def run_ours(args):
     g.load()
     stream = torch.cuda.current_stream(dev)
 
-    cols = synth.kstar4d(N_EVENTS, stream=rank)
+    from paper_2505_12414_gb300 import dist as gd
+
+    cols = synth.kstar4d(N_EVENTS, stream=gd.sample_stream(rank))
     model = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=local, stream=stream.cuda_stream)
     model.load(cols, precompute=True)
     th = thetas(args.warmup + args.steps)
@@ -323,7 +358,7 @@ def run_ours(args):
 
     sampler = ClockSampler(local)
     sampler.start()
-    time.sleep(0.3)
+    time.sleep(0.05)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -341,13 +376,9 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = gd.max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / args.steps
-    value = world * N_EVENTS / (ms_per_step * 1e-3)
+    value = gd.whole_job_rate(N_EVENTS, world, ms_per_step * 1e-3)
 
     # end to end through the public API: pinned host columns copied every step
     pinned = []
@@ -367,11 +398,7 @@ def run_ours(args):
         s1.synchronize()
         if i >= 2:
             e2e_ms.append(s0.elapsed_time(s1))
-    e2e_step = statistics.median(e2e_ms) if e2e_ms else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = gd.max_over_ranks(statistics.median(e2e_ms) if e2e_ms else float("nan"), device=dev)
 
     kms = statistics.median(kernel_ms)
     achieved = FLOPS_PER_EVENT * N_EVENTS / (kms * 1e-3) / 1e12
@@ -386,9 +413,12 @@ def run_ours(args):
     toys = None
     if args.toys > 0:
         toys = toy_fits(g, local, args.toys, args.seq_toys, seed_stream=rank)
+    study = None
+    if args.study_toys > 0:
+        study = toy_study(g, local, args.study_toys)
     served = None
     if args.requests > 0:
-        served = serving(g, local, args.requests, args.rate, seed_stream=rank)
+        served = [serving(g, local, args.requests, r, seed_stream=rank) for r in args.rate]
 
     if rank == 0:
         cpu = None
@@ -406,7 +436,7 @@ def run_ours(args):
                         "h2d_bytes_per_step": 4 * 8 * N_EVENTS, "d2h_bytes_per_step": 8 * (k_acc + 3),
                         "ms_per_step": e2e_step},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
-                "toy_fits": toys, "serving": served}
+                "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:

@@ -245,6 +245,31 @@ int nll_batch_load(nll_batch* b, const int64_t* offsets, int n_toys, const doubl
                    const double* weights, int precompute);
 
 /*
+ * nll_batch_generate -- generate the toys on the device instead of loading them (paper
+ * Sec. 2.5: accept-reject on the accelerator with the parameters fixed, so parameter-only
+ * terms fold into constants).  Toy t gets counts[t] events drawn at `theta` from stream t of
+ * a counter-based SplitMix64 generator seeded with `seed`; the result depends only on
+ * (seed, t, event index), not on the launch.  precompute as nll_batch_load.
+ * Returns NLL_ERR_ARG for an invalid theta, NLL_ERR_NOT_CONVERGED if some event exhausted its
+ * accept-reject tries (the batch is then empty).
+ */
+int nll_batch_generate(nll_batch* b, const double* theta, const int64_t* counts, int n_toys, uint64_t seed,
+                       int precompute);
+
+/*
+ * nll_generate -- generate n_events events of `kind` at `theta` into caller-owned device
+ * columns (ndim pointers, n_events doubles each) on `device`/`cuda_stream`, from stream
+ * `stream` of the generator seeded with `seed` (the same events as toy `stream` of
+ * nll_batch_generate).  Allocates small temporary device buffers.  Blocks until done.
+ */
+int nll_generate(int kind, const double* obs_ranges, const double* theta, int64_t n_events, uint64_t seed,
+                 uint64_t stream, int device, uintptr_t cuda_stream, double* const* dev_columns);
+
+/* Diagnostic: the first n uniforms in (0, 1) of stream (seed, stream) of the device generator
+ * (SplitMix64: value k = mix(state + (k+1) gamma), state = mix(seed ^ mix(stream gamma + 1))). */
+int nll_diag_uniforms(uint64_t seed, uint64_t stream, int64_t n, int device, double* host_out);
+
+/*
  * nll_batch_eval_grad -- one evaluation of every toy at its own parameter point.
  *   thetas       host [n_toys][npar]; nll_out host [n_toys]; grad_out host [n_toys][npar].
  *   status_out   host [n_toys] nll_status per toy (NULL allowed).

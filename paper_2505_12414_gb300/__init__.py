@@ -121,6 +121,11 @@ def load(path=None):
     L.nll_server_last_error.restype = ctypes.c_char_p
     L.nll_server_destroy.argtypes = [vp]
     L.nll_server_destroy.restype = None
+    L.nll_batch_generate.argtypes = [vp, _DP, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_uint64,
+                                     ctypes.c_int]
+    L.nll_generate.argtypes = [ctypes.c_int, _DP, _DP, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                               ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.nll_diag_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, _DP]
     L.nll_eval_grad_4d_noalloc.argtypes = [_DP, ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int64,
                                            _DP, ctypes.c_int, ctypes.c_int, ctypes.c_size_t, _DP, _DP]
     _lib = L
@@ -346,6 +351,29 @@ def nll_diag_math(fn, x, device=0):
 NLL_NOALLOC_MAX_BLOCKS = 1024
 
 
+def nll_generate(kind, obs_ranges, theta, n_events, seed, stream=0, device=0):
+    """Generate n_events events on the device; returns a list of CUDA torch tensors."""
+    import torch
+
+    ndim = 1 if kind == NLL_MODEL_MASS1D else 4
+    cols = [torch.empty(max(int(n_events), 1), dtype=torch.float64, device="cuda:%d" % device) for _ in range(ndim)]
+    ptrs = (ctypes.c_void_p * ndim)(*[c.data_ptr() for c in cols])
+    torch.cuda.synchronize(device)
+    st = load().nll_generate(int(kind), _p(_f64(obs_ranges)), _p(_f64(theta)), int(n_events),
+                             int(seed) & ((1 << 64) - 1), int(stream), int(device), 0, ptrs)
+    if st != NLL_OK:
+        raise NLLError(st, "nll_generate failed")
+    return [c[: int(n_events)] for c in cols]
+
+
+def nll_diag_uniforms(seed, stream, n, device=0):
+    out = np.zeros(int(n))
+    st = load().nll_diag_uniforms(int(seed) & ((1 << 64) - 1), int(stream), int(n), int(device), _p(out))
+    if st != NLL_OK:
+        raise NLLError(st, "nll_diag_uniforms failed")
+    return out
+
+
 def nll_eval_grad_4d_noalloc(obs_ranges, dev_columns, theta, dev_weights=None, blocks=0, stream=0, check=True):
     """4D NLL and gradient on caller-owned device buffers (CUDA tensors or raw pointers),
     without any device allocation by the library.  Returns (nll, grad[, status])."""
@@ -470,6 +498,16 @@ class Batch:
                                    ptrs, w.ctypes.data if w is not None else None, 1 if precompute else 0)
         _bcheck(self.handle, st)
         self.n_toys = len(off) - 1
+        return self
+
+    def generate(self, theta, counts, seed, precompute=True):
+        """Generate the toys on the device (counts[t] events for toy t) instead of loading them."""
+        c = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+        th = _f64(theta)
+        st = load().nll_batch_generate(self.handle, _p(th), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(c),
+                                       int(seed) & ((1 << 64) - 1), 1 if precompute else 0)
+        _bcheck(self.handle, st)
+        self.n_toys = len(c)
         return self
 
     def eval_grad(self, thetas):

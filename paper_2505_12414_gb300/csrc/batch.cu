@@ -912,6 +912,85 @@ int eval_all(nll_batch* b, const double* thetas, double* nll_out, double* grad_o
 }
 
 
+
+// after the events are in d_ev: angular basis, per-toy arrays and work arrays sized for the
+// largest step (every toy with a full stencil); device_sums computes sum (m - ma) per toy
+// on the device instead of uploading b->sum_wdm
+cudaError_t finish_store(nll_batch* b, bool basis, int64_t pos, bool device_sums)
+{
+    const int n_toys = b->n_toys;
+    const int64_t n_pad = b->n_pad;
+    const int64_t total = pos;
+    cudaError_t e = cudaSuccess;
+    if (basis && total > 0) {
+        BArgs ba;
+        ba.ctl = b->d_ev + (size_t)kColCtl * n_pad;
+        ba.ctk = b->d_ev + (size_t)kColCtk * n_pad;
+        ba.phi = b->d_ev + (size_t)kColPhi * n_pad;
+        for (int j = 0; j < 13; ++j) ba.out[j] = b->d_ev + (size_t)(kColH0 + j) * n_pad;
+        ba.n = pos;
+        int blocks = (int)std::min<int64_t>((pos + 255) / 256, (int64_t)b->sm_count * 8);
+        e = launch_basis(std::max(blocks, 1), 256, b->stream, ba);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) {
+            free_work(b);
+            return e;
+        }
+    }
+    b->has_basis = basis;
+    // per-toy arrays and work arrays sized for the largest step (every toy with a full stencil)
+    int64_t tiles_max = 0;
+    const int64_t min_tile_pairs = 64;  // smallest split-toy tile the schedule accepts
+    for (int t = 0; t < n_toys; ++t) {
+        int64_t np = (b->end[t] - b->begin[t] + 1) / 2;
+        tiles_max += np ? (np + min_tile_pairs - 1) / min_tile_pairs : 0;
+    }
+    int64_t max_items = (int64_t)std::max(n_toys, 1) * (2 * b->npar + 1);
+    int64_t max_units = std::max<int64_t>(tiles_max, 1) * (2 * b->npar + 1);
+    if (max_units > (1ll << 30)) {
+        free_work(b);
+        return cudaErrorInvalidValue;
+    }
+    b->max_items = (int)max_items;
+    b->max_units = (int)max_units;
+    e = cudaMalloc(&b->d_begin, sizeof(int64_t) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_end, sizeof(int64_t) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sum_wdm, sizeof(double) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_toy, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_u0, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_nt, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_kc, sizeof(KConst) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_dc, sizeof(DConst) * max_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_item, sizeof(int) * max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_tile, sizeof(int) * max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_sums, sizeof(double) * kAccMax * max_units);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_fits, sizeof(ToyFit) * std::max(n_toys, 1));
+    // every index the kernels can read is valid from the start
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_toy, 0, sizeof(int) * max_items, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_u0, 0, sizeof(int) * max_items, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_nt, 0, sizeof(int) * max_items, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_unit_item, 0, sizeof(int) * max_units, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_unit_tile, 0, sizeof(int) * max_units, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 4, b->stream);
+    if (e == cudaSuccess && n_toys) {
+        e = cudaMemcpyAsync(b->d_begin, b->begin.data(), sizeof(int64_t) * n_toys, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_end, b->end.data(), sizeof(int64_t) * n_toys, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess && !device_sums)
+            e = cudaMemcpyAsync(b->d_sum_wdm, b->sum_wdm.data(), sizeof(double) * n_toys, cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess && device_sums) {
+            e = toy_sums(b->d_ev, b->d_begin, b->d_end, b->ranges[0], n_toys, b->d_sum_wdm, b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->sum_wdm.data(), b->d_sum_wdm, sizeof(double) * n_toys, cudaMemcpyDeviceToHost,
+                                    b->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) free_work(b);
+    return e;
+}
+
 // minimiser settings shared by all toys
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
                   const fit_options& opt)
@@ -1110,66 +1189,60 @@ int nll_batch_load(nll_batch* b, const int64_t* offsets, int n_toys, const doubl
         free_work(b);
         return bcuda(b, e, "batch copy");
     }
-    if (basis && total > 0) {
-        BArgs ba;
-        ba.ctl = b->d_ev + (size_t)kColCtl * n_pad;
-        ba.ctk = b->d_ev + (size_t)kColCtk * n_pad;
-        ba.phi = b->d_ev + (size_t)kColPhi * n_pad;
-        for (int j = 0; j < 13; ++j) ba.out[j] = b->d_ev + (size_t)(kColH0 + j) * n_pad;
-        ba.n = pos;
-        int blocks = (int)std::min<int64_t>((pos + 255) / 256, (int64_t)b->sm_count * 8);
-        e = launch_basis(std::max(blocks, 1), 256, b->stream, ba);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) {
-            free_work(b);
-            return bcuda(b, e, "batch basis precompute");
-        }
-    }
-    b->has_basis = basis;
-    // per-toy arrays and work arrays sized for the largest step (every toy with a full stencil)
-    int64_t tiles_max = 0;
-    const int64_t min_tile_pairs = 64;  // smallest split-toy tile the schedule accepts
+    e = finish_store(b, basis, pos, false);
+    if (e != cudaSuccess) return bcuda(b, e, "batch work arrays");
+    b->loaded = true;
+    b->err.clear();
+    return NLL_OK;
+}
+
+int nll_batch_generate(nll_batch* b, const double* theta, const int64_t* counts, int n_toys, uint64_t seed,
+                       int precompute)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (n_toys < 0 || (n_toys > 0 && (!counts || !theta))) return bfail(b, NLL_ERR_ARG, "bad arguments");
+    for (int t = 0; t < n_toys; ++t)
+        if (counts[t] < 0) return bfail(b, NLL_ERR_ARG, "negative event count");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
+    if (follow_user_stream(b) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "stream ordering failed");
+    cudaStreamSynchronize(b->stream);
+    free_work(b);
+    b->n_toys = n_toys;
+    b->begin.assign(n_toys, 0);
+    b->end.assign(n_toys, 0);
+    b->sum_wdm.assign(n_toys, 0.0);
+    int64_t pos = 0;
     for (int t = 0; t < n_toys; ++t) {
-        int64_t np = (b->end[t] - b->begin[t] + 1) / 2;
-        tiles_max += np ? (np + min_tile_pairs - 1) / min_tile_pairs : 0;
+        pos = (pos + 1) & ~int64_t(1);
+        b->begin[t] = pos;
+        pos += counts[t];
+        b->end[t] = pos;
     }
-    int64_t max_items = (int64_t)std::max(n_toys, 1) * (2 * b->npar + 1);
-    int64_t max_units = std::max<int64_t>(tiles_max, 1) * (2 * b->npar + 1);
-    if (max_units > (1ll << 30)) return bfail(b, NLL_ERR_ARG, "too many work units");
-    b->max_items = (int)max_items;
-    b->max_units = (int)max_units;
-    e = cudaMalloc(&b->d_begin, sizeof(int64_t) * std::max(n_toys, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_end, sizeof(int64_t) * std::max(n_toys, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_sum_wdm, sizeof(double) * std::max(n_toys, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_toy, sizeof(int) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_u0, sizeof(int) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_nt, sizeof(int) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_kc, sizeof(KConst) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_dc, sizeof(DConst) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_item, sizeof(int) * max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_tile, sizeof(int) * max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_sums, sizeof(double) * kAccMax * max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_fits, sizeof(ToyFit) * std::max(n_toys, 1));
-    // every index the kernels can read is valid from the start
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_toy, 0, sizeof(int) * max_items, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_u0, 0, sizeof(int) * max_items, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_nt, 0, sizeof(int) * max_items, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_unit_item, 0, sizeof(int) * max_units, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_unit_tile, 0, sizeof(int) * max_units, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 4, b->stream);
-    if (e == cudaSuccess && n_toys) {
-        e = cudaMemcpyAsync(b->d_begin, b->begin.data(), sizeof(int64_t) * n_toys, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_end, b->end.data(), sizeof(int64_t) * n_toys, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(b->d_sum_wdm, b->sum_wdm.data(), sizeof(double) * n_toys, cudaMemcpyHostToDevice,
-                                b->stream);
+    const int64_t n_pad = std::max<int64_t>((pos + 63) / 64 * 64, 64);
+    const bool basis = b->kind == kKstar4D && precompute;
+    b->ncols = b->kind == kMass1D ? 1 : (basis ? kNumCols : 4);
+    b->n_pad = n_pad;
+    b->weighted = false;
+    cudaError_t e = cudaMalloc(&b->d_ev, sizeof(double) * n_pad * b->ncols);
+    if (e != cudaSuccess) {
+        b->d_ev = nullptr;
+        return bcuda(b, e, "batch event store");
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    e = cudaMemsetAsync(b->d_ev, 0, sizeof(double) * n_pad * b->ncols, b->stream);
     if (e != cudaSuccess) {
         free_work(b);
-        return bcuda(b, e, "batch work arrays");
+        return bcuda(b, e, "batch event store");
     }
+    double* out[4] = {b->d_ev, nullptr, nullptr, nullptr};
+    if (b->kind == kKstar4D)
+        for (int d = 1; d < 4; ++d) out[d] = b->d_ev + (size_t)d * n_pad;
+    int st = gen_toys(b->kind, b->ranges, theta, counts, n_toys, seed, b->begin.data(), out, b->sm_count, b->stream);
+    if (st != NLL_OK) {
+        free_work(b);
+        return bfail(b, st, "generation failed (invalid parameters or accept-reject did not converge)");
+    }
+    e = finish_store(b, basis, pos, true);
+    if (e != cudaSuccess) return bcuda(b, e, "batch work arrays");
     b->loaded = true;
     b->err.clear();
     return NLL_OK;

@@ -109,6 +109,14 @@ cudaError_t upload_exp2_table_values(const double* host_table);  // 2^(j/N), N =
 int exp2_table_size();
 int num_acc(int kind, bool grad);
 
+// On-device generation (gen.cu): toy t gets counts[t] events from stream (seed, t) at
+// column positions out_pos[t]...; returns an nll_status.
+int gen_toys(int kind, const double* ranges, const double* theta, const int64_t* counts, int n_toys, uint64_t seed,
+             const int64_t* out_pos, double* const* out, int sm_count, cudaStream_t stream);
+// per-toy sum of (m - ma) over [begin, end) (device arrays), fixed order
+cudaError_t toy_sums(const double* m, const int64_t* d_begin, const int64_t* d_end, double ma, int n_toys,
+                     double* d_out, cudaStream_t stream);
+
 // Static device scratch of nll_eval_grad_4d_noalloc (kernels.cu).
 constexpr int kNoAllocMaxBlocks = 1024;
 struct NoAllocScratch {
