@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--seq-toys", type=int, default=20, help="toys fitted one at a time for comparison")
     ap.add_argument("--requests", type=int, default=30, help="served fits (0 skips the serving measurement)")
     ap.add_argument("--study-toys", type=int, default=100, help="toys per size in the paper-style toy study (0 skips)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the mass-model event-count sweep")
+    ap.add_argument("--no-calibration", action="store_true", help="skip the FP64 calibration kernels")
     ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0],
                     help="Poisson arrival rates of served fits per second (one measurement each)")
     return ap.parse_args()
@@ -290,6 +292,32 @@ def toy_study(g, device, n_toys):
     return out
 
 
+def mass_sweep(g, device, stream):
+    """Mass model (Sec. 3.2, MeV configuration): NLL+gradient evaluations per second against
+    the sample size, from latency-bound (1e3 events) to throughput-bound (1e7)."""
+    import torch
+
+    out = {}
+    for n in (1000, 10000, 100000, 1000000, 10000000):
+        cols = synth.mass1d(n, stream=5)
+        m = g.Model(g.NLL_MODEL_MASS1D, synth.RANGES_1D, device=device, stream=stream.cuda_stream).load(cols)
+        m.eval_grad(synth.TRUTH_1D)
+        g.nll_autotune(m.handle)
+        th = [synth.TRUTH_1D * (1.0 + 1e-4 * k) for k in range(25)]
+        for k in range(5):
+            m.eval_grad(th[k])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(5, 25):
+            m.eval_grad(th[k])
+        e1.record(stream)
+        e1.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / 20
+        out[str(n)] = {"us_per_eval": us, "events_per_s": n / (us * 1e-6)}
+        m.close()
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -346,7 +374,7 @@ def run_ours(args):
     else:
         g.nll_autotune(model.handle)
     launch = g.nll_get_launch(model.handle)
-    rates = g.nll_calibrate_fp64(local)
+    rates = None if args.no_calibration else g.nll_calibrate_fp64(local)
     peak = FP64_PEAK_TFLOPS
     g.nll_set_profiling(model.handle, True)
 
@@ -407,12 +435,14 @@ def run_ours(args):
                 "kernel": "fused_nll_kernel<4D, precompute, grad>", "kernel_ms": kms,
                 "peak_source": "recipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
                 "flops_per_event": FLOPS_PER_EVENT,
-                "calibration": {"dfma_per_s": rates["dfma"], "cuda_exp_slots": rates["dfma"] / rates["cuda_exp"],
-                                "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}
+                "calibration": None if rates is None else {
+                    "dfma_per_s": rates["dfma"], "cuda_exp_slots": rates["dfma"] / rates["cuda_exp"],
+                    "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}
 
     toys = None
     if args.toys > 0:
         toys = toy_fits(g, local, args.toys, args.seq_toys, seed_stream=rank)
+    sweep = None if args.no_sweep else mass_sweep(g, local, stream)
     study = None
     if args.study_toys > 0:
         study = toy_study(g, local, args.study_toys)
@@ -436,7 +466,8 @@ def run_ours(args):
                         "h2d_bytes_per_step": 4 * 8 * N_EVENTS, "d2h_bytes_per_step": 8 * (k_acc + 3),
                         "ms_per_step": e2e_step},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
-                "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study}
+                "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
+                "mass_model_sweep": sweep}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:
