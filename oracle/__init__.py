@@ -1,4 +1,5 @@
-"""Oracle: plain CPU FP64 reference for the unbinned NLL of arXiv 2505.12414 and its gradient.
+"""Oracle: plain CPU FP64 reference for the unbinned NLL of arXiv 2505.12414, its gradient
+and its Hessian.
 
 TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and bench.py's
 CPU-baseline leg may import this package.  The product path (the CUDA library and its
@@ -43,6 +44,13 @@ def lib():
         L.oracle_angular_terms.restype = None
         L.oracle_mass_norms.argtypes = [ctypes.c_double] * 5 + [dp]
         L.oracle_mass_norms.restype = None
+        L.oracle_nll_hess.argtypes = [ctypes.c_int, dp, dpp, dp, ctypes.c_int64, dp, ctypes.c_int, dp, dp, dp, dp,
+                                      dp]
+        L.oracle_nll_hess.restype = ctypes.c_int
+        L.oracle_mass_norms2.argtypes = [ctypes.c_double] * 5 + [dp]
+        L.oracle_mass_norms2.restype = None
+        L.oracle_d2logpdf.argtypes = [ctypes.c_int, dp, dp, dpp, ctypes.c_int64, dp]
+        L.oracle_d2logpdf.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -117,3 +125,43 @@ def mass_norms(ma, mb, mu, sigma, alpha):
     out = np.zeros(5)
     lib().oracle_mass_norms(ma, mb, mu, sigma, alpha, _dptr(out))
     return dict(N1=out[0], dlnN1_dmu=out[1], dlnN1_dsigma=out[2], N2=out[3], dlnN2_dalpha=out[4])
+
+
+def nll_hess(kind, ranges, cols, theta, w=None, nthreads=1):
+    """Return dict(nll, grad, hess, w2, hscale, status).
+
+    ``hess`` is the Hessian of the NLL, ``w2`` = sum_i w_i^2 s_i s_i^T with s_i = d ln P_i/dtheta
+    (the middle of the weighted-fit sandwich covariance), ``hscale[a, b]`` = sum_i
+    |w_i d^2 ln P_i / da db|, the size of the terms that make up hess[a, b]."""
+    L = lib()
+    arrs, ptrs = _cols(cols)
+    n = len(arrs[0])
+    npar = NPAR[kind]
+    wa = _f64(w) if w is not None else None
+    out = np.zeros(1)
+    g = np.zeros(npar)
+    h = np.zeros((npar, npar))
+    q = np.zeros((npar, npar))
+    hs = np.zeros((npar, npar))
+    st = L.oracle_nll_hess(kind, _dptr(_f64(ranges)), ptrs, _dptr(wa) if wa is not None else None, n,
+                           _dptr(_f64(theta)), int(nthreads), _dptr(out), _dptr(g), _dptr(h), _dptr(q), _dptr(hs))
+    return dict(nll=float(out[0]), grad=g, hess=h, w2=q, hscale=hs, status=st)
+
+
+def mass_norms2(ma, mb, mu, sigma, alpha):
+    """dict with the second derivatives d2lnN1_mumu, d2lnN1_musigma, d2lnN1_sigmasigma, d2lnN2_alpha."""
+    out = np.zeros(4)
+    lib().oracle_mass_norms2(ma, mb, mu, sigma, alpha, _dptr(out))
+    return dict(d2lnN1_mumu=out[0], d2lnN1_musigma=out[1], d2lnN1_sigmasigma=out[2], d2lnN2_alpha=out[3])
+
+
+def d2logpdf(kind, ranges, theta, cols):
+    """Per-event d^2 ln P_i / dtheta dtheta^T, shape (n, npar, npar)."""
+    L = lib()
+    arrs, ptrs = _cols(cols)
+    n = len(arrs[0])
+    npar = NPAR[kind]
+    out = np.zeros((n, npar, npar))
+    st = L.oracle_d2logpdf(kind, _dptr(_f64(ranges)), _dptr(_f64(theta)), ptrs, n, _dptr(out))
+    assert st == OK
+    return out

@@ -40,6 +40,16 @@
  *     exponential-times-Chebyshev background is the reading taken for the 4D
  *     benchmark configuration.
  *
+ * Second derivatives (paper Sec. 2.1 names the analytic Hessian used for the HESSE
+ * uncertainties, and the Fisher information needed for weighted fits, without printing
+ * either): oracle_nll_hess returns
+ *     H_ab = d^2 NLL / dtheta_a dtheta_b = - sum_i w_i (P_ab / P - P_a P_b / P^2)_i
+ *     W_ab = sum_i w_i^2 (P_a / P)_i (P_b / P)_i
+ * from hand-derived second derivatives P_ab of the plain model.  For a weighted fit the
+ * asymptotic covariance is H^-1 W H^-1 (Langenbruch, Eur. Phys. J. C 82 (2022) 393, the
+ * reference the paper gives for weighted fits); for w = 1 both H and W estimate the
+ * Fisher information.
+ *
  * Threads: events are split into static contiguous chunks, each chunk sums with
  * Kahan, and the chunk sums are merged in chunk order (again with Kahan), so the
  * result does not depend on scheduling.
@@ -90,6 +100,8 @@ typedef struct {
     double dlnN1_dsig;  /* d ln N1 / d sigma                                        */
     double N2;          /* exponential normalisation over [ma, mb]                  */
     double dlnN2_dal;   /* d ln N2 / d alpha                                        */
+    double d2lnN1[3];   /* d^2 ln N1 / (dmu dmu, dmu dsigma, dsigma dsigma)          */
+    double d2lnN2_dal2; /* d^2 ln N2 / d alpha^2 = (mb - ma)^2 v(alpha (mb - ma))    */
 } mass_norm_t;
 
 static void mass_norm(mass_norm_t* n, double ma, double mb, double mu, double sigma, double alpha)
@@ -109,8 +121,42 @@ static void mass_norm(mass_norm_t* n, double ma, double mb, double mu, double si
     double dN1_dsig = -(za * ea - zb * eb) / (sqrt(kPi) * sigma);
     n->dlnN1_dmu = dN1_dmu / n->N1;
     n->dlnN1_dsig = dN1_dsig / n->N1;
+    /* second derivatives of N1: differentiate the two first derivatives above once more,
+     * with d ea / dmu = -2 za ea / (sqrt2 sigma) and d ea / dsigma = 2 za^2 ea / sigma */
+    double d2N1_mumu = -(za * ea - zb * eb) / (sqrt(kPi) * sigma * sigma);
+    double d2N1_musig = (ea * (2.0 * za * za - 1.0) - eb * (2.0 * zb * zb - 1.0)) / (sqrt(2.0 * kPi) * sigma * sigma);
+    double d2N1_sigsig = (za * ea * (2.0 - 2.0 * za * za) - zb * eb * (2.0 - 2.0 * zb * zb)) / (sqrt(kPi) * sigma * sigma);
+    /* d^2 ln N = N''/N - (N'/N)(N'/N) */
+    n->d2lnN1[0] = d2N1_mumu / n->N1 - n->dlnN1_dmu * n->dlnN1_dmu;
+    n->d2lnN1[1] = d2N1_musig / n->N1 - n->dlnN1_dmu * n->dlnN1_dsig;
+    n->d2lnN1[2] = d2N1_sigsig / n->N1 - n->dlnN1_dsig * n->dlnN1_dsig;
     /* N2 = integral exp(alpha m) dm over [ma, mb]; the paper's alpha == 0 branch gives mb - ma */
     double D = mb - ma;
+    /* d^2 ln N2 / d alpha^2 is the variance of m under exp(alpha m) on [ma, mb]:
+     * D^2 v(t), t = alpha D, v(t) = 1/t^2 - e^t / (e^t - 1)^2 = 1/t^2 - 1/(4 sinh^2(t/2)),
+     * even in t, v(0) = 1/12 (uniform).  From the series of coth,
+     *   v(t) = sum_{n >= 1} (2n - 1) B_2n t^(2n-2) / (2n)!   (|t| < 2 pi),
+     * used for |t| < 1/2 with n <= 9 (next term below 1e-18 of v there); above, the closed
+     * form loses at most ~12 u / t^2 to cancellation, written with e^-|t| so it cannot overflow. */
+    {
+        static const double bern[10] = {0.0,          1.0 / 6.0,   -1.0 / 30.0,   1.0 / 42.0,      -1.0 / 30.0,
+                                         5.0 / 66.0,   -691.0 / 2730.0, 7.0 / 6.0, -3617.0 / 510.0, 43867.0 / 798.0};
+        double a = fabs(alpha * D), v;
+        if (a < 0.5) {
+            double t2 = a * a, fact = 2.0;  /* (2n)! */
+            double coef[10];
+            for (int k = 1; k <= 9; ++k) {
+                if (k > 1) fact *= (2.0 * k - 1.0) * (2.0 * k);
+                coef[k] = (2.0 * k - 1.0) * bern[k] / fact;
+            }
+            v = coef[9];
+            for (int k = 8; k >= 1; --k) v = v * t2 + coef[k];
+        } else {
+            double em = expm1(-a);
+            v = 1.0 / (a * a) - exp(-a) / (em * em);
+        }
+        n->d2lnN2_dal2 = D * D * v;
+    }
     if (alpha == 0.0) {
         n->N2 = D;
         n->dlnN2_dal = 0.5 * (ma + mb);
@@ -280,6 +326,119 @@ static double event_density(const model_t* M, const double* x, double* dP)
     return P;
 }
 
+/* Second derivatives d2P[a * npar + b] = d^2 P / dtheta_a dtheta_b for one event, written
+ * out from the plain definition of the model term by term (symmetric; unlisted pairs are 0). */
+static void event_second(const model_t* M, const double* x, double* d2P)
+{
+    const double* th = M->theta;
+    const int np = M->npar;
+    memset(d2P, 0, sizeof(double) * np * np);
+#define SET2(a, b, v)               \
+    do {                            \
+        double v_ = (v);            \
+        d2P[(a) * np + (b)] = v_;   \
+        d2P[(b) * np + (a)] = v_;   \
+    } while (0)
+    double G, dGmu, dGsig, E, dEal;
+    mass_parts(&M->mn, x[0], &G, &dGmu, &dGsig, &E, &dEal);
+    /* second log-derivatives of the Gaussian and of the exponential (paper Eq. 2):
+     * ln G = -d^2/(2 s^2) - ln s - ln N1 + const,  ln E = alpha m - ln N2 */
+    double d = x[0] - M->mn.mu, s = M->mn.sigma;
+    double hmm = -1.0 / (s * s) - M->mn.d2lnN1[0];
+    double hms = -2.0 * d / (s * s * s) - M->mn.d2lnN1[1];
+    double hss = -3.0 * d * d / (s * s * s * s) + 1.0 / (s * s) - M->mn.d2lnN1[2];
+    double haa = -M->mn.d2lnN2_dal2;
+    /* d^2 G / da db = G (dlnG/da dlnG/db + d^2 lnG / da db), likewise for E */
+    double Gmm = G * (dGmu * dGmu + hmm), Gms = G * (dGmu * dGsig + hms), Gss = G * (dGsig * dGsig + hss);
+    double Eaa = E * (dEal * dEal + haa);
+    if (M->kind == OR_MASS1D) {
+        /* P = f G + (1 - f) E, theta = [mu, sigma, alpha, f] */
+        double f = th[3];
+        SET2(0, 0, f * Gmm);
+        SET2(0, 1, f * Gms);
+        SET2(1, 1, f * Gss);
+        SET2(2, 2, (1.0 - f) * Eaa);
+        SET2(3, 0, G * dGmu);
+        SET2(3, 1, G * dGsig);
+        SET2(3, 2, -E * dEal);
+        return;
+    }
+    /* 4D: P = f G A + (1 - f) E B;  A linear in (FL, S3..S9), so d^2 A = 0 */
+    double fa[11], S[11];
+    angular_terms(x[1], x[2], x[3], fa);
+    angular_coefs(th + 2, S);
+    double A = 0.0;
+    for (int i = 0; i < 11; ++i) A += S[i] * fa[i];
+    double dA[8];
+    dA[0] = -fa[0] + fa[1] - fa[2] - fa[3];
+    for (int k = 1; k < 8; ++k) dA[k] = fa[3 + k];
+    /* Chebyshev factors Cn_j = C_j / Nc_j and their derivatives in (c1_j, c2_j):
+     *   dCn/dc1 = x/Nc, dCn/dc2 = T2/Nc - C Nc'/Nc^2,
+     *   d2Cn/dc1^2 = 0, d2Cn/dc1dc2 = -x Nc'/Nc^2, d2Cn/dc2^2 = -2 T2 Nc'/Nc^2 + 2 C Nc'^2/Nc^3 */
+    double xs[3] = {x[1], x[2], x[3] / kPi};
+    double Cn[3], dCn[3][2], d2Cn[3][2][2];
+    for (int j = 0; j < 3; ++j) {
+        double c1 = th[11 + 2 * j], c2 = th[12 + 2 * j];
+        double xv = xs[j], T2 = 2.0 * xv * xv - 1.0;
+        double Cj = 1.0 + c1 * xv + c2 * T2;
+        double Nc = M->Nc[j], Np = M->dNc_dc2[j];
+        Cn[j] = Cj / Nc;
+        dCn[j][0] = xv / Nc;
+        dCn[j][1] = T2 / Nc - Cj * Np / (Nc * Nc);
+        d2Cn[j][0][0] = 0.0;
+        d2Cn[j][0][1] = d2Cn[j][1][0] = -xv * Np / (Nc * Nc);
+        d2Cn[j][1][1] = -2.0 * T2 * Np / (Nc * Nc) + 2.0 * Cj * Np * Np / (Nc * Nc * Nc);
+    }
+    double B = Cn[0] * Cn[1] * Cn[2];
+    /* B derivatives: index 2 j + p for coefficient p (0: c1, 1: c2) of observable j */
+    double dB[6], d2B[6][6];
+    for (int j = 0; j < 3; ++j) {
+        double others = 1.0;
+        for (int k = 0; k < 3; ++k)
+            if (k != j) others *= Cn[k];
+        for (int p = 0; p < 2; ++p) dB[2 * j + p] = others * dCn[j][p];
+    }
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+            for (int p = 0; p < 2; ++p)
+                for (int q = 0; q < 2; ++q) {
+                    double v;
+                    if (j == k) {
+                        double others = 1.0;
+                        for (int l = 0; l < 3; ++l)
+                            if (l != j) others *= Cn[l];
+                        v = others * d2Cn[j][p][q];
+                    } else {
+                        double third = 1.0;
+                        for (int l = 0; l < 3; ++l)
+                            if (l != j && l != k) third *= Cn[l];
+                        v = third * dCn[j][p] * dCn[k][q];
+                    }
+                    d2B[2 * j + p][2 * k + q] = v;
+                }
+    double f = th[17];
+    /* signal block: mass x mass, mass x angular (angular x angular is zero) */
+    SET2(0, 0, f * A * Gmm);
+    SET2(0, 1, f * A * Gms);
+    SET2(1, 1, f * A * Gss);
+    for (int k = 0; k < 8; ++k) {
+        SET2(0, 2 + k, f * G * dGmu * dA[k]);
+        SET2(1, 2 + k, f * G * dGsig * dA[k]);
+    }
+    /* background block: alpha x alpha, alpha x Chebyshev, Chebyshev x Chebyshev */
+    SET2(10, 10, (1.0 - f) * Eaa * B);
+    for (int i = 0; i < 6; ++i) SET2(10, 11 + i, (1.0 - f) * E * dEal * dB[i]);
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) SET2(11 + i, 11 + j, (1.0 - f) * E * d2B[i][j]);
+    /* signal fraction: d/df of the first derivatives (d^2 P / df^2 = 0) */
+    SET2(17, 0, A * G * dGmu);
+    SET2(17, 1, A * G * dGsig);
+    for (int k = 0; k < 8; ++k) SET2(17, 2 + k, G * dA[k]);
+    SET2(17, 10, -E * dEal * B);
+    for (int i = 0; i < 6; ++i) SET2(17, 11 + i, -E * dB[i]);
+#undef SET2
+}
+
 /* ------------------------------------------------------------------ */
 /* Event loop with Kahan sums, split over threads in static chunks.   */
 /* ------------------------------------------------------------------ */
@@ -391,6 +550,133 @@ int oracle_nll_grad(int kind, const double* ranges, const double* const* cols, c
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* Hessian of the NLL and the squared-weight score outer product.      */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    const model_t* M;
+    const double* const* cols;
+    const double* w;
+    int64_t lo, hi;
+    kahan_t nll;
+    kahan_t g[OR_MAXPAR];
+    kahan_t h[OR_MAXPAR * OR_MAXPAR];
+    kahan_t hs[OR_MAXPAR * OR_MAXPAR];
+    kahan_t w2[OR_MAXPAR * OR_MAXPAR];
+    int64_t bad;
+} hchunk_t;
+
+static void* hchunk_run(void* arg)
+{
+    hchunk_t* c = (hchunk_t*)arg;
+    const model_t* M = c->M;
+    int ndim = M->kind == OR_MASS1D ? 1 : 4;
+    int np = M->npar;
+    double x[4], dP[OR_MAXPAR], d2P[OR_MAXPAR * OR_MAXPAR], sc[OR_MAXPAR];
+    for (int64_t i = c->lo; i < c->hi; ++i) {
+        for (int d = 0; d < ndim; ++d) x[d] = c->cols[d][i];
+        double wi = c->w ? c->w[i] : 1.0;
+        double P = event_density(M, x, dP);
+        if (!(P > 0.0) || !isfinite(P)) {
+            c->bad++;
+            continue;
+        }
+        event_second(M, x, d2P);
+        kahan_add(&c->nll, -wi * log(P));
+        for (int a = 0; a < np; ++a) {
+            sc[a] = dP[a] / P;
+            kahan_add(&c->g[a], -(wi * dP[a] / P));  /* the same rounding as oracle_nll_grad */
+        }
+        for (int a = 0; a < np; ++a)
+            for (int b = a; b < np; ++b) {
+                /* d^2 ln P / da db = P_ab / P - (P_a / P)(P_b / P) */
+                double t = wi * (d2P[a * np + b] / P - sc[a] * sc[b]);
+                kahan_add(&c->h[a * np + b], -t);
+                kahan_add(&c->hs[a * np + b], fabs(t));
+                kahan_add(&c->w2[a * np + b], wi * wi * sc[a] * sc[b]);
+            }
+    }
+    return NULL;
+}
+
+/*
+ * oracle_nll_hess: NLL, gradient, Hessian H of the NLL and W = sum_i w_i^2 s_i s_i^T
+ * (s_i = d ln P_i / dtheta), all row-major npar x npar and symmetric, plus
+ * hscale_ab = sum_i |w_i d^2 ln P_i / da db| (size of the terms that make up H_ab).
+ * Arguments as oracle_nll_grad; grad, w2 and hscale may be NULL.  Status as there.
+ */
+int oracle_nll_hess(int kind, const double* ranges, const double* const* cols, const double* w, int64_t n,
+                    const double* theta, int nthreads, double* nll, double* grad, double* hess, double* w2,
+                    double* hscale)
+{
+    model_t M;
+    if (model_setup(&M, kind, ranges, theta) != OR_OK || n < 0 || nthreads < 1 || !nll || !hess) return OR_ERR_ARG;
+    if (nthreads > 256) nthreads = 256;
+    if (n < (int64_t)nthreads * 64) nthreads = 1;
+    hchunk_t* ch = (hchunk_t*)calloc((size_t)nthreads, sizeof(hchunk_t));
+    pthread_t* tid = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!ch || !tid) {
+        free(ch);
+        free(tid);
+        return OR_ERR_ARG;
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        ch[t].M = &M;
+        ch[t].cols = cols;
+        ch[t].w = w;
+        ch[t].lo = n * t / nthreads;
+        ch[t].hi = n * (t + 1) / nthreads;
+    }
+    if (nthreads == 1) {
+        hchunk_run(&ch[0]);
+    } else {
+        for (int t = 0; t < nthreads; ++t) pthread_create(&tid[t], NULL, hchunk_run, &ch[t]);
+        for (int t = 0; t < nthreads; ++t) pthread_join(tid[t], NULL);
+    }
+    const int np = M.npar;
+    kahan_t tot = {0, 0};
+    static const kahan_t zero = {0, 0};
+    kahan_t g[OR_MAXPAR], h[OR_MAXPAR * OR_MAXPAR], hs[OR_MAXPAR * OR_MAXPAR], q[OR_MAXPAR * OR_MAXPAR];
+    for (int k = 0; k < OR_MAXPAR; ++k) g[k] = zero;
+    for (int k = 0; k < OR_MAXPAR * OR_MAXPAR; ++k) h[k] = hs[k] = q[k] = zero;
+    int64_t bad = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        kahan_add(&tot, ch[t].nll.s);
+        kahan_add(&tot, -ch[t].nll.c);
+        for (int a = 0; a < np; ++a) {
+            kahan_add(&g[a], ch[t].g[a].s);
+            kahan_add(&g[a], -ch[t].g[a].c);
+            for (int b = a; b < np; ++b) {
+                int k = a * np + b;
+                kahan_add(&h[k], ch[t].h[k].s);
+                kahan_add(&h[k], -ch[t].h[k].c);
+                kahan_add(&hs[k], ch[t].hs[k].s);
+                kahan_add(&hs[k], -ch[t].hs[k].c);
+                kahan_add(&q[k], ch[t].w2[k].s);
+                kahan_add(&q[k], -ch[t].w2[k].c);
+            }
+        }
+        bad += ch[t].bad;
+    }
+    free(ch);
+    free(tid);
+    if (bad) {
+        *nll = INFINITY;
+        return OR_ERR_NONPOSITIVE;
+    }
+    *nll = tot.s;
+    for (int a = 0; a < np; ++a) {
+        if (grad) grad[a] = g[a].s;
+        for (int b = a; b < np; ++b) {
+            int k = a * np + b;
+            hess[a * np + b] = hess[b * np + a] = h[k].s;
+            if (w2) w2[a * np + b] = w2[b * np + a] = q[k].s;
+            if (hscale) hscale[a * np + b] = hscale[b * np + a] = hs[k].s;
+        }
+    }
+    return OR_OK;
+}
+
 /* Per-event density P_i (for quadrature and special-case checks). */
 int oracle_pdf(int kind, const double* ranges, const double* theta, const double* const* cols, int64_t n,
                double* out)
@@ -438,6 +724,38 @@ void oracle_mass_norms(double ma, double mb, double mu, double sigma, double alp
     out[2] = n.dlnN1_dsig;
     out[3] = n.N2;
     out[4] = n.dlnN2_dal;
+}
+
+/* Second derivatives of the normalisations: [d2lnN1/dmu2, d2lnN1/dmu dsigma, d2lnN1/dsigma2,
+ * d2lnN2/dalpha2]. */
+void oracle_mass_norms2(double ma, double mb, double mu, double sigma, double alpha, double* out)
+{
+    mass_norm_t n;
+    mass_norm(&n, ma, mb, mu, sigma, alpha);
+    out[0] = n.d2lnN1[0];
+    out[1] = n.d2lnN1[1];
+    out[2] = n.d2lnN1[2];
+    out[3] = n.d2lnN2_dal2;
+}
+
+/* Per-event second derivatives of ln P_i, row-major [n][npar][npar] (for per-event checks). */
+int oracle_d2logpdf(int kind, const double* ranges, const double* theta, const double* const* cols, int64_t n,
+                    double* out)
+{
+    model_t M;
+    if (model_setup(&M, kind, ranges, theta) != OR_OK) return OR_ERR_ARG;
+    int ndim = kind == OR_MASS1D ? 1 : 4;
+    int np = M.npar;
+    double x[4], dP[OR_MAXPAR], d2P[OR_MAXPAR * OR_MAXPAR];
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < ndim; ++d) x[d] = cols[d][i];
+        double P = event_density(&M, x, dP);
+        event_second(&M, x, d2P);
+        for (int a = 0; a < np; ++a)
+            for (int b = 0; b < np; ++b)
+                out[(i * np + a) * np + b] = d2P[a * np + b] / P - (dP[a] / P) * (dP[b] / P);
+    }
+    return OR_OK;
 }
 
 int oracle_num_params(int kind) { return npar_of(kind); }

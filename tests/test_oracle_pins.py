@@ -506,3 +506,155 @@ def test_pulls_4d_model():
     mean, width = pulls.mean(axis=0), pulls.std(axis=0)
     assert np.all(np.abs(mean) < 4.0 / math.sqrt(ntoy)), mean
     assert np.all(np.abs(width - 1.0) < 4.0 / math.sqrt(2 * ntoy)), width
+
+
+# --------------------------------------------------------------------------------------
+# second derivatives: the Hessian of the NLL (HESSE uncertainties) and the squared-weight
+# score matrix W = sum w^2 s s^T of the weighted-fit sandwich covariance
+# --------------------------------------------------------------------------------------
+def _hess_case(kind, n, stream):
+    if kind == M1:
+        return synth.mass1d(n, stream=stream), synth.RANGES_1D, np.array([5283.0, 22.0, -0.0017, 0.35])
+    return synth.kstar4d(n, stream=stream), synth.RANGES_4D, synth.TRUTH_4D + 0.01
+
+
+@pytest.mark.parametrize("kind,n", [(M1, 6), (M4, 3)])
+def test_hessian_against_40_digit_differentiation(kind, n):
+    cols, ranges, theta = _hess_case(kind, n, 90 + kind)
+    r = oracle.nll_hess(kind, ranges, cols, theta)
+    assert r["status"] == 0
+    H, hs = r["hess"], r["hscale"]
+    npar = len(theta)
+    mp.mp.dps = 40
+    t0 = [mp.mpf(float(v)) for v in theta]
+    for a in range(npar):
+        for b in range(a, npar):
+            if a == b:
+                def f1(x, a=a):
+                    t = list(t0)
+                    t[a] = x
+                    return _mp_nll(kind, ranges, cols, t)
+                ref = mp.diff(f1, t0[a], 2)
+            else:
+                def f2(x, y, a=a, b=b):
+                    t = list(t0)
+                    t[a], t[b] = x, y
+                    return _mp_nll(kind, ranges, cols, t)
+                ref = mp.diff(f2, (t0[a], t0[b]), (1, 1))
+            ref = float(ref)
+            assert abs(H[a, b] - ref) <= 1e-11 * abs(ref) + 1e-13 * hs[a, b], (a, b, H[a, b], ref)
+            assert H[a, b] == H[b, a]
+
+
+@pytest.mark.parametrize("mu,sigma", [(5279.6, 20.0), (5180.0, 12.0), (5900.0, 60.0), (5570.0, 300.0)])
+def test_gaussian_normalisation_second_derivatives_40_digits(mu, sigma):
+    ma, mb = synth.RANGES_1D
+    mp.mp.dps = 40
+
+    def lnN1(x, y):
+        return mp.log((mp.erf((x - ma) / (mp.sqrt(2) * y)) - mp.erf((x - mb) / (mp.sqrt(2) * y))) / 2)
+
+    r = oracle.mass_norms2(ma, mb, mu, sigma, 0.0)
+    x0, y0 = mp.mpf(mu), mp.mpf(sigma)
+    refs = [mp.diff(lnN1, (x0, y0), (2, 0)), mp.diff(lnN1, (x0, y0), (1, 1)), mp.diff(lnN1, (x0, y0), (0, 2))]
+    got = [r["d2lnN1_mumu"], r["d2lnN1_musigma"], r["d2lnN1_sigmasigma"]]
+    for g, ref in zip(got, refs):
+        # the first-order terms carry the erf difference's relative rounding (~1e-16 / N1)
+        assert abs(g - float(ref)) <= 1e-11 * abs(float(ref)) + 1e-20, (g, ref)
+
+
+@pytest.mark.parametrize("alpha", [-0.002, 0.003, -5e-5, 1e-4, -1.3e-4, 6.1e-4, -6.2e-4, 6.3e-4, 0.0, 1e-9, 0.9])
+def test_exponential_normalisation_second_derivative_is_the_variance(alpha):
+    # d^2 ln N2 / d alpha^2 is the variance of m under exp(alpha m) on the window
+    # (cumulant generating function); at alpha = 0 it is the uniform variance (mb-ma)^2/12.
+    ma, mb = synth.RANGES_1D
+    r = oracle.mass_norms2(ma, mb, 5279.6, 20.0, alpha)["d2lnN2_alpha"]
+    mp.mp.dps = 40
+    a = mp.mpf(alpha)
+    w = lambda x: mp.exp(a * (x - ma))
+    z = mp.quad(w, [ma, mb])
+    m1 = mp.quad(lambda x: x * w(x), [ma, mb]) / z
+    m2 = mp.quad(lambda x: (x - m1) ** 2 * w(x), [ma, mb]) / z
+    assert abs(r - float(m2)) <= 1e-13 * float(m2), (alpha, r, m2)
+    if alpha == 0.0:
+        assert abs(r - (mb - ma) ** 2 / 12) <= 1e-15 * r
+
+
+def test_hessian_pure_gaussian_closed_form():
+    # f = 1 and a window 40 sigma wide: N1 = 1 exactly, so the (mu, sigma) block is the
+    # textbook Gaussian one: sum 1/s^2, sum 2 d/s^3, sum (3 d^2/s^4 - 1/s^2).
+    mu0, s0 = 5500.0, 5.0
+    ranges = [mu0 - 200.0, mu0 + 200.0]
+    m = synth.mass1d(4000, stream=91, theta=[mu0, s0, 0.0, 1.0], ranges=ranges)[0]
+    th = [5501.0, 5.3, 0.0, 1.0]
+    r = oracle.nll_hess(M1, ranges, [m], th)
+    d = m - th[0]
+    s = th[1]
+    assert abs(r["hess"][0, 0] - len(m) / s ** 2) <= 1e-13 * len(m) / s ** 2
+    ref01 = math.fsum(2 * d / s ** 3)
+    assert abs(r["hess"][0, 1] - ref01) <= 1e-12 * math.fsum(abs(2 * d / s ** 3))
+    ref11 = math.fsum(3 * d ** 2 / s ** 4 - 1 / s ** 2)
+    assert abs(r["hess"][1, 1] - ref11) <= 1e-12 * math.fsum(3 * d ** 2 / s ** 4 + 1 / s ** 2)
+
+
+def test_hessian_pure_exponential_is_n_times_variance():
+    # f = 0: the alpha-alpha entry is N Var(m) under the fitted exponential, for any data
+    for alpha in (-0.0025, 0.0, 2e-5):
+        m = synth.mass1d(3000, stream=92, theta=[5279.6, 20.0, -0.0025, 0.0])[0]
+        r = oracle.nll_hess(M1, synth.RANGES_1D, [m], [5279.6, 20.0, alpha, 0.0])
+        v = oracle.mass_norms2(*synth.RANGES_1D, 5279.6, 20.0, alpha)["d2lnN2_alpha"]
+        assert abs(r["hess"][2, 2] - len(m) * v) <= 1e-13 * len(m) * v
+
+
+@pytest.mark.parametrize("kind", [M1, M4])
+def test_hessian_against_central_differences_of_gradient(kind):
+    cols, ranges, theta = _hess_case(kind, 3000, 93)
+    r = oracle.nll_hess(kind, ranges, cols, theta)
+    H, hs = r["hess"], r["hscale"]
+    for k in range(len(theta)):
+        h = 1e-5 * max(abs(theta[k]), 1e-2)
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += h
+        tm[k] -= h
+        fd = (oracle.nll_grad(kind, ranges, cols, tp)[1] - oracle.nll_grad(kind, ranges, cols, tm)[1]) / (2 * h)
+        assert np.all(np.abs(fd - H[:, k]) <= 1e-4 * np.abs(H[:, k]) + 1e-6 * hs[:, k]), (k, fd, H[:, k])
+
+
+@pytest.mark.parametrize("kind", [M1, M4])
+def test_score_matrix_and_weights(kind):
+    cols, ranges, theta = _hess_case(kind, 2000, 94)
+    w = synth.weights(2000, stream=95)
+    r = oracle.nll_hess(kind, ranges, cols, theta, w=w)
+    # W from the per-event scores (gradient code, pinned above) and the weights
+    s = oracle.dlogpdf(kind, ranges, theta, cols)
+    ref = (w[:, None] * s).T @ (w[:, None] * s)
+    scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+    assert np.all(np.abs(r["w2"] - ref) <= 1e-12 * scale)
+    # H and the per-event second derivatives
+    d2 = oracle.d2logpdf(kind, ranges, theta, [c[:50] for c in cols])
+    r50 = oracle.nll_hess(kind, ranges, [c[:50] for c in cols], theta, w=w[:50])
+    assert np.all(np.abs(r50["hess"] + np.einsum("i,iab->ab", w[:50], d2)) <= 1e-13 * r50["hscale"])
+    # weights enter H linearly and W quadratically; both symmetric
+    r2 = oracle.nll_hess(kind, ranges, cols, theta, w=2.0 * w)
+    assert np.array_equal(r2["hess"], 2.0 * r["hess"]) and np.array_equal(r2["w2"], 4.0 * r["w2"])
+    assert np.array_equal(r["hess"], r["hess"].T) and np.array_equal(r["w2"], r["w2"].T)
+    # the gradient returned with the Hessian is the one of nll_grad
+    _, g, _, _ = oracle.nll_grad(kind, ranges, cols, theta, w=w)
+    assert np.array_equal(r["grad"], g)
+
+
+@pytest.mark.parametrize("kind,n", [(M1, 200000), (M4, 100000)])
+def test_information_equality_at_the_truth(kind, n):
+    # For a sample drawn from the model at the true parameters, E[-d^2 ln P] = E[s s^T]
+    # (Bartlett's second identity), so H and W (w = 1) agree up to O(1/sqrt(n)) fluctuations.
+    cols = synth.mass1d(n, stream=96) if kind == M1 else synth.kstar4d(n, stream=97)
+    ranges, truth = (synth.RANGES_1D, synth.TRUTH_1D) if kind == M1 else (synth.RANGES_4D, synth.TRUTH_4D)
+    r = oracle.nll_hess(kind, ranges, cols, truth, nthreads=8)
+    H, W = r["hess"], r["w2"]
+    eH = np.sqrt(np.diag(np.linalg.inv(H)))
+    eW = np.sqrt(np.diag(np.linalg.inv(W)))
+    assert np.all(np.abs(eH / eW - 1.0) < 0.03), eH / eW
+    # off-diagonal structure too: correlations agree
+    cH = np.linalg.inv(H) / np.outer(eH, eH)
+    cW = np.linalg.inv(W) / np.outer(eW, eW)
+    assert np.max(np.abs(cH - cW)) < 0.03
