@@ -132,7 +132,8 @@ def nll_hess(kind, ranges, cols, theta, w=None, nthreads=1):
 
     ``hess`` is the Hessian of the NLL, ``w2`` = sum_i w_i^2 s_i s_i^T with s_i = d ln P_i/dtheta
     (the middle of the weighted-fit sandwich covariance), ``hscale[a, b]`` = sum_i
-    |w_i d^2 ln P_i / da db|, the size of the terms that make up hess[a, b]."""
+    |w_i| (|P_ab/P| + |P_a P_b/P^2|), the size of the two terms whose difference makes up
+    each event's share of hess[a, b] (it bounds this plain form's rounding error)."""
     L = lib()
     arrs, ptrs = _cols(cols)
     n = len(arrs[0])

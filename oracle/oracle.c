@@ -590,9 +590,12 @@ static void* hchunk_run(void* arg)
         for (int a = 0; a < np; ++a)
             for (int b = a; b < np; ++b) {
                 /* d^2 ln P / da db = P_ab / P - (P_a / P)(P_b / P) */
-                double t = wi * (d2P[a * np + b] / P - sc[a] * sc[b]);
+                double q = d2P[a * np + b] / P, pp = sc[a] * sc[b];
+                double t = wi * (q - pp);
                 kahan_add(&c->h[a * np + b], -t);
-                kahan_add(&c->hs[a * np + b], fabs(t));
+                /* the two terms cancel where one mixture component dominates the event, so
+                 * the rounding error of t is bounded by the size of the terms, not of t */
+                kahan_add(&c->hs[a * np + b], fabs(wi) * (fabs(q) + fabs(pp)));
                 kahan_add(&c->w2[a * np + b], wi * wi * sc[a] * sc[b]);
             }
     }
@@ -602,7 +605,9 @@ static void* hchunk_run(void* arg)
 /*
  * oracle_nll_hess: NLL, gradient, Hessian H of the NLL and W = sum_i w_i^2 s_i s_i^T
  * (s_i = d ln P_i / dtheta), all row-major npar x npar and symmetric, plus
- * hscale_ab = sum_i |w_i d^2 ln P_i / da db| (size of the terms that make up H_ab).
+ * hscale_ab = sum_i |w_i| (|P_ab / P| + |P_a P_b / P^2|)_i, the size of the two terms
+ * whose difference makes up each event's share of H_ab (their cancellation, where one
+ * mixture component dominates an event, is what limits this plain form's accuracy).
  * Arguments as oracle_nll_grad; grad, w2 and hscale may be NULL.  Status as there.
  */
 int oracle_nll_hess(int kind, const double* ranges, const double* const* cols, const double* w, int64_t n,

@@ -658,3 +658,24 @@ def test_information_equality_at_the_truth(kind, n):
     cH = np.linalg.inv(H) / np.outer(eH, eH)
     cW = np.linalg.inv(W) / np.outer(eW, eW)
     assert np.max(np.abs(cH - cW)) < 0.03
+
+
+def test_hessian_scale_bounds_the_plain_form_cancellation():
+    # two events deep in the background tail: the (fsig, alpha) entry is O(ps) while the two
+    # terms of the plain form are O(1); 40-digit differentiation shows the oracle's error
+    # stays within 1e-13 of the reported scale
+    cols = synth.mass1d(2, stream=302)
+    th = np.array([5283.0, 22.0, -0.0017, 0.35])
+    r = oracle.nll_hess(M1, synth.RANGES_1D, cols, th)
+    mp.mp.dps = 40
+    t0 = [mp.mpf(float(v)) for v in th]
+
+    def f2(x, y):
+        t = list(t0)
+        t[2], t[3] = x, y
+        return _mp_nll(M1, synth.RANGES_1D, cols, t)
+
+    ref = float(mp.diff(f2, (t0[2], t0[3]), (1, 1)))
+    err = abs(r["hess"][2, 3] - ref)
+    assert err > 1e-9 * abs(ref)  # the cancellation is real ...
+    assert err <= 1e-13 * r["hscale"][2, 3]  # ... and the scale accounts for it
