@@ -83,6 +83,7 @@ def parse():
     ap.add_argument("--study-toys", type=int, default=100, help="toys per size in the paper-style toy study (0 skips)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the mass-model event-count sweep")
     ap.add_argument("--no-calibration", action="store_true", help="skip the FP64 calibration kernels")
+    ap.add_argument("--no-hessian", action="store_true", help="skip the analytic-Hessian measurement")
     ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0],
                     help="Poisson arrival rates of served fits per second (one measurement each)")
     return ap.parse_args()
@@ -319,6 +320,74 @@ def mass_sweep(g, device, stream):
     return out
 
 
+def hessian_bench(g, model, theta, flush, stream, reps=5):
+    """Analytic Hessian (one pass) against the finite-difference Hessian of the analytic
+    gradient (2 n gradient passes) on the bench sample, and full fits using each."""
+    import torch
+
+    n = model.num_params
+    out = {}
+    for label, w2 in (("H", False), ("H+W", True)):
+        ms, kms = [], []
+        for i in range(reps + 2):
+            flush.zero_()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            model.eval_hess(theta, w2=w2)
+            s1.record(stream)
+            s1.synchronize()
+            if i >= 2:
+                ms.append(s0.elapsed_time(s1))
+                kms.append(g.nll_last_kernel_ms(model.handle))
+        out[label] = {"ms": statistics.median(ms), "kernel_ms": statistics.median(kms)}
+    # finite differences: 2 n gradient evaluations
+    ms = []
+    for i in range(reps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for k in range(n):
+            for sgn in (1.0, -1.0):
+                t = np.array(theta, dtype=np.float64)
+                t[k] += sgn * 1e-4 * max(abs(t[k]), 1e-2)
+                model.eval_grad(t)
+        s1.record(stream)
+        s1.synchronize()
+        ms.append(s0.elapsed_time(s1))
+    out["fd_2n_gradients"] = {"ms": statistics.median(ms)}
+    out["speedup_vs_fd"] = out["fd_2n_gradients"]["ms"] / out["H"]["ms"]
+    nslots = {"H": g.nll_hess_num_slots(model.kind, False, False), "H+W": g.nll_hess_num_slots(model.kind, False, True)}
+    for label in ("H", "H+W"):
+        k = out[label]["kernel_ms"]
+        fl = 2.0 * nslots[label] * N_EVENTS
+        out[label]["slots"] = nslots[label]
+        out[label]["slot_fma_tflops"] = fl / (k * 1e-3) / 1e12
+        out[label]["frac_of_fp64_peak"] = out[label]["slot_fma_tflops"] / FP64_PEAK_TFLOPS
+    out["roofline_note"] = ("slot FMAs only (2 flop x slots x events); the per-event staging "
+                            "(exp, log, divide, scores) is extra FP64 work not counted")
+    # fits of the bench sample: FD Hessian (strategy 1, hessian 1) vs analytic (2, 2)
+    lo, hi = np.zeros(n), np.zeros(n)
+    lo[-1], hi[-1] = 0.0, 1.0
+    step = np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    start = synth.TRUTH_4D + 0.5 * step
+    fits = {}
+    for label, st, hs in (("fd", 1, 1), ("analytic", 2, 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = model.fit(start, lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=st, hessian=hs)
+        t1 = time.perf_counter()
+        fits[label] = {"ms": 1e3 * (t1 - t0), "n_eval": int(r["n_eval"]), "n_iter": int(r["n_iter"]),
+                       "status": int(r["status"]), "edm": r["edm"]}
+        fits[label]["_theta"], fits[label]["_err"] = r["theta"], r["err"]
+    pull = np.max(np.abs((fits["analytic"]["_theta"] - fits["fd"]["_theta"]) / fits["fd"]["_err"]))
+    err_rel = np.max(np.abs(fits["analytic"]["_err"] / fits["fd"]["_err"] - 1.0))
+    for v in fits.values():
+        v.pop("_theta")
+        v.pop("_err")
+    out["fit_1e6"] = {**fits, "max_pull_between": float(pull), "max_rel_err_diff": float(err_rel)}
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -444,6 +513,8 @@ def run_ours(args):
                     "dfma_per_s": rates["dfma"], "cuda_exp_slots": rates["dfma"] / rates["cuda_exp"],
                     "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}
 
+    hess = None if args.no_hessian else hessian_bench(g, model, th[0], flush, stream)
+
     toys = None
     if args.toys > 0:
         toys = toy_fits(g, local, args.toys, args.seq_toys, seed_stream=rank)
@@ -471,7 +542,7 @@ def run_ours(args):
                         "h2d_bytes_per_step": 4 * 8 * N_EVENTS, "d2h_bytes_per_step": 8 * (k_acc + 3),
                         "ms_per_step": e2e_step, "variant": "direct (one evaluation per copied sample)"},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
-                "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
+                "hessian": hess, "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
                 "mass_model_sweep": sweep}
         print(json.dumps(line), flush=True)
     model.close()

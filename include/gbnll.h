@@ -114,9 +114,14 @@ int nll_eval_grad(nll_model* m, const double* theta, int n_params, double* nll_o
 typedef struct {
     double tol_edm; /* stop when EDM = g^T V g / 2 < tol_edm (e.g. 1e-8; <= 0 -> 1e-8)       */
     int max_iter;   /* quasi-Newton iterations (<= 0 -> 500)                                  */
-    int strategy;   /* 0: start from diag(step^2); 1: start from a finite-difference Hessian  */
+    int strategy;   /* 0: start from diag(step^2); 1: start from a finite-difference Hessian;
+                       2: start from the analytic Hessian (nll_eval_hess)                      */
     int hessian;    /* 0: covariance from the quasi-Newton matrix; 1: finite-difference
-                       Hessian of the analytic gradient at the minimum plus Newton polish     */
+                       Hessian of the analytic gradient at the minimum plus Newton polish;
+                       2: the same with the analytic Hessian, covariance H^-1;
+                       3: as 2, covariance H^-1 W H^-1 (weighted fits, see nll_eval_hess).
+                       Values 2 and 3 (and strategy 2) need a model: fit_minimise_fcn and the
+                       batched fits reject them with NLL_ERR_ARG.                              */
 } fit_options;
 
 #define FIT_MAXPAR 32
@@ -149,6 +154,28 @@ typedef int (*fit_fcn)(void* user, const double* theta, double* nll_out, double*
 int fit_minimise_fcn(fit_fcn fcn, void* user, const double* theta0, const double* lo, const double* hi,
                      const double* step, const int* fixed, int n_params, const fit_options* opt,
                      fit_result* out);
+
+/*
+ * nll_eval_hess -- NLL, gradient and the analytic Hessian of the NLL in one device pass
+ * (paper Sec. 2.1: analytic Hessian for the HESSE uncertainties; Fisher information for
+ * weighted fits), plus optionally the squared-weight score matrix
+ *     W_ab = sum_i w_i^2 (d ln P_i / d theta_a)(d ln P_i / d theta_b),
+ * so that H^-1 W H^-1 is the asymptotic covariance of a weighted fit (Langenbruch,
+ * Eur. Phys. J. C 82 (2022) 393).
+ *   theta     host array of n_params (0 < fsig < 1, as nll_eval_grad)
+ *   nll_out   host scalar; grad_out host n_params or NULL
+ *   hess_out  host n_params x n_params, row-major, symmetric: d^2 NLL / dtheta_a dtheta_b
+ *   w2_out    host n_params x n_params or NULL (W; equals the Hessian's expectation for w = 1)
+ * Deterministic for a given device.  Status as nll_eval_grad (NLL_ERR_NONPOSITIVE_PDF fills
+ * the outputs with +inf / NaN).  Its cost is a few gradient evaluations (one FMA per event
+ * per matrix entry), against 2 n_params of them for a finite-difference Hessian.
+ */
+int nll_eval_hess(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out,
+                  double* hess_out, double* w2_out);
+
+/* Slots of the Hessian pass: per-event products it sums (one FP64 FMA per event each) for
+ * model `kind`, with or without weights and W.  -1 for an unknown kind.  No GPU needed. */
+int nll_hess_num_slots(int kind, int weighted, int want_w2);
 
 /* Number of parameters of the model (4 or 18) and the name of parameter i. */
 int nll_num_params(const nll_model* m);

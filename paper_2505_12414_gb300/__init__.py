@@ -75,6 +75,8 @@ def load(path=None):
     L.nll_load_events.argtypes = [vp, ctypes.POINTER(vp), vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
     L.nll_eval.argtypes = [vp, _DP, ctypes.c_int, _DP]
     L.nll_eval_grad.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP]
+    L.nll_eval_hess.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, _DP]
+    L.nll_hess_num_slots.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.fit_minimise.argtypes = [vp, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                ctypes.POINTER(fit_options), ctypes.POINTER(fit_result)]
     L.fit_minimise_fcn.argtypes = [FIT_FCN, vp, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -224,6 +226,30 @@ def nll_eval_grad(model, theta, check=True):
         return out.value, g, st
     _check(model, st)
     return out.value, g
+
+
+def nll_eval_hess(model, theta, w2=False, check=True):
+    """(NLL, gradient, Hessian[, W]) at theta from one device pass.  W = sum w^2 s s^T is
+    returned when w2 is true (the middle of the weighted-fit covariance H^-1 W H^-1).
+    With check=False the status is appended instead of raising."""
+    L = load()
+    th = _f64(theta)
+    n = len(th)
+    out = ctypes.c_double()
+    g = np.zeros(n)
+    H = np.zeros((n, n))
+    W = np.zeros((n, n)) if w2 else None
+    st = L.nll_eval_hess(model, _p(th), n, ctypes.byref(out), _p(g), _p(H), _p(W) if w2 else None)
+    res = (out.value, g, H) + ((W,) if w2 else ())
+    if not check:
+        return res + (st,)
+    _check(model, st)
+    return res
+
+
+def nll_hess_num_slots(kind, weighted=False, w2=False):
+    """Per-event FMA slots of the Hessian pass (its FP64 cost per event, besides staging)."""
+    return load().nll_hess_num_slots(int(kind), 1 if weighted else 0, 1 if w2 else 0)
 
 
 def _fit_args(theta0, lo, hi, step, fixed):
@@ -443,6 +469,10 @@ class Model:
         st = load().nll_eval_grad(self.handle, self._thp, self._n, self._outp, self._gp)
         _check(self.handle, st)
         return self._out.value, self._g.copy()
+
+    def eval_hess(self, theta, w2=False):
+        """(NLL, gradient, Hessian[, W]); see nll_eval_hess."""
+        return nll_eval_hess(self.handle, theta, w2)
 
     def fit(self, theta0, **kw):
         return fit_minimise(self.handle, theta0, **kw)

@@ -1341,6 +1341,8 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         memset(&opt, 0, sizeof opt);
     if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
     if (opt.max_iter <= 0) opt.max_iter = 500;
+    if (opt.strategy < 0 || opt.strategy > 1 || opt.hessian < 0 || opt.hessian > 1)
+        return bfail(b, NLL_ERR_ARG, "batched fits take strategy 0/1 and hessian 0/1 (finite-difference Hessian)");
     const int n = b->n_toys, np = b->npar;
     if (n == 0) return NLL_OK;
     BatchDev d = make_dev(b);
@@ -1544,6 +1546,8 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
 {
     if (!out) return NLL_ERR_ARG;
     *out = nullptr;
+    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 1 || opt_in->hessian < 0 || opt_in->hessian > 1))
+        return NLL_ERR_ARG;  // the device-resident minimiser has the finite-difference Hessian only
     if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges || max_slots < 1 ||
         pool_events < 1 || tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
         return NLL_ERR_ARG;

@@ -92,9 +92,11 @@ struct BArgs {  // basis precompute
 struct Hoist {
     KConst k;
     double mu, sigma, alpha, f, ma;
-    double b0, b2;
+    double b0, b2, lnb1;
     double dlnN1_dmu, dlnN1_dsig, dlnN2t_dal;
     double dlnNc_dc2[3];
+    double d2lnN1[3];     // d^2 ln N1 / (dmu dmu, dmu dsigma, dsigma dsigma)
+    double d2lnN2t_dal2;  // d^2 ln Ntilde2 / dalpha^2 (= variance of m under exp(alpha m))
 };
 int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hoist& H, std::string* err);
 void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, double* nll_out, double* grad_out);
@@ -116,6 +118,46 @@ int gen_toys(int kind, const double* ranges, const double* theta, const int64_t*
 // per-toy sum of (m - ma) over [begin, end) (device arrays), fixed order
 cudaError_t toy_sums(const double* m, const int64_t* d_begin, const int64_t* d_end, double ma, int n_toys,
                      double* d_out, cudaStream_t stream);
+
+// Analytic Hessian (hess.cu).  One kernel stages per-event columns (scores and the few
+// products the second derivatives need) in shared memory and sums column products
+// ("slots") over events; the host assembles NLL, gradient, Hessian and W = sum w^2 s s^T
+// from the slot sums and the parameter-only terms.
+constexpr int kHessThreads = 128;   // threads per block = events per shared-memory tile
+constexpr int kHessMaxSlots = 384;  // at most 3 slots per thread
+constexpr int kHessMaxBlocksPerSm = 4;
+
+struct HConst {
+    double mu, b0, alpha, k0u, b2, inv_sigma;
+    double dlnN1_dmu, dlnN1_dsig, mu_ma, dlnN2t_dal, inv_f, inv_1mf;
+    double ang[8];
+    double c1[3], c2[3], dl[3];  // Chebyshev coefficients and d ln Nc_j / d c2_j
+};
+
+struct HArgs {
+    const double* col[kNumCols];
+    const double* w;
+    int64_t n;
+    HConst c;
+    int nslots;
+    double* partials;      // [kHessMaxSlots][blocks]
+    unsigned int* ticket;  // grid-completion counter, 0 between launches
+    double* out;           // [nslots]
+    uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];  // column pair of each slot
+};
+
+struct HessLayout {
+    int nslots = 0, ncols = 0;
+    uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];
+};
+// Slot table for (kind, weighted, with W); returns false if it does not fit.
+bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L);
+void hess_fill_const(int kind, const Hoist& H, const double* theta, HConst* c);
+// Assemble from the slot sums; returns the count of events with a non-positive density.
+double hess_assemble(int kind, bool weighted, bool want_w2, const Hoist& H, double sum_wdm, const HessLayout& L,
+                     const double* sums, double* nll, double* grad, double* hess, double* w2);
+cudaError_t launch_hess(int kind, int variant, bool weighted, int blocks, cudaStream_t stream, const HArgs& a);
+int hess_occupancy(int kind, int variant, bool weighted);  // resident blocks per SM
 
 // Static device scratch of nll_eval_grad_4d_noalloc (kernels.cu).
 constexpr int kNoAllocMaxBlocks = 1024;

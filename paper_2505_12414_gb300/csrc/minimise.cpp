@@ -13,7 +13,10 @@
 //     external = lo + (hi - lo) (sin(internal) + 1) / 2;
 //   * convergence on the estimated distance to minimum EDM = g^T V g / 2;
 //   * optionally a finite-difference Hessian of the analytic gradient at the minimum,
-//     Newton polish steps with it, and the covariance as its inverse.
+//     Newton polish steps with it, and the covariance as its inverse;
+//   * or, where the objective supplies them, the analytic Hessian (for the start matrix,
+//     the polish and the covariance) and the weighted-fit sandwich covariance
+//     H^-1 W H^-1, W = sum w^2 s s^T (paper Sec. 2.1 asks for both).
 #include "minimise.h"
 
 #include <math.h>
@@ -164,7 +167,8 @@ bool fd_hessian(int n, const std::vector<double>& h, G grad_at, std::vector<doub
 }  // namespace
 
 int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double* lo, const double* hi,
-                  const double* step, const int* fixed, const fit_options* opt_in, fit_result* out)
+                  const double* step, const int* fixed, const fit_options* opt_in, fit_result* out,
+                  const HessianFn* hess)
 {
     fit_options opt;
     if (opt_in)
@@ -174,7 +178,8 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
     if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
     if (opt.max_iter <= 0) opt.max_iter = 500;
     memset(out, 0, sizeof(*out));
-    if (n <= 0 || n > FIT_MAXPAR || !theta0) {
+    if (n <= 0 || n > FIT_MAXPAR || !theta0 || opt.strategy < 0 || opt.strategy > 2 || opt.hessian < 0 ||
+        opt.hessian > 3 || ((opt.strategy == 2 || opt.hessian >= 2) && !hess)) {
         out->status = NLL_ERR_ARG;
         return NLL_ERR_ARG;
     }
@@ -235,8 +240,41 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
         std::fill(V.begin(), V.end(), 0.0);
         for (int i = 0; i < nf; ++i) V[i * nf + i] = sint[i] * sint[i];
     };
+    // analytic second derivatives of the free parameters at external point th_free
+    auto analytic_at = [&](const std::vector<double>& th_free, std::vector<double>& Hf,
+                           std::vector<double>* Wf) -> bool {
+        std::vector<double> th = P.base, Hn((size_t)n * n), Wn;
+        for (int i = 0; i < nf; ++i) th[P.idx[i]] = th_free[i];
+        if (Wf) Wn.resize((size_t)n * n);
+        ++P.n_eval;
+        if ((*hess)(th.data(), Hn.data(), Wf ? Wn.data() : nullptr) != NLL_OK) return false;
+        Hf.resize((size_t)nf * nf);
+        if (Wf) Wf->resize((size_t)nf * nf);
+        for (int i = 0; i < nf; ++i)
+            for (int j = 0; j < nf; ++j) {
+                Hf[i * nf + j] = Hn[(size_t)P.idx[i] * n + P.idx[j]];
+                if (Wf) (*Wf)[i * nf + j] = Wn[(size_t)P.idx[i] * n + P.idx[j]];
+                if (!isfinite(Hf[i * nf + j])) return false;
+            }
+        return true;
+    };
     diag_init();
-    if (opt.strategy >= 1) {
+    if (opt.strategy == 2) {
+        // analytic Hessian in internal coordinates: J H J + diag(dF/dext d2ext/dx2)
+        std::vector<double> th_free(nf), He;
+        for (int i = 0; i < nf; ++i) th_free[i] = P.to_ext(i, x[i]);
+        if (analytic_at(th_free, He, nullptr)) {
+            std::vector<double> Hi((size_t)nf * nf), Vi((size_t)nf * nf);
+            for (int i = 0; i < nf; ++i) {
+                const double Ji = P.jac(i, x[i]);
+                for (int j = 0; j < nf; ++j) Hi[i * nf + j] = Ji * He[i * nf + j] * P.jac(j, x[j]);
+                const int k = P.idx[i];
+                if (P.bounded[k] && fabs(Ji) > 1e-300)
+                    Hi[i * nf + i] += (g[i] / Ji) * (-(P.hi[k] - P.lo[k]) * 0.5 * sin(x[i]));
+            }
+            if (spd_inverse(nf, Hi.data(), Vi.data())) V = Vi;
+        }
+    } else if (opt.strategy >= 1) {
         std::vector<double> h(nf), H;
         for (int i = 0; i < nf; ++i) h[i] = 0.1 * sint[i];
         auto gat = [&](int k, double dh, std::vector<double>& gg) {
@@ -370,7 +408,7 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
                     double ff;
                     return P.eval_ext(t, ff, gg) == NLL_OK;
                 };
-                if (!fd_hessian(nf, h, gat, H)) break;
+                if (opt.hessian >= 2 ? !analytic_at(th_free, H, nullptr) : !fd_hessian(nf, h, gat, H)) break;
                 std::vector<double> Hi((size_t)nf * nf);
                 if (!spd_inverse(nf, H.data(), Hi.data())) break;
                 C = Hi;
@@ -406,7 +444,32 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
                 if (!took) break;
                 for (int i = 0; i < nf; ++i) h[i] = 1e-3 * sqrt(std::max(C[i * nf + i], 1e-300));
             }
-            if (!converged) {
+            if (opt.hessian >= 2) {
+                // covariance at the final point: H^-1, or H^-1 W H^-1 for weighted fits
+                std::vector<double> Wf, Hi((size_t)nf * nf);
+                if (analytic_at(th_free, H, opt.hessian == 3 ? &Wf : nullptr) && spd_inverse(nf, H.data(), Hi.data())) {
+                    if (opt.hessian == 3) {
+                        std::vector<double> T((size_t)nf * nf, 0.0);
+                        for (int i = 0; i < nf; ++i)
+                            for (int k = 0; k < nf; ++k)
+                                for (int j = 0; j < nf; ++j) T[i * nf + j] += Hi[i * nf + k] * Wf[k * nf + j];
+                        for (int i = 0; i < nf; ++i)
+                            for (int j = 0; j < nf; ++j) {
+                                double sacc = 0.0;
+                                for (int k = 0; k < nf; ++k) sacc += T[i * nf + k] * Hi[k * nf + j];
+                                C[i * nf + j] = sacc;
+                            }
+                    } else {
+                        C = Hi;
+                    }
+                    std::vector<double> d;
+                    matvec(nf, Hi, ge, d);
+                    edm = 0.5 * dot(ge, d);
+                    converged = edm < opt.tol_edm;
+                } else {
+                    converged = false;
+                }
+            } else if (!converged) {
                 std::vector<double> d;
                 matvec(nf, C, ge, d);
                 edm = 0.5 * dot(ge, d);
@@ -437,6 +500,11 @@ extern "C" int fit_minimise_fcn(fit_fcn fcn, void* user, const double* theta0, c
                                 fit_result* out)
 {
     if (!fcn || !out) return NLL_ERR_ARG;
+    if (opt && (opt->strategy == 2 || opt->hessian >= 2)) {  // needs second derivatives it cannot get
+        memset(out, 0, sizeof(*out));
+        out->status = NLL_ERR_ARG;
+        return NLL_ERR_ARG;
+    }
     gbnll::Objective obj = [&](const double* th, double* f, double* g) {
         return fcn(user, th, f, g) == 0 ? (int)NLL_OK : (int)NLL_ERR_ARG;
     };

@@ -11,8 +11,14 @@ namespace gbnll {
 // nll_status (NLL_OK on success; any other value rejects the point).
 using Objective = std::function<int(const double* theta, double* f, double* g)>;
 
+// Analytic second derivatives at theta (full external parameter vector): H (n x n,
+// row-major) and, when W is not null, the squared-weight score matrix; returns an nll_status.
+using HessianFn = std::function<int(const double* theta, double* H, double* W)>;
+
+// strategy 2 and hessian 2/3 of fit_options need `hess`; without it they are rejected.
 int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double* lo, const double* hi,
-                  const double* step, const int* fixed, const fit_options* opt, fit_result* out);
+                  const double* step, const int* fixed, const fit_options* opt, fit_result* out,
+                  const HessianFn* hess = nullptr);
 
 // Dense symmetric positive-definite inverse by Cholesky; false if not positive definite.
 bool spd_inverse(int n, const double* a, double* inv);

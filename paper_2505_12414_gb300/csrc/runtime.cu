@@ -86,6 +86,13 @@ struct nll_model {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     double last_ms = -1.0;
 
+    // analytic Hessian scratch (allocated at the first nll_eval_hess)
+    double* d_hpart = nullptr;          // [kHessMaxSlots][hess_max_blocks]
+    unsigned int* d_hticket = nullptr;
+    double* h_hout = nullptr;           // mapped pinned [kHessMaxSlots]
+    double* d_hout = nullptr;
+    int hess_max_blocks = 0;
+
     // last valid constant block (for autotuning)
     bool have_last = false;
     Hoist last;
@@ -181,8 +188,46 @@ int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hois
         else
             H.dlnN2t_dal = D * (0.5 + t / 12.0 - t * t * t / 720.0 + t * t * t * t * t / 30240.0);
     }
+    // second derivatives (analytic Hessian): d2 ln N1 = N1''/N1 - (N1'/N1)^2 with
+    //   N1''_mumu = -(za ea - zb eb) / (sqrt(pi) sigma^2),
+    //   N1''_musigma = (ea (2 za^2 - 1) - eb (2 zb^2 - 1)) / (sqrt(2 pi) sigma^2),
+    //   N1''_sigmasigma = 2 (za ea (1 - za^2) - zb eb (1 - zb^2)) / (sqrt(pi) sigma^2)
+    {
+        const double s2 = sigma * sigma;
+        H.d2lnN1[0] = -(za * ea - zb * eb) / (sqrt(kPi) * s2 * N1) - H.dlnN1_dmu * H.dlnN1_dmu;
+        H.d2lnN1[1] = (ea * (2.0 * za * za - 1.0) - eb * (2.0 * zb * zb - 1.0)) / (sqrt(2.0 * kPi) * s2 * N1) -
+                      H.dlnN1_dmu * H.dlnN1_dsig;
+        H.d2lnN1[2] = 2.0 * (za * ea * (1.0 - za * za) - zb * eb * (1.0 - zb * zb)) / (sqrt(kPi) * s2 * N1) -
+                      H.dlnN1_dsig * H.dlnN1_dsig;
+    }
+    // d^2 ln Ntilde2 / d alpha^2 = D^2 v(|t|), v(a) = 1/a^2 - e^-a / (1 - e^-a)^2: the variance of
+    // (m - ma)/D under exp(t (m - ma)/D).  Below |t| = 1/2, its power series from the expansion
+    // of coth, v = sum_n (2n-1) B_2n a^(2n-2) / (2n)!, through a^16.
+    {
+        const double a = fabs(t);
+        double v;
+        if (a < 0.5) {
+            static const double c[9] = {1.0 / 12.0,
+                                        -1.0 / 240.0,
+                                        1.0 / 6048.0,
+                                        -1.0 / 172800.0,
+                                        9.0 * (5.0 / 66.0) / 3628800.0,
+                                        11.0 * (-691.0 / 2730.0) / 479001600.0,
+                                        13.0 * (7.0 / 6.0) / 87178291200.0,
+                                        15.0 * (-3617.0 / 510.0) / 20922789888000.0,
+                                        17.0 * (43867.0 / 798.0) / 6402373705728000.0};
+            const double a2 = a * a;
+            v = c[8];
+            for (int k = 7; k >= 0; --k) v = fma(v, a2, c[k]);
+        } else {
+            const double em = expm1(-a);
+            v = 1.0 / (a * a) - exp(-a) / (em * em);
+        }
+        H.d2lnN2t_dal2 = D * D * v;
+    }
     double b0 = 1.0 / (2.0 * sigma * sigma);
     double lnb1 = (f > 0.0) ? log(f) - 0.5 * log(2.0 * kPi) - log(sigma) - log(N1) : -INFINITY;
+    H.lnb1 = lnb1;
     double b2 = (1.0 - f) / Nt2;
     if (kind == kKstar4D) {
         for (int j = 0; j < 3; ++j) {
@@ -350,6 +395,98 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
     return NLL_OK;
 }
 
+int ensure_hess_scratch(nll_model* m)
+{
+    if (m->d_hpart) return NLL_OK;
+    m->hess_max_blocks = m->sm_count * kHessMaxBlocksPerSm;
+    cudaError_t e = cudaMalloc(&m->d_hpart, sizeof(double) * kHessMaxSlots * (size_t)m->hess_max_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_hticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(m->d_hticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaHostAlloc(&m->h_hout, sizeof(double) * kHessMaxSlots, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_hout, m->h_hout, 0);
+    if (e != cudaSuccess) {
+        if (m->d_hpart) cudaFree(m->d_hpart);
+        if (m->d_hticket) cudaFree(m->d_hticket);
+        if (m->h_hout) cudaFreeHost(m->h_hout);
+        m->d_hpart = m->h_hout = m->d_hout = nullptr;
+        m->d_hticket = nullptr;
+        return cuda_fail(m, e, "Hessian scratch");
+    }
+    return NLL_OK;
+}
+
+int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out, double* hess_out,
+              double* w2_out)
+{
+    if (!m) return NLL_ERR_ARG;
+    if (!theta || !nll_out || !hess_out) return fail(m, NLL_ERR_ARG, "null theta or output");
+    if (n_params != m->npar) return fail(m, NLL_ERR_ARG, "expected %d parameters, got %d", m->npar, n_params);
+    if (!m->loaded) return fail(m, NLL_ERR_STATE, "no events loaded");
+    Hoist H;
+    int st = hoist(m, theta, true, H);
+    if (st != NLL_OK) return st;
+    const bool want_w2 = w2_out != nullptr;
+    HessLayout L;
+    if (!hess_layout(m->kind, m->weighted, want_w2, &L)) return fail(m, NLL_ERR_ARG, "Hessian slot table overflow");
+    double sums[kHessMaxSlots];
+    for (int k = 0; k < kHessMaxSlots; ++k) sums[k] = 0.0;
+    if (m->n > 0) {
+        int var = effective_variant(m);
+        if (var < 0) return fail(m, NLL_ERR_STATE, "precompute variant requested but no basis was built");
+        if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
+        st = ensure_hess_scratch(m);
+        if (st != NLL_OK) return st;
+        static_assert(sizeof(HArgs) <= 4096, "kernel parameters");
+        HArgs a;
+        memset(&a, 0, sizeof a);
+        for (int c = 0; c < kNumCols; ++c) a.col[c] = c < m->ncols ? colptr(m, c) : nullptr;
+        a.w = m->weighted ? m->d_w : nullptr;
+        a.n = m->n;
+        hess_fill_const(m->kind, H, theta, &a.c);
+        a.nslots = L.nslots;
+        a.partials = m->d_hpart;
+        a.ticket = m->d_hticket;
+        a.out = m->d_hout;
+        memcpy(a.si, L.si, sizeof a.si);
+        memcpy(a.sj, L.sj, sizeof a.sj);
+        int occ = std::min(std::max(hess_occupancy(m->kind, var, m->weighted), 1), kHessMaxBlocksPerSm);
+        const int64_t ntiles = (m->n + kHessThreads - 1) / kHessThreads;
+        int blocks = (int)std::min<int64_t>(ntiles, (int64_t)m->sm_count * occ);
+        blocks = std::min(blocks, m->hess_max_blocks);
+        if (m->profiling) cudaEventRecord(m->ev0, m->stream);
+        cudaError_t e = launch_hess(m->kind, var, m->weighted, blocks, m->stream, a);
+        if (e != cudaSuccess) return cuda_fail(m, e, "Hessian kernel launch");
+        if (m->profiling) cudaEventRecord(m->ev1, m->stream);
+        e = cudaStreamSynchronize(m->stream);
+        if (e != cudaSuccess) return cuda_fail(m, e, "Hessian evaluation");
+        if (m->profiling) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, m->ev0, m->ev1) == cudaSuccess) m->last_ms = ms;
+        }
+        memcpy(sums, m->h_hout, sizeof(double) * L.nslots);
+    }
+    const int np = m->npar;
+    double nll, grad[18], Hm[18 * 18], Wm[18 * 18];
+    double bad = hess_assemble(m->kind, m->weighted, want_w2, H, m->sum_wdm, L, sums, &nll, grad, Hm, Wm);
+    if (bad != bad) return fail(m, NLL_ERR_ARG, "Hessian slot table incomplete");
+    if (bad != 0.0 || !isfinite(nll)) {
+        *nll_out = INFINITY;
+        for (int k = 0; k < np; ++k) {
+            if (grad_out) grad_out[k] = NAN;
+            for (int j = 0; j < np; ++j) {
+                hess_out[k * np + j] = NAN;
+                if (w2_out) w2_out[k * np + j] = NAN;
+            }
+        }
+        return fail(m, NLL_ERR_NONPOSITIVE_PDF, "density not positive for %.0f event(s)", bad);
+    }
+    *nll_out = nll;
+    if (grad_out) memcpy(grad_out, grad, sizeof(double) * np);
+    memcpy(hess_out, Hm, sizeof(double) * np * np);
+    if (w2_out) memcpy(w2_out, Wm, sizeof(double) * np * np);
+    return NLL_OK;
+}
+
 // forget the sample; the allocation is kept for reuse unless `release`
 void reset_events(nll_model* m, bool release)
 {
@@ -463,6 +600,9 @@ void nll_destroy(nll_model* m)
     if (m->d_partials) cudaFree(m->d_partials);
     if (m->d_ticket) cudaFree(m->d_ticket);
     if (m->h_out) cudaFreeHost(m->h_out);  // d_out is its device alias
+    if (m->d_hpart) cudaFree(m->d_hpart);
+    if (m->d_hticket) cudaFree(m->d_hticket);
+    if (m->h_hout) cudaFreeHost(m->h_hout);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);
@@ -574,7 +714,24 @@ int fit_minimise(nll_model* m, const double* theta0, const double* lo, const dou
     Objective obj = [m, n_params](const double* th, double* f, double* g) {
         return nll_eval_grad(m, th, n_params, f, g);
     };
-    return bfgs_minimise(obj, n_params, theta0, lo, hi, step, fixed, opt, out);
+    HessianFn hs = [m, n_params](const double* th, double* H, double* W) {
+        double f, g[18];
+        return nll_eval_hess(m, th, n_params, &f, g, H, W);
+    };
+    return bfgs_minimise(obj, n_params, theta0, lo, hi, step, fixed, opt, out, &hs);
+}
+
+int nll_eval_hess(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out,
+                  double* hess_out, double* w2_out)
+{
+    return hess_impl(m, theta, n_params, nll_out, grad_out, hess_out, w2_out);
+}
+
+int nll_hess_num_slots(int kind, int weighted, int want_w2)
+{
+    if (kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) return -1;
+    HessLayout L;
+    return hess_layout(kind, weighted != 0, want_w2 != 0, &L) ? L.nslots : -1;
 }
 
 int nll_num_params(const nll_model* m) { return m ? m->npar : -1; }

@@ -60,3 +60,17 @@ def test_null_and_bad_arguments_are_rejected_without_a_gpu(lib):
     bad = (ctypes.c_double * 2)(5970.0, 5170.0)
     assert lib.nll_create_model(1, bad, 0, 0, ctypes.byref(h)) == 1
     assert h.value is None
+
+
+def test_hessian_slot_counts_without_a_gpu(lib):
+    lib.nll_hess_num_slots.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    assert lib.nll_hess_num_slots(3, 0, 0) == -1
+    for kind, npar in ((1, 4), (2, 18)):
+        for weighted in (0, 1):
+            h = lib.nll_hess_num_slots(kind, weighted, 0)
+            hw = lib.nll_hess_num_slots(kind, weighted, 1)
+            # at least one slot per Hessian entry; W adds its npar (npar + 1) / 2 products, some
+            # of which the unweighted Hessian already holds
+            assert npar * (npar + 1) // 2 <= h < hw <= 384
+            if weighted:
+                assert hw - h == npar * (npar + 1) // 2

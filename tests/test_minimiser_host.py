@@ -105,3 +105,13 @@ def test_oracle_likelihood_minimum_matches_oracle_newton(g, kind):
     pull = (r["theta"] - ref["theta"]) / ref["err"]
     assert np.max(np.abs(pull)) < 1e-6, pull
     np.testing.assert_allclose(r["err"], ref["err"], rtol=1e-3)
+
+
+def test_analytic_hessian_options_need_a_model(g):
+    # strategy 2 and hessian 2/3 take second derivatives from a model; a host callback has none
+    def f(x):
+        return float(np.sum(x ** 2)), 2.0 * x
+
+    for strategy, hessian in ((2, 0), (0, 2), (1, 3)):
+        r = g.fit_minimise_fcn(f, [1.0, 2.0], strategy=strategy, hessian=hessian)
+        assert r["status"] == g.NLL_ERR_ARG
