@@ -128,7 +128,7 @@ constexpr int kHessMaxSlots = 384;  // at most 3 slots per thread
 constexpr int kHessMaxBlocksPerSm = 4;
 
 struct HConst {
-    double mu, b0, alpha, k0u, b2, inv_sigma;
+    double mu, b0, neg_b0s, neg_als, k0s, b2, inv_sigma;  // *s: times the exponential's scale
     double dlnN1_dmu, dlnN1_dsig, mu_ma, dlnN2t_dal, inv_f, inv_1mf;
     double ang[8];
     double c1[3], c2[3], dl[3];  // Chebyshev coefficients and d ln Nc_j / d c2_j
@@ -140,14 +140,14 @@ struct HArgs {
     int64_t n;
     HConst c;
     int nslots;
-    double* partials;      // [kHessMaxSlots][blocks]
-    unsigned int* ticket;  // grid-completion counter, 0 between launches
+    int lnp_slot;          // unweighted: slot that receives the block's sum of ln P (else -1)
+    double* partials;      // [kHessMaxSlots][blocks], reduced by a second launch
     double* out;           // [nslots]
     uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];  // column pair of each slot
 };
 
 struct HessLayout {
-    int nslots = 0, ncols = 0;
+    int nslots = 0, ncols = 0, lnp_slot = -1;
     uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];
 };
 // Slot table for (kind, weighted, with W); returns false if it does not fit.

@@ -29,16 +29,28 @@
 //     and sums their products over the tile; thread l starts at event l and wraps, so a
 //     half-warp's 64-bit reads fall in 16 different bank pairs whatever the columns;
 //   * the grid is persistent (blocks take tiles b, b + B, ...); per-block slot sums go to
-//     scratch and the last block to finish reduces them in block order (deterministic).
+//     scratch and a second launch reduces them, one block per slot, in a fixed order
+//     (deterministic, and spread over all SMs instead of one last block);
+//   * a warp runs only as many slot rows as its lanes own (195 slots: 7 warp rows, not 8);
+//   * unweighted, sum ln P is the logarithm of a running product per thread (one log per
+//     thread, as in the fused kernel), added to its slot after the tiles;
+//   * the staging uses the library's table-driven exponential and its reciprocal
+//     (fp64_math.cuh), as the fused kernel does.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
+#include <vector>
+
+#include "fp64_math.cuh"
 #include "gbnll_internal.h"
 #include "nll_device.cuh"
 
 namespace gbnll {
+
+__device__ double g_htab[kExpTable];  // 2^(j/N) for fexp_scaled, uploaded once per device
 
 // Column layout of the staged tile.  Without weights the weighted scores are the scores.
 template <int KIND, bool W>
@@ -65,7 +77,8 @@ struct HCols {
 // Device: staging of one event
 // ------------------------------------------------------------------------------------
 template <int KIND, int VAR, bool W>
-__device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z, int t)
+__device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z, int t, const double* tab,
+                                            LogProd& lp)
 {
     using L = HCols<KIND, W>;
     const HConst& c = a.c;
@@ -75,14 +88,15 @@ __device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z
     const double m = in ? __ldg(a.col[kColM] + ei) : c.mu;
     const double w = W ? (in ? __ldg(a.w + ei) : 0.0) : 1.0;
     const double d = m - c.mu;
-    const double E = exp(fma(d, fma(-c.b0, d, -c.alpha), c.k0u));  // f G e^{-alpha (m - ma)}
+    // f G e^{-alpha (m - ma)}; the constants carry the exponential's argument scale
+    const double E = fexp_scaled(fma(d, fma(c.neg_b0s, d, c.neg_als), c.k0s), tab);
     const double phmu = fma(2.0 * c.b0, d, -c.dlnN1_dmu);
     const double phsig = fma(fma(2.0 * c.b0 * d, d, -1.0), c.inv_sigma, -c.dlnN1_dsig);
     const double phal = d + c.mu_ma - c.dlnN2t_dal;
     double P, ps, pb, r;
     if (KIND == kMass1D) {
         P = E + c.b2;
-        r = 1.0 / P;
+        r = frcp(P);
         ps = E * r;
         pb = c.b2 * r;
         put(L::S + 0, ps * phmu);
@@ -118,7 +132,7 @@ __device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z
         const double O[3] = {Cb[1] * Cb[2], Cb[0] * Cb[2], Cb[0] * Cb[1]};  // the other two factors
         const double sig = A * E, bg = c.b2 * (O[2] * Cb[2]);
         P = sig + bg;
-        r = 1.0 / P;
+        r = frcp(P);
         ps = sig * r;
         pb = bg * r;
         const double rE = r * E, Q = r * c.b2;
@@ -140,11 +154,11 @@ __device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z
         for (int q3 = 0; q3 < 3; ++q3) {
             const int j = jj[q3], k = kk[q3];
             const double QC = Q * Cb[ll[q3]];
-            const double nj[2] = {x[j], nu2[j]}, nk[2] = {x[k], nu2[k]};
+            const double qn[2] = {QC * x[j], QC * nu2[j]}, nk[2] = {x[k], nu2[k]};
 #pragma unroll
             for (int p = 0; p < 2; ++p)
 #pragma unroll
-                for (int q = 0; q < 2; ++q) put(L::CROSS + 4 * q3 + 2 * p + q, QC * nj[p] * nk[q]);
+                for (int q = 0; q < 2; ++q) put(L::CROSS + 4 * q3 + 2 * p + q, qn[p] * nk[q]);
         }
     }
     if (W) {
@@ -161,8 +175,12 @@ __device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z
     put(L::WPSD, wps * d);
     put(L::ONE, 1.0);
     const bool ok = in && !not_positive_normal(P);
+    if (W)
+        put(L::WLNP, ok ? w * log(P) : 0.0);
+    else  // one logarithm per thread at the end (running product, exponent split off)
+        logprod_mul(lp, ok ? P : 1.0);
     if (ok) {
-        put(L::WLNP, w * log(P));
+        if (!W) put(L::WLNP, 0.0);
         put(L::BAD, 0.0);
     } else {  // no contribution; count it if it is a real event
 #pragma unroll 1
@@ -196,31 +214,56 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 {
     extern __shared__ double z[];
-    __shared__ int s_last;
-    const int t = threadIdx.x, lane = t & 31;
+    __shared__ double s_tab[kExpTable];
+    __shared__ double s_lnp[kHessThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int j = t; j < kExpTable; j += kHessThreads) s_tab[j] = g_htab[j];
+    __syncthreads();
     const int ns = a.nslots;
-    const int nps = (ns + kHessThreads - 1) / kHessThreads;  // uniform over the block
+    // slots t, t + 128, t + 256 of this thread; the warp runs as many slot rows as its first
+    // lane owns (slots past the end, in the last partial row only, go to unused accumulators)
+    const int w0 = t & ~31;
+    const int nrow = ns > w0 ? min(3, (ns - w0 + kHessThreads - 1) / kHessThreads) : 0;
     int ci[3], cj[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int s = t + k * kHessThreads;
-        // slots past the end multiply the ONE column by itself into an unused accumulator
         const int sc = s < ns ? s : 0;
         ci[k] = a.si[sc];
         cj[k] = a.sj[sc];
     }
     double acc[3] = {0.0, 0.0, 0.0};
+    LogProd lp{1.0, 0};  // unweighted: product of this thread's densities
     const int64_t ntiles = (a.n + kHessThreads - 1) / kHessThreads;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        stage_event<KIND, VAR, W>(a, tile * kHessThreads + t, z, t);
+        stage_event<KIND, VAR, W>(a, tile * kHessThreads + t, z, t, s_tab, lp);
         __syncthreads();
-        if (nps == 1)
+        if (nrow == 1)
             tile_slots<1>(z, ci, cj, acc, lane);
-        else if (nps == 2)
+        else if (nrow == 2)
             tile_slots<2>(z, ci, cj, acc, lane);
-        else
+        else if (nrow == 3)
             tile_slots<3>(z, ci, cj, acc, lane);
         __syncthreads();
+    }
+    if (!W) {
+        // sum over the block of the threads' ln(products), fixed tree, into the ln P slot
+        double v = logprod_value(lp);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_lnp[warp] = v;
+        __syncthreads();
+        const int ls = a.lnp_slot;
+        if (ls >= 0 && t == (ls & (kHessThreads - 1))) {
+            const double tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
+            const int row = ls / kHessThreads;  // static indices keep acc in registers
+            if (row == 0)
+                acc[0] += tot;
+            else if (row == 1)
+                acc[1] += tot;
+            else
+                acc[2] += tot;
+        }
     }
     const int nb = gridDim.x;
 #pragma unroll
@@ -228,18 +271,23 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
         const int s = t + k * kHessThreads;
         if (s < ns) a.partials[(size_t)s * nb + blockIdx.x] = acc[k];
     }
-    __threadfence();
+}
+
+// Slot totals: block s sums the per-block partials of slot s (thread l takes blocks l,
+// l + 128, ...), then a fixed butterfly per warp and the four warp sums in order.
+__global__ void __launch_bounds__(kHessThreads) hess_reduce_kernel(const double* __restrict__ partials, int nb,
+                                                                   double* __restrict__ out)
+{
+    __shared__ double s_w[kHessThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, s = blockIdx.x;
+    const double* p = partials + (size_t)s * nb;
+    double v = 0.0;
+    for (int b = t; b < nb; b += kHessThreads) v += p[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_w[t >> 5] = v;
     __syncthreads();
-    if (t == 0) s_last = (atomicAdd(a.ticket, 1u) == (unsigned)(nb - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int s = t; s < ns; s += kHessThreads) {
-        double tot = 0.0;
-        for (int b = 0; b < nb; ++b) tot += __ldcg(a.partials + (size_t)s * nb + b);
-        a.out[s] = tot;
-    }
-    if (t == 0) *a.ticket = 0u;
+    if (t == 0) out[s] = (s_w[0] + s_w[1]) + (s_w[2] + s_w[3]);
 }
 
 // ------------------------------------------------------------------------------------
@@ -387,6 +435,14 @@ bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
     assemble_any(kind, weighted, H, 0.0, want_w2, rec, &nll, grad, Hm, Wm);
     L->ncols = kind == kMass1D ? (weighted ? ncols_of<kMass1D, true>() : ncols_of<kMass1D, false>())
                                : (weighted ? ncols_of<kKstar4D, true>() : ncols_of<kKstar4D, false>());
+    L->lnp_slot = -1;
+    if (!weighted) {
+        const int wl = kind == kMass1D ? HCols<kMass1D, false>::WLNP : HCols<kKstar4D, false>::WLNP;
+        const int one = kind == kMass1D ? HCols<kMass1D, false>::ONE : HCols<kKstar4D, false>::ONE;
+        for (int s = 0; s < L->nslots; ++s)
+            if (L->si[s] == wl && L->sj[s] == one) L->lnp_slot = s;
+        if (L->lnp_slot < 0) return false;
+    }
     return !rec.overflow;
 }
 
@@ -403,8 +459,9 @@ void hess_fill_const(int kind, const Hoist& H, const double* theta, HConst* c)
     memset(c, 0, sizeof *c);
     c->mu = H.mu;
     c->b0 = H.b0;
-    c->alpha = H.alpha;
-    c->k0u = H.lnb1 - H.alpha * (H.mu - H.ma);
+    c->neg_b0s = -H.b0 * kExpArgScale;
+    c->neg_als = -H.alpha * kExpArgScale;
+    c->k0s = (H.lnb1 - H.alpha * (H.mu - H.ma)) * kExpArgScale;
     c->b2 = H.b2;
     c->inv_sigma = 1.0 / H.sigma;
     c->dlnN1_dmu = H.dlnN1_dmu;
@@ -437,6 +494,9 @@ static cudaError_t launch_t(int blocks, cudaStream_t s, const HArgs& a)
                                          (int)smem);
     if (e != cudaSuccess) return e;
     hess_kernel<KIND, VAR, W><<<blocks, kHessThreads, smem, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    hess_reduce_kernel<<<a.nslots, kHessThreads, 0, s>>>(a.partials, blocks, a.out);
     return cudaGetLastError();
 }
 
@@ -454,9 +514,31 @@ static int occ_t()
     return nb;
 }
 
+namespace {
+std::mutex g_htab_mutex;
+bool g_htab_ready[64];
+
+cudaError_t ensure_htab()
+{
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_htab_mutex);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (g_htab_ready[device]) return cudaSuccess;
+    std::vector<double> tab(kExpTable);
+    for (int j = 0; j < kExpTable; ++j) tab[j] = (double)exp2l((long double)j / (long double)kExpTable);
+    e = cudaMemcpyToSymbol(g_htab, tab.data(), sizeof(double) * kExpTable);
+    if (e == cudaSuccess) g_htab_ready[device] = true;
+    return e;
+}
+}  // namespace
+
 cudaError_t launch_hess(int kind, int variant, bool weighted, int blocks, cudaStream_t stream, const HArgs& a)
 {
     if (a.nslots <= 0 || a.nslots > kHessMaxSlots || blocks <= 0) return cudaErrorInvalidValue;
+    cudaError_t e = ensure_htab();
+    if (e != cudaSuccess) return e;
     if (kind == kMass1D)
         return weighted ? launch_t<kMass1D, kVarPrecompute, true>(blocks, stream, a)
                         : launch_t<kMass1D, kVarPrecompute, false>(blocks, stream, a);

@@ -88,7 +88,6 @@ struct nll_model {
 
     // analytic Hessian scratch (allocated at the first nll_eval_hess)
     double* d_hpart = nullptr;          // [kHessMaxSlots][hess_max_blocks]
-    unsigned int* d_hticket = nullptr;
     double* h_hout = nullptr;           // mapped pinned [kHessMaxSlots]
     double* d_hout = nullptr;
     int hess_max_blocks = 0;
@@ -400,16 +399,12 @@ int ensure_hess_scratch(nll_model* m)
     if (m->d_hpart) return NLL_OK;
     m->hess_max_blocks = m->sm_count * kHessMaxBlocksPerSm;
     cudaError_t e = cudaMalloc(&m->d_hpart, sizeof(double) * kHessMaxSlots * (size_t)m->hess_max_blocks);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_hticket, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(m->d_hticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaHostAlloc(&m->h_hout, sizeof(double) * kHessMaxSlots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_hout, m->h_hout, 0);
     if (e != cudaSuccess) {
         if (m->d_hpart) cudaFree(m->d_hpart);
-        if (m->d_hticket) cudaFree(m->d_hticket);
         if (m->h_hout) cudaFreeHost(m->h_hout);
         m->d_hpart = m->h_hout = m->d_hout = nullptr;
-        m->d_hticket = nullptr;
         return cuda_fail(m, e, "Hessian scratch");
     }
     return NLL_OK;
@@ -444,8 +439,8 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         a.n = m->n;
         hess_fill_const(m->kind, H, theta, &a.c);
         a.nslots = L.nslots;
+        a.lnp_slot = L.lnp_slot;
         a.partials = m->d_hpart;
-        a.ticket = m->d_hticket;
         a.out = m->d_hout;
         memcpy(a.si, L.si, sizeof a.si);
         memcpy(a.sj, L.sj, sizeof a.sj);
@@ -601,7 +596,6 @@ void nll_destroy(nll_model* m)
     if (m->d_ticket) cudaFree(m->d_ticket);
     if (m->h_out) cudaFreeHost(m->h_out);  // d_out is its device alias
     if (m->d_hpart) cudaFree(m->d_hpart);
-    if (m->d_hticket) cudaFree(m->d_hticket);
     if (m->h_hout) cudaFreeHost(m->h_hout);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
