@@ -78,14 +78,27 @@ typedef enum { NLL_VARIANT_AUTO = 0, NLL_VARIANT_PRECOMPUTE = 1, NLL_VARIANT_DIR
 int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t cuda_stream, nll_model** out);
 
 /*
- * nll_load_events -- copy a data sample into the model (replacing any previous one).
+ * nll_load_events -- give the model a data sample (replacing any previous one).
  *   columns      ndim pointers (1 for MASS1D: m; 4 for 4D: m, ctl, ctk, phi), each to
- *                n_events doubles.  Host pointers if on_device == 0, device pointers on
- *                the model's device if on_device == 1.  The library copies them into its
- *                own 256-byte-aligned SoA store (padded to a tile multiple).
+ *                n_events doubles.
+ *   on_device    0: host pointers, 1: device pointers on the model's device; the library
+ *                copies them into its own 256-byte-aligned SoA store (padded to a tile
+ *                multiple).
+ *                2 (in place): nothing is copied or stored; every evaluation reads the
+ *                caller's buffers where they are.  They must be memory the model's device can
+ *                read -- its own device memory, managed memory, pinned or registered host
+ *                memory, or any host memory when the device reports
+ *                cudaDevAttrPageableMemoryAccess (a coherent CPU-GPU link, as on Grace
+ *                systems) -- each 16-byte aligned (checked; NLL_ERR_ARG otherwise), and the
+ *                caller keeps them alive and unchanged until the next load or nll_destroy.
+ *                Meant for samples evaluated once or a few times (a stream of batches): the
+ *                transfer then overlaps the evaluation instead of preceding it.  The 4D model
+ *                uses the direct variant (no precompute).  Events outside the ranges are
+ *                reported by the evaluation (NLL_ERR_ARG) instead of by the load.
  *   weights      n_events per-event weights w_i (same memory space), or NULL for w_i = 1.
  *   precompute   4D only: 1 = build the event-only angular basis once here (paper
- *                Sec. 2.4.2 event-dependent precompute), 0 = keep only the raw angles.
+ *                Sec. 2.4.2 event-dependent precompute), 0 = keep only the raw angles
+ *                (ignored in place).
  * Events outside the observable ranges, or non-finite values/weights, are rejected with
  * NLL_ERR_ARG and the model keeps no sample.  n_events may be 0 (NLL = 0, gradient 0).
  */
@@ -221,7 +234,8 @@ int nll_precomputed_basis(nll_model* m, double* out);
  *                (plus one DADD), [4] the library's table exp, [5] the library's reciprocal
  *                (plus one DADD).  2 * rates[0] is the FP64 roofline in flop/s; rates[0] /
  *                rates[i] is the cost of operation i in DFMA issue slots.
- * The fused kernels are FP64-issue bound (see DESIGN), so this is their roofline.
+ * The fused kernels do more FP64 work per byte than the GPU's FP64-to-HBM ratio, so they are
+ * FP64-issue bound and this is their roofline.
  */
 int nll_calibrate_fp64(int device, double* rates);
 
@@ -229,8 +243,10 @@ int nll_calibrate_fp64(int device, double* rates);
  * nll_diag_math -- diagnostic: evaluate the library's device FP64 building blocks on n
  * host inputs x, writing host outputs y (fn 0: the table-driven exponential used by the
  * kernels, after Tang's method, which takes its argument pre-scaled: y = exp(x ln2/1024);
- * fn 1: the reciprocal, hardware approximation plus one cubic correction).  For accuracy
- * tests against the host's libm; allocates temporary device buffers.
+ * fn 1: the reciprocal, hardware approximation plus one cubic correction; fn 2 / fn 3:
+ * sin x / cos x by the table method with Cody-Waite reduction, accurate for |x| <= pi, as
+ * the 4D kernels use it for phi).  For accuracy tests against the host's libm; allocates
+ * temporary device buffers.
  */
 int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
 

@@ -170,10 +170,42 @@ def nll_create_model(kind, obs_ranges, device=0, stream=0):
     return h.value
 
 
-def nll_load_events(model, columns, weights=None, precompute=True):
-    """Copy events (numpy arrays on the host, or CUDA tensors) into the model."""
+def _in_place_ptr(x, what):
+    """Address of a float64 contiguous array or tensor, without a copy (in-place loads)."""
+    if hasattr(x, "data_ptr"):
+        import torch
+
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("%s: in-place loads need contiguous float64 tensors" % what)
+        return x.data_ptr(), int(x.numel())
+    a = np.asarray(x)
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("%s: in-place loads need contiguous float64 arrays" % what)
+    return a.ctypes.data, len(a)
+
+
+def nll_load_events(model, columns, weights=None, precompute=True, in_place=False):
+    """Copy events (numpy arrays on the host, or CUDA tensors) into the model.
+
+    With in_place=True nothing is copied: every evaluation reads these buffers (pinned host
+    memory, device memory, or on a coherent CPU-GPU system any host memory; float64,
+    contiguous, 16-byte aligned).  Returns the objects the model reads; keep them alive
+    and unchanged until the next load (Model.load keeps them)."""
     L = load()
     cols = list(columns)
+    if in_place:
+        ptrs, ns = zip(*[_in_place_ptr(c, "column %d" % i) for i, c in enumerate(cols)])
+        if len(set(ns)) != 1:
+            raise ValueError("columns differ in length")
+        wp = None
+        if weights is not None:
+            wp, nw = _in_place_ptr(weights, "weights")
+            if nw != ns[0]:
+                raise ValueError("weights differ in length from the columns")
+        arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+        st = L.nll_load_events(model, arr, wp, ns[0], 2, 0)
+        _check(model, st)
+        return cols + ([weights] if weights is not None else [])
     on_device = _is_cuda_tensor(cols[0])
     keep = []
     if on_device:
@@ -365,7 +397,8 @@ def nll_calibrate_fp64(device=0):
 
 
 def nll_diag_math(fn, x, device=0):
-    """Evaluate the library's device exp (fn=0) or reciprocal (fn=1) on host array x."""
+    """Evaluate the library's device exp (fn=0), reciprocal (fn=1), sin (fn=2) or cos (fn=3)
+    on host array x (see nll_diag_math in the C header for the argument conventions)."""
     xa = _f64(x)
     y = np.zeros_like(xa)
     st = load().nll_diag_math(int(device), int(fn), _p(xa), _p(y), len(xa))
@@ -453,8 +486,9 @@ class Model:
         self._gp = self._g.ctypes.data_as(_DP)
         self._outp = ctypes.byref(self._out)
 
-    def load(self, columns, weights=None, precompute=True):
-        nll_load_events(self.handle, columns, weights, precompute)
+    def load(self, columns, weights=None, precompute=True, in_place=False):
+        kept = nll_load_events(self.handle, columns, weights, precompute, in_place)
+        self._in_place_keep = kept if in_place else None  # the buffers the model reads
         return self
 
     def eval(self, theta):

@@ -42,7 +42,7 @@ constexpr int kEvalThreads = 128;
 constexpr int kUpdWarps = 4;
 const double kPiH = 3.14159265358979323846;
 
-__device__ double g_btab[kExpTable];
+__device__ double g_btab[kTabDoubles];
 
 enum Phase : int { kPhInit = 0, kPhSearch = 1, kPhHess = 2, kPhDone = 3 };
 
@@ -301,10 +301,11 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
 {
     constexpr int K = KIND == kMass1D ? kAcc1D : kAcc4D;
-    __shared__ double s_tab[kExpTable];
+    __shared__ double s_tab[kTabDoubles];
     __shared__ double s_red[(kEvalThreads / 32) * K];
     __shared__ int s_u;
-    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_tab[j] = g_btab[j];
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    for (int j = threadIdx.x; j < ntab; j += blockDim.x) s_tab[j] = g_btab[j];
     __syncthreads();
     const int nunits = min(b.counters[1], b.max_units);
     while (true) {
@@ -695,9 +696,9 @@ cudaError_t ensure_btab(int device)
     std::lock_guard<std::mutex> lock(g_btab_mutex);
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     if (g_btab_ready[device]) return cudaSuccess;
-    std::vector<double> tab(kExpTable);
-    for (int j = 0; j < kExpTable; ++j) tab[j] = (double)exp2l((long double)j / (long double)kExpTable);
-    cudaError_t e = cudaMemcpyToSymbol(g_btab, tab.data(), sizeof(double) * kExpTable);
+    std::vector<double> tab(kTabDoubles);
+    fill_device_tables(tab.data());
+    cudaError_t e = cudaMemcpyToSymbol(g_btab, tab.data(), sizeof(double) * kTabDoubles);
     if (e == cudaSuccess) g_btab_ready[device] = true;
     return e;
 }

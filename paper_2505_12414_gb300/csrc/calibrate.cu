@@ -14,7 +14,7 @@ namespace {
 
 constexpr int kChains = 8;
 
-__device__ double g_cal_tab[gbnll::kExpTable];
+__device__ double g_cal_tab[gbnll::kTabDoubles];
 
 template <int OP>
 __global__ void __launch_bounds__(256) cal_kernel(double* out, int iters, double a)
@@ -65,26 +65,36 @@ cudaError_t time_op(double* out, int blocks, int iters, double a, float* ms)
 
 cudaError_t upload_table()
 {
-    static double tab[gbnll::kExpTable];
-    for (int j = 0; j < gbnll::kExpTable; ++j)
-        tab[j] = (double)exp2l((long double)j / (long double)gbnll::kExpTable);
+    static double tab[gbnll::kTabDoubles];
+    gbnll::fill_device_tables(tab);
     return cudaMemcpyToSymbol(g_cal_tab, tab, sizeof tab);
 }
 
 __global__ void __launch_bounds__(256) diag_kernel(int fn, const double* x, double* y, int64_t n)
 {
-    __shared__ double s_tab[gbnll::kExpTable];
-    for (int j = threadIdx.x; j < gbnll::kExpTable; j += blockDim.x) s_tab[j] = g_cal_tab[j];
+    __shared__ double s_tab[gbnll::kTabDoubles];
+    for (int j = threadIdx.x; j < gbnll::kTabDoubles; j += blockDim.x) s_tab[j] = g_cal_tab[j];
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = fn == 0 ? gbnll::fexp_scaled(x[i], s_tab) : gbnll::frcp(x[i]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v;
+        if (fn == 0) {
+            v = gbnll::fexp_scaled(x[i], s_tab);
+        } else if (fn == 1) {
+            v = gbnll::frcp(x[i]);
+        } else {
+            double sv, cv;
+            gbnll::fsincos_pi(x[i], s_tab + gbnll::kExpTable, sv, cv);
+            v = fn == 2 ? sv : cv;
+        }
+        y[i] = v;
+    }
 }
 
 }  // namespace
 
 extern "C" int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n)
 {
-    if ((fn != 0 && fn != 1) || n < 0 || (n > 0 && (!x || !y))) return NLL_ERR_ARG;
+    if (fn < 0 || fn > 3 || n < 0 || (n > 0 && (!x || !y))) return NLL_ERR_ARG;
     if (n == 0) return NLL_OK;
     if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
     if (upload_table() != cudaSuccess) return NLL_ERR_CUDA;

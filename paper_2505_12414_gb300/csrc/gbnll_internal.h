@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <string>
 
@@ -43,6 +44,11 @@ constexpr int kAcc1D = 7;
 constexpr int kAcc4D = 21;
 constexpr int kAccNll = 2;
 constexpr int kAccMax = 21;
+// In-place evaluation (events read where the caller keeps them, nothing stored at load) adds
+// two sums the load-time statistics supply otherwise: sum w (m - ma) and the count of events
+// outside the observable ranges or with invalid weights.
+constexpr int kAccInPlace = 2;
+constexpr int kAccModel = kAccMax + kAccInPlace;  // slots of a model's own reduction buffers
 
 // Per-launch constant block: every parameter-only term the per-event work needs
 // (paper Sec. 2.4.1: terms that depend on the parameters only are computed once per
@@ -62,9 +68,13 @@ struct KArgs {
     const double* w;              // weights or NULL
     int64_t n;                    // events
     KConst c;
-    double* partials;             // [kAccMax][max_blocks] per-block sums
+    double* partials;             // [K][max_blocks] per-block sums (K = slots of the launch)
     unsigned int* ticket;         // grid-completion counter, 0 between launches
-    double* out;                  // [kAccMax] final sums
+    double* out;                  // [K] final sums
+    // in-place evaluation only: ma, and order keys of [lo, hi] per observable and of the
+    // weights' range [-0, 1e300] (slot 4); see order_key in nll_device.cuh
+    double ma;
+    long long klo[5], khi[5];
 };
 
 // Load-time statistics: sum w, sum w (m - ma), count of events outside the ranges.
@@ -103,11 +113,11 @@ void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, do
 
 // Launchers (kernels.cu).  They return the launch's cudaError_t.
 cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,
-                         cudaStream_t stream, const KArgs& a);
+                         cudaStream_t stream, const KArgs& a, bool in_place = false);
 cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a);
 cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BArgs& a);
-cudaError_t upload_exp2_table_values(const double* host_table);  // 2^(j/N), N = exp2_table_size(),
-                                                                 // into the current device
+cudaError_t upload_exp2_table_values(const double* host_table);  // exp2_table_size() doubles from
+                                                                 // fill_device_tables, current device
 int exp2_table_size();
 int num_acc(int kind, bool grad);
 
@@ -169,6 +179,15 @@ struct NoAllocScratch {
 };
 // Device addresses of the scratch on `device` (which must be current); set up once per device.
 cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out);
-int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads);  // resident blocks/SM
+int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads,
+                    bool in_place = false);  // resident blocks/SM
+// Order key of a double: key(x) <= key(y) iff x <= y for non-NaN x, y (-0 < +0); NaNs fall
+// outside any finite interval.  Host copy of the device function in nll_device.cuh.
+inline long long order_key_host(double x)
+{
+    long long b;
+    memcpy(&b, &x, sizeof b);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
 
 }  // namespace gbnll

@@ -50,7 +50,7 @@
 
 namespace gbnll {
 
-__device__ double g_htab[kExpTable];  // 2^(j/N) for fexp_scaled, uploaded once per device
+__device__ double g_htab[kTabDoubles];  // exp and sin/cos tables, uploaded once per device
 
 // Column layout of the staged tile.  Without weights the weighted scores are the scores.
 template <int KIND, bool W>
@@ -117,7 +117,7 @@ __device__ __forceinline__ void stage_event(const HArgs& a, int64_t e, double* z
         } else {
             xl = __ldg(a.col[kColCtl] + ei);
             xk = __ldg(a.col[kColCtk] + ei);
-            angular_basis(xl, xk, __ldg(a.col[kColPhi] + ei), h, t2l, t2k, xp, t2p);
+            angular_basis(xl, xk, __ldg(a.col[kColPhi] + ei), h, t2l, t2k, xp, t2p, tab + kExpTable);
         }
         double A = fma(c.ang[0], h[1], h[0]);
 #pragma unroll
@@ -214,10 +214,11 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 {
     extern __shared__ double z[];
-    __shared__ double s_tab[kExpTable];
+    __shared__ double s_tab[kTabDoubles];
     __shared__ double s_lnp[kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int j = t; j < kExpTable; j += kHessThreads) s_tab[j] = g_htab[j];
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_htab[j];
     __syncthreads();
     const int ns = a.nslots;
     // slots t, t + 128, t + 256 of this thread; the warp runs as many slot rows as its first
@@ -526,9 +527,9 @@ cudaError_t ensure_htab()
     std::lock_guard<std::mutex> lock(g_htab_mutex);
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     if (g_htab_ready[device]) return cudaSuccess;
-    std::vector<double> tab(kExpTable);
-    for (int j = 0; j < kExpTable; ++j) tab[j] = (double)exp2l((long double)j / (long double)kExpTable);
-    e = cudaMemcpyToSymbol(g_htab, tab.data(), sizeof(double) * kExpTable);
+    std::vector<double> tab(kTabDoubles);
+    fill_device_tables(tab.data());
+    e = cudaMemcpyToSymbol(g_htab, tab.data(), sizeof(double) * kTabDoubles);
     if (e == cudaSuccess) g_htab_ready[device] = true;
     return e;
 }

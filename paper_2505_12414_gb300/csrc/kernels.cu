@@ -46,16 +46,20 @@
 
 namespace gbnll {
 
-__device__ double g_exp2tab[kExpTable];  // 2^(j/N), correctly rounded, uploaded once per device
+__device__ double g_exp2tab[kTabDoubles];  // exp and sin/cos tables (fill_device_tables), once per device
 
 // Work split: block b owns the contiguous pair range [b P / B, (b+1) P / B) (P pairs, B
 // blocks), which its threads walk with a block-sized stride (coalesced).  Every block,
 // hence every SM, gets the same work to within one pair.
-template <int KIND, int VAR, bool W, bool GRAD>
+// IP (in place): the columns are the caller's buffers (device or host memory the device
+// reads), so the tail pair may not be read whole, and the kernel also sums w (m - ma) and
+// counts events outside the ranges (slots KB-1 and KB; the bad count moves to the last slot).
+template <int KIND, int VAR, bool W, bool GRAD, bool IP = false>
 __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 {
-    constexpr int K = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
-    __shared__ double s_tab[kExpTable];
+    constexpr int KB = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
+    constexpr int K = KB + (IP ? kAccInPlace : 0);
+    __shared__ double s_tab[kTabDoubles];
     __shared__ double s_red[8 * K];
 
     const int64_t n = a.n;
@@ -66,8 +70,10 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 
     // the first pair's loads are in flight while the block stages the exp table
     PairIn in;
-    if (p < end) load_pair<KIND, VAR, W>(a, p, in);
-    for (int j = threadIdx.x; j < kExpTable; j += blockDim.x) s_tab[j] = g_exp2tab[j];
+    if (p < end) load_pair<KIND, VAR, W, IP>(a, p, in);
+    // the sin/cos part of the table only where the angular basis is computed here
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    for (int j = threadIdx.x; j < ntab; j += blockDim.x) s_tab[j] = g_exp2tab[j];
     __syncthreads();
 
     double acc[K];
@@ -79,8 +85,9 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 
     while (p < end) {
         process_pair<KIND, VAR, W, GRAD>(c, in, (2 * p + 1) < n, acc, lpx, lpy, bad, s_tab);
+        if (IP) inplace_pair<KIND, VAR, W>(a, in, (2 * p + 1) < n, acc[KB - 1], acc[KB]);
         p += blockDim.x;
-        if (p < end) load_pair<KIND, VAR, W>(a, p, in);
+        if (p < end) load_pair<KIND, VAR, W, IP>(a, p, in);
     }
     if (!W) {
         // one logarithm per warp: multiply the running products across the warp first
@@ -122,7 +129,7 @@ __global__ void __launch_bounds__(256) basis_kernel(const BArgs a)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         double h[9], t2l, t2k, xp, t2p;
-        angular_basis(a.ctl[i], a.ctk[i], a.phi[i], h, t2l, t2k, xp, t2p);
+        angular_basis(a.ctl[i], a.ctk[i], a.phi[i], h, t2l, t2k, xp, t2p, g_exp2tab + kExpTable);
 #pragma unroll
         for (int j = 0; j < 9; ++j) a.out[j][i] = h[j];
         a.out[9][i] = t2l;
@@ -137,55 +144,64 @@ __global__ void __launch_bounds__(256) basis_kernel(const BArgs a)
 // ----------------------------------------------------------------------------------
 int num_acc(int kind, bool grad) { return !grad ? kAccNll : (kind == kMass1D ? kAcc1D : kAcc4D); }
 
-template <int KIND, int VAR>
+template <int KIND, int VAR, bool IP>
 static int occ_kv(bool weighted, bool grad, int threads)
 {
     int nb = 0;
     if (weighted) {
         if (grad)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, true, true>, threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, true, true, IP>, threads, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, true, false>, threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, true, false, IP>, threads, 0);
     } else {
         if (grad)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, false, true>, threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, false, true, IP>, threads, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, false, false>, threads, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fused_nll_kernel<KIND, VAR, false, false, IP>, threads, 0);
     }
     return nb;
 }
 
-int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads)
+int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads, bool in_place)
 {
-    if (kind == kMass1D) return occ_kv<kMass1D, kVarPrecompute>(weighted, grad, threads);
-    if (variant == kVarDirect) return occ_kv<kKstar4D, kVarDirect>(weighted, grad, threads);
-    return occ_kv<kKstar4D, kVarPrecompute>(weighted, grad, threads);
+    if (in_place) {  // in place: mass model, or the 4D direct variant (nothing precomputed)
+        if (kind == kMass1D) return occ_kv<kMass1D, kVarPrecompute, true>(weighted, grad, threads);
+        return occ_kv<kKstar4D, kVarDirect, true>(weighted, grad, threads);
+    }
+    if (kind == kMass1D) return occ_kv<kMass1D, kVarPrecompute, false>(weighted, grad, threads);
+    if (variant == kVarDirect) return occ_kv<kKstar4D, kVarDirect, false>(weighted, grad, threads);
+    return occ_kv<kKstar4D, kVarPrecompute, false>(weighted, grad, threads);
 }
 
-template <int KIND, int VAR>
+template <int KIND, int VAR, bool IP>
 static cudaError_t launch_kv(bool weighted, bool grad, int blocks, int threads, cudaStream_t s, const KArgs& a)
 {
     if (weighted) {
         if (grad)
-            fused_nll_kernel<KIND, VAR, true, true><<<blocks, threads, 0, s>>>(a);
+            fused_nll_kernel<KIND, VAR, true, true, IP><<<blocks, threads, 0, s>>>(a);
         else
-            fused_nll_kernel<KIND, VAR, true, false><<<blocks, threads, 0, s>>>(a);
+            fused_nll_kernel<KIND, VAR, true, false, IP><<<blocks, threads, 0, s>>>(a);
     } else {
         if (grad)
-            fused_nll_kernel<KIND, VAR, false, true><<<blocks, threads, 0, s>>>(a);
+            fused_nll_kernel<KIND, VAR, false, true, IP><<<blocks, threads, 0, s>>>(a);
         else
-            fused_nll_kernel<KIND, VAR, false, false><<<blocks, threads, 0, s>>>(a);
+            fused_nll_kernel<KIND, VAR, false, false, IP><<<blocks, threads, 0, s>>>(a);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,
-                         cudaStream_t stream, const KArgs& a)
+                         cudaStream_t stream, const KArgs& a, bool in_place)
 {
     if (threads > 256 || threads < 32 || (threads & 31)) return cudaErrorInvalidValue;
-    if (kind == kMass1D) return launch_kv<kMass1D, kVarPrecompute>(weighted, grad, blocks, threads, stream, a);
-    if (variant == kVarDirect) return launch_kv<kKstar4D, kVarDirect>(weighted, grad, blocks, threads, stream, a);
-    return launch_kv<kKstar4D, kVarPrecompute>(weighted, grad, blocks, threads, stream, a);
+    if (in_place) {
+        if (kind == kMass1D) return launch_kv<kMass1D, kVarPrecompute, true>(weighted, grad, blocks, threads, stream, a);
+        if (variant != kVarDirect) return cudaErrorInvalidValue;
+        return launch_kv<kKstar4D, kVarDirect, true>(weighted, grad, blocks, threads, stream, a);
+    }
+    if (kind == kMass1D) return launch_kv<kMass1D, kVarPrecompute, false>(weighted, grad, blocks, threads, stream, a);
+    if (variant == kVarDirect) return launch_kv<kKstar4D, kVarDirect, false>(weighted, grad, blocks, threads, stream, a);
+    return launch_kv<kKstar4D, kVarPrecompute, false>(weighted, grad, blocks, threads, stream, a);
 }
 
 cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a)
@@ -202,10 +218,10 @@ cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BAr
 
 cudaError_t upload_exp2_table_values(const double* host_table)
 {
-    return cudaMemcpyToSymbol(g_exp2tab, host_table, kExpTable * sizeof(double));
+    return cudaMemcpyToSymbol(g_exp2tab, host_table, kTabDoubles * sizeof(double));
 }
 
-int exp2_table_size() { return kExpTable; }
+int exp2_table_size() { return kTabDoubles; }
 
 // ----------------------------------------------------------------------------------
 // Static scratch for callers that cannot allocate device memory (nll_eval_grad_4d_noalloc).

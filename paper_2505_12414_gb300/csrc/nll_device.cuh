@@ -16,34 +16,37 @@ namespace gbnll {
 //   A = h0 + FL hFL + S3 h3 + S4 h4 + S5 h5 + AFB h6 + S7 h7 + S8 h8 + S9 h9,
 //   h0 = c sin^2 tK (3/4 + cos 2tl / 4), hFL = c cos^2 tK (1 - cos 2tl) - h0, ...
 // with c = 9/(32 pi).  Also the Chebyshev inputs T2(ctl), T2(ctk), phi/pi, T2(phi/pi).
+// sin tK and sin tl enter only as their product (one square root of the product of the
+// squares), and sin/cos phi come from the table method (trig = the (cos, sin) table).
 // ----------------------------------------------------------------------------------
 __device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi, double h[9], double& t2l,
-                                              double& t2k, double& xp, double& t2p)
+                                              double& t2k, double& xp, double& t2p, const double* trig)
 {
-    const double c = 0x1.6eb167b830193p-4;  // 9/(32 pi)
+    const double c = 0x1.6eb167b830193p-4;   // 9/(32 pi)
+    const double c2 = 0x1.6eb167b830193p-3;  // 2 c
     const double kInvPi = 0x1.45f306dc9c883p-2;
-    double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);
-    double sl = sqrt(sl2), sk = sqrt(sk2);
+    const double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);  // sin^2 tl, sin^2 tK
+    const double sksl = sqrt(sk2 * sl2);                                // sin tK sin tl
     double sp, cp;
-    sincos(phi, &sp, &cp);
-    t2l = fma(2.0 * ctl, ctl, -1.0);
-    t2k = fma(2.0 * ctk, ctk, -1.0);
-    double c2p = fma(2.0 * cp, cp, -1.0);  // cos 2phi
-    double s2p = 2.0 * sp * cp;            // sin 2phi
-    double h0 = c * sk2 * fma(0.25, t2l, 0.75);
-    double a = c * sk2 * sl2;              // c sin^2 tK sin^2 tl
-    double b = 2.0 * c * sk * ctk * sl;    // c sin 2tK sin tl
+    fsincos_pi(phi, trig, sp, cp);
+    t2l = fma(-2.0, sl2, 1.0);  // cos 2tl = 1 - 2 sin^2 tl
+    t2k = fma(-2.0, sk2, 1.0);
+    const double csk2 = c * sk2;
+    const double h0 = csk2 * fma(0.25, t2l, 0.75);
+    const double a = csk2 * sl2;            // c sin^2 tK sin^2 tl
+    const double b = c2 * ctk * sksl;       // c sin 2tK sin tl
+    const double bc = b * cp, bs = b * sp, ctl2 = ctl + ctl;
     h[0] = h0;
-    h[1] = c * (ctk * ctk) * (1.0 - t2l) - h0;
-    h[2] = a * c2p;                // S3
-    h[3] = 2.0 * b * ctl * cp;     // S4: c sin 2tK sin 2tl cos phi
-    h[4] = b * cp;                 // S5
-    h[5] = (4.0 / 3.0) * c * sk2 * ctl;  // AFB
-    h[6] = b * sp;                 // S7
-    h[7] = 2.0 * b * ctl * sp;     // S8
-    h[8] = a * s2p;                // S9
+    h[1] = fma(fma(-2.0, csk2, c2), sl2, -h0);  // c cos^2 tK (1 - cos 2tl) - h0
+    h[2] = a * fma(cp + cp, cp, -1.0);          // S3: a cos 2phi
+    h[3] = ctl2 * bc;                           // S4: c sin 2tK sin 2tl cos phi
+    h[4] = bc;                                  // S5
+    h[5] = csk2 * (4.0 / 3.0) * ctl;            // AFB: 4/3 c sin^2 tK cos tl
+    h[6] = bs;                                  // S7
+    h[7] = ctl2 * bs;                           // S8
+    h[8] = a * ((sp + sp) * cp);                // S9: a sin 2phi
     xp = phi * kInvPi;
-    t2p = fma(2.0 * xp, xp, -1.0);
+    t2p = fma(xp + xp, xp, -1.0);
 }
 
 // ----------------------------------------------------------------------------------
@@ -218,14 +221,25 @@ struct PairIn {
     double2 t2l, t2k, xp, t2p;
 };
 
-template <int KIND, int VAR, bool W>
+// 128-bit load of events 2p, 2p+1; with TAIL, a pair whose second event is past n loads the
+// first event alone (the caller's buffer may end there) and repeats it.
+template <bool TAIL>
+__device__ __forceinline__ double2 ld2t(const double* col, int64_t p, bool whole)
+{
+    if (!TAIL || whole) return ld2(col, p);
+    const double x = __ldg(col + 2 * p);
+    return make_double2(x, x);
+}
+
+template <int KIND, int VAR, bool W, bool TAIL = false>
 __device__ __forceinline__ void load_pair(const KArgs& a, int64_t p, PairIn& in)
 {
-    in.m = ld2(a.col[kColM], p);
-    if (W) in.w = ld2(a.w, p);
+    const bool whole = !TAIL || 2 * p + 1 < a.n;
+    in.m = ld2t<TAIL>(a.col[kColM], p, whole);
+    if (W) in.w = ld2t<TAIL>(a.w, p, whole);
     if (KIND == kKstar4D) {
-        in.l = ld2(a.col[kColCtl], p);
-        in.k = ld2(a.col[kColCtk], p);
+        in.l = ld2t<TAIL>(a.col[kColCtl], p, whole);
+        in.k = ld2t<TAIL>(a.col[kColCtk], p, whole);
         if (VAR == kVarPrecompute) {
 #pragma unroll
             for (int j = 0; j < 9; ++j) in.h[j] = ld2(a.col[kColH0 + j], p);
@@ -234,9 +248,46 @@ __device__ __forceinline__ void load_pair(const KArgs& a, int64_t p, PairIn& in)
             in.xp = ld2(a.col[kColXp], p);
             in.t2p = ld2(a.col[kColT2p], p);
         } else {
-            in.f = ld2(a.col[kColPhi], p);
+            in.f = ld2t<TAIL>(a.col[kColPhi], p, whole);
         }
     }
+}
+
+// Order key of a double (see order_key_host): integer-pipe range checks.
+__device__ __forceinline__ long long order_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ int outside_key(double x, long long lo, long long hi)
+{
+    const long long k = order_key(x);
+    return (k < lo) | (k > hi);
+}
+
+// In-place evaluation: sum w (m - ma) and the count of events outside the ranges (integer
+// compares) for one pair; `second` masks the tail.
+template <int KIND, int VAR, bool W>
+__device__ __forceinline__ void inplace_pair(const KArgs& a, const PairIn& in, bool second, double& wdm,
+                                             double& outside)
+{
+    const double wx = W ? in.w.x : 1.0, wy = W ? in.w.y : 1.0;
+    const double dy = second ? in.m.y - a.ma : 0.0;
+    wdm = fma(wx, in.m.x - a.ma, wdm);
+    wdm = fma(wy, dy, wdm);
+    int ox = outside_key(in.m.x, a.klo[0], a.khi[0]), oy = outside_key(in.m.y, a.klo[0], a.khi[0]);
+    if (W) {
+        ox |= outside_key(wx, a.klo[4], a.khi[4]);
+        oy |= outside_key(wy, a.klo[4], a.khi[4]);
+    }
+    if (KIND == kKstar4D && VAR == kVarDirect) {
+        ox |= outside_key(in.l.x, a.klo[1], a.khi[1]) | outside_key(in.k.x, a.klo[2], a.khi[2]) |
+              outside_key(in.f.x, a.klo[3], a.khi[3]);
+        oy |= outside_key(in.l.y, a.klo[1], a.khi[1]) | outside_key(in.k.y, a.klo[2], a.khi[2]) |
+              outside_key(in.f.y, a.klo[3], a.khi[3]);
+    }
+    outside += (double)(ox + (second ? oy : 0));
 }
 
 template <int KIND, int VAR, bool W, bool GRAD>
@@ -265,8 +316,8 @@ __device__ __forceinline__ void process_pair(const KConst& c, const PairIn& in, 
             t2px = in.t2p.x;
             t2py = in.t2p.y;
         } else {
-            angular_basis(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px);
-            angular_basis(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py);
+            angular_basis(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px, tab + kExpTable);
+            angular_basis(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py, tab + kExpTable);
         }
         event_4d<W, GRAD>(c, in.m.x, hx, in.l.x, t2lx, in.k.x, t2kx, xpx, t2px, wx, true, acc, lpx, bad, tab);
         event_4d<W, GRAD>(c, in.m.y, hy, in.l.y, t2ly, in.k.y, t2ky, xpy, t2py, wy, second, acc, lpy, bad, tab);

@@ -41,9 +41,8 @@ int ensure_exp2_table(int device)
     std::lock_guard<std::mutex> lock(g_table_mutex);
     if (device < 0 || device >= 64) return NLL_ERR_ARG;
     if (g_table_ready[device]) return NLL_OK;
-    const int N = exp2_table_size();
-    std::vector<double> tab(N);
-    for (int j = 0; j < N; ++j) tab[j] = (double)exp2l((long double)j / (long double)N);
+    std::vector<double> tab(exp2_table_size());
+    fill_device_tables(tab.data());
     if (upload_exp2_table_values(tab.data()) != cudaSuccess) return NLL_ERR_CUDA;
     g_table_ready[device] = true;
     return NLL_OK;
@@ -70,6 +69,10 @@ struct nll_model {
     size_t ev_bytes = 0;     // bytes used by the current sample
     size_t ev_capacity = 0;  // bytes allocated at d_ev
     double sum_w = 0.0, sum_wdm = 0.0;
+    // in-place sample (on_device = 2): the caller's buffers, read by every evaluation
+    bool in_place = false;
+    const double* ip_col[4] = {nullptr, nullptr, nullptr, nullptr};
+    const double* ip_w = nullptr;
 
     // reduction scratch and results
     int max_blocks = 0;
@@ -134,6 +137,14 @@ int cuda_fail(nll_model* m, cudaError_t e, const char* what)
 }
 
 const double* colptr(const nll_model* m, int c) { return m->d_ev ? m->d_ev + (size_t)c * m->n_pad : nullptr; }
+
+// column c and the weights as the kernels read them (the event store, or the caller's buffers)
+const double* evcol(const nll_model* m, int c)
+{
+    if (m->in_place) return c < m->ndim ? m->ip_col[c] : nullptr;
+    return c < m->ncols ? colptr(m, c) : nullptr;
+}
+const double* evw(const nll_model* m) { return !m->weighted ? nullptr : (m->in_place ? m->ip_w : m->d_w); }
 
 // N1 = 1/2 [erf(za) - erf(zb)] with za = (mu-ma)/(sqrt2 sigma), zb = (mu-mb)/(sqrt2 sigma)
 // (paper Eq. 2); evaluated with erfc on the side where both arguments share a sign.
@@ -299,17 +310,26 @@ int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int
 {
     KArgs a;
     memset(&a, 0, sizeof a);
-    for (int c = 0; c < kNumCols; ++c) a.col[c] = c < m->ncols ? colptr(m, c) : nullptr;
-    a.w = m->weighted ? m->d_w : nullptr;
+    for (int c = 0; c < kNumCols; ++c) a.col[c] = evcol(m, c);
+    a.w = evw(m);
     a.n = m->n;
     a.c = H.k;
+    if (m->in_place) {
+        a.ma = m->ranges[0];
+        for (int d = 0; d < m->ndim; ++d) {
+            a.klo[d] = order_key_host(m->ranges[2 * d]);
+            a.khi[d] = order_key_host(m->ranges[2 * d + 1]);
+        }
+        a.klo[4] = order_key_host(-0.0);
+        a.khi[4] = order_key_host(1.0e300);
+    }
     a.partials = m->d_partials;
     a.ticket = m->d_ticket;
     a.out = m->d_out;
     int blocks = launch_blocks(m, bps, threads);
     cudaError_t e;
     if (record && m->profiling) cudaEventRecord(m->ev0, m->stream);
-    e = launch_fused(m->kind, variant, m->weighted, grad, blocks, threads, m->stream, a);
+    e = launch_fused(m->kind, variant, m->weighted, grad, blocks, threads, m->stream, a, m->in_place);
     if (e != cudaSuccess) return cuda_fail(m, e, "fused kernel launch");
     if (record && m->profiling) cudaEventRecord(m->ev1, m->stream);
     return NLL_OK;
@@ -367,8 +387,9 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
     if (st != NLL_OK) return st;
     m->last = H;
     m->have_last = true;
-    const int K = num_acc(m->kind, grad);
-    double S[kAccMax] = {0};
+    const int KB = num_acc(m->kind, grad);
+    const int K = KB + (m->in_place ? kAccInPlace : 0);
+    double S[kAccModel] = {0};
     if (m->n > 0) {
         int var = effective_variant(m);
         if (var < 0) return fail(m, NLL_ERR_STATE, "precompute variant requested but no basis was built");
@@ -382,6 +403,15 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
             if (cudaEventElapsedTime(&ms, m->ev0, m->ev1) == cudaSuccess) m->last_ms = ms;
         }
         memcpy(S, m->h_out, K * sizeof(double));
+    }
+    if (m->in_place) {  // the statistics a copied load computes once come with every evaluation
+        if (S[KB] != 0.0) {
+            *nll_out = INFINITY;
+            if (grad)
+                for (int k = 0; k < m->npar; ++k) grad_out[k] = NAN;
+            return fail(m, NLL_ERR_ARG, "%.0f event(s) outside the observable ranges or with invalid weights", S[KB]);
+        }
+        m->sum_wdm = S[KB - 1];
     }
     double bad = S[K - 1];
     if (bad != 0.0 || !isfinite(S[0])) {
@@ -417,6 +447,14 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
     if (!theta || !nll_out || !hess_out) return fail(m, NLL_ERR_ARG, "null theta or output");
     if (n_params != m->npar) return fail(m, NLL_ERR_ARG, "expected %d parameters, got %d", m->npar, n_params);
     if (!m->loaded) return fail(m, NLL_ERR_STATE, "no events loaded");
+    if (m->in_place && m->n > 0) {  // range check and sum w (m - ma) come with an evaluation
+        double f, g[18];
+        int st0 = eval_impl(m, theta, n_params, &f, g);
+        if (st0 != NLL_OK) {
+            *nll_out = f;
+            return st0;
+        }
+    }
     Hoist H;
     int st = hoist(m, theta, true, H);
     if (st != NLL_OK) return st;
@@ -434,8 +472,8 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         static_assert(sizeof(HArgs) <= 4096, "kernel parameters");
         HArgs a;
         memset(&a, 0, sizeof a);
-        for (int c = 0; c < kNumCols; ++c) a.col[c] = c < m->ncols ? colptr(m, c) : nullptr;
-        a.w = m->weighted ? m->d_w : nullptr;
+        for (int c = 0; c < kNumCols; ++c) a.col[c] = evcol(m, c);
+        a.w = evw(m);
         a.n = m->n;
         hess_fill_const(m->kind, H, theta, &a.c);
         a.nslots = L.nslots;
@@ -492,6 +530,9 @@ void reset_events(nll_model* m, bool release)
     }
     m->d_w = nullptr;
     m->loaded = m->weighted = m->has_basis = false;
+    m->in_place = false;
+    for (int d = 0; d < 4; ++d) m->ip_col[d] = nullptr;
+    m->ip_w = nullptr;
     m->n = m->n_pad = 0;
     m->ncols = 0;
 }
@@ -569,11 +610,11 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
     cudaError_t e = cudaSuccess;
     m->stream = (cudaStream_t)cuda_stream;  // 0: CUDA's default stream
     m->own_stream = false;
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_partials, sizeof(double) * kAccMax * m->max_blocks);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_partials, sizeof(double) * kAccModel * m->max_blocks);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(m->d_ticket, 0, sizeof(unsigned int));
     // results land in mapped pinned host memory: the grid's last block writes them there
-    if (e == cudaSuccess) e = cudaHostAlloc(&m->h_out, sizeof(double) * kAccMax, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc(&m->h_out, sizeof(double) * kAccModel, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_out, m->h_out, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
@@ -603,6 +644,59 @@ void nll_destroy(nll_model* m)
     delete m;
 }
 
+}  // extern "C"
+
+namespace {
+// In-place sample: check that the device can read every buffer (device memory of this
+// device, pinned or registered host memory, or any host memory where the device reads
+// pageable memory) and that the 128-bit loads are aligned; store nothing.
+int check_readable(nll_model* m, const double* p, const char* what)
+{
+    if (((uintptr_t)p & 15u) != 0) return fail(m, NLL_ERR_ARG, "%s is not 16-byte aligned", what);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(m, NLL_ERR_ARG, "%s: pointer attributes unavailable", what);
+    }
+    if (at.type == cudaMemoryTypeDevice && at.device == m->device) return NLL_OK;
+    if (at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost) return NLL_OK;
+    int pageable = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, m->device);
+    if (at.type == cudaMemoryTypeUnregistered && pageable) return NLL_OK;
+    return fail(m, NLL_ERR_ARG, "%s is not memory the device can read in place", what);
+}
+
+int load_in_place(nll_model* m, const double* const* columns, const double* weights, int64_t n_events)
+{
+    if (n_events > 0) {
+        static const char* names[4] = {"column 0", "column 1", "column 2", "column 3"};
+        for (int d = 0; d < m->ndim; ++d) {
+            int st = check_readable(m, columns[d], names[d]);
+            if (st != NLL_OK) return st;
+        }
+        if (weights) {
+            int st = check_readable(m, weights, "weights");
+            if (st != NLL_OK) return st;
+        }
+        for (int d = 0; d < m->ndim; ++d) m->ip_col[d] = columns[d];
+        m->ip_w = weights;
+    }
+    m->in_place = true;
+    m->n = n_events;
+    m->n_pad = n_events;
+    m->ncols = m->ndim;
+    m->weighted = weights != nullptr;
+    m->sum_w = m->sum_wdm = 0.0;  // sum w (m - ma) comes with every evaluation
+    m->has_basis = false;
+    m->loaded = true;
+    m->err.clear();
+    return NLL_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int nll_load_events(nll_model* m, const double* const* columns, const double* weights, int64_t n_events,
                     int on_device, int precompute)
 {
@@ -610,8 +704,15 @@ int nll_load_events(nll_model* m, const double* const* columns, const double* we
     if (n_events < 0 || (n_events > 0 && !columns)) return fail(m, NLL_ERR_ARG, "bad event count or columns");
     for (int d = 0; d < m->ndim && n_events > 0; ++d)
         if (!columns[d]) return fail(m, NLL_ERR_ARG, "column %d is NULL", d);
+    if (on_device < 0 || on_device > 2) return fail(m, NLL_ERR_ARG, "on_device must be 0, 1 or 2");
     if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
-    cudaStreamSynchronize(m->stream);
+    if (on_device == 2) {
+        // nothing of the model's is written, and every evaluation has finished when it
+        // returned, so no wait for the stream: the caller's earlier work keeps running
+        reset_events(m, false);
+        return load_in_place(m, columns, weights, n_events);
+    }
+    cudaStreamSynchronize(m->stream);  // an evaluation may not run on the store being replaced
     reset_events(m, false);
     const bool basis = (m->kind == kKstar4D) && precompute;
     const int64_t n_pad = std::max<int64_t>((n_events + 63) / 64 * 64, 64);

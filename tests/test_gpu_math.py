@@ -42,3 +42,21 @@ def test_reciprocal_accuracy(gpu_lib):
     ])
     y = gpu_lib.nll_diag_math(1, x)
     assert ulp_err(y, 1.0 / x).max() <= 1.0
+
+
+def test_table_sincos_accuracy(gpu_lib):
+    # the 4D kernels take sin/cos phi from the table method for |phi| <= pi
+    rs = synth.Stream(23, 0)
+    steps = np.arange(-128, 129) * (np.pi / 128)
+    x = np.concatenate([
+        (2 * rs.uniform(300000) - 1) * np.pi,
+        steps, np.nextafter(steps, 10.0), np.nextafter(steps, -10.0),   # around the table points
+        steps + np.pi / 256, steps - np.pi / 256,                       # the reduction's edges
+        np.array([0.0, -0.0, 1e-300, -1e-300, 1e-8, np.pi, -np.pi, np.pi / 2, -np.pi / 2]),
+    ])
+    x = x[np.abs(x) <= np.pi]
+    xl = x.astype(np.longdouble)
+    for fn, ref in ((2, np.sin(xl)), (3, np.cos(xl))):
+        y = gpu_lib.nll_diag_math(fn, x)
+        err = np.abs(y.astype(np.longdouble) - ref) / np.spacing(np.abs(ref).astype(np.float64)).astype(np.longdouble)
+        assert float(err.max()) <= 2.0, (fn, float(err.max()), x[np.argmax(err)])
