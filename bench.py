@@ -63,8 +63,8 @@ FLOPS_PER_EVENT = ARITH_FLOPS_4D + 2.0 * (C_EXP_DFMA + C_RCP_DFMA)
 # FP64-pipe peak is the same 2 DFMA/clk/SM.
 FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of one fused-kernel launch (dram__bytes_read.sum + dram__bytes_write.sum,
-# one ncu capture of the current kernel at 152 x 256, profiles/fused_nll_kstar4d_1M.md).
-KERNEL_TRAFFIC_BYTES = 131.9e6
+# one ncu capture of the current kernel at 304 x 192, profiles/fused_nll_kstar4d_1M.md).
+KERNEL_TRAFFIC_BYTES = 132.0e6
 
 
 def parse():
