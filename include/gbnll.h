@@ -134,7 +134,7 @@ typedef struct {
                        2: the same with the analytic Hessian, covariance H^-1;
                        3: as 2, covariance H^-1 W H^-1 (weighted fits, see nll_eval_hess).
                        Values 2 and 3 (and strategy 2) need a model: fit_minimise_fcn and the
-                       batched fits reject them with NLL_ERR_ARG.                              */
+                       served fits reject them with NLL_ERR_ARG.                               */
 } fit_options;
 
 #define FIT_MAXPAR 32
@@ -324,9 +324,12 @@ int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, dou
  * nll_batch_fit -- minimise every toy's NLL on the device (see above).
  *   theta0       host [n_toys][npar] start points, or [npar] shared by all toys if
  *                shared_start != 0; lo, hi, step, fixed as fit_minimise (shared by all toys).
- *   opt          tol_edm, max_iter, strategy (1: start from a finite-difference Hessian),
- *                hessian (1: finite-difference Hessian of the analytic gradient at the minimum
- *                for the covariance; 0: covariance from the BFGS matrix).
+ *   opt          tol_edm, max_iter, strategy (1: start from a finite-difference Hessian;
+ *                2: from the analytic Hessian of every toy, one batched pass before the
+ *                loop), hessian (1: finite-difference Hessian of the analytic gradient at the
+ *                minimum for the covariance; 2: analytic Hessian, covariance H^-1; 3: as 2,
+ *                covariance H^-1 W H^-1 for weighted toys -- one batched pass after the loop,
+ *                no Newton polish; 0: covariance from the BFGS matrix).
  *   results      host array of n_toys fit_result.
  *   steps_out    number of graph replays (device steps) used, or NULL.
  * Returns NLL_OK when every toy converged, else NLL_ERR_NOT_CONVERGED (see results[].status).
@@ -334,6 +337,20 @@ int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, dou
 int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
                   const double* step, const int* fixed, const fit_options* opt, fit_result* results,
                   int* steps_out);
+
+/*
+ * nll_batch_eval_hess -- NLL, gradient, analytic Hessian (and optionally W = sum w^2 s s^T)
+ * of every toy at its own parameter point, in one device pass (the per-toy version of
+ * nll_eval_hess; paper Sec. 2.1).
+ *   thetas       host [n_toys][n_params], or one shared point if shared != 0.
+ *   nll_out      host [n_toys]; grad_out host [n_toys][n_params] or NULL;
+ *   hess_out     host [n_toys][n_params][n_params]; w2_out the same layout, or NULL.
+ *   status_out   host [n_toys] nll_status per toy (NLL_ERR_ARG: invalid parameter point;
+ *                NLL_ERR_NONPOSITIVE_PDF: density not positive), or NULL.
+ * Returns the first non-OK toy status, or NLL_OK; the outputs of such toys are +inf / NaN.
+ */
+int nll_batch_eval_hess(nll_batch* b, const double* thetas, int shared, double* nll_out, double* grad_out,
+                        double* hess_out, double* w2_out, int* status_out);
 
 /* Schedule: tile_events = 0 (CTA-per-toy) or > 0 (split-toy, multiple of 2);
  * blocks_per_sm of the persistent evaluation kernel (0 keeps the value). */

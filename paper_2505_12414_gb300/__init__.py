@@ -99,6 +99,7 @@ def load(path=None):
     L.nll_batch_create.argtypes = [ctypes.c_int, _DP, ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(vp)]
     L.nll_batch_load.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.POINTER(vp), vp, ctypes.c_int]
     L.nll_batch_eval_grad.argtypes = [vp, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int)]
+    L.nll_batch_eval_hess.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int)]
     L.nll_batch_fit.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(fit_options), ctypes.POINTER(fit_result), ctypes.POINTER(ctypes.c_int)]
     L.nll_batch_set_schedule.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -582,6 +583,25 @@ class Batch:
         stv = np.zeros(self.n_toys, dtype=np.int32)
         load().nll_batch_eval_grad(self.handle, _p(th), _p(nll), _p(g), stv.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         return nll, g, stv
+
+    def eval_hess(self, thetas, w2=False):
+        """Per-toy (nll [n], grad [n, np], H [n, np, np][, W], status [n]) in one device pass;
+        thetas is [n, np] or one shared [np] point."""
+        t = np.asarray(thetas, dtype=np.float64)
+        shared = 1 if t.ndim == 1 else 0
+        th = _f64(t)
+        n, npar = self.n_toys, self.npar
+        nll = np.zeros(max(n, 1))
+        g = np.zeros((max(n, 1), npar))
+        H = np.zeros((max(n, 1), npar, npar))
+        W = np.zeros((max(n, 1), npar, npar)) if w2 else None
+        st = np.zeros(max(n, 1), dtype=np.int32)
+        r = load().nll_batch_eval_hess(self.handle, _p(th), shared, _p(nll), _p(g), _p(H), _p(W) if w2 else None,
+                                       st.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        if r not in (NLL_OK, NLL_ERR_NONPOSITIVE_PDF, NLL_ERR_ARG):
+            _bcheck(self.handle, r)
+        out = (nll[:n], g[:n], H[:n]) + ((W[:n],) if w2 else ()) + (st[:n],)
+        return out
 
     def fit(self, theta0, lo=None, hi=None, step=None, fixed=None, tol_edm=1e-8, max_iter=500, strategy=1,
             hessian=1):

@@ -31,6 +31,7 @@
 #include "../../include/gbnll.h"
 #include "fp64_math.cuh"
 #include "gbnll_internal.h"
+#include "hess_device.cuh"
 #include "nll_device.cuh"
 
 namespace gbnll {
@@ -49,12 +50,14 @@ enum Phase : int { kPhInit = 0, kPhSearch = 1, kPhHess = 2, kPhDone = 3 };
 // Derivative constants of one parameter point (device copy of the host Hoist fields).
 struct DConst {
     double mu, sigma, alpha, f, ma, b0, b2, dlnN1_dmu, dlnN1_dsig, dlnN2t_dal, dlnNc[3];
+    double lnb1, d2lnN1[3], d2lnN2t_dal2;  // for the analytic Hessian
     int ok;
 };
 
 // Minimiser state of one toy (device).
 struct ToyFit {
     int phase, iter, n_eval, status, first;
+    int vset;  // the start matrix V came from the analytic Hessian (strategy 2)
     double f, ft, edm, alpha, gp;
     double x[kNP], g[kNP], p[kNP], xt[kNP], sint[kNP], hstep[kNP];
     double th[kNP];    // external parameters of the accepted point (all npar)
@@ -123,7 +126,37 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
     double ea = exp(-za * za), eb = exp(-zb * zb);
     H.dlnN1_dmu = (ea - eb) / (sqrt(2.0 * kPiH) * sigma * N1);
     H.dlnN1_dsig = -(za * ea - zb * eb) / (sqrt(kPiH) * sigma * N1);
+    {  // second derivatives of ln N1 (as the host hoisting)
+        const double s2 = sigma * sigma;
+        H.d2lnN1[0] = -(za * ea - zb * eb) / (sqrt(kPiH) * s2 * N1) - H.dlnN1_dmu * H.dlnN1_dmu;
+        H.d2lnN1[1] = (ea * (2.0 * za * za - 1.0) - eb * (2.0 * zb * zb - 1.0)) / (sqrt(2.0 * kPiH) * s2 * N1) -
+                      H.dlnN1_dmu * H.dlnN1_dsig;
+        H.d2lnN1[2] = 2.0 * (za * ea * (1.0 - za * za) - zb * eb * (1.0 - zb * zb)) / (sqrt(kPiH) * s2 * N1) -
+                      H.dlnN1_dsig * H.dlnN1_dsig;
+    }
     double t = alpha * D, Nt2;
+    {  // d^2 ln Ntilde2 / dalpha^2 = D^2 v(|t|), v(a) = 1/a^2 - e^-a/(1 - e^-a)^2, series below 1/2
+        const double a = fabs(t);
+        double v;
+        if (a < 0.5) {
+            const double c[9] = {1.0 / 12.0,
+                                 -1.0 / 240.0,
+                                 1.0 / 6048.0,
+                                 -1.0 / 172800.0,
+                                 9.0 * (5.0 / 66.0) / 3628800.0,
+                                 11.0 * (-691.0 / 2730.0) / 479001600.0,
+                                 13.0 * (7.0 / 6.0) / 87178291200.0,
+                                 15.0 * (-3617.0 / 510.0) / 20922789888000.0,
+                                 17.0 * (43867.0 / 798.0) / 6402373705728000.0};
+            const double a2 = a * a;
+            v = c[8];
+            for (int q = 7; q >= 0; --q) v = fma(v, a2, c[q]);
+        } else {
+            const double em = expm1(-a);
+            v = 1.0 / (a * a) - exp(-a) / (em * em);
+        }
+        H.d2lnN2t_dal2 = D * D * v;
+    }
     if (alpha == 0.0) {
         Nt2 = D;
         H.dlnN2t_dal = 0.5 * D;
@@ -153,6 +186,7 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
     H.ma = ma;
     H.b0 = b0;
     H.b2 = b2;
+    H.lnb1 = lnb1;
     const double S = kExpArgScale;
     k.mu = mu;
     k.neg_b0 = -b0 * S;
@@ -273,7 +307,7 @@ __global__ void batch_prepare(BatchDev b)
     if (F.phase == kPhInit || F.phase == kPhSearch) {
         for (int i = 0; i < c.nf; ++i) th[c.idx[i]] = to_ext(c, i, F.xt[i]);
         emit_item(b, t, 0, th, npairs);
-        if (F.phase == kPhInit && c.strategy) {
+        if (F.phase == kPhInit && c.strategy == 1) {
             // stencil in internal coordinates around the start point
             for (int j = 0; j < c.nf; ++j)
                 for (int sgn = 0; sgn < 2; ++sgn) {
@@ -478,7 +512,9 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
             if (lane == 0) F.f = f0;
             // initial inverse Hessian: diag(step^2), or the inverse of the stencil Hessian
             bool have = false;
-            if (c.strategy && sten_ok) {
+            if (c.strategy == 2) {
+                have = F.vset != 0;  // set by the analytic Hessian pass before the first step
+            } else if (c.strategy && sten_ok) {
                 for (int j = 0; j < nf; ++j) {
                     double h = 0.1 * F.sint[j];
                     if (mine) {
@@ -504,6 +540,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
             }
             if (!have && mine)
                 for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? F.sint[lane] * F.sint[lane] : 0.0;
+            __syncwarp();
             if (lane == 0) F.first = have ? 0 : 1;
             __syncwarp();
             // direction
@@ -671,6 +708,356 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
     }
 }
 
+// ---------------------------------------------------------------------------------
+// analytic Hessian pass over all toys (paper Sec. 2.1): the start matrix of strategy 2,
+// the covariance of hessian 2 / 3, and nll_batch_eval_hess.  The per-event work is the
+// single-sample Hessian pass (hess_device.cuh) over (toy, 4096-event) units; a warp per
+// toy then sums its units in order, assembles H (and W) and inverts.
+// ---------------------------------------------------------------------------------
+constexpr int kHessUnitEvents = 4096;
+
+enum HessMode : int { kHmEval = 0, kHmStart = 1, kHmCov = 2, kHmSandwich = 3 };
+
+struct HessDev {
+    int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
+    const int64_t* ev_begin;
+    const int64_t* ev_end;
+    const double* sum_wdm;
+    HEv ev;                     // columns and weights; n is set per unit
+    ToyFit* fits;
+    const double* thetas;       // kHmEval: [n_toys][npar]
+    HConst* hc;                 // per toy
+    HessTerms* ht;              // per toy
+    int* hok;                   // per toy: parameter point valid
+    const int* unit_toy;        // per unit
+    const int64_t* unit_e0;     // per unit: first event
+    const int* toy_u0;          // per toy: first unit
+    const int* toy_nu;          // per toy: units
+    double* unit_sums;          // [n_units][nslots]
+    const uint16_t* slot_of;    // [ncols][ncols] -> slot, 0xffff = none
+    double* out;                // kHmEval: per toy nll, grad[np], H[np*np], W[np*np]
+    int* status;                // kHmEval: per toy
+    FitConfig cfg;
+    uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];
+};
+
+struct DevSlots {
+    const double* sums;
+    const uint16_t* slot_of;
+    int nc;
+    __device__ double operator()(int i, int j) const
+    {
+        const unsigned s = slot_of[i * nc + j];
+        return s == 0xffffu ? NAN : sums[s];
+    }
+};
+
+// thread per toy: the toy's parameter point and its parameter-only terms
+__global__ void batch_hess_prep(HessDev h)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= h.n_toys) return;
+    const FitConfig& c = h.cfg;
+    const int np = c.npar;
+    double th[kNP];
+    bool use = true;
+    if (h.mode == kHmEval) {
+        for (int k = 0; k < np; ++k) th[k] = h.thetas[(size_t)t * np + k];
+    } else {
+        const ToyFit& F = h.fits[t];
+        for (int k = 0; k < np; ++k) th[k] = F.th[k];
+        if (h.mode != kHmStart) use = F.phase == kPhDone && F.status == NLL_OK;
+    }
+    KConst kc;
+    DConst dc;
+    memset(&kc, 0, sizeof kc);
+    memset(&dc, 0, sizeof dc);
+    const bool ok = use && dev_hoist(c.kind, c.ranges, th, kc, dc);
+    h.hok[t] = ok ? 1 : 0;
+    if (!ok) return;
+    HConst hc;
+    memset(&hc, 0, sizeof hc);
+    hc.mu = dc.mu;
+    hc.b0 = dc.b0;
+    hc.neg_b0s = kc.neg_b0;
+    hc.neg_als = kc.neg_alpha;
+    hc.k0s = kc.k0;
+    hc.b2 = dc.b2;
+    hc.inv_sigma = 1.0 / dc.sigma;
+    hc.dlnN1_dmu = dc.dlnN1_dmu;
+    hc.dlnN1_dsig = dc.dlnN1_dsig;
+    hc.mu_ma = dc.mu - dc.ma;
+    hc.dlnN2t_dal = dc.dlnN2t_dal;
+    hc.inv_f = 1.0 / dc.f;
+    hc.inv_1mf = 1.0 / (1.0 - dc.f);
+    if (c.kind == kKstar4D) {
+        for (int k = 0; k < 8; ++k) hc.ang[k] = th[2 + k];
+        for (int j = 0; j < 3; ++j) {
+            hc.c1[j] = th[11 + 2 * j];
+            hc.c2[j] = th[12 + 2 * j];
+            hc.dl[j] = dc.dlnNc[j];
+        }
+    }
+    h.hc[t] = hc;
+    HessTerms T;
+    T.alpha = dc.alpha;
+    T.f = dc.f;
+    T.sigma = dc.sigma;
+    T.b0 = dc.b0;
+    for (int k = 0; k < 3; ++k) {
+        T.d2lnN1[k] = dc.d2lnN1[k];
+        T.dlnNc_dc2[k] = dc.dlnNc[k];
+    }
+    T.d2lnN2t_dal2 = dc.d2lnN2t_dal2;
+    h.ht[t] = T;
+}
+
+// persistent blocks over units: unit u covers events [e0, min(e0 + 4096, end)) of its toy
+template <int KIND, int VAR, bool W>
+__global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h)
+{
+    extern __shared__ double z[];
+    __shared__ double s_tab[kTabDoubles];
+    __shared__ HConst s_c;
+    __shared__ double s_lnp[kHessThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_btab[j];
+    const int ns = h.nslots;
+    const int w0 = t & ~31;
+    const int nrow = ns > w0 ? min(3, (ns - w0 + kHessThreads - 1) / kHessThreads) : 0;
+    int ci[3], cj[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int sl = t + k * kHessThreads;
+        const int sc = sl < ns ? sl : 0;
+        ci[k] = h.si[sc];
+        cj[k] = h.sj[sc];
+    }
+    for (int u = blockIdx.x; u < h.n_units; u += gridDim.x) {
+        const int toy = h.unit_toy[u];
+        const bool ok = h.hok[toy] != 0;  // uniform over the block
+        __syncthreads();                  // s_c and z of the previous unit are no longer read
+        if (t == 0 && ok) s_c = h.hc[toy];
+        HEv ev = h.ev;
+        const int64_t e0 = h.unit_e0[u];
+        ev.n = min(e0 + (int64_t)kHessUnitEvents, h.ev_end[toy]);
+        __syncthreads();
+        double acc[3] = {0.0, 0.0, 0.0};
+        LogProd lp{1.0, 0};
+        if (ok) {
+            for (int64_t e = e0; e < ev.n; e += kHessThreads) {
+                stage_event<KIND, VAR, W>(ev, s_c, e + t, z, t, s_tab, lp);
+                __syncthreads();
+                if (nrow == 1)
+                    tile_slots<1>(z, ci, cj, acc, lane);
+                else if (nrow == 2)
+                    tile_slots<2>(z, ci, cj, acc, lane);
+                else if (nrow == 3)
+                    tile_slots<3>(z, ci, cj, acc, lane);
+                __syncthreads();
+            }
+            if (!W) {  // sum over the block of ln(products) into the ln P slot
+                double v = logprod_value(lp);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) s_lnp[warp] = v;
+                __syncthreads();
+                const int ls = h.lnp_slot;
+                if (ls >= 0 && t == (ls & (kHessThreads - 1))) {
+                    const double tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
+                    const int row = ls / kHessThreads;
+                    if (row == 0)
+                        acc[0] += tot;
+                    else if (row == 1)
+                        acc[1] += tot;
+                    else
+                        acc[2] += tot;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int sl = t + k * kHessThreads;
+            if (sl < ns) h.unit_sums[(size_t)u * ns + sl] = acc[k];
+        }
+    }
+}
+
+// warp per toy: slot totals (units in order), assembly, and the mode's matrix work
+// (two warps per block: 37.5 KB of static shared memory for the 18-parameter model)
+constexpr int kFinWarps = 2;
+
+template <int KIND, bool W>
+__global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDev h)
+{
+    constexpr int NPK = KIND == kMass1D ? 4 : 18;
+    __shared__ double s_sum[kFinWarps][kHessMaxSlots];
+    __shared__ double s_H[kFinWarps][NPK * NPK];
+    __shared__ double s_W[kFinWarps][NPK * NPK];
+    __shared__ double s_mat[kFinWarps][4][NPK * NPK];
+    __shared__ double s_g[kFinWarps][NPK];
+    __shared__ double s_nll[kFinWarps];
+    __shared__ int s_bad[kFinWarps];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = blockIdx.x * kFinWarps + wib;
+    if (t >= h.n_toys) return;
+    const FitConfig& c = h.cfg;
+    const int np = c.npar, nf = c.nf;
+    const bool mine = lane < nf;
+    if (!h.hok[t]) {
+        if (h.mode == kHmEval) {
+            if (lane == 0) h.status[t] = NLL_ERR_ARG;
+            double* o = h.out + (size_t)t * (1 + np + 2 * np * np);
+            for (int k = lane; k < 1 + np + 2 * np * np; k += 32) o[k] = k == 0 ? INFINITY : NAN;
+        }
+        return;
+    }
+    const int u0 = h.toy_u0[t], nu = h.toy_nu[t];
+    for (int sl = lane; sl < h.nslots; sl += 32) {
+        double v = 0.0;
+        for (int j = 0; j < nu; ++j) v += h.unit_sums[(size_t)(u0 + j) * h.nslots + sl];
+        s_sum[wib][sl] = v;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        DevSlots S{s_sum[wib], h.slot_of, h.ncols};
+        double bad = assemble_t<KIND, W>(h.ht[t], h.sum_wdm[t], h.want_w2 != 0, S, &s_nll[wib], s_g[wib], s_H[wib],
+                                         s_W[wib]);
+        s_bad[wib] = (bad != 0.0 || !isfinite(s_nll[wib])) ? 1 : 0;
+    }
+    __syncwarp();
+    const bool bad = s_bad[wib] != 0;
+    if (h.mode == kHmEval) {
+        double* o = h.out + (size_t)t * (1 + np + 2 * np * np);
+        if (lane == 0) {
+            h.status[t] = bad ? NLL_ERR_NONPOSITIVE_PDF : NLL_OK;
+            o[0] = bad ? INFINITY : s_nll[wib];
+        }
+        for (int k = lane; k < np; k += 32) o[1 + k] = bad ? NAN : s_g[wib][k];
+        for (int k = lane; k < np * np; k += 32) {
+            o[1 + np + k] = bad ? NAN : s_H[wib][k];
+            o[1 + np + np * np + k] = (bad || !h.want_w2) ? NAN : s_W[wib][k];
+        }
+        return;
+    }
+    if (bad) return;  // keep what the minimiser has (diagonal start, BFGS covariance)
+    ToyFit& F = h.fits[t];
+    double* A = s_mat[wib][0];
+    double* Lm = s_mat[wib][1];
+    double* Mm = s_mat[wib][2];
+    double* Out = s_mat[wib][3];
+    if (mine)
+        for (int j = 0; j < nf; ++j) A[lane * nf + j] = s_H[wib][c.idx[lane] * np + c.idx[j]];
+    __syncwarp();
+    if (h.mode == kHmStart) {
+        // internal coordinates: J H J + diag(dNLL/dext d2ext/dx2) (sine transform)
+        const double xi = mine ? F.xt[lane] : 0.0;
+        const double Ji = mine ? jac(c, lane, xi) : 0.0;
+        for (int j = 0; j < nf; ++j) {
+            const double Jj = __shfl_sync(0xffffffffu, Ji, j);
+            if (mine) A[lane * nf + j] *= Ji * Jj;
+        }
+        if (mine && c.bounded[c.idx[lane]]) {
+            const int k = c.idx[lane];
+            A[lane * nf + lane] += s_g[wib][k] * (-(c.hi[k] - c.lo[k]) * 0.5 * sin(xi));
+        }
+        __syncwarp();
+        if (warp_spd_inverse(nf, A, Lm, Mm, Out)) {
+            if (mine)
+                for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = Out[lane * nf + j];
+            if (lane == 0) F.vset = 1;
+        }
+        if (lane == 0) F.n_eval += 1;
+        return;
+    }
+    // covariance at the minimum: H^-1, or H^-1 W H^-1
+    const bool inv = warp_spd_inverse(nf, A, Lm, Mm, Out);
+    if (lane == 0) F.n_eval += 1;
+    if (!inv) return;  // the BFGS covariance stays
+    if (h.mode == kHmSandwich) {
+        double* Wf = Lm;  // reuse: W (free block), then T = Hi W
+        if (mine)
+            for (int j = 0; j < nf; ++j) Wf[lane * nf + j] = s_W[wib][c.idx[lane] * np + c.idx[j]];
+        __syncwarp();
+        if (mine)
+            for (int j = 0; j < nf; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < nf; ++k) acc += Out[lane * nf + k] * Wf[k * nf + j];
+                Mm[lane * nf + j] = acc;
+            }
+        __syncwarp();
+        if (mine)
+            for (int j = 0; j < nf; ++j) {
+                double acc = 0.0;
+                for (int k = 0; k < nf; ++k) acc += Mm[lane * nf + k] * Out[k * nf + j];
+                F.cov[lane * nf + j] = acc;
+            }
+    } else if (mine) {
+        for (int j = 0; j < nf; ++j) F.cov[lane * nf + j] = Out[lane * nf + j];
+    }
+    __syncwarp();
+    // EDM with the Hessian (as the single-sample minimiser reports it)
+    const double ge = mine ? F.gext[lane] : 0.0;
+    double hg = 0.0;
+    if (mine)
+        for (int j = 0; j < nf; ++j) hg += Out[lane * nf + j] * __shfl_sync(0xffffffffu, ge, j);
+    else
+        for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, ge, j);
+    const double edm = 0.5 * wsum(mine ? ge * hg : 0.0);
+    if (lane == 0) F.edm = edm;
+    if (mine) F.err[lane] = sqrt(fmax(F.cov[lane * nf + lane], 0.0));
+}
+
+template <int KIND, int VAR, bool W>
+size_t hess_units_smem()
+{
+    return (size_t)HCols<KIND, W>::NC * kHessThreads * sizeof(double);
+}
+
+template <int KIND, int VAR, bool W>
+cudaError_t launch_hess_units_t(int blocks, cudaStream_t s, const HessDev& h)
+{
+    const size_t smem = hess_units_smem<KIND, VAR, W>();
+    cudaError_t e =
+        cudaFuncSetAttribute(batch_hess_units<KIND, VAR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_hess_units<KIND, VAR, W><<<blocks, kHessThreads, smem, s>>>(h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStream_t s, const HessDev& h)
+{
+    batch_hess_prep<<<(h.n_toys + 127) / 128, 128, 0, s>>>(h);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (h.n_units > 0) {
+        if (kind == kMass1D)
+            e = w ? launch_hess_units_t<kMass1D, kVarPrecompute, true>(unit_blocks, s, h)
+                  : launch_hess_units_t<kMass1D, kVarPrecompute, false>(unit_blocks, s, h);
+        else if (var == kVarDirect)
+            e = w ? launch_hess_units_t<kKstar4D, kVarDirect, true>(unit_blocks, s, h)
+                  : launch_hess_units_t<kKstar4D, kVarDirect, false>(unit_blocks, s, h);
+        else
+            e = w ? launch_hess_units_t<kKstar4D, kVarPrecompute, true>(unit_blocks, s, h)
+                  : launch_hess_units_t<kKstar4D, kVarPrecompute, false>(unit_blocks, s, h);
+        if (e != cudaSuccess) return e;
+    }
+    const int fb = (h.n_toys + kFinWarps - 1) / kFinWarps;
+    if (kind == kMass1D) {
+        if (w)
+            batch_hess_finish<kMass1D, true><<<fb, kFinWarps * 32, 0, s>>>(h);
+        else
+            batch_hess_finish<kMass1D, false><<<fb, kFinWarps * 32, 0, s>>>(h);
+    } else {
+        if (w)
+            batch_hess_finish<kKstar4D, true><<<fb, kFinWarps * 32, 0, s>>>(h);
+        else
+            batch_hess_finish<kKstar4D, false><<<fb, kFinWarps * 32, 0, s>>>(h);
+    }
+    return cudaGetLastError();
+}
+
 template <int KIND, int VAR, bool W>
 cudaError_t launch_eval_t(int blocks, cudaStream_t s, const BatchDev& b)
 {
@@ -741,6 +1128,21 @@ struct nll_batch {
     int* d_unit_tile = nullptr;
     double* d_unit_sums = nullptr;
     ToyFit* d_fits = nullptr;
+    // analytic Hessian pass (allocated at its first use for the loaded toys)
+    bool hess_ready = false;
+    int n_hunits = 0;
+    int* d_hunit_toy = nullptr;
+    int64_t* d_hunit_e0 = nullptr;
+    int* d_htoy_u0 = nullptr;
+    int* d_htoy_nu = nullptr;
+    HConst* d_hc = nullptr;
+    HessTerms* d_ht = nullptr;
+    int* d_hok = nullptr;
+    double* d_hunit_sums = nullptr;
+    uint16_t* d_slot_of = nullptr;
+    double* d_hthetas = nullptr;
+    double* d_hout = nullptr;
+    int* d_hstatus = nullptr;
     // schedule
     int tile_events = 0, bps = 2;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -768,8 +1170,25 @@ int bcuda(nll_batch* b, cudaError_t e, const char* what)
                  cudaGetErrorString(e));
 }
 
+void free_hess_work(nll_batch* b)
+{
+    void* ptrs[] = {b->d_hunit_toy, b->d_hunit_e0, b->d_htoy_u0, b->d_htoy_nu, b->d_hc, b->d_ht, b->d_hok,
+                    b->d_hunit_sums, b->d_slot_of, b->d_hthetas, b->d_hout, b->d_hstatus};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    b->d_hunit_toy = b->d_htoy_u0 = b->d_htoy_nu = b->d_hok = b->d_hstatus = nullptr;
+    b->d_hunit_e0 = nullptr;
+    b->d_hc = nullptr;
+    b->d_ht = nullptr;
+    b->d_hunit_sums = b->d_hthetas = b->d_hout = nullptr;
+    b->d_slot_of = nullptr;
+    b->n_hunits = 0;
+    b->hess_ready = false;
+}
+
 void free_work(nll_batch* b)
 {
+    free_hess_work(b);
     void* ptrs[] = {b->d_ev, b->d_begin, b->d_end, b->d_sum_wdm, b->d_item_toy, b->d_item_u0, b->d_item_nt,
                     b->d_item_kc, b->d_item_dc, b->d_unit_item, b->d_unit_tile, b->d_unit_sums, b->d_fits};
     for (void* p : ptrs)
@@ -914,6 +1333,110 @@ int eval_all(nll_batch* b, const double* thetas, double* nll_out, double* grad_o
 
 
 
+// work arrays of the Hessian pass for the loaded toys: units of 4096 events per toy
+int ensure_hess_work(nll_batch* b)
+{
+    if (b->hess_ready) return NLL_OK;
+    const int n = b->n_toys, np = b->npar;
+    std::vector<int> unit_toy, toy_u0(std::max(n, 1)), toy_nu(std::max(n, 1));
+    std::vector<int64_t> unit_e0;
+    for (int t = 0; t < n; ++t) {
+        toy_u0[t] = (int)unit_toy.size();
+        for (int64_t e = b->begin[t]; e < b->end[t]; e += kHessUnitEvents) {
+            unit_toy.push_back(t);
+            unit_e0.push_back(e);
+        }
+        toy_nu[t] = (int)unit_toy.size() - toy_u0[t];
+    }
+    const size_t nu = std::max<size_t>(unit_toy.size(), 1), nt = std::max(n, 1);
+    cudaError_t e = cudaMalloc(&b->d_hunit_toy, sizeof(int) * nu);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hunit_e0, sizeof(int64_t) * nu);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_htoy_u0, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_htoy_nu, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hc, sizeof(HConst) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_ht, sizeof(HessTerms) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hok, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hunit_sums, sizeof(double) * kHessMaxSlots * nu);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_slot_of, sizeof(uint16_t) * 64 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hthetas, sizeof(double) * np * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hout, sizeof(double) * (1 + np + 2 * np * np) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_hstatus, sizeof(int) * nt);
+    if (e == cudaSuccess && !unit_toy.empty())
+        e = cudaMemcpyAsync(b->d_hunit_toy, unit_toy.data(), sizeof(int) * unit_toy.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess && !unit_e0.empty())
+        e = cudaMemcpyAsync(b->d_hunit_e0, unit_e0.data(), sizeof(int64_t) * unit_e0.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_htoy_u0, toy_u0.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_htoy_nu, toy_nu.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        free_hess_work(b);
+        return bcuda(b, e, "Hessian work arrays");
+    }
+    b->n_hunits = (int)unit_toy.size();
+    b->hess_ready = true;
+    return NLL_OK;
+}
+
+// One Hessian pass over all toys on the batch's stream.  kHmEval takes the host thetas
+// ([n_toys][npar]) and leaves per-toy results in d_hout / d_hstatus; the other modes read
+// and write the toys' fit states (the fits must be on the device).
+int run_hess_pass(nll_batch* b, const FitConfig& cfg, int mode, bool want_w2, const double* thetas)
+{
+    int st = ensure_hess_work(b);
+    if (st != NLL_OK) return st;
+    HessLayout L;
+    if (!hess_layout(b->kind, b->weighted, want_w2, &L)) return bfail(b, NLL_ERR_ARG, "Hessian slot table overflow");
+    std::vector<uint16_t> slot_of(64 * 64, 0xffff);
+    for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * L.ncols + L.sj[k]] = (uint16_t)k;
+    const int n = b->n_toys, np = b->npar;
+    cudaError_t e = cudaMemcpyAsync(b->d_slot_of, slot_of.data(), sizeof(uint16_t) * slot_of.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && mode == kHmEval)
+        e = cudaMemcpyAsync(b->d_hthetas, thetas, sizeof(double) * np * n, cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "Hessian pass upload");
+    HessDev h;
+    memset(&h, 0, sizeof h);
+    h.n_toys = n;
+    h.mode = mode;
+    h.want_w2 = want_w2 ? 1 : 0;
+    h.n_units = b->n_hunits;
+    h.nslots = L.nslots;
+    h.lnp_slot = L.lnp_slot;
+    h.ncols = L.ncols;
+    h.ev_begin = b->d_begin;
+    h.ev_end = b->d_end;
+    h.sum_wdm = b->d_sum_wdm;
+    for (int c = 0; c < kNumCols; ++c) h.ev.col[c] = c < b->ncols ? b->d_ev + (size_t)c * b->n_pad : nullptr;
+    h.ev.w = b->weighted ? b->d_w : nullptr;
+    h.fits = b->d_fits;
+    h.thetas = b->d_hthetas;
+    h.hc = b->d_hc;
+    h.ht = b->d_ht;
+    h.hok = b->d_hok;
+    h.unit_toy = b->d_hunit_toy;
+    h.unit_e0 = b->d_hunit_e0;
+    h.toy_u0 = b->d_htoy_u0;
+    h.toy_nu = b->d_htoy_nu;
+    h.unit_sums = b->d_hunit_sums;
+    h.slot_of = b->d_slot_of;
+    h.out = b->d_hout;
+    h.status = b->d_hstatus;
+    h.cfg = cfg;
+    memcpy(h.si, L.si, sizeof h.si);
+    memcpy(h.sj, L.sj, sizeof h.sj);
+    static_assert(sizeof(HessDev) <= 4096, "kernel parameters");
+    const int occ = hess_occupancy(b->kind, variant_of(b), b->weighted);
+    const int unit_blocks = std::max(1, std::min(b->n_hunits, b->sm_count * std::max(1, std::min(occ, 4))));
+    e = launch_hess_pass(b->kind, variant_of(b), b->weighted, unit_blocks, b->stream, h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "Hessian pass");
+    return NLL_OK;
+}
+
 // after the events are in d_ev: angular basis, per-toy arrays and work arrays sized for the
 // largest step (every toy with a full stencil); device_sums computes sum (m - ma) per toy
 // on the device instead of uploading b->sum_wdm
@@ -996,8 +1519,8 @@ cudaError_t finish_store(nll_batch* b, bool basis, int64_t pos, bool device_sums
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
                   const fit_options& opt)
 {
-    c.strategy = opt.strategy >= 1;
-    c.hessian = opt.hessian >= 1;
+    c.strategy = opt.strategy;          // 2: start matrix from the analytic Hessian pass
+    c.hessian = opt.hessian == 1;       // in-loop finite-difference Hessian; 2/3 run after the loop
     c.max_iter = opt.max_iter;
     c.tol_edm = opt.tol_edm;
     int nf = 0;
@@ -1342,8 +1865,8 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         memset(&opt, 0, sizeof opt);
     if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
     if (opt.max_iter <= 0) opt.max_iter = 500;
-    if (opt.strategy < 0 || opt.strategy > 1 || opt.hessian < 0 || opt.hessian > 1)
-        return bfail(b, NLL_ERR_ARG, "batched fits take strategy 0/1 and hessian 0/1 (finite-difference Hessian)");
+    if (opt.strategy < 0 || opt.strategy > 2 || opt.hessian < 0 || opt.hessian > 3)
+        return bfail(b, NLL_ERR_ARG, "strategy must be 0..2 and hessian 0..3");
     const int n = b->n_toys, np = b->npar;
     if (n == 0) return NLL_OK;
     BatchDev d = make_dev(b);
@@ -1357,6 +1880,10 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_fits, fits.data(), sizeof(ToyFit) * n, cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit state upload");
+    if (opt.strategy == 2) {  // start matrices from the analytic Hessian at every toy's start point
+        int st = run_hess_pass(b, c, kHmStart, false, nullptr);
+        if (st != NLL_OK) return st;
+    }
 
     // one device step = counter reset, prepare, evaluate, update; captured once
     const int eval_blocks = b->sm_count * b->bps;
@@ -1393,6 +1920,10 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return bcuda(b, e, "fit loop");
     if (steps_out) *steps_out = steps;
+    if (opt.hessian >= 2) {  // covariance from the analytic Hessian at every converged toy's minimum
+        int st = run_hess_pass(b, c, opt.hessian == 3 ? kHmSandwich : kHmCov, opt.hessian == 3, nullptr);
+        if (st != NLL_OK) return st;
+    }
     e = cudaMemcpyAsync(fits.data(), b->d_fits, sizeof(ToyFit) * n, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit state download");
@@ -1402,6 +1933,43 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         if (results[t].status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
     }
     return all;
+}
+
+int nll_batch_eval_hess(nll_batch* b, const double* thetas, int shared, double* nll_out, double* grad_out,
+                        double* hess_out, double* w2_out, int* status_out)
+{
+    if (!b) return NLL_ERR_ARG;
+    if (!b->loaded) return bfail(b, NLL_ERR_STATE, "no toys loaded");
+    if (!thetas || !nll_out || !hess_out) return bfail(b, NLL_ERR_ARG, "null argument");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
+    const int n = b->n_toys, np = b->npar;
+    if (n == 0) return NLL_OK;
+    std::vector<double> th((size_t)n * np);
+    for (int t = 0; t < n; ++t)
+        for (int k = 0; k < np; ++k) th[(size_t)t * np + k] = thetas[(shared ? 0 : (size_t)t * np) + k];
+    BatchDev d = make_dev(b);
+    cudaError_t e = follow_user_stream(b);
+    if (e != cudaSuccess) return bcuda(b, e, "stream order");
+    int st = run_hess_pass(b, d.cfg, kHmEval, w2_out != nullptr, th.data());
+    if (st != NLL_OK) return st;
+    const size_t per = 1 + np + 2 * (size_t)np * np;
+    std::vector<double> out(per * n);
+    std::vector<int> sts(n);
+    e = cudaMemcpyAsync(out.data(), b->d_hout, sizeof(double) * per * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sts.data(), b->d_hstatus, sizeof(int) * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "Hessian results");
+    int first_bad = NLL_OK;
+    for (int t = 0; t < n; ++t) {
+        const double* o = out.data() + per * t;
+        nll_out[t] = o[0];
+        if (grad_out) memcpy(grad_out + (size_t)t * np, o + 1, sizeof(double) * np);
+        memcpy(hess_out + (size_t)t * np * np, o + 1 + np, sizeof(double) * np * np);
+        if (w2_out) memcpy(w2_out + (size_t)t * np * np, o + 1 + np + np * np, sizeof(double) * np * np);
+        if (status_out) status_out[t] = sts[t];
+        if (sts[t] != NLL_OK && first_bad == NLL_OK) first_bad = sts[t];
+    }
+    return first_bad;
 }
 
 }  // extern "C"

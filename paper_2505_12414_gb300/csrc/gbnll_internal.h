@@ -144,10 +144,14 @@ struct HConst {
     double c1[3], c2[3], dl[3];  // Chebyshev coefficients and d ln Nc_j / d c2_j
 };
 
-struct HArgs {
+struct HEv {  // the sample as the Hessian pass reads it
     const double* col[kNumCols];
     const double* w;
-    int64_t n;
+    int64_t n;  // events with index < n are real (global index)
+};
+
+struct HArgs {
+    HEv ev;
     HConst c;
     int nslots;
     int lnp_slot;          // unweighted: slot that receives the block's sum of ln P (else -1)

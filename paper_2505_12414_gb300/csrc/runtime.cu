@@ -472,9 +472,9 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         static_assert(sizeof(HArgs) <= 4096, "kernel parameters");
         HArgs a;
         memset(&a, 0, sizeof a);
-        for (int c = 0; c < kNumCols; ++c) a.col[c] = evcol(m, c);
-        a.w = evw(m);
-        a.n = m->n;
+        for (int c = 0; c < kNumCols; ++c) a.ev.col[c] = evcol(m, c);
+        a.ev.w = evw(m);
+        a.ev.n = m->n;
         hess_fill_const(m->kind, H, theta, &a.c);
         a.nslots = L.nslots;
         a.lnp_slot = L.lnp_slot;

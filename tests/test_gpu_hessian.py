@@ -166,11 +166,113 @@ def test_weighted_fit_sandwich_covariance(gpu_lib):
     m.close()
 
 
-def test_batched_fits_reject_analytic_options(gpu_lib):
-    off = np.array([0, 100, 200], dtype=np.int64)
-    cols = synth.mass1d(200, stream=350)
-    b = gpu_lib.Batch(M1, synth.RANGES_1D).load(off, cols)
-    with pytest.raises(gpu_lib.NLLError) as e:
-        b.fit(synth.TRUTH_1D, strategy=2, hessian=1)
-    assert e.value.status == gpu_lib.NLL_ERR_ARG
+def test_served_fits_reject_analytic_options(gpu_lib):
+    for strategy, hessian in ((2, 1), (1, 2), (0, 3)):
+        with pytest.raises(gpu_lib.NLLError) as e:
+            gpu_lib.Server(M1, synth.RANGES_1D, 4, 100000, strategy=strategy, hessian=hessian)
+        assert e.value.status == gpu_lib.NLL_ERR_ARG
+
+
+# --------------------------------------------------------------------------------------
+# batched: per-toy Hessians in one device pass, and device-resident fits that use them
+# --------------------------------------------------------------------------------------
+RAGGED = [0, 1, 2, 127, 128, 129, 4095, 4096, 4097, 9000, 0, 3]
+
+
+def ragged(kind, sizes, stream0, weighted):
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(sizes)
+    parts = [synth.mass1d(n, stream=stream0 + t) if kind == M1 else synth.kstar4d(n, stream=stream0 + t)
+             for t, n in enumerate(sizes)]
+    ndim = 1 if kind == M1 else 4
+    cols = [np.concatenate([p[d] for p in parts]) for d in range(ndim)]
+    w = synth.weights(int(off[-1]), stream=stream0 + 999) if weighted else None
+    return off, cols, w
+
+
+@pytest.mark.parametrize("kind,weighted,precompute",
+                         [(M1, False, True), (M1, True, True), (M4, False, True), (M4, True, False)])
+def test_batch_hessian_parity(gpu_lib, kind, weighted, precompute):
+    off, cols, w = ragged(kind, RAGGED, 3600, weighted)
+    ranges = synth.RANGES_1D if kind == M1 else synth.RANGES_4D
+    base = np.array([5283.0, 22.0, -0.0017, 0.35]) if kind == M1 else synth.TRUTH_4D + 0.01
+    scale = np.array([2.0, 1.0, 2e-4, 0.02]) if kind == M1 else np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    thetas = np.array([synth.perturb(base, scale, k=t) for t in range(len(RAGGED))])
+    b = gpu_lib.Batch(kind, ranges).load(off, cols, w, precompute=precompute)
+    nll, g, H, W, st = b.eval_hess(thetas, w2=True)
+    for t in range(len(RAGGED)):
+        sl = slice(off[t], off[t + 1])
+        ct = [c[sl] for c in cols]
+        wt = w[sl] if w is not None else None
+        assert st[t] == 0
+        if off[t + 1] == off[t]:
+            assert nll[t] == 0.0 and np.all(g[t] == 0.0) and np.all(H[t] == 0.0)
+            continue
+        check_against_oracle(kind, ct, ranges, thetas[t], wt, nll[t], g[t], H[t], W[t])
+    # the single-sample pass on one toy gives the same numbers within rounding
+    t = 8
+    sl = slice(off[t], off[t + 1])
+    m = gpu_lib.Model(kind, ranges).load([c[sl] for c in cols], w[sl] if w is not None else None,
+                                         precompute=precompute)
+    n1, g1, H1, W1 = m.eval_hess(thetas[t], w2=True)
+    assert abs(n1 - nll[t]) <= 1e-13 * abs(n1)
+    d = np.sqrt(np.outer(np.diag(np.abs(H1)), np.diag(np.abs(H1))))
+    assert np.all(np.abs(H1 - H[t]) <= 1e-12 * d + 1e-12 * np.abs(H1))
+    m.close()
+    b.close()
+
+
+def test_batch_hessian_reports_bad_points(gpu_lib):
+    off, cols, _ = ragged(M4, [500, 600, 700], 3700, False)
+    b = gpu_lib.Batch(M4, synth.RANGES_4D).load(off, cols)
+    th = np.array([synth.TRUTH_4D] * 3)
+    th[1, 17] = 1.0   # fsig outside (0, 1): invalid parameter point
+    th[2, 6] = 3.0    # AFB far outside the physical region: negative rate somewhere
+    th[2, 17] = 0.999
+    nll, g, H, st = b.eval_hess(th)
+    assert st[0] == 0 and np.isfinite(nll[0])
+    assert st[1] == gpu_lib.NLL_ERR_ARG and np.isinf(nll[1]) and np.all(np.isnan(H[1]))
+    assert st[2] == gpu_lib.NLL_ERR_NONPOSITIVE_PDF and np.isinf(nll[2])
+    b.close()
+
+
+@pytest.mark.parametrize("kind,nev,ntoy", [(M1, 3000, 8), (M4, 3000, 4)])
+def test_batch_fits_with_analytic_hessian(gpu_lib, kind, nev, ntoy):
+    off, cols, _ = ragged(kind, [nev] * ntoy, 3800, False)
+    ranges = synth.RANGES_1D if kind == M1 else synth.RANGES_4D
+    truth = synth.TRUTH_1D if kind == M1 else synth.TRUTH_4D
+    lo, hi = _bounds(kind)
+    step = _step(kind)
+    start = truth + 0.5 * step
+    b = gpu_lib.Batch(kind, ranges).load(off, cols)
+    an = b.fit(start, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=2, hessian=2)
+    fd = b.fit(start, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=1, hessian=1)
+    assert np.all(an["status"] == 0) and np.all(fd["status"] == 0)
+    assert np.all(an["n_eval"] < fd["n_eval"])
+    for t in range(ntoy):
+        sl = slice(off[t], off[t + 1])
+        m = gpu_lib.Model(kind, ranges).load([c[sl] for c in cols])
+        s = m.fit(start, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=2, hessian=2)
+        assert s["status"] == 0
+        assert np.max(np.abs((an["theta"][t] - s["theta"]) / s["err"])) < 1e-6
+        np.testing.assert_allclose(an["err"][t], s["err"], rtol=1e-5)
+        np.testing.assert_allclose(an["err"][t], fd["err"][t], rtol=1e-3)
+        # the covariance is the inverse of the oracle's Hessian at the toy's minimum
+        ref = oracle.nll_hess(kind, ranges, [c[sl] for c in cols], an["theta"][t])
+        close_cov(an["cov"][t], np.linalg.inv(ref["hess"]))
+        m.close()
+    b.close()
+
+
+def test_batch_weighted_sandwich(gpu_lib):
+    off, cols, w = ragged(M1, [20000, 15000, 25000], 3900, True)
+    lo, hi = _bounds(M1)
+    b = gpu_lib.Batch(M1, synth.RANGES_1D).load(off, cols, w)
+    r = b.fit(synth.TRUTH_1D, lo=lo, hi=hi, step=_step(M1), tol_edm=1e-14, strategy=2, hessian=3)
+    assert np.all(r["status"] == 0)
+    for t in range(3):
+        sl = slice(off[t], off[t + 1])
+        ref = oracle.nll_hess(M1, synth.RANGES_1D, [cols[0][sl]], r["theta"][t], w=w[sl])
+        Hi = np.linalg.inv(ref["hess"])
+        close_cov(r["cov"][t], Hi @ ref["w2"] @ Hi)
     b.close()
