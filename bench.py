@@ -174,20 +174,26 @@ def cpu_baseline(cols, seconds=10.0, sample=100_000):
 def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
     """Batched device-resident fits of n_toys 4D toys (Poisson(2000) events, generated from
     truth) against the plain one-fit-at-a-time GPU path; fits/s by wall clock of the
-    synchronous calls (generation excluded, the same fitted results at tolerance 1e-8)."""
+    synchronous calls (generation excluded).  Primary: analytic second derivatives (start
+    matrix and covariance from the analytic Hessian pass, strategy 2 / hessian 2); beside it
+    the same batch with finite-difference Hessians of the analytic gradient (1 / 1)."""
     off, cols = synth.toys4d(n_toys, 2000.0, seed=synth.BASE_SEED + seed_stream)
     lo, hi = np.zeros(18), np.zeros(18)
     hi[17] = 1.0
     step = np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
-    opts = dict(lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=1, hessian=1)
+    base = dict(lo=lo, hi=hi, step=step, tol_edm=1e-8)
     b = g.Batch(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device).load(off, cols)
     b.autotune()
     sched = b.get_schedule()
-    b.fit(synth.TRUTH_4D, **opts)  # warm-up (graph instantiation, caches)
-    t0 = time.perf_counter()
-    r = b.fit(synth.TRUTH_4D, **opts)
-    dt = time.perf_counter() - t0
+    runs = {}
+    for label, st, hs in (("analytic", 2, 2), ("fd", 1, 1)):
+        b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)  # warm-up (graph instantiation, caches)
+        t0 = time.perf_counter()
+        r = b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)
+        runs[label] = (r, time.perf_counter() - t0)
     b.close()
+    r, dt = runs["analytic"]
+    rf, dtf = runs["fd"]
     m = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device)
     seq_t = 0.0
     agree = []
@@ -195,17 +201,26 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
         sl = slice(off[t], off[t + 1])
         t1 = time.perf_counter()
         m.load([c[sl] for c in cols])
-        s = m.fit(synth.TRUTH_4D, **opts)
+        s = m.fit(synth.TRUTH_4D, strategy=2, hessian=2, **base)
         if t > 0:  # the first fit is a warm-up
             seq_t += time.perf_counter() - t1
             if s["status"] == 0 and r["status"][t] == 0:
                 agree.append(float(np.max(np.abs(r["theta"][t] - s["theta"]) / s["err"])))
     m.close()
     n_seq_done = min(n_seq, n_toys)
+    both = (r["status"] == 0) & (rf["status"] == 0)
     return {"n_toys": n_toys, "mean_events": 2000, "batched_fits_per_s": n_toys / dt, "batched_wall_s": dt,
+            "second_derivatives": "analytic Hessian pass (strategy 2, hessian 2)",
             "device_steps": r["steps"], "converged": int(np.sum(r["status"] == 0)),
             "mean_evals_per_fit": float(np.mean(r["n_eval"])), "schedule": sched,
+            "fd": {"batched_fits_per_s": n_toys / dtf, "mean_evals_per_fit": float(np.mean(rf["n_eval"])),
+                   "converged": int(np.sum(rf["status"] == 0)), "device_steps": rf["steps"],
+                   "max_abs_diff_over_sigma_vs_analytic": float(np.max(np.abs(r["theta"] - rf["theta"])[both] /
+                                                                       rf["err"][both])) if np.any(both) else None,
+                   "max_rel_err_diff_vs_analytic": float(np.max(np.abs(r["err"][both] / rf["err"][both] - 1.0)))
+                   if np.any(both) else None},
             "sequential_fits_per_s": n_seq_done / seq_t if seq_t > 0 else None, "sequential_sample": n_seq_done,
+            "sequential_options": "single-sample fit_minimise, strategy 2, hessian 2 (analytic, Newton polish)",
             "max_abs_diff_over_sigma_vs_sequential": max(agree) if agree else None,
             "speedup_vs_sequential": (n_toys / dt) / (n_seq_done / seq_t) if seq_t > 0 else None}
 
@@ -266,8 +281,9 @@ def serving(g, device, n_req, rate, seed_stream=0):
 def toy_study(g, device, n_toys):
     """The paper's pseudo-experiment study on its own mass-fit configuration (Sec. 3.2, GeV
     units: [5, 7], fsig 0.3, mu 5.28, sigma 0.06, alpha -1): per N in 1e3..1e6, n_toys toys are
-    generated on the device, fitted from the generation values, and their uncertainties taken
-    from the Hessian; ms per pseudo-experiment by wall clock of the synchronous calls."""
+    generated on the device, fitted from the generation values with analytic first and second
+    derivatives (the paper's "analytic" mode: start matrix and uncertainties from the analytic
+    Hessian); ms per pseudo-experiment by wall clock of the synchronous calls."""
     lo, hi = np.zeros(4), np.zeros(4)
     hi[3] = 1.0
     step = np.array([0.005, 0.005, 0.05, 0.02])
@@ -276,11 +292,11 @@ def toy_study(g, device, n_toys):
         b = g.Batch(g.NLL_MODEL_MASS1D, synth.RANGES_1D_GEV, device=device)
         b.generate(synth.TRUTH_1D_GEV, [n] * n_toys, seed=synth.BASE_SEED)  # warm-up
         b.autotune()
-        b.fit(synth.TRUTH_1D_GEV, lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=1, hessian=1)
+        b.fit(synth.TRUTH_1D_GEV, lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=2, hessian=2)
         t0 = time.perf_counter()
         b.generate(synth.TRUTH_1D_GEV, [n] * n_toys, seed=synth.BASE_SEED + 1)
         t1 = time.perf_counter()
-        r = b.fit(synth.TRUTH_1D_GEV, lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=1, hessian=1)
+        r = b.fit(synth.TRUTH_1D_GEV, lo=lo, hi=hi, step=step, tol_edm=1e-8, strategy=2, hessian=2)
         t2 = time.perf_counter()
         sched = b.get_schedule()
         b.close()
