@@ -58,6 +58,11 @@ struct DConst {
 struct ToyFit {
     int phase, iter, n_eval, status, first;
     int vset;  // the start matrix V came from the analytic Hessian (strategy 2)
+    // Newton polish with the analytic Hessian after the loop (hessian 2 / 3)
+    int pol;                  // > 0 while polishing
+    double lam, f_acc;        // step fraction; NLL at the accepted point
+    double th_acc[kNP];       // accepted point (all parameters)
+    double dN[kNP];           // Newton direction H^-1 g (free components, external)
     double f, ft, edm, alpha, gp;
     double x[kNP], g[kNP], p[kNP], xt[kNP], sint[kNP], hstep[kNP];
     double th[kNP];    // external parameters of the accepted point (all npar)
@@ -607,8 +612,19 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
                 for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, gt, j);
             const double edm = 0.5 * wsum(mine ? gt * vg : 0.0);
             if (lane == 0) F.edm = edm;
+            // an accepted step that did not lower the NLL (its change is below the rounding of
+            // the sum near the minimum): stop, as the host minimiser does
+            const bool stalled = !(f0 < f) && F.iter > 2;
             if (edm < c.tol_edm) {
                 finish = true;
+            } else if (stalled) {
+                if (c.hessian) {
+                    finish = true;
+                } else {
+                    done_status = edm < 100.0 * c.tol_edm ? NLL_OK : NLL_ERR_NOT_CONVERGED;
+                    finish = done_status == NLL_OK;
+                    if (finish) done_status = -1;
+                }
             } else if (F.iter >= c.max_iter) {
                 done_status = NLL_ERR_NOT_CONVERGED;
             } else {
@@ -711,15 +727,17 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
 // ---------------------------------------------------------------------------------
 // analytic Hessian pass over all toys (paper Sec. 2.1): the start matrix of strategy 2,
 // the covariance of hessian 2 / 3, and nll_batch_eval_hess.  The per-event work is the
-// single-sample Hessian pass (hess_device.cuh) over (toy, 4096-event) units; a warp per
+// single-sample Hessian pass (hess_device.cuh) over (toy, 1024-event) units; a warp per
 // toy then sums its units in order, assembles H (and W) and inverts.
 // ---------------------------------------------------------------------------------
-constexpr int kHessUnitEvents = 4096;
+constexpr int kHessUnitEvents = 1024;  // 8 shared-memory tiles: several waves of units even for small toys
 
 enum HessMode : int { kHmEval = 0, kHmStart = 1, kHmCov = 2, kHmSandwich = 3 };
 
 struct HessDev {
     int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
+    int pass;                   // covariance modes: polish pass (0: the loop's final point)
+    int* n_polish;              // covariance modes: toys still polishing after this pass (mapped)
     const int64_t* ev_begin;
     const int64_t* ev_end;
     const double* sum_wdm;
@@ -766,7 +784,8 @@ __global__ void batch_hess_prep(HessDev h)
     } else {
         const ToyFit& F = h.fits[t];
         for (int k = 0; k < np; ++k) th[k] = F.th[k];
-        if (h.mode != kHmStart) use = F.phase == kPhDone && F.status == NLL_OK;
+        // covariance modes: the toys still polishing (set up by the host before pass 0)
+        if (h.mode != kHmStart) use = F.pol > 0;
     }
     KConst kc;
     DConst dc;
@@ -812,7 +831,7 @@ __global__ void batch_hess_prep(HessDev h)
     h.ht[t] = T;
 }
 
-// persistent blocks over units: unit u covers events [e0, min(e0 + 4096, end)) of its toy
+// persistent blocks over units: unit u covers events [e0, min(e0 + kHessUnitEvents, end)) of its toy
 template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h)
 {
@@ -884,6 +903,84 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
     }
 }
 
+// Newton polish helpers (warp per toy).  propose: the point th_acc - lam d, halving lam until
+// every bounded parameter stays inside its bounds; reject: halve lam and propose again, or stop
+// at the accepted point once the step is negligible.
+__device__ void polish_propose(const HessDev& h, ToyFit& F, int lane)
+{
+    const FitConfig& c = h.cfg;
+    const int nf = c.nf;
+    double lam = F.lam;
+    bool inside = false;
+    for (int tries = 0; tries < 40 && !inside; ++tries) {
+        int out = 0;
+        if (lane < nf) {
+            const int k = c.idx[lane];
+            const double v = F.th_acc[k] - lam * F.dN[lane];
+            out = c.bounded[k] && !(v > c.lo[k] && v < c.hi[k]);
+        }
+        inside = __all_sync(0xffffffffu, out == 0);
+        if (!inside) lam *= 0.5;
+    }
+    if (!inside || lam < 1e-6) {  // no admissible step: stay at the accepted point
+        for (int k = lane; k < c.npar; k += 32) F.th[k] = F.th_acc[k];
+        if (lane == 0) F.pol = 0;
+        return;
+    }
+    for (int k = lane; k < c.npar; k += 32) F.th[k] = F.th_acc[k];
+    __syncwarp();
+    if (lane < nf) F.th[c.idx[lane]] = F.th_acc[c.idx[lane]] - lam * F.dN[lane];
+    if (lane == 0) {
+        F.lam = lam;
+        F.pol = 1;
+        atomicAdd(h.n_polish, 1);
+    }
+}
+
+__device__ void polish_reject(const HessDev& h, ToyFit& F, int lane)
+{
+    if (h.pass == 0) {  // the loop's own final point failed here: nothing to step from
+        if (lane == 0) {
+            F.pol = 0;
+            F.n_eval += 1;
+        }
+        return;
+    }
+    if (lane == 0) {
+        F.lam *= 0.5;
+        F.n_eval += 1;
+    }
+    __syncwarp();
+    polish_propose(h, F, lane);
+}
+
+// thread per toy: toys that finished the loop at a parameter point (converged, or stopped by a
+// stalled line search or the iteration limit) are polished; after the last pass a toy still
+// polishing returns to its accepted point
+__global__ void batch_polish_init(ToyFit* fits, int n)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    ToyFit& F = fits[t];
+    const bool go = F.phase == kPhDone && (F.status == NLL_OK || F.status == NLL_ERR_NOT_CONVERGED);
+    F.pol = go ? 1 : 0;
+    F.lam = 1.0;
+    F.f_acc = F.f;
+    for (int k = 0; k < kNP; ++k) F.th_acc[k] = F.th[k];
+}
+
+__global__ void batch_polish_close(ToyFit* fits, int n, int npar)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    ToyFit& F = fits[t];
+    if (F.pol > 0) {
+        for (int k = 0; k < npar; ++k) F.th[k] = F.th_acc[k];
+        F.f = F.f_acc;
+        F.pol = 0;
+    }
+}
+
 // warp per toy: slot totals (units in order), assembly, and the mode's matrix work
 // (two warps per block: 37.5 KB of static shared memory for the 18-parameter model)
 constexpr int kFinWarps = 2;
@@ -905,6 +1002,12 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
     const FitConfig& c = h.cfg;
     const int np = c.npar, nf = c.nf;
     const bool mine = lane < nf;
+    const bool polish = h.mode == kHmCov || h.mode == kHmSandwich;
+    if (polish && h.fits[t].pol <= 0) return;
+    if (!h.hok[t] && polish) {  // the proposed point is not a valid parameter point: shorter step
+        polish_reject(h, h.fits[t], lane);
+        return;
+    }
     if (!h.hok[t]) {
         if (h.mode == kHmEval) {
             if (lane == 0) h.status[t] = NLL_ERR_ARG;
@@ -941,8 +1044,11 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
         }
         return;
     }
-    if (bad) return;  // keep what the minimiser has (diagonal start, BFGS covariance)
     ToyFit& F = h.fits[t];
+    if (bad) {  // start: keep the diagonal start matrix; polish: a shorter step
+        if (polish) polish_reject(h, F, lane);
+        return;
+    }
     double* A = s_mat[wib][0];
     double* Lm = s_mat[wib][1];
     double* Mm = s_mat[wib][2];
@@ -971,10 +1077,21 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
         if (lane == 0) F.n_eval += 1;
         return;
     }
-    // covariance at the minimum: H^-1, or H^-1 W H^-1
+    // Newton polish step (as the single-sample minimiser): accept the point if the NLL did not
+    // rise, take H^-1 (or H^-1 W H^-1) there as the covariance, stop when the EDM with H is
+    // below the tolerance, else propose the Newton step from the accepted point
+    const double fnew = s_nll[wib];
+    const bool accept = h.pass == 0 || fnew <= F.f_acc + 1e-15 * fabs(F.f_acc);
+    if (!accept) {
+        polish_reject(h, F, lane);
+        return;
+    }
     const bool inv = warp_spd_inverse(nf, A, Lm, Mm, Out);
     if (lane == 0) F.n_eval += 1;
-    if (!inv) return;  // the BFGS covariance stays
+    if (!inv) {  // no positive-definite Hessian here: the last covariance stays, stop
+        if (lane == 0) F.pol = 0;
+        return;
+    }
     if (h.mode == kHmSandwich) {
         double* Wf = Lm;  // reuse: W (free block), then T = Hi W
         if (mine)
@@ -996,17 +1113,35 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
     } else if (mine) {
         for (int j = 0; j < nf; ++j) F.cov[lane * nf + j] = Out[lane * nf + j];
     }
-    __syncwarp();
-    // EDM with the Hessian (as the single-sample minimiser reports it)
-    const double ge = mine ? F.gext[lane] : 0.0;
+    // accepted point: gradient, EDM with H, Newton direction d = H^-1 g
+    const double ge = mine ? s_g[wib][c.idx[lane]] : 0.0;
     double hg = 0.0;
     if (mine)
         for (int j = 0; j < nf; ++j) hg += Out[lane * nf + j] * __shfl_sync(0xffffffffu, ge, j);
     else
         for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, ge, j);
     const double edm = 0.5 * wsum(mine ? ge * hg : 0.0);
-    if (lane == 0) F.edm = edm;
-    if (mine) F.err[lane] = sqrt(fmax(F.cov[lane * nf + lane], 0.0));
+    if (mine) {
+        F.err[lane] = sqrt(fmax(F.cov[lane * nf + lane], 0.0));
+        F.gext[lane] = ge;
+        F.dN[lane] = hg;
+    }
+    for (int k = lane; k < np; k += 32) F.th_acc[k] = F.th[k];
+    if (lane == 0) {
+        F.edm = edm;
+        F.f = fnew;
+        F.f_acc = fnew;
+        F.lam = 1.0;
+    }
+    __syncwarp();
+    if (edm < c.tol_edm) {
+        if (lane == 0) {
+            F.status = NLL_OK;
+            F.pol = 0;
+        }
+        return;
+    }
+    polish_propose(h, F, lane);
 }
 
 template <int KIND, int VAR, bool W>
@@ -1119,6 +1254,8 @@ struct nll_batch {
     int* d_counters = nullptr;
     int* h_active = nullptr;  // mapped
     int* d_active = nullptr;
+    int* h_npol = nullptr;    // mapped: toys that proposed a polish step in the last pass
+    int* d_npol = nullptr;
     int* d_item_toy = nullptr;
     int* d_item_u0 = nullptr;
     int* d_item_nt = nullptr;
@@ -1333,7 +1470,7 @@ int eval_all(nll_batch* b, const double* thetas, double* nll_out, double* grad_o
 
 
 
-// work arrays of the Hessian pass for the loaded toys: units of 4096 events per toy
+// work arrays of the Hessian pass for the loaded toys: units of kHessUnitEvents events per toy
 int ensure_hess_work(nll_batch* b)
 {
     if (b->hess_ready) return NLL_OK;
@@ -1384,7 +1521,7 @@ int ensure_hess_work(nll_batch* b)
 // One Hessian pass over all toys on the batch's stream.  kHmEval takes the host thetas
 // ([n_toys][npar]) and leaves per-toy results in d_hout / d_hstatus; the other modes read
 // and write the toys' fit states (the fits must be on the device).
-int run_hess_pass(nll_batch* b, const FitConfig& cfg, int mode, bool want_w2, const double* thetas)
+int run_hess_pass(nll_batch* b, const FitConfig& cfg, int mode, bool want_w2, const double* thetas, int pass = 0)
 {
     int st = ensure_hess_work(b);
     if (st != NLL_OK) return st;
@@ -1403,6 +1540,8 @@ int run_hess_pass(nll_batch* b, const FitConfig& cfg, int mode, bool want_w2, co
     h.n_toys = n;
     h.mode = mode;
     h.want_w2 = want_w2 ? 1 : 0;
+    h.pass = pass;
+    h.n_polish = b->d_npol;
     h.n_units = b->n_hunits;
     h.nslots = L.nslots;
     h.lnp_slot = L.lnp_slot;
@@ -1616,6 +1755,8 @@ int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t c
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_active, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_active, b->h_active, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_npol, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_npol, b->h_npol, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) {
@@ -1634,6 +1775,7 @@ void nll_batch_destroy(nll_batch* b)
     free_work(b);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->h_active) cudaFreeHost(b->h_active);
+    if (b->h_npol) cudaFreeHost(b->h_npol);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -1920,9 +2062,22 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return bcuda(b, e, "fit loop");
     if (steps_out) *steps_out = steps;
-    if (opt.hessian >= 2) {  // covariance from the analytic Hessian at every converged toy's minimum
-        int st = run_hess_pass(b, c, opt.hessian == 3 ? kHmSandwich : kHmCov, opt.hessian == 3, nullptr);
-        if (st != NLL_OK) return st;
+    if (opt.hessian >= 2) {
+        // analytic Hessian at every toy's final point: covariance, EDM, and Newton polish steps
+        // (each pass evaluates the toys still polishing) until no toy proposes another step
+        const int tb = (n + 127) / 128;
+        batch_polish_init<<<tb, 128, 0, b->stream>>>(b->d_fits, n);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(b, e, "polish set-up");
+        for (int pass = 0; pass < 6; ++pass) {
+            *(volatile int*)b->h_npol = 0;
+            int st = run_hess_pass(b, c, opt.hessian == 3 ? kHmSandwich : kHmCov, opt.hessian == 3, nullptr, pass);
+            if (st != NLL_OK) return st;
+            if (*(volatile int*)b->h_npol == 0) break;
+        }
+        batch_polish_close<<<tb, 128, 0, b->stream>>>(b->d_fits, n, np);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return bcuda(b, e, "polish close");
     }
     e = cudaMemcpyAsync(fits.data(), b->d_fits, sizeof(ToyFit) * n, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
