@@ -133,8 +133,10 @@ typedef struct {
                        Hessian of the analytic gradient at the minimum plus Newton polish;
                        2: the same with the analytic Hessian, covariance H^-1;
                        3: as 2, covariance H^-1 W H^-1 (weighted fits, see nll_eval_hess).
-                       Values 2 and 3 (and strategy 2) need a model: fit_minimise_fcn and the
-                       served fits reject them with NLL_ERR_ARG.                               */
+                       Values 2 and 3 (and strategy 2) need second derivatives of a model:
+                       fit_minimise_fcn rejects them with NLL_ERR_ARG.  Batched and served fits
+                       run the analytic passes on the device (see nll_batch_fit; a server takes
+                       the start matrix at nll_server_submit and polishes at nll_server_poll). */
 } fit_options;
 
 #define FIT_MAXPAR 32

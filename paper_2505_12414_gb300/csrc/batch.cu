@@ -738,6 +738,7 @@ struct HessDev {
     int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
     int pass;                   // covariance modes: polish pass (0: the loop's final point)
     int* n_polish;              // covariance modes: toys still polishing after this pass (mapped)
+    const int* sel;             // per toy: take part in this pass (NULL: every toy)
     const int64_t* ev_begin;
     const int64_t* ev_end;
     const double* sum_wdm;
@@ -775,6 +776,10 @@ __global__ void batch_hess_prep(HessDev h)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= h.n_toys) return;
+    if (h.sel && !h.sel[t]) {
+        h.hok[t] = 0;
+        return;
+    }
     const FitConfig& c = h.cfg;
     const int np = c.npar;
     double th[kNP];
@@ -957,10 +962,10 @@ __device__ void polish_reject(const HessDev& h, ToyFit& F, int lane)
 // thread per toy: toys that finished the loop at a parameter point (converged, or stopped by a
 // stalled line search or the iteration limit) are polished; after the last pass a toy still
 // polishing returns to its accepted point
-__global__ void batch_polish_init(ToyFit* fits, int n)
+__global__ void batch_polish_init(ToyFit* fits, int n, const int* sel)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    if (t >= n || (sel && !sel[t])) return;
     ToyFit& F = fits[t];
     const bool go = F.phase == kPhDone && (F.status == NLL_OK || F.status == NLL_ERR_NOT_CONVERGED);
     F.pol = go ? 1 : 0;
@@ -969,10 +974,10 @@ __global__ void batch_polish_init(ToyFit* fits, int n)
     for (int k = 0; k < kNP; ++k) F.th_acc[k] = F.th[k];
 }
 
-__global__ void batch_polish_close(ToyFit* fits, int n, int npar)
+__global__ void batch_polish_close(ToyFit* fits, int n, int npar, const int* sel)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    if (t >= n || (sel && !sel[t])) return;
     ToyFit& F = fits[t];
     if (F.pol > 0) {
         for (int k = 0; k < npar; ++k) F.th[k] = F.th_acc[k];
@@ -1002,6 +1007,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
     const FitConfig& c = h.cfg;
     const int np = c.npar, nf = c.nf;
     const bool mine = lane < nf;
+    if (h.sel && !h.sel[t]) return;
     const bool polish = h.mode == kHmCov || h.mode == kHmSandwich;
     if (polish && h.fits[t].pol <= 0) return;
     if (!h.hok[t] && polish) {  // the proposed point is not a valid parameter point: shorter step
@@ -1233,6 +1239,196 @@ using namespace gbnll;
 // ------------------------------------------------------------------------------------
 // host runtime
 // ------------------------------------------------------------------------------------
+namespace {
+
+// Work arrays of the analytic Hessian pass: units of kHessUnitEvents events of the selected
+// toys, per-toy constants and results, per-unit slot sums, the slot table, a selection mask
+// and the polish counter.
+struct HessWork {
+    bool ready = false;
+    int cap_toys = 0, cap_units = 0, np = 0, n_units = 0;
+    int* d_unit_toy = nullptr;
+    int64_t* d_unit_e0 = nullptr;
+    int* d_toy_u0 = nullptr;
+    int* d_toy_nu = nullptr;
+    HConst* d_hc = nullptr;
+    HessTerms* d_ht = nullptr;
+    int* d_hok = nullptr;
+    double* d_unit_sums = nullptr;
+    uint16_t* d_slot_of = nullptr;
+    double* d_thetas = nullptr;
+    double* d_out = nullptr;
+    int* d_status = nullptr;
+    int* d_sel = nullptr;
+    int* h_npol = nullptr;  // mapped: toys that proposed a polish step in the last pass
+    int* d_npol = nullptr;
+};
+
+void hw_free(HessWork& w)
+{
+    void* ptrs[] = {w.d_unit_toy, w.d_unit_e0, w.d_toy_u0, w.d_toy_nu, w.d_hc, w.d_ht, w.d_hok, w.d_unit_sums,
+                    w.d_slot_of, w.d_thetas, w.d_out, w.d_status, w.d_sel};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (w.h_npol) cudaFreeHost(w.h_npol);
+    w = HessWork();
+}
+
+cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
+{
+    hw_free(w);
+    const size_t nt = std::max(cap_toys, 1), nu = std::max(cap_units, 1);
+    cudaError_t e = cudaMalloc(&w.d_unit_toy, sizeof(int) * nu);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_unit_e0, sizeof(int64_t) * nu);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_toy_u0, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_toy_nu, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_hc, sizeof(HConst) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_ht, sizeof(HessTerms) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_hok, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_unit_sums, sizeof(double) * kHessMaxSlots * nu);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_slot_of, sizeof(uint16_t) * 64 * 64);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_thetas, sizeof(double) * np * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_out, sizeof(double) * (1 + np + 2 * np * np) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_status, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&w.d_sel, sizeof(int) * nt);
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_npol, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&w.d_npol, w.h_npol, 0);
+    if (e != cudaSuccess) {
+        hw_free(w);
+        return e;
+    }
+    w.cap_toys = (int)nt;
+    w.cap_units = (int)nu;
+    w.np = np;
+    w.ready = true;
+    return cudaSuccess;
+}
+
+// Unit lists for toys t with events [begin[t], end[t]) (host positions); toys with sel[t] == 0
+// get no units (sel empty: every toy).  Fails if the units exceed the capacity.
+cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const std::vector<int64_t>& end,
+                         const std::vector<int>& sel, cudaStream_t stream)
+{
+    const int n = (int)begin.size();
+    std::vector<int> unit_toy, toy_u0(std::max(n, 1), 0), toy_nu(std::max(n, 1), 0);
+    std::vector<int64_t> unit_e0;
+    for (int t = 0; t < n; ++t) {
+        toy_u0[t] = (int)unit_toy.size();
+        if (!sel.empty() && !sel[t]) continue;
+        for (int64_t e = begin[t]; e < end[t]; e += kHessUnitEvents) {
+            unit_toy.push_back(t);
+            unit_e0.push_back(e);
+        }
+        toy_nu[t] = (int)unit_toy.size() - toy_u0[t];
+    }
+    if ((int)unit_toy.size() > w.cap_units || n > w.cap_toys) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (!unit_toy.empty())
+        e = cudaMemcpyAsync(w.d_unit_toy, unit_toy.data(), sizeof(int) * unit_toy.size(), cudaMemcpyHostToDevice,
+                            stream);
+    if (e == cudaSuccess && !unit_e0.empty())
+        e = cudaMemcpyAsync(w.d_unit_e0, unit_e0.data(), sizeof(int64_t) * unit_e0.size(), cudaMemcpyHostToDevice,
+                            stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(w.d_toy_u0, toy_u0.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(w.d_toy_nu, toy_nu.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && !sel.empty())
+        e = cudaMemcpyAsync(w.d_sel, sel.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the host vectors go out of scope
+    if (e == cudaSuccess) w.n_units = (int)unit_toy.size();
+    return e;
+}
+
+// The sample and fit states a Hessian pass works on.
+struct HessTarget {
+    int kind, variant, sm_count, n_toys;
+    bool weighted;
+    HEv ev;
+    const int64_t* d_begin;
+    const int64_t* d_end;
+    const double* d_sum_wdm;
+    ToyFit* d_fits;
+    cudaStream_t stream;
+};
+
+// One Hessian pass (see HessDev); use_sel restricts it to the toys hw_set_units selected.
+cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int mode, bool want_w2,
+                          const double* thetas, int pass, bool use_sel)
+{
+    HessLayout L;
+    if (!hess_layout(T.kind, T.weighted, want_w2, &L)) return cudaErrorInvalidValue;
+    std::vector<uint16_t> slot_of(64 * 64, 0xffff);
+    for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * L.ncols + L.sj[k]] = (uint16_t)k;
+    const int n = T.n_toys, np = cfg.npar;
+    cudaError_t e = cudaMemcpyAsync(w.d_slot_of, slot_of.data(), sizeof(uint16_t) * slot_of.size(),
+                                    cudaMemcpyHostToDevice, T.stream);
+    if (e == cudaSuccess && mode == kHmEval)
+        e = cudaMemcpyAsync(w.d_thetas, thetas, sizeof(double) * np * n, cudaMemcpyHostToDevice, T.stream);
+    if (e != cudaSuccess) return e;
+    HessDev h;
+    memset(&h, 0, sizeof h);
+    h.n_toys = n;
+    h.mode = mode;
+    h.want_w2 = want_w2 ? 1 : 0;
+    h.pass = pass;
+    h.n_polish = w.d_npol;
+    h.sel = use_sel ? w.d_sel : nullptr;
+    h.n_units = w.n_units;
+    h.nslots = L.nslots;
+    h.lnp_slot = L.lnp_slot;
+    h.ncols = L.ncols;
+    h.ev_begin = T.d_begin;
+    h.ev_end = T.d_end;
+    h.sum_wdm = T.d_sum_wdm;
+    h.ev = T.ev;
+    h.fits = T.d_fits;
+    h.thetas = w.d_thetas;
+    h.hc = w.d_hc;
+    h.ht = w.d_ht;
+    h.hok = w.d_hok;
+    h.unit_toy = w.d_unit_toy;
+    h.unit_e0 = w.d_unit_e0;
+    h.toy_u0 = w.d_toy_u0;
+    h.toy_nu = w.d_toy_nu;
+    h.unit_sums = w.d_unit_sums;
+    h.slot_of = w.d_slot_of;
+    h.out = w.d_out;
+    h.status = w.d_status;
+    h.cfg = cfg;
+    memcpy(h.si, L.si, sizeof h.si);
+    memcpy(h.sj, L.sj, sizeof h.sj);
+    static_assert(sizeof(HessDev) <= 4096, "kernel parameters");
+    const int occ = hess_occupancy(T.kind, T.variant, T.weighted);
+    const int unit_blocks = std::max(1, std::min(w.n_units, T.sm_count * std::max(1, std::min(occ, 4))));
+    e = launch_hess_pass(T.kind, T.variant, T.weighted, unit_blocks, T.stream, h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(T.stream);
+    return e;
+}
+
+// Newton polish passes with the analytic Hessian at the final points of the finished toys
+// (all toys, or those hw_set_units selected), then the accepted points stay.
+cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel)
+{
+    const int tb = (T.n_toys + 127) / 128;
+    const int* sel = use_sel ? w.d_sel : nullptr;
+    batch_polish_init<<<tb, 128, 0, T.stream>>>(T.d_fits, T.n_toys, sel);
+    cudaError_t e = cudaGetLastError();
+    for (int pass = 0; pass < 6 && e == cudaSuccess; ++pass) {
+        *(volatile int*)w.h_npol = 0;
+        e = run_hess_core(T, w, cfg, hessian == 3 ? kHmSandwich : kHmCov, hessian == 3, nullptr, pass, use_sel);
+        if (e == cudaSuccess && *(volatile int*)w.h_npol == 0) break;
+    }
+    if (e == cudaSuccess) {
+        batch_polish_close<<<tb, 128, 0, T.stream>>>(T.d_fits, T.n_toys, cfg.npar, sel);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(T.stream);
+    return e;
+}
+
+}  // namespace
+
 struct nll_batch {
     int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
     cudaStream_t user_stream = nullptr;  // caller's stream (0 = default)
@@ -1254,8 +1450,6 @@ struct nll_batch {
     int* d_counters = nullptr;
     int* h_active = nullptr;  // mapped
     int* d_active = nullptr;
-    int* h_npol = nullptr;    // mapped: toys that proposed a polish step in the last pass
-    int* d_npol = nullptr;
     int* d_item_toy = nullptr;
     int* d_item_u0 = nullptr;
     int* d_item_nt = nullptr;
@@ -1266,20 +1460,7 @@ struct nll_batch {
     double* d_unit_sums = nullptr;
     ToyFit* d_fits = nullptr;
     // analytic Hessian pass (allocated at its first use for the loaded toys)
-    bool hess_ready = false;
-    int n_hunits = 0;
-    int* d_hunit_toy = nullptr;
-    int64_t* d_hunit_e0 = nullptr;
-    int* d_htoy_u0 = nullptr;
-    int* d_htoy_nu = nullptr;
-    HConst* d_hc = nullptr;
-    HessTerms* d_ht = nullptr;
-    int* d_hok = nullptr;
-    double* d_hunit_sums = nullptr;
-    uint16_t* d_slot_of = nullptr;
-    double* d_hthetas = nullptr;
-    double* d_hout = nullptr;
-    int* d_hstatus = nullptr;
+    HessWork hw;
     // schedule
     int tile_events = 0, bps = 2;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1307,25 +1488,9 @@ int bcuda(nll_batch* b, cudaError_t e, const char* what)
                  cudaGetErrorString(e));
 }
 
-void free_hess_work(nll_batch* b)
-{
-    void* ptrs[] = {b->d_hunit_toy, b->d_hunit_e0, b->d_htoy_u0, b->d_htoy_nu, b->d_hc, b->d_ht, b->d_hok,
-                    b->d_hunit_sums, b->d_slot_of, b->d_hthetas, b->d_hout, b->d_hstatus};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    b->d_hunit_toy = b->d_htoy_u0 = b->d_htoy_nu = b->d_hok = b->d_hstatus = nullptr;
-    b->d_hunit_e0 = nullptr;
-    b->d_hc = nullptr;
-    b->d_ht = nullptr;
-    b->d_hunit_sums = b->d_hthetas = b->d_hout = nullptr;
-    b->d_slot_of = nullptr;
-    b->n_hunits = 0;
-    b->hess_ready = false;
-}
-
 void free_work(nll_batch* b)
 {
-    free_hess_work(b);
+    hw_free(b->hw);
     void* ptrs[] = {b->d_ev, b->d_begin, b->d_end, b->d_sum_wdm, b->d_item_toy, b->d_item_u0, b->d_item_nt,
                     b->d_item_kc, b->d_item_dc, b->d_unit_item, b->d_unit_tile, b->d_unit_sums, b->d_fits};
     for (void* p : ptrs)
@@ -1470,108 +1635,49 @@ int eval_all(nll_batch* b, const double* thetas, double* nll_out, double* grad_o
 
 
 
-// work arrays of the Hessian pass for the loaded toys: units of kHessUnitEvents events per toy
+HessTarget target_of(nll_batch* b)
+{
+    HessTarget T;
+    memset(&T, 0, sizeof T);
+    T.kind = b->kind;
+    T.variant = variant_of(b);
+    T.sm_count = b->sm_count;
+    T.n_toys = b->n_toys;
+    T.weighted = b->weighted;
+    for (int c = 0; c < kNumCols; ++c) T.ev.col[c] = c < b->ncols ? b->d_ev + (size_t)c * b->n_pad : nullptr;
+    T.ev.w = b->weighted ? b->d_w : nullptr;
+    T.d_begin = b->d_begin;
+    T.d_end = b->d_end;
+    T.d_sum_wdm = b->d_sum_wdm;
+    T.d_fits = b->d_fits;
+    T.stream = b->stream;
+    return T;
+}
+
+// work arrays of the Hessian pass for the loaded toys (every toy, units of kHessUnitEvents)
 int ensure_hess_work(nll_batch* b)
 {
-    if (b->hess_ready) return NLL_OK;
-    const int n = b->n_toys, np = b->npar;
-    std::vector<int> unit_toy, toy_u0(std::max(n, 1)), toy_nu(std::max(n, 1));
-    std::vector<int64_t> unit_e0;
-    for (int t = 0; t < n; ++t) {
-        toy_u0[t] = (int)unit_toy.size();
-        for (int64_t e = b->begin[t]; e < b->end[t]; e += kHessUnitEvents) {
-            unit_toy.push_back(t);
-            unit_e0.push_back(e);
-        }
-        toy_nu[t] = (int)unit_toy.size() - toy_u0[t];
-    }
-    const size_t nu = std::max<size_t>(unit_toy.size(), 1), nt = std::max(n, 1);
-    cudaError_t e = cudaMalloc(&b->d_hunit_toy, sizeof(int) * nu);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hunit_e0, sizeof(int64_t) * nu);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_htoy_u0, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_htoy_nu, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hc, sizeof(HConst) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_ht, sizeof(HessTerms) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hok, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hunit_sums, sizeof(double) * kHessMaxSlots * nu);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_slot_of, sizeof(uint16_t) * 64 * 64);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hthetas, sizeof(double) * np * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hout, sizeof(double) * (1 + np + 2 * np * np) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_hstatus, sizeof(int) * nt);
-    if (e == cudaSuccess && !unit_toy.empty())
-        e = cudaMemcpyAsync(b->d_hunit_toy, unit_toy.data(), sizeof(int) * unit_toy.size(), cudaMemcpyHostToDevice,
-                            b->stream);
-    if (e == cudaSuccess && !unit_e0.empty())
-        e = cudaMemcpyAsync(b->d_hunit_e0, unit_e0.data(), sizeof(int64_t) * unit_e0.size(), cudaMemcpyHostToDevice,
-                            b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_htoy_u0, toy_u0.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_htoy_nu, toy_nu.data(), sizeof(int) * nt, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (b->hw.ready) return NLL_OK;
+    int64_t units = 0;
+    for (int t = 0; t < b->n_toys; ++t) units += (b->end[t] - b->begin[t] + kHessUnitEvents - 1) / kHessUnitEvents;
+    if (units > (1 << 28)) return bfail(b, NLL_ERR_ARG, "too many Hessian units");
+    cudaError_t e = hw_alloc(b->hw, b->n_toys, (int)units, b->npar);
+    if (e == cudaSuccess) e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->stream);
     if (e != cudaSuccess) {
-        free_hess_work(b);
+        hw_free(b->hw);
         return bcuda(b, e, "Hessian work arrays");
     }
-    b->n_hunits = (int)unit_toy.size();
-    b->hess_ready = true;
     return NLL_OK;
 }
 
 // One Hessian pass over all toys on the batch's stream.  kHmEval takes the host thetas
-// ([n_toys][npar]) and leaves per-toy results in d_hout / d_hstatus; the other modes read
+// ([n_toys][npar]) and leaves per-toy results in hw.d_out / hw.d_status; the other modes read
 // and write the toys' fit states (the fits must be on the device).
-int run_hess_pass(nll_batch* b, const FitConfig& cfg, int mode, bool want_w2, const double* thetas, int pass = 0)
+int run_hess_pass(nll_batch* b, const FitConfig& cfg, int mode, bool want_w2, const double* thetas)
 {
     int st = ensure_hess_work(b);
     if (st != NLL_OK) return st;
-    HessLayout L;
-    if (!hess_layout(b->kind, b->weighted, want_w2, &L)) return bfail(b, NLL_ERR_ARG, "Hessian slot table overflow");
-    std::vector<uint16_t> slot_of(64 * 64, 0xffff);
-    for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * L.ncols + L.sj[k]] = (uint16_t)k;
-    const int n = b->n_toys, np = b->npar;
-    cudaError_t e = cudaMemcpyAsync(b->d_slot_of, slot_of.data(), sizeof(uint16_t) * slot_of.size(),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess && mode == kHmEval)
-        e = cudaMemcpyAsync(b->d_hthetas, thetas, sizeof(double) * np * n, cudaMemcpyHostToDevice, b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "Hessian pass upload");
-    HessDev h;
-    memset(&h, 0, sizeof h);
-    h.n_toys = n;
-    h.mode = mode;
-    h.want_w2 = want_w2 ? 1 : 0;
-    h.pass = pass;
-    h.n_polish = b->d_npol;
-    h.n_units = b->n_hunits;
-    h.nslots = L.nslots;
-    h.lnp_slot = L.lnp_slot;
-    h.ncols = L.ncols;
-    h.ev_begin = b->d_begin;
-    h.ev_end = b->d_end;
-    h.sum_wdm = b->d_sum_wdm;
-    for (int c = 0; c < kNumCols; ++c) h.ev.col[c] = c < b->ncols ? b->d_ev + (size_t)c * b->n_pad : nullptr;
-    h.ev.w = b->weighted ? b->d_w : nullptr;
-    h.fits = b->d_fits;
-    h.thetas = b->d_hthetas;
-    h.hc = b->d_hc;
-    h.ht = b->d_ht;
-    h.hok = b->d_hok;
-    h.unit_toy = b->d_hunit_toy;
-    h.unit_e0 = b->d_hunit_e0;
-    h.toy_u0 = b->d_htoy_u0;
-    h.toy_nu = b->d_htoy_nu;
-    h.unit_sums = b->d_hunit_sums;
-    h.slot_of = b->d_slot_of;
-    h.out = b->d_hout;
-    h.status = b->d_hstatus;
-    h.cfg = cfg;
-    memcpy(h.si, L.si, sizeof h.si);
-    memcpy(h.sj, L.sj, sizeof h.sj);
-    static_assert(sizeof(HessDev) <= 4096, "kernel parameters");
-    const int occ = hess_occupancy(b->kind, variant_of(b), b->weighted);
-    const int unit_blocks = std::max(1, std::min(b->n_hunits, b->sm_count * std::max(1, std::min(occ, 4))));
-    e = launch_hess_pass(b->kind, variant_of(b), b->weighted, unit_blocks, b->stream, h);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    cudaError_t e = run_hess_core(target_of(b), b->hw, cfg, mode, want_w2, thetas, 0, false);
     if (e != cudaSuccess) return bcuda(b, e, "Hessian pass");
     return NLL_OK;
 }
@@ -1755,8 +1861,6 @@ int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t c
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_active, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_active, b->h_active, 0);
-    if (e == cudaSuccess) e = cudaHostAlloc(&b->h_npol, sizeof(int), cudaHostAllocMapped);
-    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_npol, b->h_npol, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e != cudaSuccess) {
@@ -1775,7 +1879,6 @@ void nll_batch_destroy(nll_batch* b)
     free_work(b);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->h_active) cudaFreeHost(b->h_active);
-    if (b->h_npol) cudaFreeHost(b->h_npol);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -2065,19 +2168,10 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     if (opt.hessian >= 2) {
         // analytic Hessian at every toy's final point: covariance, EDM, and Newton polish steps
         // (each pass evaluates the toys still polishing) until no toy proposes another step
-        const int tb = (n + 127) / 128;
-        batch_polish_init<<<tb, 128, 0, b->stream>>>(b->d_fits, n);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return bcuda(b, e, "polish set-up");
-        for (int pass = 0; pass < 6; ++pass) {
-            *(volatile int*)b->h_npol = 0;
-            int st = run_hess_pass(b, c, opt.hessian == 3 ? kHmSandwich : kHmCov, opt.hessian == 3, nullptr, pass);
-            if (st != NLL_OK) return st;
-            if (*(volatile int*)b->h_npol == 0) break;
-        }
-        batch_polish_close<<<tb, 128, 0, b->stream>>>(b->d_fits, n, np);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return bcuda(b, e, "polish close");
+        int st = ensure_hess_work(b);
+        if (st != NLL_OK) return st;
+        e = polish_core(target_of(b), b->hw, c, opt.hessian, false);
+        if (e != cudaSuccess) return bcuda(b, e, "Newton polish");
     }
     e = cudaMemcpyAsync(fits.data(), b->d_fits, sizeof(ToyFit) * n, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -2110,8 +2204,8 @@ int nll_batch_eval_hess(nll_batch* b, const double* thetas, int shared, double* 
     const size_t per = 1 + np + 2 * (size_t)np * np;
     std::vector<double> out(per * n);
     std::vector<int> sts(n);
-    e = cudaMemcpyAsync(out.data(), b->d_hout, sizeof(double) * per * n, cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(sts.data(), b->d_hstatus, sizeof(int) * n, cudaMemcpyDeviceToHost, b->stream);
+    e = cudaMemcpyAsync(out.data(), b->hw.d_out, sizeof(double) * per * n, cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sts.data(), b->hw.d_status, sizeof(int) * n, cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "Hessian results");
     int first_bad = NLL_OK;
@@ -2142,9 +2236,11 @@ struct nll_server {
     double* d_ev = nullptr;
     std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end) in pool events, sorted
     std::vector<char> busy;
-    std::vector<int64_t> slot_id, slot_begin, slot_len;
+    std::vector<int64_t> slot_id, slot_begin, slot_len, slot_nev;
     int64_t next_id = 1;
     FitConfig cfg;
+    int hessian = 0;  // fit_options.hessian: 2 / 3 polish finished slots with the analytic Hessian
+    HessWork hw;      // analytic Hessian passes (strategy 2, hessian 2 / 3)
     std::vector<double> step;
     // device work arrays
     int64_t* d_begin = nullptr;
@@ -2196,6 +2292,7 @@ void server_free(nll_server* s)
         if (p) cudaFree(p);
     if (s->h_active) cudaFreeHost(s->h_active);
     if (s->h_done) cudaFreeHost(s->h_done);
+    hw_free(s->hw);
     if (s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -2260,6 +2357,35 @@ BatchDev server_dev(nll_server* s)
     return d;
 }
 
+HessTarget server_target(nll_server* s)
+{
+    HessTarget T;
+    memset(&T, 0, sizeof T);
+    T.kind = s->kind;
+    T.variant = kVarPrecompute;  // the server builds the angular basis at admission
+    T.sm_count = s->sm_count;
+    T.n_toys = s->max_slots;
+    T.weighted = false;
+    for (int c = 0; c < kNumCols; ++c) T.ev.col[c] = c < s->ncols ? s->d_ev + (size_t)c * s->n_pad : nullptr;
+    T.d_begin = s->d_begin;
+    T.d_end = s->d_end;
+    T.d_sum_wdm = s->d_sum_wdm;
+    T.d_fits = s->d_fits;
+    T.stream = s->stream;
+    return T;
+}
+
+// unit lists of the Hessian pass for the slots with pick[i] != 0
+cudaError_t server_pick(nll_server* s, const std::vector<int>& pick)
+{
+    std::vector<int64_t> begin(s->max_slots), end(s->max_slots);
+    for (int i = 0; i < s->max_slots; ++i) {
+        begin[i] = s->slot_begin[i];
+        end[i] = s->slot_begin[i] + (pick[i] ? s->slot_nev[i] : 0);
+    }
+    return hw_set_units(s->hw, begin, end, pick, s->stream);
+}
+
 }  // namespace
 
 extern "C" {
@@ -2270,8 +2396,8 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
 {
     if (!out) return NLL_ERR_ARG;
     *out = nullptr;
-    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 1 || opt_in->hessian < 0 || opt_in->hessian > 1))
-        return NLL_ERR_ARG;  // the device-resident minimiser has the finite-difference Hessian only
+    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 2 || opt_in->hessian < 0 || opt_in->hessian > 3))
+        return NLL_ERR_ARG;
     if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges || max_slots < 1 ||
         pool_events < 1 || tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
         return NLL_ERR_ARG;
@@ -2309,6 +2435,7 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     s->cfg.npar = s->npar;
     for (int i = 0; i < 8; ++i) s->cfg.ranges[i] = s->ranges[i];
     setup_config(s->cfg, s->npar, lo, hi, step, fixed, opt);
+    s->hessian = opt.hessian;
     s->step.assign(s->npar, 0.0);
     for (int k = 0; k < s->npar; ++k) s->step[k] = step ? step[k] : 0.0;
     // pool: padded so a range of even length starting on an even event can end anywhere
@@ -2320,6 +2447,7 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     s->slot_id.assign(max_slots, 0);
     s->slot_begin.assign(max_slots, 0);
     s->slot_len.assign(max_slots, 0);
+    s->slot_nev.assign(max_slots, 0);
     const int64_t tp = s->tile_events / 2;
     s->max_items = max_slots * (2 * s->npar + 1);
     int64_t mu = (s->pool_events / 2 / tp + max_slots + 1) * (2 * (int64_t)s->npar + 1);
@@ -2330,6 +2458,11 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     s->max_units = (int)mu;
     cudaError_t e = ensure_btab(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && (s->cfg.strategy == 2 || s->hessian >= 2)) {
+        // every slot's units fit: the pool holds at most pool_events events
+        const int64_t cap = s->pool_events / kHessUnitEvents + max_slots + 1;
+        e = cap > (1 << 28) ? cudaErrorInvalidValue : hw_alloc(s->hw, max_slots, (int)cap, s->npar);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ev, sizeof(double) * s->n_pad * s->ncols);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ev, 0, sizeof(double) * s->n_pad * s->ncols, s->stream);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_begin, sizeof(int64_t) * max_slots);
@@ -2496,12 +2629,23 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
         pool_release(s, begin, len);
         return sfail(s, NLL_ERR_CUDA, "admission: %s", cudaGetErrorString(e));
     }
+    s->slot_begin[slot] = begin;
+    s->slot_len[slot] = len;
+    s->slot_nev[slot] = n_events;
+    if (s->cfg.strategy == 2) {  // start matrix from the analytic Hessian of this request
+        std::vector<int> pick(s->max_slots, 0);
+        pick[slot] = 1;
+        e = server_pick(s, pick);
+        if (e == cudaSuccess) e = run_hess_core(server_target(s), s->hw, s->cfg, kHmStart, false, nullptr, 0, true);
+        if (e != cudaSuccess) {
+            pool_release(s, begin, len);
+            return sfail(s, NLL_ERR_CUDA, "start Hessian: %s", cudaGetErrorString(e));
+        }
+    }
     s->h_done[slot] = 0;
     __atomic_add_fetch(s->h_active, 1, __ATOMIC_SEQ_CST);
     s->busy[slot] = 1;
     s->slot_id[slot] = s->next_id;
-    s->slot_begin[slot] = begin;
-    s->slot_len[slot] = len;
     *request_id = s->next_id++;
     return NLL_OK;
 }
@@ -2512,6 +2656,20 @@ int nll_server_poll(nll_server* s, int64_t* ids_out, fit_result* results, int ma
     *n_out = 0;
     cudaError_t e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
+    if (s->hessian >= 2) {  // Newton polish and covariance with the analytic Hessian, finished slots
+        std::vector<int> pick(s->max_slots, 0);
+        int np = 0;
+        for (int i = 0; i < s->max_slots && np < max_results; ++i)
+            if (s->busy[i] && ((volatile int*)s->h_done)[i]) {
+                pick[i] = 1;
+                ++np;
+            }
+        if (np) {
+            e = server_pick(s, pick);
+            if (e == cudaSuccess) e = polish_core(server_target(s), s->hw, s->cfg, s->hessian, true);
+            if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "Newton polish: %s", cudaGetErrorString(e));
+        }
+    }
     int n = 0;
     for (int i = 0; i < s->max_slots && n < max_results; ++i) {
         if (!s->busy[i] || !((volatile int*)s->h_done)[i]) continue;

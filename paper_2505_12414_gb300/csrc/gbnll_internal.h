@@ -116,9 +116,9 @@ cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int bl
                          cudaStream_t stream, const KArgs& a, bool in_place = false);
 cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a);
 cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BArgs& a);
-cudaError_t upload_exp2_table_values(const double* host_table);  // exp2_table_size() doubles from
-                                                                 // fill_device_tables, current device
-int exp2_table_size();
+// The exp and sin/cos table of kernels.cu's kernels (fill_device_tables) on the current device,
+// uploaded at the first call per device.
+cudaError_t ensure_device_tables();
 int num_acc(int kind, bool grad);
 
 // On-device generation (gen.cu): toy t gets counts[t] events from stream (seed, t) at

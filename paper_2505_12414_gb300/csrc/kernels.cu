@@ -212,16 +212,32 @@ cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SAr
 
 cudaError_t launch_basis(int blocks, int threads, cudaStream_t stream, const BArgs& a)
 {
+    // the basis takes sin/cos phi from the table: present on every device it runs on
+    cudaError_t e = ensure_device_tables();
+    if (e != cudaSuccess) return e;
     basis_kernel<<<blocks, threads, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t upload_exp2_table_values(const double* host_table)
-{
-    return cudaMemcpyToSymbol(g_exp2tab, host_table, kTabDoubles * sizeof(double));
-}
+namespace {
+std::mutex g_tab_mutex;
+bool g_tab_ready[64];
+}  // namespace
 
-int exp2_table_size() { return kTabDoubles; }
+cudaError_t ensure_device_tables()
+{
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_tab_mutex);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (g_tab_ready[device]) return cudaSuccess;
+    static double tab[kTabDoubles];
+    fill_device_tables(tab);
+    e = cudaMemcpyToSymbol(g_exp2tab, tab, kTabDoubles * sizeof(double));
+    if (e == cudaSuccess) g_tab_ready[device] = true;
+    return e;
+}
 
 // ----------------------------------------------------------------------------------
 // Static scratch for callers that cannot allocate device memory (nll_eval_grad_4d_noalloc).

@@ -33,19 +33,10 @@ const char* kNames4D[18] = {"mu",     "sigma",  "FL",     "S3",     "S4",     "S
                             "AFB",    "S7",     "S8",     "S9",     "alpha",  "c1_ctl",
                             "c2_ctl", "c1_ctk", "c2_ctk", "c1_phi", "c2_phi", "fsig"};
 
-std::mutex g_table_mutex;
-bool g_table_ready[64];
-
 int ensure_exp2_table(int device)
 {
-    std::lock_guard<std::mutex> lock(g_table_mutex);
     if (device < 0 || device >= 64) return NLL_ERR_ARG;
-    if (g_table_ready[device]) return NLL_OK;
-    std::vector<double> tab(exp2_table_size());
-    fill_device_tables(tab.data());
-    if (upload_exp2_table_values(tab.data()) != cudaSuccess) return NLL_ERR_CUDA;
-    g_table_ready[device] = true;
-    return NLL_OK;
+    return ensure_device_tables() == cudaSuccess ? NLL_OK : NLL_ERR_CUDA;  // current device
 }
 
 }  // namespace

@@ -142,3 +142,39 @@ def test_batch_pulls_mass_model(gpu_lib):
     assert np.all(np.abs(mean) < 4.0 / math.sqrt(ntoy) + 0.02), mean
     assert np.all(np.abs(width - 1.0) < 4.0 / math.sqrt(2 * ntoy) + 0.02), width
     b.close()
+
+
+def test_4d_basis_without_any_model_in_the_process():
+    # the angular basis takes sin/cos phi from the device table: a process that builds it through
+    # a batch or a server only (no single-sample model first) must upload that table itself
+    import subprocess
+    import sys
+    import textwrap
+
+    code = textwrap.dedent("""
+        import numpy as np
+        import oracle
+        import paper_2505_12414_gb300 as g
+        from paper_2505_12414_gb300 import synth
+        off = np.array([0, 3000, 5000], dtype=np.int64)
+        cols = synth.kstar4d(5000, stream=4242)
+        b = g.Batch(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D).load(off, cols, precompute=True)
+        nll, grad, st = b.eval_grad(synth.TRUTH_4D)
+        for t in range(2):
+            sl = slice(off[t], off[t + 1])
+            rn, rg, rs, _ = oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, [c[sl] for c in cols], synth.TRUTH_4D)
+            assert abs(nll[t] - rn) <= 1e-12 * abs(rn), (nll[t], rn)
+        s = g.Server(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, 2, 10000, 1024)
+        rid = s.submit([c[:3000] for c in cols], synth.TRUTH_4D)
+        done = []
+        for _ in range(2000):
+            s.step(4)
+            done += s.poll()
+            if done:
+                break
+        assert done and done[0][1]["status"] == 0, done
+        print("fresh-process basis ok")
+    """)
+    root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "fresh-process basis ok" in r.stdout, r.stdout + r.stderr

@@ -166,11 +166,12 @@ def test_weighted_fit_sandwich_covariance(gpu_lib):
     m.close()
 
 
-def test_served_fits_reject_analytic_options(gpu_lib):
+def test_host_callback_minimiser_rejects_analytic_options(gpu_lib):
+    # a host objective has no second derivatives; batched and served fits take the options
     for strategy, hessian in ((2, 1), (1, 2), (0, 3)):
-        with pytest.raises(gpu_lib.NLLError) as e:
-            gpu_lib.Server(M1, synth.RANGES_1D, 4, 100000, strategy=strategy, hessian=hessian)
-        assert e.value.status == gpu_lib.NLL_ERR_ARG
+        r = gpu_lib.fit_minimise_fcn(lambda x: (float(np.sum(x ** 2)), 2 * x), [1.0, 2.0], strategy=strategy,
+                                     hessian=hessian)
+        assert r["status"] == gpu_lib.NLL_ERR_ARG
 
 
 # --------------------------------------------------------------------------------------

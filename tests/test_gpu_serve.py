@@ -95,3 +95,42 @@ def test_served_fits_match_model_fits(gpu_lib):
         assert np.max(np.abs(pull)) < 1e-4, pull  # served fits stop at EDM 1e-12
     for s in srv.values():
         s.close()
+
+
+def opts_analytic(kind):
+    o = opts(kind)
+    o.update(strategy=2, hessian=2)
+    return o
+
+
+def test_analytic_served_fits(gpu_lib):
+    # served fits with the analytic start matrix (at admission) and the polished analytic
+    # covariance (at poll): each result is the same alone and in the mix, and matches the
+    # single-sample analytic fit
+    from paper_2505_12414_gb300.serve import serve
+
+    def run(reqs, slots, pool):
+        srv = {k: gpu_lib.Server(k, synth.RANGES_1D if k == M1 else synth.RANGES_4D, slots, pool, 1024,
+                                 **opts_analytic(k)) for k in (M1, M4)}
+        serve(srv, reqs, realtime=False)
+        for s in srv.values():
+            s.close()
+
+    mix = make_requests(8, 9300)
+    run(mix, 8, 200000)
+    alone = make_requests(8, 9300)
+    for r in alone:
+        run([r], 1, 20000)
+    for a, b in zip(mix, alone):
+        assert a.result["status"] == 0 and b.result["status"] == 0
+        assert np.array_equal(a.result["theta"], b.result["theta"])
+        assert np.array_equal(a.result["err"], b.result["err"])
+    for r in mix:
+        ranges = synth.RANGES_1D if r.kind == M1 else synth.RANGES_4D
+        m = gpu_lib.Model(r.kind, ranges).load(r.columns)
+        s = m.fit(r.theta0, **opts_analytic(r.kind))
+        m.close()
+        assert s["status"] == 0
+        assert np.max(np.abs((r.result["theta"] - s["theta"]) / s["err"])) < 1e-5
+        np.testing.assert_allclose(r.result["err"], s["err"], rtol=1e-4)
+        assert r.result["n_eval"] < 40
