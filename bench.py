@@ -228,7 +228,9 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
 def serving(g, device, n_req, rate, seed_stream=0):
     """Poisson-arrival stream of full fits mixing the mass and 4D models, event counts
     log-uniform in [1e3, 1e6]: continuous batching (nll_server_*) against the plain
-    one-fit-at-a-time GPU path on the same requests and arrival times."""
+    one-fit-at-a-time GPU path on the same requests and arrival times, once with
+    finite-difference Hessians of the analytic gradient (strategy 1, hessian 1) and once with
+    analytic second derivatives (strategy 2, hessian 2)."""
     from paper_2505_12414_gb300.serve import Request, latency_summary, serve, serve_sequential
 
     rs = synth.Stream(synth.BASE_SEED + 4242 + seed_stream, 0)
@@ -240,11 +242,6 @@ def serving(g, device, n_req, rate, seed_stream=0):
             g.NLL_MODEL_KSTARMUMU4D: np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])}
     truth = {g.NLL_MODEL_MASS1D: synth.TRUTH_1D, g.NLL_MODEL_KSTARMUMU4D: synth.TRUTH_4D}
     ranges = {g.NLL_MODEL_MASS1D: synth.RANGES_1D, g.NLL_MODEL_KSTARMUMU4D: synth.RANGES_4D}
-    opts = {}
-    for k in step:
-        lo, hi = np.zeros(len(step[k])), np.zeros(len(step[k]))
-        hi[-1] = 1.0
-        opts[k] = dict(lo=lo, hi=hi, step=step[k], tol_edm=1e-8, strategy=1, hessian=1)
     cols = []
     for i in range(n_req):
         gen = synth.mass1d if kinds[i] == g.NLL_MODEL_MASS1D else synth.kstar4d
@@ -254,27 +251,32 @@ def serving(g, device, n_req, rate, seed_stream=0):
         return [Request(i, kinds[i], cols[i], truth[kinds[i]] + 0.3 * step[kinds[i]], float(arrivals[i]))
                 for i in range(n_req)]
 
-    servers = {g.NLL_MODEL_MASS1D: g.Server(g.NLL_MODEL_MASS1D, synth.RANGES_1D, 16, 4_000_000, 4096,
-                                            device=device, **opts[g.NLL_MODEL_MASS1D]),
-               g.NLL_MODEL_KSTARMUMU4D: g.Server(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, 16, 8_000_000, 4096,
-                                                 device=device, **opts[g.NLL_MODEL_KSTARMUMU4D])}
-    serve(servers, requests()[:2], realtime=False)  # warm-up
-    served = serve(servers, requests(), realtime=True)
-    for srv in servers.values():
-        srv.close()
-    models = {k: g.Model(k, ranges[k], device=device) for k in step}
-    serve_sequential(models, requests()[:2], opts)  # warm-up
-    seq = serve_sequential(models, requests(), opts)
-    for m in models.values():
-        m.close()
-    diffs = [float(np.max(np.abs(a.result["theta"] - b.result["theta"]) / b.result["err"]))
-             for a, b in zip(served, seq) if a.result["status"] == 0 and b.result["status"] == 0]
-    out = {"requests": n_req, "rate_per_s": rate, "events_log_uniform": [1000, 1000000],
-           "served": latency_summary(served), "sequential": latency_summary(seq),
-           "converged": int(sum(r.result["status"] == 0 for r in served)),
-           "max_abs_diff_over_sigma_vs_sequential": max(diffs) if diffs else None}
-    if out["served"]["fits_per_s"] and out["sequential"]["fits_per_s"]:
-        out["speedup_fits_per_s"] = out["served"]["fits_per_s"] / out["sequential"]["fits_per_s"]
+    out = {"requests": n_req, "rate_per_s": rate, "events_log_uniform": [1000, 1000000]}
+    for label, strategy, hessian in (("fd", 1, 1), ("analytic", 2, 2)):
+        opts = {}
+        for k in step:
+            lo, hi = np.zeros(len(step[k])), np.zeros(len(step[k]))
+            hi[-1] = 1.0
+            opts[k] = dict(lo=lo, hi=hi, step=step[k], tol_edm=1e-8, strategy=strategy, hessian=hessian)
+        servers = {k: g.Server(k, ranges[k], 16, 4_000_000 if k == g.NLL_MODEL_MASS1D else 8_000_000, 4096,
+                               device=device, **opts[k]) for k in step}
+        serve(servers, requests()[:2], realtime=False)  # warm-up
+        served = serve(servers, requests(), realtime=True)
+        for srv in servers.values():
+            srv.close()
+        models = {k: g.Model(k, ranges[k], device=device) for k in step}
+        serve_sequential(models, requests()[:2], opts)  # warm-up
+        seq = serve_sequential(models, requests(), opts)
+        for m in models.values():
+            m.close()
+        diffs = [float(np.max(np.abs(a.result["theta"] - b.result["theta"]) / b.result["err"]))
+                 for a, b in zip(served, seq) if a.result["status"] == 0 and b.result["status"] == 0]
+        r = {"options": {"strategy": strategy, "hessian": hessian}, "served": latency_summary(served),
+             "sequential": latency_summary(seq), "converged": int(sum(q.result["status"] == 0 for q in served)),
+             "max_abs_diff_over_sigma_vs_sequential": max(diffs) if diffs else None}
+        if r["served"]["fits_per_s"] and r["sequential"]["fits_per_s"]:
+            r["speedup_fits_per_s"] = r["served"]["fits_per_s"] / r["sequential"]["fits_per_s"]
+        out[label] = r
     return out
 
 

@@ -1247,6 +1247,7 @@ namespace {
 struct HessWork {
     bool ready = false;
     int cap_toys = 0, cap_units = 0, np = 0, n_units = 0;
+    int layout_key = -1;  // slot table on the device: kind, weights, W
     int* d_unit_toy = nullptr;
     int64_t* d_unit_e0 = nullptr;
     int* d_toy_u0 = nullptr;
@@ -1358,11 +1359,15 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
 {
     HessLayout L;
     if (!hess_layout(T.kind, T.weighted, want_w2, &L)) return cudaErrorInvalidValue;
-    std::vector<uint16_t> slot_of(64 * 64, 0xffff);
-    for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * L.ncols + L.sj[k]] = (uint16_t)k;
     const int n = T.n_toys, np = cfg.npar;
-    cudaError_t e = cudaMemcpyAsync(w.d_slot_of, slot_of.data(), sizeof(uint16_t) * slot_of.size(),
-                                    cudaMemcpyHostToDevice, T.stream);
+    cudaError_t e = cudaSuccess;
+    const int key = T.kind * 4 + (T.weighted ? 2 : 0) + (want_w2 ? 1 : 0);
+    if (key != w.layout_key) {  // (slot -> column pair) inverse table, uploaded when it changes
+        std::vector<uint16_t> slot_of(64 * 64, 0xffff);
+        for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * L.ncols + L.sj[k]] = (uint16_t)k;
+        e = cudaMemcpy(w.d_slot_of, slot_of.data(), sizeof(uint16_t) * slot_of.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) w.layout_key = key;
+    }
     if (e == cudaSuccess && mode == kHmEval)
         e = cudaMemcpyAsync(w.d_thetas, thetas, sizeof(double) * np * n, cudaMemcpyHostToDevice, T.stream);
     if (e != cudaSuccess) return e;
