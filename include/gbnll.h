@@ -393,14 +393,18 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
  * success *request_id identifies the fit and its events are on the device.
  * Returns NLL_ERR_STATE (nothing admitted) when no slot or no pool range is free: the
  * caller keeps the request queued and retries after nll_server_poll returned finished fits.
- * Returns NLL_ERR_ARG for events outside the ranges or more events than the whole pool.
+ * Returns NLL_ERR_ARG for events outside the ranges (checked on the device after the copy;
+ * the pool range is released again) or more events than the whole pool.
  */
 int nll_server_submit(nll_server* s, const double* const* columns, const double* weights, int64_t n_events,
                       const double* theta0, int64_t* request_id);
 
 /* Queue n_steps device steps (graph replays) advancing every busy slot; returns without
  * waiting, so steps of servers on different streams overlap on the device.  nll_server_sync
- * waits for them (nll_server_poll and nll_server_submit also wait first). */
+ * waits for them (nll_server_poll and nll_server_submit also wait first).  With strategy 2
+ * the call first runs one analytic Hessian pass over the fits admitted since the last step
+ * (their start matrices) and waits for it.  With hessian 2 / 3 nll_server_poll polishes the
+ * finished fits with the analytic Hessian (Newton passes, covariance) before returning them. */
 int nll_server_step(nll_server* s, int n_steps);
 int nll_server_sync(nll_server* s);
 

@@ -2242,10 +2242,16 @@ struct nll_server {
     std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end) in pool events, sorted
     std::vector<char> busy;
     std::vector<int64_t> slot_id, slot_begin, slot_len, slot_nev;
+    std::vector<int> need_start;  // strategy 2: admitted slots whose start matrix is still due
     int64_t next_id = 1;
     FitConfig cfg;
     int hessian = 0;  // fit_options.hessian: 2 / 3 polish finished slots with the analytic Hessian
     HessWork hw;      // analytic Hessian passes (strategy 2, hessian 2 / 3)
+    // admission statistics on the device (range check, sum (m - ma)) of a request's events
+    double* d_spart = nullptr;
+    unsigned int* d_sticket = nullptr;
+    double* h_sout = nullptr;  // mapped [3]
+    double* d_sout = nullptr;
     std::vector<double> step;
     // device work arrays
     int64_t* d_begin = nullptr;
@@ -2297,6 +2303,9 @@ void server_free(nll_server* s)
         if (p) cudaFree(p);
     if (s->h_active) cudaFreeHost(s->h_active);
     if (s->h_done) cudaFreeHost(s->h_done);
+    if (s->d_spart) cudaFree(s->d_spart);
+    if (s->d_sticket) cudaFree(s->d_sticket);
+    if (s->h_sout) cudaFreeHost(s->h_sout);
     hw_free(s->hw);
     if (s->stream) cudaStreamDestroy(s->stream);
 }
@@ -2453,6 +2462,7 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     s->slot_begin.assign(max_slots, 0);
     s->slot_len.assign(max_slots, 0);
     s->slot_nev.assign(max_slots, 0);
+    s->need_start.assign(max_slots, 0);
     const int64_t tp = s->tile_events / 2;
     s->max_items = max_slots * (2 * s->npar + 1);
     int64_t mu = (s->pool_events / 2 / tp + max_slots + 1) * (2 * (int64_t)s->npar + 1);
@@ -2468,6 +2478,11 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
         const int64_t cap = s->pool_events / kHessUnitEvents + max_slots + 1;
         e = cap > (1 << 28) ? cudaErrorInvalidValue : hw_alloc(s->hw, max_slots, (int)cap, s->npar);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_spart, sizeof(double) * 3 * 2 * s->sm_count);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_sticket, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_sout, sizeof(double) * 3, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_sout, s->h_sout, 0);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_ev, sizeof(double) * s->n_pad * s->ncols);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ev, 0, sizeof(double) * s->n_pad * s->ncols, s->stream);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_begin, sizeof(int64_t) * max_slots);
@@ -2568,6 +2583,18 @@ int nll_server_step(nll_server* s, int n_steps)
 {
     if (!s || n_steps < 0) return NLL_ERR_ARG;
     if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
+    bool starts = false;
+    for (int i = 0; i < s->max_slots; ++i) starts = starts || (s->busy[i] && s->need_start[i]);
+    if (starts && n_steps > 0) {  // start matrices of the requests admitted since the last step
+        std::vector<int> pick(s->max_slots, 0);
+        for (int i = 0; i < s->max_slots; ++i) pick[i] = s->busy[i] && s->need_start[i];
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) e = server_pick(s, pick);
+        if (e == cudaSuccess) e = run_hess_core(server_target(s), s->hw, s->cfg, kHmStart, false, nullptr, 0, true);
+        if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "start Hessians: %s", cudaGetErrorString(e));
+        for (int i = 0; i < s->max_slots; ++i)
+            if (pick[i]) s->need_start[i] = 0;
+    }
     for (int i = 0; i < n_steps; ++i) {
         cudaError_t e = cudaGraphLaunch(s->exec, s->stream);
         if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server step: %s", cudaGetErrorString(e));
@@ -2587,16 +2614,6 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
         if (!isfinite(theta0[k])) return sfail(s, NLL_ERR_ARG, "start point not finite");
     const int64_t len = std::max<int64_t>((n_events + 1) & ~int64_t(1), 2);
     if (len > s->pool_events) return sfail(s, NLL_ERR_ARG, "more events than the whole pool");
-    // validate events and sum (m - ma) on the host
-    double sum = 0.0;
-    for (int64_t i = 0; i < n_events; ++i) {
-        for (int d = 0; d < s->ndim; ++d) {
-            double x = columns[d][i];
-            if (!(x >= s->ranges[2 * d] && x <= s->ranges[2 * d + 1]))
-                return sfail(s, NLL_ERR_ARG, "event %lld outside the observable ranges", (long long)i);
-        }
-        sum += columns[0][i] - s->ranges[0];
-    }
     if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
     cudaError_t e = cudaStreamSynchronize(s->stream);  // no step may run while a slot is rewritten
     if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
@@ -2612,6 +2629,34 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
     for (int d = 0; d < s->ndim && e == cudaSuccess && n_events > 0; ++d)
         e = cudaMemcpyAsync(s->d_ev + (size_t)d * s->n_pad + begin, columns[d], sizeof(double) * n_events,
                             cudaMemcpyHostToDevice, s->stream);
+    // range check and sum (m - ma) of the request on the device (load-time statistics kernel)
+    double sum = 0.0;
+    if (e == cudaSuccess && n_events > 0) {
+        SArgs sa;
+        memset(&sa, 0, sizeof sa);
+        for (int d = 0; d < s->ndim; ++d) {
+            sa.col[d] = s->d_ev + (size_t)d * s->n_pad + begin;
+            sa.lo[d] = s->ranges[2 * d];
+            sa.hi[d] = s->ranges[2 * d + 1];
+        }
+        sa.w = nullptr;
+        sa.n = n_events;
+        sa.ndim = s->ndim;
+        sa.partials = s->d_spart;
+        sa.ticket = s->d_sticket;
+        sa.out = s->d_sout;
+        const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n_events + 255) / 256, 1), 2 * s->sm_count);
+        e = launch_stats(blocks, 256, s->stream, sa);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) {
+            if (((volatile double*)s->h_sout)[2] != 0.0) {
+                pool_release(s, begin, len);
+                return sfail(s, NLL_ERR_ARG, "%.0f event(s) outside the observable ranges",
+                             ((volatile double*)s->h_sout)[2]);
+            }
+            sum = ((volatile double*)s->h_sout)[1];
+        }
+    }
     if (e == cudaSuccess && s->kind == kKstar4D && n_events > 0) {
         BArgs ba;
         ba.ctl = s->d_ev + (size_t)kColCtl * s->n_pad + begin;
@@ -2637,16 +2682,9 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
     s->slot_begin[slot] = begin;
     s->slot_len[slot] = len;
     s->slot_nev[slot] = n_events;
-    if (s->cfg.strategy == 2) {  // start matrix from the analytic Hessian of this request
-        std::vector<int> pick(s->max_slots, 0);
-        pick[slot] = 1;
-        e = server_pick(s, pick);
-        if (e == cudaSuccess) e = run_hess_core(server_target(s), s->hw, s->cfg, kHmStart, false, nullptr, 0, true);
-        if (e != cudaSuccess) {
-            pool_release(s, begin, len);
-            return sfail(s, NLL_ERR_CUDA, "start Hessian: %s", cudaGetErrorString(e));
-        }
-    }
+    // strategy 2: the start matrix comes from one analytic Hessian pass over every request
+    // admitted since the last step, run by the next nll_server_step before its first graph step
+    s->need_start[slot] = s->cfg.strategy == 2 ? 1 : 0;
     s->h_done[slot] = 0;
     __atomic_add_fetch(s->h_active, 1, __ATOMIC_SEQ_CST);
     s->busy[slot] = 1;

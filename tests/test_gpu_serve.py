@@ -134,3 +134,18 @@ def test_analytic_served_fits(gpu_lib):
         assert np.max(np.abs((r.result["theta"] - s["theta"]) / s["err"])) < 1e-5
         np.testing.assert_allclose(r.result["err"], s["err"], rtol=1e-4)
         assert r.result["n_eval"] < 40
+
+
+def test_admission_rejects_events_outside_the_ranges(gpu_lib):
+    # the range check runs on the device at admission; a rejected request frees its pool range
+    s = gpu_lib.Server(M4, synth.RANGES_4D, 2, 6000, 1024, **opts(M4))
+    cols = [c.copy() for c in synth.kstar4d(3000, stream=77)]
+    cols[2][1234] = 1.2  # cos theta_K outside [-1, 1]
+    with pytest.raises(gpu_lib.NLLError) as e:
+        s.submit(cols, synth.TRUTH_4D)
+    assert e.value.status == gpu_lib.NLL_ERR_ARG
+    st = s.status()
+    assert st["busy"] == 0 and st["free_events"] == 6000
+    cols[2][1234] = 0.2
+    assert s.submit(cols, synth.TRUTH_4D) is not None
+    s.close()
