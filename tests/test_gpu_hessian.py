@@ -277,3 +277,27 @@ def test_batch_weighted_sandwich(gpu_lib):
         Hi = np.linalg.inv(ref["hess"])
         close_cov(r["cov"][t], Hi @ ref["w2"] @ Hi)
     b.close()
+
+
+def test_batched_weighted_pulls_with_the_sandwich(gpu_lib):
+    # 1000 weighted toys (weights 0.2 or 2, unrelated to the data): pulls with the sandwich
+    # covariance (hessian 3) have unit width; with the plain inverse Hessian (hessian 2) the
+    # spread is underestimated by sqrt(E[w^2] / E[w]) = 1.36
+    import math
+
+    ntoy, nev = 1000, 2000
+    off, cols = synth.toys1d(ntoy, nev, fixed_size=True)
+    w = np.where(synth.Stream(synth.BASE_SEED, 830000).uniform(int(off[-1])) < 0.5, 0.2, 2.0)
+    lo, hi = _bounds(M1)
+    b = gpu_lib.Batch(M1, synth.RANGES_1D).load(off, cols, w)
+    widths = {}
+    for hessian in (3, 2):
+        r = b.fit(synth.TRUTH_1D, lo=lo, hi=hi, step=_step(M1), tol_edm=1e-10, strategy=2, hessian=hessian)
+        assert np.mean(r["status"] == 0) > 0.995
+        ok = r["status"] == 0
+        pulls = (r["theta"][ok] - synth.TRUTH_1D) / r["err"][ok]
+        widths[hessian] = pulls.std(axis=0)
+        assert np.all(np.abs(pulls.mean(axis=0)) < 4.0 / math.sqrt(ntoy) * widths[hessian] + 0.02)
+    assert np.all(np.abs(widths[3] - 1.0) < 4.0 / math.sqrt(2 * ntoy) + 0.02), widths[3]
+    assert np.all(widths[2] > 1.2), widths[2]
+    b.close()

@@ -679,3 +679,34 @@ def test_hessian_scale_bounds_the_plain_form_cancellation():
     err = abs(r["hess"][2, 3] - ref)
     assert err > 1e-9 * abs(ref)  # the cancellation is real ...
     assert err <= 1e-13 * r["hscale"][2, 3]  # ... and the scale accounts for it
+
+
+def two_valued_weights(n, stream):
+    # weights independent of the events, 0.2 or 2 with equal probability:
+    # E[w] = 1.1, E[w^2] = 2.02, so the weighted estimator's spread exceeds the inverse
+    # Hessian's prediction by sqrt(E[w^2] / E[w]) = 1.36
+    return np.where(synth.Stream(synth.BASE_SEED, stream).uniform(n) < 0.5, 0.2, 2.0)
+
+
+def test_sandwich_covariance_matches_the_spread_of_weighted_fits():
+    # statistical pin of reading "weighted-fit covariance": over pseudo-experiments with
+    # weights unrelated to the data, the sandwich H^-1 W H^-1 predicts the spread of the fitted
+    # values; the plain inverse Hessian does not
+    ntoy, nev = 300, 2000
+    fitted, sand, naive = [], [], []
+    for t in range(ntoy):
+        m = synth.mass1d(nev, stream=810000 + t)
+        w = two_valued_weights(nev, 820000 + t)
+        r = ofit.fit(M1, synth.RANGES_1D, m, synth.TRUTH_1D, w=w, tol_edm=1e-12, h0=[0.5, 0.5, 2e-5, 0.02])
+        assert r["converged"]
+        h = oracle.nll_hess(M1, synth.RANGES_1D, m, r["theta"], w=w)
+        Hi = np.linalg.inv(h["hess"])
+        fitted.append(r["theta"])
+        sand.append(np.sqrt(np.diag(Hi @ h["w2"] @ Hi)))
+        naive.append(np.sqrt(np.diag(Hi)))
+    spread = np.std(np.array(fitted), axis=0)
+    ratio_sand = spread / np.mean(np.array(sand), axis=0)
+    ratio_naive = spread / np.mean(np.array(naive), axis=0)
+    # the standard deviation of 300 values is known to ~4 %; 4 sigma bands
+    assert np.all(np.abs(ratio_sand - 1.0) < 0.17), ratio_sand
+    assert np.all(ratio_naive > 1.2), ratio_naive
