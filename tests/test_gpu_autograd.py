@@ -58,3 +58,30 @@ def test_backward_against_oracle_10M_weighted(gpu_lib):
     g = theta.grad.cpu().numpy() / 2.0
     assert np.all(np.abs(g - rg) <= 1e-9 * np.abs(rg) + 1e-13 * rs)
     m.close()
+
+
+def test_second_derivatives_through_autograd(gpu_lib):
+    # double backward and torch.autograd.functional.hessian use the analytic Hessian pass
+    import torch
+
+    from paper_2505_12414_gb300 import autograd
+
+    cols = synth.kstar4d(20000, stream=32)
+    w = synth.weights(20000, stream=33)
+    m = gpu_lib.Model(gpu_lib.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D).load(cols, w)
+    th0 = synth.TRUTH_4D + 0.01
+    _, g_ref, H_ref = m.eval_hess(th0)
+    theta = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    H = torch.autograd.functional.hessian(lambda t: autograd.nll(m, t), theta)
+    assert np.array_equal(H.numpy(), H_ref)
+    # Hessian-vector product by double backward
+    v = torch.linspace(-1.0, 1.0, 18, dtype=torch.float64)
+    y = autograd.nll(m, theta)
+    (g,) = torch.autograd.grad(y, theta, create_graph=True)
+    assert np.array_equal(g.detach().numpy(), m.eval_grad(th0)[1])
+    (hv,) = torch.autograd.grad(g @ v, theta)
+    np.testing.assert_allclose(hv.numpy(), H_ref @ v.numpy(), rtol=1e-13, atol=1e-13 * np.abs(H_ref).max())
+    # and the Hessian agrees with the oracle
+    ref = oracle.nll_hess(oracle.KSTAR4D, synth.RANGES_4D, cols, th0, w=w)
+    assert np.all(np.abs(H.numpy() - ref["hess"]) <= 1e-9 * np.abs(ref["hess"]) + 1e-12 * ref["hscale"])
+    m.close()
