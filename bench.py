@@ -85,6 +85,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the mass-model event-count sweep")
     ap.add_argument("--no-calibration", action="store_true", help="skip the FP64 calibration kernels")
     ap.add_argument("--no-hessian", action="store_true", help="skip the analytic-Hessian measurement")
+    ap.add_argument("--no-capacity", action="store_true", help="skip the 2e8-event resident-sample measurement")
     ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0],
                     help="Poisson arrival rates of served fits per second (one measurement each)")
     return ap.parse_args()
@@ -409,6 +410,35 @@ def hessian_bench(g, model, theta, flush, stream, reps=5):
     return out
 
 
+def capacity(g, device, stream, n_events=200_000_000, reps=5):
+    """Throughput on a large resident 4D sample: n_events generated on the device at the truth,
+    loaded with the precomputed basis (17 FP64 columns, 136 B/event in HBM), NLL+gradient
+    evaluated reps times (the sample is 200x the L2, no flush needed)."""
+    import torch
+
+    cols = g.nll_generate(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, synth.TRUTH_4D, n_events,
+                          seed=synth.BASE_SEED, stream=99, device=device)
+    m = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    m.load(cols, precompute=True)
+    load_s = time.perf_counter() - t0
+    del cols
+    torch.cuda.empty_cache()
+    th = thetas(reps + 2)
+    m.eval_grad(th[0])
+    g.nll_set_profiling(m.handle, True)
+    kms = []
+    for i in range(reps):
+        m.eval_grad(th[1 + i])
+        kms.append(g.nll_last_kernel_ms(m.handle))
+    k = statistics.median(kms)
+    out = {"n_events": n_events, "hbm_bytes_resident": 136 * n_events, "load_s": load_s,
+           "kernel_ms": k, "events_per_s": n_events / (k * 1e-3),
+           "fp64_tflops_algorithmic": FLOPS_PER_EVENT * n_events / (k * 1e-3) / 1e12}
+    m.close()
+    return out
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -547,6 +577,7 @@ def run_ours(args):
                     "lib_exp_slots": rates["dfma"] / rates["lib_exp"]}}
 
     hess = None if args.no_hessian else hessian_bench(g, model, th[0], flush, stream)
+    cap = None if args.no_capacity else capacity(g, local, stream)
 
     toys = None
     if args.toys > 0:
@@ -580,7 +611,7 @@ def run_ours(args):
                                       "ms_per_step": e2e_copy_step,
                                       "mode": "load() copies the pinned columns, then eval_grad, direct variant"}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": args.steps,
-                "hessian": hess, "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
+                "hessian": hess, "capacity_4d": cap, "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
                 "mass_model_sweep": sweep}
         print(json.dumps(line), flush=True)
     model.close()
