@@ -71,6 +71,8 @@ struct KArgs {
     double* partials;             // [K][max_blocks] per-block sums (K = slots of the launch)
     unsigned int* ticket;         // grid-completion counter, 0 between launches
     double* out;                  // [K] final sums
+    unsigned int* done;           // or NULL: completion word, set to seq once out is written
+    unsigned int seq;
     // in-place evaluation only: ma, and order keys of [lo, hi] per observable and of the
     // weights' range [-0, 1e300] (slot 4); see order_key in nll_device.cuh
     double ma;

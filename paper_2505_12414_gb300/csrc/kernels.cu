@@ -68,12 +68,24 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
     const int64_t end = npairs * (blockIdx.x + 1) / gridDim.x;
     int64_t p = begin + threadIdx.x;
 
-    // the first pair's loads are in flight while the block stages the exp table
+    // The table's loads are issued first and the first pair's behind them, so the block's
+    // first barrier does not wait for the pair data; the sin/cos part of the table is
+    // staged only where the angular basis is computed here.
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    constexpr int nper = ntab / 64;  // per thread at the smallest block (64 threads)
+    double tv[nper];
+#pragma unroll
+    for (int i = 0; i < nper; ++i) {
+        const int j = threadIdx.x + i * blockDim.x;
+        if (j < ntab) tv[i] = g_exp2tab[j];
+    }
     PairIn in;
     if (p < end) load_pair<KIND, VAR, W, IP>(a, p, in);
-    // the sin/cos part of the table only where the angular basis is computed here
-    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
-    for (int j = threadIdx.x; j < ntab; j += blockDim.x) s_tab[j] = g_exp2tab[j];
+#pragma unroll
+    for (int i = 0; i < nper; ++i) {
+        const int j = threadIdx.x + i * blockDim.x;
+        if (j < ntab) s_tab[j] = tv[i];
+    }
     __syncthreads();
 
     double acc[K];
@@ -95,7 +107,38 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
         acc[0] = (threadIdx.x & 31) == 0 ? lw : 0.0;
     }
     acc[K - 1] = (double)bad;
-    grid_reduce<K>(acc, s_red, a.partials, a.ticket, a.out);
+    block_partials<K>(acc, s_red, a.partials);
+}
+
+// Final sums of a fused launch: block k adds slot k's nb block partials in a fixed order
+// (thread t takes blocks t, t + 64, ...; then a shuffle tree and the two warps), writes
+// out[k] and, with `done` set, stores seq into done[k] after a system-scope fence, so a host
+// thread polling done[0..K) reads complete results.  It is launched as a programmatic
+// dependent of the fused kernel: griddepcontrol.wait returns once that grid has finished and
+// its partials are visible, about a microsecond after its last block exits, where a plain
+// stream-ordered launch would start several microseconds later.  Spreading the K slots over
+// K blocks (K SMs) keeps this step off the single-SM FP64 bottleneck a last-block reduction
+// has, and needs no ticket or grid-wide fence in the fused kernel.
+__global__ void __launch_bounds__(64) final_reduce_kernel(const double* partials, int nb, double* out,
+                                                          unsigned int* done, unsigned int seq)
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    __shared__ double s_hi;
+    const double* pk = partials + (int64_t)blockIdx.x * nb;
+    double r = 0.0;
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nb; b += 64) r += __ldcg(pk + b);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (threadIdx.x == 32) s_hi = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[blockIdx.x] = r + s_hi;
+        if (done) {
+            __threadfence_system();
+            reinterpret_cast<volatile unsigned int*>(done)[blockIdx.x] = seq;
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------------
@@ -190,18 +233,42 @@ static cudaError_t launch_kv(bool weighted, bool grad, int blocks, int threads, 
     return cudaGetLastError();
 }
 
+static cudaError_t launch_final(int nslots, int nb, cudaStream_t stream, const KArgs& a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nslots);
+    cfg.blockDim = dim3(64);
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, final_reduce_kernel, (const double*)a.partials, nb, a.out, a.done, a.seq);
+}
+
+// The fused kernel (block partials) and, behind it, the final per-slot sums into a.out.
 cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,
                          cudaStream_t stream, const KArgs& a, bool in_place)
 {
-    if (threads > 256 || threads < 32 || (threads & 31)) return cudaErrorInvalidValue;
+    if (threads > 256 || threads < 64 || (threads & 31) || blocks < 1) return cudaErrorInvalidValue;
+    cudaError_t e;
     if (in_place) {
-        if (kind == kMass1D) return launch_kv<kMass1D, kVarPrecompute, true>(weighted, grad, blocks, threads, stream, a);
-        if (variant != kVarDirect) return cudaErrorInvalidValue;
-        return launch_kv<kKstar4D, kVarDirect, true>(weighted, grad, blocks, threads, stream, a);
+        if (kind == kMass1D)
+            e = launch_kv<kMass1D, kVarPrecompute, true>(weighted, grad, blocks, threads, stream, a);
+        else if (variant != kVarDirect)
+            return cudaErrorInvalidValue;
+        else
+            e = launch_kv<kKstar4D, kVarDirect, true>(weighted, grad, blocks, threads, stream, a);
+    } else if (kind == kMass1D) {
+        e = launch_kv<kMass1D, kVarPrecompute, false>(weighted, grad, blocks, threads, stream, a);
+    } else if (variant == kVarDirect) {
+        e = launch_kv<kKstar4D, kVarDirect, false>(weighted, grad, blocks, threads, stream, a);
+    } else {
+        e = launch_kv<kKstar4D, kVarPrecompute, false>(weighted, grad, blocks, threads, stream, a);
     }
-    if (kind == kMass1D) return launch_kv<kMass1D, kVarPrecompute, false>(weighted, grad, blocks, threads, stream, a);
-    if (variant == kVarDirect) return launch_kv<kKstar4D, kVarDirect, false>(weighted, grad, blocks, threads, stream, a);
-    return launch_kv<kKstar4D, kVarPrecompute, false>(weighted, grad, blocks, threads, stream, a);
+    if (e != cudaSuccess) return e;
+    return launch_final(num_acc(kind, grad) + (in_place ? kAccInPlace : 0), blocks, stream, a);
 }
 
 cudaError_t launch_stats(int blocks, int threads, cudaStream_t stream, const SArgs& a)

@@ -177,8 +177,8 @@ __device__ __forceinline__ double block_reduce(const double (&v)[K], double* sme
     return res;
 }
 
-// Block partials -> scratch; the last block to arrive sums them in block order into
-// out[0..K).  Resets the ticket for the next launch.
+// Block partials -> scratch; the last block to arrive sums them in a fixed order into
+// out[0..K) and resets the ticket for the next launch (used by the load-time statistics).
 template <int K>
 __device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, double* partials,
                                             unsigned int* ticket, double* out)
@@ -193,7 +193,6 @@ __device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // each thread sums a fixed strided subset of blocks for every slot, then a fixed tree
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
@@ -204,6 +203,15 @@ __device__ __forceinline__ void grid_reduce(const double (&v)[K], double* smem, 
     double tot = block_reduce<K>(acc, smem);
     if (threadIdx.x < K) out[threadIdx.x] = tot;
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// Block partials -> scratch, slot-major (partials[k * nb + block]); the final sums are
+// taken by final_reduce_kernel, launched behind the fused kernel.
+template <int K>
+__device__ __forceinline__ void block_partials(const double (&v)[K], double* smem, double* partials)
+{
+    double bsum = block_reduce<K>(v, smem);
+    if (threadIdx.x < K) partials[threadIdx.x * gridDim.x + blockIdx.x] = bsum;
 }
 
 // ----------------------------------------------------------------------------------

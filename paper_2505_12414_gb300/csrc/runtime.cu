@@ -71,6 +71,11 @@ struct nll_model {
     unsigned int* d_ticket = nullptr;
     double* d_out = nullptr;  // device alias of h_out
     double* h_out = nullptr;  // mapped pinned host memory, written by the kernels
+    // completion words after the kAccModel result slots, one per slot: an evaluation launch
+    // stores its sequence number in word k once slot k is written, and the host polls them
+    unsigned int* h_done = nullptr;
+    unsigned int* d_done = nullptr;
+    unsigned int seq = 0;
 
     // launch shape
     int bps = 2, threads = 256, variant = 0;
@@ -78,7 +83,8 @@ struct nll_model {
     // profiling
     bool profiling = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    double last_ms = -1.0;
+    mutable double last_ms = -1.0;
+    mutable bool ms_pending = false;  // ev0/ev1 bracket a launch whose time is not read yet
 
     // analytic Hessian scratch (allocated at the first nll_eval_hess)
     double* d_hpart = nullptr;          // [kHessMaxSlots][hess_max_blocks]
@@ -317,6 +323,11 @@ int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int
     a.partials = m->d_partials;
     a.ticket = m->d_ticket;
     a.out = m->d_out;
+    if (record) {
+        if (++m->seq == 0u) m->seq = 1u;  // 0 is the word's initial value
+        a.done = m->d_done;
+        a.seq = m->seq;
+    }
     int blocks = launch_blocks(m, bps, threads);
     cudaError_t e;
     if (record && m->profiling) cudaEventRecord(m->ev0, m->stream);
@@ -366,6 +377,27 @@ void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, do
 
 namespace {
 
+// Waits for the evaluation launch numbered seq with K result slots: polls the mapped
+// completion words, which the final-sum kernel sets after a system-scope fence once each
+// slot is in h_out (this returns a few microseconds before the stream would report the
+// launch complete), and asks the stream every 1024 polls whether it failed or went idle
+// without setting them.
+cudaError_t wait_done(nll_model* m, unsigned int seq, int K)
+{
+    int k = 0;
+    for (unsigned int it = 1;; ++it) {
+        while (k < K && __atomic_load_n(m->h_done + k, __ATOMIC_ACQUIRE) == seq) ++k;
+        if (k == K) return cudaSuccess;
+        if ((it & 1023u) == 0u) {
+            cudaError_t q = cudaStreamQuery(m->stream);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) return q;
+            while (k < K && __atomic_load_n(m->h_done + k, __ATOMIC_ACQUIRE) == seq) ++k;
+            return k == K ? cudaSuccess : cudaErrorLaunchFailure;  // stream idle, words not set
+        }
+    }
+}
+
 int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out)
 {
     if (!m) return NLL_ERR_ARG;
@@ -387,11 +419,11 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
         st = run_fused(m, H, grad, m->bps, m->threads, var, true);
         if (st != NLL_OK) return st;
-        cudaError_t e = cudaStreamSynchronize(m->stream);
+        cudaError_t e = wait_done(m, m->seq, K);
         if (e != cudaSuccess) return cuda_fail(m, e, "evaluation");
-        if (m->profiling) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, m->ev0, m->ev1) == cudaSuccess) m->last_ms = ms;
+        if (m->profiling) {  // the kernel time is read when asked for (nll_last_kernel_ms)
+            m->ms_pending = true;
+            m->last_ms = -1.0;
         }
         memcpy(S, m->h_out, K * sizeof(double));
     }
@@ -485,6 +517,7 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         if (e != cudaSuccess) return cuda_fail(m, e, "Hessian evaluation");
         if (m->profiling) {
             float ms = 0.f;
+            m->ms_pending = false;
             if (cudaEventElapsedTime(&ms, m->ev0, m->ev1) == cudaSuccess) m->last_ms = ms;
         }
         memcpy(sums, m->h_hout, sizeof(double) * L.nslots);
@@ -605,8 +638,14 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
     if (e == cudaSuccess) e = cudaMalloc(&m->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(m->d_ticket, 0, sizeof(unsigned int));
     // results land in mapped pinned host memory: the grid's last block writes them there
-    if (e == cudaSuccess) e = cudaHostAlloc(&m->h_out, sizeof(double) * kAccModel, cudaHostAllocMapped);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&m->h_out, sizeof(double) * kAccModel + sizeof(unsigned int) * kAccModel, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_out, m->h_out, 0);
+    if (e == cudaSuccess) {
+        m->h_done = reinterpret_cast<unsigned int*>(m->h_out + kAccModel);
+        m->d_done = reinterpret_cast<unsigned int*>(m->d_out + kAccModel);
+        for (int k = 0; k < kAccModel; ++k) m->h_done[k] = 0u;
+    }
     if (e == cudaSuccess) e = cudaEventCreate(&m->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&m->ev1);
     if (e != cudaSuccess) {
@@ -860,6 +899,8 @@ int nll_autotune(nll_model* m)
     if (!m->loaded || !m->have_last || m->n == 0)
         return fail(m, NLL_ERR_STATE, "autotune needs loaded events and one prior evaluation");
     if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
+    m->ms_pending = false;  // the sweep below re-records ev0/ev1
+    m->last_ms = -1.0;
     // candidate shapes: for each block size, 1x and 2x the resident blocks per SM
     std::vector<std::pair<int, int>> shapes;
     bool grad_ok = m->last.f > 0.0 && m->last.f < 1.0;
@@ -912,12 +953,19 @@ int nll_set_profiling(nll_model* m, int on)
     if (!m) return NLL_ERR_ARG;
     m->profiling = on != 0;
     m->last_ms = -1.0;
+    m->ms_pending = false;
     return NLL_OK;
 }
 
 int nll_last_kernel_ms(const nll_model* m, double* ms)
 {
     if (!m || !ms) return NLL_ERR_ARG;
+    if (m->ms_pending) {
+        m->ms_pending = false;
+        float t = 0.f;
+        if (cudaEventSynchronize(m->ev1) == cudaSuccess && cudaEventElapsedTime(&t, m->ev0, m->ev1) == cudaSuccess)
+            m->last_ms = t;
+    }
     if (m->last_ms < 0.0) return NLL_ERR_STATE;
     *ms = m->last_ms;
     return NLL_OK;
