@@ -55,6 +55,18 @@ class fit_result(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+_FIT_RESULT_DTYPE = np.dtype(fit_result)  # the same layout as a numpy record
+
+
+def _results_of(res, n, **extra):
+    """Per-fit arrays from a record array of fit_result (n parameters)."""
+    out = dict(theta=res["theta"][:, :n].copy(), err=res["err"][:, :n].copy(), nll=res["nll"].copy(),
+               edm=res["edm"].copy(), n_eval=res["n_eval"].copy(), n_iter=res["n_iter"].copy(),
+               status=res["status"].copy(), cov=res["cov"][:, : n * n].reshape(-1, n, n).copy())
+    out.update(extra)
+    return out
+
+
 FIT_FCN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
 
@@ -611,23 +623,14 @@ class Batch:
         th, lo, hi, step, fx = _fit_args(t0.reshape(-1)[: self.npar] if shared else t0[0], lo, hi, step, fixed)
         th = _f64(t0)
         opt = fit_options(tol_edm, max_iter, strategy, hessian)
-        res = (fit_result * max(self.n_toys, 1))()
+        res = np.empty(max(self.n_toys, 1), dtype=_FIT_RESULT_DTYPE)  # filled by the library
         steps = ctypes.c_int()
         st = load().nll_batch_fit(self.handle, _p(th), shared, _p(lo), _p(hi), _p(step),
-                                  fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt), res,
-                                  ctypes.byref(steps))
+                                  fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt),
+                                  res.ctypes.data_as(ctypes.POINTER(fit_result)), ctypes.byref(steps))
         if st not in (NLL_OK, NLL_ERR_NOT_CONVERGED):
             _bcheck(self.handle, st)
-        n = self.npar
-        out = dict(theta=np.array([r.theta[:n] for r in res[: self.n_toys]]),
-                   err=np.array([r.err[:n] for r in res[: self.n_toys]]),
-                   nll=np.array([r.nll for r in res[: self.n_toys]]),
-                   edm=np.array([r.edm for r in res[: self.n_toys]]),
-                   n_eval=np.array([r.n_eval for r in res[: self.n_toys]]),
-                   n_iter=np.array([r.n_iter for r in res[: self.n_toys]]),
-                   status=np.array([r.status for r in res[: self.n_toys]]), steps=steps.value)
-        out["cov"] = np.array([np.ctypeslib.as_array(r.cov)[: n * n].reshape(n, n) for r in res[: self.n_toys]])
-        return out
+        return _results_of(res[: self.n_toys], self.npar, steps=steps.value)
 
     def set_schedule(self, tile_events=0, blocks_per_sm=0):
         _bcheck(self.handle, load().nll_batch_set_schedule(self.handle, int(tile_events), int(blocks_per_sm)))

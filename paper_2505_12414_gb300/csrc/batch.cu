@@ -962,6 +962,68 @@ __device__ void polish_reject(const HessDev& h, ToyFit& F, int lane)
 // thread per toy: toys that finished the loop at a parameter point (converged, or stopped by a
 // stalled line search or the iteration limit) are polished; after the last pass a toy still
 // polishing returns to its accepted point
+// Every toy's fit state set up on the device (block per toy): zeroed, then the start state
+// from th0 (one shared point, or n x npar) and the steps (or NULL).
+static_assert(sizeof(ToyFit) % 8 == 0, "ToyFit is zeroed as 64-bit words");
+// Start state of one toy's fit (F zeroed by the caller): transformed start point and
+// internal steps.  Host (served fits) and device (batched fits) share it.
+__host__ __device__ void init_fit_fields(ToyFit& F, const FitConfig& c, const double* th0, const double* step)
+{
+    for (int k = 0; k < c.npar; ++k) F.th[k] = th0[k];
+    for (int i = 0; i < c.nf; ++i) {
+        const int k = c.idx[i];
+        double x = th0[k];
+        double J = 1.0;
+        if (c.bounded[k]) {
+            double u = 2.0 * (x - c.lo[k]) / (c.hi[k] - c.lo[k]) - 1.0;
+            u = fmin(fmax(u, -1.0 + 1e-10), 1.0 - 1e-10);
+            x = asin(u);
+            J = (c.hi[k] - c.lo[k]) * 0.5 * cos(x);
+        }
+        F.xt[i] = x;
+        double s0 = step && step[k] > 0.0 ? step[k] : fmax(1e-3 * fabs(th0[k]), 1e-3);
+        double si = s0 / fmax(fabs(J), 1e-8);
+        if (c.bounded[k]) si = fmin(si, 0.5);
+        F.sint[i] = si;
+    }
+    F.phase = kPhInit;
+    F.status = NLL_ERR_NOT_CONVERGED;
+    for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
+}
+
+__global__ void __launch_bounds__(128) batch_init_fits(ToyFit* fits, int n, const FitConfig c, const double* th0,
+                                                       int shared, const double* step)
+{
+    const int t = blockIdx.x;
+    if (t >= n) return;
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(fits + t);
+    for (int i = threadIdx.x; i < (int)(sizeof(ToyFit) / 8); i += blockDim.x) w[i] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) init_fit_fields(fits[t], c, shared ? th0 : th0 + (size_t)t * c.npar, step);
+}
+
+// Results of every toy packed for the host (block per toy), kResStride doubles each:
+// th[npar] | err[nf] | cov[nf x nf] (free parameters) | nll, edm, n_eval, n_iter, status.
+constexpr int kResStride = 2 * kNP + kNP * kNP + 5;
+__global__ void __launch_bounds__(128) batch_pack_results(const ToyFit* fits, int n, int np, int nf, double* res)
+{
+    const int t = blockIdx.x;
+    if (t >= n) return;
+    const ToyFit& F = fits[t];
+    double* r = res + (size_t)t * kResStride;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) r[i] = F.th[i];
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) r[kNP + i] = F.err[i];
+    for (int i = threadIdx.x; i < nf * nf; i += blockDim.x) r[2 * kNP + i] = F.cov[i];
+    if (threadIdx.x == 0) {
+        double* tail = r + 2 * kNP + kNP * kNP;
+        tail[0] = F.f;
+        tail[1] = F.edm;
+        tail[2] = (double)F.n_eval;
+        tail[3] = (double)F.iter;
+        tail[4] = (double)(F.phase == kPhDone ? F.status : NLL_ERR_NOT_CONVERGED);
+    }
+}
+
 __global__ void batch_polish_init(ToyFit* fits, int n, const int* sel)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1464,6 +1526,15 @@ struct nll_batch {
     int* d_unit_tile = nullptr;
     double* d_unit_sums = nullptr;
     ToyFit* d_fits = nullptr;
+    // fit set-up and results (allocated at the first nll_batch_fit for the loaded toys)
+    double* d_init = nullptr;  // start points [n_toys x npar] then steps [npar]
+    double* h_res = nullptr;   // mapped pinned, kResStride doubles per toy (batch_pack_results)
+    double* d_res = nullptr;
+    // the instantiated device step of nll_batch_fit and the parameters it was captured with
+    cudaGraph_t fit_graph = nullptr;
+    cudaGraphExec_t fit_exec = nullptr;
+    BatchDev fit_dev;
+    int fit_shape[4] = {0, 0, 0, 0};
     // analytic Hessian pass (allocated at its first use for the loaded toys)
     HessWork hw;
     // schedule
@@ -1496,6 +1567,13 @@ int bcuda(nll_batch* b, cudaError_t e, const char* what)
 void free_work(nll_batch* b)
 {
     hw_free(b->hw);
+    if (b->fit_exec) cudaGraphExecDestroy(b->fit_exec);
+    if (b->fit_graph) cudaGraphDestroy(b->fit_graph);
+    b->fit_exec = nullptr;
+    b->fit_graph = nullptr;
+    if (b->d_init) cudaFree(b->d_init);
+    if (b->h_res) cudaFreeHost(b->h_res);
+    b->d_init = b->h_res = b->d_res = nullptr;
     void* ptrs[] = {b->d_ev, b->d_begin, b->d_end, b->d_sum_wdm, b->d_item_toy, b->d_item_u0, b->d_item_nt,
                     b->d_item_kc, b->d_item_dc, b->d_unit_item, b->d_unit_tile, b->d_unit_sums, b->d_fits};
     for (void* p : ptrs)
@@ -1792,26 +1870,7 @@ void setup_config(FitConfig& c, int np, const double* lo, const double* hi, cons
 void init_fit(ToyFit& F, const FitConfig& c, const double* th0, const double* step)
 {
     memset(&F, 0, sizeof F);
-    for (int k = 0; k < c.npar; ++k) F.th[k] = th0[k];
-    for (int i = 0; i < c.nf; ++i) {
-        const int k = c.idx[i];
-        double x = th0[k];
-        double J = 1.0;
-        if (c.bounded[k]) {
-            double u = 2.0 * (x - c.lo[k]) / (c.hi[k] - c.lo[k]) - 1.0;
-            u = std::min(std::max(u, -1.0 + 1e-10), 1.0 - 1e-10);
-            x = asin(u);
-            J = (c.hi[k] - c.lo[k]) * 0.5 * cos(x);
-        }
-        F.xt[i] = x;
-        double s0 = step && step[k] > 0.0 ? step[k] : std::max(1e-3 * fabs(th0[k]), 1e-3);
-        double si = s0 / std::max(fabs(J), 1e-8);
-        if (c.bounded[k]) si = std::min(si, 0.5);
-        F.sint[i] = si;
-    }
-    F.phase = kPhInit;
-    F.status = NLL_ERR_NOT_CONVERGED;
-    for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
+    init_fit_fields(F, c, th0, step);
 }
 
 // fit_result of one finished toy
@@ -1829,6 +1888,24 @@ void fill_result(const ToyFit& F, const FitConfig& c, fit_result& r)
     r.n_eval = F.n_eval;
     r.n_iter = F.iter;
     r.status = F.phase == kPhDone ? F.status : NLL_ERR_NOT_CONVERGED;
+}
+
+// fit_result of one toy from its batch_pack_results record
+void fill_result_packed(const double* p, const FitConfig& c, fit_result& r)
+{
+    const int np = c.npar, nf = c.nf;
+    memset(&r, 0, sizeof r);
+    for (int k = 0; k < np; ++k) r.theta[k] = p[k];
+    for (int i = 0; i < nf; ++i) {
+        r.err[c.idx[i]] = p[kNP + i];
+        for (int j = 0; j < nf; ++j) r.cov[c.idx[i] * np + c.idx[j]] = p[2 * kNP + i * nf + j];
+    }
+    const double* tail = p + 2 * kNP + kNP * kNP;
+    r.nll = tail[0];
+    r.edm = tail[1];
+    r.n_eval = (int)tail[2];
+    r.n_iter = (int)tail[3];
+    r.status = (int)tail[4];
 }
 
 }  // namespace
@@ -2123,51 +2200,76 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     FitConfig& c = d.cfg;
     setup_config(c, np, lo, hi, step, fixed, opt);
     const int nf = c.nf;
-    std::vector<ToyFit> fits(n);
-    for (int t = 0; t < n; ++t) init_fit(fits[t], c, shared_start ? theta0 : theta0 + (size_t)t * np, step);
+    // start states on the device: only the start points and steps cross the link
+    cudaError_t e = cudaSuccess;
+    if (!b->d_init) e = cudaMalloc(&b->d_init, sizeof(double) * ((size_t)n + 1) * kNP);
+    if (e == cudaSuccess && !b->h_res) {
+        e = cudaHostAlloc(&b->h_res, sizeof(double) * (size_t)n * kResStride, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_res, b->h_res, 0);
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "fit set-up buffers");
+    const size_t nth = shared_start ? (size_t)np : (size_t)n * np;
+    double* d_step = b->d_init + (size_t)n * kNP;
     *b->h_active = n;
-    cudaError_t e = follow_user_stream(b);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_fits, fits.data(), sizeof(ToyFit) * n, cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "fit state upload");
+    e = follow_user_stream(b);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_init, theta0, sizeof(double) * nth, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess && step)
+        e = cudaMemcpyAsync(d_step, step, sizeof(double) * np, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) {
+        batch_init_fits<<<n, 128, 0, b->stream>>>(b->d_fits, n, c, b->d_init, shared_start ? 1 : 0,
+                                                  step ? d_step : nullptr);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return bcuda(b, e, "fit state set-up");
     if (opt.strategy == 2) {  // start matrices from the analytic Hessian at every toy's start point
         int st = run_hess_pass(b, c, kHmStart, false, nullptr);
         if (st != NLL_OK) return st;
     }
 
-    // one device step = counter reset, prepare, evaluate, update; captured once
+    // one device step = counter reset, prepare, evaluate, update; captured once and kept while
+    // the batch's buffers and the fit configuration stay the same
     const int eval_blocks = b->sm_count * b->bps;
     const int prep_blocks = (n + 127) / 128;
     const int upd_blocks = (n + kUpdWarps - 1) / kUpdWarps;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 3, b->stream);
-        batch_prepare<<<prep_blocks, 128, 0, b->stream>>>(d);
-        launch_eval(b->kind, variant_of(b), b->weighted, eval_blocks, b->stream, d);
-        if (b->kind == kMass1D)
-            batch_update<kMass1D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
-        else
-            batch_update<kKstar4D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
-        e = cudaStreamEndCapture(b->stream, &graph);
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        return bcuda(b, e, "fit graph");
+    const int shape[4] = {eval_blocks, prep_blocks, upd_blocks, variant_of(b)};
+    if (!b->fit_exec || memcmp(&b->fit_dev, &d, sizeof d) != 0 || memcmp(b->fit_shape, shape, sizeof shape) != 0) {
+        if (b->fit_exec) cudaGraphExecDestroy(b->fit_exec);
+        if (b->fit_graph) cudaGraphDestroy(b->fit_graph);
+        b->fit_exec = nullptr;
+        b->fit_graph = nullptr;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 3, b->stream);
+            batch_prepare<<<prep_blocks, 128, 0, b->stream>>>(d);
+            launch_eval(b->kind, variant_of(b), b->weighted, eval_blocks, b->stream, d);
+            if (b->kind == kMass1D)
+                batch_update<kMass1D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
+            else
+                batch_update<kKstar4D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
+            e = cudaStreamEndCapture(b->stream, &graph);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return bcuda(b, e, "fit graph");
+        }
+        b->fit_graph = graph;
+        b->fit_exec = exec;
+        b->fit_dev = d;
+        memcpy(b->fit_shape, shape, sizeof shape);
     }
     const int max_steps = opt.max_iter * 40 + 8;  // every line-search trial is one step
     int steps = 0;
     while (steps < max_steps) {
         const int burst = steps < 8 ? 1 : 4;  // poll often at first, then every few steps
-        for (int r = 0; r < burst && e == cudaSuccess; ++r, ++steps) e = cudaGraphLaunch(exec, b->stream);
+        for (int r = 0; r < burst && e == cudaSuccess; ++r, ++steps) e = cudaGraphLaunch(b->fit_exec, b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) break;
         if (*(volatile int*)b->h_active <= 0) break;
     }
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
     if (e != cudaSuccess) return bcuda(b, e, "fit loop");
     if (steps_out) *steps_out = steps;
     if (opt.hessian >= 2) {
@@ -2178,12 +2280,13 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         e = polish_core(target_of(b), b->hw, c, opt.hessian, false);
         if (e != cudaSuccess) return bcuda(b, e, "Newton polish");
     }
-    e = cudaMemcpyAsync(fits.data(), b->d_fits, sizeof(ToyFit) * n, cudaMemcpyDeviceToHost, b->stream);
+    batch_pack_results<<<n, 128, 0, b->stream>>>(b->d_fits, n, np, nf, b->d_res);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "fit state download");
+    if (e != cudaSuccess) return bcuda(b, e, "fit results");
     int all = NLL_OK;
     for (int t = 0; t < n; ++t) {
-        fill_result(fits[t], c, results[t]);
+        fill_result_packed(b->h_res + (size_t)t * kResStride, c, results[t]);
         if (results[t].status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
     }
     return all;
