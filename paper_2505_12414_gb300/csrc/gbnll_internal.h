@@ -159,6 +159,8 @@ struct HArgs {
     int lnp_slot;          // unweighted: slot that receives the block's sum of ln P (else -1)
     double* partials;      // [kHessMaxSlots][blocks], reduced by a second launch
     double* out;           // [nslots]
+    unsigned int* done;    // or NULL: completion words [nslots], set to seq once out[s] is written
+    unsigned int seq;
     uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];  // column pair of each slot
 };
 

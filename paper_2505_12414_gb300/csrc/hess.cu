@@ -118,10 +118,15 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 }
 
 // Slot totals: block s sums the per-block partials of slot s (thread l takes blocks l,
-// l + 128, ...), then a fixed butterfly per warp and the four warp sums in order.
+// l + 128, ...), then a fixed butterfly per warp and the four warp sums in order; with
+// `done` set it then stores seq into done[s] after a system-scope fence (the host polls
+// these words).  Launched as a programmatic dependent of hess_kernel: griddepcontrol.wait
+// returns once that grid has finished and its partials are visible.
 __global__ void __launch_bounds__(kHessThreads) hess_reduce_kernel(const double* __restrict__ partials, int nb,
-                                                                   double* __restrict__ out)
+                                                                   double* __restrict__ out, unsigned int* done,
+                                                                   unsigned int seq)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ double s_w[kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, s = blockIdx.x;
     const double* p = partials + (size_t)s * nb;
@@ -131,7 +136,13 @@ __global__ void __launch_bounds__(kHessThreads) hess_reduce_kernel(const double*
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) s_w[t >> 5] = v;
     __syncthreads();
-    if (t == 0) out[s] = (s_w[0] + s_w[1]) + (s_w[2] + s_w[3]);
+    if (t == 0) {
+        out[s] = (s_w[0] + s_w[1]) + (s_w[2] + s_w[3]);
+        if (done) {
+            __threadfence_system();
+            reinterpret_cast<volatile unsigned int*>(done)[s] = seq;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -279,8 +290,16 @@ static cudaError_t launch_t(int blocks, cudaStream_t s, const HArgs& a)
     hess_kernel<KIND, VAR, W><<<blocks, kHessThreads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    hess_reduce_kernel<<<a.nslots, kHessThreads, 0, s>>>(a.partials, blocks, a.out);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.nslots);
+    cfg.blockDim = dim3(kHessThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, hess_reduce_kernel, (const double*)a.partials, blocks, a.out, a.done, a.seq);
 }
 
 template <int KIND, int VAR, bool W>

@@ -88,8 +88,10 @@ struct nll_model {
 
     // analytic Hessian scratch (allocated at the first nll_eval_hess)
     double* d_hpart = nullptr;          // [kHessMaxSlots][hess_max_blocks]
-    double* h_hout = nullptr;           // mapped pinned [kHessMaxSlots]
+    double* h_hout = nullptr;           // mapped pinned [kHessMaxSlots], then kHessMaxSlots completion words
     double* d_hout = nullptr;
+    unsigned int* h_hdone = nullptr;
+    unsigned int* d_hdone = nullptr;
     int hess_max_blocks = 0;
 
     // last valid constant block (for autotuning)
@@ -303,6 +305,12 @@ int effective_variant(const nll_model* m)
     return m->has_basis ? kVarPrecompute : kVarDirect;
 }
 
+unsigned int next_seq(nll_model* m)
+{
+    if (++m->seq == 0u) m->seq = 1u;  // 0 is the words' initial value
+    return m->seq;
+}
+
 int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int variant, bool record)
 {
     KArgs a;
@@ -324,9 +332,8 @@ int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int
     a.ticket = m->d_ticket;
     a.out = m->d_out;
     if (record) {
-        if (++m->seq == 0u) m->seq = 1u;  // 0 is the word's initial value
         a.done = m->d_done;
-        a.seq = m->seq;
+        a.seq = next_seq(m);
     }
     int blocks = launch_blocks(m, bps, threads);
     cudaError_t e;
@@ -377,26 +384,27 @@ void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, do
 
 namespace {
 
-// Waits for the evaluation launch numbered seq with K result slots: polls the mapped
-// completion words, which the final-sum kernel sets after a system-scope fence once each
-// slot is in h_out (this returns a few microseconds before the stream would report the
-// launch complete), and asks the stream every 1024 polls whether it failed or went idle
-// without setting them.
-cudaError_t wait_done(nll_model* m, unsigned int seq, int K)
+// Waits for a launch numbered seq with K result slots: polls the K mapped completion words,
+// which the final-sum kernels set after a system-scope fence once each slot's result is in
+// host memory (this returns a few microseconds before the stream would report the launch
+// complete), and asks the stream every 1024 polls whether it failed or went idle without
+// setting them.
+cudaError_t wait_words(cudaStream_t stream, const unsigned int* words, unsigned int seq, int K)
 {
     int k = 0;
     for (unsigned int it = 1;; ++it) {
-        while (k < K && __atomic_load_n(m->h_done + k, __ATOMIC_ACQUIRE) == seq) ++k;
+        while (k < K && __atomic_load_n(words + k, __ATOMIC_ACQUIRE) == seq) ++k;
         if (k == K) return cudaSuccess;
         if ((it & 1023u) == 0u) {
-            cudaError_t q = cudaStreamQuery(m->stream);
+            cudaError_t q = cudaStreamQuery(stream);
             if (q == cudaErrorNotReady) continue;
             if (q != cudaSuccess) return q;
-            while (k < K && __atomic_load_n(m->h_done + k, __ATOMIC_ACQUIRE) == seq) ++k;
+            while (k < K && __atomic_load_n(words + k, __ATOMIC_ACQUIRE) == seq) ++k;
             return k == K ? cudaSuccess : cudaErrorLaunchFailure;  // stream idle, words not set
         }
     }
 }
+
 
 int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, double* grad_out)
 {
@@ -419,7 +427,7 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
         st = run_fused(m, H, grad, m->bps, m->threads, var, true);
         if (st != NLL_OK) return st;
-        cudaError_t e = wait_done(m, m->seq, K);
+        cudaError_t e = wait_words(m->stream, m->h_done, m->seq, K);
         if (e != cudaSuccess) return cuda_fail(m, e, "evaluation");
         if (m->profiling) {  // the kernel time is read when asked for (nll_last_kernel_ms)
             m->ms_pending = true;
@@ -452,8 +460,14 @@ int ensure_hess_scratch(nll_model* m)
     if (m->d_hpart) return NLL_OK;
     m->hess_max_blocks = m->sm_count * kHessMaxBlocksPerSm;
     cudaError_t e = cudaMalloc(&m->d_hpart, sizeof(double) * kHessMaxSlots * (size_t)m->hess_max_blocks);
-    if (e == cudaSuccess) e = cudaHostAlloc(&m->h_hout, sizeof(double) * kHessMaxSlots, cudaHostAllocMapped);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(&m->h_hout, (sizeof(double) + sizeof(unsigned int)) * kHessMaxSlots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_hout, m->h_hout, 0);
+    if (e == cudaSuccess) {
+        m->h_hdone = reinterpret_cast<unsigned int*>(m->h_hout + kHessMaxSlots);
+        m->d_hdone = reinterpret_cast<unsigned int*>(m->d_hout + kHessMaxSlots);
+        for (int k = 0; k < kHessMaxSlots; ++k) m->h_hdone[k] = 0u;
+    }
     if (e != cudaSuccess) {
         if (m->d_hpart) cudaFree(m->d_hpart);
         if (m->h_hout) cudaFreeHost(m->h_hout);
@@ -503,6 +517,8 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         a.lnp_slot = L.lnp_slot;
         a.partials = m->d_hpart;
         a.out = m->d_hout;
+        a.done = m->d_hdone;
+        a.seq = next_seq(m);
         memcpy(a.si, L.si, sizeof a.si);
         memcpy(a.sj, L.sj, sizeof a.sj);
         int occ = std::min(std::max(hess_occupancy(m->kind, var, m->weighted), 1), kHessMaxBlocksPerSm);
@@ -513,12 +529,11 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         cudaError_t e = launch_hess(m->kind, var, m->weighted, blocks, m->stream, a);
         if (e != cudaSuccess) return cuda_fail(m, e, "Hessian kernel launch");
         if (m->profiling) cudaEventRecord(m->ev1, m->stream);
-        e = cudaStreamSynchronize(m->stream);
+        e = wait_words(m->stream, m->h_hdone, a.seq, L.nslots);
         if (e != cudaSuccess) return cuda_fail(m, e, "Hessian evaluation");
-        if (m->profiling) {
-            float ms = 0.f;
-            m->ms_pending = false;
-            if (cudaEventElapsedTime(&ms, m->ev0, m->ev1) == cudaSuccess) m->last_ms = ms;
+        if (m->profiling) {  // the kernel time is read when asked for (nll_last_kernel_ms)
+            m->ms_pending = true;
+            m->last_ms = -1.0;
         }
         memcpy(sums, m->h_hout, sizeof(double) * L.nslots);
     }
