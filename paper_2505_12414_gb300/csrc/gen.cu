@@ -45,12 +45,15 @@ __host__ __device__ __forceinline__ uint64_t stream_state(uint64_t seed, uint64_
     return sm64_mix(seed ^ sm64_mix(stream * kGamma + 1));
 }
 
-// double in (0, 1) from 64 random bits
-__device__ __forceinline__ double u01(uint64_t x) { return ((double)(x >> 11) + 0.5) * 0x1p-53; }
+// double in (0, 1) from 64 random bits: ((x >> 11) + 1/2) 2^-53, as one conversion and one
+// fma (the fma rounds k 2^-53 + 2^-54 once, which is (k + 1/2) rounded, then scaled exactly)
+__device__ __forceinline__ double u01(uint64_t x) { return fma((double)(x >> 11), 0x1p-53, 0x1p-54); }
 
 struct GenConst {
     int kind;
     double ma, mb, mu, sigma, alpha, em1;  // em1 = expm1(alpha (mb - ma))
+    double inv_alpha;                      // 1 / alpha (0 when alpha is 0)
+    int bg_log1p;                          // |em1| < 1/16: background mass from log1p (see gen_kernel)
     double fsig;
     double ang[8];                         // FL, S3, S4, S5, AFB, S7, S8, S9
     double amax;                           // accept-reject bound of the angular rate
@@ -81,7 +84,7 @@ __device__ double angular_rate(const GenConst& g, double ctl, double ctk, double
                g.ang[4] * (4.0 / 3.0) * sk2 * ctl;
     if (!g.fold_phi) {
         double sp, cp;
-        sincos(phi, &sp, &cp);
+        sincospi(phi * (1.0 / kPiG), &sp, &cp);
         double c2p = 2.0 * cp * cp - 1.0, s2p = 2.0 * sp * cp;
         r += g.ang[1] * sk2 * sl2 * c2p + g.ang[7] * sk2 * sl2 * s2p;
         if (!g.fold_sin) {
@@ -114,9 +117,19 @@ __global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
         double m = g.ma, ctl = 0.0, ctk = 0.0, phi = 0.0;
         bool ok = false;
         int k = 1;
+        // Draw (1, 0) is the Box-Muller radius draw of the first signal try and the
+        // inverse-distribution draw of a background mass: one logarithm, taken by the whole
+        // warp, serves both (log(1 + u em1) for the background: 1 + u em1 lies in
+        // [exp(alpha (mb - ma)), 1] and is formed with one rounding, which costs no accuracy
+        // that matters unless |em1| is small; then log1p takes the background, a branch that
+        // is uniform because em1 is a constant of the launch).
+        const double u1 = draw(1, 0);
+        const double lg1 = g.bg_log1p ? (sig ? log(u1) : log1p(u1 * g.em1)) : log(sig ? u1 : fma(u1, g.em1, 1.0));
         if (sig) {
+            double lg = lg1;
             for (; k < kMaxTries; ++k) {  // Box-Muller, truncated to the window
-                double z = sqrt(-2.0 * log(draw(k, 0))) * cos(2.0 * kPiG * draw(k, 1));
+                if (k > 1) lg = log(draw(k, 0));
+                double z = sqrt(-2.0 * lg) * cospi(2.0 * draw(k, 1));
                 m = g.mu + g.sigma * z;
                 if (m >= g.ma && m <= g.mb) {
                     ok = true;
@@ -136,8 +149,7 @@ __global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
                 }
             }
         } else {
-            double u = draw(1, 0);
-            m = g.alpha == 0.0 ? g.ma + u * D : g.ma + log1p(u * g.em1) / g.alpha;
+            m = g.alpha == 0.0 ? fma(u1, D, g.ma) : fma(lg1, g.inv_alpha, g.ma);
             m = fmin(fmax(m, g.ma), g.mb);
             ok = true;
             if (g.kind == kKstar4D) {
@@ -193,6 +205,8 @@ static bool gen_setup(int kind, const double* ranges, const double* th, GenConst
     g.fsig = kind == kMass1D ? th[3] : th[17];
     if (!(g.sigma > 0.0) || !(g.fsig >= 0.0 && g.fsig <= 1.0)) return false;
     g.em1 = expm1(g.alpha * (g.mb - g.ma));
+    g.inv_alpha = g.alpha == 0.0 ? 0.0 : 1.0 / g.alpha;
+    g.bg_log1p = fabs(g.em1) < 0.0625 ? 1 : 0;
     if (kind == kKstar4D) {
         double sum = 0.0;
         for (int j = 0; j < 8; ++j) g.ang[j] = th[2 + j];
