@@ -200,6 +200,8 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
     k.b2 = b2;
     if (kind == kKstar4D) {
         for (int j = 0; j < 8; ++j) k.ang[j] = th[2 + j];
+        k.k0d = (lnb1 + kLnBasisC - alpha * (mu - ma)) * S;
+        for (int j = 0; j < 8; ++j) k.angd[j] = th[2 + j] * direct_factor(j + 1);
         k.cq[0] = b2;
         k.cq[1] = b2 * th[11];
         k.cq[2] = b2 * th[12];
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
             acc[0] = (threadIdx.x & 31) == 0 ? lw : 0.0;
         }
         acc[K - 1] = (double)bad;
+        if (KIND == kKstar4D && VAR == kVarDirect) direct_unscale<K>(acc);
         double r = block_reduce<K>(acc, s_red);
         if (threadIdx.x < K) b.unit_sums[(size_t)u * kAccMax + threadIdx.x] = r;
     }

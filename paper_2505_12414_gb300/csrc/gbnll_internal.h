@@ -61,7 +61,19 @@ struct KConst {
     double b2;         // mass model: background constant (1-f) / Ntilde2
     double ang[8];     // FL, S3, S4, S5, AFB, S7, S8, S9
     double cq[9];      // background factors: C_j = cq[3j] + cq[3j+1] x_j + cq[3j+2] T2(x_j)
+    // 4D, angular basis computed per evaluation (direct variant), which drops the basis'
+    // constant factors: h_k = c F_k q_k with c = 9/(32 pi) (direct_factor gives F_k), so
+    // A = c (q_0 + sum_k ang_k F_k q_k); c goes into the exponent, F_k into the coefficients.
+    double k0d;        // S (ln b1 + ln c - alpha (mu - ma))
+    double angd[8];    // ang[k] F_{k+1}
 };
+
+// F_k of the direct variant's basis (k = 1..8: FL, S3, S4, S5, AFB, S7, S8, S9).
+__host__ __device__ constexpr double direct_factor(int k)
+{
+    return k == 3 || k == 7 ? 4.0 : (k == 4 || k == 6 || k == 8) ? 2.0 : k == 5 ? 4.0 / 3.0 : 1.0;
+}
+constexpr double kLnBasisC = -2.41324121131290733843909748479889;  // ln(9 / (32 pi))
 
 struct KArgs {
     const double* col[kNumCols];  // device column pointers (unused ones NULL)

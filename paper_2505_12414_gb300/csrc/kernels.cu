@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
         acc[0] = (threadIdx.x & 31) == 0 ? lw : 0.0;
     }
     acc[K - 1] = (double)bad;
+    if (KIND == kKstar4D && VAR == kVarDirect && GRAD) direct_unscale<K>(acc);
     block_partials<K>(acc, s_red, a.partials);
 }
 

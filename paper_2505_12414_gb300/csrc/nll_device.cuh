@@ -49,6 +49,50 @@ __device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi
     t2p = fma(xp + xp, xp, -1.0);
 }
 
+// The same basis without its constant factors, for evaluations that compute it per event
+// (direct variant): h_k = c F_k q_k with c = 9/(32 pi) and F_k = direct_factor(k) (F_0 = 1),
+//   q0 = sK^2 (1 - sl^2/2), q1 = 2 cK^2 sl^2 - q0, q2 = sK^2 sl^2 cos 2phi,
+//   q3 = ctl q4, q4 = ctK sK sl cos phi, q5 = sK^2 ctl, q6 = ctK sK sl sin phi, q7 = ctl q6,
+//   q8 = sK^2 sl^2 sin phi cos phi,
+// which saves the multiplications by c, 2, 4 and 4/3 (the callers put c into the exponent
+// and F_k into the coefficients and the gradient sums).
+__device__ __forceinline__ void angular_basis_direct(double ctl, double ctk, double phi, double q[9], double& t2l,
+                                                     double& t2k, double& xp, double& t2p, const double* trig)
+{
+    const double kInvPi = 0x1.45f306dc9c883p-2;
+    const double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);
+    const double a = sk2 * sl2;
+    const double sksl = sqrt(a);
+    double sp, cp;
+    fsincos_pi(phi, trig, sp, cp);
+    t2l = fma(-2.0, sl2, 1.0);
+    t2k = fma(-2.0, sk2, 1.0);
+    const double q0 = fma(-0.5, a, sk2);
+    const double ck2 = ctk * ctk;
+    const double bq = ctk * sksl;
+    const double q4 = bq * cp, q6 = bq * sp;
+    q[0] = q0;
+    q[1] = fma(ck2 + ck2, sl2, -q0);
+    q[2] = a * fma(cp + cp, cp, -1.0);
+    q[3] = ctl * q4;
+    q[4] = q4;
+    q[5] = sk2 * ctl;
+    q[6] = q6;
+    q[7] = ctl * q6;
+    q[8] = a * (sp * cp);
+    xp = phi * kInvPi;
+    t2p = fma(xp + xp, xp, -1.0);
+}
+
+// Per-thread gradient sums of the direct variant back to the basis h_k: sum R E' q_k times F_k.
+template <int K>
+__device__ __forceinline__ void direct_unscale(double (&acc)[K])
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+        if (direct_factor(k + 1) != 1.0) acc[4 + k] *= direct_factor(k + 1);
+}
+
 // ----------------------------------------------------------------------------------
 // Per-event bodies.  acc[] slots as documented in gbnll_internal.h.  `valid` == false
 // turns the event into an exact no-op (factor 1 in the product, R = 0 in every sum), so
@@ -81,16 +125,16 @@ __device__ __forceinline__ void event_mass(const KConst& c, double m, double w, 
     }
 }
 
-template <bool W, bool GRAD>
+template <bool W, bool GRAD, bool DIR = false>
 __device__ __forceinline__ void event_4d(const KConst& c, double m, const double h[9], double xl, double t2l,
                                          double xk, double t2k, double xp, double t2p, double w, bool valid,
                                          double* acc, LogProd& lp, int& bad, const double* tab)
 {
     double d = m - c.mu;
-    double E = fexp_scaled(fma(d, fma(c.neg_b0, d, c.neg_alpha), c.k0), tab);
-    double A = fma(c.ang[0], h[1], h[0]);
+    double E = fexp_scaled(fma(d, fma(c.neg_b0, d, c.neg_alpha), DIR ? c.k0d : c.k0), tab);
+    double A = fma(DIR ? c.angd[0] : c.ang[0], h[1], h[0]);
 #pragma unroll
-    for (int k = 1; k < 8; ++k) A = fma(c.ang[k], h[k + 1], A);
+    for (int k = 1; k < 8; ++k) A = fma(DIR ? c.angd[k] : c.ang[k], h[k + 1], A);
     double C1 = fma(c.cq[1], xl, fma(c.cq[2], t2l, c.cq[0]));
     double C2 = fma(c.cq[4], xk, fma(c.cq[5], t2k, c.cq[3]));
     double C3 = fma(c.cq[7], xp, fma(c.cq[8], t2p, c.cq[6]));
@@ -323,12 +367,13 @@ __device__ __forceinline__ void process_pair(const KConst& c, const PairIn& in, 
             xpy = in.xp.y;
             t2px = in.t2p.x;
             t2py = in.t2p.y;
-        } else {
-            angular_basis(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px, tab + kExpTable);
-            angular_basis(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py, tab + kExpTable);
+        } else {  // factored basis: the caller applies direct_unscale to the gradient sums
+            angular_basis_direct(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px, tab + kExpTable);
+            angular_basis_direct(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py, tab + kExpTable);
         }
-        event_4d<W, GRAD>(c, in.m.x, hx, in.l.x, t2lx, in.k.x, t2kx, xpx, t2px, wx, true, acc, lpx, bad, tab);
-        event_4d<W, GRAD>(c, in.m.y, hy, in.l.y, t2ly, in.k.y, t2ky, xpy, t2py, wy, second, acc, lpy, bad, tab);
+        constexpr bool DIR = VAR != kVarPrecompute;
+        event_4d<W, GRAD, DIR>(c, in.m.x, hx, in.l.x, t2lx, in.k.x, t2kx, xpx, t2px, wx, true, acc, lpx, bad, tab);
+        event_4d<W, GRAD, DIR>(c, in.m.y, hy, in.l.y, t2ly, in.k.y, t2ky, xpy, t2py, wy, second, acc, lpy, bad, tab);
     }
 }
 

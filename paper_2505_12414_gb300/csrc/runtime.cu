@@ -267,6 +267,8 @@ int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hois
     k.b2 = b2;
     if (kind == kKstar4D) {
         for (int j = 0; j < 8; ++j) k.ang[j] = th[2 + j];
+        k.k0d = (lnb1 + kLnBasisC - alpha * (mu - ma)) * S;
+        for (int j = 0; j < 8; ++j) k.angd[j] = th[2 + j] * direct_factor(j + 1);
         k.cq[0] = b2;
         k.cq[1] = b2 * th[11];
         k.cq[2] = b2 * th[12];
