@@ -31,8 +31,9 @@
 //  * Warp reductions halve the slot count per shuffle level (31 FP64 adds per warp for
 //    up to 32 slots) instead of a shuffle tree per slot.
 //  * The grid is a small multiple of the SM count; block partial sums are written to a
-//    scratch buffer and the last block to finish (atomic ticket) reduces them in a fixed
-//    order, so results are bitwise reproducible for a given launch shape.
+//    scratch buffer and final_reduce_kernel, launched behind the fused kernel as a
+//    programmatic dependent, adds them in a fixed order (one block per slot), so results
+//    are bitwise reproducible for a given launch shape.
 
 #include <cuda_runtime.h>
 #include <math.h>
