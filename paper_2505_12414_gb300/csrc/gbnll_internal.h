@@ -169,6 +169,7 @@ struct HArgs {
     HConst c;
     int nslots;
     int lnp_slot;          // unweighted: slot that receives the block's sum of ln P (else -1)
+    int tail_begin, tail_count;  // slots summed while staging (HessLayout)
     double* partials;      // [kHessMaxSlots][blocks], reduced by a second launch
     double* out;           // [nslots]
     unsigned int* done;    // or NULL: completion words [nslots], set to seq once out[s] is written
@@ -176,8 +177,13 @@ struct HArgs {
     uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];  // column pair of each slot
 };
 
+// The Hessian table's few slots past its last full warp row (tail_count <= kHessTailMax, the
+// same with or without the W slots after them) are summed by the thread that stages each
+// event instead of costing a whole warp row of FMAs per event.
+constexpr int kHessTailMax = 4;
 struct HessLayout {
     int nslots = 0, ncols = 0, lnp_slot = -1;
+    int tail_begin = 0, tail_count = 0;
     uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];
 };
 // Slot table for (kind, weighted, with W); returns false if it does not fit.

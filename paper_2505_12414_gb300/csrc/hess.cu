@@ -59,15 +59,29 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
     extern __shared__ double z[];
     __shared__ double s_tab[kTabDoubles];
     __shared__ double s_lnp[kHessThreads / 32];
+    __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_htab[j];
     __syncthreads();
     const int ns = a.nslots;
+    // Tail slots [tb, tb + tn) are summed by the staging thread of each event; when they end
+    // the table the warp rows stop before them (195 slots: 6 rows instead of 7).
+    const int tb = a.tail_begin, tn = a.tail_count;
+    const int ns_rows = (tn > 0 && tb + tn == ns) ? tb : ns;
     // slots t, t + 128, t + 256 of this thread; the warp runs as many slot rows as its first
     // lane owns (slots past the end, in the last partial row only, go to unused accumulators)
     const int w0 = t & ~31;
-    const int nrow = ns > w0 ? min(3, (ns - w0 + kHessThreads - 1) / kHessThreads) : 0;
+    const int nrow = ns_rows > w0 ? min(3, (ns_rows - w0 + kHessThreads - 1) / kHessThreads) : 0;
+    int tci[kHessTailMax], tcj[kHessTailMax];
+    double tacc[kHessTailMax];
+#pragma unroll
+    for (int r = 0; r < kHessTailMax; ++r) {
+        const int sr = r < tn ? tb + r : 0;
+        tci[r] = a.si[sr] * kHessThreads + t;
+        tcj[r] = a.sj[sr] * kHessThreads + t;
+        tacc[r] = 0.0;
+    }
     int ci[3], cj[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -81,6 +95,9 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
     const int64_t ntiles = (a.ev.n + kHessThreads - 1) / kHessThreads;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         stage_event<KIND, VAR, W>(a.ev, a.c, tile * kHessThreads + t, z, t, s_tab, lp);
+#pragma unroll
+        for (int r = 0; r < kHessTailMax; ++r)  // this thread's own event, just staged
+            if (r < tn) tacc[r] = fma(z[tci[r]], z[tcj[r]], tacc[r]);
         __syncthreads();
         if (nrow == 1)
             tile_slots<1>(z, ci, cj, acc, lane);
@@ -110,10 +127,24 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
         }
     }
     const int nb = gridDim.x;
+    if (tn > 0) {  // tail slots: fixed tree over the block
+#pragma unroll
+        for (int r = 0; r < kHessTailMax; ++r) {
+            double v = tacc[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_tail[r][warp] = v;
+        }
+        __syncthreads();
+        if (t < tn) {
+            const double tot = (s_tail[t][0] + s_tail[t][1]) + (s_tail[t][2] + s_tail[t][3]);
+            a.partials[(size_t)(tb + t) * nb + blockIdx.x] = tot;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int s = t + k * kHessThreads;
-        if (s < ns) a.partials[(size_t)s * nb + blockIdx.x] = acc[k];
+        if (s < ns && !(s >= tb && s < tb + tn)) a.partials[(size_t)s * nb + blockIdx.x] = acc[k];
     }
 }
 
@@ -236,6 +267,18 @@ bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
         for (int s = 0; s < L->nslots; ++s)
             if (L->si[s] == wl && L->sj[s] == one) L->lnp_slot = s;
         if (L->lnp_slot < 0) return false;
+    }
+    // the H table's slots past its last full warp row (W slots are recorded after H's)
+    int nh = L->nslots;
+    if (want_w2) {
+        HessLayout Lh;
+        if (!hess_layout(kind, weighted, false, &Lh)) return false;
+        nh = Lh.nslots;
+    }
+    const int r = nh % 32;
+    if (r > 0 && r <= kHessTailMax && !(L->lnp_slot >= nh - r && L->lnp_slot < nh)) {
+        L->tail_begin = nh - r;
+        L->tail_count = r;
     }
     return !rec.overflow;
 }

@@ -517,6 +517,8 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         hess_fill_const(m->kind, H, theta, &a.c);
         a.nslots = L.nslots;
         a.lnp_slot = L.lnp_slot;
+        a.tail_begin = L.tail_begin;
+        a.tail_count = L.tail_count;
         a.partials = m->d_hpart;
         a.out = m->d_hout;
         a.done = m->d_hdone;
