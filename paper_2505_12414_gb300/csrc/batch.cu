@@ -739,6 +739,7 @@ enum HessMode : int { kHmEval = 0, kHmStart = 1, kHmCov = 2, kHmSandwich = 3 };
 
 struct HessDev {
     int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
+    int tail_begin, tail_count;  // slots summed while staging (HessLayout)
     int pass;                   // covariance modes: polish pass (0: the loop's final point)
     int* n_polish;              // covariance modes: toys still polishing after this pass (mapped)
     const int* sel;             // per toy: take part in this pass (NULL: every toy)
@@ -847,12 +848,23 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
     __shared__ double s_tab[kTabDoubles];
     __shared__ HConst s_c;
     __shared__ double s_lnp[kHessThreads / 32];
+    __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_btab[j];
     const int ns = h.nslots;
+    // tail slots [tb, tb + tn): summed by each event's staging thread (as in hess_kernel)
+    const int tb = h.tail_begin, tn = h.tail_count;
+    const int ns_rows = (tn > 0 && tb + tn == ns) ? tb : ns;
     const int w0 = t & ~31;
-    const int nrow = ns > w0 ? min(3, (ns - w0 + kHessThreads - 1) / kHessThreads) : 0;
+    const int nrow = ns_rows > w0 ? min(3, (ns_rows - w0 + kHessThreads - 1) / kHessThreads) : 0;
+    int tci[kHessTailMax], tcj[kHessTailMax];
+#pragma unroll
+    for (int r = 0; r < kHessTailMax; ++r) {
+        const int sr = r < tn ? tb + r : 0;
+        tci[r] = h.si[sr] * kHessThreads + t;
+        tcj[r] = h.sj[sr] * kHessThreads + t;
+    }
     int ci[3], cj[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -871,10 +883,14 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
         ev.n = min(e0 + (int64_t)kHessUnitEvents, h.ev_end[toy]);
         __syncthreads();
         double acc[3] = {0.0, 0.0, 0.0};
+        double tacc[kHessTailMax] = {0.0, 0.0, 0.0, 0.0};
         LogProd lp{1.0, 0};
         if (ok) {
             for (int64_t e = e0; e < ev.n; e += kHessThreads) {
                 stage_event<KIND, VAR, W>(ev, s_c, e + t, z, t, s_tab, lp);
+#pragma unroll
+                for (int r = 0; r < kHessTailMax; ++r)  // this thread's own event, just staged
+                    if (r < tn) tacc[r] = fma(z[tci[r]], z[tcj[r]], tacc[r]);
                 __syncthreads();
                 if (nrow == 1)
                     tile_slots<1>(z, ci, cj, acc, lane);
@@ -903,10 +919,22 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
                 }
             }
         }
+        if (tn > 0) {  // tail slots: fixed tree over the block
+#pragma unroll
+            for (int r = 0; r < kHessTailMax; ++r) {
+                double v = tacc[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) s_tail[r][warp] = v;
+            }
+            __syncthreads();
+            if (t < tn)
+                h.unit_sums[(size_t)u * ns + tb + t] = (s_tail[t][0] + s_tail[t][1]) + (s_tail[t][2] + s_tail[t][3]);
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int sl = t + k * kHessThreads;
-            if (sl < ns) h.unit_sums[(size_t)u * ns + sl] = acc[k];
+            if (sl < ns && !(sl >= tb && sl < tb + tn)) h.unit_sums[(size_t)u * ns + sl] = acc[k];
         }
     }
 }
@@ -1447,6 +1475,8 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
     h.n_units = w.n_units;
     h.nslots = L.nslots;
     h.lnp_slot = L.lnp_slot;
+    h.tail_begin = L.tail_begin;
+    h.tail_count = L.tail_count;
     h.ncols = L.ncols;
     h.ev_begin = T.d_begin;
     h.ev_end = T.d_end;
