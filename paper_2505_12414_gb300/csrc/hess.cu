@@ -31,7 +31,9 @@
 //   * the grid is persistent (blocks take tiles b, b + B, ...); per-block slot sums go to
 //     scratch and a second launch reduces them, one block per slot, in a fixed order
 //     (deterministic, and spread over all SMs instead of one last block);
-//   * a warp runs only as many slot rows as its lanes own (195 slots: 7 warp rows, not 8);
+//   * a warp runs only as many slot rows as its lanes own, and the few slots past the last
+//     full warp row of the H table are summed by each event's staging thread (4D, 195 slots:
+//     6 warp rows of FMAs per event instead of 7);
 //   * unweighted, sum ln P is the logarithm of a running product per thread (one log per
 //     thread, as in the fused kernel), added to its slot after the tiles;
 //   * the staging uses the library's table-driven exponential and its reciprocal
