@@ -74,3 +74,26 @@ def test_hessian_slot_counts_without_a_gpu(lib):
             assert npar * (npar + 1) // 2 <= h < hw <= 384
             if weighted:
                 assert hw - h == npar * (npar + 1) // 2
+
+
+def test_fit_result_record_layout_matches_the_header():
+    """The binding reads batched fit results as numpy records of the C struct fit_result
+    (include/gbnll.h): same size, same field offsets."""
+    import numpy as np
+
+    import paper_2505_12414_gb300 as g
+
+    dt = g._FIT_RESULT_DTYPE
+    assert dt.itemsize == ctypes.sizeof(g.fit_result)
+    for name, _ in g.fit_result._fields_:
+        assert dt.fields[name][1] == getattr(g.fit_result, name).offset
+    rec = np.zeros(2, dtype=dt)
+    rec["theta"][1, :3] = [1.0, 2.0, 3.0]
+    rec["cov"][1, :9] = np.arange(9.0)
+    rec["status"][1] = 5
+    view = (g.fit_result * 2).from_buffer(rec)
+    assert view[1].theta[2] == 3.0 and view[1].cov[4] == 4.0 and view[1].status == 5
+    out = g._results_of(rec, 3, steps=4)
+    assert out["theta"][1].tolist() == [1.0, 2.0, 3.0]
+    assert out["cov"][1].tolist() == [[0.0, 1.0, 2.0], [3.0, 4.0, 5.0], [6.0, 7.0, 8.0]]
+    assert out["status"].tolist() == [0, 5] and out["steps"] == 4
