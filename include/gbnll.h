@@ -209,8 +209,11 @@ void nll_destroy(nll_model* m);
  *   nll_autotune    times the candidate launch shapes (and both 4D variants when the basis is
  *                   loaded) on the loaded sample and keeps the fastest; blocks the host.
  *   nll_set_profiling / nll_last_kernel_ms   when profiling is on, each evaluation records
- *                   CUDA events on the model's stream around its fused kernel; the last
- *                   kernel duration in milliseconds is returned.
+ *                   CUDA events on the model's stream around its launches (the fused
+ *                   kernel and the final-sum kernel behind it; for nll_eval_hess the
+ *                   Hessian kernel and its slot totals); nll_last_kernel_ms waits for the
+ *                   last one and returns its duration in milliseconds (NLL_ERR_STATE if no
+ *                   evaluation was timed since profiling was switched on).
  *   nll_get_launch  reports blocks per SM, threads per block, variant and the SM count.
  */
 int nll_set_launch(nll_model* m, int blocks_per_sm, int threads_per_block, int variant);
