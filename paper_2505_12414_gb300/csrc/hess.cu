@@ -187,7 +187,7 @@ namespace {
 struct Recorder {
     HessLayout* L;
     bool overflow = false;
-    double operator()(int i, int j)
+    __host__ __device__ double operator()(int i, int j)  // host only in use; both for assemble_t
     {
         for (int s = 0; s < L->nslots; ++s)
             if (L->si[s] == i && L->sj[s] == j) return 0.0;
@@ -206,7 +206,7 @@ struct Reader {
     const HessLayout* L;
     const double* sums;
     bool missing = false;
-    double operator()(int i, int j)
+    __host__ __device__ double operator()(int i, int j)
     {
         for (int s = 0; s < L->nslots; ++s)
             if (L->si[s] == i && L->sj[s] == j) return sums[s];
