@@ -97,3 +97,19 @@ def test_fit_result_record_layout_matches_the_header():
     assert out["theta"][1].tolist() == [1.0, 2.0, 3.0]
     assert out["cov"][1].tolist() == [[0.0, 1.0, 2.0], [3.0, 4.0, 5.0], [6.0, 7.0, 8.0]]
     assert out["status"].tolist() == [0, 5] and out["steps"] == 4
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No CPU fallback: loading a library path that does not exist raises, in a fresh
+    interpreter so the already-loaded library of this process is not reused."""
+    import subprocess
+    import sys
+
+    code = ("import paper_2505_12414_gb300 as g\n"
+            "try:\n"
+            "    g.load(%r)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'not built' in str(e))\n" % str(tmp_path / "libgbnll.so"))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "raised True"
