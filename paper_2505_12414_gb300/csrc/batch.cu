@@ -342,7 +342,7 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
 {
     constexpr int K = KIND == kMass1D ? kAcc1D : kAcc4D;
-    __shared__ double s_tab[kTabDoubles];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
     __shared__ double s_red[(kEvalThreads / 32) * K];
     __shared__ int s_u;
     constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
@@ -845,7 +845,7 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h)
 {
     extern __shared__ double z[];
-    __shared__ double s_tab[kTabDoubles];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
     __shared__ HConst s_c;
     __shared__ double s_lnp[kHessThreads / 32];
     __shared__ double s_tail[kHessTailMax][kHessThreads / 32];

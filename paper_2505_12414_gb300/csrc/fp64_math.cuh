@@ -13,8 +13,8 @@ constexpr int kExpTable = 1 << kExpTableBits;
 // Scale of the exponential's argument: fexp_scaled(x * kExpArgScale) = exp(x).
 constexpr double kExpArgScale = 0x1.71547652b82fep+10;  // N/ln2, N = 1024
 
-// sin/cos table: (cos, sin) of k pi/128 for k = 0..255 (a full period), after the exp table.
-constexpr int kTrigSteps = 256;
+// sin/cos table: (cos, sin) of k pi/512 for k = 0..1023 (a full period), after the exp table.
+constexpr int kTrigSteps = 1024;
 constexpr int kTabDoubles = kExpTable + 2 * kTrigSteps;  // one table per translation unit
 
 // Host: the values of the device table, rounded from long double; the exact zeros of sin and
@@ -24,9 +24,9 @@ inline void fill_device_tables(double* t)
     const long double pi = 3.141592653589793238462643383279502884L;
     for (int j = 0; j < kExpTable; ++j) t[j] = (double)exp2l((long double)j / (long double)kExpTable);
     for (int k = 0; k < kTrigSteps; ++k) {
-        const long double a = pi * (long double)k / 128.0L;
-        t[kExpTable + 2 * k] = (k % 128 == 64) ? 0.0 : (double)cosl(a);
-        t[kExpTable + 2 * k + 1] = (k % 128 == 0) ? 0.0 : (double)sinl(a);
+        const long double a = pi * (long double)k / 512.0L;
+        t[kExpTable + 2 * k] = (k % 512 == 256) ? 0.0 : (double)cosl(a);
+        t[kExpTable + 2 * k + 1] = (k % 512 == 0) ? 0.0 : (double)sinl(a);
     }
 }
 
@@ -64,30 +64,27 @@ __device__ __forceinline__ double fexp_scaled(double xs, const double* __restric
 
 // sin x and cos x for |x| <= pi (any x is safe; accuracy degrades slowly beyond), from the
 // classical table method with Cody-Waite reduction (W. J. Cody and W. Waite, Software Manual
-// for the Elementary Functions, 1980): x = k pi/128 + r with k = rint(128 x/pi) and
-// |r| <= pi/256, the reduction x - k (P1 + P2) done with two FMAs (P1 + P2 = pi/128 to ~106
+// for the Elementary Functions, 1980): x = k pi/512 + r with k = rint(512 x/pi) and
+// |r| <= pi/1024, the reduction x - k (P1 + P2) done with two FMAs (P1 + P2 = pi/512 to ~106
 // bits, so r carries at most one rounding); sin r and cos r - 1 from their Taylor series
-// through r^7 and r^6 (next terms below 2e-20 relative); then
+// through r^5 and r^4 (the next terms are below 2e-19 and 2e-18 relative at |r| = pi/1024);
+// then
 //   sin x = S + (S (cos r - 1) + C sin r),  cos x = C + (C (cos r - 1) - S sin r)
-// with (C, S) = (cos, sin)(k pi/128) from the table.  17 FP64 instructions, no branch.
+// with (C, S) = (cos, sin)(k pi/512) from the table.  15 FP64 instructions, no branch.
 __device__ __forceinline__ void fsincos_pi(double x, const double* __restrict__ trig, double& s, double& c)
 {
     const double kMagic = 0x1.8p52;
-    const double kScale = 0x1.45f306dc9c883p+5;  // 128/pi
-    const double P1 = 0x1.921fb54442d18p-6;      // pi/128, leading 53 bits
-    const double P2 = 0x1.1a62633145c07p-60;     // pi/128 - P1
+    const double kScale = 0x1.45f306dc9c883p+7;  // 512/pi
+    const double P1 = 0x1.921fb54442d18p-8;      // pi/512, leading 53 bits
+    const double P2 = 0x1.1a62633145c07p-62;     // pi/512 - P1
     double kd = fma(x, kScale, kMagic);
     int k = __double2loint(kd);
     double kf = kd - kMagic;
     double r = fma(-kf, P1, x);
     r = fma(-kf, P2, r);
     double r2 = r * r;
-    double ps = fma(r2, -1.0 / 5040.0, 1.0 / 120.0);
-    ps = fma(r2, ps, -1.0 / 6.0);
-    double sr = fma(r * r2, ps, r);
-    double pc = fma(r2, -1.0 / 720.0, 1.0 / 24.0);
-    pc = fma(r2, pc, -0.5);
-    double cm = r2 * pc;  // cos r - 1
+    double sr = fma(r * r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), r);
+    double cm = r2 * fma(r2, 1.0 / 24.0, -0.5);  // cos r - 1
     const double2 cs = reinterpret_cast<const double2*>(trig)[k & (kTrigSteps - 1)];
     s = fma(cs.y, cm, fma(cs.x, sr, cs.y));
     c = fma(cs.x, cm, fma(-cs.y, sr, cs.x));

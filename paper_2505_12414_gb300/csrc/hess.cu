@@ -59,7 +59,7 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 {
     extern __shared__ double z[];
-    __shared__ double s_tab[kTabDoubles];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
     __shared__ double s_lnp[kHessThreads / 32];
     __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 {
     constexpr int KB = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
     constexpr int K = KB + (IP ? kAccInPlace : 0);
-    __shared__ double s_tab[kTabDoubles];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
     __shared__ double s_red[8 * K];
 
     const int64_t n = a.n;
