@@ -86,7 +86,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the mass-model event-count sweep")
     ap.add_argument("--no-calibration", action="store_true", help="skip the FP64 calibration kernels")
     ap.add_argument("--no-hessian", action="store_true", help="skip the analytic-Hessian measurement")
-    ap.add_argument("--no-capacity", action="store_true", help="skip the 2e8-event resident-sample measurement")
+    ap.add_argument("--no-capacity", action="store_true",
+                    help="skip the 2e8-event resident-sample and the 1e7 weighted-sample measurements")
     ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0],
                     help="Poisson arrival rates of served fits per second (one measurement each)")
     return ap.parse_args()
@@ -448,6 +449,37 @@ def capacity(g, device, stream, n_events=200_000_000, reps=5):
     return out
 
 
+def scale_weighted(g, device, stream, n_events=10_000_000, reps=10):
+    """The scale configuration: 10^7 weighted 4D events (w ~ U(0.5, 1.5)), generated on the
+    device at the truth, loaded with the precomputed basis (18 FP64 columns, 144 B/event,
+    1.44 GB: far larger than L2, no flush needed); NLL+gradient per evaluation."""
+    import torch
+
+    cols = g.nll_generate(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, synth.TRUTH_4D, n_events,
+                          seed=synth.BASE_SEED, stream=98, device=device)
+    gen = torch.Generator(device="cuda:%d" % device)
+    gen.manual_seed(synth.BASE_SEED + 98)
+    w = 0.5 + torch.rand(n_events, dtype=torch.float64, device="cuda:%d" % device, generator=gen)
+    m = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device, stream=stream.cuda_stream)
+    m.load(cols, w, precompute=True)
+    del cols, w
+    torch.cuda.empty_cache()
+    th = thetas(reps + 2)
+    m.eval_grad(th[0])
+    g.nll_autotune(m.handle)
+    launch = g.nll_get_launch(m.handle)
+    g.nll_set_profiling(m.handle, True)
+    kms = []
+    for i in range(reps):
+        m.eval_grad(th[1 + i])
+        kms.append(g.nll_last_kernel_ms(m.handle))
+    k = statistics.median(kms)
+    m.close()
+    return {"n_events": n_events, "weighted": True, "hbm_bytes_resident": 144 * n_events,
+            "blocks_per_sm": launch["blocks_per_sm"], "threads": launch["threads"],
+            "kernel_ms": k, "events_per_s": n_events / (k * 1e-3)}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -589,6 +621,7 @@ def run_ours(args):
 
     hess = None if args.no_hessian else hessian_bench(g, model, th[0], flush, stream)
     cap = None if args.no_capacity else capacity(g, local, stream)
+    scale = None if args.no_capacity else scale_weighted(g, local, stream)
 
     toys = None
     if args.toys > 0:
@@ -623,7 +656,7 @@ def run_ours(args):
                                       "ms_per_step": e2e_copy_step,
                                       "mode": "load() copies the pinned columns, then eval_grad, direct variant"}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 2 * args.steps,
-                "hessian": hess, "capacity_4d": cap, "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
+                "hessian": hess, "capacity_4d": cap, "scale_4d_weighted_1e7": scale, "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
                 "mass_model_sweep": sweep}
         print(json.dumps(line), flush=True)
     model.close()

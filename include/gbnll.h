@@ -250,8 +250,9 @@ int nll_calibrate_fp64(int device, double* rates);
  * kernels, after Tang's method, which takes its argument pre-scaled: y = exp(x ln2/1024);
  * fn 1: the reciprocal, hardware approximation plus one cubic correction; fn 2 / fn 3:
  * sin x / cos x by the table method with Cody-Waite reduction, accurate for |x| <= pi, as
- * the 4D kernels use it for phi).  For accuracy tests against the host's libm; allocates
- * temporary device buffers.
+ * the 4D kernels use it for phi; fn 4: ln x after Tang's table-driven method, for positive
+ * normal x, as the weighted kernels use it).  For accuracy tests against the host's libm;
+ * allocates temporary device buffers.
  */
 int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
 

@@ -342,10 +342,10 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
 {
     constexpr int K = KIND == kMass1D ? kAcc1D : kAcc4D;
-    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
     __shared__ double s_red[(kEvalThreads / 32) * K];
     __shared__ int s_u;
-    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     for (int j = threadIdx.x; j < ntab; j += blockDim.x) s_tab[j] = g_btab[j];
     __syncthreads();
     const int nunits = min(b.counters[1], b.max_units);
@@ -845,12 +845,12 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h)
 {
     extern __shared__ double z[];
-    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
     __shared__ HConst s_c;
     __shared__ double s_lnp[kHessThreads / 32];
     __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_btab[j];
     const int ns = h.nslots;
     // tail slots [tb, tb + tn): summed by each event's staging thread (as in hess_kernel)

@@ -13,9 +13,21 @@ constexpr int kExpTable = 1 << kExpTableBits;
 // Scale of the exponential's argument: fexp_scaled(x * kExpArgScale) = exp(x).
 constexpr double kExpArgScale = 0x1.71547652b82fep+10;  // N/ln2, N = 1024
 
-// sin/cos table: (cos, sin) of k pi/512 for k = 0..1023 (a full period), after the exp table.
+// log table after the exp table: for F_j = 1 + j/128, j = 0..128, ln F_j split into a head
+// (a multiple of 2^-42) and a tail, and 1/F_j; padded to an even count.
+constexpr int kLogSteps = 128;
+constexpr int kLogTab = 3 * (kLogSteps + 1) + 1;
+constexpr int kLogOffset = kExpTable;
+// sin/cos table: (cos, sin) of k pi/512 for k = 0..1023 (a full period), after the log table.
 constexpr int kTrigSteps = 1024;
-constexpr int kTabDoubles = kExpTable + 2 * kTrigSteps;  // one table per translation unit
+constexpr int kTrigOffset = kExpTable + kLogTab;  // even: the (cos, sin) pairs are read as double2
+constexpr int kTabDoubles = kTrigOffset + 2 * kTrigSteps;  // one table per translation unit
+static_assert(kTrigOffset % 2 == 0, "16-byte aligned (cos, sin) pairs");
+
+// ln 2 split for the logarithm: head with 42 significant bits (e ln2_head is exact for any
+// binary exponent e of a double) and the rest.
+constexpr double kLn2Head = 0x1.62e42fefa3800p-1;
+constexpr double kLn2Tail = 0x1.ef35793c76730p-45;
 
 // Host: the values of the device table, rounded from long double; the exact zeros of sin and
 // cos at multiples of pi/2 are set exactly (long double pi is not pi).
@@ -23,10 +35,19 @@ inline void fill_device_tables(double* t)
 {
     const long double pi = 3.141592653589793238462643383279502884L;
     for (int j = 0; j < kExpTable; ++j) t[j] = (double)exp2l((long double)j / (long double)kExpTable);
+    for (int j = 0; j <= kLogSteps; ++j) {
+        const long double F = 1.0L + (long double)j / (long double)kLogSteps;
+        const long double l = logl(F);
+        const double head = (double)(nearbyintl(ldexpl(l, 42)) / 4398046511104.0L);  // multiple of 2^-42
+        t[kLogOffset + j] = head;
+        t[kLogOffset + (kLogSteps + 1) + j] = (double)(l - (long double)head);
+        t[kLogOffset + 2 * (kLogSteps + 1) + j] = (double)(1.0L / F);
+    }
+    t[kLogOffset + kLogTab - 1] = 0.0;
     for (int k = 0; k < kTrigSteps; ++k) {
         const long double a = pi * (long double)k / 512.0L;
-        t[kExpTable + 2 * k] = (k % 512 == 256) ? 0.0 : (double)cosl(a);
-        t[kExpTable + 2 * k + 1] = (k % 512 == 0) ? 0.0 : (double)sinl(a);
+        t[kTrigOffset + 2 * k] = (k % 512 == 256) ? 0.0 : (double)cosl(a);
+        t[kTrigOffset + 2 * k + 1] = (k % 512 == 0) ? 0.0 : (double)sinl(a);
     }
 }
 
@@ -60,6 +81,36 @@ __device__ __forceinline__ double fexp_scaled(double xs, const double* __restric
     int xhi = __double2hiint(xs);
     if ((xhi & 0x7fffffff) >= 0x412fbd00) y = (xhi < 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
     return y;
+}
+
+// ln x for a positive normal double x, after Tang's table-driven method (P. T. P. Tang,
+// ACM TOMS 16 (1990) 378): x = 2^e m, m in [1, 2), F = 1 + j/128 the table point nearest m
+// (j from the top mantissa bits with integer instructions), f = m - F (exact, |f| <= 1/256),
+// u = f / F = f (1/F) with |u| <= 2^-8, and
+//   ln x = (e ln2_head + ln F_head) + (e ln2_tail + ln F_tail + ln(1 + u)),
+// the first sum exact (both heads are multiples of 2^-42), ln(1 + u) from its Taylor series
+// through u^7 (the next term is below 2e-18 relative).  14 FP64 instructions.  The caller
+// guarantees x positive and normal (the kernels check that before taking the logarithm).
+__device__ __forceinline__ double flog(double x, const double* __restrict__ tab)
+{
+    const int hi = __double2hiint(x);
+    const int mh = hi & 0x000fffff;
+    const int j = (mh + (1 << 12)) >> 13;                      // nearest of 128 steps (0..128)
+    const double m = __hiloint2double(mh | 0x3ff00000, __double2loint(x));
+    const double F = __hiloint2double(0x3ff00000 + (j << 13), 0);
+    const double ed = (double)((hi >> 20) - 1023);
+    const double* lt = tab + kLogOffset;
+    const double u = (m - F) * lt[2 * (kLogSteps + 1) + j];
+    const double q = u * u;
+    double t = fma(u, 1.0 / 7.0, -1.0 / 6.0);
+    t = fma(u, t, 1.0 / 5.0);
+    t = fma(u, t, -1.0 / 4.0);
+    t = fma(u, t, 1.0 / 3.0);
+    t = fma(u, t, -1.0 / 2.0);
+    const double p = fma(q, t, u);
+    const double head = fma(ed, kLn2Head, lt[j]);
+    const double tail = fma(ed, kLn2Tail, lt[(kLogSteps + 1) + j]);
+    return head + (tail + p);
 }
 
 // sin x and cos x for |x| <= pi (any x is safe; accuracy degrades slowly beyond), from the

@@ -59,11 +59,11 @@ template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 {
     extern __shared__ double z[];
-    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
     __shared__ double s_lnp[kHessThreads / 32];
     __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_htab[j];
     __syncthreads();
     const int ns = a.nslots;

@@ -86,7 +86,7 @@ __device__ __forceinline__ void stage_event(const HEv& a, const HConst& c, int64
         } else {
             xl = __ldg(a.col[kColCtl] + ei);
             xk = __ldg(a.col[kColCtk] + ei);
-            angular_basis(xl, xk, __ldg(a.col[kColPhi] + ei), h, t2l, t2k, xp, t2p, tab + kExpTable);
+            angular_basis(xl, xk, __ldg(a.col[kColPhi] + ei), h, t2l, t2k, xp, t2p, tab + kTrigOffset);
         }
         double A = fma(c.ang[0], h[1], h[0]);
 #pragma unroll
@@ -145,7 +145,7 @@ __device__ __forceinline__ void stage_event(const HEv& a, const HConst& c, int64
     put(L::ONE, 1.0);
     const bool ok = in && !not_positive_normal(P);
     if (W)
-        put(L::WLNP, ok ? w * log(P) : 0.0);
+        put(L::WLNP, ok ? w * flog(P, tab) : 0.0);
     else  // one logarithm per thread at the end (running product, exponent split off)
         logprod_mul(lp, ok ? P : 1.0);
     if (ok) {

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 {
     constexpr int KB = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
     constexpr int K = KB + (IP ? kAccInPlace : 0);
-    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable];
+    __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
     __shared__ double s_red[8 * K];
 
     const int64_t n = a.n;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
     // The table's loads are issued first and the first pair's behind them, so the block's
     // first barrier does not wait for the pair data; the sin/cos part of the table is
     // staged only where the angular basis is computed here.
-    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : kExpTable;
+    constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     constexpr int nper = ntab / 64;  // per thread at the smallest block (64 threads)
     double tv[nper];
 #pragma unroll
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) basis_kernel(const BArgs a)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         double h[9], t2l, t2k, xp, t2p;
-        angular_basis(a.ctl[i], a.ctk[i], a.phi[i], h, t2l, t2k, xp, t2p, g_exp2tab + kExpTable);
+        angular_basis(a.ctl[i], a.ctk[i], a.phi[i], h, t2l, t2k, xp, t2p, g_exp2tab + kTrigOffset);
 #pragma unroll
         for (int j = 0; j < 9; ++j) a.out[j][i] = h[j];
         a.out[9][i] = t2l;

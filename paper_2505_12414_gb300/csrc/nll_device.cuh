@@ -108,7 +108,7 @@ __device__ __forceinline__ void event_mass(const KConst& c, double m, double w, 
     bad |= valid ? not_positive_normal(P) : 0;
     P = valid ? P : 1.0;
     if (W)
-        acc[0] = fma(valid ? w : 0.0, log(P), acc[0]);
+        acc[0] = fma(valid ? w : 0.0, flog(P, tab), acc[0]);
     else
         logprod_mul(lp, P);
     if (GRAD) {
@@ -144,7 +144,7 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
     bad |= valid ? not_positive_normal(P) : 0;
     P = valid ? P : 1.0;
     if (W)
-        acc[0] = fma(valid ? w : 0.0, log(P), acc[0]);
+        acc[0] = fma(valid ? w : 0.0, flog(P, tab), acc[0]);
     else
         logprod_mul(lp, P);
     if (GRAD) {
@@ -368,8 +368,8 @@ __device__ __forceinline__ void process_pair(const KConst& c, const PairIn& in, 
             t2px = in.t2p.x;
             t2py = in.t2p.y;
         } else {  // factored basis: the caller applies direct_unscale to the gradient sums
-            angular_basis_direct(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px, tab + kExpTable);
-            angular_basis_direct(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py, tab + kExpTable);
+            angular_basis_direct(in.l.x, in.k.x, in.f.x, hx, t2lx, t2kx, xpx, t2px, tab + kTrigOffset);
+            angular_basis_direct(in.l.y, in.k.y, in.f.y, hy, t2ly, t2ky, xpy, t2py, tab + kTrigOffset);
         }
         constexpr bool DIR = VAR != kVarPrecompute;
         event_4d<W, GRAD, DIR>(c, in.m.x, hx, in.l.x, t2lx, in.k.x, t2kx, xpx, t2px, wx, true, acc, lpx, bad, tab);

@@ -47,11 +47,11 @@ def test_reciprocal_accuracy(gpu_lib):
 def test_table_sincos_accuracy(gpu_lib):
     # the 4D kernels take sin/cos phi from the table method for |phi| <= pi
     rs = synth.Stream(23, 0)
-    steps = np.arange(-128, 129) * (np.pi / 128)
+    steps = np.arange(-512, 513) * (np.pi / 512)
     x = np.concatenate([
         (2 * rs.uniform(300000) - 1) * np.pi,
         steps, np.nextafter(steps, 10.0), np.nextafter(steps, -10.0),   # around the table points
-        steps + np.pi / 256, steps - np.pi / 256,                       # the reduction's edges
+        steps + np.pi / 1024, steps - np.pi / 1024,                     # the reduction's edges
         np.array([0.0, -0.0, 1e-300, -1e-300, 1e-8, np.pi, -np.pi, np.pi / 2, -np.pi / 2]),
     ])
     x = x[np.abs(x) <= np.pi]
@@ -60,3 +60,24 @@ def test_table_sincos_accuracy(gpu_lib):
         y = gpu_lib.nll_diag_math(fn, x)
         err = np.abs(y.astype(np.longdouble) - ref) / np.spacing(np.abs(ref).astype(np.float64)).astype(np.longdouble)
         assert float(err.max()) <= 2.0, (fn, float(err.max()), x[np.argmax(err)])
+
+
+def test_table_log_accuracy(gpu_lib):
+    # the weighted kernels take ln P from the table-driven logarithm (positive normal P)
+    rs = synth.Stream(29, 0)
+    F = 1.0 + np.arange(129) / 128.0
+    x = np.concatenate([
+        10.0 ** (600.0 * rs.uniform(200000) - 300.0),                  # the whole normal range
+        1.0 + (2.0 * rs.uniform(100000) - 1.0) * 1e-3,                 # around 1
+        F, np.nextafter(F, 3.0), np.nextafter(F, 0.0),                  # the table points
+        1.0 + (np.arange(128) + 0.5) / 128.0,                           # the rounding edges of j
+        np.ldexp(F, (rs.uniform(129) * 200 - 100).astype(int)),
+        np.array([0.5, 1.0, 2.0, np.nextafter(2.0, 0.0), np.nextafter(1.0, 0.0), np.nextafter(1.0, 2.0),
+                  np.finfo(np.float64).tiny, np.finfo(np.float64).max]),
+    ])
+    ref = np.log(x.astype(np.longdouble))
+    y = gpu_lib.nll_diag_math(4, x)
+    ok = ref != 0
+    assert np.all(y[~ok] == 0.0)
+    err = np.abs(y[ok].astype(np.longdouble) - ref[ok]) / np.spacing(np.abs(ref[ok]).astype(np.float64)).astype(np.longdouble)
+    assert float(err.max()) <= 1.0, (float(err.max()), x[ok][np.argmax(err)])
