@@ -111,6 +111,10 @@ int nll_load_events(nll_model* m, const double* const* columns, const double* we
  *                sigma > 0, 0 <= fsig <= 1, all finite; 4D: 2 - (2/3) c2_j > 0.
  *   nll_out      host double.
  * Returns NLL_ERR_NONPOSITIVE_PDF with *nll_out = +inf if some P_i <= 0 or is not finite.
+ * Synchronous: returns once the results are on the host (the last launch writes them to
+ * mapped host memory and sets completion words the call polls, so it may return a few
+ * microseconds before the stream reports the launch complete; later work on the model's
+ * stream is ordered after it as usual).
  */
 int nll_eval(nll_model* m, const double* theta, int n_params, double* nll_out);
 
