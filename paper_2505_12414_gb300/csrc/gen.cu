@@ -20,13 +20,36 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "../../include/gbnll.h"
+#include "fp64_math.cuh"
 #include "gbnll_internal.h"
 
 namespace gbnll {
 namespace {
+
+// exp, log and sin/cos tables (fill_device_tables), uploaded once per device; the generation
+// kernel reads the logarithm's part through the read-only cache
+__device__ double g_gtab[kTabDoubles];
+std::mutex g_gtab_mutex;
+bool g_gtab_ready[64];
+
+cudaError_t ensure_gen_tables()
+{
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_gtab_mutex);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (g_gtab_ready[device]) return cudaSuccess;
+    static double tab[kTabDoubles];
+    fill_device_tables(tab);
+    e = cudaMemcpyToSymbol(g_gtab, tab, kTabDoubles * sizeof(double));
+    if (e == cudaSuccess) g_gtab_ready[device] = true;
+    return e;
+}
 
 constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
 constexpr int kMaxTries = 4096;  // per event and stage; P(no acceptance) < 1e-180 at 10 %
@@ -122,13 +145,16 @@ __global__ void __launch_bounds__(256) gen_kernel(GenArgs a)
         // warp, serves both (log(1 + u em1) for the background: 1 + u em1 lies in
         // [exp(alpha (mb - ma)), 1] and is formed with one rounding, which costs no accuracy
         // that matters unless |em1| is small; then log1p takes the background, a branch that
-        // is uniform because em1 is a constant of the launch).
+        // is uniform because em1 is a constant of the launch).  The logarithm is the
+        // table-driven one of fp64_math.cuh: its arguments here are at least 2^-53 (u draws
+        // lie in [2^-53, 1 - 2^-53] and em1 > -1), so always positive normals.
         const double u1 = draw(1, 0);
-        const double lg1 = g.bg_log1p ? (sig ? log(u1) : log1p(u1 * g.em1)) : log(sig ? u1 : fma(u1, g.em1, 1.0));
+        const double lg1 = g.bg_log1p ? (sig ? flog(u1, g_gtab) : log1p(u1 * g.em1))
+                                      : flog(sig ? u1 : fma(u1, g.em1, 1.0), g_gtab);
         if (sig) {
             double lg = lg1;
             for (; k < kMaxTries; ++k) {  // Box-Muller, truncated to the window
-                if (k > 1) lg = log(draw(k, 0));
+                if (k > 1) lg = flog(draw(k, 0), g_gtab);
                 double z = sqrt(-2.0 * lg) * cospi(2.0 * draw(k, 1));
                 m = g.mu + g.sigma * z;
                 if (m >= g.ma && m <= g.mb) {
@@ -235,6 +261,8 @@ static cudaError_t gen_launch(const GenConst& g, const int64_t* counts, const ui
     const int64_t total = first[n_toys];
     *failed = 0;
     if (total == 0) return cudaSuccess;
+    cudaError_t et = ensure_gen_tables();
+    if (et != cudaSuccess) return et;
     int64_t *d_first = nullptr, *d_count = nullptr, *d_pos = nullptr;
     uint64_t* d_state = nullptr;
     int* d_fail = nullptr;
