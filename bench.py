@@ -53,7 +53,7 @@ METRIC = "events/s per NLL+grad eval (4D, 1M ev, FP64)"
 #  => 82 flops of arithmetic, plus one exponential and one reciprocal per event charged
 #  at the cost of CUDA's own exp() and 1.0/x on GB300, in DFMA issue slots of 2 flops:
 #  16.0 and 4.7 slots, measured once with nll_calibrate_fp64 (exp: 1.5996e1 slots; division:
-#  5.688 slots including one DADD) and frozen here (profiles/fp64_calibration.md).
+#  5.688 slots including one DADD) and frozen here.
 ARITH_FLOPS_4D = 82.0
 C_EXP_DFMA = 16.0
 C_RCP_DFMA = 4.7
@@ -62,10 +62,13 @@ FLOPS_PER_EVENT = ARITH_FLOPS_4D + 2.0 * (C_EXP_DFMA + C_RCP_DFMA)
 # = 1.26 TFLOP/s, the nominal 1.25 TFLOP/s (MEASURED_PEAKS.json has no FP64 entry).  ncu's
 # FP64-pipe peak is the same 2 DFMA/clk/SM.
 FP64_PEAK_TFLOPS = 1.25
-# DRAM traffic of one evaluation (dram__bytes_read.sum + dram__bytes_write.sum of the fused
-# kernel at 152 x 256 plus its final-sum kernel, one ncu capture of the current kernels,
-# profiles/fused_nll_kstar4d_1M.md).
+# DRAM traffic of one evaluation: dram__bytes_read.sum + dram__bytes_write.sum of the fused
+# kernel at 152 x 256 plus its final-sum kernel on this 1M-event sample, from one ncu capture
+# of the current kernels (ncu cannot run inside the timed bench).
 KERNEL_TRAFFIC_BYTES = 132.6e6
+KERNEL_TRAFFIC_SOURCE = ("ncu --set full --clock-control none capture of fused_nll_kernel<4D, precompute, grad> "
+                         "(152 x 256) and final_reduce_kernel on the 1M-event 4D sample after an L2 flush: "
+                         "dram__bytes_read.sum + dram__bytes_write.sum")
 
 
 def parse():
@@ -153,33 +156,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(cols, seconds=10.0, sample=100_000, seconds_1t=5.0, sample_1t=20_000):
-    """The oracle, as it stands, on the host cores: events/s per NLL+grad evaluation, with all
-    the cores this process may use (the reported figure) and with one thread."""
+def cpu_baseline(cols, seconds=10.0, seconds_1t=5.0):
+    """The oracle, as it stands, on the host cores: events/s per NLL+grad evaluation of the
+    whole 1M-event sample (the workload of the timed GPU steps, and the sample of every step of
+    the reference arm), with all the cores this process may use (the reported figure) and with
+    one thread.  Each evaluation takes a different parameter point of the same sequence."""
     import oracle
 
     cores = len(os.sched_getaffinity(0))
-    th = thetas(3)
+    n = len(cols[0])
+    th = thetas(8)
 
-    def rate(n, nthreads, budget):
-        sub = [c[:n] for c in cols]
-        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[0], nthreads=nthreads)
+    def rate(nthreads, budget):
+        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, cols, th[0], nthreads=nthreads)  # warm-up
         t0 = time.perf_counter()
         evals = 0
         while True:
-            oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[evals % 3], nthreads=nthreads)
+            oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, cols, th[1 + evals % 7], nthreads=nthreads)
             evals += 1
             if time.perf_counter() - t0 > budget:
                 break
         return evals * n / (time.perf_counter() - t0), evals
 
-    v, evals = rate(sample, cores, seconds)
-    v1, evals1 = rate(sample_1t, 1, seconds_1t)
+    v, evals = rate(cores, seconds)
+    v1, evals1 = rate(1, seconds_1t)
     return {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": "%d NLL+grad evals of the first %d events of the 4D 1M-event sample, %d threads" %
-                      (evals, sample, cores),
+            "sample": "%d NLL+grad evaluations of the whole %d-event 4D sample, %d threads" % (evals, n, cores),
             "single_thread": {"value": v1, "unit": "events/s", "cores": 1,
-                              "sample": "%d NLL+grad evals of the first %d events, 1 thread" % (evals1, sample_1t)}}
+                              "sample": "%d NLL+grad evaluations of the whole %d-event sample, 1 thread" %
+                                        (evals1, n)}}
 
 
 def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
@@ -481,6 +486,9 @@ def scale_weighted(g, device, stream, n_events=10_000_000, reps=10):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (plain C, FP64, Kahan), as it stands, on the host cores,
+    each step one NLL+gradient evaluation of the whole 1M-event 4D sample (the workload of our
+    arm) at a new parameter point."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -488,21 +496,20 @@ def run_reference(args):
 
     cols = synth.kstar4d(N_EVENTS, stream=0)
     cores = len(os.sched_getaffinity(0))
-    sample = 200_000
-    sub = [c[:sample] for c in cols]
     th = thetas(args.warmup + args.steps)
     for i in range(args.warmup):
-        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[i], nthreads=cores)
+        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, cols, th[i], nthreads=cores)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, sub, th[args.warmup + i], nthreads=cores)
+        oracle.nll_grad(oracle.KSTAR4D, synth.RANGES_4D, cols, th[args.warmup + i], nthreads=cores)
     dt = time.perf_counter() - t0
-    value = args.steps * sample / dt
-    desc = "%d events of the 4D 1M-event sample per step, oracle (C, FP64, Kahan), %d threads" % (sample, cores)
+    value = args.steps * N_EVENTS / dt
+    desc = ("%d NLL+grad evaluations of the whole %d-event 4D sample (one per step), oracle (C, FP64, Kahan), "
+            "%d threads" % (args.steps, N_EVENTS, cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "sample_events": sample},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_events": N_EVENTS},
             "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -554,12 +561,17 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kernel_ms = []
+    kernel_ms, host_ms = [], []
     for i in range(args.steps):
         flush.zero_()
+        # wait for the flush, so that the step's start event is not queued behind it and the
+        # step time covers the host work (hoisting, launch) as well as the device work
+        stream.synchronize()
+        t0 = time.perf_counter()
         starts[i].record(stream)
         model.eval_grad(th[args.warmup + i])
         ends[i].record(stream)
+        host_ms.append(1e3 * (time.perf_counter() - t0))
         kernel_ms.append(g.nll_last_kernel_ms(model.handle))
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -610,7 +622,7 @@ def run_ours(args):
     kms = statistics.fmean(kernel_ms)  # average launch duration over the timed steps
     achieved = FLOPS_PER_EVENT * N_EVENTS / (kms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": KERNEL_TRAFFIC_BYTES,
+                "frac": achieved / peak, "traffic": KERNEL_TRAFFIC_BYTES, "traffic_source": KERNEL_TRAFFIC_SOURCE,
                 "kernel": "fused_nll_kernel<4D, precompute, grad> + final_reduce_kernel", "kernel_ms": kms,
                 "kernel_ms_median": statistics.median(kernel_ms),
                 "peak_source": "recipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s FP64)",
@@ -642,6 +654,9 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step,
                 "ms_per_step_median": median_step_ms,
+                "host_wall_ms_per_call": {"median": statistics.median(host_ms), "mean": statistics.fmean(host_ms),
+                                          "what": "perf_counter around the blocking eval_grad call (Python "
+                                                  "binding, hoisting, launch, wait for the results, assembly)"},
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "n_events": N_EVENTS, "model": "B0->K*0mumu 4D, 18 params",
                            "variant": {1: "precompute", 2: "direct"}.get(launch["variant"]),

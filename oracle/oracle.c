@@ -52,7 +52,8 @@
  *
  * Threads: events are split into static contiguous chunks, each chunk sums with
  * Kahan, and the chunk sums are merged in chunk order (again with Kahan), so the
- * result does not depend on scheduling.
+ * result does not depend on scheduling.  The chunks run on worker threads started at
+ * the first multi-threaded call and kept until the process exits.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared (no -ffast-math).
  */
@@ -440,6 +441,103 @@ static void event_second(const model_t* M, const double* x, double* d2P)
 }
 
 /* ------------------------------------------------------------------ */
+/* Worker threads, started once and kept for the life of the process, */
+/* so that a call's time is its arithmetic and not thread start-up.   */
+/* A call hands chunk t (t >= 1) to worker t-1 and runs chunk 0       */
+/* itself; which thread runs a chunk does not change any result,      */
+/* since every chunk is summed on its own and merged in chunk order.  */
+/* ------------------------------------------------------------------ */
+#define OR_POOL_MAX 256
+
+typedef struct {
+    pthread_mutex_t mu;       /* guards everything below                        */
+    pthread_cond_t go, done;  /* new work published / a worker finished         */
+    pthread_mutex_t call_mu;  /* one call at a time uses the workers             */
+    int nworkers;
+    unsigned long gen;        /* incremented for every call's work               */
+    int pending;              /* chunks handed out and not yet finished          */
+    int ntasks;               /* chunks of the current call (chunk 0: the caller) */
+    void* (*fn)(void*);
+    char* args;
+    size_t stride;
+} pool_t;
+
+static pool_t g_pool = {PTHREAD_MUTEX_INITIALIZER, PTHREAD_COND_INITIALIZER, PTHREAD_COND_INITIALIZER,
+                        PTHREAD_MUTEX_INITIALIZER, 0, 0, 0, 0, NULL, NULL, 0};
+/* generation counter at each worker's creation: work published after it is the worker's */
+static unsigned long g_worker_gen0[OR_POOL_MAX];
+static pthread_once_t g_pool_once = PTHREAD_ONCE_INIT;
+
+static void* pool_worker(void* arg)
+{
+    const int id = (int)(intptr_t)arg; /* runs chunk id + 1 */
+    pthread_mutex_lock(&g_pool.mu);
+    unsigned long seen = g_worker_gen0[id];
+    for (;;) {
+        while (g_pool.gen == seen) pthread_cond_wait(&g_pool.go, &g_pool.mu);
+        seen = g_pool.gen;
+        if (id + 1 >= g_pool.ntasks) continue;
+        void* (*fn)(void*) = g_pool.fn;
+        void* a = g_pool.args + (size_t)(id + 1) * g_pool.stride;
+        pthread_mutex_unlock(&g_pool.mu);
+        fn(a);
+        pthread_mutex_lock(&g_pool.mu);
+        if (--g_pool.pending == 0) pthread_cond_signal(&g_pool.done);
+    }
+    return NULL;
+}
+
+/* A child made by fork() has none of the parent's worker threads: forget them there. */
+static void pool_after_fork_child(void)
+{
+    pthread_mutex_init(&g_pool.mu, NULL);
+    pthread_cond_init(&g_pool.go, NULL);
+    pthread_cond_init(&g_pool.done, NULL);
+    pthread_mutex_init(&g_pool.call_mu, NULL);
+    g_pool.nworkers = 0;
+    g_pool.pending = 0;
+    g_pool.ntasks = 0;
+}
+
+static void pool_register_fork(void) { pthread_atfork(NULL, NULL, pool_after_fork_child); }
+
+/* Run fn on ntasks argument blocks (args + t * stride); returns once all have finished.
+ * Falls back to running everything on the calling thread if workers cannot be started. */
+static void pool_run(void* (*fn)(void*), void* args, size_t stride, int ntasks)
+{
+    char* base = (char*)args;
+    if (ntasks <= 1) {
+        if (ntasks == 1) fn(base);
+        return;
+    }
+    pthread_once(&g_pool_once, pool_register_fork);
+    pthread_mutex_lock(&g_pool.call_mu);
+    pthread_mutex_lock(&g_pool.mu);
+    while (g_pool.nworkers < ntasks - 1 && g_pool.nworkers < OR_POOL_MAX - 1) {
+        pthread_t t;
+        g_worker_gen0[g_pool.nworkers] = g_pool.gen;
+        if (pthread_create(&t, NULL, pool_worker, (void*)(intptr_t)g_pool.nworkers) != 0) break;
+        pthread_detach(t);
+        g_pool.nworkers++;
+    }
+    int nw = g_pool.nworkers < ntasks - 1 ? g_pool.nworkers : ntasks - 1;
+    g_pool.fn = fn;
+    g_pool.args = base;
+    g_pool.stride = stride;
+    g_pool.ntasks = nw + 1;
+    g_pool.pending = nw;
+    g_pool.gen++;
+    pthread_cond_broadcast(&g_pool.go);
+    pthread_mutex_unlock(&g_pool.mu);
+    fn(base);
+    for (int t = nw + 1; t < ntasks; ++t) fn(base + (size_t)t * stride); /* chunks no worker took */
+    pthread_mutex_lock(&g_pool.mu);
+    while (g_pool.pending > 0) pthread_cond_wait(&g_pool.done, &g_pool.mu);
+    pthread_mutex_unlock(&g_pool.mu);
+    pthread_mutex_unlock(&g_pool.call_mu);
+}
+
+/* ------------------------------------------------------------------ */
 /* Event loop with Kahan sums, split over threads in static chunks.   */
 /* ------------------------------------------------------------------ */
 typedef struct {
@@ -501,12 +599,7 @@ int oracle_nll_grad(int kind, const double* ranges, const double* const* cols, c
     if (nthreads > 256) nthreads = 256;
     if (n < (int64_t)nthreads * 64) nthreads = 1;
     chunk_t* ch = (chunk_t*)calloc((size_t)nthreads, sizeof(chunk_t));
-    pthread_t* tid = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
-    if (!ch || !tid) {
-        free(ch);
-        free(tid);
-        return OR_ERR_ARG;
-    }
+    if (!ch) return OR_ERR_ARG;
     for (int t = 0; t < nthreads; ++t) {
         ch[t].M = &M;
         ch[t].cols = cols;
@@ -515,12 +608,7 @@ int oracle_nll_grad(int kind, const double* ranges, const double* const* cols, c
         ch[t].hi = n * (t + 1) / nthreads;
         ch[t].want_grad = want_grad;
     }
-    if (nthreads == 1) {
-        chunk_run(&ch[0]);
-    } else {
-        for (int t = 0; t < nthreads; ++t) pthread_create(&tid[t], NULL, chunk_run, &ch[t]);
-        for (int t = 0; t < nthreads; ++t) pthread_join(tid[t], NULL);
-    }
+    pool_run(chunk_run, ch, sizeof(chunk_t), nthreads);
     kahan_t tot = {0, 0}, g[OR_MAXPAR], sc[OR_MAXPAR];
     memset(g, 0, sizeof g);
     memset(sc, 0, sizeof sc);
@@ -537,7 +625,6 @@ int oracle_nll_grad(int kind, const double* ranges, const double* const* cols, c
         bad += ch[t].bad;
     }
     free(ch);
-    free(tid);
     if (bad) {
         *nll = INFINITY;
         return OR_ERR_NONPOSITIVE;
@@ -619,12 +706,7 @@ int oracle_nll_hess(int kind, const double* ranges, const double* const* cols, c
     if (nthreads > 256) nthreads = 256;
     if (n < (int64_t)nthreads * 64) nthreads = 1;
     hchunk_t* ch = (hchunk_t*)calloc((size_t)nthreads, sizeof(hchunk_t));
-    pthread_t* tid = (pthread_t*)calloc((size_t)nthreads, sizeof(pthread_t));
-    if (!ch || !tid) {
-        free(ch);
-        free(tid);
-        return OR_ERR_ARG;
-    }
+    if (!ch) return OR_ERR_ARG;
     for (int t = 0; t < nthreads; ++t) {
         ch[t].M = &M;
         ch[t].cols = cols;
@@ -632,12 +714,7 @@ int oracle_nll_hess(int kind, const double* ranges, const double* const* cols, c
         ch[t].lo = n * t / nthreads;
         ch[t].hi = n * (t + 1) / nthreads;
     }
-    if (nthreads == 1) {
-        hchunk_run(&ch[0]);
-    } else {
-        for (int t = 0; t < nthreads; ++t) pthread_create(&tid[t], NULL, hchunk_run, &ch[t]);
-        for (int t = 0; t < nthreads; ++t) pthread_join(tid[t], NULL);
-    }
+    pool_run(hchunk_run, ch, sizeof(hchunk_t), nthreads);
     const int np = M.npar;
     kahan_t tot = {0, 0};
     static const kahan_t zero = {0, 0};
@@ -664,7 +741,6 @@ int oracle_nll_hess(int kind, const double* ranges, const double* const* cols, c
         bad += ch[t].bad;
     }
     free(ch);
-    free(tid);
     if (bad) {
         *nll = INFINITY;
         return OR_ERR_NONPOSITIVE;
