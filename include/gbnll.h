@@ -433,27 +433,30 @@ void nll_server_destroy(nll_server* s);
  * counterpart: this entry exists for callers that cannot call cudaMalloc -- for example code
  * running where another allocator owns the device's memory (a framework that has reserved
  * the memory in its own pool), or loops that cannot afford cudaMalloc's implicit device-wide
- * synchronisation.  It runs the same fused kernel as a 4D model in the direct variant (the
- * angular basis is recomputed from the angles), so nothing per event is stored.
+ * synchronisation.  It runs the fused kernel of an in-place 4D model (nll_load_events with
+ * on_device = 2): the direct angular variant (the basis is recomputed from the angles), loads
+ * that never read past event n_events - 1, and the range check and sum w (m - ma) in the same
+ * pass, so nothing per event is stored and one launch (plus its final sums) does the work.
  *   obs_ranges   [ma, mb, -1, 1, -1, 1, -pi, pi] (as nll_create_model).
  *   dev_columns  4 device pointers on the current device (m, ctl, ctk, phi), each 16-byte
- *                aligned and readable for n_events rounded up to an even count of doubles
- *                (the kernel loads two consecutive events with one 128-bit load).
+ *                aligned (checked), holding at least n_events doubles.
  *   dev_weights  device pointer with the same layout, or NULL for w_i = 1.
  *   theta        host array of 18 parameters (order of nll_create_model); 0 < fsig < 1.
  *   blocks       grid size of the fused kernel, 0 = two blocks per SM; at most
  *                NLL_NOALLOC_MAX_BLOCKS, larger values are rejected with NLL_ERR_ARG.
- *   cuda_stream  stream of the launches and copies (0 = CUDA's default stream).
+ *   cuda_stream  stream of the launches and copies (0 = CUDA's default stream); the caller
+ *                orders the writes of the columns before it.
  *   nll_out, grad_out  host outputs (1 and 18 doubles).  The call blocks until they are set.
- * Scratch: block partials, result slots and the grid ticket live in one static __device__
- * array of (21 x NLL_NOALLOC_MAX_BLOCKS + 64) doubles (about 172 KB), which every GPU that
- * loads this library holds until the process exits.  All calls share it and it keeps the
- * last call's contents; the call clears the ticket itself.  Calls that overlap on the GPU
- * (from different host threads or streams) race on it and must be serialised by the caller.
- * The first call on a device looks up the array's device address and uploads the
- * exponential table for that device (no allocation); make that first call before any
- * stream capture.  Errors: NLL_ERR_ARG (sizes, alignment, ranges, parameters, events
- * outside the ranges), NLL_ERR_NONPOSITIVE_PDF, NLL_ERR_CUDA.  No text via nll_last_error.
+ * Scratch: the block partials and the final sums live in one static __device__ array of
+ * (23 x NLL_NOALLOC_MAX_BLOCKS + 32) doubles (about 189 KB), which every GPU that loads this
+ * library holds until the process exits.  All calls share it and it keeps the last call's
+ * contents; nothing in it needs clearing, since every launch writes each value it reads.
+ * Calls that overlap on the GPU (from different host threads or streams) race on it and
+ * must be serialised by the caller.  The first call on a device looks up the array's device
+ * address and uploads the exponential and sin/cos table for that device (no allocation); make
+ * that first call before any stream capture.  Errors: NLL_ERR_ARG (sizes, alignment, ranges,
+ * parameters, events outside the ranges or negative weights: outputs +inf / NaN),
+ * NLL_ERR_NONPOSITIVE_PDF, NLL_ERR_CUDA.  No text via nll_last_error.
  */
 #define NLL_NOALLOC_MAX_BLOCKS 1024
 int nll_eval_grad_4d_noalloc(const double* obs_ranges, const double* const* dev_columns, const double* dev_weights,

@@ -446,15 +446,47 @@ def nll_diag_uniforms(seed, stream, n, device=0):
     return out
 
 
-def nll_eval_grad_4d_noalloc(obs_ranges, dev_columns, theta, dev_weights=None, blocks=0, stream=0, check=True):
-    """4D NLL and gradient on caller-owned device buffers (CUDA tensors or raw pointers),
-    without any device allocation by the library.  Returns (nll, grad[, status])."""
+def _noalloc_stream(stream, dev_columns):
+    """The stream to run on: the given one, else torch's current stream when the columns are
+    CUDA tensors (so that work queued on it, such as the columns' own writes, comes first),
+    else CUDA's default stream."""
+    if stream:
+        return int(stream)
+    if dev_columns and _is_cuda_tensor(dev_columns[0]):
+        import torch
+
+        return int(torch.cuda.current_stream(dev_columns[0].device).cuda_stream)
+    return 0
+
+
+def nll_eval_grad_4d_noalloc(obs_ranges, dev_columns, theta, dev_weights=None, blocks=0, stream=0, check=True,
+                             n_events=None):
+    """4D NLL and gradient on caller-owned device buffers, without any device allocation by the
+    library.  dev_columns are four CUDA tensors (the event count is their length unless
+    n_events says otherwise) or four raw device pointers (then n_events is required).  Returns
+    (nll, grad) or, with check=False, (nll, grad, status)."""
     L = load()
     r = _f64(obs_ranges)
+    if len(dev_columns) != 4:
+        raise ValueError("four device columns (m, cos theta_l, cos theta_K, phi) expected")
+    tensors = all(_is_cuda_tensor(c) for c in dev_columns)
+    if n_events is None:
+        if not tensors:
+            raise ValueError("n_events is required when raw device pointers are passed")
+        n_events = int(dev_columns[0].numel())
+    if tensors:
+        for c in dev_columns:
+            if c.dtype != _torch_f64() or not c.is_contiguous() or c.numel() < n_events:
+                raise ValueError("columns must be contiguous float64 CUDA tensors of at least n_events elements")
     ptrs = [c.data_ptr() if hasattr(c, "data_ptr") else int(c) for c in dev_columns]
     arr = (ctypes.c_void_p * 4)(*ptrs)
-    n = int(dev_columns[0].numel()) if hasattr(dev_columns[0], "numel") else None
-    return _noalloc_call(L, r, arr, dev_weights, n, theta, blocks, stream, check)
+    return _noalloc_call(L, r, arr, dev_weights, n_events, theta, blocks, _noalloc_stream(stream, dev_columns), check)
+
+
+def _torch_f64():
+    import torch
+
+    return torch.float64
 
 
 def _noalloc_call(L, r, arr, dev_weights, n, theta, blocks, stream, check):
@@ -476,11 +508,8 @@ def _noalloc_call(L, r, arr, dev_weights, n, theta, blocks, stream, check):
 def nll_eval_grad_4d_noalloc_n(obs_ranges, dev_columns, n_events, theta, dev_weights=None, blocks=0, stream=0,
                                check=True):
     """As nll_eval_grad_4d_noalloc with an explicit event count (buffers may be longer)."""
-    L = load()
-    r = _f64(obs_ranges)
-    ptrs = [c.data_ptr() if hasattr(c, "data_ptr") else int(c) for c in dev_columns]
-    arr = (ctypes.c_void_p * 4)(*ptrs)
-    return _noalloc_call(L, r, arr, dev_weights, n_events, theta, blocks, stream, check)
+    return nll_eval_grad_4d_noalloc(obs_ranges, dev_columns, theta, dev_weights=dev_weights, blocks=blocks,
+                                    stream=stream, check=check, n_events=n_events)
 
 
 class Model:

@@ -198,9 +198,8 @@ int hess_occupancy(int kind, int variant, bool weighted);  // resident blocks pe
 // Static device scratch of nll_eval_grad_4d_noalloc (kernels.cu).
 constexpr int kNoAllocMaxBlocks = 1024;
 struct NoAllocScratch {
-    double* partials;      // [kAccMax][max_blocks]
-    double* out;           // [32]
-    unsigned int* ticket;  // grid-completion counter
+    double* partials;  // [kAccModel][max_blocks]
+    double* out;       // [32] final sums
     int max_blocks;
 };
 // Device addresses of the scratch on `device` (which must be current); set up once per device.

@@ -310,10 +310,11 @@ cudaError_t ensure_device_tables()
 
 // ----------------------------------------------------------------------------------
 // Static scratch for callers that cannot allocate device memory (nll_eval_grad_4d_noalloc).
-// One array per process and device, zero at module load, holding the block partials
-// ([kAccMax][kNoAllocMaxBlocks]), the final sums (32 slots) and the grid ticket.
+// One array per process and device, holding the block partials of the in-place 4D launch
+// ([kAccModel][kNoAllocMaxBlocks]) and its final sums (32 slots).  Nothing in it has to start
+// at zero: every launch writes each partial and each sum it later reads.
 // ----------------------------------------------------------------------------------
-constexpr int kNoAllocDoubles = kAccMax * kNoAllocMaxBlocks + 64;
+constexpr int kNoAllocDoubles = kAccModel * kNoAllocMaxBlocks + 32;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
 cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out)
@@ -331,8 +332,7 @@ cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out)
         base[device] = ptr;
     }
     out->partials = base[device];
-    out->out = base[device] + (size_t)kAccMax * kNoAllocMaxBlocks;
-    out->ticket = reinterpret_cast<unsigned int*>(out->out + 32);
+    out->out = base[device] + (size_t)kAccModel * kNoAllocMaxBlocks;
     out->max_blocks = kNoAllocMaxBlocks;
     return cudaSuccess;
 }

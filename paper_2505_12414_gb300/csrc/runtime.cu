@@ -1008,9 +1008,10 @@ int nll_precomputed_basis(nll_model* m, double* out)
 
 // ------------------------------------------------------------------------------------
 // No-allocation evaluation for callers that cannot call cudaMalloc.  The paper has no
-// counterpart.  Same fused kernel as the 4D model's direct variant; the block partials,
-// result slots and grid ticket live in a static device array (kernels.cu), and the sample
-// stays in the caller's device buffers.
+// counterpart.  One launch of the fused kernel's in-place 4D instance (direct angular
+// variant, tail-safe loads, range check and sum w (m - ma) in the same pass) and its final
+// sums; the block partials and the sums live in a static device array (kernels.cu), and the
+// sample stays in the caller's device buffers.
 // ------------------------------------------------------------------------------------
 int nll_eval_grad_4d_noalloc(const double* obs_ranges, const double* const* dev_columns, const double* dev_weights,
                              int64_t n_events, const double* theta, int n_params, int blocks, uintptr_t cuda_stream,
@@ -1055,71 +1056,44 @@ int nll_eval_grad_4d_noalloc(const double* obs_ranges, const double* const* dev_
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     const int64_t npairs = (n_events + 1) / 2;
 
-    // 1) range check and sum w (m - ma) over the caller's events
-    SArgs sa;
-    memset(&sa, 0, sizeof sa);
-    for (int d = 0; d < 4; ++d) {
-        sa.col[d] = dev_columns[d];
-        sa.lo[d] = m.ranges[2 * d];
-        sa.hi[d] = m.ranges[2 * d + 1];
-    }
-    sa.w = dev_weights;
-    sa.n = n_events;
-    sa.ndim = 4;
-    sa.partials = sc.partials;
-    sa.ticket = sc.ticket;
-    sa.out = sc.out;
-    int sblocks = (int)std::min<int64_t>(std::max<int64_t>((n_events + 255) / 256, 1), (int64_t)sms * 2);
-    sblocks = std::min(sblocks, sc.max_blocks);
-    double stats[3];
-    cudaError_t e = cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned int), stream);  // must start at zero
-    if (e == cudaSuccess) e = launch_stats(sblocks, 256, stream, sa);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(stats, sc.out, sizeof stats, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return NLL_ERR_CUDA;
-    if (stats[2] != 0.0) return NLL_ERR_ARG;
-
-    // 2) fused NLL + gradient
     KArgs a;
     memset(&a, 0, sizeof a);
     for (int d = 0; d < 4; ++d) a.col[d] = dev_columns[d];
     a.w = dev_weights;
     a.n = n_events;
     a.c = H.k;
+    a.ma = m.ranges[0];
+    for (int d = 0; d < 4; ++d) {
+        a.klo[d] = order_key_host(m.ranges[2 * d]);
+        a.khi[d] = order_key_host(m.ranges[2 * d + 1]);
+    }
+    a.klo[4] = order_key_host(-0.0);
+    a.khi[4] = order_key_host(1.0e300);
     a.partials = sc.partials;
-    a.ticket = sc.ticket;
-    a.out = sc.out;
+    a.out = sc.out;  // no completion words: the call synchronises the stream
     const int threads = 128;
     int nb = blocks ? blocks
                     : (int)std::min<int64_t>((int64_t)sms * 2, std::max<int64_t>((npairs + threads - 1) / threads, 1));
-    double S[kAccMax];
-    e = cudaMemsetAsync(sc.ticket, 0, sizeof(unsigned int), stream);
-    if (e == cudaSuccess) e = launch_fused(kKstar4D, kVarDirect, dev_weights != nullptr, true, nb, threads, stream, a);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(S, sc.out, sizeof(double) * kAcc4D, cudaMemcpyDeviceToHost, stream);
+    constexpr int KB = kAcc4D, K = kAcc4D + kAccInPlace;
+    double S[K];
+    cudaError_t e = launch_fused(kKstar4D, kVarDirect, dev_weights != nullptr, true, nb, threads, stream, a, true);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S, sc.out, sizeof S, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return NLL_ERR_CUDA;
 
-    // 3) assembly (as for the 4D model: see eval_impl)
-    if (S[kAcc4D - 1] != 0.0 || !isfinite(S[0])) {
+    // slot KB counts events outside the ranges (or with invalid weights), slot KB - 1 holds
+    // sum w (m - ma), the last slot the invalid densities; assembly as for a 4D model
+    if (S[KB] != 0.0) {
+        *nll_out = INFINITY;
+        for (int k = 0; k < 18; ++k) grad_out[k] = NAN;
+        return NLL_ERR_ARG;
+    }
+    if (S[K - 1] != 0.0 || !isfinite(S[0])) {
         *nll_out = INFINITY;
         for (int k = 0; k < 18; ++k) grad_out[k] = NAN;
         return NLL_ERR_NONPOSITIVE_PDF;
     }
-    *nll_out = -(H.alpha * stats[1] + S[0]);
-    const double two_b0 = 2.0 * H.b0, dma = H.mu - H.ma;
-    double dL[18];
-    dL[0] = two_b0 * S[2] - H.dlnN1_dmu * S[1];
-    dL[1] = two_b0 / H.sigma * S[3] - (1.0 / H.sigma + H.dlnN1_dsig) * S[1];
-    for (int k = 0; k < 8; ++k) dL[2 + k] = S[4 + k];
-    dL[10] = S[13] + dma * S[12] - H.dlnN2t_dal * S[12];
-    dL[11] = H.b2 * S[14];
-    dL[12] = H.b2 * S[15] - H.dlnNc_dc2[0] * S[12];
-    dL[13] = S[16];
-    dL[14] = S[17] - H.dlnNc_dc2[1] * S[12];
-    dL[15] = S[18];
-    dL[16] = S[19] - H.dlnNc_dc2[2] * S[12];
-    dL[17] = S[1] / H.f - S[12] / (1.0 - H.f);
-    for (int k = 0; k < 18; ++k) grad_out[k] = -dL[k];
+    assemble_core(kKstar4D, H, S[KB - 1], S, nll_out, grad_out);
     return NLL_OK;
 }
 
