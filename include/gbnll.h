@@ -255,8 +255,9 @@ int nll_calibrate_fp64(int device, double* rates);
  * fn 1: the reciprocal, hardware approximation plus one cubic correction; fn 2 / fn 3:
  * sin x / cos x by the table method with Cody-Waite reduction, accurate for |x| <= pi, as
  * the 4D kernels use it for phi; fn 4: ln x after Tang's table-driven method, for positive
- * normal x, as the weighted kernels use it).  For accuracy tests against the host's libm;
- * allocates temporary device buffers.
+ * normal x, as the weighted kernels use it; fn 5: the hardware approximation of 1/x alone
+ * (rcp.approx.ftz.f64); fn 6: that approximation plus one Newton step).  For accuracy tests
+ * against the host's libm; allocates temporary device buffers.
  */
 int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
 

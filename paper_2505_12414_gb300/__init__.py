@@ -410,8 +410,9 @@ def nll_calibrate_fp64(device=0):
 
 
 def nll_diag_math(fn, x, device=0):
-    """Evaluate the library's device exp (fn=0), reciprocal (fn=1), sin (fn=2), cos (fn=3) or
-    log (fn=4) on host array x (see nll_diag_math in the C header for the argument conventions)."""
+    """Evaluate the library's device exp (fn=0), reciprocal (fn=1), sin (fn=2), cos (fn=3), log
+    (fn=4), the hardware reciprocal approximation alone (fn=5) or with one Newton step (fn=6) on
+    host array x (see nll_diag_math in the C header for the argument conventions)."""
     xa = _f64(x)
     y = np.zeros_like(xa)
     st = load().nll_diag_math(int(device), int(fn), _p(xa), _p(y), len(xa))

@@ -141,15 +141,32 @@ __device__ __forceinline__ void fsincos_pi(double x, const double* __restrict__ 
     c = fma(cs.x, cm, fma(-cs.y, sr, cs.x));
 }
 
+// The hardware reciprocal approximation alone (diagnostics: its accuracy decides how many
+// correction terms the kernels need).
+__device__ __forceinline__ double frcp_approx(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
 // 1/x from the hardware approximation plus one cubic correction: with e = 1 - x y0,
 // 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...).  3 FP64 instructions + 1 MUFU.
 __device__ __forceinline__ double frcp(double x)
 {
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double y = frcp_approx(x);
     double e = fma(-x, y, 1.0);
     double t = fma(e, e, e);
     return fma(y, t, y);
+}
+
+// 1/x from the hardware approximation plus one Newton step y0 (1 + e): relative error e^2.
+// 2 FP64 instructions + 1 MUFU.
+__device__ __forceinline__ double frcp_newton(double x)
+{
+    const double y = frcp_approx(x);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, e, y);
 }
 
 // 1 if x is not a positive normal finite double (integer pipe only).

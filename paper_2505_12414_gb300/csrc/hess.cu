@@ -63,6 +63,9 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
     __shared__ double s_lnp[kHessThreads / 32];
     __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // the slot-total kernel behind this one may be scheduled now: it waits (griddepcontrol.wait)
+    // for this grid to complete, so its launch latency overlaps the event loop
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_htab[j];
     __syncthreads();

@@ -28,8 +28,9 @@
 //    thread handles two consecutive events per iteration of a grid-stride loop, in one
 //    basic block (the ragged tail masks the second event arithmetically, no branch), so
 //    the two events' dependency chains interleave in the FP64 pipe.
-//  * Warp reductions halve the slot count per shuffle level (31 FP64 adds per warp for
-//    up to 32 slots) instead of a shuffle tree per slot.
+//  * Warp reductions halve the slot count per shuffle level (ceil(K/2) + ceil(K/4) + ...
+//    FP64 adds per warp: 23 for the 21 slots of the 4D gradient, 9 for the mass model's 7)
+//    instead of a shuffle tree per slot.
 //  * The grid is a small multiple of the SM count; block partial sums are written to a
 //    scratch buffer and final_reduce_kernel, launched behind the fused kernel as a
 //    programmatic dependent, adds them in a fixed order (one block per slot), so results
@@ -63,6 +64,9 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
     __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
     __shared__ double s_red[8 * K];
 
+    // the final-sum kernel behind this one may be scheduled now: it waits (griddepcontrol.wait)
+    // for this grid to complete, so its launch latency overlaps the event loop
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int64_t n = a.n;
     const int64_t npairs = (n + 1) >> 1;
     const int64_t begin = npairs * blockIdx.x / gridDim.x;
@@ -116,9 +120,10 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
 // (thread t takes blocks t, t + 64, ...; then a shuffle tree and the two warps), writes
 // out[k] and, with `done` set, stores seq into done[k] after a system-scope fence, so a host
 // thread polling done[0..K) reads complete results.  It is launched as a programmatic
-// dependent of the fused kernel: griddepcontrol.wait returns once that grid has finished and
-// its partials are visible, about a microsecond after its last block exits, where a plain
-// stream-ordered launch would start several microseconds later.  Spreading the K slots over
+// dependent of the fused kernel, which lets it be scheduled as soon as every fused block has
+// started (griddepcontrol.launch_dependents at the top of the fused kernel):
+// griddepcontrol.wait then returns once that grid has finished and its partials are visible,
+// where a plain stream-ordered launch would start several microseconds later.  Spreading the K slots over
 // K blocks (K SMs) keeps this step off the single-SM FP64 bottleneck a last-block reduction
 // has, and needs no ticket or grid-wide fence in the fused kernel.
 __global__ void __launch_bounds__(64) final_reduce_kernel(const double* partials, int nb, double* out,

@@ -180,28 +180,60 @@ __device__ __forceinline__ void event_4d(const KConst& c, double m, const double
 // Fixed-order reductions
 // ----------------------------------------------------------------------------------
 
-// Warp reduction of K slots by recursive halving: at level s each lane keeps half of its
-// slots, sends the other half to lane ^ s and adds what it receives, so the warp spends
-// 16 + 8 + 4 + 2 + 1 = 31 FP64 additions instead of 5 K.  On return lane l holds the
-// warp total of slot l (l < K).  The pairing is fixed, so the result is deterministic.
+// Warp reduction of K slots by recursive halving: at each level a lane keeps the lower or
+// upper part of the slots it holds (the lower part has ceil(n/2) of its n slots, the upper the
+// rest, padded with a zero), sends the other part to lane ^ s and adds what it receives, so
+// the warp spends ceil(K/2) + ceil(K/4) + ... FP64 additions (23 for 21 slots, 21 for 19)
+// instead of 5 K.  On return each lane holds the warp total of slot reduce_slot_of<K>(lane)
+// (-1: none).  The pairing is fixed, so the result is deterministic.
+template <int K>
+__device__ __forceinline__ int reduce_slot_of(int lane)
+{
+    // the split of each level is the same for all lanes: h = ceil(n/2) of the n = K, ceil(K/2),
+    // ... slots the level starts from; a lane's group holds min(cnt, h) (lower) or
+    // max(cnt - h, 0) (upper) of them
+    int first = 0, cnt = K, n = K;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const int h = (n + 1) >> 1;
+        if (lane & s) {
+            first += h;
+            cnt = cnt > h ? cnt - h : 0;
+        } else {
+            cnt = cnt < h ? cnt : h;
+        }
+        n = h;
+    }
+    return cnt == 1 ? first : -1;
+}
+
 template <int K>
 __device__ __forceinline__ double warp_reduce_slots(const double (&in)[K])
 {
     static_assert(K <= 32, "at most 32 slots");
     const int lane = threadIdx.x & 31;
-    double v[32];
+    double v[K];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = k < K ? in[k] : 0.0;
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool upper = (lane & s) != 0;
-#pragma unroll
-        for (int i = 0; i < s; ++i) {
-            double send = upper ? v[i] : v[i + s];
-            double keep = upper ? v[i + s] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
-        }
+    for (int k = 0; k < K; ++k) v[k] = in[k];
+    constexpr int h16 = (K + 1) >> 1, h8 = (h16 + 1) >> 1, h4 = (h8 + 1) >> 1, h2 = (h4 + 1) >> 1;
+    // one level: n slots held, h = ceil(n/2) kept (indices past n read as zero)
+#define GBNLL_HALVE(S, N, H)                                                  \
+    {                                                                         \
+        const bool upper = (lane & (S)) != 0;                                 \
+        _Pragma("unroll") for (int i = 0; i < (H); ++i)                       \
+        {                                                                     \
+            const double hi = (i + (H) < (N)) ? v[(i + (H)) % K] : 0.0;       \
+            const double send = upper ? v[i] : hi;                            \
+            const double keep = upper ? hi : v[i];                            \
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, (S));            \
+        }                                                                     \
     }
+    GBNLL_HALVE(16, K, h16)
+    GBNLL_HALVE(8, h16, h8)
+    GBNLL_HALVE(4, h8, h4)
+    GBNLL_HALVE(2, h4, h2)
+    GBNLL_HALVE(1, h2, 1)
+#undef GBNLL_HALVE
     return v[0];
 }
 
@@ -211,7 +243,8 @@ __device__ __forceinline__ double block_reduce(const double (&v)[K], double* sme
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     double s = warp_reduce_slots<K>(v);
-    if (lane < K) smem[warp * K + lane] = s;
+    const int slot = reduce_slot_of<K>(lane);
+    if (slot >= 0) smem[warp * K + slot] = s;
     __syncthreads();
     double res = 0.0;
     if (threadIdx.x < K) {

@@ -81,3 +81,18 @@ def test_table_log_accuracy(gpu_lib):
     assert np.all(y[~ok] == 0.0)
     err = np.abs(y[ok].astype(np.longdouble) - ref[ok]) / np.spacing(np.abs(ref[ok]).astype(np.float64)).astype(np.longdouble)
     assert float(err.max()) <= 1.0, (float(err.max()), x[ok][np.argmax(err)])
+
+
+def test_reciprocal_correction_order(gpu_lib):
+    """Why the kernels correct the hardware reciprocal cubically: rcp.approx.ftz.f64 alone is
+    good to about 2^-20, so one Newton step (error e^2) leaves about 2^-40 (1e-12, which would
+    enter every gradient term), while the cubic step (error e^3) reaches a correctly rounded
+    result (test_reciprocal_accuracy)."""
+    rs = synth.Stream(24, 0)
+    x = np.concatenate([np.exp((2 * rs.uniform(400000) - 1) * 600.0), 1.0 + rs.uniform(200000)])
+    xl = x.astype(np.longdouble)
+    e_approx = np.abs(gpu_lib.nll_diag_math(5, x).astype(np.longdouble) * xl - 1)
+    e_newton = np.abs(gpu_lib.nll_diag_math(6, x).astype(np.longdouble) * xl - 1)
+    assert 2.0 ** -24 < float(e_approx.max()) < 2.0 ** -18, float(e_approx.max())
+    assert float(e_newton.max()) <= 4.0 * float(e_approx.max()) ** 2 + 2.0 ** -52
+    assert float(e_newton.max()) > 2.0 ** -46  # far from the 2^-53 of the cubic correction
