@@ -84,15 +84,16 @@ def parse():
     ap.add_argument("--threads", type=int, default=128, help="threads per block without autotuning")
     ap.add_argument("--toys", type=int, default=1000, help="batched 4D toys (0 skips the toy-fit measurement)")
     ap.add_argument("--seq-toys", type=int, default=20, help="toys fitted one at a time for comparison")
-    ap.add_argument("--requests", type=int, default=30, help="served fits (0 skips the serving measurement)")
+    ap.add_argument("--requests", type=int, default=100, help="served fits (0 skips the serving measurement)")
     ap.add_argument("--study-toys", type=int, default=100, help="toys per size in the paper-style toy study (0 skips)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the mass-model event-count sweep")
     ap.add_argument("--no-calibration", action="store_true", help="skip the FP64 calibration kernels")
     ap.add_argument("--no-hessian", action="store_true", help="skip the analytic-Hessian measurement")
     ap.add_argument("--no-capacity", action="store_true",
                     help="skip the 2e8-event resident-sample and the 1e7 weighted-sample measurements")
-    ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0],
-                    help="Poisson arrival rates of served fits per second (one measurement each)")
+    ap.add_argument("--rate", type=float, nargs="+", default=[50.0, 2000.0, 20000.0],
+                    help="Poisson arrival rates of served fits per second (one measurement each; the highest "
+                         "offers more fits than either path completes, so fits/s measures capacity)")
     return ap.parse_args()
 
 
@@ -277,7 +278,8 @@ def serving(g, device, n_req, rate, seed_stream=0):
         servers = {k: g.Server(k, ranges[k], 16, 4_000_000 if k == g.NLL_MODEL_MASS1D else 8_000_000, 4096,
                                device=device, **opts[k]) for k in step}
         serve(servers, requests()[:2], realtime=False)  # warm-up
-        served = serve(servers, requests(), realtime=True)
+        phases = {}
+        served = serve(servers, requests(), realtime=True, phases=phases)
         for srv in servers.values():
             srv.close()
         models = {k: g.Model(k, ranges[k], device=device) for k in step}
@@ -287,8 +289,12 @@ def serving(g, device, n_req, rate, seed_stream=0):
             m.close()
         diffs = [float(np.max(np.abs(a.result["theta"] - b.result["theta"]) / b.result["err"]))
                  for a, b in zip(served, seq) if a.result["status"] == 0 and b.result["status"] == 0]
+        span_s = max(q.done for q in served) - min(q.arrival for q in served)
         r = {"options": {"strategy": strategy, "hessian": hessian}, "served": latency_summary(served),
              "sequential": latency_summary(seq), "converged": int(sum(q.result["status"] == 0 for q in served)),
+             "served_host_phases_ms": {k.replace("_s", "_ms"): (1e3 * v if k.endswith("_s") else v)
+                                       for k, v in phases.items()},
+             "served_span_ms": 1e3 * span_s,
              "max_abs_diff_over_sigma_vs_sequential": max(diffs) if diffs else None}
         if r["served"]["fits_per_s"] and r["sequential"]["fits_per_s"]:
             r["speedup_fits_per_s"] = r["served"]["fits_per_s"] / r["sequential"]["fits_per_s"]

@@ -139,8 +139,9 @@ typedef struct {
                        3: as 2, covariance H^-1 W H^-1 (weighted fits, see nll_eval_hess).
                        Values 2 and 3 (and strategy 2) need second derivatives of a model:
                        fit_minimise_fcn rejects them with NLL_ERR_ARG.  Batched and served fits
-                       run the analytic passes on the device (see nll_batch_fit; a server takes
-                       the start matrix at nll_server_submit and polishes at nll_server_poll). */
+                       run the analytic passes on the device (see nll_batch_fit; a server queues
+                       the start-matrix pass with the first step after admission and polishes
+                       at nll_server_poll). */
 } fit_options;
 
 #define FIT_MAXPAR 32
@@ -399,7 +400,9 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
 /*
  * nll_server_submit -- admit one fit: n_events events (host SoA columns; weights must be NULL,
  * a server serves unweighted fits) and its start point theta0 (host, npar doubles).  On
- * success *request_id identifies the fit and its events are on the device.
+ * success *request_id identifies the fit and its events are on the device.  The events go to
+ * the device on the server's collection stream and the call waits only for that copy and the
+ * range check, not for the steps in flight; the fit joins the steps queued after it.
  * Returns NLL_ERR_STATE (nothing admitted) when no slot or no pool range is free: the
  * caller keeps the request queued and retries after nll_server_poll returned finished fits.
  * Returns NLL_ERR_ARG for events outside the ranges (checked on the device after the copy;
@@ -409,19 +412,36 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
                       const double* theta0, int64_t* request_id);
 
 /* Queue n_steps device steps (graph replays) advancing every busy slot; returns without
- * waiting, so steps of servers on different streams overlap on the device.  nll_server_sync
- * waits for them (nll_server_poll and nll_server_submit also wait first).  With strategy 2
- * the call first runs one analytic Hessian pass over the fits admitted since the last step
- * (their start matrices) and waits for it.  With hessian 2 / 3 nll_server_poll polishes the
- * finished fits with the analytic Hessian (Newton passes, covariance) before returning them. */
+ * waiting, so steps of servers on different streams overlap on the device.  With strategy 2
+ * the call first queues one analytic Hessian pass over the fits admitted since the last step
+ * (their start matrices) on the server's step stream, ahead of the steps (no wait).
+ * nll_server_sync waits for everything queued. */
 int nll_server_step(nll_server* s, int n_steps);
 int nll_server_sync(nll_server* s);
 
 /*
+ * nll_server_progress -- non-blocking: *steps_in_flight receives the number of queued steps
+ * not yet completed (of the last 64), *finished the number of fits that have finished and
+ * wait for nll_server_poll (either output may be NULL).  A request loop keeps a couple of
+ * steps queued and polls when fits have finished, so the device never waits for the host.
+ */
+int nll_server_progress(const nll_server* s, int* steps_in_flight, int* finished);
+
+/*
  * nll_server_poll -- collect up to max_results finished fits: ids_out[i] and results[i]
- * (host arrays); *n_out receives the count.  Their slots and pool ranges are released.
+ * (host arrays); *n_out receives the count (0 when none has finished; the call does not wait
+ * for steps in flight).  Their slots and pool ranges are released.  With hessian 2 / 3 the
+ * finished fits are first polished with the analytic Hessian (Newton passes, covariance) on
+ * the server's collection stream, while the steps of the other fits go on.
  */
 int nll_server_poll(nll_server* s, int64_t* ids_out, fit_result* results, int max_results, int* n_out);
+
+/*
+ * nll_server_cancel -- withdraw an admitted fit that has not been polled yet: waits for the
+ * queued steps, marks the fit finished on the device and releases its slot and pool range
+ * without returning a result.  NLL_ERR_ARG if no such request is in the server.
+ */
+int nll_server_cancel(nll_server* s, int64_t request_id);
 
 /* Busy slots, free slots and free pool events (any output may be NULL). */
 int nll_server_status(const nll_server* s, int* busy, int* free_slots, int64_t* free_events);

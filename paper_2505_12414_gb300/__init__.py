@@ -132,6 +132,8 @@ def load(path=None):
                                   ctypes.POINTER(ctypes.c_int)]
     L.nll_server_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                     ctypes.POINTER(ctypes.c_int64)]
+    L.nll_server_progress.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.nll_server_cancel.argtypes = [vp, ctypes.c_int64]
     L.nll_server_last_error.argtypes = [vp]
     L.nll_server_last_error.restype = ctypes.c_char_p
     L.nll_server_destroy.argtypes = [vp]
@@ -733,8 +735,18 @@ class Server:
     def sync(self):
         _scheck(self.handle, load().nll_server_sync(self.handle))
 
+    def progress(self):
+        """Non-blocking: (steps queued and not yet completed, fits finished and not yet polled)."""
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _scheck(self.handle, load().nll_server_progress(self.handle, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def cancel(self, request_id):
+        """Withdraw an admitted fit that has not been polled: its slot and pool range are freed."""
+        _scheck(self.handle, load().nll_server_cancel(self.handle, int(request_id)))
+
     def poll(self):
-        """Finished fits as a list of (id, result dict)."""
+        """Finished fits as a list of (id, result dict); empty when none has finished (no wait)."""
         n = ctypes.c_int()
         _scheck(self.handle, load().nll_server_poll(self.handle, self._ids, self._res, self.max_slots, ctypes.byref(n)))
         return [(self._ids[i], _result_dict(self._res[i], self.npar)) for i in range(n.value)]

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 
-CU_SOURCES = ["kernels.cu", "runtime.cu", "calibrate.cu", "batch.cu", "gen.cu", "hess.cu"]
+CU_SOURCES = ["kernels.cu", "runtime.cu", "calibrate.cu", "batch.cu", "server.cu", "gen.cu", "hess.cu"]
 CXX_SOURCES = ["minimise.cpp"]
 
 

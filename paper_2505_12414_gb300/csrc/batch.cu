@@ -31,79 +31,17 @@
 #include "../../include/gbnll.h"
 #include "fp64_math.cuh"
 #include "gbnll_internal.h"
+#include "batch_internal.h"
 #include "hess_device.cuh"
 #include "nll_device.cuh"
 
 namespace gbnll {
 namespace {
 
-constexpr int kNP = 18;                 // largest parameter count
-constexpr int kMaxSlots = 2 * kNP + 1;  // trial point + stencil points per toy and step
-constexpr int kEvalThreads = 128;
-constexpr int kUpdWarps = 4;
 const double kPiH = 3.14159265358979323846;
 
 __device__ double g_btab[kTabDoubles];
 
-enum Phase : int { kPhInit = 0, kPhSearch = 1, kPhHess = 2, kPhDone = 3 };
-
-// Derivative constants of one parameter point (device copy of the host Hoist fields).
-struct DConst {
-    double mu, sigma, alpha, f, ma, b0, b2, dlnN1_dmu, dlnN1_dsig, dlnN2t_dal, dlnNc[3];
-    double lnb1, d2lnN1[3], d2lnN2t_dal2;  // for the analytic Hessian
-    int ok;
-};
-
-// Minimiser state of one toy (device).
-struct ToyFit {
-    int phase, iter, n_eval, status, first;
-    int vset;  // the start matrix V came from the analytic Hessian (strategy 2)
-    // Newton polish with the analytic Hessian after the loop (hessian 2 / 3)
-    int pol;                  // > 0 while polishing
-    double lam, f_acc;        // step fraction; NLL at the accepted point
-    double th_acc[kNP];       // accepted point (all parameters)
-    double dN[kNP];           // Newton direction H^-1 g (free components, external)
-    double f, ft, edm, alpha, gp;
-    double x[kNP], g[kNP], p[kNP], xt[kNP], sint[kNP], hstep[kNP];
-    double th[kNP];    // external parameters of the accepted point (all npar)
-    double gext[kNP];  // external gradient (free components) at the accepted point
-    double V[kNP * kNP];
-    double gsten[2 * kNP][kNP];
-    double cov[kNP * kNP];
-    double err[kNP];
-    int item[kMaxSlots];
-};
-
-struct FitConfig {
-    int kind, npar, nf, strategy, hessian, max_iter;
-    double tol_edm;
-    double ranges[8];
-    int idx[kNP];
-    int bounded[kNP];
-    double lo[kNP], hi[kNP];
-};
-
-struct BatchDev {
-    int n_toys, tile_pairs;        // tile_pairs = 0: one unit per item
-    const int64_t* ev_begin;       // per toy, even
-    const int64_t* ev_end;         // per toy, exclusive
-    const double* sum_wdm;         // per toy: sum w (m - ma)
-    KArgs cols;                    // column pointers and weights
-    ToyFit* fits;
-    int* counters;                 // [0] items, [1] units, [2] next unit
-    int* n_active;                 // toys not yet done (mapped host memory)
-    int* done_flags;               // per toy, set to 1 when it finishes (mapped), or NULL
-    int* item_toy;
-    int* item_u0;
-    int* item_nt;
-    KConst* item_kc;
-    DConst* item_dc;
-    int* unit_item;
-    int* unit_tile;
-    double* unit_sums;             // [max_units][kAccMax]
-    int max_items, max_units;
-    FitConfig cfg;
-};
 
 // ---------------------------------------------------------------------------------
 // device-side parameter-only terms and gradient assembly (same formulas as runtime.cu)
@@ -719,9 +657,13 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
             done_status = NLL_OK;
         }
     }
+    __syncwarp();  // every lane's writes to F come before the flag below
     if (done_status >= 0 && lane == 0) {
         F.status = done_status;
         F.phase = kPhDone;
+        // a host thread that sees the done flag may collect this fit's state from another
+        // stream while later steps run: make the state visible first
+        __threadfence_system();
         atomicSub(b.n_active, 1);
         if (b.done_flags) b.done_flags[t] = 1;
     }
@@ -733,9 +675,6 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
 // single-sample Hessian pass (hess_device.cuh) over (toy, 1024-event) units; a warp per
 // toy then sums its units in order, assembles H (and W) and inverts.
 // ---------------------------------------------------------------------------------
-constexpr int kHessUnitEvents = 1024;  // 8 shared-memory tiles: several waves of units even for small toys
-
-enum HessMode : int { kHmEval = 0, kHmStart = 1, kHmCov = 2, kHmSandwich = 3 };
 
 struct HessDev {
     int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
@@ -1035,12 +974,12 @@ __global__ void __launch_bounds__(128) batch_init_fits(ToyFit* fits, int n, cons
 
 // Results of every toy packed for the host (block per toy), kResStride doubles each:
 // th[npar] | err[nf] | cov[nf x nf] (free parameters) | nll, edm, n_eval, n_iter, status.
-constexpr int kResStride = 2 * kNP + kNP * kNP + 5;
-__global__ void __launch_bounds__(128) batch_pack_results(const ToyFit* fits, int n, int np, int nf, double* res)
+__global__ void __launch_bounds__(128) batch_pack_results(const ToyFit* fits, const int* idx, int n, int np, int nf,
+                                                          double* res)
 {
     const int t = blockIdx.x;
     if (t >= n) return;
-    const ToyFit& F = fits[t];
+    const ToyFit& F = fits[idx ? idx[t] : t];
     double* r = res + (size_t)t * kResStride;
     for (int i = threadIdx.x; i < np; i += blockDim.x) r[i] = F.th[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) r[kNP + i] = F.err[i];
@@ -1292,6 +1231,8 @@ cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStr
     return cudaGetLastError();
 }
 
+}  // namespace
+
 template <int KIND, int VAR, bool W>
 cudaError_t launch_eval_t(int blocks, cudaStream_t s, const BatchDev& b)
 {
@@ -1309,8 +1250,10 @@ cudaError_t launch_eval(int kind, int var, bool w, int blocks, cudaStream_t s, c
              : launch_eval_t<kKstar4D, kVarPrecompute, false>(blocks, s, b);
 }
 
+namespace {
 std::mutex g_btab_mutex;
 bool g_btab_ready[64];
+}  // namespace
 
 cudaError_t ensure_btab(int device)
 {
@@ -1324,7 +1267,33 @@ cudaError_t ensure_btab(int device)
     return e;
 }
 
-}  // namespace
+// One device step of the batched fit loop on stream s (for graph capture): reset the work
+// counters, prepare (hoisting of every active toy's points), evaluate, update.
+cudaError_t launch_step(const BatchDev& d, int var, bool weighted, int eval_blocks, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d.counters, 0, sizeof(int) * 3, s);
+    if (e != cudaSuccess) return e;
+    batch_prepare<<<(d.n_toys + 127) / 128, 128, 0, s>>>(d);
+    e = launch_eval(d.cfg.kind, var, weighted, eval_blocks, s, d);
+    if (e != cudaSuccess) return e;
+    const int ub = (d.n_toys + kUpdWarps - 1) / kUpdWarps;
+    if (d.cfg.kind == kMass1D)
+        batch_update<kMass1D><<<ub, kUpdWarps * 32, 0, s>>>(d);
+    else
+        batch_update<kKstar4D><<<ub, kUpdWarps * 32, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+// Results of n toys packed for the host, kResStride doubles each (batch_pack_results): toys
+// idx[0..n) (device array), or 0 .. n-1 when idx is NULL.
+cudaError_t launch_pack_results(const ToyFit* fits, const int* idx, int n, int np, int nf, double* res,
+                                cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    batch_pack_results<<<n, 128, 0, s>>>(fits, idx, n, np, nf, res);
+    return cudaGetLastError();
+}
+
 }  // namespace gbnll
 
 using namespace gbnll;
@@ -1332,39 +1301,20 @@ using namespace gbnll;
 // ------------------------------------------------------------------------------------
 // host runtime
 // ------------------------------------------------------------------------------------
-namespace {
+namespace gbnll {
 
-// Work arrays of the analytic Hessian pass: units of kHessUnitEvents events of the selected
-// toys, per-toy constants and results, per-unit slot sums, the slot table, a selection mask
-// and the polish counter.
-struct HessWork {
-    bool ready = false;
-    int cap_toys = 0, cap_units = 0, np = 0, n_units = 0;
-    int layout_key = -1;  // slot table on the device: kind, weights, W
-    int* d_unit_toy = nullptr;
-    int64_t* d_unit_e0 = nullptr;
-    int* d_toy_u0 = nullptr;
-    int* d_toy_nu = nullptr;
-    HConst* d_hc = nullptr;
-    HessTerms* d_ht = nullptr;
-    int* d_hok = nullptr;
-    double* d_unit_sums = nullptr;
-    uint16_t* d_slot_of = nullptr;
-    double* d_thetas = nullptr;
-    double* d_out = nullptr;
-    int* d_status = nullptr;
-    int* d_sel = nullptr;
-    int* h_npol = nullptr;  // mapped: toys that proposed a polish step in the last pass
-    int* d_npol = nullptr;
-};
 
 void hw_free(HessWork& w)
 {
+    if (w.staged_pending) cudaEventSynchronize(w.staged_ev);
     void* ptrs[] = {w.d_unit_toy, w.d_unit_e0, w.d_toy_u0, w.d_toy_nu, w.d_hc, w.d_ht, w.d_hok, w.d_unit_sums,
                     w.d_slot_of, w.d_thetas, w.d_out, w.d_status, w.d_sel};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (w.h_npol) cudaFreeHost(w.h_npol);
+    void* hptrs[] = {w.h_npol, w.h_unit_toy, w.h_unit_e0, w.h_toy_u0, w.h_toy_nu, w.h_sel};
+    for (void* p : hptrs)
+        if (p) cudaFreeHost(p);
+    if (w.staged_ev) cudaEventDestroy(w.staged_ev);
     w = HessWork();
 }
 
@@ -1387,6 +1337,13 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
     if (e == cudaSuccess) e = cudaMalloc(&w.d_sel, sizeof(int) * nt);
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_npol, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&w.d_npol, w.h_npol, 0);
+    // pinned staging of the unit lists, so that they can be copied without the host waiting
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_unit_toy, sizeof(int) * nu, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_unit_e0, sizeof(int64_t) * nu, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_toy_u0, sizeof(int) * nt, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_toy_nu, sizeof(int) * nt, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&w.h_sel, sizeof(int) * nt, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.staged_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         hw_free(w);
         return e;
@@ -1399,56 +1356,57 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
 }
 
 // Unit lists for toys t with events [begin[t], end[t]) (host positions); toys with sel[t] == 0
-// get no units (sel empty: every toy).  Fails if the units exceed the capacity.
+// get no units (sel empty: every toy).  Fails if the units exceed the capacity.  The lists go
+// through pinned staging; with wait the call returns once they are on the device, without it
+// as soon as the copies are queued (the staging is reused only after they have completed).
 cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const std::vector<int64_t>& end,
-                         const std::vector<int>& sel, cudaStream_t stream)
+                         const std::vector<int>& sel, cudaStream_t stream, bool wait)
 {
     const int n = (int)begin.size();
-    std::vector<int> unit_toy, toy_u0(std::max(n, 1), 0), toy_nu(std::max(n, 1), 0);
-    std::vector<int64_t> unit_e0;
-    for (int t = 0; t < n; ++t) {
-        toy_u0[t] = (int)unit_toy.size();
-        if (!sel.empty() && !sel[t]) continue;
-        for (int64_t e = begin[t]; e < end[t]; e += kHessUnitEvents) {
-            unit_toy.push_back(t);
-            unit_e0.push_back(e);
-        }
-        toy_nu[t] = (int)unit_toy.size() - toy_u0[t];
-    }
-    if ((int)unit_toy.size() > w.cap_units || n > w.cap_toys) return cudaErrorInvalidValue;
+    if (n > w.cap_toys) return cudaErrorInvalidValue;
+    int64_t nu = 0;
+    for (int t = 0; t < n; ++t)
+        if (sel.empty() || sel[t]) nu += (std::max<int64_t>(end[t] - begin[t], 0) + kHessUnitEvents - 1) / kHessUnitEvents;
+    if (nu > w.cap_units) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
-    if (!unit_toy.empty())
-        e = cudaMemcpyAsync(w.d_unit_toy, unit_toy.data(), sizeof(int) * unit_toy.size(), cudaMemcpyHostToDevice,
-                            stream);
-    if (e == cudaSuccess && !unit_e0.empty())
-        e = cudaMemcpyAsync(w.d_unit_e0, unit_e0.data(), sizeof(int64_t) * unit_e0.size(), cudaMemcpyHostToDevice,
-                            stream);
+    if (w.staged_pending) {  // the previous lists may still be in flight from the staging
+        e = cudaEventSynchronize(w.staged_ev);
+        if (e != cudaSuccess) return e;
+        w.staged_pending = false;
+    }
+    int u = 0;
+    for (int t = 0; t < n; ++t) {
+        w.h_toy_u0[t] = u;
+        w.h_toy_nu[t] = 0;
+        if (!sel.empty() && !sel[t]) continue;
+        for (int64_t ev = begin[t]; ev < end[t]; ev += kHessUnitEvents) {
+            w.h_unit_toy[u] = t;
+            w.h_unit_e0[u] = ev;
+            ++u;
+        }
+        w.h_toy_nu[t] = u - w.h_toy_u0[t];
+    }
+    if (!sel.empty())
+        for (int t = 0; t < n; ++t) w.h_sel[t] = sel[t];
+    if (u > 0) e = cudaMemcpyAsync(w.d_unit_toy, w.h_unit_toy, sizeof(int) * u, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && u > 0)
+        e = cudaMemcpyAsync(w.d_unit_e0, w.h_unit_e0, sizeof(int64_t) * u, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && n)
-        e = cudaMemcpyAsync(w.d_toy_u0, toy_u0.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+        e = cudaMemcpyAsync(w.d_toy_u0, w.h_toy_u0, sizeof(int) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && n)
-        e = cudaMemcpyAsync(w.d_toy_nu, toy_nu.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+        e = cudaMemcpyAsync(w.d_toy_nu, w.h_toy_nu, sizeof(int) * n, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess && !sel.empty())
-        e = cudaMemcpyAsync(w.d_sel, sel.data(), sizeof(int) * n, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);  // the host vectors go out of scope
-    if (e == cudaSuccess) w.n_units = (int)unit_toy.size();
+        e = cudaMemcpyAsync(w.d_sel, w.h_sel, sizeof(int) * n, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(w.staged_ev, stream);
+    if (e == cudaSuccess) w.staged_pending = true;
+    if (e == cudaSuccess && wait) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) w.n_units = u;
     return e;
 }
 
-// The sample and fit states a Hessian pass works on.
-struct HessTarget {
-    int kind, variant, sm_count, n_toys;
-    bool weighted;
-    HEv ev;
-    const int64_t* d_begin;
-    const int64_t* d_end;
-    const double* d_sum_wdm;
-    ToyFit* d_fits;
-    cudaStream_t stream;
-};
-
 // One Hessian pass (see HessDev); use_sel restricts it to the toys hw_set_units selected.
 cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int mode, bool want_w2,
-                          const double* thetas, int pass, bool use_sel)
+                          const double* thetas, int pass, bool use_sel, bool wait)
 {
     HessLayout L;
     if (!hess_layout(T.kind, T.weighted, want_w2, &L)) return cudaErrorInvalidValue;
@@ -1502,7 +1460,7 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
     const int occ = hess_occupancy(T.kind, T.variant, T.weighted);
     const int unit_blocks = std::max(1, std::min(w.n_units, T.sm_count * std::max(1, std::min(occ, 4))));
     e = launch_hess_pass(T.kind, T.variant, T.weighted, unit_blocks, T.stream, h);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(T.stream);
+    if (e == cudaSuccess && wait) e = cudaStreamSynchronize(T.stream);
     return e;
 }
 
@@ -1527,7 +1485,7 @@ cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, 
     return e;
 }
 
-}  // namespace
+}  // namespace gbnll
 
 struct nll_batch {
     int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
@@ -1876,6 +1834,10 @@ cudaError_t finish_store(nll_batch* b, bool basis, int64_t pos, bool device_sums
     return e;
 }
 
+}  // namespace
+
+namespace gbnll {
+
 // minimiser settings shared by all toys
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
                   const fit_options& opt)
@@ -1941,7 +1903,7 @@ void fill_result_packed(const double* p, const FitConfig& c, fit_result& r)
     r.status = (int)tail[4];
 }
 
-}  // namespace
+}  // namespace gbnll
 
 extern "C" {
 
@@ -2313,7 +2275,7 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         e = polish_core(target_of(b), b->hw, c, opt.hessian, false);
         if (e != cudaSuccess) return bcuda(b, e, "Newton polish");
     }
-    batch_pack_results<<<n, 128, 0, b->stream>>>(b->d_fits, n, np, nf, b->d_res);
+    batch_pack_results<<<n, 128, 0, b->stream>>>(b->d_fits, nullptr, n, np, nf, b->d_res);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit results");
@@ -2360,511 +2322,6 @@ int nll_batch_eval_hess(nll_batch* b, const double* thetas, int shared, double* 
         if (sts[t] != NLL_OK && first_bad == NLL_OK) first_bad = sts[t];
     }
     return first_bad;
-}
-
-}  // extern "C"
-
-// ------------------------------------------------------------------------------------
-// serving: continuous batching of fits into fixed slots over a device event pool
-// ------------------------------------------------------------------------------------
-struct nll_server {
-    int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
-    cudaStream_t stream = nullptr;
-    double ranges[8] = {0};
-    int max_slots = 0;
-    int64_t pool_events = 0, n_pad = 0;
-    int ncols = 0, tile_events = 4096;
-    double* d_ev = nullptr;
-    std::vector<std::pair<int64_t, int64_t>> free_ranges;  // [begin, end) in pool events, sorted
-    std::vector<char> busy;
-    std::vector<int64_t> slot_id, slot_begin, slot_len, slot_nev;
-    std::vector<int> need_start;  // strategy 2: admitted slots whose start matrix is still due
-    int64_t next_id = 1;
-    FitConfig cfg;
-    int hessian = 0;  // fit_options.hessian: 2 / 3 polish finished slots with the analytic Hessian
-    HessWork hw;      // analytic Hessian passes (strategy 2, hessian 2 / 3)
-    // admission statistics on the device (range check, sum (m - ma)) of a request's events
-    double* d_spart = nullptr;
-    unsigned int* d_sticket = nullptr;
-    double* h_sout = nullptr;  // mapped [3]
-    double* d_sout = nullptr;
-    std::vector<double> step;
-    // device work arrays
-    int64_t* d_begin = nullptr;
-    int64_t* d_end = nullptr;
-    double* d_sum_wdm = nullptr;
-    ToyFit* d_fits = nullptr;
-    int* d_counters = nullptr;
-    int* h_active = nullptr;
-    int* d_active = nullptr;
-    int* h_done = nullptr;
-    int* d_done = nullptr;
-    int* d_item_toy = nullptr;
-    int* d_item_u0 = nullptr;
-    int* d_item_nt = nullptr;
-    KConst* d_item_kc = nullptr;
-    DConst* d_item_dc = nullptr;
-    int* d_unit_item = nullptr;
-    int* d_unit_tile = nullptr;
-    double* d_unit_sums = nullptr;
-    int max_items = 0, max_units = 0;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    std::string err;
-};
-
-namespace {
-
-int sfail(nll_server* s, int status, const char* fmt, ...)
-{
-    if (s) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        s->err = buf;
-    }
-    return status;
-}
-
-void server_free(nll_server* s)
-{
-    if (s->exec) cudaGraphExecDestroy(s->exec);
-    if (s->graph) cudaGraphDestroy(s->graph);
-    void* ptrs[] = {s->d_ev, s->d_begin, s->d_end, s->d_sum_wdm, s->d_fits, s->d_counters, s->d_item_toy,
-                    s->d_item_u0, s->d_item_nt, s->d_item_kc, s->d_item_dc, s->d_unit_item, s->d_unit_tile,
-                    s->d_unit_sums};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
-    if (s->h_active) cudaFreeHost(s->h_active);
-    if (s->h_done) cudaFreeHost(s->h_done);
-    if (s->d_spart) cudaFree(s->d_spart);
-    if (s->d_sticket) cudaFree(s->d_sticket);
-    if (s->h_sout) cudaFreeHost(s->h_sout);
-    hw_free(s->hw);
-    if (s->stream) cudaStreamDestroy(s->stream);
-}
-
-// first-fit allocation of `len` (even) pool events starting on an even event
-bool pool_alloc(nll_server* s, int64_t len, int64_t* begin)
-{
-    for (size_t i = 0; i < s->free_ranges.size(); ++i) {
-        auto& r = s->free_ranges[i];
-        if (r.second - r.first >= len) {
-            *begin = r.first;
-            r.first += len;
-            if (r.first == r.second) s->free_ranges.erase(s->free_ranges.begin() + i);
-            return true;
-        }
-    }
-    return false;
-}
-
-void pool_release(nll_server* s, int64_t begin, int64_t len)
-{
-    auto& fr = s->free_ranges;
-    auto it = std::lower_bound(fr.begin(), fr.end(), std::make_pair(begin, begin + len));
-    it = fr.insert(it, {begin, begin + len});
-    // merge with neighbours
-    size_t i = it - fr.begin();
-    if (i + 1 < fr.size() && fr[i].second == fr[i + 1].first) {
-        fr[i].second = fr[i + 1].second;
-        fr.erase(fr.begin() + i + 1);
-    }
-    if (i > 0 && fr[i - 1].second == fr[i].first) {
-        fr[i - 1].second = fr[i].second;
-        fr.erase(fr.begin() + i);
-    }
-}
-
-BatchDev server_dev(nll_server* s)
-{
-    BatchDev d;
-    memset(&d, 0, sizeof d);
-    d.n_toys = s->max_slots;
-    d.tile_pairs = s->tile_events / 2;
-    d.ev_begin = s->d_begin;
-    d.ev_end = s->d_end;
-    d.sum_wdm = s->d_sum_wdm;
-    for (int c = 0; c < kNumCols; ++c) d.cols.col[c] = c < s->ncols ? s->d_ev + (size_t)c * s->n_pad : nullptr;
-    d.cols.w = nullptr;
-    d.fits = s->d_fits;
-    d.counters = s->d_counters;
-    d.n_active = s->d_active;
-    d.done_flags = s->d_done;
-    d.item_toy = s->d_item_toy;
-    d.item_u0 = s->d_item_u0;
-    d.item_nt = s->d_item_nt;
-    d.item_kc = s->d_item_kc;
-    d.item_dc = s->d_item_dc;
-    d.unit_item = s->d_unit_item;
-    d.unit_tile = s->d_unit_tile;
-    d.unit_sums = s->d_unit_sums;
-    d.max_items = s->max_items;
-    d.max_units = s->max_units;
-    d.cfg = s->cfg;
-    return d;
-}
-
-HessTarget server_target(nll_server* s)
-{
-    HessTarget T;
-    memset(&T, 0, sizeof T);
-    T.kind = s->kind;
-    T.variant = kVarPrecompute;  // the server builds the angular basis at admission
-    T.sm_count = s->sm_count;
-    T.n_toys = s->max_slots;
-    T.weighted = false;
-    for (int c = 0; c < kNumCols; ++c) T.ev.col[c] = c < s->ncols ? s->d_ev + (size_t)c * s->n_pad : nullptr;
-    T.d_begin = s->d_begin;
-    T.d_end = s->d_end;
-    T.d_sum_wdm = s->d_sum_wdm;
-    T.d_fits = s->d_fits;
-    T.stream = s->stream;
-    return T;
-}
-
-// unit lists of the Hessian pass for the slots with pick[i] != 0
-cudaError_t server_pick(nll_server* s, const std::vector<int>& pick)
-{
-    std::vector<int64_t> begin(s->max_slots), end(s->max_slots);
-    for (int i = 0; i < s->max_slots; ++i) {
-        begin[i] = s->slot_begin[i];
-        end[i] = s->slot_begin[i] + (pick[i] ? s->slot_nev[i] : 0);
-    }
-    return hw_set_units(s->hw, begin, end, pick, s->stream);
-}
-
-}  // namespace
-
-extern "C" {
-
-int nll_server_create(int kind, const double* obs_ranges, int device, int max_slots, int64_t pool_events,
-                      int tile_events, const double* lo, const double* hi, const double* step, const int* fixed,
-                      const fit_options* opt_in, nll_server** out)
-{
-    if (!out) return NLL_ERR_ARG;
-    *out = nullptr;
-    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 2 || opt_in->hessian < 0 || opt_in->hessian > 3))
-        return NLL_ERR_ARG;
-    if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges || max_slots < 1 ||
-        pool_events < 1 || tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
-        return NLL_ERR_ARG;
-    if (!(isfinite(obs_ranges[0]) && isfinite(obs_ranges[1]) && obs_ranges[0] < obs_ranges[1])) return NLL_ERR_ARG;
-    if (kind == NLL_MODEL_KSTARMUMU4D) {
-        const double want[6] = {-1.0, 1.0, -1.0, 1.0, -kPiH, kPiH};
-        for (int i = 0; i < 6; ++i)
-            if (fabs(obs_ranges[2 + i] - want[i]) > 1e-12) return NLL_ERR_ARG;
-    }
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
-    if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
-    nll_server* s = new nll_server();
-    s->kind = kind;
-    s->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
-    s->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
-    s->device = device;
-    s->max_slots = max_slots;
-    s->tile_events = tile_events ? tile_events : 4096;
-    memcpy(s->ranges, obs_ranges, sizeof(double) * 2 * s->ndim);
-    if (kind == NLL_MODEL_KSTARMUMU4D) {
-        s->ranges[6] = -kPiH;
-        s->ranges[7] = kPiH;
-    }
-    cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, device);
-    fit_options opt;
-    if (opt_in)
-        opt = *opt_in;
-    else
-        memset(&opt, 0, sizeof opt);
-    if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
-    if (opt.max_iter <= 0) opt.max_iter = 500;
-    memset(&s->cfg, 0, sizeof s->cfg);
-    s->cfg.kind = kind;
-    s->cfg.npar = s->npar;
-    for (int i = 0; i < 8; ++i) s->cfg.ranges[i] = s->ranges[i];
-    setup_config(s->cfg, s->npar, lo, hi, step, fixed, opt);
-    s->hessian = opt.hessian;
-    s->step.assign(s->npar, 0.0);
-    for (int k = 0; k < s->npar; ++k) s->step[k] = step ? step[k] : 0.0;
-    // pool: padded so a range of even length starting on an even event can end anywhere
-    s->pool_events = (pool_events + 1) & ~int64_t(1);
-    s->n_pad = std::max<int64_t>((s->pool_events + 63) / 64 * 64, 64);
-    s->ncols = kind == kMass1D ? 1 : kNumCols;
-    s->free_ranges.push_back({0, s->pool_events});
-    s->busy.assign(max_slots, 0);
-    s->slot_id.assign(max_slots, 0);
-    s->slot_begin.assign(max_slots, 0);
-    s->slot_len.assign(max_slots, 0);
-    s->slot_nev.assign(max_slots, 0);
-    s->need_start.assign(max_slots, 0);
-    const int64_t tp = s->tile_events / 2;
-    s->max_items = max_slots * (2 * s->npar + 1);
-    int64_t mu = (s->pool_events / 2 / tp + max_slots + 1) * (2 * (int64_t)s->npar + 1);
-    if (mu > (1ll << 30)) {
-        delete s;
-        return NLL_ERR_ARG;
-    }
-    s->max_units = (int)mu;
-    cudaError_t e = ensure_btab(device);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess && (s->cfg.strategy == 2 || s->hessian >= 2)) {
-        // every slot's units fit: the pool holds at most pool_events events
-        const int64_t cap = s->pool_events / kHessUnitEvents + max_slots + 1;
-        e = cap > (1 << 28) ? cudaErrorInvalidValue : hw_alloc(s->hw, max_slots, (int)cap, s->npar);
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_spart, sizeof(double) * 3 * 2 * s->sm_count);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_sticket, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(s->d_sticket, 0, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_sout, sizeof(double) * 3, cudaHostAllocMapped);
-    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_sout, s->h_sout, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_ev, sizeof(double) * s->n_pad * s->ncols);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ev, 0, sizeof(double) * s->n_pad * s->ncols, s->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_begin, sizeof(int64_t) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_end, sizeof(int64_t) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_sum_wdm, sizeof(double) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_fits, sizeof(ToyFit) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, sizeof(int) * 4);
-    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_active, sizeof(int), cudaHostAllocMapped);
-    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_active, s->h_active, 0);
-    if (e == cudaSuccess) e = cudaHostAlloc(&s->h_done, sizeof(int) * max_slots, cudaHostAllocMapped);
-    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_done, s->h_done, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_toy, sizeof(int) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_u0, sizeof(int) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_nt, sizeof(int) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_kc, sizeof(KConst) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_dc, sizeof(DConst) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_item, sizeof(int) * s->max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_tile, sizeof(int) * s->max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_sums, sizeof(double) * kAccMax * s->max_units);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_toy, 0, sizeof(int) * s->max_items, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_u0, 0, sizeof(int) * s->max_items, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_nt, 0, sizeof(int) * s->max_items, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_unit_item, 0, sizeof(int) * s->max_units, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_unit_tile, 0, sizeof(int) * s->max_units, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_begin, 0, sizeof(int64_t) * max_slots, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_end, 0, sizeof(int64_t) * max_slots, s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_sum_wdm, 0, sizeof(double) * max_slots, s->stream);
-    if (e == cudaSuccess) {
-        // every slot starts finished (empty); the prepare kernel skips finished slots
-        std::vector<ToyFit> idle(max_slots);
-        for (auto& F : idle) {
-            memset(&F, 0, sizeof F);
-            F.phase = kPhDone;
-            for (int q = 0; q < kMaxSlots; ++q) F.item[q] = -1;
-        }
-        e = cudaMemcpyAsync(s->d_fits, idle.data(), sizeof(ToyFit) * max_slots, cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    }
-    if (e == cudaSuccess) {
-        memset(s->h_done, 0, sizeof(int) * max_slots);
-        *s->h_active = 0;
-        BatchDev d = server_dev(s);
-        const int eval_blocks = s->sm_count * 2;
-        e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaMemsetAsync(s->d_counters, 0, sizeof(int) * 3, s->stream);
-            batch_prepare<<<(max_slots + 127) / 128, 128, 0, s->stream>>>(d);
-            launch_eval(kind, kVarPrecompute, false, eval_blocks, s->stream, d);
-            if (kind == kMass1D)
-                batch_update<kMass1D><<<(max_slots + kUpdWarps - 1) / kUpdWarps, kUpdWarps * 32, 0, s->stream>>>(d);
-            else
-                batch_update<kKstar4D><<<(max_slots + kUpdWarps - 1) / kUpdWarps, kUpdWarps * 32, 0, s->stream>>>(d);
-            e = cudaStreamEndCapture(s->stream, &s->graph);
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->exec, s->graph, 0);
-    }
-    if (e != cudaSuccess) {
-        server_free(s);
-        delete s;
-        return e == cudaErrorMemoryAllocation ? NLL_ERR_OOM : NLL_ERR_CUDA;
-    }
-    *out = s;
-    return NLL_OK;
-}
-
-void nll_server_destroy(nll_server* s)
-{
-    if (!s) return;
-    cudaSetDevice(s->device);
-    if (s->stream) cudaStreamSynchronize(s->stream);
-    server_free(s);
-    delete s;
-}
-
-const char* nll_server_last_error(const nll_server* s) { return s ? s->err.c_str() : "null server"; }
-
-int nll_server_status(const nll_server* s, int* busy, int* free_slots, int64_t* free_events)
-{
-    if (!s) return NLL_ERR_ARG;
-    int nb = 0;
-    for (char c : s->busy) nb += c ? 1 : 0;
-    int64_t fe = 0;
-    for (auto& r : s->free_ranges) fe += r.second - r.first;
-    if (busy) *busy = nb;
-    if (free_slots) *free_slots = s->max_slots - nb;
-    if (free_events) *free_events = fe;
-    return NLL_OK;
-}
-
-int nll_server_sync(nll_server* s)
-{
-    if (!s) return NLL_ERR_ARG;
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    return e == cudaSuccess ? NLL_OK : sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
-}
-
-int nll_server_step(nll_server* s, int n_steps)
-{
-    if (!s || n_steps < 0) return NLL_ERR_ARG;
-    if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
-    bool starts = false;
-    for (int i = 0; i < s->max_slots; ++i) starts = starts || (s->busy[i] && s->need_start[i]);
-    if (starts && n_steps > 0) {  // start matrices of the requests admitted since the last step
-        std::vector<int> pick(s->max_slots, 0);
-        for (int i = 0; i < s->max_slots; ++i) pick[i] = s->busy[i] && s->need_start[i];
-        cudaError_t e = cudaStreamSynchronize(s->stream);
-        if (e == cudaSuccess) e = server_pick(s, pick);
-        if (e == cudaSuccess) e = run_hess_core(server_target(s), s->hw, s->cfg, kHmStart, false, nullptr, 0, true);
-        if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "start Hessians: %s", cudaGetErrorString(e));
-        for (int i = 0; i < s->max_slots; ++i)
-            if (pick[i]) s->need_start[i] = 0;
-    }
-    for (int i = 0; i < n_steps; ++i) {
-        cudaError_t e = cudaGraphLaunch(s->exec, s->stream);
-        if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server step: %s", cudaGetErrorString(e));
-    }
-    return NLL_OK;
-}
-
-int nll_server_submit(nll_server* s, const double* const* columns, const double* weights, int64_t n_events,
-                      const double* theta0, int64_t* request_id)
-{
-    if (!s || !theta0 || !request_id || n_events < 0) return NLL_ERR_ARG;
-    if (weights) return sfail(s, NLL_ERR_ARG, "a server serves unweighted fits");
-    if (n_events > 0 && !columns) return sfail(s, NLL_ERR_ARG, "null columns");
-    for (int d = 0; d < s->ndim && n_events > 0; ++d)
-        if (!columns[d]) return sfail(s, NLL_ERR_ARG, "column %d is NULL", d);
-    for (int k = 0; k < s->npar; ++k)
-        if (!isfinite(theta0[k])) return sfail(s, NLL_ERR_ARG, "start point not finite");
-    const int64_t len = std::max<int64_t>((n_events + 1) & ~int64_t(1), 2);
-    if (len > s->pool_events) return sfail(s, NLL_ERR_ARG, "more events than the whole pool");
-    if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
-    cudaError_t e = cudaStreamSynchronize(s->stream);  // no step may run while a slot is rewritten
-    if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
-    int slot = -1;
-    for (int i = 0; i < s->max_slots; ++i)
-        if (!s->busy[i]) {
-            slot = i;
-            break;
-        }
-    int64_t begin = 0;
-    if (slot < 0 || !pool_alloc(s, len, &begin)) return sfail(s, NLL_ERR_STATE, "no free slot or pool range");
-    // events into the pool range (and the angular basis for the 4D model)
-    for (int d = 0; d < s->ndim && e == cudaSuccess && n_events > 0; ++d)
-        e = cudaMemcpyAsync(s->d_ev + (size_t)d * s->n_pad + begin, columns[d], sizeof(double) * n_events,
-                            cudaMemcpyHostToDevice, s->stream);
-    // range check and sum (m - ma) of the request on the device (load-time statistics kernel)
-    double sum = 0.0;
-    if (e == cudaSuccess && n_events > 0) {
-        SArgs sa;
-        memset(&sa, 0, sizeof sa);
-        for (int d = 0; d < s->ndim; ++d) {
-            sa.col[d] = s->d_ev + (size_t)d * s->n_pad + begin;
-            sa.lo[d] = s->ranges[2 * d];
-            sa.hi[d] = s->ranges[2 * d + 1];
-        }
-        sa.w = nullptr;
-        sa.n = n_events;
-        sa.ndim = s->ndim;
-        sa.partials = s->d_spart;
-        sa.ticket = s->d_sticket;
-        sa.out = s->d_sout;
-        const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n_events + 255) / 256, 1), 2 * s->sm_count);
-        e = launch_stats(blocks, 256, s->stream, sa);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e == cudaSuccess) {
-            if (((volatile double*)s->h_sout)[2] != 0.0) {
-                pool_release(s, begin, len);
-                return sfail(s, NLL_ERR_ARG, "%.0f event(s) outside the observable ranges",
-                             ((volatile double*)s->h_sout)[2]);
-            }
-            sum = ((volatile double*)s->h_sout)[1];
-        }
-    }
-    if (e == cudaSuccess && s->kind == kKstar4D && n_events > 0) {
-        BArgs ba;
-        ba.ctl = s->d_ev + (size_t)kColCtl * s->n_pad + begin;
-        ba.ctk = s->d_ev + (size_t)kColCtk * s->n_pad + begin;
-        ba.phi = s->d_ev + (size_t)kColPhi * s->n_pad + begin;
-        for (int j = 0; j < 13; ++j) ba.out[j] = s->d_ev + (size_t)(kColH0 + j) * s->n_pad + begin;
-        ba.n = n_events;
-        int blocks = (int)std::min<int64_t>((n_events + 255) / 256, (int64_t)s->sm_count * 8);
-        e = launch_basis(std::max(blocks, 1), 256, s->stream, ba);
-    }
-    ToyFit F;
-    init_fit(F, s->cfg, theta0, s->step.data());
-    const int64_t end = begin + n_events;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_fits + slot, &F, sizeof F, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_begin + slot, &begin, sizeof begin, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_end + slot, &end, sizeof end, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_sum_wdm + slot, &sum, sizeof sum, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) {
-        pool_release(s, begin, len);
-        return sfail(s, NLL_ERR_CUDA, "admission: %s", cudaGetErrorString(e));
-    }
-    s->slot_begin[slot] = begin;
-    s->slot_len[slot] = len;
-    s->slot_nev[slot] = n_events;
-    // strategy 2: the start matrix comes from one analytic Hessian pass over every request
-    // admitted since the last step, run by the next nll_server_step before its first graph step
-    s->need_start[slot] = s->cfg.strategy == 2 ? 1 : 0;
-    s->h_done[slot] = 0;
-    __atomic_add_fetch(s->h_active, 1, __ATOMIC_SEQ_CST);
-    s->busy[slot] = 1;
-    s->slot_id[slot] = s->next_id;
-    *request_id = s->next_id++;
-    return NLL_OK;
-}
-
-int nll_server_poll(nll_server* s, int64_t* ids_out, fit_result* results, int max_results, int* n_out)
-{
-    if (!s || !n_out || max_results < 0 || (max_results > 0 && (!ids_out || !results))) return NLL_ERR_ARG;
-    *n_out = 0;
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "server sync: %s", cudaGetErrorString(e));
-    if (s->hessian >= 2) {  // Newton polish and covariance with the analytic Hessian, finished slots
-        std::vector<int> pick(s->max_slots, 0);
-        int np = 0;
-        for (int i = 0; i < s->max_slots && np < max_results; ++i)
-            if (s->busy[i] && ((volatile int*)s->h_done)[i]) {
-                pick[i] = 1;
-                ++np;
-            }
-        if (np) {
-            e = server_pick(s, pick);
-            if (e == cudaSuccess) e = polish_core(server_target(s), s->hw, s->cfg, s->hessian, true);
-            if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "Newton polish: %s", cudaGetErrorString(e));
-        }
-    }
-    int n = 0;
-    for (int i = 0; i < s->max_slots && n < max_results; ++i) {
-        if (!s->busy[i] || !((volatile int*)s->h_done)[i]) continue;
-        ToyFit F;
-        e = cudaMemcpyAsync(&F, s->d_fits + i, sizeof F, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "result copy: %s", cudaGetErrorString(e));
-        fill_result(F, s->cfg, results[n]);
-        ids_out[n] = s->slot_id[i];
-        ++n;
-        s->busy[i] = 0;
-        s->h_done[i] = 0;
-        pool_release(s, s->slot_begin[i], s->slot_len[i]);
-    }
-    *n_out = n;
-    return NLL_OK;
 }
 
 }  // extern "C"

@@ -1,10 +1,12 @@
 """Request loop for serving fits with continuous batching.
 
 Requests (model kind, events, start point, arrival time) are admitted into the servers of
-their model kind as slots and pool memory free up; every loop iteration queues a few device
-steps on each busy server (servers run on their own CUDA streams, so their steps overlap on
-the device), then collects finished fits.  The loop only schedules: all fitting runs in the
-library (nll_server_*).
+their model kind as slots and pool memory free up.  The loop keeps a couple of device steps
+queued on every server with fits in it (servers run on their own CUDA streams, so their steps
+overlap on the device) and collects finished fits as soon as their done flags are up, so the
+device does not wait for the host between steps and admissions and collections overlap the
+steps of the other fits.  The loop only schedules: all fitting runs in the library
+(nll_server_*).
 """
 import collections
 import time
@@ -26,12 +28,19 @@ class Request:
         self.result = None
 
 
-def serve(servers, requests, steps_per_iter=2, realtime=True):
+def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phases=None):
     """Run `requests` (sorted by arrival, seconds from start) through `servers` {kind: Server}.
 
     With realtime=True requests become visible at their arrival times on the wall clock;
-    otherwise all are queued at once.  Returns the requests with admitted/done times and
-    results filled in."""
+    otherwise all are queued at once.  Every server with fits in it gets `steps_per_iter` more
+    steps whenever fewer than `max_queued` of its steps are still in flight.  If `phases` is a
+    dict, the host time spent in admission (submit), step queueing (step), progress queries
+    and collection (poll) is added to it, in seconds, with the number of steps queued.
+    Returns the requests with admitted/done times and results filled in."""
+    clock = time.perf_counter
+    acc = phases if phases is not None else {}
+    for key in ("admit_s", "step_s", "progress_s", "collect_s", "steps"):
+        acc.setdefault(key, 0.0)
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     queues = {k: collections.deque() for k in servers}
     inflight = {k: {} for k in servers}
@@ -45,21 +54,36 @@ def serve(servers, requests, steps_per_iter=2, realtime=True):
         for k, srv in servers.items():
             q = queues[k]
             while q:
+                c0 = clock()
                 rid = srv.submit(q[0].columns, q[0].theta0)
+                acc["admit_s"] += clock() - c0
                 if rid is None:
                     break
                 r = q.popleft()
                 r.admitted = time.perf_counter() - t0
                 inflight[k][rid] = r
-        busy = [k for k in servers if inflight[k]]
-        for k in busy:
-            servers[k].step(steps_per_iter)
-        for k in busy:
-            for rid, res in servers[k].poll():
-                r = inflight[k].pop(rid)
-                r.done = time.perf_counter() - t0
-                r.result = res
-                left -= 1
+        busy = False
+        for k, srv in servers.items():
+            if not inflight[k]:
+                continue
+            busy = True
+            c0 = clock()
+            queued, finished = srv.progress()
+            c1 = clock()
+            acc["progress_s"] += c1 - c0
+            if queued < max_queued:
+                srv.step(steps_per_iter)
+                acc["steps"] += steps_per_iter
+            c2 = clock()
+            acc["step_s"] += c2 - c1
+            if finished:
+                done = srv.poll()
+                acc["collect_s"] += clock() - c2
+                for rid, res in done:
+                    r = inflight[k].pop(rid)
+                    r.done = time.perf_counter() - t0
+                    r.result = res
+                    left -= 1
         if not busy and pending and realtime:
             time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
     return requests

@@ -70,6 +70,7 @@ def test_admission_by_pool_budget(gpu_lib):
     done = []
     for _ in range(500):
         s.step(4)
+        s.sync()  # poll does not wait for the steps in flight
         done += s.poll()
         if done:
             break
@@ -148,4 +149,65 @@ def test_admission_rejects_events_outside_the_ranges(gpu_lib):
     assert st["busy"] == 0 and st["free_events"] == 6000
     cols[2][1234] = 0.2
     assert s.submit(cols, synth.TRUTH_4D) is not None
+    s.close()
+
+
+def test_progress_and_non_blocking_poll(gpu_lib):
+    s = gpu_lib.Server(M1, synth.RANGES_1D, 4, 20000, 1024, **opts(M1))
+    assert s.progress() == (0, 0) and s.poll() == []
+    rid = s.submit(synth.mass1d(5000, stream=31), synth.TRUTH_1D)
+    s.step(3)
+    queued, finished = s.progress()
+    assert 0 <= queued <= 3 and finished in (0, 1)
+    done = []
+    for _ in range(400):
+        queued, finished = s.progress()
+        if finished:
+            done += s.poll()
+            break
+        if queued < 2:
+            s.step(2)
+    assert [d[0] for d in done] == [rid] and done[0][1]["status"] == 0
+    assert s.progress()[1] == 0
+    s.sync()
+    assert s.progress() == (0, 0)
+    s.close()
+
+
+def test_cancel_frees_the_slot_and_the_pool_range(gpu_lib):
+    s = gpu_lib.Server(M4, synth.RANGES_4D, 2, 12000, 1024, **opts(M4))
+    c1, c2, c3 = (synth.kstar4d(5000, stream=k) for k in (41, 42, 43))
+    r1 = s.submit(c1, synth.TRUTH_4D)
+    r2 = s.submit(c2, synth.TRUTH_4D)
+    assert s.submit(c3, synth.TRUTH_4D) is None  # both slots busy
+    s.step(2)
+    s.cancel(r1)  # withdrawn while its steps run
+    st = s.status()
+    assert st["busy"] == 1 and st["free_slots"] == 1 and st["free_events"] == 12000 - 5000
+    with pytest.raises(gpu_lib.NLLError) as e:
+        s.cancel(r1)
+    assert e.value.status == gpu_lib.NLL_ERR_ARG
+    r3 = s.submit(c3, synth.TRUTH_4D)  # the freed slot and range take the next request
+    assert r3 is not None
+    got = {}
+    for _ in range(2000):
+        s.step(2)
+        s.sync()
+        for rid, res in s.poll():
+            got[rid] = res
+        if len(got) == 2:
+            break
+    assert set(got) == {r2, r3} and all(v["status"] == 0 for v in got.values())
+    # the fit admitted into the cancelled fit's slot gives what it gives alone
+    alone = gpu_lib.Server(M4, synth.RANGES_4D, 1, 6000, 1024, **opts(M4))
+    ra = alone.submit(c3, synth.TRUTH_4D)
+    res = []
+    for _ in range(2000):
+        alone.step(2)
+        alone.sync()
+        res += alone.poll()
+        if res:
+            break
+    assert np.array_equal(res[0][1]["theta"], got[r3]["theta"])
+    alone.close()
     s.close()
