@@ -31,6 +31,12 @@
  *     serialised on that stream and block the calling host thread until their results
  *     are on the host.  A model is not thread-safe; different models are independent.
  *   - Arrays of doubles are IEEE binary64.  Event columns are structure-of-arrays.
+ *   - Device memory: every model, batch and server counts the device memory it allocates
+ *     against a limit read at its creation from the environment variable
+ *     GBNLL_DEVICE_ALLOC_LIMIT (bytes; unset or 0: none).  An allocation past the limit fails
+ *     like a failed cudaMalloc: the call returns NLL_ERR_OOM, the object keeps its previous
+ *     state (a model or batch without a sample after a failed load) and can be destroyed.  This
+ *     lets callers and tests provoke device-memory exhaustion from the host.
  */
 #ifndef GBNLL_H
 #define GBNLL_H
@@ -132,7 +138,12 @@ typedef struct {
     double tol_edm; /* stop when EDM = g^T V g / 2 < tol_edm (e.g. 1e-8; <= 0 -> 1e-8)       */
     int max_iter;   /* quasi-Newton iterations (<= 0 -> 500)                                  */
     int strategy;   /* 0: start from diag(step^2); 1: start from a finite-difference Hessian;
-                       2: start from the analytic Hessian (nll_eval_hess)                      */
+                       2: start from the analytic Hessian (nll_eval_hess);
+                       3 (batched and served fits; fit_minimise rejects it): as 2, the start
+                       matrix of every fit from part of its events -- its first 1024 events, or
+                       4 x 1024 spread over samples of more than 8192 -- scaled to the whole
+                       sample; it only preconditions the quasi-Newton steps (the minimum and,
+                       with hessian 2 / 3, the covariance are those of the whole sample)      */
     int hessian;    /* 0: covariance from the quasi-Newton matrix; 1: finite-difference
                        Hessian of the analytic gradient at the minimum plus Newton polish;
                        2: the same with the analytic Hessian, covariance H^-1;
@@ -275,8 +286,9 @@ int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
  *   update   -- one warp per toy sums its units in tile order, assembles NLL and gradient and
  *               advances that toy's minimiser (BFGS, Armijo line search, sine-transform bounds,
  *               finite-difference Hessian of the analytic gradient at the minimum).
- * The three launches are captured once in a CUDA graph and the graph is replayed until every
- * toy has finished.  Schedules: tile_events = 0 gives one work unit per toy and point
+ * The three launches and a one-thread control kernel form the body of a while node of a CUDA
+ * graph: the control kernel continues the loop while some toy is still fitting, so one graph
+ * launch runs the whole fit loop on the device.  Schedules: tile_events = 0 gives one work unit per toy and point
  * (CTA-per-toy); tile_events > 0 splits every toy into tiles of that many events whose sums
  * are combined in tile order (split-toy).  Results are deterministic for a given schedule.
  * ------------------------------------------------------------------------------------ */
@@ -338,12 +350,13 @@ int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, dou
  *                shared_start != 0; lo, hi, step, fixed as fit_minimise (shared by all toys).
  *   opt          tol_edm, max_iter, strategy (1: start from a finite-difference Hessian;
  *                2: from the analytic Hessian of every toy, one batched pass before the
- *                loop), hessian (1: finite-difference Hessian of the analytic gradient at the
+ *                loop; 3: the same pass over part of every toy's events, see fit_options),
+ *                hessian (1: finite-difference Hessian of the analytic gradient at the
  *                minimum for the covariance; 2: analytic Hessian, covariance H^-1; 3: as 2,
  *                covariance H^-1 W H^-1 for weighted toys -- one batched pass after the loop,
  *                no Newton polish; 0: covariance from the BFGS matrix).
  *   results      host array of n_toys fit_result.
- *   steps_out    number of graph replays (device steps) used, or NULL.
+ *   steps_out    number of device steps (iterations of the device-resident loop) used, or NULL.
  * Returns NLL_OK when every toy converged, else NLL_ERR_NOT_CONVERGED (see results[].status).
  */
 int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,

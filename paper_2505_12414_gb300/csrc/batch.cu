@@ -16,7 +16,8 @@
 //                                    Armijo line search, optionally started from and finished
 //                                    with a finite-difference Hessian of the analytic gradient
 //                                    (all stencil points of all toys in one step).
-// The three launches (plus a counter reset) are captured once in a CUDA graph and replayed.
+// The three launches (plus a counter reset) and a one-thread control kernel are the body of
+// a while node of a CUDA graph, so one launch runs the whole fit loop on the device.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdarg.h>
@@ -53,7 +54,9 @@ __device__ double dev_gauss_norm(double za, double zb)
     return 0.5 * (erf(za) - erf(zb));
 }
 
-__device__ bool dev_hoist(int kind, const double* ranges, const double* th, KConst& k, DConst& H)
+// second: also the second derivatives of the normalisations (the Hessian passes need them,
+// the steps of the fit loop do not)
+__device__ bool dev_hoist(int kind, const double* ranges, const double* th, KConst& k, DConst& H, bool second)
 {
     const int npar = kind == kMass1D ? 4 : 18;
     for (int i = 0; i < npar; ++i)
@@ -69,7 +72,7 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
     double ea = exp(-za * za), eb = exp(-zb * zb);
     H.dlnN1_dmu = (ea - eb) / (sqrt(2.0 * kPiH) * sigma * N1);
     H.dlnN1_dsig = -(za * ea - zb * eb) / (sqrt(kPiH) * sigma * N1);
-    {  // second derivatives of ln N1 (as the host hoisting)
+    if (second) {  // second derivatives of ln N1 (as the host hoisting)
         const double s2 = sigma * sigma;
         H.d2lnN1[0] = -(za * ea - zb * eb) / (sqrt(kPiH) * s2 * N1) - H.dlnN1_dmu * H.dlnN1_dmu;
         H.d2lnN1[1] = (ea * (2.0 * za * za - 1.0) - eb * (2.0 * zb * zb - 1.0)) / (sqrt(2.0 * kPiH) * s2 * N1) -
@@ -78,7 +81,7 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
                       H.dlnN1_dsig * H.dlnN1_dsig;
     }
     double t = alpha * D, Nt2;
-    {  // d^2 ln Ntilde2 / dalpha^2 = D^2 v(|t|), v(a) = 1/a^2 - e^-a/(1 - e^-a)^2, series below 1/2
+    if (second) {  // d^2 ln Ntilde2 / dalpha^2 = D^2 v(|t|), v(a) = 1/a^2 - e^-a/(1 - e^-a)^2, series below 1/2
         const double a = fabs(t);
         double v;
         if (a < 0.5) {
@@ -214,7 +217,7 @@ __device__ void emit_item(const BatchDev& b, int toy, int slot, const double* th
     DConst dc;
     memset(&kc, 0, sizeof kc);
     memset(&dc, 0, sizeof dc);
-    bool ok = dev_hoist(b.cfg.kind, b.cfg.ranges, th, kc, dc);
+    bool ok = dev_hoist(b.cfg.kind, b.cfg.ranges, th, kc, dc, false);
     if (!ok) nt = 0;
     int it = atomicAdd(&b.counters[0], 1);
     if (it >= b.max_items) {  // cannot happen with the host's sizing; keep the toy consistent
@@ -678,6 +681,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
 
 struct HessDev {
     int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
+    int subsample;              // the units cover part of each toy's events: scale the sums to all of them
     int tail_begin, tail_count;  // slots summed while staging (HessLayout)
     int pass;                   // covariance modes: polish pass (0: the loop's final point)
     int* n_polish;              // covariance modes: toys still polishing after this pass (mapped)
@@ -739,7 +743,7 @@ __global__ void batch_hess_prep(HessDev h)
     DConst dc;
     memset(&kc, 0, sizeof kc);
     memset(&dc, 0, sizeof dc);
-    const bool ok = use && dev_hoist(c.kind, c.ranges, th, kc, dc);
+    const bool ok = use && dev_hoist(c.kind, c.ranges, th, kc, dc, true);
     h.hok[t] = ok ? 1 : 0;
     if (!ok) return;
     HConst hc;
@@ -1055,10 +1059,16 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
         return;
     }
     const int u0 = h.toy_u0[t], nu = h.toy_nu[t];
+    double scale = 1.0;
+    if (h.subsample) {  // events of the toy over events in its units (a start matrix only)
+        int64_t covered = 0;
+        for (int j = 0; j < nu; ++j) covered += min((int64_t)kHessUnitEvents, h.ev_end[t] - h.unit_e0[u0 + j]);
+        if (covered > 0) scale = (double)(h.ev_end[t] - h.ev_begin[t]) / (double)covered;
+    }
     for (int sl = lane; sl < h.nslots; sl += 32) {
         double v = 0.0;
         for (int j = 0; j < nu; ++j) v += h.unit_sums[(size_t)(u0 + j) * h.nslots + sl];
-        s_sum[wib][sl] = v;
+        s_sum[wib][sl] = v * scale;
     }
     __syncwarp();
     if (lane == 0) {
@@ -1201,7 +1211,7 @@ cudaError_t launch_hess_units_t(int blocks, cudaStream_t s, const HessDev& h)
 
 cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStream_t s, const HessDev& h)
 {
-    batch_hess_prep<<<(h.n_toys + 127) / 128, 128, 0, s>>>(h);
+    batch_hess_prep<<<(h.n_toys + 31) / 32, 32, 0, s>>>(h);  // a warp per block: see launch_step
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (h.n_units > 0) {
@@ -1267,13 +1277,26 @@ cudaError_t ensure_btab(int device)
     return e;
 }
 
+// End of one iteration of the device-resident fit loop (a while node of the fit graph): count
+// the step and continue while some toy is still fitting and the step limit is not reached.
+// One thread: the condition is set once per iteration.
+__global__ void batch_loop_control(cudaGraphConditionalHandle handle, const int* n_active, int* steps, int max_steps)
+{
+    const int s = *steps + 1;
+    *steps = s;
+    const int active = *(volatile const int*)n_active;
+    cudaGraphSetConditional(handle, (active > 0 && s < max_steps) ? 1u : 0u);
+}
+
 // One device step of the batched fit loop on stream s (for graph capture): reset the work
 // counters, prepare (hoisting of every active toy's points), evaluate, update.
 cudaError_t launch_step(const BatchDev& d, int var, bool weighted, int eval_blocks, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(d.counters, 0, sizeof(int) * 3, s);
     if (e != cudaSuccess) return e;
-    batch_prepare<<<(d.n_toys + 127) / 128, 128, 0, s>>>(d);
+    // one warp per block: each toy's hoisting is a long dependent FP64 chain, so the warps go
+    // to different SMs instead of sharing one SM's FP64 pipe
+    batch_prepare<<<(d.n_toys + 31) / 32, 32, 0, s>>>(d);
     e = launch_eval(d.cfg.kind, var, weighted, eval_blocks, s, d);
     if (e != cudaSuccess) return e;
     const int ub = (d.n_toys + kUpdWarps - 1) / kUpdWarps;
@@ -1310,31 +1333,33 @@ void hw_free(HessWork& w)
     void* ptrs[] = {w.d_unit_toy, w.d_unit_e0, w.d_toy_u0, w.d_toy_nu, w.d_hc, w.d_ht, w.d_hok, w.d_unit_sums,
                     w.d_slot_of, w.d_thetas, w.d_out, w.d_status, w.d_sel};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) gb_free(p);
     void* hptrs[] = {w.h_npol, w.h_unit_toy, w.h_unit_e0, w.h_toy_u0, w.h_toy_nu, w.h_sel};
     for (void* p : hptrs)
         if (p) cudaFreeHost(p);
     if (w.staged_ev) cudaEventDestroy(w.staged_ev);
+    DevBudget* budget = w.budget;
     w = HessWork();
+    w.budget = budget;
 }
 
 cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
 {
     hw_free(w);
     const size_t nt = std::max(cap_toys, 1), nu = std::max(cap_units, 1);
-    cudaError_t e = cudaMalloc(&w.d_unit_toy, sizeof(int) * nu);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_unit_e0, sizeof(int64_t) * nu);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_toy_u0, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_toy_nu, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_hc, sizeof(HConst) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_ht, sizeof(HessTerms) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_hok, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_unit_sums, sizeof(double) * kHessMaxSlots * nu);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_slot_of, sizeof(uint16_t) * 64 * 64);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_thetas, sizeof(double) * np * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_out, sizeof(double) * (1 + np + 2 * np * np) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_status, sizeof(int) * nt);
-    if (e == cudaSuccess) e = cudaMalloc(&w.d_sel, sizeof(int) * nt);
+    cudaError_t e = gb_malloc(w.budget, &w.d_unit_toy, sizeof(int) * nu);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_unit_e0, sizeof(int64_t) * nu);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_toy_u0, sizeof(int) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_toy_nu, sizeof(int) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_hc, sizeof(HConst) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_ht, sizeof(HessTerms) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_hok, sizeof(int) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_unit_sums, sizeof(double) * kHessMaxSlots * nu);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_slot_of, sizeof(uint16_t) * 64 * 64);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_thetas, sizeof(double) * np * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_out, sizeof(double) * (1 + np + 2 * np * np) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_status, sizeof(int) * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_sel, sizeof(int) * nt);
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_npol, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&w.d_npol, w.h_npol, 0);
     // pinned staging of the unit lists, so that they can be copied without the host waiting
@@ -1359,14 +1384,32 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
 // get no units (sel empty: every toy).  Fails if the units exceed the capacity.  The lists go
 // through pinned staging; with wait the call returns once they are on the device, without it
 // as soon as the copies are queued (the staging is reused only after they have completed).
+// units of a toy with `total` units that a subsampled pass takes: the first unit of a sample of
+// up to 8 units, else 4 units spread evenly over the sample (so that a sample stored in some
+// order still contributes from its whole range)
+static int subsample_units(int64_t total, int64_t* pick)
+{
+    if (total <= 0) return 0;
+    if (total <= 8) {
+        pick[0] = 0;
+        return 1;
+    }
+    for (int k = 0; k < 4; ++k) pick[k] = k * total / 4;
+    return 4;
+}
+
 cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const std::vector<int64_t>& end,
-                         const std::vector<int>& sel, cudaStream_t stream, bool wait)
+                         const std::vector<int>& sel, cudaStream_t stream, bool wait, bool subsample)
 {
     const int n = (int)begin.size();
     if (n > w.cap_toys) return cudaErrorInvalidValue;
     int64_t nu = 0;
     for (int t = 0; t < n; ++t)
-        if (sel.empty() || sel[t]) nu += (std::max<int64_t>(end[t] - begin[t], 0) + kHessUnitEvents - 1) / kHessUnitEvents;
+        if (sel.empty() || sel[t]) {
+            const int64_t total = (std::max<int64_t>(end[t] - begin[t], 0) + kHessUnitEvents - 1) / kHessUnitEvents;
+            int64_t pick[4];
+            nu += subsample ? subsample_units(total, pick) : total;
+        }
     if (nu > w.cap_units) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     if (w.staged_pending) {  // the previous lists may still be in flight from the staging
@@ -1379,10 +1422,21 @@ cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const s
         w.h_toy_u0[t] = u;
         w.h_toy_nu[t] = 0;
         if (!sel.empty() && !sel[t]) continue;
-        for (int64_t ev = begin[t]; ev < end[t]; ev += kHessUnitEvents) {
-            w.h_unit_toy[u] = t;
-            w.h_unit_e0[u] = ev;
-            ++u;
+        if (subsample) {
+            const int64_t total = (std::max<int64_t>(end[t] - begin[t], 0) + kHessUnitEvents - 1) / kHessUnitEvents;
+            int64_t pick[4];
+            const int k = subsample_units(total, pick);
+            for (int j = 0; j < k; ++j) {
+                w.h_unit_toy[u] = t;
+                w.h_unit_e0[u] = begin[t] + pick[j] * kHessUnitEvents;
+                ++u;
+            }
+        } else {
+            for (int64_t ev = begin[t]; ev < end[t]; ev += kHessUnitEvents) {
+                w.h_unit_toy[u] = t;
+                w.h_unit_e0[u] = ev;
+                ++u;
+            }
         }
         w.h_toy_nu[t] = u - w.h_toy_u0[t];
     }
@@ -1406,7 +1460,7 @@ cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const s
 
 // One Hessian pass (see HessDev); use_sel restricts it to the toys hw_set_units selected.
 cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int mode, bool want_w2,
-                          const double* thetas, int pass, bool use_sel, bool wait)
+                          const double* thetas, int pass, bool use_sel, bool wait, bool subsample)
 {
     HessLayout L;
     if (!hess_layout(T.kind, T.weighted, want_w2, &L)) return cudaErrorInvalidValue;
@@ -1431,6 +1485,7 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
     h.n_polish = w.d_npol;
     h.sel = use_sel ? w.d_sel : nullptr;
     h.n_units = w.n_units;
+    h.subsample = subsample ? 1 : 0;
     h.nslots = L.nslots;
     h.lnp_slot = L.lnp_slot;
     h.tail_begin = L.tail_begin;
@@ -1489,6 +1544,7 @@ cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, 
 
 struct nll_batch {
     int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
+    DevBudget budget;  // device memory of this batch (limit from GBNLL_DEVICE_ALLOC_LIMIT)
     cudaStream_t user_stream = nullptr;  // caller's stream (0 = default)
     cudaStream_t stream = nullptr;       // the batch's own stream (graph capture needs one)
     double ranges[8] = {0};
@@ -1562,13 +1618,13 @@ void free_work(nll_batch* b)
     if (b->fit_graph) cudaGraphDestroy(b->fit_graph);
     b->fit_exec = nullptr;
     b->fit_graph = nullptr;
-    if (b->d_init) cudaFree(b->d_init);
+    if (b->d_init) gb_free(b->d_init);
     if (b->h_res) cudaFreeHost(b->h_res);
     b->d_init = b->h_res = b->d_res = nullptr;
     void* ptrs[] = {b->d_ev, b->d_begin, b->d_end, b->d_sum_wdm, b->d_item_toy, b->d_item_u0, b->d_item_nt,
                     b->d_item_kc, b->d_item_dc, b->d_unit_item, b->d_unit_tile, b->d_unit_sums, b->d_fits};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) gb_free(p);
     b->d_ev = nullptr;
     b->d_w = nullptr;
     b->d_begin = b->d_end = nullptr;
@@ -1796,18 +1852,18 @@ cudaError_t finish_store(nll_batch* b, bool basis, int64_t pos, bool device_sums
     }
     b->max_items = (int)max_items;
     b->max_units = (int)max_units;
-    e = cudaMalloc(&b->d_begin, sizeof(int64_t) * std::max(n_toys, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_end, sizeof(int64_t) * std::max(n_toys, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_sum_wdm, sizeof(double) * std::max(n_toys, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_toy, sizeof(int) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_u0, sizeof(int) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_nt, sizeof(int) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_kc, sizeof(KConst) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_item_dc, sizeof(DConst) * max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_item, sizeof(int) * max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_tile, sizeof(int) * max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_unit_sums, sizeof(double) * kAccMax * max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_fits, sizeof(ToyFit) * std::max(n_toys, 1));
+    e = gb_malloc(&b->budget, &b->d_begin, sizeof(int64_t) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_end, sizeof(int64_t) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_sum_wdm, sizeof(double) * std::max(n_toys, 1));
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_item_toy, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_item_u0, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_item_nt, sizeof(int) * max_items);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_item_kc, sizeof(KConst) * max_items);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_item_dc, sizeof(DConst) * max_items);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_unit_item, sizeof(int) * max_units);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_unit_tile, sizeof(int) * max_units);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_unit_sums, sizeof(double) * kAccMax * max_units);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_fits, sizeof(ToyFit) * std::max(n_toys, 1));
     // every index the kernels can read is valid from the start
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_toy, 0, sizeof(int) * max_items, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_item_u0, 0, sizeof(int) * max_items, b->stream);
@@ -1842,7 +1898,7 @@ namespace gbnll {
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
                   const fit_options& opt)
 {
-    c.strategy = opt.strategy;          // 2: start matrix from the analytic Hessian pass
+    c.strategy = opt.strategy == 3 ? 2 : opt.strategy;  // 2, 3: start matrix from the analytic Hessian pass
     c.hessian = opt.hessian == 1;       // in-loop finite-difference Hessian; 2/3 run after the loop
     c.max_iter = opt.max_iter;
     c.tol_edm = opt.tol_edm;
@@ -1922,6 +1978,8 @@ int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t c
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
     if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
     nll_batch* b = new nll_batch();
+    b->budget.limit = dev_budget_limit_from_env();
+    b->hw.budget = &b->budget;
     b->kind = kind;
     b->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
     b->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
@@ -1935,7 +1993,7 @@ int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t c
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = ensure_btab(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * 4);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_counters, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_active, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_active, b->h_active, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
@@ -1954,7 +2012,7 @@ void nll_batch_destroy(nll_batch* b)
     cudaSetDevice(b->device);
     if (b->stream) cudaStreamSynchronize(b->stream);
     free_work(b);
-    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->d_counters) gb_free(b->d_counters);
     if (b->h_active) cudaFreeHost(b->h_active);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
@@ -2009,7 +2067,7 @@ int nll_batch_load(nll_batch* b, const int64_t* offsets, int n_toys, const doubl
     b->ncols = b->kind == kMass1D ? 1 : (basis ? kNumCols : 4);
     const int nalloc = b->ncols + (weights ? 1 : 0);
     b->n_pad = n_pad;
-    cudaError_t e = cudaMalloc(&b->d_ev, sizeof(double) * n_pad * nalloc);
+    cudaError_t e = gb_malloc(&b->budget, &b->d_ev, sizeof(double) * n_pad * nalloc);
     if (e != cudaSuccess) {
         b->d_ev = nullptr;
         return bcuda(b, e, "batch event store");
@@ -2069,7 +2127,7 @@ int nll_batch_generate(nll_batch* b, const double* theta, const int64_t* counts,
     b->ncols = b->kind == kMass1D ? 1 : (basis ? kNumCols : 4);
     b->n_pad = n_pad;
     b->weighted = false;
-    cudaError_t e = cudaMalloc(&b->d_ev, sizeof(double) * n_pad * b->ncols);
+    cudaError_t e = gb_malloc(&b->budget, &b->d_ev, sizeof(double) * n_pad * b->ncols);
     if (e != cudaSuccess) {
         b->d_ev = nullptr;
         return bcuda(b, e, "batch event store");
@@ -2187,8 +2245,8 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         memset(&opt, 0, sizeof opt);
     if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
     if (opt.max_iter <= 0) opt.max_iter = 500;
-    if (opt.strategy < 0 || opt.strategy > 2 || opt.hessian < 0 || opt.hessian > 3)
-        return bfail(b, NLL_ERR_ARG, "strategy must be 0..2 and hessian 0..3");
+    if (opt.strategy < 0 || opt.strategy > 3 || opt.hessian < 0 || opt.hessian > 3)
+        return bfail(b, NLL_ERR_ARG, "strategy must be 0..3 and hessian 0..3");
     const int n = b->n_toys, np = b->npar;
     if (n == 0) return NLL_OK;
     BatchDev d = make_dev(b);
@@ -2197,7 +2255,7 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     const int nf = c.nf;
     // start states on the device: only the start points and steps cross the link
     cudaError_t e = cudaSuccess;
-    if (!b->d_init) e = cudaMalloc(&b->d_init, sizeof(double) * ((size_t)n + 1) * kNP);
+    if (!b->d_init) e = gb_malloc(&b->budget, &b->d_init, sizeof(double) * ((size_t)n + 1) * kNP);
     if (e == cudaSuccess && !b->h_res) {
         e = cudaHostAlloc(&b->h_res, sizeof(double) * (size_t)n * kResStride, cudaHostAllocMapped);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_res, b->h_res, 0);
@@ -2220,14 +2278,27 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     if (opt.strategy == 2) {  // start matrices from the analytic Hessian at every toy's start point
         int st = run_hess_pass(b, c, kHmStart, false, nullptr);
         if (st != NLL_OK) return st;
+    } else if (opt.strategy == 3) {
+        // the same from a subsample of every toy's events, queued without a wait; the unit lists
+        // of the whole toys are restored behind it for the later passes
+        int st = ensure_hess_work(b);
+        if (st != NLL_OK) return st;
+        e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->stream, false, true);
+        if (e == cudaSuccess)
+            e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false, true);
+        if (e == cudaSuccess) e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->stream, false, false);
+        if (e != cudaSuccess) return bcuda(b, e, "start matrices");
     }
 
-    // one device step = counter reset, prepare, evaluate, update; captured once and kept while
-    // the batch's buffers and the fit configuration stay the same
+    // The fit loop runs on the device: a CUDA graph with one while node whose body is a device
+    // step (counter reset, prepare, evaluate, update) followed by a one-thread control kernel
+    // that counts the step and keeps the loop going while some toy is still fitting (and the
+    // step limit is not reached).  The graph is built once and kept while the batch's buffers
+    // and the fit configuration stay the same; one launch runs the whole loop.
     const int eval_blocks = b->sm_count * b->bps;
-    const int prep_blocks = (n + 127) / 128;
-    const int upd_blocks = (n + kUpdWarps - 1) / kUpdWarps;
-    const int shape[4] = {eval_blocks, prep_blocks, upd_blocks, variant_of(b)};
+    const int max_steps = opt.max_iter * 40 + 8;  // every line-search trial is one step
+    const int shape[4] = {eval_blocks, max_steps, 0, variant_of(b)};
+    int* d_steps = b->d_counters + 3;
     if (!b->fit_exec || memcmp(&b->fit_dev, &d, sizeof d) != 0 || memcmp(b->fit_shape, shape, sizeof shape) != 0) {
         if (b->fit_exec) cudaGraphExecDestroy(b->fit_exec);
         if (b->fit_graph) cudaGraphDestroy(b->fit_graph);
@@ -2235,16 +2306,30 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         b->fit_graph = nullptr;
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
-        e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        cudaGraphConditionalHandle handle;
+        e = cudaGraphCreate(&graph, 0);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1u, cudaGraphCondAssignDefault);
+        cudaGraphNodeParams np_ = {};
+        cudaGraphNode_t node;
         if (e == cudaSuccess) {
-            cudaMemsetAsync(b->d_counters, 0, sizeof(int) * 3, b->stream);
-            batch_prepare<<<prep_blocks, 128, 0, b->stream>>>(d);
-            launch_eval(b->kind, variant_of(b), b->weighted, eval_blocks, b->stream, d);
-            if (b->kind == kMass1D)
-                batch_update<kMass1D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
-            else
-                batch_update<kKstar4D><<<upd_blocks, kUpdWarps * 32, 0, b->stream>>>(d);
-            e = cudaStreamEndCapture(b->stream, &graph);
+            np_.type = cudaGraphNodeTypeConditional;
+            np_.conditional.handle = handle;
+            np_.conditional.type = cudaGraphCondTypeWhile;
+            np_.conditional.size = 1;
+            e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np_);
+        }
+        if (e == cudaSuccess) {
+            cudaGraph_t body = np_.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(b->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t ec = launch_step(d, variant_of(b), b->weighted, eval_blocks, b->stream);
+                if (ec == cudaSuccess) {
+                    batch_loop_control<<<1, 1, 0, b->stream>>>(handle, d.n_active, d_steps, max_steps);
+                    ec = cudaGetLastError();
+                }
+                e = cudaStreamEndCapture(b->stream, &body);
+                if (e == cudaSuccess) e = ec;
+            }
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
         if (e != cudaSuccess) {
@@ -2256,15 +2341,11 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         b->fit_dev = d;
         memcpy(b->fit_shape, shape, sizeof shape);
     }
-    const int max_steps = opt.max_iter * 40 + 8;  // every line-search trial is one step
     int steps = 0;
-    while (steps < max_steps) {
-        const int burst = steps < 8 ? 1 : 4;  // poll often at first, then every few steps
-        for (int r = 0; r < burst && e == cudaSuccess; ++r, ++steps) e = cudaGraphLaunch(b->fit_exec, b->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) break;
-        if (*(volatile int*)b->h_active <= 0) break;
-    }
+    e = cudaMemsetAsync(d_steps, 0, sizeof(int), b->stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->fit_exec, b->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&steps, d_steps, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit loop");
     if (steps_out) *steps_out = steps;
     if (opt.hessian >= 2) {

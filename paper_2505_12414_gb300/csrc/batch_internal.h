@@ -119,6 +119,7 @@ struct HessWork {
     int* h_sel = nullptr;
     cudaEvent_t staged_ev = nullptr;
     bool staged_pending = false;
+    DevBudget* budget = nullptr;  // the owner's device-memory count (kept by hw_free)
 };
 
 // The sample and fit states a Hessian pass works on.
@@ -139,12 +140,17 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np);
 // Unit lists for toys t with events [begin[t], end[t]); toys with sel[t] == 0 get no units
 // (sel empty: every toy).  With wait, returns once they are on the device; without, once the
 // copies (from pinned staging) are queued on the stream.
+// With subsample, a toy takes the first of its 1024-event units when it has up to 8, else 4
+// units spread evenly over its events (a start matrix; see run_hess_core).
 cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const std::vector<int64_t>& end,
-                         const std::vector<int>& sel, cudaStream_t stream, bool wait = true);
+                         const std::vector<int>& sel, cudaStream_t stream, bool wait = true,
+                         bool subsample = false);
 // One Hessian pass (mode HessMode); use_sel restricts it to the toys hw_set_units selected.
 // With wait, returns once the pass has finished; without, once it is queued on T.stream.
+// subsample: the unit lists cover part of each toy's events (hw_set_units with subsample); the
+// slot sums are scaled by events / events covered before the assembly (start matrices only).
 cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int mode, bool want_w2,
-                          const double* thetas, int pass, bool use_sel, bool wait = true);
+                          const double* thetas, int pass, bool use_sel, bool wait = true, bool subsample = false);
 // Newton polish passes with the analytic Hessian at the final points of the finished toys.
 cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel);
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,

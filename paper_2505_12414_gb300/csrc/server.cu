@@ -40,6 +40,7 @@ constexpr int kStepRing = 64;  // events of the most recent graph steps (steps i
 
 struct nll_server {
     int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
+    DevBudget budget;  // device memory of this server (limit from GBNLL_DEVICE_ALLOC_LIMIT)
     cudaStream_t stream = nullptr;   // steps and start passes
     cudaStream_t cstream = nullptr;  // admission and collection
     double ranges[8] = {0};
@@ -54,6 +55,7 @@ struct nll_server {
     int64_t next_id = 1;
     FitConfig cfg;
     int hessian = 0;  // fit_options.hessian: 2 / 3 polish finished slots with the analytic Hessian
+    bool subsample_start = false;  // strategy 3: start matrices from a subsample of each fit's events
     HessWork hw;      // start passes (strategy 2), on the step stream
     HessWork hwp;     // polish passes (hessian 2 / 3), on the collection stream
     // admission statistics on the device (range check, sum (m - ma)) of a request's events
@@ -121,7 +123,7 @@ void server_free(nll_server* s)
                     s->d_item_u0, s->d_item_nt, s->d_item_kc, s->d_item_dc, s->d_unit_item, s->d_unit_tile,
                     s->d_unit_sums, s->d_spart, s->d_sticket, s->d_pick};
     for (void* p : ptrs)
-        if (p) cudaFree(p);
+        if (p) gb_free(p);
     void* hptrs[] = {s->h_active, s->h_done, s->h_sout, s->h_fit_stage, s->h_be_stage, s->h_sum_stage, s->h_pick,
                      s->h_res};
     for (void* p : hptrs)
@@ -214,14 +216,15 @@ HessTarget server_target(nll_server* s, cudaStream_t stream)
 }
 
 // unit lists of a Hessian pass over the slots with pick[i] != 0
-cudaError_t server_pick(nll_server* s, HessWork& w, const std::vector<int>& pick, cudaStream_t stream, bool wait)
+cudaError_t server_pick(nll_server* s, HessWork& w, const std::vector<int>& pick, cudaStream_t stream, bool wait,
+                        bool subsample = false)
 {
     std::vector<int64_t> begin(s->max_slots), end(s->max_slots);
     for (int i = 0; i < s->max_slots; ++i) {
         begin[i] = s->slot_begin[i];
         end[i] = s->slot_begin[i] + (pick[i] ? s->slot_nev[i] : 0);
     }
-    return hw_set_units(w, begin, end, pick, stream, wait);
+    return hw_set_units(w, begin, end, pick, stream, wait, subsample);
 }
 
 int finished_count(const nll_server* s)
@@ -242,7 +245,7 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
 {
     if (!out) return NLL_ERR_ARG;
     *out = nullptr;
-    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 2 || opt_in->hessian < 0 || opt_in->hessian > 3))
+    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 3 || opt_in->hessian < 0 || opt_in->hessian > 3))
         return NLL_ERR_ARG;
     if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges || max_slots < 1 ||
         pool_events < 1 || tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
@@ -257,6 +260,9 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
     if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
     nll_server* s = new nll_server();
+    s->budget.limit = dev_budget_limit_from_env();
+    s->hw.budget = &s->budget;
+    s->hwp.budget = &s->budget;
     s->kind = kind;
     s->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
     s->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
@@ -282,6 +288,7 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     for (int i = 0; i < 8; ++i) s->cfg.ranges[i] = s->ranges[i];
     setup_config(s->cfg, s->npar, lo, hi, step, fixed, opt);
     s->hessian = opt.hessian;
+    s->subsample_start = opt.strategy == 3;
     s->step.assign(s->npar, 0.0);
     for (int k = 0; k < s->npar; ++k) s->step[k] = step ? step[k] : 0.0;
     // pool: padded so a range of even length starting on an even event can end anywhere
@@ -314,8 +321,8 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
         e = cap > (1 << 28) ? cudaErrorInvalidValue : hw_alloc(s->hwp, max_slots, (int)cap, s->npar);
     for (int i = 0; i < kStepRing && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&s->step_ev[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_spart, sizeof(double) * 3 * 2 * s->sm_count);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_sticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_spart, sizeof(double) * 3 * 2 * s->sm_count);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_sticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(s->d_sticket, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_sout, sizeof(double) * 3, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_sout, s->h_sout, 0);
@@ -323,28 +330,28 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_be_stage, sizeof(int64_t) * 2 * max_slots, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_sum_stage, sizeof(double) * max_slots, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_pick, sizeof(int) * max_slots, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_pick, sizeof(int) * max_slots);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_pick, sizeof(int) * max_slots);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_res, sizeof(double) * kResStride * max_slots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_res, s->h_res, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_ev, sizeof(double) * s->n_pad * s->ncols);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_ev, sizeof(double) * s->n_pad * s->ncols);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_ev, 0, sizeof(double) * s->n_pad * s->ncols, s->stream);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_begin, sizeof(int64_t) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_end, sizeof(int64_t) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_sum_wdm, sizeof(double) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_fits, sizeof(ToyFit) * max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, sizeof(int) * 4);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_begin, sizeof(int64_t) * max_slots);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_end, sizeof(int64_t) * max_slots);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_sum_wdm, sizeof(double) * max_slots);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_fits, sizeof(ToyFit) * max_slots);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_counters, sizeof(int) * 4);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_active, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_active, s->h_active, 0);
     if (e == cudaSuccess) e = cudaHostAlloc(&s->h_done, sizeof(int) * max_slots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&s->d_done, s->h_done, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_toy, sizeof(int) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_u0, sizeof(int) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_nt, sizeof(int) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_kc, sizeof(KConst) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_item_dc, sizeof(DConst) * s->max_items);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_item, sizeof(int) * s->max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_tile, sizeof(int) * s->max_units);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_unit_sums, sizeof(double) * kAccMax * s->max_units);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_item_toy, sizeof(int) * s->max_items);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_item_u0, sizeof(int) * s->max_items);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_item_nt, sizeof(int) * s->max_items);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_item_kc, sizeof(KConst) * s->max_items);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_item_dc, sizeof(DConst) * s->max_items);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_unit_item, sizeof(int) * s->max_units);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_unit_tile, sizeof(int) * s->max_units);
+    if (e == cudaSuccess) e = gb_malloc(&s->budget, &s->d_unit_sums, sizeof(double) * kAccMax * s->max_units);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_toy, 0, sizeof(int) * s->max_items, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_u0, 0, sizeof(int) * s->max_items, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_item_nt, 0, sizeof(int) * s->max_items, s->stream);
@@ -453,9 +460,10 @@ int nll_server_step(nll_server* s, int n_steps)
         // pass queued on the step stream ahead of the steps (no wait)
         std::vector<int> pick(s->max_slots, 0);
         for (int i = 0; i < s->max_slots; ++i) pick[i] = s->busy[i] && s->need_start[i];
-        cudaError_t e = server_pick(s, s->hw, pick, s->stream, false);
+        cudaError_t e = server_pick(s, s->hw, pick, s->stream, false, s->subsample_start);
         if (e == cudaSuccess)
-            e = run_hess_core(server_target(s, s->stream), s->hw, s->cfg, kHmStart, false, nullptr, 0, true, false);
+            e = run_hess_core(server_target(s, s->stream), s->hw, s->cfg, kHmStart, false, nullptr, 0, true, false,
+                              s->subsample_start);
         if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "start Hessians: %s", cudaGetErrorString(e));
         for (int i = 0; i < s->max_slots; ++i)
             if (pick[i]) s->need_start[i] = 0;

@@ -178,3 +178,39 @@ def test_4d_basis_without_any_model_in_the_process():
     root = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "fresh-process basis ok" in r.stdout, r.stdout + r.stderr
+
+
+def test_subsampled_start_matrices_reach_the_same_minima(gpu_lib):
+    """strategy 3 (start matrices from part of every toy's events) only changes the quasi-Newton
+    path: the polished minima and covariances equal those of strategy 2."""
+    off, cols = synth.toys4d(64, 3000.0, seed=synth.BASE_SEED + 55)
+    lo, hi = np.zeros(18), np.zeros(18)
+    hi[17] = 1.0
+    step = np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    b = gpu_lib.Batch(gpu_lib.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D).load(off, cols)
+    # both stop within sqrt(2 EDM) of the minimum: 1e-14 puts that below 1e-6 of the uncertainty
+    r2 = b.fit(synth.TRUTH_4D, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=2, hessian=2)
+    r3 = b.fit(synth.TRUTH_4D, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=3, hessian=2)
+    b.close()
+    ok = (r2["status"] == 0) & (r3["status"] == 0)
+    assert ok.mean() > 0.98
+    assert np.max(np.abs(r3["theta"][ok] - r2["theta"][ok]) / r2["err"][ok]) < 1e-6
+    np.testing.assert_allclose(r3["err"][ok], r2["err"][ok], rtol=1e-6)
+    assert np.mean(r3["n_eval"]) < 2.0 * np.mean(r2["n_eval"])
+
+
+def test_device_loop_reports_its_steps(gpu_lib):
+    # the fit loop runs as a while node on the device; the step count comes back from it
+    off, cols = synth.toys1d(50, 1000.0, seed=synth.BASE_SEED + 56)
+    b = gpu_lib.Batch(gpu_lib.NLL_MODEL_MASS1D, synth.RANGES_1D).load(off, cols)
+    lo, hi = np.zeros(4), np.zeros(4)
+    hi[3] = 1.0
+    step = np.array([2.0, 1.0, 2e-4, 0.02])
+    r = b.fit(synth.TRUTH_1D, lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=2, hessian=0)
+    assert np.all(r["status"] == 0)
+    assert r["steps"] >= np.max(r["n_eval"]) - 1 and r["steps"] <= np.max(r["n_eval"]) + 1
+    # with max_iter 1 every toy stops after its first iteration
+    r1 = b.fit(synth.TRUTH_1D + 0.5 * step, lo=lo, hi=hi, step=step, tol_edm=1e-14, max_iter=1, strategy=0,
+               hessian=0)
+    assert r1["steps"] <= 1 * 40 + 8
+    b.close()
