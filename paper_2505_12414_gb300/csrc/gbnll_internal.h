@@ -125,6 +125,25 @@ struct Hoist {
 int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hoist& H, std::string* err);
 void assemble_core(int kind, const Hoist& H, double sum_wdm, const double* S, double* nll_out, double* grad_out);
 
+// Device memory of the library's objects (models, batches, servers) is counted against a
+// per-object limit read at creation from the environment variable GBNLL_DEVICE_ALLOC_LIMIT
+// (bytes; unset or 0: no limit), so that running out of device memory can be provoked from
+// the host in tests: an allocation past the limit fails as cudaMalloc fails
+// (cudaErrorMemoryAllocation) and allocates nothing.  gb_free returns the bytes to the
+// object's count.
+struct DevBudget {
+    size_t limit = 0;  // 0: no limit
+    size_t used = 0;
+};
+size_t dev_budget_limit_from_env();
+cudaError_t gb_malloc_bytes(DevBudget* budget, void** p, size_t bytes);
+template <class T>
+inline cudaError_t gb_malloc(DevBudget* budget, T** p, size_t bytes)
+{
+    return gb_malloc_bytes(budget, reinterpret_cast<void**>(p), bytes);
+}
+void gb_free(void* p);
+
 // Launchers (kernels.cu).  They return the launch's cudaError_t.
 cudaError_t launch_fused(int kind, int variant, bool weighted, bool grad, int blocks, int threads,
                          cudaStream_t stream, const KArgs& a, bool in_place = false);

@@ -10,11 +10,13 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/gbnll.h"
@@ -42,6 +44,7 @@ int ensure_exp2_table(int device)
 }  // namespace
 
 struct nll_model {
+    DevBudget budget;  // device memory of this model (limit from GBNLL_DEVICE_ALLOC_LIMIT)
     int kind = 0;
     int ndim = 0;
     int npar = 0;
@@ -164,6 +167,55 @@ double gauss_norm(double za, double zb)
 }  // namespace
 
 namespace gbnll {
+
+namespace {
+std::mutex g_alloc_mutex;
+std::unordered_map<void*, std::pair<DevBudget*, size_t>>& alloc_registry()
+{
+    static std::unordered_map<void*, std::pair<DevBudget*, size_t>> reg;
+    return reg;
+}
+}  // namespace
+
+size_t dev_budget_limit_from_env()
+{
+    const char* v = getenv("GBNLL_DEVICE_ALLOC_LIMIT");
+    if (!v || !*v) return 0;
+    char* end = nullptr;
+    const unsigned long long x = strtoull(v, &end, 10);
+    return (end && *end == '\0') ? (size_t)x : 0;
+}
+
+cudaError_t gb_malloc_bytes(DevBudget* budget, void** p, size_t bytes)
+{
+    *p = nullptr;
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (budget && budget->limit && budget->used + bytes > budget->limit) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return e;
+    }
+    alloc_registry()[*p] = {budget, bytes};
+    if (budget) budget->used += bytes;
+    return cudaSuccess;
+}
+
+void gb_free(void* p)
+{
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mutex);
+        auto& reg = alloc_registry();
+        auto it = reg.find(p);
+        if (it != reg.end()) {
+            if (it->second.first) it->second.first->used -= it->second.second;
+            reg.erase(it);
+        }
+    }
+    cudaFree(p);
+}
+
 int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hoist& H, std::string* err)
 {
     memset(&H, 0, sizeof H);
@@ -461,7 +513,7 @@ int ensure_hess_scratch(nll_model* m)
 {
     if (m->d_hpart) return NLL_OK;
     m->hess_max_blocks = m->sm_count * kHessMaxBlocksPerSm;
-    cudaError_t e = cudaMalloc(&m->d_hpart, sizeof(double) * kHessMaxSlots * (size_t)m->hess_max_blocks);
+    cudaError_t e = gb_malloc(&m->budget, &m->d_hpart, sizeof(double) * kHessMaxSlots * (size_t)m->hess_max_blocks);
     if (e == cudaSuccess)
         e = cudaHostAlloc(&m->h_hout, (sizeof(double) + sizeof(unsigned int)) * kHessMaxSlots, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&m->d_hout, m->h_hout, 0);
@@ -471,7 +523,7 @@ int ensure_hess_scratch(nll_model* m)
         for (int k = 0; k < kHessMaxSlots; ++k) m->h_hdone[k] = 0u;
     }
     if (e != cudaSuccess) {
-        if (m->d_hpart) cudaFree(m->d_hpart);
+        if (m->d_hpart) gb_free(m->d_hpart);
         if (m->h_hout) cudaFreeHost(m->h_hout);
         m->d_hpart = m->h_hout = m->d_hout = nullptr;
         return cuda_fail(m, e, "Hessian scratch");
@@ -567,7 +619,7 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
 void reset_events(nll_model* m, bool release)
 {
     if (release && m->d_ev) {
-        cudaFree(m->d_ev);
+        gb_free(m->d_ev);
         m->d_ev = nullptr;
         m->ev_capacity = 0;
     }
@@ -629,6 +681,7 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return NLL_ERR_CUDA;
     if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
     nll_model* m = new nll_model();
+    m->budget.limit = dev_budget_limit_from_env();
     m->kind = kind;
     m->ndim = kind == NLL_MODEL_MASS1D ? 1 : 4;
     m->npar = kind == NLL_MODEL_MASS1D ? 4 : 18;
@@ -653,8 +706,8 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
     cudaError_t e = cudaSuccess;
     m->stream = (cudaStream_t)cuda_stream;  // 0: CUDA's default stream
     m->own_stream = false;
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_partials, sizeof(double) * kAccModel * m->max_blocks);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_ticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = gb_malloc(&m->budget, &m->d_partials, sizeof(double) * kAccModel * m->max_blocks);
+    if (e == cudaSuccess) e = gb_malloc(&m->budget, &m->d_ticket, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(m->d_ticket, 0, sizeof(unsigned int));
     // results land in mapped pinned host memory: the grid's last block writes them there
     if (e == cudaSuccess)
@@ -682,10 +735,10 @@ void nll_destroy(nll_model* m)
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
     free_events(m);
-    if (m->d_partials) cudaFree(m->d_partials);
-    if (m->d_ticket) cudaFree(m->d_ticket);
+    if (m->d_partials) gb_free(m->d_partials);
+    if (m->d_ticket) gb_free(m->d_ticket);
     if (m->h_out) cudaFreeHost(m->h_out);  // d_out is its device alias
-    if (m->d_hpart) cudaFree(m->d_hpart);
+    if (m->d_hpart) gb_free(m->d_hpart);
     if (m->h_hout) cudaFreeHost(m->h_hout);
     if (m->ev0) cudaEventDestroy(m->ev0);
     if (m->ev1) cudaEventDestroy(m->ev1);
@@ -772,7 +825,7 @@ int nll_load_events(nll_model* m, const double* const* columns, const double* we
     cudaError_t e = cudaSuccess;
     if (bytes > m->ev_capacity) {
         reset_events(m, true);
-        e = cudaMalloc(&m->d_ev, bytes);
+        e = gb_malloc(&m->budget, &m->d_ev, bytes);
         if (e != cudaSuccess) {
             m->d_ev = nullptr;
             return cuda_fail(m, e, "event store allocation");
