@@ -361,6 +361,41 @@ def mass_sweep(g, device, stream):
     return out
 
 
+def single_fit_latency(g, device, n_events=10_000, n_fits=100):
+    """Latency of one full fit of the mass model (10^4 events, 4 free parameters, analytic
+    derivatives), one fit at a time through fit_minimise: the quasi-Newton route (analytic
+    start matrix and Newton polish, strategy 2 / hessian 2) against damped Newton steps with
+    the analytic Hessian at every iterate (strategy 4).  Each fit starts from its own seeded
+    point near the truth; wall clock of the blocking call."""
+    cols = synth.mass1d(n_events, stream=91)
+    m = g.Model(g.NLL_MODEL_MASS1D, synth.RANGES_1D, device=device).load(cols)
+    step = np.array([2.0, 1.0, 2e-4, 0.02])
+    lo, hi = np.zeros(4), np.zeros(4)
+    hi[3] = 1.0
+    starts = [synth.perturb(synth.TRUTH_1D, step, seed=synth.BASE_SEED + 91, k=i, frac=1.0) for i in range(n_fits)]
+    out = {"n_events": n_events, "fits": n_fits}
+    res = {}
+    for label, strategy in (("quasi_newton", 2), ("newton", 4)):
+        m.fit(starts[0], lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=strategy, hessian=2)  # warm-up
+        times, evals, thetas = [], [], []
+        for th0 in starts:
+            t0 = time.perf_counter()
+            r = m.fit(th0, lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=strategy, hessian=2)
+            times.append(1e3 * (time.perf_counter() - t0))
+            evals.append(r["n_eval"])
+            thetas.append((r["theta"], r["err"], r["status"]))
+        res[label] = thetas
+        out[label] = {"strategy": strategy, "hessian": 2, "p50_ms": float(np.percentile(times, 50)),
+                      "p99_ms": float(np.percentile(times, 99)), "mean_passes": float(np.mean(evals)),
+                      "converged": int(sum(t[2] == 0 for t in thetas))}
+    m.close()
+    diffs = [float(np.max(np.abs(a[0] - b[0]) / b[1])) for a, b in zip(res["newton"], res["quasi_newton"])
+             if a[2] == 0 and b[2] == 0]
+    out["max_abs_diff_over_sigma"] = max(diffs) if diffs else None
+    out["p50_speedup"] = out["quasi_newton"]["p50_ms"] / out["newton"]["p50_ms"]
+    return out
+
+
 def hessian_bench(g, model, theta, flush, stream, reps=5):
     """Analytic Hessian (one pass) against the finite-difference Hessian of the analytic
     gradient (2 n gradient passes) on the bench sample, and full fits using each."""
@@ -672,6 +707,7 @@ def run_ours(args):
     if args.toys > 0:
         toys = toy_fits(g, local, args.toys, args.seq_toys, seed_stream=rank)
     sweep = None if args.no_sweep else mass_sweep(g, local, stream)
+    single_fit = None if args.no_sweep else single_fit_latency(g, local)
     study = None
     if args.study_toys > 0:
         study = toy_study(g, local, args.study_toys)
@@ -706,7 +742,7 @@ def run_ours(args):
                                       "mode": "load() copies the pinned columns, then eval_grad, direct variant"}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 2 * args.steps,
                 "hessian": hess, "capacity_4d": cap, "scale_4d_weighted_1e7": scale, "toy_fits": toys, "serving": served, "toy_study_paper_mass_fit": study,
-                "mass_model_sweep": sweep}
+                "mass_model_sweep": sweep, "single_fit_mass_1e4": single_fit}
         print(json.dumps(line), flush=True)
     model.close()
     if world > 1:

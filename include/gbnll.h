@@ -143,13 +143,19 @@ typedef struct {
                        matrix of every fit from part of its events -- its first 1024 events, or
                        4 x 1024 spread over samples of more than 8192 -- scaled to the whole
                        sample; it only preconditions the quasi-Newton steps (the minimum and,
-                       with hessian 2 / 3, the covariance are those of the whole sample)      */
+                       with hessian 2 / 3, the covariance are those of the whole sample);
+                       4 (fit_minimise): damped Newton steps with the analytic Hessian at every
+                       iterate (one nll_eval_hess pass each, line search included); the
+                       covariance is the inverse Hessian of the final point (sandwich with
+                       hessian 3, any other hessian value acts as 2).  Far fewer passes than
+                       the quasi-Newton route, so faster where a pass is mostly launch latency
+                       (samples of up to ~10^5 events)                                         */
     int hessian;    /* 0: covariance from the quasi-Newton matrix; 1: finite-difference
                        Hessian of the analytic gradient at the minimum plus Newton polish;
                        2: the same with the analytic Hessian, covariance H^-1;
                        3: as 2, covariance H^-1 W H^-1 (weighted fits, see nll_eval_hess).
-                       Values 2 and 3 (and strategy 2) need second derivatives of a model:
-                       fit_minimise_fcn rejects them with NLL_ERR_ARG.  Batched and served fits
+                       Values 2 and 3 (and strategies 2 and 4) need second derivatives of a
+                       model: fit_minimise_fcn rejects them with NLL_ERR_ARG.  Batched and served fits
                        run the analytic passes on the device (see nll_batch_fit; a server queues
                        the start-matrix pass with the first step after admission and polishes
                        at nll_server_poll). */

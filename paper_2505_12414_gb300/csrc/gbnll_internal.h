@@ -193,8 +193,11 @@ struct HArgs {
     double* out;           // [nslots]
     unsigned int* done;    // or NULL: completion words [nslots], set to seq once out[s] is written
     unsigned int seq;
-    uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];  // column pair of each slot
+    // column pair of each slot: sij[s] and sij[kHessMaxSlots + s], a device table of the layout
+    // (hess_slot_table), so that the launch parameters stay small
+    const uint8_t* sij;
 };
+
 
 // The Hessian table's few slots past its last full warp row (tail_count <= kHessTailMax, the
 // same with or without the W slots after them) are summed by the thread that stages each
@@ -207,6 +210,9 @@ struct HessLayout {
 };
 // Slot table for (kind, weighted, with W); returns false if it does not fit.
 bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L);
+// Device copy of a layout's slot table on the current device (uploaded once per device and
+// layout); *out receives its address.
+cudaError_t hess_slot_table(int kind, bool weighted, bool want_w2, const HessLayout& L, const uint8_t** out);
 void hess_fill_const(int kind, const Hoist& H, const double* theta, HConst* c);
 // Assemble from the slot sums; returns the count of events with a non-positive density.
 double hess_assemble(int kind, bool weighted, bool want_w2, const Hoist& H, double sum_wdm, const HessLayout& L,

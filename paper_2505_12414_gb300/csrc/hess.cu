@@ -43,6 +43,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -83,8 +84,8 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 #pragma unroll
     for (int r = 0; r < kHessTailMax; ++r) {
         const int sr = r < tn ? tb + r : 0;
-        tci[r] = a.si[sr] * kHessThreads + t;
-        tcj[r] = a.sj[sr] * kHessThreads + t;
+        tci[r] = a.sij[sr] * kHessThreads + t;
+        tcj[r] = a.sij[kHessMaxSlots + sr] * kHessThreads + t;
         tacc[r] = 0.0;
     }
     int ci[3], cj[3];
@@ -92,8 +93,8 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
     for (int k = 0; k < 3; ++k) {
         const int s = t + k * kHessThreads;
         const int sc = s < ns ? s : 0;
-        ci[k] = a.si[sc];
-        cj[k] = a.sj[sc];
+        ci[k] = a.sij[sc];
+        cj[k] = a.sij[kHessMaxSlots + sc];
     }
     double acc[3] = {0.0, 0.0, 0.0};
     LogProd lp{1.0, 0};  // unweighted: product of this thread's densities
@@ -205,16 +206,19 @@ struct Recorder {
     }
 };
 
+// slot sums by column pair through an inverse table (slot_of[i * 64 + j], 0xffff: none)
 struct Reader {
-    const HessLayout* L;
+    const uint16_t* slot_of;
     const double* sums;
     bool missing = false;
-    __host__ __device__ double operator()(int i, int j)
+    double operator()(int i, int j)
     {
-        for (int s = 0; s < L->nslots; ++s)
-            if (L->si[s] == i && L->sj[s] == j) return sums[s];
-        missing = true;
-        return NAN;
+        const unsigned s = slot_of[i * 64 + j];
+        if (s == 0xffffu) {
+            missing = true;
+            return NAN;
+        }
+        return sums[s];
     }
 };
 
@@ -253,7 +257,7 @@ int ncols_of()
 
 }  // namespace
 
-bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
+static bool hess_layout_build(int kind, bool weighted, bool want_w2, HessLayout* L)
 {
     memset(L, 0, sizeof *L);
     Hoist H;
@@ -277,7 +281,7 @@ bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
     int nh = L->nslots;
     if (want_w2) {
         HessLayout Lh;
-        if (!hess_layout(kind, weighted, false, &Lh)) return false;
+        if (!hess_layout_build(kind, weighted, false, &Lh)) return false;
         nh = Lh.nslots;
     }
     const int r = nh % 32;
@@ -288,10 +292,57 @@ bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
     return !rec.overflow;
 }
 
+namespace {
+__device__ uint8_t g_hsij[8][2 * kHessMaxSlots];  // slot tables by layout key, per device
+std::mutex g_hsij_mutex;
+bool g_hsij_ready[64][8];
+}  // namespace
+
+cudaError_t hess_slot_table(int kind, bool weighted, bool want_w2, const HessLayout& L, const uint8_t** out)
+{
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    const int key = (kind == kMass1D ? 0 : 4) + (weighted ? 2 : 0) + (want_w2 ? 1 : 0);
+    std::lock_guard<std::mutex> lock(g_hsij_mutex);
+    if (!g_hsij_ready[device][key]) {
+        uint8_t t[2 * kHessMaxSlots];
+        memcpy(t, L.si, kHessMaxSlots);
+        memcpy(t + kHessMaxSlots, L.sj, kHessMaxSlots);
+        e = cudaMemcpyToSymbol(g_hsij, t, sizeof t, (size_t)key * sizeof t);
+        if (e != cudaSuccess) return e;
+        g_hsij_ready[device][key] = true;
+    }
+    uint8_t* base = nullptr;
+    e = cudaGetSymbolAddress((void**)&base, g_hsij);
+    if (e != cudaSuccess) return e;
+    *out = base + (size_t)key * 2 * kHessMaxSlots;
+    return cudaSuccess;
+}
+
+// The slot table of (kind, weighted, W) is built once (recording the assembly is quadratic in
+// the slot count) and copied out on every call.
+bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
+{
+    static std::mutex mu;
+    static HessLayout cache[2][2][2];
+    static signed char state[2][2][2];  // 0: not built, 1: built, -1: does not fit
+    const int k = kind == kMass1D ? 0 : 1, w = weighted ? 1 : 0, x = want_w2 ? 1 : 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (state[k][w][x] == 0) state[k][w][x] = hess_layout_build(kind, weighted, want_w2, &cache[k][w][x]) ? 1 : -1;
+    if (state[k][w][x] < 0) return false;
+    *L = cache[k][w][x];
+    return true;
+}
+
 double hess_assemble(int kind, bool weighted, bool want_w2, const Hoist& H, double sum_wdm, const HessLayout& L,
                      const double* sums, double* nll, double* grad, double* hess, double* w2)
 {
-    Reader rd{&L, sums};
+    uint16_t slot_of[64 * 64];
+    memset(slot_of, 0xff, sizeof slot_of);
+    for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * 64 + L.sj[k]] = (uint16_t)k;
+    Reader rd{slot_of, sums};
     double bad = assemble_any(kind, weighted, H, sum_wdm, want_w2, rd, nll, grad, hess, w2);
     return rd.missing ? NAN : bad;
 }
@@ -328,13 +379,47 @@ static size_t hess_smem()
     return (size_t)HCols<KIND, W>::NC * kHessThreads * sizeof(double);
 }
 
+// Per device and kernel instance: the dynamic shared-memory attribute is set once, and the
+// occupancy (resident blocks per SM) is computed once; both cost host API calls that would
+// otherwise add to every pass (small samples are latency-bound).
+constexpr int kHessInstances = 6;
+template <int KIND, int VAR, bool W>
+constexpr int hess_instance()
+{
+    return KIND == kMass1D ? (W ? 1 : 0) : (VAR == kVarDirect ? (W ? 3 : 2) : (W ? 5 : 4));
+}
+namespace {
+std::mutex g_hinst_mutex;
+signed char g_hinst_occ[64][kHessInstances];  // 0: not set up yet; else occupancy + 1 (0 -> error)
+}  // namespace
+
+template <int KIND, int VAR, bool W>
+static int setup_t()
+{
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess || device < 0 || device >= 64) return -1;
+    constexpr int slot = hess_instance<KIND, VAR, W>();
+    std::lock_guard<std::mutex> lock(g_hinst_mutex);
+    signed char& c = g_hinst_occ[device][slot];
+    if (c == 0) {
+        const size_t smem = hess_smem<KIND, VAR, W>();
+        int nb = 0;
+        if (cudaFuncSetAttribute(hess_kernel<KIND, VAR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hess_kernel<KIND, VAR, W>, kHessThreads, smem) !=
+                cudaSuccess)
+            return -1;  // not cached: the next call tries again
+        c = (signed char)std::min(nb + 1, 127);
+    }
+    return c - 1;
+}
+
 template <int KIND, int VAR, bool W>
 static cudaError_t launch_t(int blocks, cudaStream_t s, const HArgs& a)
 {
     const size_t smem = hess_smem<KIND, VAR, W>();
-    cudaError_t e = cudaFuncSetAttribute(hess_kernel<KIND, VAR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    if (setup_t<KIND, VAR, W>() < 0) return cudaErrorInvalidValue;
+    cudaError_t e;
     hess_kernel<KIND, VAR, W><<<blocks, kHessThreads, smem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -353,15 +438,7 @@ static cudaError_t launch_t(int blocks, cudaStream_t s, const HArgs& a)
 template <int KIND, int VAR, bool W>
 static int occ_t()
 {
-    const size_t smem = hess_smem<KIND, VAR, W>();
-    if (cudaFuncSetAttribute(hess_kernel<KIND, VAR, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, hess_kernel<KIND, VAR, W>, kHessThreads, smem) !=
-        cudaSuccess)
-        return 0;
-    return nb;
+    return std::max(setup_t<KIND, VAR, W>(), 0);
 }
 
 namespace {

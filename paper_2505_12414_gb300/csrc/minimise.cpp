@@ -16,7 +16,10 @@
 //     Newton polish steps with it, and the covariance as its inverse;
 //   * or, where the objective supplies them, the analytic Hessian (for the start matrix,
 //     the polish and the covariance) and the weighted-fit sandwich covariance
-//     H^-1 W H^-1, W = sum w^2 s s^T (paper Sec. 2.1 asks for both).
+//     H^-1 W H^-1, W = sum w^2 s s^T (paper Sec. 2.1 asks for both);
+//   * or (strategy 4) damped Newton steps with the analytic Hessian at every iterate, which
+//     takes far fewer passes over the events where a pass with second derivatives costs about
+//     what one without does (small samples, where each pass is launch latency).
 #include "minimise.h"
 
 #include <math.h>
@@ -164,6 +167,152 @@ bool fd_hessian(int n, const std::vector<double>& h, G grad_at, std::vector<doub
     return true;
 }
 
+// Damped Newton minimisation with the analytic Hessian at every iterate (strategy 4).  Each
+// evaluation is one pass that returns f, g and H together; in internal coordinates the
+// Hessian is J H J + diag(dF/dext d2ext/dx2) (sine transform), and the step -H_int^-1 g_int is
+// taken with the Armijo backtracking of the quasi-Newton line search.  Where H_int is not
+// positive definite the step falls back to the scaled gradient -diag(s^2) g.  At convergence
+// (EDM with the exact Hessian below tol_edm) the covariance is the inverse external Hessian
+// of the final point, or the sandwich H^-1 W H^-1 with hessian 3: no further pass is needed.
+// For samples whose evaluations cost about the same with or without second derivatives (small,
+// latency-bound samples) this takes a few passes where the quasi-Newton route takes many.
+struct NewtonPoint {
+    std::vector<double> x, th_free, g_ext, H_ext, W_ext;
+    double f = 0.0;
+};
+
+int newton_minimise(Problem& P, const HessianFn& hess, const fit_options& opt, std::vector<double> x,
+                    const std::vector<double>& sint, const double* theta0, fit_result* out)
+{
+    const int n = P.n, nf = P.nf;
+    const bool sandwich = opt.hessian == 3;
+    std::vector<double> th, gn(n), Hn((size_t)n * n), Wn(sandwich ? (size_t)n * n : 0);  // reused every pass
+    auto eval_at = [&](const std::vector<double>& xi, NewtonPoint& pt) -> int {
+        P.external(xi, th);
+        ++P.n_eval;
+        double f;
+        int st = hess(th.data(), &f, gn.data(), Hn.data(), sandwich ? Wn.data() : nullptr);
+        if (st != NLL_OK) return st;
+        if (!isfinite(f)) return NLL_ERR_NONPOSITIVE_PDF;
+        pt.x = xi;
+        pt.f = f;
+        pt.th_free.resize(nf);
+        pt.g_ext.resize(nf);
+        pt.H_ext.resize((size_t)nf * nf);
+        if (sandwich) pt.W_ext.resize((size_t)nf * nf);
+        for (int i = 0; i < nf; ++i) {
+            pt.th_free[i] = th[P.idx[i]];
+            pt.g_ext[i] = gn[P.idx[i]];
+            if (!isfinite(pt.g_ext[i])) return NLL_ERR_NONPOSITIVE_PDF;
+            for (int j = 0; j < nf; ++j) {
+                pt.H_ext[i * nf + j] = Hn[(size_t)P.idx[i] * n + P.idx[j]];
+                if (sandwich) pt.W_ext[i * nf + j] = Wn[(size_t)P.idx[i] * n + P.idx[j]];
+            }
+        }
+        return NLL_OK;
+    };
+    NewtonPoint cur;
+    int st = eval_at(x, cur);
+    if (st != NLL_OK) {
+        out->status = st;
+        out->n_eval = P.n_eval;
+        return st;
+    }
+    std::vector<double> gi(nf), Hi((size_t)nf * nf), Vi((size_t)nf * nf), p(nf), Vg;
+    double edm = INFINITY;
+    bool converged = false, have_inverse = false;
+    int iter = 0;
+    for (;;) {
+        // internal gradient and Hessian at the current point
+        for (int i = 0; i < nf; ++i) {
+            const double Ji = P.jac(i, cur.x[i]);
+            gi[i] = cur.g_ext[i] * Ji;
+            for (int j = 0; j < nf; ++j) Hi[i * nf + j] = Ji * cur.H_ext[i * nf + j] * P.jac(j, cur.x[j]);
+            const int k = P.idx[i];
+            if (P.bounded[k]) Hi[i * nf + i] += cur.g_ext[i] * (-(P.hi[k] - P.lo[k]) * 0.5 * sin(cur.x[i]));
+        }
+        have_inverse = spd_inverse(nf, Hi.data(), Vi.data());
+        if (have_inverse) {
+            matvec(nf, Vi, gi, Vg);
+            edm = 0.5 * dot(gi, Vg);
+            for (int i = 0; i < nf; ++i) p[i] = -Vg[i];
+        } else {
+            edm = INFINITY;
+            for (int i = 0; i < nf; ++i) p[i] = -sint[i] * sint[i] * gi[i];
+        }
+        converged = have_inverse && edm < opt.tol_edm;
+        if (converged || iter >= opt.max_iter) break;
+        ++iter;
+        const double gp = dot(gi, p);
+        if (!(gp < 0.0)) break;
+        // Armijo backtracking (every trial is a full pass: its Hessian serves the next step)
+        const double c1 = 1e-4;
+        double alpha = 1.0;
+        bool ok = false;
+        NewtonPoint trial;
+        std::vector<double> xn(nf);
+        for (int ls = 0; ls < 40; ++ls) {
+            for (int i = 0; i < nf; ++i) xn[i] = cur.x[i] + alpha * p[i];
+            const int s2 = eval_at(xn, trial);
+            if (s2 == NLL_OK && trial.f <= cur.f + c1 * alpha * gp) {
+                ok = true;
+                break;
+            }
+            double anew;
+            if (s2 == NLL_OK && isfinite(trial.f)) {
+                const double denom = 2.0 * (trial.f - cur.f - gp * alpha);
+                anew = denom > 0.0 ? -gp * alpha * alpha / denom : 0.5 * alpha;
+                anew = std::min(std::max(anew, 0.1 * alpha), 0.5 * alpha);
+            } else {
+                anew = 0.25 * alpha;
+            }
+            alpha = anew;
+        }
+        if (!ok) break;
+        const double fprev = cur.f;
+        cur = trial;
+        // an accepted step that no longer lowers the NLL (its change is below the rounding of
+        // the sum): the exact EDM of this point decides convergence below
+        if (!(cur.f < fprev) && iter > 2) break;
+    }
+    // external covariance at the final point: H^-1, or H^-1 W H^-1 (hessian 3)
+    std::vector<double> C((size_t)nf * nf, 0.0), He_inv((size_t)nf * nf);
+    if (spd_inverse(nf, cur.H_ext.data(), He_inv.data())) {
+        if (sandwich) {
+            std::vector<double> T((size_t)nf * nf, 0.0);
+            for (int i = 0; i < nf; ++i)
+                for (int k = 0; k < nf; ++k)
+                    for (int j = 0; j < nf; ++j) T[i * nf + j] += He_inv[i * nf + k] * cur.W_ext[k * nf + j];
+            for (int i = 0; i < nf; ++i)
+                for (int j = 0; j < nf; ++j) {
+                    double sacc = 0.0;
+                    for (int k = 0; k < nf; ++k) sacc += T[i * nf + k] * He_inv[k * nf + j];
+                    C[i * nf + j] = sacc;
+                }
+        } else {
+            C = He_inv;
+        }
+        std::vector<double> d;
+        matvec(nf, He_inv, cur.g_ext, d);
+        edm = 0.5 * dot(cur.g_ext, d);
+        converged = edm < opt.tol_edm;
+    } else {
+        converged = false;
+    }
+    for (int k = 0; k < n; ++k) out->theta[k] = theta0[k];
+    for (int i = 0; i < nf; ++i) out->theta[P.idx[i]] = cur.th_free[i];
+    for (int i = 0; i < nf; ++i) {
+        for (int j = 0; j < nf; ++j) out->cov[P.idx[i] * n + P.idx[j]] = C[i * nf + j];
+        out->err[P.idx[i]] = sqrt(std::max(C[i * nf + i], 0.0));
+    }
+    out->nll = cur.f;
+    out->edm = edm;
+    out->n_eval = P.n_eval;
+    out->n_iter = iter;
+    out->status = converged ? NLL_OK : NLL_ERR_NOT_CONVERGED;
+    return out->status;
+}
+
 }  // namespace
 
 int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double* lo, const double* hi,
@@ -178,8 +327,8 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
     if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
     if (opt.max_iter <= 0) opt.max_iter = 500;
     memset(out, 0, sizeof(*out));
-    if (n <= 0 || n > FIT_MAXPAR || !theta0 || opt.strategy < 0 || opt.strategy > 2 || opt.hessian < 0 ||
-        opt.hessian > 3 || ((opt.strategy == 2 || opt.hessian >= 2) && !hess)) {
+    if (n <= 0 || n > FIT_MAXPAR || !theta0 || opt.strategy < 0 || opt.strategy > 4 || opt.strategy == 3 ||
+        opt.hessian < 0 || opt.hessian > 3 || ((opt.strategy >= 2 || opt.hessian >= 2) && !hess)) {
         out->status = NLL_ERR_ARG;
         return NLL_ERR_ARG;
     }
@@ -226,6 +375,8 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
         sint[i] = s0[i] / std::max(J, 1e-8);
         if (P.bounded[P.idx[i]]) sint[i] = std::min(sint[i], 0.5);
     }
+    if (opt.strategy == 4) return newton_minimise(P, *hess, opt, x, sint, theta0, out);
+
     double f;
     int st = P.eval_int(x, f, g);
     if (st != NLL_OK) {
@@ -247,7 +398,9 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
         for (int i = 0; i < nf; ++i) th[P.idx[i]] = th_free[i];
         if (Wf) Wn.resize((size_t)n * n);
         ++P.n_eval;
-        if ((*hess)(th.data(), Hn.data(), Wf ? Wn.data() : nullptr) != NLL_OK) return false;
+        double fh;
+        std::vector<double> gh(n);
+        if ((*hess)(th.data(), &fh, gh.data(), Hn.data(), Wf ? Wn.data() : nullptr) != NLL_OK) return false;
         Hf.resize((size_t)nf * nf);
         if (Wf) Wf->resize((size_t)nf * nf);
         for (int i = 0; i < nf; ++i)
@@ -500,7 +653,7 @@ extern "C" int fit_minimise_fcn(fit_fcn fcn, void* user, const double* theta0, c
                                 fit_result* out)
 {
     if (!fcn || !out) return NLL_ERR_ARG;
-    if (opt && (opt->strategy == 2 || opt->hessian >= 2)) {  // needs second derivatives it cannot get
+    if (opt && (opt->strategy == 2 || opt->strategy == 4 || opt->hessian >= 2)) {  // needs second derivatives
         memset(out, 0, sizeof(*out));
         out->status = NLL_ERR_ARG;
         return NLL_ERR_ARG;

@@ -575,8 +575,8 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         a.out = m->d_hout;
         a.done = m->d_hdone;
         a.seq = next_seq(m);
-        memcpy(a.si, L.si, sizeof a.si);
-        memcpy(a.sj, L.sj, sizeof a.sj);
+        cudaError_t et = hess_slot_table(m->kind, m->weighted, want_w2, L, &a.sij);
+        if (et != cudaSuccess) return cuda_fail(m, et, "Hessian slot table");
         int occ = std::min(std::max(hess_occupancy(m->kind, var, m->weighted), 1), kHessMaxBlocksPerSm);
         const int64_t ntiles = (m->n + kHessThreads - 1) / kHessThreads;
         int blocks = (int)std::min<int64_t>(ntiles, (int64_t)m->sm_count * occ);
@@ -911,9 +911,8 @@ int fit_minimise(nll_model* m, const double* theta0, const double* lo, const dou
     Objective obj = [m, n_params](const double* th, double* f, double* g) {
         return nll_eval_grad(m, th, n_params, f, g);
     };
-    HessianFn hs = [m, n_params](const double* th, double* H, double* W) {
-        double f, g[18];
-        return nll_eval_hess(m, th, n_params, &f, g, H, W);
+    HessianFn hs = [m, n_params](const double* th, double* f, double* g, double* H, double* W) {
+        return nll_eval_hess(m, th, n_params, f, g, H, W);
     };
     return bfgs_minimise(obj, n_params, theta0, lo, hi, step, fixed, opt, out, &hs);
 }
