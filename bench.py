@@ -67,8 +67,8 @@ FP64_PEAK_TFLOPS = 1.25
 # of the current kernels (ncu cannot run inside the timed bench).
 KERNEL_TRAFFIC_BYTES = 132.6e6
 KERNEL_TRAFFIC_SOURCE = ("ncu --set full --clock-control none capture of fused_nll_kernel<4D, precompute, grad> "
-                         "(152 x 256) and final_reduce_kernel on the 1M-event 4D sample after an L2 flush: "
-                         "dram__bytes_read.sum + dram__bytes_write.sum")
+                         "(304 x 128) and final_reduce_kernel on the 1M-event 4D sample after an L2 flush: "
+                         "dram__bytes_read.sum + dram__bytes_write.sum (128.57 + 4.03 + 0.03 MB)")
 
 
 def parse():
@@ -242,13 +242,13 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
             "speedup_vs_sequential": (n_toys / dt) / (n_seq_done / seq_t) if seq_t > 0 else None}
 
 
-def serving(g, device, n_req, rate, seed_stream=0):
+def serving(g, device, n_req, rate, seed_stream=0, size_classes=False, max_queued=2, admit_all=True):
     """Poisson-arrival stream of full fits mixing the mass and 4D models, event counts
     log-uniform in [1e3, 1e6]: continuous batching (nll_server_*) against the plain
     one-fit-at-a-time GPU path on the same requests and arrival times, once with
     finite-difference Hessians of the analytic gradient (strategy 1, hessian 1) and once with
     analytic second derivatives (strategy 2, hessian 2)."""
-    from paper_2505_12414_gb300.serve import Request, latency_summary, serve, serve_sequential
+    from paper_2505_12414_gb300.serve import Request, by_kind, by_kind_and_size, latency_summary, serve, serve_sequential
 
     rs = synth.Stream(synth.BASE_SEED + 4242 + seed_stream, 0)
     sizes = np.exp(np.log(1e3) + (np.log(1e6) - np.log(1e3)) * rs.uniform(n_req)).astype(int)
@@ -275,15 +275,32 @@ def serving(g, device, n_req, rate, seed_stream=0):
             lo, hi = np.zeros(len(step[k])), np.zeros(len(step[k]))
             hi[-1] = 1.0
             opts[k] = dict(lo=lo, hi=hi, step=step[k], tol_edm=1e-8, strategy=strategy, hessian=hessian)
-        servers = {k: g.Server(k, ranges[k], 16, 4_000_000 if k == g.NLL_MODEL_MASS1D else 8_000_000, 4096,
-                               device=device, **opts[k]) for k in step}
-        serve(servers, requests()[:2], realtime=False)  # warm-up
+        pool = {g.NLL_MODEL_MASS1D: 4_000_000, g.NLL_MODEL_KSTARMUMU4D: 8_000_000}
+        if size_classes:
+            # one server per model kind and size class: fits of up to 3e4 events get short steps
+            # of their own while the large fits run on the other servers' streams
+            small = 30_000
+            route = by_kind_and_size(small)
+            servers = {}
+            for k in step:
+                servers[(k, True)] = g.Server(k, ranges[k], 16, 16 * small, 1024, device=device, **opts[k])
+                servers[(k, False)] = g.Server(k, ranges[k], 8, pool[k], 4096, device=device, **opts[k])
+        else:
+            route = by_kind
+            servers = {k: g.Server(k, ranges[k], 16, pool[k], 4096, device=device, **opts[k]) for k in step}
+        warm, seen = [], set()
+        for r in requests():  # warm-up: one fit on every server
+            if route(r) not in seen:
+                seen.add(route(r))
+                warm.append(r)
+        serve(servers, warm, realtime=False, route=route)
         phases = {}
-        served = serve(servers, requests(), realtime=True, phases=phases)
+        served = serve(servers, requests(), realtime=True, phases=phases, route=route, max_queued=max_queued,
+                       admit_all=admit_all)
         for srv in servers.values():
             srv.close()
         models = {k: g.Model(k, ranges[k], device=device) for k in step}
-        serve_sequential(models, requests()[:2], opts)  # warm-up
+        serve_sequential(models, warm, opts)  # warm-up
         seq = serve_sequential(models, requests(), opts)
         for m in models.values():
             m.close()
@@ -682,7 +699,7 @@ def run_ours(args):
             if i >= 2:
                 times.append(s0.elapsed_time(s1))
         m2.close()
-        return gd.max_over_ranks(statistics.median(times) if times else float("nan"), device=dev)
+        return gd.max_over_ranks(statistics.median(times), device=dev) if times else None
 
     e2e_step = e2e_run(lambda mm: mm.load(pinned, in_place=True))
     e2e_copy_step = e2e_run(lambda mm: mm.load([t.numpy() for t in pinned], precompute=False))
@@ -732,12 +749,12 @@ def run_ours(args):
                            "blocks_per_sm": launch["blocks_per_sm"], "threads": launch["threads"],
                            "launch_sweep_kernel_ms": launch_sweep,
                            "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas/weak"},
-                "e2e": {"value": world * N_EVENTS / (e2e_step * 1e-3), "unit": "events/s",
+                "e2e": {"value": world * N_EVENTS / (e2e_step * 1e-3) if e2e_step else None, "unit": "events/s",
                         "h2d_bytes_per_step": 4 * 8 * N_EVENTS, "d2h_bytes_per_step": 8 * (k_acc + 2),
                         "ms_per_step": e2e_step,
                         "mode": "in place: the fused kernel reads the pinned host columns over the CPU-GPU "
                                 "link (load(in_place=True) + eval_grad per step)",
-                        "copy_mode": {"value": world * N_EVENTS / (e2e_copy_step * 1e-3),
+                        "copy_mode": {"value": world * N_EVENTS / (e2e_copy_step * 1e-3) if e2e_copy_step else None,
                                       "ms_per_step": e2e_copy_step,
                                       "mode": "load() copies the pinned columns, then eval_grad, direct variant"}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "gpu_launches": 2 * args.steps,

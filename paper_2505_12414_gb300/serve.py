@@ -28,15 +28,37 @@ class Request:
         self.result = None
 
 
-def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phases=None):
-    """Run `requests` (sorted by arrival, seconds from start) through `servers` {kind: Server}.
+def by_kind(request):
+    """Default routing: one server per model kind."""
+    return request.kind
+
+
+def by_kind_and_size(limit):
+    """Routing by model kind and sample size: fits of at most `limit` events go to their own
+    servers, so their steps (which cost about the events of all the fits in a server) stay
+    short while the large fits run on the other servers' streams."""
+
+    def route(request):
+        return (request.kind, len(request.columns[0]) <= limit)
+
+    return route
+
+
+def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phases=None, route=by_kind,
+          admit_all=True):
+    """Run `requests` (sorted by arrival, seconds from start) through `servers` {key: Server},
+    each request going to servers[route(request)].
 
     With realtime=True requests become visible at their arrival times on the wall clock;
     otherwise all are queued at once.  Every server with fits in it gets `steps_per_iter` more
-    steps whenever fewer than `max_queued` of its steps are still in flight.  If `phases` is a
-    dict, the host time spent in admission (submit), step queueing (step), progress queries
-    and collection (poll) is added to it, in seconds, with the number of steps queued.
-    Returns the requests with admitted/done times and results filled in."""
+    steps whenever fewer than `max_queued` of its steps are still in flight; the loop tops the
+    step queues up between single admissions and collections, so that the device keeps
+    working while the host admits and collects.  With admit_all every server takes as many
+    waiting requests as it has room for in each pass of the loop (fits that start together
+    share their steps); otherwise one per pass.  If `phases` is a dict, the host time spent in
+    admission (submit), step queueing (step), progress queries and collection (poll) is added
+    to it, in seconds, with the number of steps queued.  Returns the requests with
+    admitted/done times and results filled in."""
     clock = time.perf_counter
     acc = phases if phases is not None else {}
     for key in ("admit_s", "step_s", "progress_s", "collect_s", "steps"):
@@ -44,14 +66,31 @@ def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phas
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     queues = {k: collections.deque() for k in servers}
     inflight = {k: {} for k in servers}
+    finished = {k: 0 for k in servers}
     left = len(requests)
-    t0 = time.perf_counter()
+    t0 = clock()
+
+    def feed():
+        """Top up the step queues of the servers with fits in them; note finished fits."""
+        for k, srv in servers.items():
+            if not inflight[k]:
+                continue
+            c0 = clock()
+            queued, finished[k] = srv.progress()
+            c1 = clock()
+            acc["progress_s"] += c1 - c0
+            if queued < max_queued:
+                srv.step(steps_per_iter)
+                acc["steps"] += steps_per_iter
+                acc["step_s"] += clock() - c1
+
     while left:
-        now = time.perf_counter() - t0
+        now = clock() - t0
         while pending and (not realtime or pending[0].arrival <= now):
             r = pending.popleft()
-            queues[r.kind].append(r)
-        for k, srv in servers.items():
+            queues[route(r)].append(r)
+        feed()
+        for k, srv in servers.items():  # admissions, feeding the step queues after each
             q = queues[k]
             while q:
                 c0 = clock()
@@ -60,32 +99,25 @@ def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phas
                 if rid is None:
                     break
                 r = q.popleft()
-                r.admitted = time.perf_counter() - t0
+                r.admitted = clock() - t0
                 inflight[k][rid] = r
-        busy = False
+                feed()
+                if not admit_all:
+                    break
         for k, srv in servers.items():
-            if not inflight[k]:
-                continue
-            busy = True
-            c0 = clock()
-            queued, finished = srv.progress()
-            c1 = clock()
-            acc["progress_s"] += c1 - c0
-            if queued < max_queued:
-                srv.step(steps_per_iter)
-                acc["steps"] += steps_per_iter
-            c2 = clock()
-            acc["step_s"] += c2 - c1
-            if finished:
+            if finished[k]:
+                c0 = clock()
                 done = srv.poll()
-                acc["collect_s"] += clock() - c2
+                acc["collect_s"] += clock() - c0
+                finished[k] = 0
                 for rid, res in done:
                     r = inflight[k].pop(rid)
-                    r.done = time.perf_counter() - t0
+                    r.done = clock() - t0
                     r.result = res
                     left -= 1
-        if not busy and pending and realtime:
-            time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
+                feed()
+        if not any(inflight.values()) and pending and realtime:
+            time.sleep(max(0.0, min(pending[0].arrival - (clock() - t0), 0.01)))
     return requests
 
 

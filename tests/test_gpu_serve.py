@@ -211,3 +211,27 @@ def test_cancel_frees_the_slot_and_the_pool_range(gpu_lib):
     assert np.array_equal(res[0][1]["theta"], got[r3]["theta"])
     alone.close()
     s.close()
+
+
+def test_routing_by_size_class_gives_the_same_results(gpu_lib):
+    # each fit's result depends on its own events only: serving the same requests with small
+    # and large fits on separate servers gives the same bits as one server per model kind
+    from paper_2505_12414_gb300.serve import by_kind_and_size, serve
+
+    per_kind = make_requests(8, 9400)
+    srv = servers(gpu_lib, 8, 200000)
+    serve(srv, per_kind, realtime=False)
+    for s_ in srv.values():
+        s_.close()
+    routed = make_requests(8, 9400)
+    route = by_kind_and_size(3000)
+    srv2 = {(k, small): gpu_lib.Server(k, synth.RANGES_1D if k == M1 else synth.RANGES_4D, 8, 200000, 1024, **opts(k))
+            for k in (M1, M4) for small in (True, False)}
+    serve(srv2, routed, realtime=False, route=route)
+    for s_ in srv2.values():
+        s_.close()
+    assert len({route(r) for r in routed}) > 2  # both size classes took fits
+    for a, b in zip(per_kind, routed):
+        assert a.result["status"] == 0 and b.result["status"] == 0
+        assert np.array_equal(a.result["theta"], b.result["theta"])
+        assert np.array_equal(a.result["err"], b.result["err"])
