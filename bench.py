@@ -203,7 +203,7 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
     b.autotune()
     sched = b.get_schedule()
     runs = {}
-    for label, st, hs in (("analytic", 2, 2), ("fd", 1, 1)):
+    for label, st, hs in (("analytic", 2, 2), ("subsample_start", 3, 2), ("fd", 1, 1)):
         b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)  # warm-up (graph instantiation, caches)
         t0 = time.perf_counter()
         r = b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)
@@ -211,6 +211,7 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
     b.close()
     r, dt = runs["analytic"]
     rf, dtf = runs["fd"]
+    r3, dt3 = runs["subsample_start"]
     m = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device)
     seq_t = 0.0
     agree = []
@@ -230,6 +231,12 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
             "second_derivatives": "analytic Hessian pass (strategy 2, hessian 2)",
             "device_steps": r["steps"], "converged": int(np.sum(r["status"] == 0)),
             "mean_evals_per_fit": float(np.mean(r["n_eval"])), "schedule": sched,
+            "subsample_start": {"options": "start matrices from part of every toy's events (strategy 3, hessian 2)",
+                                "batched_fits_per_s": n_toys / dt3, "mean_evals_per_fit": float(np.mean(r3["n_eval"])),
+                                "converged": int(np.sum(r3["status"] == 0)), "device_steps": r3["steps"],
+                                "max_abs_diff_over_sigma_vs_analytic": float(np.max(np.abs(r["theta"] - r3["theta"])[
+                                    (r["status"] == 0) & (r3["status"] == 0)] / r["err"][(r["status"] == 0) &
+                                                                                      (r3["status"] == 0)]))},
             "fd": {"batched_fits_per_s": n_toys / dtf, "mean_evals_per_fit": float(np.mean(rf["n_eval"])),
                    "converged": int(np.sum(rf["status"] == 0)), "device_steps": rf["steps"],
                    "max_abs_diff_over_sigma_vs_analytic": float(np.max(np.abs(r["theta"] - rf["theta"])[both] /
