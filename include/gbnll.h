@@ -149,7 +149,14 @@ typedef struct {
                        covariance is the inverse Hessian of the final point (sandwich with
                        hessian 3, any other hessian value acts as 2).  Far fewer passes than
                        the quasi-Newton route, so faster where a pass is mostly launch latency
-                       (samples of up to ~10^5 events)                                         */
+                       (samples of up to ~10^5 events);
+                       5 (batched and served fits; fit_minimise rejects it): as 2, the start
+                       matrix from an event pass in single precision (staging, slot products
+                       and per-1024-event sums in float, relative error ~1e-6); a start matrix
+                       only preconditions, so the minimum and the covariance (hessian 2 / 3,
+                       always in double precision) are those of strategy 2, while the pass
+                       costs a fraction of the double-precision one.  Unlike 2, the fit loop
+                       evaluates the start point itself (in double precision)            */
     int hessian;    /* 0: covariance from the quasi-Newton matrix; 1: finite-difference
                        Hessian of the analytic gradient at the minimum plus Newton polish;
                        2: the same with the analytic Hessian, covariance H^-1;
@@ -356,7 +363,8 @@ int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, dou
  *                shared_start != 0; lo, hi, step, fixed as fit_minimise (shared by all toys).
  *   opt          tol_edm, max_iter, strategy (1: start from a finite-difference Hessian;
  *                2: from the analytic Hessian of every toy, one batched pass before the
- *                loop; 3: the same pass over part of every toy's events, see fit_options),
+ *                loop; 3: the same pass over part of every toy's events; 5: the same pass
+ *                in single precision; see fit_options),
  *                hessian (1: finite-difference Hessian of the analytic gradient at the
  *                minimum for the covariance; 2: analytic Hessian, covariance H^-1; 3: as 2,
  *                covariance H^-1 W H^-1 for weighted toys -- one batched pass after the loop,
@@ -368,6 +376,21 @@ int nll_batch_eval_grad(nll_batch* b, const double* thetas, double* nll_out, dou
 int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
                   const double* step, const int* fixed, const fit_options* opt, fit_result* results,
                   int* steps_out);
+
+/*
+ * nll_batch_fit_arrays -- nll_batch_fit with the results in plain per-toy arrays instead of
+ * fit_result records (a fit_result holds FIT_MAXPAR-sized fields, over 8 KB per toy): the same
+ * fit, arguments and return value.  Every output is host memory owned by the caller, or NULL
+ * when not wanted:
+ *   theta_out    [n_toys][npar] fitted parameters (fixed ones unchanged);
+ *   err_out      [n_toys][npar] sqrt(diag(cov)), 0 for fixed parameters;
+ *   cov_out      [n_toys][npar][npar] covariance, rows and columns of fixed parameters 0;
+ *   nll_out, edm_out [n_toys]; n_eval_out, n_iter_out, status_out [n_toys] (nll_status).
+ */
+int nll_batch_fit_arrays(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
+                         const double* step, const int* fixed, const fit_options* opt, double* theta_out,
+                         double* err_out, double* cov_out, double* nll_out, double* edm_out, int* n_eval_out,
+                         int* n_iter_out, int* status_out, int* steps_out);
 
 /*
  * nll_batch_eval_hess -- NLL, gradient, analytic Hessian (and optionally W = sum w^2 s s^T)

@@ -114,6 +114,9 @@ def load(path=None):
     L.nll_batch_eval_hess.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int)]
     L.nll_batch_fit.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(fit_options), ctypes.POINTER(fit_result), ctypes.POINTER(ctypes.c_int)]
+    _IPp = ctypes.POINTER(ctypes.c_int)
+    L.nll_batch_fit_arrays.argtypes = [vp, _DP, ctypes.c_int, _DP, _DP, _DP, _IPp, ctypes.POINTER(fit_options),
+                                       _DP, _DP, _DP, _DP, _DP, _IPp, _IPp, _IPp, _IPp]
     L.nll_batch_set_schedule.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.nll_batch_get_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.nll_batch_autotune.argtypes = [vp]
@@ -655,14 +658,22 @@ class Batch:
         th, lo, hi, step, fx = _fit_args(t0.reshape(-1)[: self.npar] if shared else t0[0], lo, hi, step, fixed)
         th = _f64(t0)
         opt = fit_options(tol_edm, max_iter, strategy, hessian)
-        res = np.empty(max(self.n_toys, 1), dtype=_FIT_RESULT_DTYPE)  # filled by the library
+        n, npar = max(self.n_toys, 1), self.npar
+        ip = ctypes.POINTER(ctypes.c_int)
+        out = dict(theta=np.empty((n, npar)), err=np.empty((n, npar)), nll=np.empty(n), edm=np.empty(n),
+                   n_eval=np.empty(n, dtype=np.int32), n_iter=np.empty(n, dtype=np.int32),
+                   status=np.empty(n, dtype=np.int32), cov=np.empty((n, npar, npar)))
         steps = ctypes.c_int()
-        st = load().nll_batch_fit(self.handle, _p(th), shared, _p(lo), _p(hi), _p(step),
-                                  fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt),
-                                  res.ctypes.data_as(ctypes.POINTER(fit_result)), ctypes.byref(steps))
+        st = load().nll_batch_fit_arrays(self.handle, _p(th), shared, _p(lo), _p(hi), _p(step), fx.ctypes.data_as(ip),
+                                         ctypes.byref(opt), _p(out["theta"]), _p(out["err"]), _p(out["cov"]),
+                                         _p(out["nll"]), _p(out["edm"]), out["n_eval"].ctypes.data_as(ip),
+                                         out["n_iter"].ctypes.data_as(ip), out["status"].ctypes.data_as(ip),
+                                         ctypes.byref(steps))
         if st not in (NLL_OK, NLL_ERR_NOT_CONVERGED):
             _bcheck(self.handle, st)
-        return _results_of(res[: self.n_toys], self.npar, steps=steps.value)
+        res = {k: v[: self.n_toys] for k, v in out.items()}
+        res["steps"] = steps.value
+        return res
 
     def set_schedule(self, tile_events=0, blocks_per_sm=0):
         _bcheck(self.handle, load().nll_batch_set_schedule(self.handle, int(tile_events), int(blocks_per_sm)))

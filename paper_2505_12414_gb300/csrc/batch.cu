@@ -66,18 +66,24 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
     double alpha = kind == kMass1D ? th[2] : th[10];
     double f = kind == kMass1D ? th[3] : th[17];
     if (!(sigma > 0.0) || !(f > 0.0 && f < 1.0)) return false;
-    double za = (mu - ma) / (sqrt(2.0) * sigma), zb = (mu - mb) / (sqrt(2.0) * sigma);
+    // the formulas of the host hoisting, with the divisions by the same quantity taken as one
+    // reciprocal each (this chain runs once per toy and step, and FP64 is scarce)
+    const double kInvSqrt2 = 0.70710678118654752440, kInvSqrtPi = 0.56418958354775628695;
+    const double kInvSqrt2Pi = 0.39894228040143267794, kHalfLn2Pi = 0.91893853320467274178;
+    const double inv_s = 1.0 / sigma, r2s = kInvSqrt2 * inv_s;
+    double za = (mu - ma) * r2s, zb = (mu - mb) * r2s;
     double N1 = dev_gauss_norm(za, zb);
     if (!(N1 > 1e-300)) return false;
     double ea = exp(-za * za), eb = exp(-zb * zb);
-    H.dlnN1_dmu = (ea - eb) / (sqrt(2.0 * kPiH) * sigma * N1);
-    H.dlnN1_dsig = -(za * ea - zb * eb) / (sqrt(kPiH) * sigma * N1);
+    const double q = inv_s / N1;  // 1 / (sigma N1)
+    H.dlnN1_dmu = (ea - eb) * (kInvSqrt2Pi * q);
+    H.dlnN1_dsig = -(za * ea - zb * eb) * (kInvSqrtPi * q);
     if (second) {  // second derivatives of ln N1 (as the host hoisting)
-        const double s2 = sigma * sigma;
-        H.d2lnN1[0] = -(za * ea - zb * eb) / (sqrt(kPiH) * s2 * N1) - H.dlnN1_dmu * H.dlnN1_dmu;
-        H.d2lnN1[1] = (ea * (2.0 * za * za - 1.0) - eb * (2.0 * zb * zb - 1.0)) / (sqrt(2.0 * kPiH) * s2 * N1) -
+        const double q2 = q * inv_s;  // 1 / (sigma^2 N1)
+        H.d2lnN1[0] = -(za * ea - zb * eb) * (kInvSqrtPi * q2) - H.dlnN1_dmu * H.dlnN1_dmu;
+        H.d2lnN1[1] = (ea * (2.0 * za * za - 1.0) - eb * (2.0 * zb * zb - 1.0)) * (kInvSqrt2Pi * q2) -
                       H.dlnN1_dmu * H.dlnN1_dsig;
-        H.d2lnN1[2] = 2.0 * (za * ea * (1.0 - za * za) - zb * eb * (1.0 - zb * zb)) / (sqrt(kPiH) * s2 * N1) -
+        H.d2lnN1[2] = 2.0 * (za * ea * (1.0 - za * za) - zb * eb * (1.0 - zb * zb)) * (kInvSqrtPi * q2) -
                       H.dlnN1_dsig * H.dlnN1_dsig;
     }
     double t = alpha * D, Nt2;
@@ -107,22 +113,26 @@ __device__ bool dev_hoist(int kind, const double* ranges, const double* th, KCon
         Nt2 = D;
         H.dlnN2t_dal = 0.5 * D;
     } else {
-        Nt2 = expm1(t) / alpha;
-        if (fabs(t) > 1e-3)
-            H.dlnN2t_dal = D * (-1.0 / expm1(-t) - 1.0 / t);
+        const double em = expm1(t);
+        Nt2 = em / alpha;
+        if (fabs(t) > 1e-3)  // -1/expm1(-t) = 1 + 1/expm1(t)
+            H.dlnN2t_dal = D * ((1.0 + 1.0 / em) - 1.0 / t);
         else
             H.dlnN2t_dal = D * (0.5 + t / 12.0 - t * t * t / 720.0 + t * t * t * t * t / 30240.0);
     }
-    double b0 = 1.0 / (2.0 * sigma * sigma);
-    double lnb1 = log(f) - 0.5 * log(2.0 * kPiH) - log(sigma) - log(N1);
+    double b0 = 0.5 * inv_s * inv_s;
+    double lnb1 = log(f * q) - kHalfLn2Pi;  // ln(f / (sqrt(2 pi) sigma N1))
     double b2 = (1.0 - f) / Nt2;
     if (kind == kKstar4D) {
+        double rprod = 1.0 / kPiH;  // 1 / (pi Nc_0 Nc_1 Nc_2)
         for (int j = 0; j < 3; ++j) {
             double nc = 2.0 - (2.0 / 3.0) * th[12 + 2 * j];
             if (!(nc > 0.0)) return false;
-            H.dlnNc[j] = (-2.0 / 3.0) / nc;
-            b2 /= nc * (j == 2 ? kPiH : 1.0);
+            const double rnc = 1.0 / nc;
+            H.dlnNc[j] = (-2.0 / 3.0) * rnc;
+            rprod *= rnc;
         }
+        b2 *= rprod;
     }
     if (fabs(alpha) * D + fmax(lnb1, 0.0) > 700.0) return false;
     H.mu = mu;
@@ -186,7 +196,9 @@ __device__ bool dev_assemble(int kind, const DConst& H, double sum_wdm, const do
         dL[17] = S[1] / H.f - sre / (1.0 - H.f);
         npar = 18;
     }
-    for (int k = 0; k < npar; ++k) g[k] = -dL[k];
+#pragma unroll
+    for (int k = 0; k < kNP; ++k)
+        if (k < npar) g[k] = -dL[k];
     return isfinite(nll);
 }
 
@@ -246,16 +258,21 @@ __global__ void batch_prepare(BatchDev b)
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= b.n_toys) return;
     ToyFit& F = b.fits[t];
-    for (int s = 0; s < kMaxSlots; ++s) F.item[s] = -1;
-    if (F.phase == kPhDone) return;
+    if (F.phase == kPhDone) {
+        F.nitem = 0;
+        return;
+    }
     const FitConfig& c = b.cfg;
     const int64_t npairs = (b.ev_end[t] - b.ev_begin[t] + 1) / 2;
     double th[kNP];
     for (int k = 0; k < c.npar; ++k) th[k] = F.th[k];
+    int ni = 0;  // item slots written this step
     if (F.phase == kPhInit || F.phase == kPhSearch) {
         for (int i = 0; i < c.nf; ++i) th[c.idx[i]] = to_ext(c, i, F.xt[i]);
         emit_item(b, t, 0, th, npairs);
+        ni = 1;
         if (F.phase == kPhInit && c.strategy == 1) {
+            ni = 1 + 2 * c.nf;
             // stencil in internal coordinates around the start point
             for (int j = 0; j < c.nf; ++j)
                 for (int sgn = 0; sgn < 2; ++sgn) {
@@ -266,7 +283,9 @@ __global__ void batch_prepare(BatchDev b)
                 }
         }
     } else if (F.phase == kPhHess) {
-        // stencil in external coordinates around the minimum
+        // stencil in external coordinates around the minimum (slot 0 unused)
+        F.item[0] = -1;
+        ni = 1 + 2 * c.nf;
         for (int j = 0; j < c.nf; ++j)
             for (int sgn = 0; sgn < 2; ++sgn) {
                 for (int k = 0; k < c.npar; ++k) th[k] = F.th[k];
@@ -274,6 +293,7 @@ __global__ void batch_prepare(BatchDev b)
                 emit_item(b, t, 1 + 2 * j + sgn, th, npairs);
             }
     }
+    F.nitem = ni;
 }
 
 // ---------------------------------------------------------------------------------
@@ -337,48 +357,114 @@ __device__ __forceinline__ double wsum(double v)
     return v;
 }
 
-// inverse of the symmetric positive-definite n x n matrix A (row-major, smem) into Out by a
-// warp: Cholesky A = L L^T (right-looking, lane i owns row i), M = L^-1 (lane j owns column j),
-// Out = M^T M.  Returns false (all lanes) if A is not positive definite.
-__device__ bool warp_spd_inverse(int n, double* A, double* L, double* M, double* Out)
+// inverse of the symmetric positive-definite n x n matrix A (row-major, smem; its upper
+// triangle is read and destroyed) into Out by a warp, with the sweep operator (Beaton 1964;
+// Goodnight, Am. Stat. 33 (1979) 149): sweeping pivot k replaces
+//   A_kk -> -1/A_kk,  A_ik -> A_ik / A_kk (i != k),  A_ij -> A_ij - A_ik A_kj / A_kk (i, j != k),
+// which keeps A symmetric, and after every pivot has been swept A holds -A^-1.  Each lane owns
+// up to kSweepPerLane entries of the upper triangle, so one pivot costs a reciprocal and two
+// FP64 instructions per owned entry (the FP64 pipe is charged per warp instruction, however few
+// lanes take part).  The pivots are the diagonal of the successive Schur complements: a pivot
+// that is not positive and finite means A is not positive definite, and the call returns false
+// (all lanes).
+constexpr int kSweepPerLane = (kNP * (kNP + 1) / 2 + 31) / 32;
+
+__device__ bool warp_spd_inverse(int n, double* A, double* Out)
 {
     const int lane = threadIdx.x & 31;
-    for (int i = 0; i < n * n; i += 32)
-        if (i + lane < n * n) L[i + lane] = 0.0;
+    const int ne = n * (n + 1) / 2;
+    int ei[kSweepPerLane], ej[kSweepPerLane];
+#pragma unroll
+    for (int q = 0; q < kSweepPerLane; ++q) {
+        int idx = lane + 32 * q, i = 0;
+        if (idx < ne) {
+            while (idx >= n - i) idx -= n - i++;
+            ei[q] = i;
+            ej[q] = i + idx;
+        } else {
+            ei[q] = -1;
+            ej[q] = -1;
+        }
+    }
     __syncwarp();
-    bool ok = true;
     for (int k = 0; k < n; ++k) {
-        double d = A[k * n + k];
-        if (!(d > 0.0) || !isfinite(d)) ok = false;
-        double lkk = sqrt(fmax(d, 1e-300));
-        if (lane == k) L[k * n + k] = lkk;
-        if (lane > k && lane < n) L[lane * n + k] = A[lane * n + k] / lkk;
-        __syncwarp();
-        if (lane > k && lane < n)
-            for (int j = k + 1; j <= lane; ++j) A[lane * n + j] -= L[lane * n + k] * L[j * n + k];
-        __syncwarp();
-    }
-    if (!ok) return false;
-    if (lane < n) {
-        const int j = lane;
-        for (int i = 0; i < n; ++i) M[i * n + j] = 0.0;
-        for (int i = j; i < n; ++i) {
-            double s = (i == j) ? 1.0 : 0.0;
-            for (int k = j; k < i; ++k) s -= L[i * n + k] * M[k * n + j];
-            M[i * n + j] = s / L[i * n + i];
+        const double D = A[k * n + k];
+        if (!(D > 0.0) || !isfinite(D)) return false;  // the same value on every lane
+        const double r = frcp(D);  // 3 FP64 instructions where a division takes several more
+        double nv[kSweepPerLane];
+#pragma unroll
+        for (int q = 0; q < kSweepPerLane; ++q) {
+            const int i = ei[q], j = ej[q];
+            nv[q] = 0.0;
+            if (i < 0) continue;
+            const double aij = A[i * n + j];
+            if (i == k && j == k)
+                nv[q] = -r;
+            else if (i == k || j == k)
+                nv[q] = aij * r;
+            else {
+                const double aik = i < k ? A[i * n + k] : A[k * n + i];
+                const double akj = k < j ? A[k * n + j] : A[j * n + k];
+                nv[q] = fma(-aik * r, akj, aij);
+            }
         }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kSweepPerLane; ++q)
+            if (ei[q] >= 0) A[ei[q] * n + ej[q]] = nv[q];
+        __syncwarp();
     }
-    __syncwarp();
-    if (lane < n) {
-        const int i = lane;
-        for (int j = 0; j < n; ++j) {
-            double s = 0.0;
-            for (int k = max(i, j); k < n; ++k) s += M[k * n + i] * M[k * n + j];
-            Out[i * n + j] = s;
-        }
-    }
+#pragma unroll
+    for (int q = 0; q < kSweepPerLane; ++q)
+        if (ei[q] >= 0) Out[ei[q] * n + ej[q]] = Out[ej[q] * n + ei[q]] = -A[ei[q] * n + ej[q]];
     __syncwarp();
     return true;
+}
+
+// The minimiser's first step from its start point x = F.xt (warp per toy): f0 and the free
+// components of the external gradient there (lane i holds component i of g0), the start
+// matrix in F.V when `have` (else diag(step^2) is set).  Records the point, its gradient and
+// EDM and proposes the trial point x + p, p = -V g (phase kPhSearch).  Returns true when the
+// EDM already meets the tolerance; with `defer` (and `have`) it then changes nothing, leaving
+// the start to the fit loop's first step.
+__device__ bool begin_search(const FitConfig& c, ToyFit& F, double f0, double g0, bool have, bool defer, int lane)
+{
+    const int nf = c.nf;
+    const bool mine = lane < nf;
+    const double xi = mine ? F.xt[lane] : 0.0;
+    const double gi = mine ? g0 * jac(c, lane, xi) : 0.0;
+    if (!have && mine)
+        for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? F.sint[lane] * F.sint[lane] : 0.0;
+    __syncwarp();
+    double vg = 0.0;
+    if (mine)
+        for (int j = 0; j < nf; ++j) vg += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, gi, j);
+    else
+        for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, gi, j);
+    const double edm = 0.5 * wsum(mine ? gi * vg : 0.0);
+    const bool met = edm < c.tol_edm;
+    if (defer && met) return true;
+    const double pi = -vg;
+    const double gp = wsum(mine ? gi * pi : 0.0);
+    if (mine) {
+        F.x[lane] = xi;
+        F.g[lane] = gi;
+        F.gext[lane] = g0;
+        F.th[c.idx[lane]] = to_ext(c, lane, xi);
+        F.p[lane] = pi;
+        F.xt[lane] = xi + pi;
+    }
+    if (lane == 0) {
+        F.f = f0;
+        F.first = have ? 0 : 1;
+        F.edm = edm;
+        F.gp = gp;
+        F.alpha = 1.0;
+        F.iter = 1;
+        if (!met) F.phase = kPhSearch;
+    }
+    __syncwarp();
+    return met;
 }
 
 template <int KIND>
@@ -387,7 +473,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
     constexpr int K = KIND == kMass1D ? kAcc1D : kAcc4D;
     __shared__ double s_S[kUpdWarps][32];
     __shared__ double s_g[kUpdWarps][kNP];
-    __shared__ double s_mat[kUpdWarps][4][kNP * kNP];
+    __shared__ double s_mat[kUpdWarps][2][kNP * kNP];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = blockIdx.x * kUpdWarps + wib;
     if (t >= b.n_toys) return;
@@ -401,7 +487,8 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
     double f0 = INFINITY, g0 = 0.0;  // slot 0 (lane-uniform f0; lane i holds component i)
     bool ok0 = false, sten_ok = true;
     int nslots = 0;
-    for (int s = 0; s < kMaxSlots; ++s) {
+    const int ni = F.nitem;
+    for (int s = 0; s < ni; ++s) {
         const int it = F.item[s];
         if (it < 0) continue;
         ++nslots;
@@ -413,18 +500,14 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
         __syncwarp();
         double fv = INFINITY;
         int okv = 0;
-        if (lane == 0) {
+        if (lane == 0) {  // the full external gradient into shared memory
             const DConst dc = b.item_dc[it];
-            double gfull[kNP];
-            if (dc.ok && dev_assemble(c.kind, dc, b.sum_wdm[t], s_S[wib], fv, gfull)) {
-                okv = 1;
-                for (int i = 0; i < nf; ++i) s_g[wib][i] = gfull[c.idx[i]];
-            }
+            if (dc.ok && dev_assemble(c.kind, dc, b.sum_wdm[t], s_S[wib], fv, s_g[wib])) okv = 1;
         }
         __syncwarp();
         fv = __shfl_sync(0xffffffffu, fv, 0);
         okv = __shfl_sync(0xffffffffu, okv, 0);
-        double gi = (mine && okv) ? s_g[wib][lane] : 0.0;
+        double gi = (mine && okv) ? s_g[wib][c.idx[lane]] : 0.0;
         __syncwarp();
         if (s == 0) {
             f0 = fv;
@@ -438,9 +521,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
     if (lane == 0) F.n_eval += nslots;
 
     double* A = s_mat[wib][0];
-    double* Lm = s_mat[wib][1];
-    double* Mm = s_mat[wib][2];
-    double* Out = s_mat[wib][3];
+    double* Out = s_mat[wib][1];
     const double c1 = 1e-4;
     bool finish = false;      // reached the convergence test (go to the Hessian or done)
     int done_status = -1;     // >= 0: toy ends with this status
@@ -449,21 +530,14 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
         if (!ok0) {
             done_status = NLL_ERR_NONPOSITIVE_PDF;
         } else {
-            const double xi = mine ? F.xt[lane] : 0.0;
-            const double Ji = mine ? jac(c, lane, xi) : 0.0;
-            double gi = g0 * Ji;
-            if (mine) {
-                F.x[lane] = xi;
-                F.g[lane] = gi;
-                F.gext[lane] = g0;
-                F.th[c.idx[lane]] = to_ext(c, lane, xi);
-            }
-            if (lane == 0) F.f = f0;
-            // initial inverse Hessian: diag(step^2), or the inverse of the stencil Hessian
+            // initial inverse Hessian: from the analytic Hessian pass, the inverse of the
+            // stencil Hessian, or diag(step^2)
             bool have = false;
             if (c.strategy == 2) {
                 have = F.vset != 0;  // set by the analytic Hessian pass before the first step
             } else if (c.strategy && sten_ok) {
+                const double xi = mine ? F.xt[lane] : 0.0;
+                const double Ji = mine ? jac(c, lane, xi) : 0.0;
                 for (int j = 0; j < nf; ++j) {
                     double h = 0.1 * F.sint[j];
                     if (mine) {
@@ -483,36 +557,12 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
                 if (mine)
                     for (int j = lane + 1; j < nf; ++j) A[lane * nf + j] = A[j * nf + lane];
                 __syncwarp();
-                have = warp_spd_inverse(nf, A, Lm, Mm, Out);
+                have = warp_spd_inverse(nf, A, Out);
                 if (have && mine)
                     for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = Out[lane * nf + j];
+                __syncwarp();
             }
-            if (!have && mine)
-                for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? F.sint[lane] * F.sint[lane] : 0.0;
-            __syncwarp();
-            if (lane == 0) F.first = have ? 0 : 1;
-            __syncwarp();
-            // direction
-            double vg = 0.0;
-            if (mine)
-                for (int j = 0; j < nf; ++j) vg += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, gi, j);
-            else
-                for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, gi, j);
-            double edm = 0.5 * wsum(mine ? gi * vg : 0.0);
-            double pi = -vg;
-            double gp = wsum(mine ? gi * pi : 0.0);
-            if (lane == 0) {
-                F.edm = edm;
-                F.gp = gp;
-                F.alpha = 1.0;
-                F.iter = 1;
-            }
-            if (mine) {
-                F.p[lane] = pi;
-                F.xt[lane] = xi + pi;
-            }
-            if (edm < c.tol_edm) finish = true;
-            else if (lane == 0) F.phase = kPhSearch;
+            finish = begin_search(c, F, f0, g0, have, false, lane);
         }
     } else if (F.phase == kPhSearch) {
         const double f = F.f, alpha = F.alpha, gp = F.gp;
@@ -522,25 +572,28 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
             const double gt = mine ? g0 * jac(c, lane, xt) : 0.0;
             const double si = xt - x, yi = gt - gi_old;
             const double ys = wsum(yi * si), yy = wsum(yi * yi), ss = wsum(si * si);
+            // the lane's row of V in registers: one load and one store per step instead of a
+            // global round trip per product (lanes beyond nf and columns beyond nf hold 0)
+            double vr[kNP];
+#pragma unroll
+            for (int j = 0; j < kNP; ++j) vr[j] = (mine && j < nf) ? F.V[lane * nf + j] : 0.0;
             if (ys > 1e-300 && ys > 1e-12 * sqrt(yy * ss)) {
-                if (F.first && mine)
-                    for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? ys / yy : 0.0;
-                __syncwarp();
+                if (F.first) {
+#pragma unroll
+                    for (int j = 0; j < kNP; ++j) vr[j] = (mine && lane == j) ? ys / yy : 0.0;
+                }
                 double vy = 0.0;
-                if (mine)
-                    for (int j = 0; j < nf; ++j) vy += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, yi, j);
-                else
-                    for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, yi, j);
+#pragma unroll
+                for (int j = 0; j < kNP; ++j) vy += vr[j] * __shfl_sync(0xffffffffu, yi, j);
                 const double yvy = wsum(mine ? yi * vy : 0.0);
                 const double rho = 1.0 / ys;
-                __syncwarp();
-                for (int j = 0; j < nf; ++j) {
+#pragma unroll
+                for (int j = 0; j < kNP; ++j) {
                     const double sj = __shfl_sync(0xffffffffu, si, j), vyj = __shfl_sync(0xffffffffu, vy, j);
-                    if (mine) F.V[lane * nf + j] += rho * ((1.0 + rho * yvy) * si * sj - vy * sj - si * vyj);
+                    if (mine && j < nf) vr[j] += rho * ((1.0 + rho * yvy) * si * sj - vy * sj - si * vyj);
                 }
                 if (lane == 0) F.first = 0;
             }
-            __syncwarp();
             if (mine) {
                 F.x[lane] = xt;
                 F.g[lane] = gt;
@@ -548,12 +601,9 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
                 F.th[c.idx[lane]] = to_ext(c, lane, xt);
             }
             if (lane == 0) F.f = f0;
-            __syncwarp();
             double vg = 0.0;
-            if (mine)
-                for (int j = 0; j < nf; ++j) vg += F.V[lane * nf + j] * __shfl_sync(0xffffffffu, gt, j);
-            else
-                for (int j = 0; j < nf; ++j) (void)__shfl_sync(0xffffffffu, gt, j);
+#pragma unroll
+            for (int j = 0; j < kNP; ++j) vg += vr[j] * __shfl_sync(0xffffffffu, gt, j);
             const double edm = 0.5 * wsum(mine ? gt * vg : 0.0);
             if (lane == 0) F.edm = edm;
             // an accepted step that did not lower the NLL (its change is below the rounding of
@@ -575,9 +625,10 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
                 double pi = -vg;
                 double gpn = wsum(mine ? gt * pi : 0.0);
                 if (!(gpn < 0.0)) {  // not a descent direction: restart from the diagonal
-                    if (mine)
-                        for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = lane == j ? F.sint[lane] * F.sint[lane] : 0.0;
-                    pi = mine ? -F.sint[lane] * F.sint[lane] * gt : 0.0;
+                    const double s2 = mine ? F.sint[lane] * F.sint[lane] : 0.0;
+#pragma unroll
+                    for (int j = 0; j < kNP; ++j) vr[j] = (mine && lane == j) ? s2 : 0.0;
+                    pi = -s2 * gt;
                     gpn = wsum(mine ? gt * pi : 0.0);
                 }
                 if (mine) {
@@ -590,6 +641,12 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
                     F.iter += 1;
                 }
             }
+            if (mine) {
+#pragma unroll
+                for (int j = 0; j < kNP; ++j)
+                    if (j < nf) F.V[lane * nf + j] = vr[j];
+            }
+            __syncwarp();
         } else {
             double anew;
             if (ok0 && isfinite(f0)) {
@@ -620,7 +677,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
             if (mine)
                 for (int j = lane + 1; j < nf; ++j) A[lane * nf + j] = A[j * nf + lane];
             __syncwarp();
-            have = warp_spd_inverse(nf, A, Lm, Mm, Out);
+            have = warp_spd_inverse(nf, A, Out);
         }
         if (have) {
             if (mine)
@@ -682,6 +739,7 @@ __global__ void __launch_bounds__(kUpdWarps * 32) batch_update(BatchDev b)
 struct HessDev {
     int n_toys, mode, want_w2, n_units, nslots, lnp_slot, ncols;
     int subsample;              // the units cover part of each toy's events: scale the sums to all of them
+    int single;                 // start matrices from the single-precision event pass
     int tail_begin, tail_count;  // slots summed while staging (HessLayout)
     int pass;                   // covariance modes: polish pass (0: the loop's final point)
     int* n_polish;              // covariance modes: toys still polishing after this pass (mapped)
@@ -700,22 +758,13 @@ struct HessDev {
     const int* toy_u0;          // per toy: first unit
     const int* toy_nu;          // per toy: units
     double* unit_sums;          // [n_units][nslots]
+    double* tot;                // per toy slot totals, [nslots][n_toys]
+    double* asmb;               // per toy assembly, [kAsmEntries][n_toys]: nll, grad, H, W, bad
     const uint16_t* slot_of;    // [ncols][ncols] -> slot, 0xffff = none
     double* out;                // kHmEval: per toy nll, grad[np], H[np*np], W[np*np]
     int* status;                // kHmEval: per toy
     FitConfig cfg;
     uint8_t si[kHessMaxSlots], sj[kHessMaxSlots];
-};
-
-struct DevSlots {
-    const double* sums;
-    const uint16_t* slot_of;
-    int nc;
-    __device__ double operator()(int i, int j) const
-    {
-        const unsigned s = slot_of[i * nc + j];
-        return s == 0xffffu ? NAN : sums[s];
-    }
 };
 
 // thread per toy: the toy's parameter point and its parameter-only terms
@@ -882,6 +931,85 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
     }
 }
 
+// The same pass in single precision (start matrices only, HessDev::single): staging, slot
+// products and the per-unit sums in float, the unit sums stored as doubles for the (double)
+// totals and assembly.  The ln P column is zero, so the NLL it gives is not the sample's; the
+// start matrix needs H and the gradient only.
+template <int KIND, int VAR, bool W>
+__global__ void __launch_bounds__(kHessThreads) batch_hess32_units(const HessDev h)
+{
+    extern __shared__ float z32[];
+    __shared__ HConst32 s_c;
+    __shared__ float s_tail[kHessTailMax][kHessThreads / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int ns = h.nslots;
+    const int tb = h.tail_begin, tn = h.tail_count;
+    const int ns_rows = (tn > 0 && tb + tn == ns) ? tb : ns;
+    const int w0 = t & ~31;
+    const int nrow = ns_rows > w0 ? min(3, (ns_rows - w0 + kHessThreads - 1) / kHessThreads) : 0;
+    int tci[kHessTailMax], tcj[kHessTailMax];
+#pragma unroll
+    for (int r = 0; r < kHessTailMax; ++r) {
+        const int sr = r < tn ? tb + r : 0;
+        tci[r] = h.si[sr] * kHessThreads + t;
+        tcj[r] = h.sj[sr] * kHessThreads + t;
+    }
+    int ci[3], cj[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int sl = t + k * kHessThreads;
+        const int sc = sl < ns ? sl : 0;
+        ci[k] = h.si[sc];
+        cj[k] = h.sj[sc];
+    }
+    for (int u = blockIdx.x; u < h.n_units; u += gridDim.x) {
+        const int toy = h.unit_toy[u];
+        const bool ok = h.hok[toy] != 0;  // uniform over the block
+        __syncthreads();                  // s_c and z32 of the previous unit are no longer read
+        if (t == 0 && ok) s_c = to_single(h.hc[toy]);
+        HEv ev = h.ev;
+        const int64_t e0 = h.unit_e0[u];
+        ev.n = min(e0 + (int64_t)kHessUnitEvents, h.ev_end[toy]);
+        __syncthreads();
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        float tacc[kHessTailMax] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (ok) {
+            for (int64_t e = e0; e < ev.n; e += kHessThreads) {
+                stage_event32<KIND, VAR, W>(ev, s_c, e + t, z32, t);
+#pragma unroll
+                for (int r = 0; r < kHessTailMax; ++r)
+                    if (r < tn) tacc[r] = fmaf(z32[tci[r]], z32[tcj[r]], tacc[r]);
+                __syncthreads();
+                if (nrow == 1)
+                    tile_slots32<1>(z32, ci, cj, acc, lane);
+                else if (nrow == 2)
+                    tile_slots32<2>(z32, ci, cj, acc, lane);
+                else if (nrow == 3)
+                    tile_slots32<3>(z32, ci, cj, acc, lane);
+                __syncthreads();
+            }
+        }
+        if (tn > 0) {
+#pragma unroll
+            for (int r = 0; r < kHessTailMax; ++r) {
+                float v = tacc[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) s_tail[r][warp] = v;
+            }
+            __syncthreads();
+            if (t < tn)
+                h.unit_sums[(size_t)u * ns + tb + t] =
+                    (double)((s_tail[t][0] + s_tail[t][1]) + (s_tail[t][2] + s_tail[t][3]));
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int sl = t + k * kHessThreads;
+            if (sl < ns && !(sl >= tb && sl < tb + tn)) h.unit_sums[(size_t)u * ns + sl] = (double)acc[k];
+        }
+    }
+}
+
 // Newton polish helpers (warp per toy).  propose: the point th_acc - lam d, halving lam until
 // every bounded parameter stays inside its bounds; reject: halve lam and propose again, or stop
 // at the accepted point once the step is negligible.
@@ -1022,15 +1150,100 @@ __global__ void batch_polish_close(ToyFit* fits, int n, int npar, const int* sel
     }
 }
 
-// warp per toy: slot totals (units in order), assembly, and the mode's matrix work
-// (two warps per block: 37.5 KB of static shared memory for the 18-parameter model)
+// a toy whose sums this pass assembles: selected, still polishing (covariance modes) and at a
+// valid parameter point
+__device__ __forceinline__ bool hess_toy_assembled(const HessDev& h, int t)
+{
+    if (h.sel && !h.sel[t]) return false;
+    if ((h.mode == kHmCov || h.mode == kHmSandwich) && h.fits[t].pol <= 0) return false;
+    return h.hok[t] != 0;
+}
+
+// warp per toy: the toy's slot totals, its units added in order (lanes over slots), stored
+// slot-major so that the assembly reads them coalesced
+__global__ void __launch_bounds__(128) batch_hess_totals(const HessDev h)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (t >= h.n_toys || !hess_toy_assembled(h, t)) return;
+    const int u0 = h.toy_u0[t], nu = h.toy_nu[t];
+    double scale = 1.0;
+    if (h.subsample) {  // events of the toy over events in its units (a start matrix only)
+        int64_t covered = 0;
+        for (int j = 0; j < nu; ++j) covered += min((int64_t)kHessUnitEvents, h.ev_end[t] - h.unit_e0[u0 + j]);
+        if (covered > 0) scale = (double)(h.ev_end[t] - h.ev_begin[t]) / (double)covered;
+    }
+    for (int sl = lane; sl < h.nslots; sl += 32) {
+        double v = 0.0;
+        for (int j = 0; j < nu; ++j) v += h.unit_sums[(size_t)(u0 + j) * h.nslots + sl];
+        h.tot[(size_t)sl * h.n_toys + t] = v * scale;
+    }
+}
+
+// column of an entry-major per-toy array: element i of toy t at p[i * stride]
+struct Strided {
+    double* p;
+    int stride;
+    __device__ double& operator[](int i) const { return p[(size_t)i * stride]; }
+};
+
+// slot totals of the block's 32 toys staged in shared memory ([slot][lane]) and the
+// (column pair -> slot) table after them
+struct StagedSlots {
+    const double* tot;  // this lane's first total; slot s at tot[32 s]
+    const uint16_t* slot_of;
+    int nc;
+    __device__ double operator()(int i, int j) const
+    {
+        const unsigned s = slot_of[i * nc + j];
+        return s == 0xffffu ? NAN : tot[32 * s];
+    }
+};
+
+// dynamic shared memory of batch_hess_assemble: every slot of 32 toys and the slot table
+constexpr size_t kAsmSmem = sizeof(double) * 32 * kHessMaxSlots + sizeof(uint16_t) * 64 * 64;
+
+// a block per 32 toys, thread per toy: NLL, gradient, H (and W) from the totals, the
+// single-sample assembly.  A thread per toy runs each FP64 instruction for 32 toys at once,
+// where a lane per toy would occupy the FP64 pipe for a whole warp instruction per toy; the
+// totals and the slot table are staged in shared memory first (coalesced, independent loads),
+// and the block's kAsmWarps warps take every kAsmWarps-th row of H each (the assembly is
+// bound by instruction issue, not by the FP64 pipe).
+constexpr int kAsmWarps = 4;
+
+template <int KIND, bool W>
+__global__ void __launch_bounds__(kAsmWarps * 32) batch_hess_assemble(const HessDev h)
+{
+    using L = HCols<KIND, W>;
+    constexpr int NP = L::NP;
+    extern __shared__ double sm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = h.n_toys, ns = h.nslots, nc = h.ncols;
+    const int t = blockIdx.x * 32 + lane;
+    const bool use = t < n && hess_toy_assembled(h, t);
+    uint16_t* s_slot = reinterpret_cast<uint16_t*>(sm + 32 * kHessMaxSlots);
+    const int nv = (nc * nc + 7) / 8;  // the table is 64 x 64 entries: whole 16-byte vectors
+    for (int k = threadIdx.x; k < nv; k += kAsmWarps * 32)
+        reinterpret_cast<uint4*>(s_slot)[k] = reinterpret_cast<const uint4*>(h.slot_of)[k];
+#pragma unroll 4
+    for (int sl = warp; sl < ns; sl += kAsmWarps) sm[32 * sl + lane] = use ? h.tot[(size_t)sl * n + t] : 0.0;
+    __syncthreads();
+    if (!use) return;
+    StagedSlots S{sm + lane, s_slot, nc};
+    double* a = h.asmb + t;
+    const double bad = assemble_t<KIND, W>(h.ht[t], h.sum_wdm[t], h.want_w2 != 0, S, Strided{a, n},
+                                           Strided{a + (size_t)n, n}, Strided{a + (size_t)(1 + NP) * n, n},
+                                           Strided{a + (size_t)(1 + NP + NP * NP) * n, n}, warp, kAsmWarps);
+    if (warp == 0) a[(size_t)(1 + NP + 2 * NP * NP) * n] = (bad != 0.0 || !isfinite(a[0])) ? 1.0 : 0.0;
+}
+
+// warp per toy: the mode's matrix work on the assembled pass
+// (two warps per block: 31 KB of static shared memory for the 18-parameter model)
 constexpr int kFinWarps = 2;
 
 template <int KIND, bool W>
 __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDev h)
 {
     constexpr int NPK = KIND == kMass1D ? 4 : 18;
-    __shared__ double s_sum[kFinWarps][kHessMaxSlots];
     __shared__ double s_H[kFinWarps][NPK * NPK];
     __shared__ double s_W[kFinWarps][NPK * NPK];
     __shared__ double s_mat[kFinWarps][4][NPK * NPK];
@@ -1058,24 +1271,19 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
         }
         return;
     }
-    const int u0 = h.toy_u0[t], nu = h.toy_nu[t];
-    double scale = 1.0;
-    if (h.subsample) {  // events of the toy over events in its units (a start matrix only)
-        int64_t covered = 0;
-        for (int j = 0; j < nu; ++j) covered += min((int64_t)kHessUnitEvents, h.ev_end[t] - h.unit_e0[u0 + j]);
-        if (covered > 0) scale = (double)(h.ev_end[t] - h.ev_begin[t]) / (double)covered;
-    }
-    for (int sl = lane; sl < h.nslots; sl += 32) {
-        double v = 0.0;
-        for (int j = 0; j < nu; ++j) v += h.unit_sums[(size_t)(u0 + j) * h.nslots + sl];
-        s_sum[wib][sl] = v * scale;
-    }
-    __syncwarp();
-    if (lane == 0) {
-        DevSlots S{s_sum[wib], h.slot_of, h.ncols};
-        double bad = assemble_t<KIND, W>(h.ht[t], h.sum_wdm[t], h.want_w2 != 0, S, &s_nll[wib], s_g[wib], s_H[wib],
-                                         s_W[wib]);
-        s_bad[wib] = (bad != 0.0 || !isfinite(s_nll[wib])) ? 1 : 0;
+    {
+        const int n = h.n_toys;
+        const double* a = h.asmb + t;
+        for (int k = lane; k < NPK; k += 32) s_g[wib][k] = a[(size_t)(1 + k) * n];
+#pragma unroll 4
+        for (int k = lane; k < NPK * NPK; k += 32) {
+            s_H[wib][k] = a[(size_t)(1 + NPK + k) * n];
+            if (h.want_w2) s_W[wib][k] = a[(size_t)(1 + NPK + NPK * NPK + k) * n];
+        }
+        if (lane == 0) {
+            s_nll[wib] = a[0];
+            s_bad[wib] = a[(size_t)(1 + NPK + 2 * NPK * NPK) * n] != 0.0;
+        }
     }
     __syncwarp();
     const bool bad = s_bad[wib] != 0;
@@ -1117,10 +1325,16 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
             A[lane * nf + lane] += s_g[wib][k] * (-(c.hi[k] - c.lo[k]) * 0.5 * sin(xi));
         }
         __syncwarp();
-        if (warp_spd_inverse(nf, A, Lm, Mm, Out)) {
+        if (warp_spd_inverse(nf, A, Out)) {
             if (mine)
                 for (int j = 0; j < nf; ++j) F.V[lane * nf + j] = Out[lane * nf + j];
             if (lane == 0) F.vset = 1;
+            __syncwarp();
+            // the pass gave the NLL and gradient at the start point as well: the first step is
+            // taken from them here, so that the fit loop starts with the first trial point (a
+            // subsampled or single-precision pass gives estimates only)
+            if (!h.subsample && !h.single)
+                begin_search(c, F, s_nll[wib], mine ? s_g[wib][c.idx[lane]] : 0.0, true, true, lane);
         }
         if (lane == 0) F.n_eval += 1;
         return;
@@ -1134,7 +1348,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
         polish_reject(h, F, lane);
         return;
     }
-    const bool inv = warp_spd_inverse(nf, A, Lm, Mm, Out);
+    const bool inv = warp_spd_inverse(nf, A, Out);
     if (lane == 0) F.n_eval += 1;
     if (!inv) {  // no positive-definite Hessian here: the last covariance stays, stop
         if (lane == 0) F.pol = 0;
@@ -1209,12 +1423,46 @@ cudaError_t launch_hess_units_t(int blocks, cudaStream_t s, const HessDev& h)
     return cudaGetLastError();
 }
 
+template <int KIND, int VAR, bool W>
+cudaError_t launch_hess32_units_t(int blocks, cudaStream_t s, const HessDev& h)
+{
+    const size_t smem = (size_t)HCols<KIND, W>::NC * kHessThreads * sizeof(float);  // below 48 KB
+    batch_hess32_units<KIND, VAR, W><<<blocks, kHessThreads, smem, s>>>(h);
+    return cudaGetLastError();
+}
+
+// the assembly's shared memory exceeds the default 48 KB: allowed once per device (the work
+// arrays of every batch and server are set up through hw_alloc on their device)
+cudaError_t set_assemble_smem()
+{
+    const int v = (int)kAsmSmem;
+    cudaError_t e = cudaFuncSetAttribute(batch_hess_assemble<kMass1D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_hess_assemble<kMass1D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_hess_assemble<kKstar4D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_hess_assemble<kKstar4D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
+    return e;
+}
+
 cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStream_t s, const HessDev& h)
 {
     batch_hess_prep<<<(h.n_toys + 31) / 32, 32, 0, s>>>(h);  // a warp per block: see launch_step
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (h.n_units > 0) {
+    if (h.n_units > 0 && h.single) {
+        if (kind == kMass1D)
+            e = w ? launch_hess32_units_t<kMass1D, kVarPrecompute, true>(unit_blocks, s, h)
+                  : launch_hess32_units_t<kMass1D, kVarPrecompute, false>(unit_blocks, s, h);
+        else if (var == kVarDirect)
+            e = w ? launch_hess32_units_t<kKstar4D, kVarDirect, true>(unit_blocks, s, h)
+                  : launch_hess32_units_t<kKstar4D, kVarDirect, false>(unit_blocks, s, h);
+        else
+            e = w ? launch_hess32_units_t<kKstar4D, kVarPrecompute, true>(unit_blocks, s, h)
+                  : launch_hess32_units_t<kKstar4D, kVarPrecompute, false>(unit_blocks, s, h);
+        if (e != cudaSuccess) return e;
+    } else if (h.n_units > 0) {
         if (kind == kMass1D)
             e = w ? launch_hess_units_t<kMass1D, kVarPrecompute, true>(unit_blocks, s, h)
                   : launch_hess_units_t<kMass1D, kVarPrecompute, false>(unit_blocks, s, h);
@@ -1226,6 +1474,14 @@ cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStr
                   : launch_hess_units_t<kKstar4D, kVarPrecompute, false>(unit_blocks, s, h);
         if (e != cudaSuccess) return e;
     }
+    batch_hess_totals<<<(h.n_toys + 3) / 4, 128, 0, s>>>(h);
+    const int ab = (h.n_toys + 31) / 32, at = kAsmWarps * 32;
+    if (kind == kMass1D)
+        w ? batch_hess_assemble<kMass1D, true><<<ab, at, kAsmSmem, s>>>(h)
+          : batch_hess_assemble<kMass1D, false><<<ab, at, kAsmSmem, s>>>(h);
+    else
+        w ? batch_hess_assemble<kKstar4D, true><<<ab, at, kAsmSmem, s>>>(h)
+          : batch_hess_assemble<kKstar4D, false><<<ab, at, kAsmSmem, s>>>(h);
     const int fb = (h.n_toys + kFinWarps - 1) / kFinWarps;
     if (kind == kMass1D) {
         if (w)
@@ -1330,8 +1586,8 @@ namespace gbnll {
 void hw_free(HessWork& w)
 {
     if (w.staged_pending) cudaEventSynchronize(w.staged_ev);
-    void* ptrs[] = {w.d_unit_toy, w.d_unit_e0, w.d_toy_u0, w.d_toy_nu, w.d_hc, w.d_ht, w.d_hok, w.d_unit_sums,
-                    w.d_slot_of, w.d_thetas, w.d_out, w.d_status, w.d_sel};
+    void* ptrs[] = {w.d_unit_toy, w.d_unit_e0, w.d_toy_u0, w.d_toy_nu, w.d_hc,    w.d_ht,     w.d_hok, w.d_unit_sums,
+                    w.d_tot,      w.d_asm,    w.d_slot_of, w.d_thetas, w.d_out, w.d_status,  w.d_sel};
     for (void* p : ptrs)
         if (p) gb_free(p);
     void* hptrs[] = {w.h_npol, w.h_unit_toy, w.h_unit_e0, w.h_toy_u0, w.h_toy_nu, w.h_sel};
@@ -1355,6 +1611,8 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
     if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_ht, sizeof(HessTerms) * nt);
     if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_hok, sizeof(int) * nt);
     if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_unit_sums, sizeof(double) * kHessMaxSlots * nu);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_tot, sizeof(double) * kHessMaxSlots * nt);
+    if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_asm, sizeof(double) * kAsmEntries * nt);
     if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_slot_of, sizeof(uint16_t) * 64 * 64);
     if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_thetas, sizeof(double) * np * nt);
     if (e == cudaSuccess) e = gb_malloc(w.budget, &w.d_out, sizeof(double) * (1 + np + 2 * np * np) * nt);
@@ -1369,6 +1627,7 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_toy_nu, sizeof(int) * nt, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_sel, sizeof(int) * nt, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.staged_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = set_assemble_smem();
     if (e != cudaSuccess) {
         hw_free(w);
         return e;
@@ -1460,7 +1719,7 @@ cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const s
 
 // One Hessian pass (see HessDev); use_sel restricts it to the toys hw_set_units selected.
 cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int mode, bool want_w2,
-                          const double* thetas, int pass, bool use_sel, bool wait, bool subsample)
+                          const double* thetas, int pass, bool use_sel, bool wait, bool subsample, bool single)
 {
     HessLayout L;
     if (!hess_layout(T.kind, T.weighted, want_w2, &L)) return cudaErrorInvalidValue;
@@ -1486,6 +1745,7 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
     h.sel = use_sel ? w.d_sel : nullptr;
     h.n_units = w.n_units;
     h.subsample = subsample ? 1 : 0;
+    h.single = single && mode == kHmStart ? 1 : 0;
     h.nslots = L.nslots;
     h.lnp_slot = L.lnp_slot;
     h.tail_begin = L.tail_begin;
@@ -1505,6 +1765,8 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
     h.toy_u0 = w.d_toy_u0;
     h.toy_nu = w.d_toy_nu;
     h.unit_sums = w.d_unit_sums;
+    h.tot = w.d_tot;
+    h.asmb = w.d_asm;
     h.slot_of = w.d_slot_of;
     h.out = w.d_out;
     h.status = w.d_status;
@@ -1898,7 +2160,7 @@ namespace gbnll {
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
                   const fit_options& opt)
 {
-    c.strategy = opt.strategy == 3 ? 2 : opt.strategy;  // 2, 3: start matrix from the analytic Hessian pass
+    c.strategy = (opt.strategy == 3 || opt.strategy == 5) ? 2 : opt.strategy;  // 2, 3, 5: start matrix from a Hessian pass
     c.hessian = opt.hessian == 1;       // in-loop finite-difference Hessian; 2/3 run after the loop
     c.max_iter = opt.max_iter;
     c.tol_edm = opt.tol_edm;
@@ -2231,12 +2493,15 @@ int nll_batch_autotune(nll_batch* b)
     return NLL_OK;
 }
 
-int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
-                  const double* step, const int* fixed, const fit_options* opt_in, fit_result* results, int* steps_out)
+// The whole batched fit (nll_batch_fit and nll_batch_fit_arrays): leaves every toy's packed
+// result (kResStride doubles, batch_pack_results) in b->h_res and the configuration in *cfg_out.
+static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
+                          const double* step, const int* fixed, const fit_options* opt_in, int* steps_out,
+                          FitConfig* cfg_out)
 {
     if (!b) return NLL_ERR_ARG;
     if (!b->loaded) return bfail(b, NLL_ERR_STATE, "no toys loaded");
-    if (!theta0 || !results) return bfail(b, NLL_ERR_ARG, "null argument");
+    if (!theta0) return bfail(b, NLL_ERR_ARG, "null argument");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
     fit_options opt;
     if (opt_in)
@@ -2245,8 +2510,8 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         memset(&opt, 0, sizeof opt);
     if (!(opt.tol_edm > 0.0)) opt.tol_edm = 1e-8;
     if (opt.max_iter <= 0) opt.max_iter = 500;
-    if (opt.strategy < 0 || opt.strategy > 3 || opt.hessian < 0 || opt.hessian > 3)
-        return bfail(b, NLL_ERR_ARG, "strategy must be 0..3 and hessian 0..3");
+    if (opt.strategy < 0 || opt.strategy > 5 || opt.strategy == 4 || opt.hessian < 0 || opt.hessian > 3)
+        return bfail(b, NLL_ERR_ARG, "strategy must be 0..3 or 5 and hessian 0..3");
     const int n = b->n_toys, np = b->npar;
     if (n == 0) return NLL_OK;
     BatchDev d = make_dev(b);
@@ -2275,9 +2540,14 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return bcuda(b, e, "fit state set-up");
-    if (opt.strategy == 2) {  // start matrices from the analytic Hessian at every toy's start point
-        int st = run_hess_pass(b, c, kHmStart, false, nullptr);
+    if (opt.strategy == 2 || opt.strategy == 5) {
+        // start matrices from the analytic Hessian at every toy's start point, queued without a
+        // wait (the fit loop follows on the same stream); strategy 5 takes its event pass in
+        // single precision
+        int st = ensure_hess_work(b);
         if (st != NLL_OK) return st;
+        e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false, false, opt.strategy == 5);
+        if (e != cudaSuccess) return bcuda(b, e, "start matrices");
     } else if (opt.strategy == 3) {
         // the same from a subsample of every toy's events, queued without a wait; the unit lists
         // of the whole toys are restored behind it for the later passes
@@ -2360,10 +2630,59 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit results");
+    *cfg_out = c;
+    return NLL_OK;
+}
+
+int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
+                  const double* step, const int* fixed, const fit_options* opt_in, fit_result* results, int* steps_out)
+{
+    if (b && !results) return bfail(b, NLL_ERR_ARG, "null argument");
+    FitConfig c;
+    memset(&c, 0, sizeof c);
+    const int st = batch_fit_core(b, theta0, shared_start, lo, hi, step, fixed, opt_in, steps_out, &c);
+    if (st != NLL_OK || b->n_toys == 0) return st;
     int all = NLL_OK;
-    for (int t = 0; t < n; ++t) {
+    for (int t = 0; t < b->n_toys; ++t) {
         fill_result_packed(b->h_res + (size_t)t * kResStride, c, results[t]);
         if (results[t].status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
+    }
+    return all;
+}
+
+int nll_batch_fit_arrays(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
+                         const double* step, const int* fixed, const fit_options* opt_in, double* theta_out,
+                         double* err_out, double* cov_out, double* nll_out, double* edm_out, int* n_eval_out,
+                         int* n_iter_out, int* status_out, int* steps_out)
+{
+    FitConfig c;
+    memset(&c, 0, sizeof c);
+    const int st = batch_fit_core(b, theta0, shared_start, lo, hi, step, fixed, opt_in, steps_out, &c);
+    if (st != NLL_OK || b->n_toys == 0) return st;
+    const int np = c.npar, nf = c.nf;
+    int all = NLL_OK;
+    for (int t = 0; t < b->n_toys; ++t) {
+        const double* p = b->h_res + (size_t)t * kResStride;
+        const double* tail = p + 2 * kNP + kNP * kNP;
+        if (theta_out) memcpy(theta_out + (size_t)t * np, p, sizeof(double) * np);
+        if (err_out) {
+            double* e = err_out + (size_t)t * np;
+            for (int k = 0; k < np; ++k) e[k] = 0.0;
+            for (int i = 0; i < nf; ++i) e[c.idx[i]] = p[kNP + i];
+        }
+        if (cov_out) {
+            double* v = cov_out + (size_t)t * np * np;
+            memset(v, 0, sizeof(double) * np * np);
+            for (int i = 0; i < nf; ++i)
+                for (int j = 0; j < nf; ++j) v[c.idx[i] * np + c.idx[j]] = p[2 * kNP + i * nf + j];
+        }
+        if (nll_out) nll_out[t] = tail[0];
+        if (edm_out) edm_out[t] = tail[1];
+        if (n_eval_out) n_eval_out[t] = (int)tail[2];
+        if (n_iter_out) n_iter_out[t] = (int)tail[3];
+        const int status = (int)tail[4];
+        if (status_out) status_out[t] = status;
+        if (status != NLL_OK) all = NLL_ERR_NOT_CONVERGED;
     }
     return all;
 }

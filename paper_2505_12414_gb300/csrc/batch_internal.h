@@ -33,6 +33,7 @@ struct DConst {
 struct ToyFit {
     int phase, iter, n_eval, status, first;
     int vset;  // the start matrix V came from the analytic Hessian (strategy 2)
+    int nitem;  // item slots [0, nitem) written by the last prepare (the rest are unused)
     // Newton polish with the analytic Hessian after the loop (hessian 2 / 3)
     int pol;                  // > 0 while polishing
     double lam, f_acc;        // step fraction; NLL at the accepted point
@@ -86,6 +87,10 @@ constexpr int kHessUnitEvents = 1024;  // 8 shared-memory tiles: several waves o
 
 enum HessMode : int { kHmEval = 0, kHmStart = 1, kHmCov = 2, kHmSandwich = 3 };
 
+// per toy, the assembled Hessian pass (stored entry-major, [entry][toy]): nll, grad[NP],
+// H[NP x NP], W[NP x NP], the non-positive-density count
+constexpr int kAsmEntries = 2 + kNP + 2 * kNP * kNP;
+
 // doubles per toy of a packed result: th[npar] | err[nf] | cov[nf x nf] | nll, edm, n_eval, n_iter, status
 constexpr int kResStride = 2 * kNP + kNP * kNP + 5;
 
@@ -104,6 +109,8 @@ struct HessWork {
     HessTerms* d_ht = nullptr;
     int* d_hok = nullptr;
     double* d_unit_sums = nullptr;
+    double* d_tot = nullptr;   // slot totals per toy
+    double* d_asm = nullptr;   // assembled NLL, gradient, H, W per toy
     uint16_t* d_slot_of = nullptr;
     double* d_thetas = nullptr;
     double* d_out = nullptr;
@@ -149,8 +156,10 @@ cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const s
 // With wait, returns once the pass has finished; without, once it is queued on T.stream.
 // subsample: the unit lists cover part of each toy's events (hw_set_units with subsample); the
 // slot sums are scaled by events / events covered before the assembly (start matrices only).
+// single: the event pass in single precision (start matrices only).
 cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int mode, bool want_w2,
-                          const double* thetas, int pass, bool use_sel, bool wait = true, bool subsample = false);
+                          const double* thetas, int pass, bool use_sel, bool wait = true, bool subsample = false,
+                          bool single = false);
 // Newton polish passes with the analytic Hessian at the final points of the finished toys.
 cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel);
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,

@@ -56,6 +56,7 @@ struct nll_server {
     FitConfig cfg;
     int hessian = 0;  // fit_options.hessian: 2 / 3 polish finished slots with the analytic Hessian
     bool subsample_start = false;  // strategy 3: start matrices from a subsample of each fit's events
+    bool single_start = false;     // strategy 5: start matrices from a single-precision event pass
     HessWork hw;      // start passes (strategy 2), on the step stream
     HessWork hwp;     // polish passes (hessian 2 / 3), on the collection stream
     // admission statistics on the device (range check, sum (m - ma)) of a request's events
@@ -245,7 +246,8 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
 {
     if (!out) return NLL_ERR_ARG;
     *out = nullptr;
-    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 3 || opt_in->hessian < 0 || opt_in->hessian > 3))
+    if (opt_in && (opt_in->strategy < 0 || opt_in->strategy > 5 || opt_in->strategy == 4 || opt_in->hessian < 0 ||
+                   opt_in->hessian > 3))
         return NLL_ERR_ARG;
     if ((kind != NLL_MODEL_MASS1D && kind != NLL_MODEL_KSTARMUMU4D) || !obs_ranges || max_slots < 1 ||
         pool_events < 1 || tile_events < 0 || (tile_events > 0 && (tile_events < 128 || (tile_events & 1))))
@@ -289,6 +291,7 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     setup_config(s->cfg, s->npar, lo, hi, step, fixed, opt);
     s->hessian = opt.hessian;
     s->subsample_start = opt.strategy == 3;
+    s->single_start = opt.strategy == 5;
     s->step.assign(s->npar, 0.0);
     for (int k = 0; k < s->npar; ++k) s->step[k] = step ? step[k] : 0.0;
     // pool: padded so a range of even length starting on an even event can end anywhere
@@ -463,7 +466,7 @@ int nll_server_step(nll_server* s, int n_steps)
         cudaError_t e = server_pick(s, s->hw, pick, s->stream, false, s->subsample_start);
         if (e == cudaSuccess)
             e = run_hess_core(server_target(s, s->stream), s->hw, s->cfg, kHmStart, false, nullptr, 0, true, false,
-                              s->subsample_start);
+                              s->subsample_start, s->single_start);
         if (e != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "start Hessians: %s", cudaGetErrorString(e));
         for (int i = 0; i < s->max_slots; ++i)
             if (pick[i]) s->need_start[i] = 0;

@@ -214,3 +214,61 @@ def test_device_loop_reports_its_steps(gpu_lib):
                hessian=0)
     assert r1["steps"] <= 1 * 40 + 8
     b.close()
+
+
+@pytest.mark.parametrize("kind,precompute,weighted",
+                         [(M1, True, False), (M1, True, True), (M4, True, False), (M4, False, True)])
+def test_single_precision_start_matrices_reach_the_same_minima(gpu_lib, kind, precompute, weighted):
+    """strategy 5 (start matrices from the single-precision event pass) only changes the
+    quasi-Newton path: the polished minima and covariances equal those of strategy 2, in every
+    instance of the single-precision pass (mass and 4D, basis stored or recomputed, weights)."""
+    n_toys, mean = (64, 2000.0) if kind == M1 else (48, 3000.0)
+    if kind == M1:
+        off, cols = synth.toys1d(n_toys, mean, seed=synth.BASE_SEED + 57)
+    else:
+        off, cols = synth.toys4d(n_toys, mean, seed=synth.BASE_SEED + 57)
+    w = synth.weights(int(off[-1]), stream=58) if weighted else None
+    step = scale_of(kind)
+    npar = len(step)
+    lo, hi = np.zeros(npar), np.zeros(npar)
+    hi[-1] = 1.0
+    mkind = gpu_lib.NLL_MODEL_MASS1D if kind == M1 else gpu_lib.NLL_MODEL_KSTARMUMU4D
+    b = gpu_lib.Batch(mkind, ranges_of(kind)).load(off, cols, weights=w, precompute=precompute)
+    r2 = b.fit(truth_of(kind), lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=2, hessian=2)
+    r5 = b.fit(truth_of(kind), lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=5, hessian=2)
+    b.close()
+    ok = (r2["status"] == 0) & (r5["status"] == 0)
+    assert ok.mean() > 0.98
+    assert np.max(np.abs(r5["theta"][ok] - r2["theta"][ok]) / r2["err"][ok]) < 1e-6
+    np.testing.assert_allclose(r5["err"][ok], r2["err"][ok], rtol=1e-6)
+    # the single-precision start matrix is as good a preconditioner: at most one more
+    # evaluation per fit on average (strategy 2 takes its first step from the pass itself)
+    assert np.mean(r5["n_eval"]) <= np.mean(r2["n_eval"]) + 1.5
+
+
+def test_record_and_array_results_agree(gpu_lib):
+    """nll_batch_fit (fit_result records) and nll_batch_fit_arrays (what Batch.fit calls) run the
+    same fit: identical results, fixed parameters' rows and columns zero."""
+    import ctypes
+    off, cols = synth.toys1d(40, 1500.0, seed=synth.BASE_SEED + 59)
+    b = gpu_lib.Batch(gpu_lib.NLL_MODEL_MASS1D, synth.RANGES_1D).load(off, cols)
+    step = scale_of(M1)
+    lo, hi = np.zeros(4), np.zeros(4)
+    hi[3] = 1.0
+    fixed = np.array([0, 0, 1, 0], dtype=np.int32)
+    ra = b.fit(synth.TRUTH_1D, lo=lo, hi=hi, step=step, fixed=fixed, tol_edm=1e-12, strategy=2, hessian=2)
+    th, lo2, hi2, step2, fx = gpu_lib._fit_args(np.asarray(synth.TRUTH_1D, dtype=np.float64), lo, hi, step, fixed)
+    rec = np.zeros(40, dtype=gpu_lib._FIT_RESULT_DTYPE)
+    steps = ctypes.c_int()
+    opt = gpu_lib.fit_options(1e-12, 500, 2, 2)
+    st = gpu_lib.load().nll_batch_fit(b.handle, gpu_lib._p(np.ascontiguousarray(synth.TRUTH_1D, dtype=np.float64)), 1,
+                                      gpu_lib._p(lo2), gpu_lib._p(hi2), gpu_lib._p(step2),
+                                      fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt),
+                                      rec.ctypes.data_as(ctypes.POINTER(gpu_lib.fit_result)), ctypes.byref(steps))
+    b.close()
+    assert st == gpu_lib.NLL_OK and steps.value == ra["steps"]
+    rr = gpu_lib._results_of(rec, 4)
+    for k in ("theta", "err", "nll", "edm", "n_eval", "n_iter", "status", "cov"):
+        np.testing.assert_array_equal(rr[k], ra[k], err_msg=k)
+    assert np.all(ra["err"][:, 2] == 0.0) and np.all(ra["cov"][:, 2, :] == 0.0) and np.all(ra["cov"][:, :, 2] == 0.0)
+    assert np.all(ra["theta"][:, 2] == synth.TRUTH_1D[2])
