@@ -386,6 +386,9 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
  *   err_out      [n_toys][npar] sqrt(diag(cov)), 0 for fixed parameters;
  *   cov_out      [n_toys][npar][npar] covariance, rows and columns of fixed parameters 0;
  *   nll_out, edm_out [n_toys]; n_eval_out, n_iter_out, status_out [n_toys] (nll_status).
+ * Where the device can write every given output (pinned or managed memory, or ordinary host
+ * memory on a system with pageable-memory access such as Grace-Blackwell) and status_out is
+ * given, the last kernel of the fit writes them in place; otherwise the host unpacks them.
  */
 int nll_batch_fit_arrays(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
                          const double* step, const int* fixed, const fit_options* opt, double* theta_out,

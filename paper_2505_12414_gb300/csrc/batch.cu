@@ -1104,6 +1104,48 @@ __global__ void __launch_bounds__(128) batch_init_fits(ToyFit* fits, int n, cons
     if (threadIdx.x == 0) init_fit_fields(fits[t], c, shared ? th0 : th0 + (size_t)t * c.npar, step);
 }
 
+// The results of nll_batch_fit_arrays, written by the device straight into the caller's
+// arrays (block per toy; each toy's rows are contiguous), laid out as that call documents.
+struct ArrayOut {
+    double* theta;
+    double* err;
+    double* cov;
+    double* nll;
+    double* edm;
+    int* n_eval;
+    int* n_iter;
+    int* status;
+};
+
+__global__ void __launch_bounds__(128) batch_write_arrays(const ToyFit* fits, int n, const FitConfig c, ArrayOut o)
+{
+    __shared__ int s_inv[kNP];  // parameter -> free index, -1 for a fixed one
+    const int t = blockIdx.x;
+    if (t >= n) return;
+    const ToyFit& F = fits[t];
+    const int np = c.npar, nf = c.nf;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) s_inv[k] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) s_inv[c.idx[i]] = i;
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        if (o.theta) o.theta[(size_t)t * np + k] = F.th[k];
+        if (o.err) o.err[(size_t)t * np + k] = s_inv[k] >= 0 ? F.err[s_inv[k]] : 0.0;
+    }
+    if (o.cov)
+        for (int q = threadIdx.x; q < np * np; q += blockDim.x) {
+            const int ia = s_inv[q / np], ib = s_inv[q % np];
+            o.cov[(size_t)t * np * np + q] = (ia >= 0 && ib >= 0) ? F.cov[ia * nf + ib] : 0.0;
+        }
+    if (threadIdx.x == 0) {
+        if (o.nll) o.nll[t] = F.f;
+        if (o.edm) o.edm[t] = F.edm;
+        if (o.n_eval) o.n_eval[t] = F.n_eval;
+        if (o.n_iter) o.n_iter[t] = F.iter;
+        if (o.status) o.status[t] = F.phase == kPhDone ? F.status : NLL_ERR_NOT_CONVERGED;
+    }
+}
+
 // Results of every toy packed for the host (block per toy), kResStride doubles each:
 // th[npar] | err[nf] | cov[nf x nf] (free parameters) | nll, edm, n_eval, n_iter, status.
 __global__ void __launch_bounds__(128) batch_pack_results(const ToyFit* fits, const int* idx, int n, int np, int nf,
@@ -2493,11 +2535,28 @@ int nll_batch_autotune(nll_batch* b)
     return NLL_OK;
 }
 
+// memory that kernels on the batch's device can write: its own device memory, pinned or
+// managed memory, or ordinary host memory where the device has pageable-memory access
+static bool device_writable(nll_batch* b, const void* p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice) return at.device == b->device;
+    if (at.type == cudaMemoryTypeManaged || at.type == cudaMemoryTypeHost) return true;
+    int pageable = 0;
+    cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, b->device);
+    return at.type == cudaMemoryTypeUnregistered && pageable != 0;
+}
+
 // The whole batched fit (nll_batch_fit and nll_batch_fit_arrays): leaves every toy's packed
-// result (kResStride doubles, batch_pack_results) in b->h_res and the configuration in *cfg_out.
+// result (kResStride doubles, batch_pack_results) in b->h_res, or with `direct` writes the
+// results into those arrays from the device; the configuration goes to *cfg_out.
 static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, const double* lo, const double* hi,
                           const double* step, const int* fixed, const fit_options* opt_in, int* steps_out,
-                          FitConfig* cfg_out)
+                          FitConfig* cfg_out, const ArrayOut* direct)
 {
     if (!b) return NLL_ERR_ARG;
     if (!b->loaded) return bfail(b, NLL_ERR_STATE, "no toys loaded");
@@ -2626,7 +2685,10 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
         e = polish_core(target_of(b), b->hw, c, opt.hessian, false);
         if (e != cudaSuccess) return bcuda(b, e, "Newton polish");
     }
-    batch_pack_results<<<n, 128, 0, b->stream>>>(b->d_fits, nullptr, n, np, nf, b->d_res);
+    if (direct)
+        batch_write_arrays<<<n, 128, 0, b->stream>>>(b->d_fits, n, c, *direct);
+    else
+        batch_pack_results<<<n, 128, 0, b->stream>>>(b->d_fits, nullptr, n, np, nf, b->d_res);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit results");
@@ -2640,7 +2702,7 @@ int nll_batch_fit(nll_batch* b, const double* theta0, int shared_start, const do
     if (b && !results) return bfail(b, NLL_ERR_ARG, "null argument");
     FitConfig c;
     memset(&c, 0, sizeof c);
-    const int st = batch_fit_core(b, theta0, shared_start, lo, hi, step, fixed, opt_in, steps_out, &c);
+    const int st = batch_fit_core(b, theta0, shared_start, lo, hi, step, fixed, opt_in, steps_out, &c, nullptr);
     if (st != NLL_OK || b->n_toys == 0) return st;
     int all = NLL_OK;
     for (int t = 0; t < b->n_toys; ++t) {
@@ -2657,8 +2719,22 @@ int nll_batch_fit_arrays(nll_batch* b, const double* theta0, int shared_start, c
 {
     FitConfig c;
     memset(&c, 0, sizeof c);
-    const int st = batch_fit_core(b, theta0, shared_start, lo, hi, step, fixed, opt_in, steps_out, &c);
+    // where the device can write every output (pinned, managed, or -- on a system with
+    // pageable-memory access such as the Grace-Blackwell link -- ordinary host memory) the
+    // results go there directly; else they are unpacked on the host from the packed buffer
+    ArrayOut o{theta_out, err_out, cov_out, nll_out, edm_out, n_eval_out, n_iter_out, status_out};
+    bool direct = b && status_out;
+    const void* outs[8] = {theta_out, err_out, cov_out, nll_out, edm_out, n_eval_out, n_iter_out, status_out};
+    for (int k = 0; k < 8 && direct; ++k)
+        if (outs[k]) direct = device_writable(b, outs[k]);
+    const int st = batch_fit_core(b, theta0, shared_start, lo, hi, step, fixed, opt_in, steps_out, &c,
+                                  direct ? &o : nullptr);
     if (st != NLL_OK || b->n_toys == 0) return st;
+    if (direct) {
+        for (int t = 0; t < b->n_toys; ++t)
+            if (status_out[t] != NLL_OK) return NLL_ERR_NOT_CONVERGED;
+        return NLL_OK;
+    }
     const int np = c.npar, nf = c.nf;
     int all = NLL_OK;
     for (int t = 0; t < b->n_toys; ++t) {

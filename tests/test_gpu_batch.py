@@ -265,7 +265,18 @@ def test_record_and_array_results_agree(gpu_lib):
                                       gpu_lib._p(lo2), gpu_lib._p(hi2), gpu_lib._p(step2),
                                       fx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(opt),
                                       rec.ctypes.data_as(ctypes.POINTER(gpu_lib.fit_result)), ctypes.byref(steps))
+    # the host-unpack route of nll_batch_fit_arrays (taken without status_out)
+    th_h, err_h, cov_h = np.zeros((40, 4)), np.zeros((40, 4)), np.zeros((40, 4, 4))
+    nll_h = np.zeros(40)
+    ip = ctypes.POINTER(ctypes.c_int)
+    st2 = gpu_lib.load().nll_batch_fit_arrays(b.handle, gpu_lib._p(np.ascontiguousarray(synth.TRUTH_1D, dtype=np.float64)),
+                                              1, gpu_lib._p(lo2), gpu_lib._p(hi2), gpu_lib._p(step2), fx.ctypes.data_as(ip),
+                                              ctypes.byref(opt), gpu_lib._p(th_h), gpu_lib._p(err_h), gpu_lib._p(cov_h),
+                                              gpu_lib._p(nll_h), None, None, None, None, None)
     b.close()
+    assert st2 == gpu_lib.NLL_OK
+    for got, k in ((th_h, "theta"), (err_h, "err"), (cov_h, "cov"), (nll_h, "nll")):
+        np.testing.assert_array_equal(got, ra[k], err_msg="host unpack " + k)
     assert st == gpu_lib.NLL_OK and steps.value == ra["steps"]
     rr = gpu_lib._results_of(rec, 4)
     for k in ("theta", "err", "nll", "edm", "n_eval", "n_iter", "status", "cov"):
