@@ -152,7 +152,7 @@ typedef struct {
                        (samples of up to ~10^5 events);
                        5 (batched and served fits; fit_minimise rejects it): as 2, the start
                        matrix from an event pass in single precision (staging, slot products
-                       and per-1024-event sums in float, relative error ~1e-6); a start matrix
+                       and per-512-event sums in float, relative error ~1e-6); a start matrix
                        only preconditions, so the minimum and the covariance (hessian 2 / 3,
                        always in double precision) are those of strategy 2, while the pass
                        costs a fraction of the double-precision one.  Unlike 2, the fit loop

@@ -220,11 +220,15 @@ __device__ __forceinline__ double jac(const FitConfig& c, int i, double x)
 // ---------------------------------------------------------------------------------
 // prepare: one thread per toy
 // ---------------------------------------------------------------------------------
+// event pairs per work unit this step (0: one unit per item)
+__device__ __forceinline__ int step_tile(const BatchDev& b) { return (b.tile_pairs && b.step_tp) ? *b.step_tp : b.tile_pairs; }
+
 __device__ void emit_item(const BatchDev& b, int toy, int slot, const double* th, int64_t npairs)
 {
     ToyFit& F = b.fits[toy];
     int nt = 0;
-    if (npairs > 0) nt = b.tile_pairs ? (int)((npairs + b.tile_pairs - 1) / b.tile_pairs) : 1;
+    const int tp = step_tile(b);
+    if (npairs > 0) nt = tp ? (int)((npairs + tp - 1) / tp) : 1;
     KConst kc;
     DConst dc;
     memset(&kc, 0, sizeof kc);
@@ -310,6 +314,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
     for (int j = threadIdx.x; j < ntab; j += blockDim.x) s_tab[j] = g_btab[j];
     __syncthreads();
     const int nunits = min(b.counters[1], b.max_units);
+    const int tp = step_tile(b);
     while (true) {
         if (threadIdx.x == 0) s_u = atomicAdd(&b.counters[2], 1);
         __syncthreads();
@@ -322,9 +327,9 @@ __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
         const int64_t ev_end = b.ev_end[toy];
         const int64_t p_first = b.ev_begin[toy] / 2, p_last = (ev_end + 1) / 2;
         int64_t pb = p_first, pe = p_last;
-        if (b.tile_pairs) {
-            pb = p_first + (int64_t)tile * b.tile_pairs;
-            pe = min(pb + (int64_t)b.tile_pairs, p_last);
+        if (tp) {
+            pb = p_first + (int64_t)tile * tp;
+            pe = min(pb + (int64_t)tp, p_last);
         }
         double acc[K];
 #pragma unroll
@@ -1578,12 +1583,23 @@ cudaError_t ensure_btab(int device)
 // End of one iteration of the device-resident fit loop (a while node of the fit graph): count
 // the step and continue while some toy is still fitting and the step limit is not reached.
 // One thread: the condition is set once per iteration.
-__global__ void batch_loop_control(cudaGraphConditionalHandle handle, const int* n_active, int* steps, int max_steps)
+// The tile of the next step: the schedule's, or a quarter of it once at most a quarter of the
+// toys are still fitting (a unit of the schedule's tile keeps one SM busy for ~15 us of FP64
+// work, so a few toys' units would leave most SMs idle).
+__global__ void batch_loop_control(cudaGraphConditionalHandle handle, const int* n_active, int* steps, int max_steps,
+                                   int* step_tp, int n_toys, int base_tp)
 {
     const int s = *steps + 1;
     *steps = s;
     const int active = *(volatile const int*)n_active;
+    *step_tp = (4 * active <= n_toys) ? max(base_tp / 4, 64) : base_tp;  // 64: the smallest tile the work arrays are sized for
     cudaGraphSetConditional(handle, (active > 0 && s < max_steps) ? 1u : 0u);
+}
+
+__global__ void batch_loop_init(int* steps, int* step_tp, int base_tp)
+{
+    *steps = 0;
+    *step_tp = base_tp;
 }
 
 // One device step of the batched fit loop on stream s (for graph capture): reset the work
@@ -1685,18 +1701,25 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
 // get no units (sel empty: every toy).  Fails if the units exceed the capacity.  The lists go
 // through pinned staging; with wait the call returns once they are on the device, without it
 // as soon as the copies are queued (the staging is reused only after they have completed).
-// units of a toy with `total` units that a subsampled pass takes: the first unit of a sample of
-// up to 8 units, else 4 units spread evenly over the sample (so that a sample stored in some
-// order still contributes from its whole range)
+// units of a toy with `total` units that a subsampled pass takes: the first 1024 events of a
+// sample of up to 8192, else four 1024-event blocks spread evenly over the sample (so that a
+// sample stored in some order still contributes from its whole range); at most kSubsampleMax
+constexpr int kSubsampleBlock = 1024 / kHessUnitEvents;  // units per 1024-event block
+constexpr int kSubsampleMax = 4 * kSubsampleBlock;
+static_assert(1024 % kHessUnitEvents == 0, "1024-event blocks of whole units");
 static int subsample_units(int64_t total, int64_t* pick)
 {
     if (total <= 0) return 0;
-    if (total <= 8) {
-        pick[0] = 0;
-        return 1;
+    int k = 0;
+    if (total <= 8 * kSubsampleBlock) {
+        for (int j = 0; j < kSubsampleBlock && j < total; ++j) pick[k++] = j;
+        return k;
     }
-    for (int k = 0; k < 4; ++k) pick[k] = k * total / 4;
-    return 4;
+    for (int q = 0; q < 4; ++q) {
+        const int64_t start = q * (total / 4);
+        for (int j = 0; j < kSubsampleBlock && start + j < total; ++j) pick[k++] = start + j;
+    }
+    return k;
 }
 
 cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const std::vector<int64_t>& end,
@@ -1708,7 +1731,7 @@ cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const s
     for (int t = 0; t < n; ++t)
         if (sel.empty() || sel[t]) {
             const int64_t total = (std::max<int64_t>(end[t] - begin[t], 0) + kHessUnitEvents - 1) / kHessUnitEvents;
-            int64_t pick[4];
+            int64_t pick[kSubsampleMax];
             nu += subsample ? subsample_units(total, pick) : total;
         }
     if (nu > w.cap_units) return cudaErrorInvalidValue;
@@ -1725,7 +1748,7 @@ cudaError_t hw_set_units(HessWork& w, const std::vector<int64_t>& begin, const s
         if (!sel.empty() && !sel[t]) continue;
         if (subsample) {
             const int64_t total = (std::max<int64_t>(end[t] - begin[t], 0) + kHessUnitEvents - 1) / kHessUnitEvents;
-            int64_t pick[4];
+            int64_t pick[kSubsampleMax];
             const int k = subsample_units(total, pick);
             for (int j = 0; j < k; ++j) {
                 w.h_unit_toy[u] = t;
@@ -2297,7 +2320,7 @@ int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t c
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = ensure_btab(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_counters, sizeof(int) * 4);
+    if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_counters, sizeof(int) * 8);  // items, units, next, steps, tile
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_active, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_active, b->h_active, 0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
@@ -2628,6 +2651,8 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
     const int max_steps = opt.max_iter * 40 + 8;  // every line-search trial is one step
     const int shape[4] = {eval_blocks, max_steps, 0, variant_of(b)};
     int* d_steps = b->d_counters + 3;
+    int* d_step_tp = b->d_counters + 4;
+    d.step_tp = d_step_tp;
     if (!b->fit_exec || memcmp(&b->fit_dev, &d, sizeof d) != 0 || memcmp(b->fit_shape, shape, sizeof shape) != 0) {
         if (b->fit_exec) cudaGraphExecDestroy(b->fit_exec);
         if (b->fit_graph) cudaGraphDestroy(b->fit_graph);
@@ -2653,7 +2678,8 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
             if (e == cudaSuccess) {
                 cudaError_t ec = launch_step(d, variant_of(b), b->weighted, eval_blocks, b->stream);
                 if (ec == cudaSuccess) {
-                    batch_loop_control<<<1, 1, 0, b->stream>>>(handle, d.n_active, d_steps, max_steps);
+                    batch_loop_control<<<1, 1, 0, b->stream>>>(handle, d.n_active, d_steps, max_steps, d_step_tp,
+                                                              n, d.tile_pairs);
                     ec = cudaGetLastError();
                 }
                 e = cudaStreamEndCapture(b->stream, &body);
@@ -2671,7 +2697,8 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
         memcpy(b->fit_shape, shape, sizeof shape);
     }
     int steps = 0;
-    e = cudaMemsetAsync(d_steps, 0, sizeof(int), b->stream);
+    batch_loop_init<<<1, 1, 0, b->stream>>>(d_steps, d_step_tp, d.tile_pairs);
+    e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaGraphLaunch(b->fit_exec, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&steps, d_steps, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);

@@ -61,6 +61,8 @@ struct FitConfig {
 
 struct BatchDev {
     int n_toys, tile_pairs;        // tile_pairs = 0: one unit per item
+    const int* step_tp;            // or NULL: the tile of this step (a device step of the fit loop
+                                   // shrinks it once few toys are left), in place of tile_pairs
     const int64_t* ev_begin;       // per toy, even
     const int64_t* ev_end;         // per toy, exclusive
     const double* sum_wdm;         // per toy: sum w (m - ma)
@@ -83,7 +85,8 @@ struct BatchDev {
 
 
 // analytic Hessian pass over the toys (paper Sec. 2.1)
-constexpr int kHessUnitEvents = 1024;  // 8 shared-memory tiles: several waves of units even for small toys
+constexpr int kHessUnitEvents = 512;  // 4 shared-memory tiles: the units of 1000 toys of 2000 events
+                                       // spread over the SMs within 4 % (1024: 7 %)
 
 enum HessMode : int { kHmEval = 0, kHmStart = 1, kHmCov = 2, kHmSandwich = 3 };
 
