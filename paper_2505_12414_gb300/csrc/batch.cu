@@ -776,6 +776,9 @@ struct HessDev {
 __global__ void batch_hess_prep(HessDev h)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    // covariance modes: the count of toys that propose another polish step restarts with every
+    // pass (the host reads it after the last pass it queued)
+    if (t == 0 && (h.mode == kHmCov || h.mode == kHmSandwich)) *h.n_polish = 0;
     if (t >= h.n_toys) return;
     if (h.sel && !h.sel[t]) {
         h.hok[t] = 0;
@@ -1606,13 +1609,24 @@ __global__ void batch_loop_init(int* steps, int* step_tp, int base_tp)
 // counters, prepare (hoisting of every active toy's points), evaluate, update.
 cudaError_t launch_step(const BatchDev& d, int var, bool weighted, int eval_blocks, cudaStream_t s)
 {
+    cudaError_t e = launch_step_eval(d, var, weighted, eval_blocks, s);
+    return e == cudaSuccess ? launch_step_update(d, s) : e;
+}
+
+// The first part of a step: counters reset, prepare, evaluate.
+cudaError_t launch_step_eval(const BatchDev& d, int var, bool weighted, int eval_blocks, cudaStream_t s)
+{
     cudaError_t e = cudaMemsetAsync(d.counters, 0, sizeof(int) * 3, s);
     if (e != cudaSuccess) return e;
     // one warp per block: each toy's hoisting is a long dependent FP64 chain, so the warps go
     // to different SMs instead of sharing one SM's FP64 pipe
     batch_prepare<<<(d.n_toys + 31) / 32, 32, 0, s>>>(d);
-    e = launch_eval(d.cfg.kind, var, weighted, eval_blocks, s, d);
-    if (e != cudaSuccess) return e;
+    return launch_eval(d.cfg.kind, var, weighted, eval_blocks, s, d);
+}
+
+// The second part: every toy's minimiser advances.
+cudaError_t launch_step_update(const BatchDev& d, cudaStream_t s)
+{
     const int ub = (d.n_toys + kUpdWarps - 1) / kUpdWarps;
     if (d.cfg.kind == kMass1D)
         batch_update<kMass1D><<<ub, kUpdWarps * 32, 0, s>>>(d);
@@ -1840,7 +1854,8 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
     memcpy(h.sj, L.sj, sizeof h.sj);
     static_assert(sizeof(HessDev) <= 4096, "kernel parameters");
     const int occ = hess_occupancy(T.kind, T.variant, T.weighted);
-    const int unit_blocks = std::max(1, std::min(w.n_units, T.sm_count * std::max(1, std::min(occ, 4))));
+    const int bps = std::max(1, std::min(occ, T.max_bps > 0 ? T.max_bps : 4));
+    const int unit_blocks = std::max(1, std::min(w.n_units, T.sm_count * bps));
     e = launch_hess_pass(T.kind, T.variant, T.weighted, unit_blocks, T.stream, h);
     if (e == cudaSuccess && wait) e = cudaStreamSynchronize(T.stream);
     return e;
@@ -1854,10 +1869,13 @@ cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, 
     const int* sel = use_sel ? w.d_sel : nullptr;
     batch_polish_init<<<tb, 128, 0, T.stream>>>(T.d_fits, T.n_toys, sel);
     cudaError_t e = cudaGetLastError();
+    // passes 0 and 1 are queued back to back (nearly every batch has some toy that takes a
+    // Newton step after pass 0, and a pass over no polishing toy costs little); from then on the
+    // host looks at the count after each pass
     for (int pass = 0; pass < 6 && e == cudaSuccess; ++pass) {
-        *(volatile int*)w.h_npol = 0;
-        e = run_hess_core(T, w, cfg, hessian == 3 ? kHmSandwich : kHmCov, hessian == 3, nullptr, pass, use_sel);
-        if (e == cudaSuccess && *(volatile int*)w.h_npol == 0) break;
+        const bool wait = pass >= 1;
+        e = run_hess_core(T, w, cfg, hessian == 3 ? kHmSandwich : kHmCov, hessian == 3, nullptr, pass, use_sel, wait);
+        if (e == cudaSuccess && wait && __atomic_load_n(w.h_npol, __ATOMIC_ACQUIRE) == 0) break;
     }
     if (e == cudaSuccess) {
         batch_polish_close<<<tb, 128, 0, T.stream>>>(T.d_fits, T.n_toys, cfg.npar, sel);
@@ -1904,6 +1922,8 @@ struct nll_batch {
     double* d_init = nullptr;  // start points [n_toys x npar] then steps [npar]
     double* h_res = nullptr;   // mapped pinned, kResStride doubles per toy (batch_pack_results)
     double* d_res = nullptr;
+    cudaStream_t aux_stream = nullptr;  // start-matrix passes that run beside the loop's first step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // the instantiated device step of nll_batch_fit and the parameters it was captured with
     cudaGraph_t fit_graph = nullptr;
     cudaGraphExec_t fit_exec = nullptr;
@@ -2320,6 +2340,9 @@ int nll_batch_create(int kind, const double* obs_ranges, int device, uintptr_t c
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, device);
     cudaError_t e = ensure_btab(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = gb_malloc(&b->budget, &b->d_counters, sizeof(int) * 8);  // items, units, next, steps, tile
     if (e == cudaSuccess) e = cudaHostAlloc(&b->h_active, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&b->d_active, b->h_active, 0);
@@ -2344,6 +2367,9 @@ void nll_batch_destroy(nll_batch* b)
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->aux_stream) cudaStreamDestroy(b->aux_stream);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     delete b;
 }
 
@@ -2622,24 +2648,50 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return bcuda(b, e, "fit state set-up");
-    if (opt.strategy == 2 || opt.strategy == 5) {
+    int* d_steps = b->d_counters + 3;
+    int* d_step_tp = b->d_counters + 4;
+    d.step_tp = d_step_tp;
+    batch_loop_init<<<1, 1, 0, b->stream>>>(d_steps, d_step_tp, d.tile_pairs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bcuda(b, e, "fit loop set-up");
+    int steps_before = 0;  // steps run ahead of the loop's graph
+    if (opt.strategy == 2) {
         // start matrices from the analytic Hessian at every toy's start point, queued without a
-        // wait (the fit loop follows on the same stream); strategy 5 takes its event pass in
-        // single precision
+        // wait (the fit loop follows on the same stream); the pass takes each toy's first step
         int st = ensure_hess_work(b);
         if (st != NLL_OK) return st;
-        e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false, false, opt.strategy == 5);
+        e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false);
         if (e != cudaSuccess) return bcuda(b, e, "start matrices");
-    } else if (opt.strategy == 3) {
-        // the same from a subsample of every toy's events, queued without a wait; the unit lists
-        // of the whole toys are restored behind it for the later passes
+    } else if (opt.strategy == 3 || opt.strategy == 5) {
+        // Start matrices that give no NLL and gradient at the start point (from a subsample of
+        // every toy's events, strategy 3, or in single precision, strategy 5): the pass runs on
+        // the auxiliary stream beside the loop's first step, whose evaluation of the start points
+        // (FP64 bound) overlaps the pass (bound by single-precision and shared-memory work, or
+        // short); the step's update waits for the start matrices.  The pass takes at most two
+        // blocks per SM, so that the evaluation's blocks find room.
         int st = ensure_hess_work(b);
         if (st != NLL_OK) return st;
-        e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->stream, false, true);
-        if (e == cudaSuccess)
-            e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false, true);
-        if (e == cudaSuccess) e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->stream, false, false);
+        HessTarget Ta = target_of(b);
+        Ta.stream = b->aux_stream;
+        Ta.max_bps = 2;
+        e = cudaEventRecord(b->ev_fork, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux_stream, b->ev_fork, 0);
+        if (e == cudaSuccess) e = launch_step_eval(d, variant_of(b), b->weighted, b->sm_count * b->bps, b->stream);
+        if (opt.strategy == 3) {
+            // the subsample's unit lists, then the whole toys' lists again for the later passes
+            if (e == cudaSuccess)
+                e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->aux_stream, false, true);
+            if (e == cudaSuccess) e = run_hess_core(Ta, b->hw, c, kHmStart, false, nullptr, 0, false, false, true);
+            if (e == cudaSuccess)
+                e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->aux_stream, false, false);
+        } else if (e == cudaSuccess) {
+            e = run_hess_core(Ta, b->hw, c, kHmStart, false, nullptr, 0, false, false, false, true);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->aux_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+        if (e == cudaSuccess) e = launch_step_update(d, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "start matrices");
+        steps_before = 1;
     }
 
     // The fit loop runs on the device: a CUDA graph with one while node whose body is a device
@@ -2650,9 +2702,6 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
     const int eval_blocks = b->sm_count * b->bps;
     const int max_steps = opt.max_iter * 40 + 8;  // every line-search trial is one step
     const int shape[4] = {eval_blocks, max_steps, 0, variant_of(b)};
-    int* d_steps = b->d_counters + 3;
-    int* d_step_tp = b->d_counters + 4;
-    d.step_tp = d_step_tp;
     if (!b->fit_exec || memcmp(&b->fit_dev, &d, sizeof d) != 0 || memcmp(b->fit_shape, shape, sizeof shape) != 0) {
         if (b->fit_exec) cudaGraphExecDestroy(b->fit_exec);
         if (b->fit_graph) cudaGraphDestroy(b->fit_graph);
@@ -2697,13 +2746,11 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
         memcpy(b->fit_shape, shape, sizeof shape);
     }
     int steps = 0;
-    batch_loop_init<<<1, 1, 0, b->stream>>>(d_steps, d_step_tp, d.tile_pairs);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaGraphLaunch(b->fit_exec, b->stream);
+    e = cudaGraphLaunch(b->fit_exec, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&steps, d_steps, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bcuda(b, e, "fit loop");
-    if (steps_out) *steps_out = steps;
+    if (steps_out) *steps_out = steps + steps_before;
     if (opt.hessian >= 2) {
         // analytic Hessian at every toy's final point: covariance, EDM, and Newton polish steps
         // (each pass evaluates the toys still polishing) until no toy proposes another step

@@ -135,6 +135,7 @@ struct HessWork {
 // The sample and fit states a Hessian pass works on.
 struct HessTarget {
     int kind, variant, sm_count, n_toys;
+    int max_bps;  // event-pass blocks per SM at most (0: as many as fit, up to 4)
     bool weighted;
     HEv ev;
     const int64_t* d_begin;
@@ -175,6 +176,8 @@ cudaError_t ensure_btab(int device);
 cudaError_t launch_eval(int kind, int var, bool w, int blocks, cudaStream_t s, const BatchDev& b);
 // One device step (counter reset, prepare, evaluate, update) on stream s, for graph capture.
 cudaError_t launch_step(const BatchDev& d, int var, bool weighted, int eval_blocks, cudaStream_t s);
+cudaError_t launch_step_eval(const BatchDev& d, int var, bool weighted, int eval_blocks, cudaStream_t s);
+cudaError_t launch_step_update(const BatchDev& d, cudaStream_t s);
 // Results of n toys packed for the host, kResStride doubles each: toys idx[0..n) (device
 // array), or 0 .. n-1 when idx is NULL.
 cudaError_t launch_pack_results(const ToyFit* fits, const int* idx, int n, int np, int nf, double* res,
