@@ -191,9 +191,12 @@ def cpu_baseline(cols, seconds=10.0, seconds_1t=5.0):
 def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
     """Batched device-resident fits of n_toys 4D toys (Poisson(2000) events, generated from
     truth) against the plain one-fit-at-a-time GPU path; fits/s by wall clock of the
-    synchronous calls (generation excluded).  Primary: analytic second derivatives (start
-    matrix and covariance from the analytic Hessian pass, strategy 2 / hessian 2); beside it
-    the same batch with finite-difference Hessians of the analytic gradient (1 / 1)."""
+    synchronous calls (generation excluded), the median of five timed fits.  Primary: analytic
+    second derivatives (start matrix and covariance from the analytic Hessian pass, strategy 2 /
+    hessian 2); beside it the start matrices from part of every toy's events (strategy 3) or
+    from a single-precision pass (strategy 5), and finite-difference Hessians of the analytic
+    gradient (1 / 1).  Strategies 2 and 5 are also run at EDM 1e-14, where two fits of the same
+    sample agree to 1e-6 of the uncertainty, to show that they reach the same minima."""
     off, cols = synth.toys4d(n_toys, 2000.0, seed=synth.BASE_SEED + seed_stream)
     lo, hi = np.zeros(18), np.zeros(18)
     hi[17] = 1.0
@@ -203,15 +206,27 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
     b.autotune()
     sched = b.get_schedule()
     runs = {}
-    for label, st, hs in (("analytic", 2, 2), ("subsample_start", 3, 2), ("fd", 1, 1)):
+    for label, st, hs, reps in (("analytic", 2, 2, 5), ("subsample_start", 3, 2, 5), ("single_precision_start", 5, 2, 5),
+                                ("fd", 1, 1, 2)):
         b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)  # warm-up (graph instantiation, caches)
-        t0 = time.perf_counter()
-        r = b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)
-        runs[label] = (r, time.perf_counter() - t0)
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = b.fit(synth.TRUTH_4D, strategy=st, hessian=hs, **base)
+            ts.append(time.perf_counter() - t0)
+        runs[label] = (r, statistics.median(ts))
+    tight = {st: b.fit(synth.TRUTH_4D, strategy=st, hessian=2, **dict(base, tol_edm=1e-14)) for st in (2, 5)}
     b.close()
     r, dt = runs["analytic"]
     rf, dtf = runs["fd"]
     r3, dt3 = runs["subsample_start"]
+    r5, dt5 = runs["single_precision_start"]
+    ok_t = (tight[2]["status"] == 0) & (tight[5]["status"] == 0)
+
+    def vs_analytic(rx):
+        both = (r["status"] == 0) & (rx["status"] == 0)
+        return float(np.max(np.abs(r["theta"] - rx["theta"])[both] / r["err"][both])) if np.any(both) else None
+
     m = g.Model(g.NLL_MODEL_KSTARMUMU4D, synth.RANGES_4D, device=device)
     seq_t = 0.0
     agree = []
@@ -234,9 +249,20 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
             "subsample_start": {"options": "start matrices from part of every toy's events (strategy 3, hessian 2)",
                                 "batched_fits_per_s": n_toys / dt3, "mean_evals_per_fit": float(np.mean(r3["n_eval"])),
                                 "converged": int(np.sum(r3["status"] == 0)), "device_steps": r3["steps"],
-                                "max_abs_diff_over_sigma_vs_analytic": float(np.max(np.abs(r["theta"] - r3["theta"])[
-                                    (r["status"] == 0) & (r3["status"] == 0)] / r["err"][(r["status"] == 0) &
-                                                                                      (r3["status"] == 0)]))},
+                                "max_abs_diff_over_sigma_vs_analytic": vs_analytic(r3)},
+            "single_precision_start": {
+                "options": "start matrices from a single-precision pass of the analytic Hessian (strategy 5, "
+                           "hessian 2); minimiser, covariance and polish in double precision",
+                "batched_fits_per_s": n_toys / dt5, "mean_evals_per_fit": float(np.mean(r5["n_eval"])),
+                "converged": int(np.sum(r5["status"] == 0)), "device_steps": r5["steps"],
+                "max_abs_diff_over_sigma_vs_analytic": vs_analytic(r5),
+                "at_edm_1e-14": {"max_abs_diff_over_sigma_vs_analytic": float(np.max(
+                    np.abs(tight[5]["theta"] - tight[2]["theta"])[ok_t] / tight[2]["err"][ok_t])),
+                    "max_rel_err_diff_vs_analytic": float(np.max(np.abs(tight[5]["err"][ok_t] /
+                                                                        tight[2]["err"][ok_t] - 1.0))),
+                    "converged_both": int(np.sum(ok_t))}},
+            "tolerance_note": "fits stop at EDM 1e-8, within sqrt(2e-8) = 1.4e-4 of the uncertainty of the minimum, "
+                              "so two routes differ by up to that much; at EDM 1e-14 they agree to 1e-6",
             "fd": {"batched_fits_per_s": n_toys / dtf, "mean_evals_per_fit": float(np.mean(rf["n_eval"])),
                    "converged": int(np.sum(rf["status"] == 0)), "device_steps": rf["steps"],
                    "max_abs_diff_over_sigma_vs_analytic": float(np.max(np.abs(r["theta"] - rf["theta"])[both] /
