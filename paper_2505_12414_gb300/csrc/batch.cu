@@ -846,25 +846,28 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
 {
     extern __shared__ double z[];
     __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
+    constexpr int TM = HessTailMax<KIND>::value;
     __shared__ HConst s_c;
     __shared__ double s_lnp[kHessThreads / 32];
-    __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
+    __shared__ double s_tred[(kHessThreads / 32) * TM];
+    __shared__ uint8_t s_ti[TM], s_tj[TM];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_btab[j];
     const int ns = h.nslots;
-    // tail slots [tb, tb + tn): summed by each event's staging thread (as in hess_kernel)
+    // tail slots [tb, tb + tn): summed by each event's staging thread (as in hess_kernel; the
+    // mass model's whole table)
     const int tb = h.tail_begin, tn = h.tail_count;
+    if (t < TM) {
+        const int sr = t < tn ? tb + t : 0;
+        s_ti[t] = h.si[sr];
+        s_tj[t] = h.sj[sr];
+    }
     const int ns_rows = (tn > 0 && tb + tn == ns) ? tb : ns;
     const int w0 = t & ~31;
     const int nrow = ns_rows > w0 ? min(3, (ns_rows - w0 + kHessThreads - 1) / kHessThreads) : 0;
-    int tci[kHessTailMax], tcj[kHessTailMax];
-#pragma unroll
-    for (int r = 0; r < kHessTailMax; ++r) {
-        const int sr = r < tn ? tb + r : 0;
-        tci[r] = h.si[sr] * kHessThreads + t;
-        tcj[r] = h.sj[sr] * kHessThreads + t;
-    }
+    const int ls = h.lnp_slot;
+    const bool lnp_in_tail = ls >= tb && ls < tb + tn;
     int ci[3], cj[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -883,22 +886,27 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
         ev.n = min(e0 + (int64_t)kHessUnitEvents, h.ev_end[toy]);
         __syncthreads();
         double acc[3] = {0.0, 0.0, 0.0};
-        double tacc[kHessTailMax] = {0.0, 0.0, 0.0, 0.0};
+        double tacc[TM];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) tacc[r] = 0.0;
         LogProd lp{1.0, 0};
+        double lnp_tot = 0.0;
         if (ok) {
             for (int64_t e = e0; e < ev.n; e += kHessThreads) {
                 stage_event<KIND, VAR, W>(ev, s_c, e + t, z, t, s_tab, lp);
 #pragma unroll
-                for (int r = 0; r < kHessTailMax; ++r)  // this thread's own event, just staged
-                    if (r < tn) tacc[r] = fma(z[tci[r]], z[tcj[r]], tacc[r]);
-                __syncthreads();
-                if (nrow == 1)
-                    tile_slots<1>(z, ci, cj, acc, lane);
-                else if (nrow == 2)
-                    tile_slots<2>(z, ci, cj, acc, lane);
-                else if (nrow == 3)
-                    tile_slots<3>(z, ci, cj, acc, lane);
-                __syncthreads();
+                for (int r = 0; r < TM; ++r)  // this thread's own event, just staged
+                    if (r < tn) tacc[r] = fma(z[s_ti[r] * kHessThreads + t], z[s_tj[r] * kHessThreads + t], tacc[r]);
+                if (ns_rows > 0) {  // the tile's warp rows read every thread's columns
+                    __syncthreads();
+                    if (nrow == 1)
+                        tile_slots<1>(z, ci, cj, acc, lane);
+                    else if (nrow == 2)
+                        tile_slots<2>(z, ci, cj, acc, lane);
+                    else if (nrow == 3)
+                        tile_slots<3>(z, ci, cj, acc, lane);
+                    __syncthreads();
+                }
             }
             if (!W) {  // sum over the block of ln(products) into the ln P slot
                 double v = logprod_value(lp);
@@ -906,9 +914,9 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) s_lnp[warp] = v;
                 __syncthreads();
-                const int ls = h.lnp_slot;
-                if (ls >= 0 && t == (ls & (kHessThreads - 1))) {
-                    const double tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
+                lnp_tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
+                if (ls >= 0 && !lnp_in_tail && t == (ls & (kHessThreads - 1))) {
+                    const double tot = lnp_tot;
                     const int row = ls / kHessThreads;
                     if (row == 0)
                         acc[0] += tot;
@@ -919,17 +927,12 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
                 }
             }
         }
-        if (tn > 0) {  // tail slots: fixed tree over the block
-#pragma unroll
-            for (int r = 0; r < kHessTailMax; ++r) {
-                double v = tacc[r];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) s_tail[r][warp] = v;
+        if (tn > 0) {  // tail slots: fixed tree over the block (slot tb + t in thread t)
+            double tot = block_reduce<TM>(tacc, s_tred);
+            if (t < tn) {
+                if (!W && tb + t == ls) tot += lnp_tot;
+                h.unit_sums[(size_t)u * ns + tb + t] = tot;
             }
-            __syncthreads();
-            if (t < tn)
-                h.unit_sums[(size_t)u * ns + tb + t] = (s_tail[t][0] + s_tail[t][1]) + (s_tail[t][2] + s_tail[t][3]);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -946,22 +949,22 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
 template <int KIND, int VAR, bool W>
 __global__ void __launch_bounds__(kHessThreads) batch_hess32_units(const HessDev h)
 {
+    constexpr int TM = HessTailMax<KIND>::value;
     extern __shared__ float z32[];
     __shared__ HConst32 s_c;
-    __shared__ float s_tail[kHessTailMax][kHessThreads / 32];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __shared__ double s_tred[(kHessThreads / 32) * TM];
+    __shared__ uint8_t s_ti[TM], s_tj[TM];
+    const int t = threadIdx.x, lane = t & 31;
     const int ns = h.nslots;
     const int tb = h.tail_begin, tn = h.tail_count;
+    if (t < TM) {
+        const int sr = t < tn ? tb + t : 0;
+        s_ti[t] = h.si[sr];
+        s_tj[t] = h.sj[sr];
+    }
     const int ns_rows = (tn > 0 && tb + tn == ns) ? tb : ns;
     const int w0 = t & ~31;
     const int nrow = ns_rows > w0 ? min(3, (ns_rows - w0 + kHessThreads - 1) / kHessThreads) : 0;
-    int tci[kHessTailMax], tcj[kHessTailMax];
-#pragma unroll
-    for (int r = 0; r < kHessTailMax; ++r) {
-        const int sr = r < tn ? tb + r : 0;
-        tci[r] = h.si[sr] * kHessThreads + t;
-        tcj[r] = h.sj[sr] * kHessThreads + t;
-    }
     int ci[3], cj[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -980,35 +983,33 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess32_units(const HessDev
         ev.n = min(e0 + (int64_t)kHessUnitEvents, h.ev_end[toy]);
         __syncthreads();
         float acc[3] = {0.0f, 0.0f, 0.0f};
-        float tacc[kHessTailMax] = {0.0f, 0.0f, 0.0f, 0.0f};
+        float tacc[TM];
+#pragma unroll
+        for (int r = 0; r < TM; ++r) tacc[r] = 0.0f;
         if (ok) {
             for (int64_t e = e0; e < ev.n; e += kHessThreads) {
                 stage_event32<KIND, VAR, W>(ev, s_c, e + t, z32, t);
 #pragma unroll
-                for (int r = 0; r < kHessTailMax; ++r)
-                    if (r < tn) tacc[r] = fmaf(z32[tci[r]], z32[tcj[r]], tacc[r]);
-                __syncthreads();
-                if (nrow == 1)
-                    tile_slots32<1>(z32, ci, cj, acc, lane);
-                else if (nrow == 2)
-                    tile_slots32<2>(z32, ci, cj, acc, lane);
-                else if (nrow == 3)
-                    tile_slots32<3>(z32, ci, cj, acc, lane);
-                __syncthreads();
+                for (int r = 0; r < TM; ++r)
+                    if (r < tn) tacc[r] = fmaf(z32[s_ti[r] * kHessThreads + t], z32[s_tj[r] * kHessThreads + t], tacc[r]);
+                if (ns_rows > 0) {
+                    __syncthreads();
+                    if (nrow == 1)
+                        tile_slots32<1>(z32, ci, cj, acc, lane);
+                    else if (nrow == 2)
+                        tile_slots32<2>(z32, ci, cj, acc, lane);
+                    else if (nrow == 3)
+                        tile_slots32<3>(z32, ci, cj, acc, lane);
+                    __syncthreads();
+                }
             }
         }
-        if (tn > 0) {
+        if (tn > 0) {  // per-thread float sums, then the block tree in double
+            double td[TM];
 #pragma unroll
-            for (int r = 0; r < kHessTailMax; ++r) {
-                float v = tacc[r];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) s_tail[r][warp] = v;
-            }
-            __syncthreads();
-            if (t < tn)
-                h.unit_sums[(size_t)u * ns + tb + t] =
-                    (double)((s_tail[t][0] + s_tail[t][1]) + (s_tail[t][2] + s_tail[t][3]));
+            for (int r = 0; r < TM; ++r) td[r] = (double)tacc[r];
+            const double tot = block_reduce<TM>(td, s_tred);
+            if (t < tn) h.unit_sums[(size_t)u * ns + tb + t] = tot;
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {

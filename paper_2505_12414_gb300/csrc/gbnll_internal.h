@@ -201,8 +201,15 @@ struct HArgs {
 
 // The Hessian table's few slots past its last full warp row (tail_count <= kHessTailMax, the
 // same with or without the W slots after them) are summed by the thread that stages each
-// event instead of costing a whole warp row of FMAs per event.
+// event instead of costing a whole warp row of FMAs per event.  The mass model's table (at most
+// kHessOwnMax slots) is summed that way entirely: each thread accumulates its own events'
+// products, all threads busy and no tile phase, where a warp row would leave most lanes idle.
 constexpr int kHessTailMax = 4;
+constexpr int kHessOwnMax = 32;
+template <int KIND>
+struct HessTailMax {
+    static constexpr int value = KIND == kMass1D ? kHessOwnMax : kHessTailMax;
+};
 struct HessLayout {
     int nslots = 0, ncols = 0, lnp_slot = -1;
     int tail_begin = 0, tail_count = 0;

@@ -61,33 +61,35 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
 {
     extern __shared__ double z[];
     __shared__ double s_tab[(KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable)];
+    constexpr int TM = HessTailMax<KIND>::value;
     __shared__ double s_lnp[kHessThreads / 32];
-    __shared__ double s_tail[kHessTailMax][kHessThreads / 32];
+    __shared__ double s_tred[(kHessThreads / 32) * TM];
+    __shared__ uint8_t s_ti[TM], s_tj[TM];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     // the slot-total kernel behind this one may be scheduled now: it waits (griddepcontrol.wait)
     // for this grid to complete, so its launch latency overlaps the event loop
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int ntab = (KIND == kKstar4D && VAR == kVarDirect) ? kTabDoubles : (W ? kTrigOffset : kExpTable);
     for (int j = t; j < ntab; j += kHessThreads) s_tab[j] = g_htab[j];
-    __syncthreads();
     const int ns = a.nslots;
     // Tail slots [tb, tb + tn) are summed by the staging thread of each event; when they end
-    // the table the warp rows stop before them (195 slots: 6 rows instead of 7).
+    // the table the warp rows stop before them (195 slots: 6 rows instead of 7; the mass
+    // model's table is all tail).
     const int tb = a.tail_begin, tn = a.tail_count;
+    if (t < TM) {
+        const int sr = t < tn ? tb + t : 0;
+        s_ti[t] = a.sij[sr];
+        s_tj[t] = a.sij[kHessMaxSlots + sr];
+    }
+    __syncthreads();
     const int ns_rows = (tn > 0 && tb + tn == ns) ? tb : ns;
     // slots t, t + 128, t + 256 of this thread; the warp runs as many slot rows as its first
     // lane owns (slots past the end, in the last partial row only, go to unused accumulators)
     const int w0 = t & ~31;
     const int nrow = ns_rows > w0 ? min(3, (ns_rows - w0 + kHessThreads - 1) / kHessThreads) : 0;
-    int tci[kHessTailMax], tcj[kHessTailMax];
-    double tacc[kHessTailMax];
+    double tacc[TM];
 #pragma unroll
-    for (int r = 0; r < kHessTailMax; ++r) {
-        const int sr = r < tn ? tb + r : 0;
-        tci[r] = a.sij[sr] * kHessThreads + t;
-        tcj[r] = a.sij[kHessMaxSlots + sr] * kHessThreads + t;
-        tacc[r] = 0.0;
-    }
+    for (int r = 0; r < TM; ++r) tacc[r] = 0.0;
     int ci[3], cj[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -102,17 +104,22 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         stage_event<KIND, VAR, W>(a.ev, a.c, tile * kHessThreads + t, z, t, s_tab, lp);
 #pragma unroll
-        for (int r = 0; r < kHessTailMax; ++r)  // this thread's own event, just staged
-            if (r < tn) tacc[r] = fma(z[tci[r]], z[tcj[r]], tacc[r]);
-        __syncthreads();
-        if (nrow == 1)
-            tile_slots<1>(z, ci, cj, acc, lane);
-        else if (nrow == 2)
-            tile_slots<2>(z, ci, cj, acc, lane);
-        else if (nrow == 3)
-            tile_slots<3>(z, ci, cj, acc, lane);
-        __syncthreads();
+        for (int r = 0; r < TM; ++r)  // this thread's own event, just staged
+            if (r < tn) tacc[r] = fma(z[s_ti[r] * kHessThreads + t], z[s_tj[r] * kHessThreads + t], tacc[r]);
+        if (ns_rows > 0) {  // the tile's warp rows read every thread's columns
+            __syncthreads();
+            if (nrow == 1)
+                tile_slots<1>(z, ci, cj, acc, lane);
+            else if (nrow == 2)
+                tile_slots<2>(z, ci, cj, acc, lane);
+            else if (nrow == 3)
+                tile_slots<3>(z, ci, cj, acc, lane);
+            __syncthreads();
+        }
     }
+    const int ls = a.lnp_slot;
+    const bool lnp_in_tail = ls >= tb && ls < tb + tn;
+    double lnp_tot = 0.0;
     if (!W) {
         // sum over the block of the threads' ln(products), fixed tree, into the ln P slot
         double v = logprod_value(lp);
@@ -120,9 +127,9 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) s_lnp[warp] = v;
         __syncthreads();
-        const int ls = a.lnp_slot;
-        if (ls >= 0 && t == (ls & (kHessThreads - 1))) {
-            const double tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
+        lnp_tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
+        if (ls >= 0 && !lnp_in_tail && t == (ls & (kHessThreads - 1))) {
+            const double tot = lnp_tot;
             const int row = ls / kHessThreads;  // static indices keep acc in registers
             if (row == 0)
                 acc[0] += tot;
@@ -133,17 +140,10 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
         }
     }
     const int nb = gridDim.x;
-    if (tn > 0) {  // tail slots: fixed tree over the block
-#pragma unroll
-        for (int r = 0; r < kHessTailMax; ++r) {
-            double v = tacc[r];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) s_tail[r][warp] = v;
-        }
-        __syncthreads();
+    if (tn > 0) {  // tail slots: fixed tree over the block (slot tb + t in thread t)
+        double tot = block_reduce<TM>(tacc, s_tred);
         if (t < tn) {
-            const double tot = (s_tail[t][0] + s_tail[t][1]) + (s_tail[t][2] + s_tail[t][3]);
+            if (!W && tb + t == ls) tot += lnp_tot;
             a.partials[(size_t)(tb + t) * nb + blockIdx.x] = tot;
         }
     }
@@ -211,7 +211,7 @@ struct Reader {
     const uint16_t* slot_of;
     const double* sums;
     bool missing = false;
-    double operator()(int i, int j)
+    __host__ __device__ double operator()(int i, int j)  // host only in use; both for assemble_t
     {
         const unsigned s = slot_of[i * 64 + j];
         if (s == 0xffffu) {
@@ -285,7 +285,10 @@ static bool hess_layout_build(int kind, bool weighted, bool want_w2, HessLayout*
         nh = Lh.nslots;
     }
     const int r = nh % 32;
-    if (r > 0 && r <= kHessTailMax && !(L->lnp_slot >= nh - r && L->lnp_slot < nh)) {
+    if (kind == kMass1D && L->nslots <= kHessOwnMax) {  // every slot by the staging thread
+        L->tail_begin = 0;
+        L->tail_count = L->nslots;
+    } else if (r > 0 && r <= kHessTailMax && !(L->lnp_slot >= nh - r && L->lnp_slot < nh)) {
         L->tail_begin = nh - r;
         L->tail_count = r;
     }
