@@ -1238,48 +1238,66 @@ struct Strided {
     __device__ double& operator[](int i) const { return p[(size_t)i * stride]; }
 };
 
-// slot totals of the block's 32 toys staged in shared memory ([slot][lane]) and the
+// slot totals of the block's toys staged in shared memory ([slot][toy]) and the
 // (column pair -> slot) table after them
 struct StagedSlots {
-    const double* tot;  // this lane's first total; slot s at tot[32 s]
+    const double* tot;  // this toy's first total; slot s at tot[s * stride]
+    int stride;
     const uint16_t* slot_of;
     int nc;
     __device__ double operator()(int i, int j) const
     {
         const unsigned s = slot_of[i * nc + j];
-        return s == 0xffffu ? NAN : tot[32 * s];
+        return s == 0xffffu ? NAN : tot[(size_t)s * stride];
     }
 };
 
-// dynamic shared memory of batch_hess_assemble: every slot of 32 toys and the slot table
-constexpr size_t kAsmSmem = sizeof(double) * 32 * kHessMaxSlots + sizeof(uint16_t) * 64 * 64;
-
-// a block per 32 toys, thread per toy: NLL, gradient, H (and W) from the totals, the
-// single-sample assembly.  A thread per toy runs each FP64 instruction for 32 toys at once,
-// where a lane per toy would occupy the FP64 pipe for a whole warp instruction per toy; the
-// totals and the slot table are staged in shared memory first (coalesced, independent loads),
-// and the block's kAsmWarps warps take every kAsmWarps-th row of H each (the assembly is
-// bound by instruction issue, not by the FP64 pipe).
+// Shared memory of batch_hess_assemble stays within the 48 KB every kernel may take without
+// opting in: a kernel that needs a larger shared-memory carve-out cannot start on an SM that
+// runs blocks of other kernels under a smaller one, so it would wait for idle SMs behind the
+// fit loop's (or a server's step) kernels.  The block therefore takes as many toys as the
+// table allows: 32 for the 4D table without W (195 slots), fewer with W.
+constexpr int kAsmSmemMax = 48 * 1024;
 constexpr int kAsmWarps = 4;
 
+size_t asm_smem(int nslots, int ncols, int tpb)
+{
+    return (((size_t)nslots * tpb * sizeof(double) + 15) / 16) * 16 + ((ncols * ncols * 2 + 15) / 16) * 16;
+}
+
+int asm_toys_per_block(int nslots, int ncols)
+{
+    for (int tpb : {32, 24, 16, 12, 8, 4})
+        if (asm_smem(nslots, ncols, tpb) <= (size_t)kAsmSmemMax) return tpb;
+    return 2;  // (the largest table, 384 slots of 64 columns, fits 12)
+}
+
+// a block per tpb toys, thread per toy (lanes 0 .. tpb-1 of each warp): NLL, gradient, H (and
+// W) from the totals, the single-sample assembly.  A thread per toy runs each FP64 instruction
+// for up to 32 toys at once, where a lane per toy would occupy the FP64 pipe for a whole warp
+// instruction per toy; the totals and the slot table are staged in shared memory first
+// (coalesced, independent loads), and the block's kAsmWarps warps take every kAsmWarps-th row
+// of H each (the assembly is bound by instruction issue, not by the FP64 pipe).
 template <int KIND, bool W>
-__global__ void __launch_bounds__(kAsmWarps * 32) batch_hess_assemble(const HessDev h)
+__global__ void __launch_bounds__(kAsmWarps * 32) batch_hess_assemble(const HessDev h, int tpb)
 {
     using L = HCols<KIND, W>;
     constexpr int NP = L::NP;
     extern __shared__ double sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n = h.n_toys, ns = h.nslots, nc = h.ncols;
-    const int t = blockIdx.x * 32 + lane;
-    const bool use = t < n && hess_toy_assembled(h, t);
-    uint16_t* s_slot = reinterpret_cast<uint16_t*>(sm + 32 * kHessMaxSlots);
-    const int nv = (nc * nc + 7) / 8;  // the table is 64 x 64 entries: whole 16-byte vectors
+    const int t = blockIdx.x * tpb + lane;
+    const bool use = lane < tpb && t < n && hess_toy_assembled(h, t);
+    uint16_t* s_slot = reinterpret_cast<uint16_t*>(sm + (((size_t)ns * tpb + 1) / 2) * 2);
+    const int nv = (nc * nc + 7) / 8;  // whole 16-byte vectors of the table (64 x 64 allocated)
     for (int k = threadIdx.x; k < nv; k += kAsmWarps * 32)
         reinterpret_cast<uint4*>(s_slot)[k] = reinterpret_cast<const uint4*>(h.slot_of)[k];
+    if (lane < tpb) {
 #pragma unroll 4
-    for (int sl = warp; sl < ns; sl += kAsmWarps) sm[32 * sl + lane] = use ? h.tot[(size_t)sl * n + t] : 0.0;
+        for (int sl = warp; sl < ns; sl += kAsmWarps) sm[sl * tpb + lane] = use ? h.tot[(size_t)sl * n + t] : 0.0;
+    }
     __syncthreads();
     if (!use) return;
-    StagedSlots S{sm + lane, s_slot, nc};
+    StagedSlots S{sm + lane, tpb, s_slot, nc};
     double* a = h.asmb + t;
     const double bad = assemble_t<KIND, W>(h.ht[t], h.sum_wdm[t], h.want_w2 != 0, S, Strided{a, n},
                                            Strided{a + (size_t)n, n}, Strided{a + (size_t)(1 + NP) * n, n},
@@ -1482,21 +1500,6 @@ cudaError_t launch_hess32_units_t(int blocks, cudaStream_t s, const HessDev& h)
     return cudaGetLastError();
 }
 
-// the assembly's shared memory exceeds the default 48 KB: allowed once per device (the work
-// arrays of every batch and server are set up through hw_alloc on their device)
-cudaError_t set_assemble_smem()
-{
-    const int v = (int)kAsmSmem;
-    cudaError_t e = cudaFuncSetAttribute(batch_hess_assemble<kMass1D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_hess_assemble<kMass1D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_hess_assemble<kKstar4D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batch_hess_assemble<kKstar4D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, v);
-    return e;
-}
-
 cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStream_t s, const HessDev& h)
 {
     batch_hess_prep<<<(h.n_toys + 31) / 32, 32, 0, s>>>(h);  // a warp per block: see launch_step
@@ -1526,13 +1529,15 @@ cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStr
         if (e != cudaSuccess) return e;
     }
     batch_hess_totals<<<(h.n_toys + 3) / 4, 128, 0, s>>>(h);
-    const int ab = (h.n_toys + 31) / 32, at = kAsmWarps * 32;
+    const int tpb = asm_toys_per_block(h.nslots, h.ncols);
+    const int ab = (h.n_toys + tpb - 1) / tpb, at = kAsmWarps * 32;
+    const size_t asmem = asm_smem(h.nslots, h.ncols, tpb);
     if (kind == kMass1D)
-        w ? batch_hess_assemble<kMass1D, true><<<ab, at, kAsmSmem, s>>>(h)
-          : batch_hess_assemble<kMass1D, false><<<ab, at, kAsmSmem, s>>>(h);
+        w ? batch_hess_assemble<kMass1D, true><<<ab, at, asmem, s>>>(h, tpb)
+          : batch_hess_assemble<kMass1D, false><<<ab, at, asmem, s>>>(h, tpb);
     else
-        w ? batch_hess_assemble<kKstar4D, true><<<ab, at, kAsmSmem, s>>>(h)
-          : batch_hess_assemble<kKstar4D, false><<<ab, at, kAsmSmem, s>>>(h);
+        w ? batch_hess_assemble<kKstar4D, true><<<ab, at, asmem, s>>>(h, tpb)
+          : batch_hess_assemble<kKstar4D, false><<<ab, at, asmem, s>>>(h, tpb);
     const int fb = (h.n_toys + kFinWarps - 1) / kFinWarps;
     if (kind == kMass1D) {
         if (w)
@@ -1700,7 +1705,6 @@ cudaError_t hw_alloc(HessWork& w, int cap_toys, int cap_units, int np)
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_toy_nu, sizeof(int) * nt, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaHostAlloc(&w.h_sel, sizeof(int) * nt, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.staged_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = set_assemble_smem();
     if (e != cudaSuccess) {
         hw_free(w);
         return e;
@@ -1864,17 +1868,18 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
 
 // Newton polish passes with the analytic Hessian at the final points of the finished toys
 // (all toys, or those hw_set_units selected), then the accepted points stay.
-cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel)
+cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel,
+                        bool speculate)
 {
     const int tb = (T.n_toys + 127) / 128;
     const int* sel = use_sel ? w.d_sel : nullptr;
     batch_polish_init<<<tb, 128, 0, T.stream>>>(T.d_fits, T.n_toys, sel);
     cudaError_t e = cudaGetLastError();
-    // passes 0 and 1 are queued back to back (nearly every batch has some toy that takes a
-    // Newton step after pass 0, and a pass over no polishing toy costs little); from then on the
-    // host looks at the count after each pass
+    // with `speculate`, passes 0 and 1 are queued back to back (nearly every large batch has
+    // some toy that takes a Newton step after pass 0, and a pass over no polishing toy costs
+    // little); otherwise, and from then on, the host looks at the count after each pass
     for (int pass = 0; pass < 6 && e == cudaSuccess; ++pass) {
-        const bool wait = pass >= 1;
+        const bool wait = pass >= 1 || !speculate;
         e = run_hess_core(T, w, cfg, hessian == 3 ? kHmSandwich : kHmCov, hessian == 3, nullptr, pass, use_sel, wait);
         if (e == cudaSuccess && wait && __atomic_load_n(w.h_npol, __ATOMIC_ACQUIRE) == 0) break;
     }
@@ -2757,7 +2762,7 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
         // (each pass evaluates the toys still polishing) until no toy proposes another step
         int st = ensure_hess_work(b);
         if (st != NLL_OK) return st;
-        e = polish_core(target_of(b), b->hw, c, opt.hessian, false);
+        e = polish_core(target_of(b), b->hw, c, opt.hessian, false, n >= 64);
         if (e != cudaSuccess) return bcuda(b, e, "Newton polish");
     }
     if (direct)

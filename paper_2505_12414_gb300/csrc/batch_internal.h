@@ -165,7 +165,9 @@ cudaError_t run_hess_core(const HessTarget& T, HessWork& w, const FitConfig& cfg
                           const double* thetas, int pass, bool use_sel, bool wait = true, bool subsample = false,
                           bool single = false);
 // Newton polish passes with the analytic Hessian at the final points of the finished toys.
-cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel);
+// speculate: queue passes 0 and 1 without waiting in between (large batches).
+cudaError_t polish_core(const HessTarget& T, HessWork& w, const FitConfig& cfg, int hessian, bool use_sel,
+                        bool speculate = false);
 void setup_config(FitConfig& c, int np, const double* lo, const double* hi, const double* step, const int* fixed,
                   const fit_options& opt);
 void init_fit(ToyFit& F, const FitConfig& c, const double* th0, const double* step);
