@@ -236,7 +236,13 @@ void nll_destroy(nll_model* m);
  *   nll_set_launch  blocks per SM (1..32) and threads per block (64..1024, multiple of 64)
  *                   of the fused kernel, and the 4D variant (nll_variant).  0 keeps a value.
  *   nll_autotune    times the candidate launch shapes (and both 4D variants when the basis is
- *                   loaded) on the loaded sample and keeps the fastest; blocks the host.
+ *                   loaded) on the loaded sample and keeps the fastest; blocks the host.  With
+ *                   the environment variable GBNLL_TUNE_CACHE naming a file, a result kept
+ *                   there for the same device, model, variant choice, weights, gradient,
+ *                   in-place mode and power-of-two sample size is taken without timing, and a
+ *                   new measurement is appended to it (plain text, one line per result;
+ *                   nll_batch_autotune likewise, keyed by model, weights, basis and the
+ *                   power-of-two classes of the toy count and the mean toy size).
  *   nll_set_profiling / nll_last_kernel_ms   when profiling is on, each evaluation records
  *                   CUDA events on the model's stream around its launches (the fused
  *                   kernel and the final-sum kernel behind it; for nll_eval_hess the

@@ -19,9 +19,10 @@ LIB = os.path.join(OUT, "libgbnll.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
+# (plus the CUDA toolkit's include directory, for the header-only NVTX of trace.h)
 
 CU_SOURCES = ["kernels.cu", "runtime.cu", "calibrate.cu", "batch.cu", "server.cu", "gen.cu", "hess.cu"]
-CXX_SOURCES = ["minimise.cpp"]
+CXX_SOURCES = ["minimise.cpp", "tune_cache.cpp"]
 
 
 def _nvcc():
@@ -55,9 +56,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         extra = ["-Xptxas", "-v"] if verbose else []
         jobs.append([nvcc] + ARCH + NVCC_FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj])
         objs.append(obj)
+    cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
     for src in CXX_SOURCES:
         obj = os.path.join(OUT, src + ".o")
-        jobs.append(["g++"] + CXX_FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj])
+        jobs.append(["g++"] + CXX_FLAGS + ["-I", cuda_inc, "-c", os.path.join(CSRC, src), "-o", obj])
         objs.append(obj)
 
     def run(cmd):

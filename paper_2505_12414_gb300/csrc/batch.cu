@@ -35,6 +35,8 @@
 #include "batch_internal.h"
 #include "hess_device.cuh"
 #include "nll_device.cuh"
+#include "trace.h"
+#include "tune_cache.h"
 
 namespace gbnll {
 namespace {
@@ -2567,6 +2569,27 @@ int nll_batch_autotune(nll_batch* b)
     std::vector<double> nll(b->n_toys), g((size_t)b->n_toys * np);
     const int tiles[] = {0, 256, 512, 1024, 2048, 4096};
     const int bpss[] = {1, 2, 4};
+    // a result kept from an earlier process for the same device and workload (GBNLL_TUNE_CACHE)
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "device properties");
+    int64_t events = 0;
+    for (int t = 0; t < b->n_toys; ++t) events += b->end[t] - b->begin[t];
+    int toys_class = 0, events_class = 0;
+    while ((1 << (toys_class + 1)) <= b->n_toys) ++toys_class;
+    while ((int64_t(1) << (events_class + 1)) <= events / b->n_toys) ++events_class;
+    const std::string key = tune_cache_key(prop.name, b->sm_count, "batch", b->kind,
+                                           (b->weighted ? 1 : 0) + (b->has_basis ? 2 : 0), toys_class, events_class);
+    int kept[3];
+    if (tune_cache_lookup(key, kept)) {
+        bool tile_ok = false, bps_ok = false;
+        for (int tile : tiles) tile_ok = tile_ok || tile == kept[0];
+        for (int bps : bpss) bps_ok = bps_ok || bps == kept[1];
+        if (tile_ok && bps_ok) {
+            b->tile_events = kept[0];
+            b->bps = kept[1];
+            return NLL_OK;
+        }
+    }
     float best = 1e30f;
     int bt = b->tile_events, bb = b->bps;
     for (int tile : tiles)
@@ -2587,6 +2610,8 @@ int nll_batch_autotune(nll_batch* b)
         }
     b->tile_events = bt;
     b->bps = bb;
+    const int result[3] = {bt, bb, 0};
+    tune_cache_store(key, result);
     return NLL_OK;
 }
 
@@ -2616,6 +2641,7 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
     if (!b) return NLL_ERR_ARG;
     if (!b->loaded) return bfail(b, NLL_ERR_STATE, "no toys loaded");
     if (!theta0) return bfail(b, NLL_ERR_ARG, "null argument");
+    GBNLL_TRACE("nll_batch_fit");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, NLL_ERR_CUDA, "cudaSetDevice failed");
     fit_options opt;
     if (opt_in)
@@ -2661,43 +2687,46 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return bcuda(b, e, "fit loop set-up");
     int steps_before = 0;  // steps run ahead of the loop's graph
-    if (opt.strategy == 2) {
-        // start matrices from the analytic Hessian at every toy's start point, queued without a
-        // wait (the fit loop follows on the same stream); the pass takes each toy's first step
-        int st = ensure_hess_work(b);
-        if (st != NLL_OK) return st;
-        e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false);
-        if (e != cudaSuccess) return bcuda(b, e, "start matrices");
-    } else if (opt.strategy == 3 || opt.strategy == 5) {
-        // Start matrices that give no NLL and gradient at the start point (from a subsample of
-        // every toy's events, strategy 3, or in single precision, strategy 5): the pass runs on
-        // the auxiliary stream beside the loop's first step, whose evaluation of the start points
-        // (FP64 bound) overlaps the pass (bound by single-precision and shared-memory work, or
-        // short); the step's update waits for the start matrices.  The pass takes at most two
-        // blocks per SM, so that the evaluation's blocks find room.
-        int st = ensure_hess_work(b);
-        if (st != NLL_OK) return st;
-        HessTarget Ta = target_of(b);
-        Ta.stream = b->aux_stream;
-        Ta.max_bps = 2;
-        e = cudaEventRecord(b->ev_fork, b->stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux_stream, b->ev_fork, 0);
-        if (e == cudaSuccess) e = launch_step_eval(d, variant_of(b), b->weighted, b->sm_count * b->bps, b->stream);
-        if (opt.strategy == 3) {
-            // the subsample's unit lists, then the whole toys' lists again for the later passes
-            if (e == cudaSuccess)
-                e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->aux_stream, false, true);
-            if (e == cudaSuccess) e = run_hess_core(Ta, b->hw, c, kHmStart, false, nullptr, 0, false, false, true);
-            if (e == cudaSuccess)
-                e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->aux_stream, false, false);
-        } else if (e == cudaSuccess) {
-            e = run_hess_core(Ta, b->hw, c, kHmStart, false, nullptr, 0, false, false, false, true);
+    {
+        GBNLL_TRACE("start matrices (queued)");
+        if (opt.strategy == 2) {
+            // start matrices from the analytic Hessian at every toy's start point, queued without a
+            // wait (the fit loop follows on the same stream); the pass takes each toy's first step
+            int st = ensure_hess_work(b);
+            if (st != NLL_OK) return st;
+            e = run_hess_core(target_of(b), b->hw, c, kHmStart, false, nullptr, 0, false, false);
+            if (e != cudaSuccess) return bcuda(b, e, "start matrices");
+        } else if (opt.strategy == 3 || opt.strategy == 5) {
+            // Start matrices that give no NLL and gradient at the start point (from a subsample of
+            // every toy's events, strategy 3, or in single precision, strategy 5): the pass runs on
+            // the auxiliary stream beside the loop's first step, whose evaluation of the start points
+            // (FP64 bound) overlaps the pass (bound by single-precision and shared-memory work, or
+            // short); the step's update waits for the start matrices.  The pass takes at most two
+            // blocks per SM, so that the evaluation's blocks find room.
+            int st = ensure_hess_work(b);
+            if (st != NLL_OK) return st;
+            HessTarget Ta = target_of(b);
+            Ta.stream = b->aux_stream;
+            Ta.max_bps = 2;
+            e = cudaEventRecord(b->ev_fork, b->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux_stream, b->ev_fork, 0);
+            if (e == cudaSuccess) e = launch_step_eval(d, variant_of(b), b->weighted, b->sm_count * b->bps, b->stream);
+            if (opt.strategy == 3) {
+                // the subsample's unit lists, then the whole toys' lists again for the later passes
+                if (e == cudaSuccess)
+                    e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->aux_stream, false, true);
+                if (e == cudaSuccess) e = run_hess_core(Ta, b->hw, c, kHmStart, false, nullptr, 0, false, false, true);
+                if (e == cudaSuccess)
+                    e = hw_set_units(b->hw, b->begin, b->end, std::vector<int>(), b->aux_stream, false, false);
+            } else if (e == cudaSuccess) {
+                e = run_hess_core(Ta, b->hw, c, kHmStart, false, nullptr, 0, false, false, false, true);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->aux_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+            if (e == cudaSuccess) e = launch_step_update(d, b->stream);
+            if (e != cudaSuccess) return bcuda(b, e, "start matrices");
+            steps_before = 1;
         }
-        if (e == cudaSuccess) e = cudaEventRecord(b->ev_join, b->aux_stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
-        if (e == cudaSuccess) e = launch_step_update(d, b->stream);
-        if (e != cudaSuccess) return bcuda(b, e, "start matrices");
-        steps_before = 1;
     }
 
     // The fit loop runs on the device: a CUDA graph with one while node whose body is a device
@@ -2752,12 +2781,16 @@ static int batch_fit_core(nll_batch* b, const double* theta0, int shared_start, 
         memcpy(b->fit_shape, shape, sizeof shape);
     }
     int steps = 0;
-    e = cudaGraphLaunch(b->fit_exec, b->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&steps, d_steps, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    {
+        GBNLL_TRACE("fit loop (device)");
+        e = cudaGraphLaunch(b->fit_exec, b->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&steps, d_steps, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
     if (e != cudaSuccess) return bcuda(b, e, "fit loop");
     if (steps_out) *steps_out = steps + steps_before;
     if (opt.hessian >= 2) {
+        GBNLL_TRACE("Newton polish");
         // analytic Hessian at every toy's final point: covariance, EDM, and Newton polish steps
         // (each pass evaluates the toys still polishing) until no toy proposes another step
         int st = ensure_hess_work(b);

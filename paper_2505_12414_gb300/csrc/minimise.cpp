@@ -21,6 +21,7 @@
 //     takes far fewer passes over the events where a pass with second derivatives costs about
 //     what one without does (small samples, where each pass is launch latency).
 #include "minimise.h"
+#include "trace.h"
 
 #include <math.h>
 #include <string.h>
@@ -319,6 +320,7 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
                   const double* step, const int* fixed, const fit_options* opt_in, fit_result* out,
                   const HessianFn* hess)
 {
+    GBNLL_TRACE("minimiser");
     fit_options opt;
     if (opt_in)
         opt = *opt_in;
@@ -453,6 +455,7 @@ int bfgs_minimise(const Objective& fn, int n, const double* theta0, const double
     bool converged = edm < opt.tol_edm;
     bool first_update = true;
     while (!converged && iter < opt.max_iter) {
+        GBNLL_TRACE("quasi-Newton iteration");
         ++iter;
         matvec(nf, V, g, p);
         for (int i = 0; i < nf; ++i) p[i] = -p[i];

@@ -22,6 +22,8 @@
 #include "../../include/gbnll.h"
 #include "fp64_math.cuh"
 #include "gbnll_internal.h"
+#include "trace.h"
+#include "tune_cache.h"
 #include "minimise.h"
 
 using namespace gbnll;
@@ -467,8 +469,13 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
     if (!theta || !nll_out) return fail(m, NLL_ERR_ARG, "null theta or output");
     if (n_params != m->npar) return fail(m, NLL_ERR_ARG, "expected %d parameters, got %d", m->npar, n_params);
     if (!m->loaded) return fail(m, NLL_ERR_STATE, "no events loaded");
+    GBNLL_TRACE(grad ? "nll_eval_grad" : "nll_eval");
     Hoist H;
-    int st = hoist(m, theta, grad, H);
+    int st;
+    {
+        GBNLL_TRACE("hoist");
+        st = hoist(m, theta, grad, H);
+    }
     if (st != NLL_OK) return st;
     m->last = H;
     m->have_last = true;
@@ -479,9 +486,16 @@ int eval_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         int var = effective_variant(m);
         if (var < 0) return fail(m, NLL_ERR_STATE, "precompute variant requested but no basis was built");
         if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
-        st = run_fused(m, H, grad, m->bps, m->threads, var, true);
+        {
+            GBNLL_TRACE("launch");
+            st = run_fused(m, H, grad, m->bps, m->threads, var, true);
+        }
         if (st != NLL_OK) return st;
-        cudaError_t e = wait_words(m->stream, m->h_done, m->seq, K);
+        cudaError_t e;
+        {
+            GBNLL_TRACE("wait for the sums");
+            e = wait_words(m->stream, m->h_done, m->seq, K);
+        }
         if (e != cudaSuccess) return cuda_fail(m, e, "evaluation");
         if (m->profiling) {  // the kernel time is read when asked for (nll_last_kernel_ms)
             m->ms_pending = true;
@@ -546,8 +560,13 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
             return st0;
         }
     }
+    GBNLL_TRACE("nll_eval_hess");
     Hoist H;
-    int st = hoist(m, theta, true, H);
+    int st;
+    {
+        GBNLL_TRACE("hoist");
+        st = hoist(m, theta, true, H);
+    }
     if (st != NLL_OK) return st;
     const bool want_w2 = w2_out != nullptr;
     HessLayout L;
@@ -582,10 +601,17 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
         int blocks = (int)std::min<int64_t>(ntiles, (int64_t)m->sm_count * occ);
         blocks = std::min(blocks, m->hess_max_blocks);
         if (m->profiling) cudaEventRecord(m->ev0, m->stream);
-        cudaError_t e = launch_hess(m->kind, var, m->weighted, blocks, m->stream, a);
+        cudaError_t e;
+        {
+            GBNLL_TRACE("launch");
+            e = launch_hess(m->kind, var, m->weighted, blocks, m->stream, a);
+        }
         if (e != cudaSuccess) return cuda_fail(m, e, "Hessian kernel launch");
         if (m->profiling) cudaEventRecord(m->ev1, m->stream);
-        e = wait_words(m->stream, m->h_hdone, a.seq, L.nslots);
+        {
+            GBNLL_TRACE("wait for the sums");
+            e = wait_words(m->stream, m->h_hdone, a.seq, L.nslots);
+        }
         if (e != cudaSuccess) return cuda_fail(m, e, "Hessian evaluation");
         if (m->profiling) {  // the kernel time is read when asked for (nll_last_kernel_ms)
             m->ms_pending = true;
@@ -595,7 +621,11 @@ int hess_impl(nll_model* m, const double* theta, int n_params, double* nll_out, 
     }
     const int np = m->npar;
     double nll, grad[18], Hm[18 * 18], Wm[18 * 18];
-    double bad = hess_assemble(m->kind, m->weighted, want_w2, H, m->sum_wdm, L, sums, &nll, grad, Hm, Wm);
+    double bad;
+    {
+        GBNLL_TRACE("assemble");
+        bad = hess_assemble(m->kind, m->weighted, want_w2, H, m->sum_wdm, L, sums, &nll, grad, Hm, Wm);
+    }
     if (bad != bad) return fail(m, NLL_ERR_ARG, "Hessian slot table incomplete");
     if (bad != 0.0 || !isfinite(nll)) {
         *nll_out = INFINITY;
@@ -990,6 +1020,26 @@ int nll_autotune(nll_model* m)
         variants.push_back(effective_variant(m));
     }
     bool grad = grad_ok;
+    // a result kept from an earlier process for the same device and workload (GBNLL_TUNE_CACHE)
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "device properties");
+    int size_class = 0;
+    while ((int64_t(1) << (size_class + 1)) <= m->n) ++size_class;
+    const std::string key = tune_cache_key(prop.name, m->sm_count, "fused", m->kind,
+                                           variants.size() > 1 ? -1 : variants[0],
+                                           (m->weighted ? 1 : 0) + (grad ? 2 : 0) + (m->in_place ? 4 : 0), size_class);
+    int kept[3];
+    if (tune_cache_lookup(key, kept)) {
+        bool valid = kept[0] >= 1 && kept[0] <= 32 && kept[1] >= 64 && kept[1] <= 1024 && kept[1] % 64 == 0;
+        bool var_ok = false;
+        for (int v : variants) var_ok = var_ok || v == kept[2];
+        if (valid && var_ok) {
+            m->bps = kept[0];
+            m->threads = kept[1];
+            if (variants.size() > 1) m->variant = kept[2] == kVarDirect ? NLL_VARIANT_DIRECT : NLL_VARIANT_PRECOMPUTE;
+            return NLL_OK;
+        }
+    }
     float best = 1e30f;
     int best_bps = m->bps, best_thr = m->threads, best_var = variants[0];
     for (int var : variants)
@@ -1016,6 +1066,8 @@ int nll_autotune(nll_model* m)
     m->bps = best_bps;
     m->threads = best_thr;
     if (variants.size() > 1) m->variant = best_var == kVarDirect ? NLL_VARIANT_DIRECT : NLL_VARIANT_PRECOMPUTE;
+    const int result[3] = {best_bps, best_thr, best_var};
+    tune_cache_store(key, result);
     return NLL_OK;
 }
 

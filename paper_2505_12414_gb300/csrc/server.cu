@@ -29,6 +29,7 @@
 
 #include "../../include/gbnll.h"
 #include "batch_internal.h"
+#include "trace.h"
 #include "gbnll_internal.h"
 
 using namespace gbnll;
@@ -456,6 +457,7 @@ int nll_server_step(nll_server* s, int n_steps)
 {
     if (!s || n_steps < 0) return NLL_ERR_ARG;
     if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
+    GBNLL_TRACE("server step");
     bool starts = false;
     for (int i = 0; i < s->max_slots; ++i) starts = starts || (s->busy[i] && s->need_start[i]);
     if (starts && n_steps > 0) {
@@ -484,6 +486,7 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
                       const double* theta0, int64_t* request_id)
 {
     if (!s || !theta0 || !request_id || n_events < 0) return NLL_ERR_ARG;
+    GBNLL_TRACE("server admission");
     if (weights) return sfail(s, NLL_ERR_ARG, "a server serves unweighted fits");
     if (n_events > 0 && !columns) return sfail(s, NLL_ERR_ARG, "null columns");
     for (int d = 0; d < s->ndim && n_events > 0; ++d)
@@ -589,6 +592,7 @@ int nll_server_poll(nll_server* s, int64_t* ids_out, fit_result* results, int ma
 {
     if (!s || !n_out || max_results < 0 || (max_results > 0 && (!ids_out || !results))) return NLL_ERR_ARG;
     *n_out = 0;
+    GBNLL_TRACE("server collection");
     if (cudaSetDevice(s->device) != cudaSuccess) return sfail(s, NLL_ERR_CUDA, "cudaSetDevice failed");
     // fits whose done flag is set: their final state is in device memory and no step changes it
     std::vector<int> pick(s->max_slots, 0);

@@ -235,3 +235,35 @@ def test_routing_by_size_class_gives_the_same_results(gpu_lib):
         assert a.result["status"] == 0 and b.result["status"] == 0
         assert np.array_equal(a.result["theta"], b.result["theta"])
         assert np.array_equal(a.result["err"], b.result["err"])
+
+
+@pytest.mark.parametrize("strategy", [3, 5])
+def test_served_fits_with_estimated_start_matrices(gpu_lib, strategy):
+    """Served fits whose start matrix comes from a subsample (strategy 3) or a single-precision
+    pass (strategy 5): the same result alone and in the mix, and the minimum and covariance of
+    the analytic served fit (strategy 2) to within the stopping tolerance."""
+    from paper_2505_12414_gb300.serve import serve
+
+    def run(reqs, slots, pool, st):
+        srv = {k: gpu_lib.Server(k, synth.RANGES_1D if k == M1 else synth.RANGES_4D, slots, pool, 1024,
+                                 **dict(opts_analytic(k), strategy=st, tol_edm=1e-14)) for k in (M1, M4)}
+        serve(srv, reqs, realtime=False)
+        for s in srv.values():
+            s.close()
+
+    mix = make_requests(8, 9400)
+    run(mix, 8, 200000, strategy)
+    alone = make_requests(8, 9400)
+    for r in alone[:3]:
+        run([r], 1, 20000, strategy)
+    for a, b in zip(mix, alone[:3]):
+        assert a.result["status"] == 0 and b.result["status"] == 0
+        assert np.array_equal(a.result["theta"], b.result["theta"])
+        assert np.array_equal(a.result["err"], b.result["err"])
+    ref = make_requests(8, 9400)
+    run(ref, 8, 200000, 2)
+    for a, r in zip(mix, ref):
+        assert r.result["status"] == 0
+        # both stop at EDM 1e-14: within sqrt(2e-14) = 1.4e-7 of the uncertainty of the minimum
+        assert np.max(np.abs(a.result["theta"] - r.result["theta"]) / r.result["err"]) < 1e-6
+        np.testing.assert_allclose(a.result["err"], r.result["err"], rtol=1e-6)
