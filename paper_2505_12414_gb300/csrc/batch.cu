@@ -1311,10 +1311,30 @@ __global__ void __launch_bounds__(kAsmWarps * 32) batch_hess_assemble(const Hess
 // (two warps per block: 31 KB of static shared memory for the 18-parameter model)
 constexpr int kFinWarps = 2;
 
-template <int KIND, bool W>
+// slot totals of one toy in shared memory, found through the (column pair -> slot) table
+struct SumSlots {
+    const double* sums;
+    const uint16_t* slot_of;
+    int nc;
+    __device__ double operator()(int i, int j) const
+    {
+        const unsigned s = slot_of[i * nc + j];
+        return s == 0xffffu ? NAN : sums[s];
+    }
+};
+
+// SMALL (passes over at most kFinSmallToys toys, such as a server's collections): the toy's
+// slot totals and its assembly are done here, by the toy's warp (totals) and lane 0 (assembly),
+// instead of by batch_hess_totals and batch_hess_assemble: two launches fewer per pass, and for
+// a few toys a lane's FP64 instructions cost little.  Both paths add the same unit sums in the
+// same order and assemble with the same code.
+constexpr int kFinSmallToys = 64;
+
+template <int KIND, bool W, bool SMALL>
 __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDev h)
 {
     constexpr int NPK = KIND == kMass1D ? 4 : 18;
+    __shared__ double s_sum[SMALL ? kFinWarps : 1][SMALL ? kHessMaxSlots : 1];
     __shared__ double s_H[kFinWarps][NPK * NPK];
     __shared__ double s_W[kFinWarps][NPK * NPK];
     __shared__ double s_mat[kFinWarps][4][NPK * NPK];
@@ -1342,7 +1362,27 @@ __global__ void __launch_bounds__(kFinWarps * 32) batch_hess_finish(const HessDe
         }
         return;
     }
-    {
+    if (SMALL) {
+        const int u0 = h.toy_u0[t], nu = h.toy_nu[t];
+        double scale = 1.0;
+        if (h.subsample) {  // events of the toy over events in its units (a start matrix only)
+            int64_t covered = 0;
+            for (int j = 0; j < nu; ++j) covered += min((int64_t)kHessUnitEvents, h.ev_end[t] - h.unit_e0[u0 + j]);
+            if (covered > 0) scale = (double)(h.ev_end[t] - h.ev_begin[t]) / (double)covered;
+        }
+        for (int sl = lane; sl < h.nslots; sl += 32) {
+            double v = 0.0;
+            for (int j = 0; j < nu; ++j) v += h.unit_sums[(size_t)(u0 + j) * h.nslots + sl];
+            s_sum[wib][sl] = v * scale;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            SumSlots S{s_sum[wib], h.slot_of, h.ncols};
+            const double bad = assemble_t<KIND, W>(h.ht[t], h.sum_wdm[t], h.want_w2 != 0, S, &s_nll[wib], s_g[wib],
+                                                   s_H[wib], s_W[wib]);
+            s_bad[wib] = (bad != 0.0 || !isfinite(s_nll[wib])) ? 1 : 0;
+        }
+    } else {
         const int n = h.n_toys;
         const double* a = h.asmb + t;
         for (int k = lane; k < NPK; k += 32) s_g[wib][k] = a[(size_t)(1 + k) * n];
@@ -1530,6 +1570,16 @@ cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStr
                   : launch_hess_units_t<kKstar4D, kVarPrecompute, false>(unit_blocks, s, h);
         if (e != cudaSuccess) return e;
     }
+    const int fb = (h.n_toys + kFinWarps - 1) / kFinWarps;
+    if (h.n_toys <= kFinSmallToys) {  // totals and assembly inside the finish
+        if (kind == kMass1D)
+            w ? batch_hess_finish<kMass1D, true, true><<<fb, kFinWarps * 32, 0, s>>>(h)
+              : batch_hess_finish<kMass1D, false, true><<<fb, kFinWarps * 32, 0, s>>>(h);
+        else
+            w ? batch_hess_finish<kKstar4D, true, true><<<fb, kFinWarps * 32, 0, s>>>(h)
+              : batch_hess_finish<kKstar4D, false, true><<<fb, kFinWarps * 32, 0, s>>>(h);
+        return cudaGetLastError();
+    }
     batch_hess_totals<<<(h.n_toys + 3) / 4, 128, 0, s>>>(h);
     const int tpb = asm_toys_per_block(h.nslots, h.ncols);
     const int ab = (h.n_toys + tpb - 1) / tpb, at = kAsmWarps * 32;
@@ -1540,17 +1590,16 @@ cudaError_t launch_hess_pass(int kind, int var, bool w, int unit_blocks, cudaStr
     else
         w ? batch_hess_assemble<kKstar4D, true><<<ab, at, asmem, s>>>(h, tpb)
           : batch_hess_assemble<kKstar4D, false><<<ab, at, asmem, s>>>(h, tpb);
-    const int fb = (h.n_toys + kFinWarps - 1) / kFinWarps;
     if (kind == kMass1D) {
         if (w)
-            batch_hess_finish<kMass1D, true><<<fb, kFinWarps * 32, 0, s>>>(h);
+            batch_hess_finish<kMass1D, true, false><<<fb, kFinWarps * 32, 0, s>>>(h);
         else
-            batch_hess_finish<kMass1D, false><<<fb, kFinWarps * 32, 0, s>>>(h);
+            batch_hess_finish<kMass1D, false, false><<<fb, kFinWarps * 32, 0, s>>>(h);
     } else {
         if (w)
-            batch_hess_finish<kKstar4D, true><<<fb, kFinWarps * 32, 0, s>>>(h);
+            batch_hess_finish<kKstar4D, true, false><<<fb, kFinWarps * 32, 0, s>>>(h);
         else
-            batch_hess_finish<kKstar4D, false><<<fb, kFinWarps * 32, 0, s>>>(h);
+            batch_hess_finish<kKstar4D, false, false><<<fb, kFinWarps * 32, 0, s>>>(h);
     }
     return cudaGetLastError();
 }
