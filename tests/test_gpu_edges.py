@@ -260,6 +260,27 @@ def test_batch_hessian_edges(gpu_lib, kind, weighted):
     b.close()
 
 
+@pytest.mark.parametrize("kind", [M1, M4])
+@pytest.mark.parametrize("weighted,precompute", [(False, True), (True, False)])
+def test_estimated_start_matrix_fits_on_edges(gpu_lib, kind, weighted, precompute):
+    """Batched fits of the edge sample (events on every face, edge and corner of the box) whose
+    start matrices come from the single-precision pass (strategy 5) or a subsample (strategy
+    3): the single-precision staging meets cos = +-1 (a zero basis column), phi = +-pi and the
+    window edges, and the fits reach the minima of strategy 2."""
+    cols, w = data(kind, weighted)
+    b = _batch(gpu_lib, kind, cols, w, 4, precompute=precompute)
+    step = np.array([2.0, 1.0, 2e-4, 0.02]) if kind == M1 else np.array([1.0, 1.0] + [0.03] * 8 + [2e-4] + [0.03] * 6 + [0.02])
+    lo, hi = np.zeros(len(step)), np.zeros(len(step))
+    hi[-1] = 1.0
+    th0 = (synth.TRUTH_1D if kind == M1 else synth.TRUTH_4D) + 0.3 * step
+    r = {st: b.fit(th0, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=st, hessian=2) for st in (2, 3, 5)}
+    b.close()
+    for st in (3, 5):
+        assert np.all(r[st]["status"] == 0) and np.all(r[2]["status"] == 0)
+        assert np.max(np.abs(r[st]["theta"] - r[2]["theta"]) / r[2]["err"]) < 1e-6
+        np.testing.assert_allclose(r[st]["err"], r[2]["err"], rtol=1e-6)
+
+
 # --------------------------------------------------------------------------------------
 # served fits (device-side hoisting at every step of the fit) against the oracle's fits
 # --------------------------------------------------------------------------------------
