@@ -275,12 +275,14 @@ def toy_fits(g, device, n_toys, n_seq, seed_stream=0):
             "speedup_vs_sequential": (n_toys / dt) / (n_seq_done / seq_t) if seq_t > 0 else None}
 
 
-def serving(g, device, n_req, rate, seed_stream=0, size_classes=False, max_queued=2, admit_all=True):
+def serving(g, device, n_req, rate, seed_stream=0, size_classes=False, max_queued=2, admit_all=True, idle_direct=True):
     """Poisson-arrival stream of full fits mixing the mass and 4D models, event counts
     log-uniform in [1e3, 1e6]: continuous batching (nll_server_*) against the plain
     one-fit-at-a-time GPU path on the same requests and arrival times, once with
     finite-difference Hessians of the analytic gradient (strategy 1, hessian 1) and once with
-    analytic second derivatives (strategy 2, hessian 2)."""
+    analytic second derivatives (strategy 2, hessian 2).  With idle_direct, a request that
+    finds the serving loop idle (no fit in flight, no other request waiting) is fitted at once
+    through the single-fit path (serve(direct=...)); its count is reported (direct_fits)."""
     from paper_2505_12414_gb300.serve import Request, by_kind, by_kind_and_size, latency_summary, serve, serve_sequential
 
     rs = synth.Stream(synth.BASE_SEED + 4242 + seed_stream, 0)
@@ -326,13 +328,17 @@ def serving(g, device, n_req, rate, seed_stream=0, size_classes=False, max_queue
             if route(r) not in seen:
                 seen.add(route(r))
                 warm.append(r)
+        # a request that finds the loop idle (nothing in flight, nothing waiting) takes the
+        # single-fit path on these models; the same models run the sequential baseline
+        models = {k: g.Model(k, ranges[k], device=device) for k in step}
+        direct = {key: (models[key if not isinstance(key, tuple) else key[0]],
+                        opts[key if not isinstance(key, tuple) else key[0]]) for key in servers}
         serve(servers, warm, realtime=False, route=route)
         phases = {}
         served = serve(servers, requests(), realtime=True, phases=phases, route=route, max_queued=max_queued,
-                       admit_all=admit_all)
+                       admit_all=admit_all, direct=direct if idle_direct else None)
         for srv in servers.values():
             srv.close()
-        models = {k: g.Model(k, ranges[k], device=device) for k in step}
         serve_sequential(models, warm, opts)  # warm-up
         seq = serve_sequential(models, requests(), opts)
         for m in models.values():

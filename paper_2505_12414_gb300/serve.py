@@ -6,7 +6,7 @@ queued on every server with fits in it (servers run on their own CUDA streams, s
 overlap on the device) and collects finished fits as soon as their done flags are up, so the
 device does not wait for the host between steps and admissions and collections overlap the
 steps of the other fits.  The loop only schedules: all fitting runs in the library
-(nll_server_*).
+(nll_server_*, or fit_minimise for a lone request on an idle loop).
 """
 import collections
 import time
@@ -45,7 +45,7 @@ def by_kind_and_size(limit):
 
 
 def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phases=None, route=by_kind,
-          admit_all=True):
+          admit_all=True, direct=None):
     """Run `requests` (sorted by arrival, seconds from start) through `servers` {key: Server},
     each request going to servers[route(request)].
 
@@ -57,11 +57,16 @@ def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phas
     waiting requests as it has room for in each pass of the loop (fits that start together
     share their steps); otherwise one per pass.  If `phases` is a dict, the host time spent in
     admission (submit), step queueing (step), progress queries and collection (poll) is added
-    to it, in seconds, with the number of steps queued.  Returns the requests with
-    admitted/done times and results filled in."""
+    to it, in seconds, with the number of steps queued.  With `direct` ({key: (Model, fit
+    keyword arguments)}, keyed as the servers), a request that finds every server idle and no
+    other request waiting is fitted at once through the single-fit path of its key's model
+    (nll_load_events + fit_minimise) instead of being admitted: a lone fit would otherwise pay
+    the device loop's per-step latency for every step, where batching has nothing to share
+    (the time goes to direct_s).  Returns the requests with admitted/done times and results
+    filled in."""
     clock = time.perf_counter
     acc = phases if phases is not None else {}
-    for key in ("admit_s", "step_s", "progress_s", "collect_s", "steps"):
+    for key in ("admit_s", "step_s", "progress_s", "collect_s", "direct_s", "steps", "direct_fits"):
         acc.setdefault(key, 0.0)
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     queues = {k: collections.deque() for k in servers}
@@ -89,6 +94,20 @@ def serve(servers, requests, steps_per_iter=2, realtime=True, max_queued=2, phas
         while pending and (not realtime or pending[0].arrival <= now):
             r = pending.popleft()
             queues[route(r)].append(r)
+        if direct is not None and not any(inflight.values()) and sum(len(q) for q in queues.values()) == 1:
+            k = next(k for k, q in queues.items() if q)
+            if k in direct:  # the lone request: the single-fit path
+                r = queues[k].popleft()
+                model, kwargs = direct[k]
+                c0 = clock()
+                r.admitted = c0 - t0
+                model.load(r.columns)
+                r.result = model.fit(r.theta0, **kwargs)
+                r.done = clock() - t0
+                acc["direct_s"] += clock() - c0
+                acc["direct_fits"] += 1
+                left -= 1
+                continue
         feed()
         for k, srv in servers.items():  # admissions, feeding the step queues after each
             q = queues[k]

@@ -267,3 +267,31 @@ def test_served_fits_with_estimated_start_matrices(gpu_lib, strategy):
         # both stop at EDM 1e-14: within sqrt(2e-14) = 1.4e-7 of the uncertainty of the minimum
         assert np.max(np.abs(a.result["theta"] - r.result["theta"]) / r.result["err"]) < 1e-6
         np.testing.assert_allclose(a.result["err"], r.result["err"], rtol=1e-6)
+
+
+def test_lone_request_takes_the_single_fit_path(gpu_lib):
+    """With direct models, a request that finds the loop idle is fitted through fit_minimise
+    (the same result as Model.fit, bitwise); requests that arrive together still go through the
+    servers."""
+    from paper_2505_12414_gb300.serve import serve
+
+    srv = servers(gpu_lib, 4, 100000)
+    models = {k: gpu_lib.Model(k, synth.RANGES_1D if k == M1 else synth.RANGES_4D) for k in (M1, M4)}
+    direct = {k: (models[k], opts(k)) for k in (M1, M4)}
+    lone = make_requests(1, 9500)
+    phases = {}
+    serve(srv, lone, realtime=False, direct=direct, phases=phases)
+    assert phases["direct_fits"] == 1
+    ref = gpu_lib.Model(lone[0].kind, synth.RANGES_1D).load(lone[0].columns)
+    s = ref.fit(lone[0].theta0, **opts(lone[0].kind))
+    ref.close()
+    assert np.array_equal(lone[0].result["theta"], s["theta"]) and lone[0].result["nll"] == s["nll"]
+    together = make_requests(4, 9510)
+    phases = {}
+    serve(srv, together, realtime=False, direct=direct, phases=phases)
+    assert phases["direct_fits"] == 0
+    assert all(r.result["status"] == 0 for r in together)
+    for s_ in srv.values():
+        s_.close()
+    for m in models.values():
+        m.close()
