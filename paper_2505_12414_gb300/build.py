@@ -21,7 +21,7 @@ NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.
 CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I", os.path.join(ROOT, "include")]
 # (plus the CUDA toolkit's include directory, for the header-only NVTX of trace.h)
 
-CU_SOURCES = ["kernels.cu", "runtime.cu", "calibrate.cu", "batch.cu", "server.cu", "gen.cu", "hess.cu"]
+CU_SOURCES = ["kernels.cu", "runtime.cu", "calibrate.cu", "batch.cu", "batch_hess.cu", "server.cu", "gen.cu", "hess.cu"]
 CXX_SOURCES = ["minimise.cpp", "tune_cache.cpp"]
 
 
