@@ -153,7 +153,7 @@ def load(path=None):
 
 
 def _f64(a):
-    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return np.ascontiguousarray(a, dtype=np.float64)
 
 
 def _p(a):
@@ -305,17 +305,18 @@ def nll_hess_num_slots(kind, weighted=False, w2=False):
 def _fit_args(theta0, lo, hi, step, fixed):
     th = _f64(theta0)
     n = len(th)
-    lo = _f64(lo if lo is not None else np.zeros(n))
-    hi = _f64(hi if hi is not None else np.zeros(n))
-    step = _f64(step if step is not None else np.maximum(1e-3 * np.abs(th), 1e-3))
-    fx = np.ascontiguousarray(np.asarray(fixed if fixed is not None else np.zeros(n), dtype=np.int32))
+    lo = _f64(lo) if lo is not None else np.zeros(n)
+    hi = _f64(hi) if hi is not None else np.zeros(n)
+    step = _f64(step) if step is not None else np.maximum(1e-3 * np.abs(th), 1e-3)
+    fx = np.ascontiguousarray(fixed, dtype=np.int32) if fixed is not None else np.zeros(n, dtype=np.int32)
     return th, lo, hi, step, fx
 
 
 def _result_dict(res, n):
-    cov = np.ctypeslib.as_array(res.cov)[: FIT_MAXPAR * FIT_MAXPAR].reshape(FIT_MAXPAR, FIT_MAXPAR)
-    cov = cov.reshape(-1)[: n * n].reshape(n, n).copy()
-    return dict(theta=np.array(res.theta[:n]), err=np.array(res.err[:n]), cov=cov, nll=res.nll, edm=res.edm,
+    # theta, err and cov lead the record as one run of doubles: one view, three slices
+    a = np.frombuffer(res, dtype=np.float64, count=2 * FIT_MAXPAR + FIT_MAXPAR * FIT_MAXPAR)
+    return dict(theta=a[:n].copy(), err=a[FIT_MAXPAR:FIT_MAXPAR + n].copy(),
+                cov=a[2 * FIT_MAXPAR:2 * FIT_MAXPAR + n * n].reshape(n, n).copy(), nll=res.nll, edm=res.edm,
                 n_eval=res.n_eval, n_iter=res.n_iter, status=res.status)
 
 
