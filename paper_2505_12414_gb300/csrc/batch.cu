@@ -595,7 +595,8 @@ __global__ void batch_loop_control(cudaGraphConditionalHandle handle, const int*
     const int s = *steps + 1;
     *steps = s;
     const int active = *(volatile const int*)n_active;
-    *step_tp = (4 * active <= n_toys) ? max(base_tp / 4, 64) : base_tp;  // 64: the smallest tile the work arrays are sized for
+    // 64 pairs: the smallest tile the work arrays are sized for (a smaller schedule tile stays)
+    *step_tp = (4 * active <= n_toys) ? min(base_tp, max(base_tp / 4, 64)) : base_tp;
     cudaGraphSetConditional(handle, (active > 0 && s < max_steps) ? 1u : 0u);
 }
 
