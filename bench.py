@@ -63,8 +63,8 @@ FLOPS_PER_EVENT = ARITH_FLOPS_4D + 2.0 * (C_EXP_DFMA + C_RCP_DFMA)
 # FP64-pipe peak is the same 2 DFMA/clk/SM.
 FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic of one evaluation: dram__bytes_read.sum + dram__bytes_write.sum of the fused
-# kernel at 152 x 256 plus its final-sum kernel on this 1M-event sample, from one ncu capture
-# of the current kernels (ncu cannot run inside the timed bench).
+# kernel at the bench's shape (304 x 128) plus its final-sum kernel on this 1M-event sample,
+# from one ncu capture of the current kernels (ncu cannot run inside the timed bench).
 KERNEL_TRAFFIC_BYTES = 132.6e6
 KERNEL_TRAFFIC_SOURCE = ("ncu --set full --clock-control none capture of fused_nll_kernel<4D, precompute, grad> "
                          "(304 x 128) and final_reduce_kernel on the 1M-event 4D sample after an L2 flush: "
@@ -417,12 +417,13 @@ def mass_sweep(g, device, stream):
     return out
 
 
-def single_fit_latency(g, device, n_events=10_000, n_fits=100):
+def single_fit_latency(g, device, n_events=10_000, n_fits=300):
     """Latency of one full fit of the mass model (10^4 events, 4 free parameters, analytic
     derivatives), one fit at a time through fit_minimise: the quasi-Newton route (analytic
     start matrix and Newton polish, strategy 2 / hessian 2) against damped Newton steps with
     the analytic Hessian at every iterate (strategy 4).  Each fit starts from its own seeded
-    point near the truth; wall clock of the blocking call."""
+    point near the truth; the two routes alternate from one start point to the next, so that
+    clock and host drift fall on both alike; wall clock of the blocking call."""
     cols = synth.mass1d(n_events, stream=91)
     m = g.Model(g.NLL_MODEL_MASS1D, synth.RANGES_1D, device=device).load(cols)
     step = np.array([2.0, 1.0, 2e-4, 0.02])
@@ -430,20 +431,23 @@ def single_fit_latency(g, device, n_events=10_000, n_fits=100):
     hi[3] = 1.0
     starts = [synth.perturb(synth.TRUTH_1D, step, seed=synth.BASE_SEED + 91, k=i, frac=1.0) for i in range(n_fits)]
     out = {"n_events": n_events, "fits": n_fits}
-    res = {}
-    for label, strategy in (("quasi_newton", 2), ("newton", 4)):
-        m.fit(starts[0], lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=strategy, hessian=2)  # warm-up
-        times, evals, thetas = [], [], []
-        for th0 in starts:
+    routes = (("quasi_newton", 2), ("newton", 4))
+    for _, strategy in routes:  # warm-up
+        m.fit(starts[0], lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=strategy, hessian=2)
+    times = {label: [] for label, _ in routes}
+    evals = {label: [] for label, _ in routes}
+    res = {label: [] for label, _ in routes}
+    for th0 in starts:
+        for label, strategy in routes:
             t0 = time.perf_counter()
             r = m.fit(th0, lo=lo, hi=hi, step=step, tol_edm=1e-10, strategy=strategy, hessian=2)
-            times.append(1e3 * (time.perf_counter() - t0))
-            evals.append(r["n_eval"])
-            thetas.append((r["theta"], r["err"], r["status"]))
-        res[label] = thetas
-        out[label] = {"strategy": strategy, "hessian": 2, "p50_ms": float(np.percentile(times, 50)),
-                      "p99_ms": float(np.percentile(times, 99)), "mean_passes": float(np.mean(evals)),
-                      "converged": int(sum(t[2] == 0 for t in thetas))}
+            times[label].append(1e3 * (time.perf_counter() - t0))
+            evals[label].append(r["n_eval"])
+            res[label].append((r["theta"], r["err"], r["status"]))
+    for label, strategy in routes:
+        out[label] = {"strategy": strategy, "hessian": 2, "p50_ms": float(np.percentile(times[label], 50)),
+                      "p99_ms": float(np.percentile(times[label], 99)), "mean_passes": float(np.mean(evals[label])),
+                      "converged": int(sum(t[2] == 0 for t in res[label]))}
     # the same fits to EDM 1e-14, where two routes to one minimum agree to 1e-6 of the
     # uncertainty (at 1e-10 they may differ by up to sqrt(2e-10) = 1.4e-5 of it)
     tight = {}
