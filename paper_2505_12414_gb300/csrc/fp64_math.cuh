@@ -1,12 +1,15 @@
-// fp64_math.cuh -- FP64 building blocks of the fused kernels (device code only).
+// fp64_math.cuh -- FP64 building blocks of the fused kernels (device code; the integer
+// exponential and its helpers also compile for the host).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
+#include <string.h>
 
 namespace gbnll {
 
-// Size of the 2^(j/N) table used by fexp (held in shared memory by every block).
+// Size of the 2^(j/N) table used by fexp_scaled (held in shared memory by every block).
 constexpr int kExpTableBits = 10;
 constexpr int kExpTable = 1 << kExpTableBits;
 
@@ -34,7 +37,10 @@ constexpr double kLn2Tail = 0x1.ef35793c76730p-45;
 inline void fill_device_tables(double* t)
 {
     const long double pi = 3.141592653589793238462643383279502884L;
-    for (int j = 0; j < kExpTable; ++j) t[j] = (double)exp2l((long double)j / (long double)kExpTable);
+    for (int j = 0; j < kExpTable; ++j) {  // 2^(j/N) 2^62 as an integer in the slot's bits
+        const uint64_t v = (uint64_t)llroundl(ldexpl(exp2l((long double)j / (long double)kExpTable), 62));
+        memcpy(t + j, &v, sizeof v);
+    }
     for (int j = 0; j <= kLogSteps; ++j) {
         const long double F = 1.0L + (long double)j / (long double)kLogSteps;
         const long double l = logl(F);
@@ -51,35 +57,87 @@ inline void fill_device_tables(double* t)
     }
 }
 
-// exp(xs / S), S = N/ln2, after Tang's table-driven method (P. T. P. Tang, ACM TOMS 15
-// (1989) 144), N = 1024.  The argument arrives pre-scaled (the kernels fold S into the
-// hoisted constants), so the reduction is exact without a split constant:
-//   xs = N q + j + r,  |r| <= 1/2,  exp(xs / S) = 2^q 2^(j/N) exp(r ln2/N).
-// exp(r ln2/N) - 1 is a cubic in r obtained by Chebyshev economisation of the degree-4
-// Taylor polynomial on [-ln2/2N, ln2/2N] (the r^4 term replaced by its best lower-degree
-// approximation), with the powers of ln2/N folded into the coefficients; truncation error
-// below 0.62 ulp of 1.  |xs| >= 1.04e6 (|x| >= 704) returns 0 (xs < 0) or +inf (xs > 0,
-// and NaN).  7 FP64 instructions on the fast path.
-__device__ __forceinline__ double fexp_scaled(double xs, const double* __restrict__ tab)
+// Bit patterns and integer products that compile the same on the host and the device (the
+// host build of the exponential below serves its accuracy tests).
+__host__ __device__ __forceinline__ uint64_t bits_of(double x)
 {
-    const double kMagic = 0x1.8p52;  // 1.5 * 2^52: xs + kMagic rounds xs to an integer
-    const double C1 = 0x1.62e42fefa39efp-11;  // ln2/N
-    const double C2 = 0x1.ebfbe046f706bp-23;  // (1/2 + h^2/24) (ln2/N)^2, h = ln2/2N
-    const double C3 = 0x1.c6b08d704a0c0p-35;  // (1/6) (ln2/N)^3
-    const double C0 = -0x1.3b2ab6fba4e77p-54;  // -h^4/192
-    double kd = xs + kMagic;
-    int k = __double2loint(kd);
-    double kf = kd - kMagic;
-    double r = xs - kf;  // exact
-    double T = tab[k & (kExpTable - 1)];
-    double p = fma(r, C3, C2);
-    p = fma(p, r, C1);
-    p = fma(p, r, C0);
-    double y = fma(T, p, T);
-    int hi = __double2hiint(y) + ((k >> kExpTableBits) << 20);
-    y = __hiloint2double(hi, __double2loint(y));
-    int xhi = __double2hiint(xs);
-    if ((xhi & 0x7fffffff) >= 0x412fbd00) y = (xhi < 0) ? 0.0 : __longlong_as_double(0x7ff0000000000000ll);
+#ifdef __CUDA_ARCH__
+    return (uint64_t)__double_as_longlong(x);
+#else
+    uint64_t b;
+    memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+
+__host__ __device__ __forceinline__ double double_of(uint64_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)b);
+#else
+    double x;
+    memcpy(&x, &b, sizeof x);
+    return x;
+#endif
+}
+
+__host__ __device__ __forceinline__ uint32_t umulhi32(uint32_t a, uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// floor(a b / 2^64) - d, 0 <= d <= 2: the three upper 32-bit partial products; the lowest one
+// and the carries out of the middle column are dropped (3 integer multiplies).
+__host__ __device__ __forceinline__ uint64_t umulhi64_trunc(uint64_t a, uint64_t b)
+{
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    return (uint64_t)a1 * b1 + ((uint64_t)umulhi32(a1, b0) + umulhi32(a0, b1));
+}
+
+// ln 2 in 0.64 fixed point, rounded.
+constexpr uint64_t kLn2Q64 = 0xb17217f7d1cf79acull;
+
+// exp(xs / S), S = N/ln2, N = 1024, with Tang's table reduction (P. T. P. Tang, ACM TOMS 15
+// (1989) 144) carried out in fixed-point integer arithmetic, so that the exponential costs no
+// FP64 instruction (on GB300 an FP64 warp instruction holds its SM sub-partition's FP64 pipe
+// for 64 cycles; an integer one a few).  The argument arrives pre-scaled (the kernels fold S
+// into the hoisted constants):
+//   xs = k + f, k = floor(xs), 0 <= f < 1 (read off the bits of xs exactly),
+//   exp(xs / S) = 2^(k >> 10) 2^((k & 1023)/N) exp(x), x = f ln2/N in [0, 6.77e-4),
+// exp(x) - 1 = x (1 + x (1/2 + x (1/6 + x/24))) in fixed point, each factor to the precision
+// its term needs (the omitted x^5/120 is below 1.2e-18), the table holding 2^(j/N) 2^62 as
+// integers.  The result is rounded once from 63 bits: error below 0.52 ulp.  |xs| >= 1.04e6
+// (|x| >= 704) returns 0 (xs < 0) or +inf (xs > 0, and NaN).
+__host__ __device__ __forceinline__ double fexp_scaled(double xs, const double* __restrict__ tab)
+{
+    const uint64_t b = bits_of(xs);
+    const uint32_t hi = (uint32_t)(b >> 32);
+    int sh = 1075 - (int)((hi >> 20) & 0x7ff);  // |xs| = M 2^-sh
+    sh = sh > 33 ? sh : 33;                      // reached only by the saturated range
+    const uint64_t M = (b & 0x000fffffffffffffull) | (1ull << 52);
+    const uint32_t ip = (uint32_t)(M >> 32) >> (sh - 32 < 31 ? sh - 32 : 31);      // floor |xs|
+    uint64_t F = sh <= 64 ? M << (64 - sh) : (sh < 128 ? M >> (sh - 64) : 0ull);  // frac |xs|, 2^64
+    int k = (int)ip;
+    if (hi >> 31) {  // xs = -(ip + frac) = -(ip + 1) + (1 - frac)
+        k = -k - (F != 0ull ? 1 : 0);
+        F = 0ull - F;
+    }
+    const uint64_t X = umulhi64_trunc(F, kLn2Q64);                          // x 2^74
+    const uint32_t Xh = (uint32_t)(X >> 32);                                // x 2^42
+    const uint32_t Q3 = 2863311531u + umulhi32(Xh, 699051u);                // (1/6 + x/24) 2^34
+    const uint64_t Q2 = (1ull << 62) + ((uint64_t)umulhi32(Xh, Q3) << 19);  // (1/2 + x q3) 2^63
+    const uint64_t Q1 = (1ull << 63) + (umulhi64_trunc(X, Q2) >> 10);       // (1 + x q2) 2^63
+    const uint64_t P = umulhi64_trunc(X, Q1);                               // (exp(x) - 1) 2^73
+    const uint64_t T = bits_of(tab[k & (kExpTable - 1)]);                   // 2^(j/N) 2^62
+    const uint64_t Y = T + (umulhi64_trunc(T, P) >> 9);                     // 2^(j/N) exp(x) 2^62
+    const int s = (int)(Y >> 63);                                           // Y < 2^63 but for rounding
+    const uint64_t m = (Y + (512ull << s)) >> (10 + s);                     // 53 bits; may carry to 2^53
+    double y = double_of(((uint64_t)((k >> kExpTableBits) + 1023 + s) << 52) + (m - (1ull << 52)));
+    if ((hi & 0x7fffffff) >= 0x412fbd00u) y = (hi >> 31) ? 0.0 : double_of(0x7ff0000000000000ull);
     return y;
 }
 
@@ -150,14 +208,45 @@ __device__ __forceinline__ double frcp_approx(double x)
     return y;
 }
 
-// 1/x from the hardware approximation plus one cubic correction: with e = 1 - x y0,
-// 1/x = y0 / (1 - e) = y0 (1 + e + e^2 + ...).  3 FP64 instructions + 1 MUFU.
-__device__ __forceinline__ double frcp(double x)
+// 1/x for a finite normal double x (either sign) in integer arithmetic, so that it costs no FP64
+// instruction: x = +-m 2^E, m in [1, 2); a single-precision seed y0 ~ 1/m (hardware reciprocal
+// of m's leading 24 bits; on the host, the rounded single-precision quotient), the residual
+// e = 1 - m y0 exactly (|e| < 2^-21: the 53 x 31-bit product taken modulo 2^64), and
+//   1/m = y0 / (1 - e) = y0 (1 + e + e^2) + y0 e^3 / (1 - e),
+// the last term below 2^-62 of the result.  One rounding from 62 bits: error below 0.51 ulp.
+// |x| >= 2^1022 returns +-0 (the result would be subnormal), subnormal x and 0 return +-inf.
+__host__ __device__ __forceinline__ double frcp(double x)
 {
-    const double y = frcp_approx(x);
-    double e = fma(-x, y, 1.0);
-    double t = fma(e, e, e);
-    return fma(y, t, y);
+    const uint64_t b = bits_of(x);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int be = (int)((hi >> 20) & 0x7ff);
+    const uint64_t M = (b & 0x000fffffffffffffull) | (1ull << 52);  // m 2^52
+    const uint32_t mf_bits = 0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29);  // m to 24 bits
+    uint32_t yb;
+#ifdef __CUDA_ARCH__
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(__uint_as_float(mf_bits)));
+    yb = __float_as_uint(y0);
+#else
+    float mf;
+    memcpy(&mf, &mf_bits, sizeof mf);
+    const float y0 = 1.0f / mf;
+    memcpy(&yb, &y0, sizeof yb);
+#endif
+    const int ye = (int)(yb >> 23) - 120;                                  // y0 in (0.49, 1]
+    const uint32_t Y0 = ((yb & 0x7fffffu) | 0x800000u) << (ye > 0 ? ye : 0);  // y0 2^30, exact
+    const int64_t E = (int64_t)(0ull - M * (uint64_t)Y0);                  // e 2^82 (2^82 = 0 mod 2^64)
+    const int32_t Eh = (int32_t)(E >> 32);                                 // e 2^50
+    const int64_t t = E + (((int64_t)Eh * Eh) >> 18);                      // (e + e^2) 2^82
+    const int64_t u = (int64_t)(int32_t)(t >> 32) * (int64_t)Y0 + umulhi32((uint32_t)t, Y0);  // y0 (e + e^2) 2^80
+    const uint64_t Y = ((uint64_t)Y0 << 32) + (uint64_t)(u >> 18);         // 1/m 2^62, in (2^61, 2^62]
+    const int s = (int)((Y >> 62) & 1);
+    const uint64_t m53 = (Y + (256ull << s)) >> (9 + s);                   // 53 bits; may carry to 2^53
+    const uint64_t sign = b & 0x8000000000000000ull;
+    uint64_t r = sign | ((((uint64_t)(2045 - be + s)) << 52) + (m53 - (1ull << 52)));
+    if (be >= 2045) r = sign;                                              // |1/x| below the normal range
+    if (be == 0) r = sign | 0x7ff0000000000000ull;
+    return double_of(r);
 }
 
 // 1/x from the hardware approximation plus one Newton step y0 (1 + e): relative error e^2.

@@ -4,6 +4,8 @@ import pytest
 
 from paper_2505_12414_gb300 import synth
 
+import test_math_host as hm
+
 pytestmark = pytest.mark.gpu
 
 
@@ -11,22 +13,15 @@ def ulp_err(a, ref):
     return np.abs(a - ref) / np.spacing(np.abs(ref))
 
 
-def test_table_exponential_accuracy(gpu_lib):
-    # the kernels' exponential takes its argument pre-scaled by S = 1024/ln2
-    S = 1024.0 / np.log(2.0)
-    rs = synth.Stream(21, 0)
-    xs = np.concatenate([
-        (2 * rs.uniform(200000) - 1) * 703.0 * S,       # the whole fast range
-        (2 * rs.uniform(200000) - 1) * 40.0 * S,        # the range the likelihood uses
-        (2 * rs.uniform(50000) - 1) * 2.0,              # a few table steps around zero
-        np.array([0.0, -0.0, 0.5, -0.5, 1023.5, -1024.5, 1e-300, 703.9 * S, -703.9 * S]),
-    ])
+def test_table_exponential_accuracy(gpu_lib, tmp_path):
+    # the kernels' exponential takes its argument pre-scaled by S = 1024/ln2; it is integer
+    # arithmetic throughout, so the device must reproduce the host build bit for bit
+    xs = hm.exp_arguments(21)
     y = gpu_lib.nll_diag_math(0, xs)
-    # reference exp(xs ln2 / 1024) in extended precision (x87 80-bit here, binary128 on Arm)
-    ln2 = np.log(np.longdouble(2.0))
-    ref = np.exp(xs.astype(np.longdouble) * (ln2 / np.longdouble(1024.0)))
-    err = np.abs(y.astype(np.longdouble) - ref) / np.spacing(ref.astype(np.float64)).astype(np.longdouble)
-    assert float(err.max()) <= 2.0, float(err.max())
+    err = hm.ulp_error(y, hm.exp_reference(xs))
+    assert float(err.max()) < 0.52, float(err.max())
+    host = hm.host_math(hm.host_math_binary(tmp_path), "exp", xs, tmp_path)
+    np.testing.assert_array_equal(y.view(np.int64), host.view(np.int64))
     # the saturated range: 0 below -1.04e6 (|x| >= 704), +inf above
     big = np.array([-1.04e6, -2e6, -1e300, -np.inf, 1.04e6, 1e300, np.inf])
     yb = gpu_lib.nll_diag_math(0, big)
@@ -34,14 +29,13 @@ def test_table_exponential_accuracy(gpu_lib):
 
 
 def test_reciprocal_accuracy(gpu_lib):
-    rs = synth.Stream(22, 0)
-    x = np.concatenate([
-        np.exp((2 * rs.uniform(200000) - 1) * 60.0),
-        -np.exp((2 * rs.uniform(20000) - 1) * 60.0),
-        np.array([1.0, 2.0, 3.0, 0.1, 1.0 - 2 ** -52, 1.0 + 2 ** -52]),
-    ])
+    # the hardware single-precision seed refined in integer arithmetic (the host build of the same
+    # refinement is checked without a GPU)
+    x = hm.rcp_arguments(22)
     y = gpu_lib.nll_diag_math(1, x)
-    assert ulp_err(y, 1.0 / x).max() <= 1.0
+    err = hm.ulp_error(y, np.longdouble(1) / x.astype(np.longdouble))
+    assert float(err.max()) < 0.51, float(err.max())
+    assert np.all(np.signbit(y) == np.signbit(x))
 
 
 def test_table_sincos_accuracy(gpu_lib):
