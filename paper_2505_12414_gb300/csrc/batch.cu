@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) batch_eval(BatchDev b)
         double acc[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) acc[k] = 0.0;
-        LogProd lpx{1.0, 0}, lpy{1.0, 0};
+        LogProd lpx = logprod_one(), lpy = logprod_one();
         int bad = 0;
         for (int64_t p = pb + threadIdx.x; p < pe; p += blockDim.x) {
             PairIn in;

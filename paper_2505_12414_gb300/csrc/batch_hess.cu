@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
         double tacc[TM];
 #pragma unroll
         for (int r = 0; r < TM; ++r) tacc[r] = 0.0;
-        LogProd lp{1.0, 0};
+        LogProd lp = logprod_one();
         double lnp_tot = 0.0;
         if (ok) {
             for (int64_t e = e0; e < ev.n; e += kHessThreads) {

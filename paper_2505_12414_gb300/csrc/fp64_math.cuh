@@ -16,10 +16,11 @@ constexpr int kExpTable = 1 << kExpTableBits;
 // Scale of the exponential's argument: fexp_scaled(x * kExpArgScale) = exp(x).
 constexpr double kExpArgScale = 0x1.71547652b82fep+10;  // N/ln2, N = 1024
 
-// log table after the exp table: for F_j = 1 + j/128, j = 0..128, ln F_j split into a head
-// (a multiple of 2^-42) and a tail, and 1/F_j; padded to an even count.
+// log table after the exp table, for F_j = 1 + j/128, j = 0..127, as integers in the slots'
+// bits: ln F_j 2^115 as two 64-bit words (high words, then low words), then 1/F_j 2^63;
+// padded to an even count.
 constexpr int kLogSteps = 128;
-constexpr int kLogTab = 3 * (kLogSteps + 1) + 1;
+constexpr int kLogTab = 3 * kLogSteps;
 constexpr int kLogOffset = kExpTable;
 // sin/cos table: (cos, sin) of k pi/512 for k = 0..1023 (a full period), after the log table.
 constexpr int kTrigSteps = 1024;
@@ -27,13 +28,32 @@ constexpr int kTrigOffset = kExpTable + kLogTab;  // even: the (cos, sin) pairs 
 constexpr int kTabDoubles = kTrigOffset + 2 * kTrigSteps;  // one table per translation unit
 static_assert(kTrigOffset % 2 == 0, "16-byte aligned (cos, sin) pairs");
 
-// ln 2 split for the logarithm: head with 42 significant bits (e ln2_head is exact for any
-// binary exponent e of a double) and the rest.
-constexpr double kLn2Head = 0x1.62e42fefa3800p-1;
-constexpr double kLn2Tail = 0x1.ef35793c76730p-45;
+// ln 2 2^115 (two 64-bit words), for the logarithm's fixed-point sum; equals
+// ln_ratio_q115(2, 1) (checked by the tests).
+constexpr uint64_t kLn2Q115Hi = 0x58b90bfbe8e7bull;
+constexpr uint64_t kLn2Q115Lo = 0xcd5e4f1d9cc01f98ull;
 
-// Host: the values of the device table, rounded from long double; the exact zeros of sin and
-// cos at multiples of pi/2 are set exactly (long double pi is not pi).
+// Host: ln(a/b) 2^115 for integers 0 < b <= a < 3b, from ln(a/b) = 2 atanh(z), z = (a-b)/(a+b),
+// summed as 2 sum z^(2k+1)/(2k+1) in 0.126-bit fixed point (|z| <= 1/2: 64 terms leave less than
+// 2^-126; each term is truncated, so the sum is at most 2^-119 low), rounded to 2^-115.  Integer
+// arithmetic only, so the tables come out the same on every host.
+inline unsigned __int128 ln_ratio_q115(uint64_t a, uint64_t b)
+{
+    const uint64_t num = a - b, den = a + b;  // z = num/den
+    const unsigned __int128 one = (unsigned __int128)1 << 126;
+    unsigned __int128 pw = one / den * num + (one % den) * num / den;  // z 2^126
+    unsigned __int128 sum = 0;
+    for (int k = 0; k < 64 && pw != 0; ++k) {
+        sum += pw / (unsigned __int128)(2 * k + 1);
+        pw = pw / den * num;  // times z^2 in two steps, each truncated
+        pw = pw / den * num;
+    }
+    return (2 * sum + ((unsigned __int128)1 << 10)) >> 11;  // 2 sum, 2^126 -> 2^115
+}
+
+// Host: the values of the device table (the exponential's and the logarithm's in integer
+// fixed point); the exact zeros of sin and cos at multiples of pi/2 are set exactly (long
+// double pi is not pi).
 inline void fill_device_tables(double* t)
 {
     const long double pi = 3.141592653589793238462643383279502884L;
@@ -41,15 +61,12 @@ inline void fill_device_tables(double* t)
         const uint64_t v = (uint64_t)llroundl(ldexpl(exp2l((long double)j / (long double)kExpTable), 62));
         memcpy(t + j, &v, sizeof v);
     }
-    for (int j = 0; j <= kLogSteps; ++j) {
-        const long double F = 1.0L + (long double)j / (long double)kLogSteps;
-        const long double l = logl(F);
-        const double head = (double)(nearbyintl(ldexpl(l, 42)) / 4398046511104.0L);  // multiple of 2^-42
-        t[kLogOffset + j] = head;
-        t[kLogOffset + (kLogSteps + 1) + j] = (double)(l - (long double)head);
-        t[kLogOffset + 2 * (kLogSteps + 1) + j] = (double)(1.0L / F);
+    for (int j = 0; j < kLogSteps; ++j) {
+        const unsigned __int128 l = ln_ratio_q115(kLogSteps + j, kLogSteps);
+        const uint64_t words[3] = {(uint64_t)(l >> 64), (uint64_t)l,
+                                   (uint64_t)((((unsigned __int128)1 << 70) + (kLogSteps + j) / 2) / (unsigned)(kLogSteps + j))};
+        for (int w = 0; w < 3; ++w) memcpy(t + kLogOffset + w * kLogSteps + j, &words[w], sizeof(uint64_t));
     }
-    t[kLogOffset + kLogTab - 1] = 0.0;
     for (int k = 0; k < kTrigSteps; ++k) {
         const long double a = pi * (long double)k / 512.0L;
         t[kTrigOffset + 2 * k] = (k % 512 == 256) ? 0.0 : (double)cosl(a);
@@ -141,34 +158,80 @@ __host__ __device__ __forceinline__ double fexp_scaled(double xs, const double* 
     return y;
 }
 
-// ln x for a positive normal double x, after Tang's table-driven method (P. T. P. Tang,
-// ACM TOMS 16 (1990) 378): x = 2^e m, m in [1, 2), F = 1 + j/128 the table point nearest m
-// (j from the top mantissa bits with integer instructions), f = m - F (exact, |f| <= 1/256),
-// u = f / F = f (1/F) with |u| <= 2^-8, and
-//   ln x = (e ln2_head + ln F_head) + (e ln2_tail + ln F_tail + ln(1 + u)),
-// the first sum exact (both heads are multiples of 2^-42), ln(1 + u) from its Taylor series
-// through u^7 (the next term is below 2e-18 relative).  14 FP64 instructions.  The caller
-// guarantees x positive and normal (the kernels check that before taking the logarithm).
-__device__ __forceinline__ double flog(double x, const double* __restrict__ tab)
+// Leading zeros of a 64-bit word (64 for 0).
+__host__ __device__ __forceinline__ int clz64(uint64_t v)
 {
-    const int hi = __double2hiint(x);
-    const int mh = hi & 0x000fffff;
-    const int j = (mh + (1 << 12)) >> 13;                      // nearest of 128 steps (0..128)
-    const double m = __hiloint2double(mh | 0x3ff00000, __double2loint(x));
-    const double F = __hiloint2double(0x3ff00000 + (j << 13), 0);
-    const double ed = (double)((hi >> 20) - 1023);
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// a + s t for s = -1 (neg false) or +1 (neg true), in 2^64 arithmetic.
+__host__ __device__ __forceinline__ uint64_t add_signed(uint64_t a, uint64_t t, bool neg)
+{
+    return neg ? a + t : a - t;
+}
+
+__host__ __device__ __forceinline__ uint32_t add_signed32(uint32_t a, uint32_t t, bool neg)
+{
+    return neg ? a + t : a - t;
+}
+
+// ln x for a positive normal double x, after Tang's table-driven method (P. T. P. Tang,
+// ACM TOMS 16 (1990) 378) carried out in fixed-point integer arithmetic, so that it costs no
+// FP64 instruction: x = 2^E m with F = 1 + j/128 (j = 0..127) the table point nearest m (m near
+// 2 counts as 2 (m/2) with F = 1), f = m - F exact, u = f/F = f (1/F) with |u| <= 2^-8, and
+//   ln x = E ln2 + ln F + u g(u),  g(u) = ln(1 + u)/u = 1 - u/2 + u^2/3 - ... - u^7/8
+// (the next term is below 2^-67), summed in a signed 128-bit accumulator at scale 2^115 (ln 2
+// and ln F to 2^-115 from the table; u to 2^-70, exact for F = 1, so results near x = 1 keep
+// their relative accuracy), then normalised and rounded once: error below 0.51 ulp.  The
+// caller guarantees x positive and normal (the kernels check that before taking the log).
+__host__ __device__ __forceinline__ double flog(double x, const double* __restrict__ tab)
+{
+    const uint64_t b = bits_of(x);
+    int E = (int)((b >> 52) & 0x7ff) - 1023;
+    const uint64_t M = (b & 0x000fffffffffffffull) | (1ull << 52);  // m 2^52
+    int j = (int)(((b >> 32) & 0xfffffu) + (1u << 12)) >> 13;       // nearest of 128 steps (0..128)
+    int64_t f;                                                       // (m - F) 2^53, |f| <= 2^45
+    if (j == kLogSteps) {  // m/2 in [1 - 2^-9, 1): F = 1 at the next exponent
+        E += 1;
+        j = 0;
+        f = (int64_t)M - (1ll << 53);
+    } else {
+        f = (int64_t)(M << 1) - ((1ll << 53) + ((int64_t)j << 46));
+    }
+    const bool neg = f < 0;
     const double* lt = tab + kLogOffset;
-    const double u = (m - F) * lt[2 * (kLogSteps + 1) + j];
-    const double q = u * u;
-    double t = fma(u, 1.0 / 7.0, -1.0 / 6.0);
-    t = fma(u, t, 1.0 / 5.0);
-    t = fma(u, t, -1.0 / 4.0);
-    t = fma(u, t, 1.0 / 3.0);
-    t = fma(u, t, -1.0 / 2.0);
-    const double p = fma(q, t, u);
-    const double head = fma(ed, kLn2Head, lt[j]);
-    const double tail = fma(ed, kLn2Tail, lt[(kLogSteps + 1) + j]);
-    return head + (tail + p);
+    // |u| 2^70 (|f| 2^18 (1/F) 2^63 / 2^64); exact for F = 1
+    const uint64_t ua = umulhi64_trunc((uint64_t)(neg ? -f : f) << 18, bits_of(lt[2 * kLogSteps + j]));
+    // g(u) by Horner from the inside, c_k - u (c_(k+1) - u (...)) with c_k = 1/(k+1); the level
+    // of c_k enters g times u^k, so it needs 2^-63 / 2^-8k: 32 bits for c_4..c_6, 64 below
+    const uint32_t uh = (uint32_t)(ua >> 31);                                       // |u| 2^39
+    uint32_t h = add_signed32(0x24924925u, umulhi32(uh, 0x20000000u) >> 7, neg);    // 1/7 - u/8, 2^32
+    h = add_signed32(0x2aaaaaabu, umulhi32(uh, h) >> 7, neg);                        // 1/6 - u (..)
+    h = add_signed32(0x33333333u, umulhi32(uh, h) >> 7, neg);                        // 1/5 - u (..)
+    uint64_t H = add_signed(0x4000000000000000ull, umulhi64_trunc(ua, (uint64_t)h << 32) >> 6, neg);  // 1/4, 2^64
+    H = add_signed(0x5555555555555555ull, umulhi64_trunc(ua, H) >> 6, neg);         // 1/3 - u (..)
+    H = add_signed(0x8000000000000000ull, umulhi64_trunc(ua, H) >> 6, neg);         // 1/2 - u (..)
+    const uint64_t g = add_signed(1ull << 63, umulhi64_trunc(ua, H) >> 7, neg);     // g(u) 2^63
+    // u g(u) 2^115 and the sum
+    const unsigned __int128 ug = ((unsigned __int128)ua * g) >> 18;
+    const __int128 ln2 = (__int128)(((unsigned __int128)kLn2Q115Hi << 64) | kLn2Q115Lo);
+    const __int128 lnF = (__int128)(((unsigned __int128)bits_of(lt[j]) << 64) | bits_of(lt[kLogSteps + j]));
+    __int128 acc = (__int128)E * ln2 + lnF;
+    acc = neg ? acc - (__int128)ug : acc + (__int128)ug;
+    // round to double
+    const bool rneg = acc < 0;
+    unsigned __int128 a = rneg ? (unsigned __int128)(-acc) : (unsigned __int128)acc;
+    const uint64_t ahi = (uint64_t)(a >> 64);
+    const int lz = ahi ? clz64(ahi) : 64 + clz64((uint64_t)a);
+    if (lz >= 128) return 0.0;  // x = 1
+    a <<= lz;
+    const uint64_t m = (uint64_t)(((a >> 74) + 1) >> 1);  // 53 bits, rounded; may carry to 2^53
+    const uint64_t r = ((uint64_t)(1035 - lz) << 52) + (m - (1ull << 52));
+    return double_of(r | (rneg ? 0x8000000000000000ull : 0ull));
 }
 
 // sin x and cos x for |x| <= pi (any x is safe; accuracy degrades slowly beyond), from the
@@ -264,25 +327,38 @@ __device__ __forceinline__ int not_positive_normal(double x)
     return (unsigned)(__double2hiint(x) - 0x00100000) >= 0x7fe00000u;
 }
 
-// Running product with the binary exponent split off: value = m * 2^e, m in [1, 2).
+// Running product with the binary exponent split off, in integer arithmetic (no FP64
+// instruction): value = m 2^(e - 63), m in [2^63, 2^64) (a 64-bit mantissa).  Each factor's
+// mantissa multiplies in with the three upper partial products (umulhi64_trunc: at most
+// 2^-62 below the exact product, far below a double rounding), its exponent adds to e.
 struct LogProd {
-    double m;
+    uint64_t m;
     int e;
 };
 
-__device__ __forceinline__ void logprod_mul(LogProd& lp, double x)
+__host__ __device__ __forceinline__ LogProd logprod_one() { return LogProd{1ull << 63, 0}; }
+
+// Multiply by 2^ex q/2^63 for a mantissa q in [2^63, 2^64).
+__host__ __device__ __forceinline__ void logprod_mul_mant(LogProd& lp, uint64_t q, int ex)
 {
-    double q = lp.m * x;
-    int hi = __double2hiint(q);
-    lp.e += (hi >> 20) - 1023;
-    lp.m = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(q));
+    const uint64_t p = umulhi64_trunc(lp.m, q);  // (m/2^63)(q/2^63) 2^62, in [2^62, 2^64)
+    const int top = (int)(p >> 63);
+    lp.m = top ? p : p << 1;
+    lp.e += ex + top;
 }
 
-// Product of two running products (exact exponent bookkeeping, one rounding).
-__device__ __forceinline__ LogProd logprod_combine(const LogProd& a, const LogProd& b)
+// Multiply by a positive normal double x (integer pipe only).
+__host__ __device__ __forceinline__ void logprod_mul(LogProd& lp, double x)
 {
-    LogProd r{a.m, a.e + b.e};
-    logprod_mul(r, b.m);
+    const uint64_t b = bits_of(x);
+    logprod_mul_mant(lp, ((b & 0x000fffffffffffffull) | (1ull << 52)) << 11, (int)((b >> 52) & 0x7ff) - 1023);
+}
+
+// Product of two running products.
+__host__ __device__ __forceinline__ LogProd logprod_combine(const LogProd& a, const LogProd& b)
+{
+    LogProd r{a.m, a.e};
+    logprod_mul_mant(r, b.m, b.e);
     return r;
 }
 
@@ -297,11 +373,13 @@ __device__ __forceinline__ LogProd logprod_warp(LogProd lp)
     return lp;
 }
 
-__device__ __forceinline__ double logprod_value(const LogProd& lp)
+// ln of the product: ln(m 2^-63) + e ln2, the mantissa rounded to a double in [1, 2].
+__host__ __device__ __forceinline__ double logprod_value(const LogProd& lp)
 {
     const double kLn2hi = 0x1.62e42ff000000p-1, kLn2lo = -0x1.718432a1b0e26p-35;
+    const double md = double_of((1023ull << 52) + (((lp.m >> 10) + 1) >> 1) - (1ull << 52));
     double e = (double)lp.e;
-    return fma(e, kLn2hi, fma(e, kLn2lo, log(lp.m)));
+    return fma(e, kLn2hi, fma(e, kLn2lo, log(md)));
 }
 
 }  // namespace gbnll

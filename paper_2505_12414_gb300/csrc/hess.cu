@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
         cj[k] = a.sij[kHessMaxSlots + sc];
     }
     double acc[3] = {0.0, 0.0, 0.0};
-    LogProd lp{1.0, 0};  // unweighted: product of this thread's densities
+    LogProd lp = logprod_one();  // unweighted: product of this thread's densities
     const int64_t ntiles = (a.ev.n + kHessThreads - 1) / kHessThreads;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         stage_event<KIND, VAR, W>(a.ev, a.c, tile * kHessThreads + t, z, t, s_tab, lp);

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256, 1) fused_nll_kernel(const KArgs a)
     double acc[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] = 0.0;
-    LogProd lpx{1.0, 0}, lpy{1.0, 0};
+    LogProd lpx = logprod_one(), lpy = logprod_one();
     int bad = 0;
     const KConst& c = a.c;
 

@@ -56,7 +56,7 @@ def test_table_sincos_accuracy(gpu_lib):
         assert float(err.max()) <= 2.0, (fn, float(err.max()), x[np.argmax(err)])
 
 
-def test_table_log_accuracy(gpu_lib):
+def test_table_log_accuracy(gpu_lib, tmp_path):
     # the weighted kernels take ln P from the table-driven logarithm (positive normal P)
     rs = synth.Stream(29, 0)
     F = 1.0 + np.arange(129) / 128.0
@@ -69,19 +69,23 @@ def test_table_log_accuracy(gpu_lib):
         np.array([0.5, 1.0, 2.0, np.nextafter(2.0, 0.0), np.nextafter(1.0, 0.0), np.nextafter(1.0, 2.0),
                   np.finfo(np.float64).tiny, np.finfo(np.float64).max]),
     ])
+    x = np.concatenate([x, hm.log_arguments(30)])
     ref = np.log(x.astype(np.longdouble))
     y = gpu_lib.nll_diag_math(4, x)
     ok = ref != 0
     assert np.all(y[~ok] == 0.0)
     err = np.abs(y[ok].astype(np.longdouble) - ref[ok]) / np.spacing(np.abs(ref[ok]).astype(np.float64)).astype(np.longdouble)
-    assert float(err.max()) <= 1.0, (float(err.max()), x[ok][np.argmax(err)])
+    assert float(err.max()) < 0.51, (float(err.max()), x[ok][np.argmax(err)])
+    # integer arithmetic throughout: the device reproduces the host build bit for bit
+    host = hm.host_math(hm.host_math_binary(tmp_path), "log", x, tmp_path)
+    np.testing.assert_array_equal(y.view(np.int64), host.view(np.int64))
 
 
 def test_reciprocal_correction_order(gpu_lib):
-    """Why the kernels correct the hardware reciprocal cubically: rcp.approx.ftz.f64 alone is
-    good to about 2^-20, so one Newton step (error e^2) leaves about 2^-40 (1e-12, which would
-    enter every gradient term), while the cubic step (error e^3) reaches a correctly rounded
-    result (test_reciprocal_accuracy)."""
+    """Why a reciprocal refinement keeps the e^2 term: a hardware approximation alone
+    (rcp.approx.ftz.f64 here) is good to about 2^-20, so one Newton step (error e^2) leaves
+    about 2^-40 (1e-12, which would enter every gradient term); the kernels' refinement
+    y0 (1 + e + e^2) has error e^3 and rounds to within 0.51 ulp (test_reciprocal_accuracy)."""
     rs = synth.Stream(24, 0)
     x = np.concatenate([np.exp((2 * rs.uniform(400000) - 1) * 600.0), 1.0 + rs.uniform(200000)])
     xl = x.astype(np.longdouble)

@@ -1,11 +1,13 @@
-"""The kernels' integer exponential and reciprocal (fexp_scaled, frcp), built for the host from the
-same header, against extended-precision references (no GPU).  The exponential is integer
-arithmetic throughout, so the host build computes the device's results bit for bit (test_gpu_math
-checks that on a GPU); the reciprocal's host build seeds with the rounded single-precision
+"""The kernels' integer exponential, logarithm, reciprocal and running product (fexp_scaled, flog,
+frcp, LogProd), built for the host from the same header, against extended-precision references (no GPU).  The exponential and the
+logarithm are integer arithmetic throughout, so the host build computes the device's results bit
+for bit (test_gpu_math checks that on a GPU); the reciprocal's host build seeds with the rounded single-precision
 quotient where the device takes the hardware approximation, and refines the seed the same way."""
 import os
 import shutil
 import subprocess
+
+from decimal import Decimal, getcontext
 
 import numpy as np
 import pytest
@@ -110,3 +112,68 @@ def test_integer_reciprocal_accuracy(tmp_path):
     edge = host_math(binary, "rcp", np.array([2.0 ** 1022, -(2.0 ** 1023), 0.0, -0.0, 1e-310]), tmp_path)
     assert edge[0] == 0.0 and edge[1] == 0.0 and np.signbit(edge[1])
     assert np.isinf(edge[2]) and edge[2] > 0 and np.isinf(edge[3]) and edge[3] < 0 and np.isinf(edge[4])
+
+
+def test_integer_running_product(tmp_path):
+    # ln of products of 64 factors spanning many binades, against the sum of extended-precision logs
+    binary = host_math_binary(tmp_path)
+    rs = synth.Stream(33, 0)
+    x = np.exp((2 * rs.uniform(64 * 4000) - 1) * 30.0)
+    x[:64] = 1.0                      # the empty product's neutral factors
+    x[64:128] = 2.0 ** -1022          # the smallest normal, 64 times
+    x[128:192] = 1.0 + 2.0 ** -52     # one ulp above 1, 64 times
+    y = host_math(binary, "lprod", x, tmp_path)
+    ref = np.log(x.astype(np.longdouble)).reshape(-1, 64).sum(axis=1)
+    err = np.abs(y.astype(np.longdouble) - ref)
+    # 64 truncated products (< 2^-62 each), the mantissa rounded to 53 bits, log and the e ln2 terms
+    bound = 64 * 2.0 ** -62 + 2.0 ** -53 + 4 * np.spacing(np.abs(ref.astype(np.float64))).astype(np.longdouble)
+    assert np.all(err <= bound), float((err / bound).max())
+    assert y[0] == 0.0
+
+
+def log_arguments(seed):
+    rs = synth.Stream(seed, 0)
+    steps = 1.0 + np.arange(257) / 256.0  # table points and the midpoints between them
+    return np.concatenate([
+        np.exp((2 * rs.uniform(300000) - 1) * 700.0),  # the whole normal range
+        rs.uniform(100000) + 1e-300,                    # (0, 1], as in the generator
+        1.0 + (2 * rs.uniform(100000) - 1) * 2.0 ** -8,  # around 1, where ln x is small
+        1.0 + (2 * rs.uniform(20000) - 1) * 2.0 ** -40,
+        steps, np.nextafter(steps, 0.0), np.nextafter(steps, 3.0), steps / 2, np.nextafter(steps / 2, 0.0),
+        np.array([1.0, 1.0 + 2.0 ** -52, 1.0 - 2.0 ** -53, 2.0, 0.5, 2.0 ** -1022, np.finfo(np.float64).max,
+                  np.e, 10.0, 0.1]),
+    ])
+
+
+def test_integer_logarithm_accuracy(tmp_path):
+    binary = host_math_binary(tmp_path)
+    x = log_arguments(34)
+    y = host_math(binary, "log", x, tmp_path)
+    ref = np.log(x.astype(np.longdouble))
+    err = ulp_error(y, ref)
+    assert float(err.max()) < 0.51, float(err.max())
+    assert y[x == 1.0].tolist() == [0.0] * int((x == 1.0).sum())
+    np.testing.assert_array_equal(np.sign(y), np.sign(np.log(x)))
+
+
+def test_logarithm_tables_against_decimal(tmp_path):
+    # ln F_j 2^115 and 1/F_j 2^63 (F_j = 1 + j/128) and ln 2 2^115, against 60-digit decimals
+    binary = host_math_binary(tmp_path)
+    src = tmp_path / "none.bin"
+    np.zeros(1).tofile(src)
+    out = tmp_path / "tab.bin"
+    subprocess.check_call([binary, "logtab", str(src), str(out)])
+    w = [int(v) for v in np.fromfile(out, dtype=np.uint64)]
+    n = 128
+    getcontext().prec = 60
+    for j in range(n):
+        F = 1 + Decimal(j) / 128
+        lnF = (w[j] << 64) | w[n + j]
+        exact = F.ln() * (Decimal(2) ** 115)
+        assert abs(Decimal(lnF) - exact) <= 1, j
+        inv = w[2 * n + j]
+        assert abs(Decimal(inv) - (Decimal(2) ** 63) / F) <= Decimal("0.5"), j
+    ln2_series = (w[3 * n] << 64) | w[3 * n + 1]
+    ln2_const = (w[3 * n + 2] << 64) | w[3 * n + 3]
+    assert ln2_series == ln2_const
+    assert abs(Decimal(ln2_const) - Decimal(2).ln() * (Decimal(2) ** 115)) <= Decimal("0.5")
