@@ -84,6 +84,9 @@ struct nll_model {
 
     // launch shape
     int bps = 2, threads = 256, variant = 0;
+    // resident blocks per SM of the fused kernel, by [variant - 1][grad][threads / 64 - 1]
+    // (0: not asked yet, -1: the occupancy query gave nothing)
+    int occ[2][2][4] = {};
 
     // profiling
     bool profiling = false;
@@ -345,6 +348,21 @@ int hoist(nll_model* m, const double* th, bool grad, Hoist& H)
     return hoist_core(m->kind, m->ranges, th, grad, H, &m->err);
 }
 
+// Resident blocks per SM of the fused kernel that a launch at this shape would run (cached).
+int fused_resident(nll_model* m, int variant, bool grad, int threads)
+{
+    if (variant < 1 || variant > 2 || threads < 64 || threads > 256 || threads % 64) return -1;
+    int& o = m->occ[variant - 1][grad ? 1 : 0][threads / 64 - 1];
+    if (o == 0) {
+        const int r = fused_occupancy(m->kind, variant, m->weighted, grad, threads, m->in_place);
+        o = r > 0 ? r : -1;
+    }
+    return o;
+}
+
+// Blocks of a fused launch: bps per SM, at most the blocks one wave holds (the kernel strides
+// over the pairs, so blocks past the resident ones would only wait for a second wave), and no
+// more than the pairs need.
 int launch_blocks(const nll_model* m, int bps, int threads)
 {
     int64_t npairs = (m->n + 1) / 2;
@@ -391,7 +409,8 @@ int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int
         a.done = m->d_done;
         a.seq = next_seq(m);
     }
-    int blocks = launch_blocks(m, bps, threads);
+    const int resident = fused_resident(m, variant, grad, threads);
+    int blocks = launch_blocks(m, resident > 0 && resident < bps ? resident : bps, threads);
     cudaError_t e;
     if (record && m->profiling) cudaEventRecord(m->ev0, m->stream);
     e = launch_fused(m->kind, variant, m->weighted, grad, blocks, threads, m->stream, a, m->in_place);
@@ -656,6 +675,7 @@ void reset_events(nll_model* m, bool release)
     m->d_w = nullptr;
     m->loaded = m->weighted = m->has_basis = false;
     m->in_place = false;
+    memset(m->occ, 0, sizeof m->occ);  // the next load may pick other kernels (weights, in place)
     for (int d = 0; d < 4; ++d) m->ip_col[d] = nullptr;
     m->ip_w = nullptr;
     m->n = m->n_pad = 0;
@@ -1002,15 +1022,16 @@ int nll_autotune(nll_model* m)
     if (cudaSetDevice(m->device) != cudaSuccess) return fail(m, NLL_ERR_CUDA, "cudaSetDevice failed");
     m->ms_pending = false;  // the sweep below re-records ev0/ev1
     m->last_ms = -1.0;
-    // candidate shapes: for each block size, 1x and 2x the resident blocks per SM
+    // candidate shapes: for each block size, one wave of resident blocks and one block fewer per
+    // SM (launches never exceed one wave)
     std::vector<std::pair<int, int>> shapes;
     bool grad_ok = m->last.f > 0.0 && m->last.f < 1.0;
     for (int thr : {64, 128, 192, 256}) {
         int occ = fused_occupancy(m->kind, effective_variant(m) < 0 ? kVarDirect : effective_variant(m), m->weighted,
-                                  grad_ok, thr);
+                                  grad_ok, thr, m->in_place);
         if (occ <= 0) continue;
-        for (int mult : {1, 2})
-            if (occ * mult <= 32) shapes.push_back({occ * mult, thr});
+        shapes.push_back({std::min(occ, 32), thr});
+        if (occ > 1) shapes.push_back({std::min(occ - 1, 32), thr});
     }
     std::vector<int> variants;
     if (m->kind == kKstar4D && m->has_basis && m->variant == NLL_VARIANT_AUTO) {
