@@ -95,6 +95,8 @@ struct KArgs {
 struct SArgs {
     const double* col[4];
     const double* w;
+    double* dst[4];  // non-null: the kernel also stores col[d] there (a copy read in place)
+    double* dst_w;   // the same for w
     int64_t n;
     int ndim;
     double lo[4], hi[4];
@@ -236,6 +238,9 @@ struct NoAllocScratch {
 };
 // Device addresses of the scratch on `device` (which must be current); set up once per device.
 cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out);
+// True when p is ordinary (pageable, unregistered) host memory that kernels on `device` can
+// read in place (the device reports pageable memory access, as with ATS over NVLink-C2C).
+bool host_pageable_readable(int device, const void* p);
 int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads,
                     bool in_place = false);  // resident blocks/SM
 // Order key of a double: key(x) <= key(y) iff x <= y for non-NaN x, y (-0 < +0); NaNs fall

@@ -149,7 +149,10 @@ __global__ void __launch_bounds__(64) final_reduce_kernel(const double* partials
 }
 
 // ----------------------------------------------------------------------------------
-// Load-time statistics and range validation: sum w, sum w (m - ma), events outside.
+// Load-time statistics and range validation: sum w, sum w (m - ma), events outside.  With
+// dst pointers set, the kernel also stores what it reads there: columns in host memory that the
+// device reads in place (pageable memory with ATS) arrive in the event store in the same pass,
+// with no host-side staging copy.
 // ----------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) stats_kernel(const SArgs a)
 {
@@ -158,9 +161,11 @@ __global__ void __launch_bounds__(256) stats_kernel(const SArgs a)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
         double w = a.w ? a.w[i] : 1.0;
+        if (a.dst_w) a.dst_w[i] = w;
         bool outside = !(w >= 0.0 && w <= 1.0e300);  // also catches NaN
         for (int d = 0; d < a.ndim; ++d) {
             double x = a.col[d][i];
+            if (a.dst[d]) a.dst[d][i] = x;
             outside |= !(x >= a.lo[d] && x <= a.hi[d]);
         }
         double m = a.col[0][i];

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -339,6 +340,31 @@ int hoist_core(int kind, const double* ranges, const double* th, bool grad, Hois
     return NLL_OK;
 }
 
+}  // namespace gbnll
+
+namespace gbnll {
+bool host_pageable_readable(int device, const void* p)
+{
+    static std::atomic<int> attr[64];  // 0: not asked, 1: no pageable access, 2: access
+    if (device < 0 || device >= 64 || !p) return false;
+    int a = attr[device].load(std::memory_order_relaxed);
+    if (a == 0) {
+        int pageable = 0;
+        if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess) {
+            cudaGetLastError();
+            pageable = 0;
+        }
+        a = pageable ? 2 : 1;
+        attr[device].store(a, std::memory_order_relaxed);
+    }
+    if (a != 2) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeUnregistered;
+}
 }  // namespace gbnll
 
 namespace {
@@ -684,16 +710,21 @@ void reset_events(nll_model* m, bool release)
 
 void free_events(nll_model* m) { reset_events(m, true); }
 
-int run_stats(nll_model* m, const double* const* cols, const double* w, int64_t n, double out[3])
+// Range check and sums of the loaded events (stats_kernel); dst/dst_w (may be null) receive
+// the columns read from host memory in place.
+int run_stats(nll_model* m, const double* const* cols, double* const* dst, const double* w, double* dst_w, int64_t n,
+              double out[3])
 {
     SArgs s;
     memset(&s, 0, sizeof s);
     for (int d = 0; d < m->ndim; ++d) {
         s.col[d] = cols[d];
+        s.dst[d] = dst ? dst[d] : nullptr;
         s.lo[d] = m->ranges[2 * d];
         s.hi[d] = m->ranges[2 * d + 1];
     }
     s.w = w;
+    s.dst_w = dst_w;
     s.n = n;
     s.ndim = m->ndim;
     s.partials = m->d_partials;
@@ -890,13 +921,35 @@ int nll_load_events(nll_model* m, const double* const* columns, const double* we
             e = cudaMemsetAsync(m->d_ev + (size_t)c * n_pad + n_events, 0,
                                 sizeof(double) * (size_t)(n_pad - n_events), m->stream);
     }
+    // Columns in pageable host memory that the device reads in place (ATS) are copied by the
+    // statistics kernel as it reads them; the rest by DMA (device or pinned memory) or the
+    // driver's staged copy.
     cudaMemcpyKind kindc = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    for (int d = 0; d < m->ndim && e == cudaSuccess && n_events > 0; ++d)
-        e = cudaMemcpyAsync(m->d_ev + (size_t)d * n_pad, columns[d], sizeof(double) * n_events, kindc, m->stream);
+    const double* src[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* dst[4] = {nullptr, nullptr, nullptr, nullptr};
+    const double* src_w = nullptr;
+    double* dst_w = nullptr;
+    for (int d = 0; d < m->ndim && e == cudaSuccess && n_events > 0; ++d) {
+        double* to = m->d_ev + (size_t)d * n_pad;
+        if (!on_device && host_pageable_readable(m->device, columns[d])) {
+            src[d] = columns[d];
+            dst[d] = to;
+        } else {
+            src[d] = to;
+            e = cudaMemcpyAsync(to, columns[d], sizeof(double) * n_events, kindc, m->stream);
+        }
+    }
     if (weights) {
         m->d_w = m->d_ev + (size_t)ncols * n_pad;
-        if (e == cudaSuccess && n_events > 0)
-            e = cudaMemcpyAsync(m->d_w, weights, sizeof(double) * n_events, kindc, m->stream);
+        src_w = m->d_w;
+        if (e == cudaSuccess && n_events > 0) {
+            if (!on_device && host_pageable_readable(m->device, weights)) {
+                src_w = weights;
+                dst_w = m->d_w;
+            } else {
+                e = cudaMemcpyAsync(m->d_w, weights, sizeof(double) * n_events, kindc, m->stream);
+            }
+        }
     }
     if (e != cudaSuccess) {
         free_events(m);
@@ -906,9 +959,7 @@ int nll_load_events(nll_model* m, const double* const* columns, const double* we
     m->weighted = weights != nullptr;
     double stats[3] = {0.0, 0.0, 0.0};
     if (n_events > 0) {
-        const double* dcols[4];
-        for (int d = 0; d < m->ndim; ++d) dcols[d] = m->d_ev + (size_t)d * n_pad;
-        int st = run_stats(m, dcols, m->d_w, n_events, stats);
+        int st = run_stats(m, src, dst, src_w, dst_w, n_events, stats);
         if (st != NLL_OK) {
             free_events(m);
             return st;

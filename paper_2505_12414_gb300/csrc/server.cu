@@ -43,7 +43,7 @@ struct nll_server {
     int kind = 0, ndim = 0, npar = 0, device = 0, sm_count = 0;
     DevBudget budget;  // device memory of this server (limit from GBNLL_DEVICE_ALLOC_LIMIT)
     cudaStream_t stream = nullptr;   // steps and start passes
-    cudaStream_t cstream = nullptr;  // admission and collection
+    cudaStream_t cstream = nullptr;  // admission and collection (highest stream priority)
     double ranges[8] = {0};
     int max_slots = 0;
     int64_t pool_events = 0, n_pad = 0;
@@ -316,7 +316,10 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
     s->max_units = (int)mu;
     cudaError_t e = ensure_btab(device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking);
+    // admissions and collections wait on the host: their kernels go ahead of queued step blocks
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->cstream, cudaStreamNonBlocking, prio_greatest);
     // every slot's Hessian units fit: the pool holds at most pool_events events
     const int64_t cap = s->pool_events / kHessUnitEvents + max_slots + 1;
     if (e == cudaSuccess && s->cfg.strategy == 2)
@@ -506,18 +509,30 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
     if (slot < 0 || !pool_alloc(s, len, &begin)) return sfail(s, NLL_ERR_STATE, "no free slot or pool range");
     // The pool range is free: no queued step or pass reads it, so the request's events go in on
     // the collection stream without waiting for the steps in flight.
+    // Columns in pageable host memory that the device reads in place (ATS) go into the pool as
+    // the statistics kernel reads them, with no host-side staging copy; the rest by cudaMemcpyAsync.
     const cudaStream_t cs = s->cstream;
     cudaError_t e = cudaSuccess;
-    for (int d = 0; d < s->ndim && e == cudaSuccess && n_events > 0; ++d)
-        e = cudaMemcpyAsync(s->d_ev + (size_t)d * s->n_pad + begin, columns[d], sizeof(double) * n_events,
-                            cudaMemcpyHostToDevice, cs);
+    const double* src[4] = {nullptr, nullptr, nullptr, nullptr};
+    double* dst[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int d = 0; d < s->ndim && e == cudaSuccess && n_events > 0; ++d) {
+        double* to = s->d_ev + (size_t)d * s->n_pad + begin;
+        if (host_pageable_readable(s->device, columns[d])) {
+            src[d] = columns[d];
+            dst[d] = to;
+        } else {
+            src[d] = to;
+            e = cudaMemcpyAsync(to, columns[d], sizeof(double) * n_events, cudaMemcpyHostToDevice, cs);
+        }
+    }
     // range check and sum (m - ma) of the request on the device (load-time statistics kernel)
     double sum = 0.0;
     if (e == cudaSuccess && n_events > 0) {
         SArgs sa;
         memset(&sa, 0, sizeof sa);
         for (int d = 0; d < s->ndim; ++d) {
-            sa.col[d] = s->d_ev + (size_t)d * s->n_pad + begin;
+            sa.col[d] = src[d];
+            sa.dst[d] = dst[d];
             sa.lo[d] = s->ranges[2 * d];
             sa.hi[d] = s->ranges[2 * d + 1];
         }
@@ -527,8 +542,10 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
         sa.partials = s->d_spart;
         sa.ticket = s->d_sticket;
         sa.out = s->d_sout;
-        const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n_events + 255) / 256, 1), 2 * s->sm_count);
-        e = launch_stats(blocks, 256, cs, sa);
+        // small blocks (64 threads, 2 warps): they fit beside the step kernels' resident blocks,
+        // so an admission does not wait for a step to drain its SM
+        const int blocks = (int)std::min<int64_t>(std::max<int64_t>((n_events + 63) / 64, 1), 2 * s->sm_count);
+        e = launch_stats(blocks, 64, cs, sa);
     }
     if (e == cudaSuccess && s->kind == kKstar4D && n_events > 0) {
         BArgs ba;
@@ -537,8 +554,8 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
         ba.phi = s->d_ev + (size_t)kColPhi * s->n_pad + begin;
         for (int j = 0; j < 13; ++j) ba.out[j] = s->d_ev + (size_t)(kColH0 + j) * s->n_pad + begin;
         ba.n = n_events;
-        int blocks = (int)std::min<int64_t>((n_events + 255) / 256, (int64_t)s->sm_count * 8);
-        e = launch_basis(std::max(blocks, 1), 256, cs, ba);
+        int blocks = (int)std::min<int64_t>((n_events + 63) / 64, (int64_t)s->sm_count * 16);
+        e = launch_basis(std::max(blocks, 1), 64, cs, ba);
     }
     // the copies read the caller's buffers and the check decides the admission: wait for them
     if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
