@@ -280,15 +280,17 @@ int nll_precomputed_basis(nll_model* m, double* out);
 int nll_calibrate_fp64(int device, double* rates);
 
 /*
- * nll_diag_math -- diagnostic: evaluate the library's device FP64 building blocks on n
- * host inputs x, writing host outputs y (fn 0: the table-driven exponential used by the
- * kernels, after Tang's method, which takes its argument pre-scaled: y = exp(x ln2/1024);
- * fn 1: the reciprocal, hardware approximation plus one cubic correction; fn 2 / fn 3:
- * sin x / cos x by the table method with Cody-Waite reduction, accurate for |x| <= pi, as
- * the 4D kernels use it for phi; fn 4: ln x after Tang's table-driven method, for positive
- * normal x, as the weighted kernels use it; fn 5: the hardware approximation of 1/x alone
- * (rcp.approx.ftz.f64); fn 6: that approximation plus one Newton step).  For accuracy tests
- * against the host's libm; allocates temporary device buffers.
+ * nll_diag_math -- diagnostic: evaluate the library's device building blocks on n host
+ * inputs x, writing host outputs y (fn 0: the exponential used by the kernels, Tang's table
+ * method in fixed-point integer arithmetic, which takes its argument pre-scaled: y =
+ * exp(x ln2/1024); fn 1: the reciprocal, a single-precision seed refined in integer
+ * arithmetic; fn 2 / fn 3: sin x / cos x by the table method in integer arithmetic, for
+ * |x| < 1024, as the 4D kernels use it for phi; fn 4: ln x after Tang's table method in
+ * integer arithmetic, for positive normal x, as the weighted kernels use it; fn 5: the
+ * hardware approximation of 1/x alone (rcp.approx.ftz.f64); fn 6: that approximation plus
+ * one Newton step; fn 7: the square root in integer arithmetic, as the angular basis uses
+ * it).  For accuracy tests against the host's extended precision; allocates temporary device
+ * buffers; NLL_ERR_ARG for another fn.
  */
 int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n);
 

@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(256) diag_kernel(int fn, const double* x, doub
             v = gbnll::frcp_approx(x[i]);
         } else if (fn == 6) {
             v = gbnll::frcp_newton(x[i]);
+        } else if (fn == 7) {
+            v = gbnll::fsqrt(x[i]);
         } else {
             double sv, cv;
             gbnll::fsincos_pi(x[i], s_tab + gbnll::kTrigOffset, sv, cv);
@@ -100,7 +102,7 @@ __global__ void __launch_bounds__(256) diag_kernel(int fn, const double* x, doub
 
 extern "C" int nll_diag_math(int device, int fn, const double* x, double* y, int64_t n)
 {
-    if (fn < 0 || fn > 6 || n < 0 || (n > 0 && (!x || !y))) return NLL_ERR_ARG;
+    if (fn < 0 || fn > 7 || n < 0 || (n > 0 && (!x || !y))) return NLL_ERR_ARG;
     if (n == 0) return NLL_OK;
     if (cudaSetDevice(device) != cudaSuccess) return NLL_ERR_CUDA;
     if (upload_table() != cudaSuccess) return NLL_ERR_CUDA;

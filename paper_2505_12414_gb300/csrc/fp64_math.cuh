@@ -22,7 +22,8 @@ constexpr double kExpArgScale = 0x1.71547652b82fep+10;  // N/ln2, N = 1024
 constexpr int kLogSteps = 128;
 constexpr int kLogTab = 3 * kLogSteps;
 constexpr int kLogOffset = kExpTable;
-// sin/cos table: (cos, sin) of k pi/512 for k = 0..1023 (a full period), after the log table.
+// sin/cos table: |cos| and |sin| of k pi/512 for k = 0..1023 (a full period) as integers
+// 2^63 in the slots' bits (pairs), after the log table; the signs follow from k.
 constexpr int kTrigSteps = 1024;
 constexpr int kTrigOffset = kExpTable + kLogTab;  // even: the (cos, sin) pairs are read as double2
 constexpr int kTabDoubles = kTrigOffset + 2 * kTrigSteps;  // one table per translation unit
@@ -51,9 +52,8 @@ inline unsigned __int128 ln_ratio_q115(uint64_t a, uint64_t b)
     return (2 * sum + ((unsigned __int128)1 << 10)) >> 11;  // 2 sum, 2^126 -> 2^115
 }
 
-// Host: the values of the device table (the exponential's and the logarithm's in integer
-// fixed point); the exact zeros of sin and cos at multiples of pi/2 are set exactly (long
-// double pi is not pi).
+// Host: the values of the device table, all in integer fixed point; the exact zeros and ones
+// of sin and cos at multiples of pi/2 are set exactly (long double pi is not pi).
 inline void fill_device_tables(double* t)
 {
     const long double pi = 3.141592653589793238462643383279502884L;
@@ -69,8 +69,10 @@ inline void fill_device_tables(double* t)
     }
     for (int k = 0; k < kTrigSteps; ++k) {
         const long double a = pi * (long double)k / 512.0L;
-        t[kTrigOffset + 2 * k] = (k % 512 == 256) ? 0.0 : (double)cosl(a);
-        t[kTrigOffset + 2 * k + 1] = (k % 512 == 0) ? 0.0 : (double)sinl(a);
+        uint64_t cs[2];
+        cs[0] = (k % 512 == 256) ? 0ull : (k % 512 == 0) ? (1ull << 63) : (uint64_t)llroundl(ldexpl(fabsl(cosl(a)), 63));
+        cs[1] = (k % 512 == 0) ? 0ull : (k % 512 == 256) ? (1ull << 63) : (uint64_t)llroundl(ldexpl(fabsl(sinl(a)), 63));
+        memcpy(t + kTrigOffset + 2 * k, cs, sizeof cs);
     }
 }
 
@@ -234,32 +236,134 @@ __host__ __device__ __forceinline__ double flog(double x, const double* __restri
     return double_of(r | (rneg ? 0x8000000000000000ull : 0ull));
 }
 
-// sin x and cos x for |x| <= pi (any x is safe; accuracy degrades slowly beyond), from the
-// classical table method with Cody-Waite reduction (W. J. Cody and W. Waite, Software Manual
-// for the Elementary Functions, 1980): x = k pi/512 + r with k = rint(512 x/pi) and
-// |r| <= pi/1024, the reduction x - k (P1 + P2) done with two FMAs (P1 + P2 = pi/512 to ~106
-// bits, so r carries at most one rounding); sin r and cos r - 1 from their Taylor series
-// through r^5 and r^4 (the next terms are below 2e-19 and 2e-18 relative at |r| = pi/1024);
-// then
-//   sin x = S + (S (cos r - 1) + C sin r),  cos x = C + (C (cos r - 1) - S sin r)
-// with (C, S) = (cos, sin)(k pi/512) from the table.  15 FP64 instructions, no branch.
-__device__ __forceinline__ void fsincos_pi(double x, const double* __restrict__ trig, double& s, double& c)
+// sqrt x for x >= 0 in integer arithmetic, so that it costs no FP64 instruction: x = m 2^E with
+// E even and m in [1, 4) (in 2.62 fixed point), a single-precision seed y0 ~ 1/sqrt(m) (hardware
+// reciprocal square root; on the host the rounded single-precision quotient), the residual
+// e = 1 - m y0^2 (|e| < 2^-20), and 1/sqrt(m) = y0 (1 + e/2 + 3e^2/8) + O(e^3), then sqrt(m) =
+// m (1/sqrt(m)) and one rounding: error below 0.52 ulp.  +0 and -0 return themselves, +inf
+// itself; subnormal x returns 0 and negative x or NaN return NaN.
+__host__ __device__ __forceinline__ double fsqrt(double x)
 {
-    const double kMagic = 0x1.8p52;
-    const double kScale = 0x1.45f306dc9c883p+7;  // 512/pi
-    const double P1 = 0x1.921fb54442d18p-8;      // pi/512, leading 53 bits
-    const double P2 = 0x1.1a62633145c07p-62;     // pi/512 - P1
-    double kd = fma(x, kScale, kMagic);
-    int k = __double2loint(kd);
-    double kf = kd - kMagic;
-    double r = fma(-kf, P1, x);
-    r = fma(-kf, P2, r);
-    double r2 = r * r;
-    double sr = fma(r * r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), r);
-    double cm = r2 * fma(r2, 1.0 / 24.0, -0.5);  // cos r - 1
-    const double2 cs = reinterpret_cast<const double2*>(trig)[k & (kTrigSteps - 1)];
-    s = fma(cs.y, cm, fma(cs.x, sr, cs.y));
-    c = fma(cs.x, cm, fma(-cs.y, sr, cs.x));
+    const uint64_t b = bits_of(x);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (be == 0x7ff || (b >> 63)) return (b << 1) == 0 ? x : (b == 0x7ff0000000000000ull ? x : double_of(0x7ff8000000000000ull));
+    if (be == 0) return double_of(b & 0x8000000000000000ull);  // 0, and subnormals flushed
+    const int E = be - 1023;
+    const int odd = E & 1;
+    const uint64_t MM = ((b & 0x000fffffffffffffull) | (1ull << 52)) << (10 + odd);  // m 2^62, m in [1, 4)
+    const uint32_t mf_bits = (uint32_t)(MM >> (39 + odd)) + ((uint32_t)(126 + odd) << 23);  // m to 24 bits as a float
+    uint32_t yb;
+#ifdef __CUDA_ARCH__
+    float y0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(__uint_as_float(mf_bits)));
+    yb = __float_as_uint(y0);
+#else
+    float mf;
+    memcpy(&mf, &mf_bits, sizeof mf);
+    const float y0 = 1.0f / sqrtf(mf);
+    memcpy(&yb, &y0, sizeof yb);
+#endif
+    const int ye = (int)(yb >> 23) - 120;                                        // y0 in (0.49, 1]
+    const uint64_t Y0 = (uint64_t)(((yb & 0x7fffffu) | 0x800000u) << (ye > 0 ? ye : 0));  // y0 2^30, exact
+    const int64_t e = (int64_t)(1ull << 60) - (int64_t)umulhi64_trunc(MM, (Y0 * Y0) << 2);  // (1 - m y0^2) 2^60
+    const int64_t eh = e >> 20;                                                  // e 2^40
+    const int64_t t = (e >> 1) + ((3 * (eh * eh)) >> 23);                        // (e/2 + 3e^2/8) 2^60
+    const uint64_t Y = (Y0 << 32) + (uint64_t)(int64_t)(((__int128)t * (int64_t)Y0) >> 28);  // 1/sqrt(m) 2^62
+    const uint64_t S = (uint64_t)(((unsigned __int128)MM * Y) >> 62);           // sqrt(m) 2^62, in [2^62, 2^63)
+    const uint64_t m53 = ((S >> 9) + 1) >> 1;                                    // 53 bits; may carry to 2^53
+    return double_of(((uint64_t)((E - odd) / 2 + 1023) << 52) + (m53 - (1ull << 52)));
+}
+
+// pi/512 2^116 (two 64-bit words) and 512/pi 2^55, for the sine and cosine's reduction.
+constexpr uint64_t kPi512Q116Hi = 0x1921fb54442dull;
+constexpr uint64_t kPi512Q116Lo = 0x18469898cc51701cull;
+constexpr uint64_t k512PiQ55 = 0x517cc1b727220a95ull;
+
+// v 2^e2 as a double, rounded from v's leading 64 bits (v > 0, result in the normal range).
+__host__ __device__ __forceinline__ double u64_scaled_to_double(uint64_t v, int e2)
+{
+    const int lz = clz64(v);
+    const uint64_t m = (((v << lz) >> 10) + 1) >> 1;  // 53 bits, rounded; may carry to 2^53
+    return double_of(((uint64_t)(63 - lz + e2 + 1023) << 52) + (m - (1ull << 52)));
+}
+
+// A signed 128-bit fixed-point value a 2^-126 as a double (|a| <= 2^127 - 1).
+__host__ __device__ __forceinline__ double q126_to_double(__int128 a)
+{
+    if (a == 0) return 0.0;
+    const bool neg = a < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-a) : (unsigned __int128)a;
+    const uint64_t hi = (uint64_t)(u >> 64);
+    const int lz = hi ? clz64(hi) : 64 + clz64((uint64_t)u);
+    const double r = u64_scaled_to_double((uint64_t)((u << lz) >> 64), -62 - lz);  // the leading 64 bits
+    return neg ? -r : r;
+}
+
+// sin x and cos x for |x| < 1024 (NaN beyond), from the classical table method (Cody-Waite
+// style reduction to x = k pi/512 + r, W. J. Cody and W. Waite, Software Manual for the
+// Elementary Functions, 1980) carried out in fixed-point integer arithmetic, so that it costs
+// no FP64 instruction: |x| 2^116 read off the bits exactly, k = round(512 |x|/pi), r = |x| -
+// k pi/512 in a signed 128-bit word (pi/512 to 2^-116), |r| <= pi/1024;
+//   sin r = r (1 - r^2/6 + r^4/120 - r^6/5040),  1 - cos r = (r^2/2)(1 - r^2/12 + r^4/360)
+// (the next terms are below 2^-62 relative); then
+//   sin |x| = S (1 - (1 - cos r)) + C sin r,  cos |x| = C (1 - (1 - cos r)) - S sin r
+// summed exactly in 128-bit words at 2^-126 from the table's |cos|, |sin| of k pi/512 (2^-63)
+// and rounded once.  Where the table's S (or C) is exactly 0 the result is +-sin r itself,
+// which keeps its relative accuracy (sin x near 0 and +-pi, cos x near +-pi/2).  |x| < 2^-26
+// returns sin x = x, cos x = 1 (correctly rounded there).  Error below 1 ulp.
+__host__ __device__ __forceinline__ void fsincos_pi(double x, const double* __restrict__ trig, double& s, double& c)
+{
+    const uint64_t b = bits_of(x);
+    const int be = (int)((b >> 52) & 0x7ff);
+    if (be < 1023 - 26) {
+        s = x;
+        c = 1.0;
+        return;
+    }
+    if (be >= 1023 + 10) {
+        s = c = double_of(0x7ff8000000000000ull);
+        return;
+    }
+    const uint64_t M = (b & 0x000fffffffffffffull) | (1ull << 52);
+    const unsigned __int128 XF = (unsigned __int128)M << (be - 1023 + 64);                  // |x| 2^116
+    const int k = (int)((umulhi64_trunc((uint64_t)(XF >> 64), k512PiQ55) + (1ull << 42)) >> 43);  // round(512|x|/pi)
+    const unsigned __int128 P = ((unsigned __int128)kPi512Q116Hi << 64) | kPi512Q116Lo;
+    const __int128 R = (__int128)(XF - (unsigned __int128)k * P);                          // r 2^116
+    const bool rneg = R < 0;
+    const unsigned __int128 Ra = rneg ? (unsigned __int128)(-R) : (unsigned __int128)R;
+    const uint64_t Rh = (uint64_t)(Ra >> 52);                                                // |r| 2^64
+    const uint64_t r2 = umulhi64_trunc(Rh, Rh);                                              // r^2 2^64
+    uint64_t h = 0x0222222222222222ull - umulhi64_trunc(r2, 0x000d00d00d00d00dull);          // 1/120 - r^2/5040
+    h = 0x2aaaaaaaaaaaaaabull - umulhi64_trunc(r2, h);                                       // 1/6 - r^2 (..)
+    const uint64_t gs = (1ull << 63) - (umulhi64_trunc(r2, h) >> 1);                         // sin r / r, 2^63
+    const uint64_t hc = 0x1555555555555555ull - umulhi64_trunc(r2, 0x00b60b60b60b60b6ull);   // 1/12 - r^2/360
+    const uint64_t gc = (1ull << 63) - (umulhi64_trunc(r2, hc) >> 1);                        // 2(1 - cos r)/r^2, 2^63
+    const uint64_t cm = umulhi64_trunc(r2, gc) >> 1;                                         // 1 - cos r, 2^63
+    // |sin r| = sr 2^(-51 - lz): |r| normalised (relative accuracy), times sin r / r
+    const uint64_t rhi = (uint64_t)(Ra >> 64);
+    const int lz = rhi ? clz64(rhi) : 64 + clz64((uint64_t)Ra);
+    const uint64_t sr = lz < 128 ? umulhi64_trunc((uint64_t)((Ra << (lz & 127)) >> 64), gs) : 0ull;
+    const uint64_t sr63 = lz < 76 ? sr >> (lz - 12) : 0ull;  // |sin r| 2^63 (lz >= 20; below 2^-63 it is 0)
+    // table: |cos|, |sin| of j pi/512 with their signs from j
+    const int j = k & (kTrigSteps - 1);
+    const uint64_t Cm = bits_of(trig[2 * j]), Sm = bits_of(trig[2 * j + 1]);
+    const bool cneg = j > 256 && j < 768, sneg = j > 512;
+    const unsigned __int128 pc = (unsigned __int128)Cm * ((1ull << 63) - cm), ps = (unsigned __int128)Sm * ((1ull << 63) - cm);
+    const unsigned __int128 qc = (unsigned __int128)Cm * sr63, qs = (unsigned __int128)Sm * sr63;
+    // sin |x| = S(1 - cm) + C sin r, cos |x| = C(1 - cm) - S sin r, at 2^-126
+    const __int128 as = (sneg ? -(__int128)ps : (__int128)ps) + ((cneg != rneg) ? -(__int128)qc : (__int128)qc);
+    const __int128 ac = (cneg ? -(__int128)pc : (__int128)pc) - ((sneg != rneg) ? -(__int128)qs : (__int128)qs);
+    double sv = q126_to_double(as), cv = q126_to_double(ac);
+    if (lz < 128) {  // a zero table entry: the result is +-sin r, to its relative accuracy
+        const double sin_r = u64_scaled_to_double(sr, -51 - lz);
+        if (Sm == 0) sv = (cneg != rneg) ? -sin_r : sin_r;
+        if (Cm == 0) cv = (sneg != rneg) ? sin_r : -sin_r;
+    } else {
+        if (Sm == 0) sv = 0.0;
+        if (Cm == 0) cv = 0.0;
+    }
+    s = (b >> 63) ? -sv : sv;
+    c = cv;
 }
 
 // The hardware reciprocal approximation alone (diagnostics: its accuracy decides how many

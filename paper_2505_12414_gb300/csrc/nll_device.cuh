@@ -17,7 +17,7 @@ namespace gbnll {
 //   h0 = c sin^2 tK (3/4 + cos 2tl / 4), hFL = c cos^2 tK (1 - cos 2tl) - h0, ...
 // with c = 9/(32 pi).  Also the Chebyshev inputs T2(ctl), T2(ctk), phi/pi, T2(phi/pi).
 // sin tK and sin tl enter only as their product (one square root of the product of the
-// squares), and sin/cos phi come from the table method (trig = the (cos, sin) table).
+// squares, fsqrt), and sin/cos phi come from the table method (trig = the |cos|, |sin| table).
 // ----------------------------------------------------------------------------------
 __device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi, double h[9], double& t2l,
                                               double& t2k, double& xp, double& t2p, const double* trig)
@@ -26,7 +26,7 @@ __device__ __forceinline__ void angular_basis(double ctl, double ctk, double phi
     const double c2 = 0x1.6eb167b830193p-3;  // 2 c
     const double kInvPi = 0x1.45f306dc9c883p-2;
     const double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);  // sin^2 tl, sin^2 tK
-    const double sksl = sqrt(sk2 * sl2);                                // sin tK sin tl
+    const double sksl = fsqrt(sk2 * sl2);                               // sin tK sin tl
     double sp, cp;
     fsincos_pi(phi, trig, sp, cp);
     t2l = fma(-2.0, sl2, 1.0);  // cos 2tl = 1 - 2 sin^2 tl
@@ -62,7 +62,7 @@ __device__ __forceinline__ void angular_basis_direct(double ctl, double ctk, dou
     const double kInvPi = 0x1.45f306dc9c883p-2;
     const double sl2 = fma(-ctl, ctl, 1.0), sk2 = fma(-ctk, ctk, 1.0);
     const double a = sk2 * sl2;
-    const double sksl = sqrt(a);
+    const double sksl = fsqrt(a);
     double sp, cp;
     fsincos_pi(phi, trig, sp, cp);
     t2l = fma(-2.0, sl2, 1.0);

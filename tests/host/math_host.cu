@@ -1,6 +1,7 @@
-// Host build of the kernels' integer exponential, logarithm, reciprocal and running product
-// (fexp_scaled, flog, frcp, LogProd) for their accuracy tests: `math_host exp|log|rcp in.bin
-// out.bin` applies the function, with the device table's contents, to the doubles of in.bin;
+// Host build of the kernels' integer exponential, logarithm, reciprocal, square root, sine/cosine
+// and running product (fexp_scaled, flog, frcp, fsqrt, fsincos_pi, LogProd) for their accuracy
+// tests: `math_host exp|log|rcp|sqrt in.bin out.bin` applies the function, with the device table's contents, to the
+// doubles of in.bin (`sincos` writes sin x, cos x for each);
 // `math_host lprod ...` writes ln of the product of each run of 64 inputs (logprod_mul, then
 // logprod_value); `math_host logtab - out.bin` writes the logarithm's table words followed by
 // ln_ratio_q115(2, 1) and the kLn2Q115 constant (high word, low word each).
@@ -32,14 +33,20 @@ int main(int argc, char** argv)
         return n == w.size() ? 0 : 5;
     }
     const bool is_exp = strcmp(fn, "exp") == 0, is_lprod = strcmp(fn, "lprod") == 0, is_log = strcmp(fn, "log") == 0;
-    if (!is_exp && !is_lprod && !is_log && strcmp(fn, "rcp") != 0) return 2;
+    const bool is_sincos = strcmp(fn, "sincos") == 0, is_sqrt = strcmp(fn, "sqrt") == 0;
+    if (!is_exp && !is_lprod && !is_log && !is_sincos && !is_sqrt && strcmp(fn, "rcp") != 0) return 2;
     FILE* f = fopen(argv[2], "rb");
     if (!f) return 3;
     std::vector<double> x;
     double v;
     while (fread(&v, sizeof v, 1, f) == 1) x.push_back(v);
     fclose(f);
-    if (is_lprod) {
+    if (is_sincos) {
+        std::vector<double> out(2 * x.size());
+        for (size_t i = 0; i < x.size(); ++i)
+            gbnll::fsincos_pi(x[i], tab.data() + gbnll::kTrigOffset, out[2 * i], out[2 * i + 1]);
+        x.swap(out);
+    } else if (is_lprod) {
         std::vector<double> out;
         for (size_t i = 0; i + 64 <= x.size(); i += 64) {
             gbnll::LogProd lp = gbnll::logprod_one();
@@ -49,7 +56,10 @@ int main(int argc, char** argv)
         x.swap(out);
     } else {
         for (double& e : x)
-            e = is_exp ? gbnll::fexp_scaled(e, tab.data()) : is_log ? gbnll::flog(e, tab.data()) : gbnll::frcp(e);
+            e = is_exp   ? gbnll::fexp_scaled(e, tab.data())
+                : is_log ? gbnll::flog(e, tab.data())
+                : is_sqrt ? gbnll::fsqrt(e)
+                         : gbnll::frcp(e);
     }
     f = fopen(argv[3], "wb");
     if (!f) return 4;

@@ -99,6 +99,10 @@ def test_batch_fits_match_single_fits(gpu_lib, kind, nev, ntoy):
 
 
 def test_batch_schedules_agree(gpu_lib):
+    # The analytic route (Newton polish with the analytic Hessian) reaches EDM 1e-14 on these
+    # 900-3100-event toys; the quasi-Newton route's line search compares NLL values whose
+    # rounding (~1e-11 at an NLL of ~1e4) exceeds the decrease an EDM of 1e-12 allows, so it
+    # cannot be held to this tolerance.
     off, cols, _ = ragged_toys(M4, [1500, 2500, 900, 3100], 8100)
     lo, hi = _bounds(M4)
     step = scale_of(M4)
@@ -106,7 +110,7 @@ def test_batch_schedules_agree(gpu_lib):
     for tile in (0, 256):
         b = gpu_lib.Batch(M4, synth.RANGES_4D).load(off, cols)
         b.set_schedule(tile, 2)
-        res.append(b.fit(synth.TRUTH_4D, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=1, hessian=1))
+        res.append(b.fit(synth.TRUTH_4D, lo=lo, hi=hi, step=step, tol_edm=1e-14, strategy=2, hessian=2))
         b.close()
     assert np.all(res[0]["status"] == 0) and np.all(res[1]["status"] == 0)
     pull = (res[0]["theta"] - res[1]["theta"]) / res[0]["err"]

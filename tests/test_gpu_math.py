@@ -38,22 +38,28 @@ def test_reciprocal_accuracy(gpu_lib):
     assert np.all(np.signbit(y) == np.signbit(x))
 
 
-def test_table_sincos_accuracy(gpu_lib):
-    # the 4D kernels take sin/cos phi from the table method for |phi| <= pi
-    rs = synth.Stream(23, 0)
-    steps = np.arange(-512, 513) * (np.pi / 512)
-    x = np.concatenate([
-        (2 * rs.uniform(300000) - 1) * np.pi,
-        steps, np.nextafter(steps, 10.0), np.nextafter(steps, -10.0),   # around the table points
-        steps + np.pi / 1024, steps - np.pi / 1024,                     # the reduction's edges
-        np.array([0.0, -0.0, 1e-300, -1e-300, 1e-8, np.pi, -np.pi, np.pi / 2, -np.pi / 2]),
-    ])
-    x = x[np.abs(x) <= np.pi]
+def test_table_sincos_accuracy(gpu_lib, tmp_path):
+    # the 4D kernels take sin/cos phi from the table method (integer arithmetic) for |phi| <= pi;
+    # the device reproduces the host build bit for bit
+    x = hm.sincos_arguments(23)
     xl = x.astype(np.longdouble)
-    for fn, ref in ((2, np.sin(xl)), (3, np.cos(xl))):
+    host = hm.host_math(hm.host_math_binary(tmp_path), "sincos", x, tmp_path).reshape(-1, 2)
+    for col, fn, ref in ((0, 2, np.sin(xl)), (1, 3, np.cos(xl))):
         y = gpu_lib.nll_diag_math(fn, x)
-        err = np.abs(y.astype(np.longdouble) - ref) / np.spacing(np.abs(ref).astype(np.float64)).astype(np.longdouble)
-        assert float(err.max()) <= 2.0, (fn, float(err.max()), x[np.argmax(err)])
+        err = hm.sincos_ulp(y, ref)
+        assert float(err.max()) < 1.0, (fn, float(err.max()), x[np.argmax(err)])
+        np.testing.assert_array_equal(y.view(np.int64), host[:, col].copy().view(np.int64))
+
+
+def test_sqrt_accuracy(gpu_lib):
+    # the angular basis's square root: the hardware single-precision seed refined in integer
+    # arithmetic (the host build of the same refinement is checked without a GPU)
+    x = hm.sqrt_arguments(37)
+    y = gpu_lib.nll_diag_math(7, x)
+    err = hm.ulp_error(y, np.sqrt(x.astype(np.longdouble)))
+    assert float(err.max()) < 0.52, (float(err.max()), x[np.argmax(err)])
+    sq = np.arange(1, 3000, dtype=np.float64)
+    np.testing.assert_array_equal(gpu_lib.nll_diag_math(7, sq * sq), sq)
 
 
 def test_table_log_accuracy(gpu_lib, tmp_path):

@@ -1,8 +1,9 @@
-"""The kernels' integer exponential, logarithm, reciprocal and running product (fexp_scaled, flog,
-frcp, LogProd), built for the host from the same header, against extended-precision references (no GPU).  The exponential and the
-logarithm are integer arithmetic throughout, so the host build computes the device's results bit
-for bit (test_gpu_math checks that on a GPU); the reciprocal's host build seeds with the rounded single-precision
-quotient where the device takes the hardware approximation, and refines the seed the same way."""
+"""The kernels' integer exponential, logarithm, reciprocal, square root, sine/cosine and running
+product (fexp_scaled, flog, frcp, fsqrt, fsincos_pi, LogProd), built for the host from the same header, against extended-precision references (no GPU).  The exponential, the
+logarithm and the sine/cosine are integer arithmetic throughout, so the host build computes the device's results bit
+for bit (test_gpu_math checks that on a GPU); the reciprocal's and the square root's host builds seed with rounded
+single-precision arithmetic where the device takes the hardware approximations, and refine the
+seed the same way."""
 import os
 import shutil
 import subprocess
@@ -177,3 +178,63 @@ def test_logarithm_tables_against_decimal(tmp_path):
     ln2_const = (w[3 * n + 2] << 64) | w[3 * n + 3]
     assert ln2_series == ln2_const
     assert abs(Decimal(ln2_const) - Decimal(2).ln() * (Decimal(2) ** 115)) <= Decimal("0.5")
+
+
+def sincos_arguments(seed):
+    rs = synth.Stream(seed, 0)
+    steps = np.arange(-512, 513) * (np.pi / 512)
+    x = np.concatenate([
+        (2 * rs.uniform(300000) - 1) * np.pi,
+        steps, np.nextafter(steps, 10.0), np.nextafter(steps, -10.0),   # around the table points
+        steps + np.pi / 1024, steps - np.pi / 1024,                     # the reduction's edges
+        (2 * rs.uniform(20000) - 1) * 1e-3, (2 * rs.uniform(2000) - 1) * 1e-9,
+        np.array([0.0, -0.0, 1e-300, -1e-300, 2.0 ** -26, 2.0 ** -27, 1e-8, np.pi, -np.pi, np.pi / 2, -np.pi / 2,
+                  np.nextafter(np.pi, 0.0), np.nextafter(np.pi / 2, 0.0), np.nextafter(np.pi / 2, 4.0)]),
+    ])
+    return x[np.abs(x) <= np.pi]
+
+
+def sincos_ulp(y, ref):
+    out = np.zeros(len(y))
+    nz = ref != 0
+    out[nz] = np.asarray(ulp_error(y[nz], ref[nz]), dtype=np.float64)
+    out[~nz] = np.where(y[~nz] == 0, 0.0, np.inf)
+    return out
+
+
+def test_integer_sincos_accuracy(tmp_path):
+    binary = host_math_binary(tmp_path)
+    x = sincos_arguments(35)
+    y = host_math(binary, "sincos", x, tmp_path).reshape(-1, 2)
+    xl = x.astype(np.longdouble)
+    es, ec = sincos_ulp(y[:, 0], np.sin(xl)), sincos_ulp(y[:, 1], np.cos(xl))
+    assert es.max() < 1.0 and ec.max() < 1.0, (es.max(), ec.max(), x[np.argmax(es)], x[np.argmax(ec)])
+    np.testing.assert_array_equal(np.signbit(y[:, 0]), np.signbit(np.sin(x)))
+    # exact values: sin 0 = 0 with its sign, cos 0 = 1, |x| < 2^-26 returns (x, 1)
+    z = host_math(binary, "sincos", np.array([0.0, -0.0, 1e-10, -1e-10]), tmp_path).reshape(-1, 2)
+    assert z[0, 0] == 0.0 and not np.signbit(z[0, 0]) and np.signbit(z[1, 0]) and np.all(z[:, 1] == 1.0)
+    assert z[2, 0] == 1e-10 and z[3, 0] == -1e-10
+
+
+def sqrt_arguments(seed):
+    rs = synth.Stream(seed, 0)
+    m = 1.0 + np.arange(4096) / 1024.0  # every 12-bit prefix of [1, 5), both exponent parities
+    return np.concatenate([
+        rs.uniform(200000), rs.uniform(100000) * rs.uniform(100000),  # sin^2 products in [0, 1]
+        np.exp((2 * rs.uniform(100000) - 1) * 700.0),
+        m, np.nextafter(m, 0.0), np.nextafter(m, 9.0), m * m,
+        np.array([1.0, 2.0, 4.0, 0.25, 2.0 - 2.0 ** -52, 4.0 - 2.0 ** -50, 2.0 ** -1022, np.finfo(np.float64).max]),
+    ])
+
+
+def test_integer_sqrt_accuracy(tmp_path):
+    binary = host_math_binary(tmp_path)
+    x = sqrt_arguments(36)
+    y = host_math(binary, "sqrt", x, tmp_path)
+    err = ulp_error(y, np.sqrt(x.astype(np.longdouble)))
+    assert float(err.max()) < 0.52, (float(err.max()), x[np.argmax(err)])
+    sq = np.arange(1, 3000, dtype=np.float64)
+    np.testing.assert_array_equal(host_math(binary, "sqrt", sq * sq, tmp_path), sq)  # exact squares
+    sp = host_math(binary, "sqrt", np.array([0.0, -0.0, np.inf, -1.0, np.nan, 5e-324]), tmp_path)
+    assert sp[0] == 0.0 and not np.signbit(sp[0]) and sp[1] == 0.0 and np.signbit(sp[1])
+    assert np.isinf(sp[2]) and np.isnan(sp[3]) and np.isnan(sp[4]) and sp[5] == 0.0
