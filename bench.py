@@ -335,12 +335,15 @@ def serving(g, device, n_req, rate, seed_stream=0, size_classes=False, max_queue
                         opts[key if not isinstance(key, tuple) else key[0]]) for key in servers}
         serve(servers, warm, realtime=False, route=route)
         phases = {}
+        load = [os.getloadavg()[0]]  # the machine's host is shared: its load explains slow runs
         served = serve(servers, requests(), realtime=True, phases=phases, route=route, max_queued=max_queued,
                        admit_all=admit_all, direct=direct if idle_direct else None)
+        load.append(os.getloadavg()[0])
         for srv in servers.values():
             srv.close()
         serve_sequential(models, warm, opts)  # warm-up
         seq = serve_sequential(models, requests(), opts)
+        load.append(os.getloadavg()[0])
         for m in models.values():
             m.close()
         diffs = [float(np.max(np.abs(a.result["theta"] - b.result["theta"]) / b.result["err"]))
@@ -351,6 +354,8 @@ def serving(g, device, n_req, rate, seed_stream=0, size_classes=False, max_queue
              "served_host_phases_ms": {k.replace("_s", "_ms"): (1e3 * v if k.endswith("_s") else v)
                                        for k, v in phases.items()},
              "served_span_ms": 1e3 * span_s,
+             "host_load_1min": {"before": load[0], "after_served": load[1], "after_sequential": load[2],
+                                "host_cpus": os.cpu_count()},
              "max_abs_diff_over_sigma_vs_sequential": max(diffs) if diffs else None}
         if r["served"]["fits_per_s"] and r["sequential"]["fits_per_s"]:
             r["speedup_fits_per_s"] = r["served"]["fits_per_s"] / r["sequential"]["fits_per_s"]
