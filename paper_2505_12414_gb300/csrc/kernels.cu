@@ -56,11 +56,12 @@ __device__ double g_exp2tab[kTabDoubles];  // exp and sin/cos tables (fill_devic
 // IP (in place): the columns are the caller's buffers (device or host memory the device
 // reads), so the tail pair may not be read whole, and the kernel also sums w (m - ma) and
 // counts events outside the ranges (slots KB-1 and KB; the bad count moves to the last slot).
-// In place, the kernel waits on host memory over NVLink-C2C: at most 168 registers (a few
-// spilled) let 12 warps per SM (3 x 128) hide that latency instead of 8; measured 4 % faster
-// per in-place step than the 242 registers the compiler otherwise takes (144 and 128: slower).
+// Registers: up to 255 (a 256-thread block still fits the register file).  In place, the
+// kernel waits on host memory over NVLink-C2C: at most 168 registers (52-80 B spilled) let 12
+// warps per SM (3 x 128) hide that latency instead of 8; measured 4 % faster per in-place step
+// than the 242 registers the compiler otherwise takes (144 and 128: slower).
 template <int KIND, int VAR, bool W, bool GRAD, bool IP = false>
-__global__ void __launch_bounds__(256, 1) __maxnreg__(IP ? 168 : 255) fused_nll_kernel(const KArgs a)
+__global__ void __maxnreg__(IP ? 168 : 255) fused_nll_kernel(const KArgs a)
 {
     constexpr int KB = !GRAD ? kAccNll : (KIND == kMass1D ? kAcc1D : kAcc4D);
     constexpr int K = KB + (IP ? kAccInPlace : 0);
