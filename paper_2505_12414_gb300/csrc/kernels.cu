@@ -104,11 +104,22 @@ __global__ void __maxnreg__(IP ? 168 : 255) fused_nll_kernel(const KArgs a)
     int bad = 0;
     const KConst& c = a.c;
 
+    // The direct variant reads few columns (4, +1 weight) and spends long on each pair: its next
+    // pair's loads are issued before the current pair is processed (double-buffered in
+    // registers), so their latency -- long from host memory -- overlaps the arithmetic.  The
+    // precompute variant's 16 columns would not fit a second buffer; its loads are issued after.
+    constexpr bool kAhead = VAR == kVarDirect;
     while (p < end) {
+        const int64_t pn = p + blockDim.x;
+        PairIn nx;
+        if (kAhead && pn < end) load_pair<KIND, VAR, W, IP>(a, pn, nx);
         process_pair<KIND, VAR, W, GRAD>(c, in, (2 * p + 1) < n, acc, lpx, lpy, bad, s_tab);
         if (IP) inplace_pair<KIND, VAR, W>(a, in, (2 * p + 1) < n, acc[KB - 1], acc[KB]);
-        p += blockDim.x;
-        if (p < end) load_pair<KIND, VAR, W, IP>(a, p, in);
+        p = pn;
+        if (kAhead)
+            in = nx;
+        else if (p < end)
+            load_pair<KIND, VAR, W, IP>(a, p, in);
     }
     if (!W) {
         // one logarithm per warp: multiply the running products across the warp first
