@@ -89,10 +89,12 @@ int nll_create_model(int kind, const double* obs_ranges, int device, uintptr_t c
  *                n_events doubles.
  *   on_device    0: host pointers, 1: device pointers on the model's device; the library
  *                copies them into its own 256-byte-aligned SoA store (padded to a tile
- *                multiple) before returning.  Ordinary (pageable) host memory on a device
- *                with cudaDevAttrPageableMemoryAccess is read in place by the load's
- *                statistics kernel, which stores the events as it checks them (no
- *                host-side staging copy); pinned host memory is copied by DMA.
+ *                multiple) before returning.  Host columns the device can read -- pinned
+ *                or registered memory, and ordinary pageable memory on a device with
+ *                cudaDevAttrPageableMemoryAccess -- are read in place by the load's
+ *                statistics kernel, which stores the events as it checks them (one pass,
+ *                no copy-engine transfer or host-side staging); other host memory is
+ *                copied by cudaMemcpyAsync.
  *                2 (in place): nothing is copied or stored; every evaluation reads the
  *                caller's buffers where they are.  They must be memory the model's device can
  *                read -- its own device memory, managed memory, pinned or registered host
@@ -457,9 +459,9 @@ int nll_server_create(int kind, const double* obs_ranges, int device, int max_sl
  * nll_server_submit -- admit one fit: n_events events (host SoA columns; weights must be NULL,
  * a server serves unweighted fits) and its start point theta0 (host, npar doubles).  On
  * success *request_id identifies the fit and its events are on the device.  The events go to
- * the device on the server's collection stream (highest stream priority; pageable host
- * columns are read in place by the range-check kernel where the device has pageable-memory
- * access, others copied) and the call waits only for that copy and the range check, not for
+ * the device on the server's collection stream (highest stream priority; host columns the
+ * device can read -- pinned, or pageable with pageable-memory access -- are read in place by
+ * the range-check kernel, others copied) and the call waits only for that copy and the range check, not for
  * the steps in flight; the fit joins the steps queued after it.
  * Returns NLL_ERR_STATE (nothing admitted) when no slot or no pool range is free: the
  * caller keeps the request queued and retries after nll_server_poll returned finished fits.

@@ -238,9 +238,10 @@ struct NoAllocScratch {
 };
 // Device addresses of the scratch on `device` (which must be current); set up once per device.
 cudaError_t noalloc_scratch_setup(int device, NoAllocScratch* out);
-// True when p is ordinary (pageable, unregistered) host memory that kernels on `device` can
-// read in place (the device reports pageable memory access, as with ATS over NVLink-C2C).
-bool host_pageable_readable(int device, const void* p);
+// True when p is host memory that kernels on `device` read in place: pinned or registered host
+// memory, or ordinary pageable memory where the device reports pageable memory access (ATS over
+// NVLink-C2C).
+bool host_read_in_place(int device, const void* p);
 int fused_occupancy(int kind, int variant, bool weighted, bool grad, int threads,
                     bool in_place = false);  // resident blocks/SM
 // Order key of a double: key(x) <= key(y) iff x <= y for non-NaN x, y (-0 < +0); NaNs fall

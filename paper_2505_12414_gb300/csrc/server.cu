@@ -509,7 +509,7 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
     if (slot < 0 || !pool_alloc(s, len, &begin)) return sfail(s, NLL_ERR_STATE, "no free slot or pool range");
     // The pool range is free: no queued step or pass reads it, so the request's events go in on
     // the collection stream without waiting for the steps in flight.
-    // Columns in pageable host memory that the device reads in place (ATS) go into the pool as
+    // Host columns the device reads in place (pinned, or pageable with ATS) go into the pool as
     // the statistics kernel reads them, with no host-side staging copy; the rest by cudaMemcpyAsync.
     const cudaStream_t cs = s->cstream;
     cudaError_t e = cudaSuccess;
@@ -517,7 +517,7 @@ int nll_server_submit(nll_server* s, const double* const* columns, const double*
     double* dst[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int d = 0; d < s->ndim && e == cudaSuccess && n_events > 0; ++d) {
         double* to = s->d_ev + (size_t)d * s->n_pad + begin;
-        if (host_pageable_readable(s->device, columns[d])) {
+        if (host_read_in_place(s->device, columns[d])) {
             src[d] = columns[d];
             dst[d] = to;
         } else {
