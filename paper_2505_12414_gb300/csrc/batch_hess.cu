@@ -207,11 +207,9 @@ __global__ void __launch_bounds__(kHessThreads) batch_hess_units(const HessDev h
                     __syncthreads();
                 }
             }
-            if (!W) {  // sum over the block of ln(products) into the ln P slot
-                double v = logprod_value(lp);
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) s_lnp[warp] = v;
+            if (!W) {  // products across the warp, one logarithm per warp, into the ln P slot
+                const LogProd wp = logprod_warp(lp);
+                if (lane == 0) s_lnp[warp] = logprod_value(wp);
                 __syncthreads();
                 lnp_tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
                 if (ls >= 0 && !lnp_in_tail && t == (ls & (kHessThreads - 1))) {

@@ -121,11 +121,10 @@ __global__ void __launch_bounds__(kHessThreads) hess_kernel(const HArgs a)
     const bool lnp_in_tail = ls >= tb && ls < tb + tn;
     double lnp_tot = 0.0;
     if (!W) {
-        // sum over the block of the threads' ln(products), fixed tree, into the ln P slot
-        double v = logprod_value(lp);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_lnp[warp] = v;
+        // the threads' products multiplied across the warp (integer pipe), one logarithm per
+        // warp, then the four warps in a fixed order, into the ln P slot
+        const LogProd wp = logprod_warp(lp);
+        if (lane == 0) s_lnp[warp] = logprod_value(wp);
         __syncthreads();
         lnp_tot = (s_lnp[0] + s_lnp[1]) + (s_lnp[2] + s_lnp[3]);
         if (ls >= 0 && !lnp_in_tail && t == (ls & (kHessThreads - 1))) {

@@ -436,6 +436,10 @@ int run_fused(nll_model* m, const Hoist& H, bool grad, int bps, int threads, int
         a.done = m->d_done;
         a.seq = next_seq(m);
     }
+    // A sample too small to give every SM a block at this block size runs in 64-thread blocks:
+    // the events' FP64 work then spreads over up to four times as many SMs (an SM's FP64 pipe,
+    // not the launch, bounds a small evaluation).
+    if (threads > 64 && (m->n + 1) / 2 < (int64_t)m->sm_count * threads) threads = 64;
     const int resident = fused_resident(m, variant, grad, threads);
     int blocks = launch_blocks(m, resident > 0 && resident < bps ? resident : bps, threads);
     cudaError_t e;
