@@ -246,7 +246,9 @@ __host__ __device__ __forceinline__ double fsqrt(double x)
 {
     const uint64_t b = bits_of(x);
     const int be = (int)((b >> 52) & 0x7ff);
-    if (be == 0x7ff || (b >> 63)) return (b << 1) == 0 ? x : (b == 0x7ff0000000000000ull ? x : double_of(0x7ff8000000000000ull));
+    const double nan = double_of(0x7ff8000000000000ull);
+    if (b >> 63) return (b << 1) == 0 ? x : nan;         // -0 itself; negative x and NaN
+    if (be == 0x7ff) return (b << 12) == 0 ? x : nan;    // +inf itself; NaN
     if (be == 0) return double_of(b & 0x8000000000000000ull);  // 0, and subnormals flushed
     const int E = be - 1023;
     const int odd = E & 1;
