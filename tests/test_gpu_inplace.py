@@ -115,3 +115,27 @@ def test_in_place_hessian_and_fit(gpu_lib):
     np.testing.assert_allclose(ra["err"], rb["err"], rtol=1e-6)
     m.close()
     c.close()
+
+
+@pytest.mark.parametrize("n", [1, 129, 100001])
+@pytest.mark.parametrize("kind,weighted", [(M1, True), (M4, False), (M4, True)])
+def test_copying_load_reads_pinned_and_pageable_alike(gpu_lib, kind, weighted, n):
+    # load() stores host columns through its statistics kernel (pinned memory, and pageable
+    # memory where the device reads it) or by cudaMemcpyAsync: every route stores the same
+    # events, so the evaluations agree bit for bit, and out-of-range events are still refused
+    cols, ranges, theta, w = sample(kind, n, 470 + n, weighted)
+    res = []
+    for where in ("pageable", "pinned", "device"):
+        arrs = placed(list(cols) + ([w] if weighted else []), where)
+        m = gpu_lib.Model(kind, ranges).load(arrs[:len(cols)], arrs[len(cols)] if weighted else None)
+        res.append(m.eval_grad(theta))
+        m.close()
+    for f, g in res[1:]:
+        assert f == res[0][0] and np.array_equal(g, res[0][1])
+    bad = [c.copy() for c in cols]
+    bad[0][n // 2] = ranges[1] + 1.0  # one event above the mass window
+    m = gpu_lib.Model(kind, ranges)
+    with pytest.raises(gpu_lib.NLLError) as e:
+        m.load([pinned(c) for c in bad], pinned(w) if weighted else None)
+    assert e.value.status == gpu_lib.NLL_ERR_ARG
+    m.close()
