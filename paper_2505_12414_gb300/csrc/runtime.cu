@@ -352,7 +352,8 @@ bool host_read_in_place(int device, const void* p)
         cudaGetLastError();
         return false;
     }
-    if (at.type == cudaMemoryTypeHost) return true;  // pinned or registered: mapped for every device
+    // pinned or registered: read in place where the device addresses it at the host pointer
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer == p;
     if (at.type != cudaMemoryTypeUnregistered) return false;
     int a = attr[device].load(std::memory_order_relaxed);
     if (a == 0) {
