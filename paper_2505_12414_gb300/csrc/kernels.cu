@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(64) final_reduce_kernel(const double* partials
 // ----------------------------------------------------------------------------------
 // Load-time statistics and range validation: sum w, sum w (m - ma), events outside.  With
 // dst pointers set, the kernel also stores what it reads there: columns in host memory that the
-// device reads in place (pageable memory with ATS) arrive in the event store in the same pass,
-// with no host-side staging copy.
+// device reads in place (pinned memory, or pageable memory with ATS) arrive in the event store
+// in the same pass, with no copy-engine transfer or host-side staging copy.
 // ----------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) stats_kernel(const SArgs a)
 {
