@@ -297,7 +297,7 @@ static bool hess_layout_build(int kind, bool weighted, bool want_w2, HessLayout*
 namespace {
 __device__ uint8_t g_hsij[8][2 * kHessMaxSlots];  // slot tables by layout key, per device
 std::mutex g_hsij_mutex;
-bool g_hsij_ready[64][8];
+const uint8_t* g_hsij_addr[64][8];  // device address of each uploaded table (null: not yet)
 }  // namespace
 
 cudaError_t hess_slot_table(int kind, bool weighted, bool want_w2, const HessLayout& L, const uint8_t** out)
@@ -308,43 +308,61 @@ cudaError_t hess_slot_table(int kind, bool weighted, bool want_w2, const HessLay
     if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
     const int key = (kind == kMass1D ? 0 : 4) + (weighted ? 2 : 0) + (want_w2 ? 1 : 0);
     std::lock_guard<std::mutex> lock(g_hsij_mutex);
-    if (!g_hsij_ready[device][key]) {
+    if (!g_hsij_addr[device][key]) {
         uint8_t t[2 * kHessMaxSlots];
         memcpy(t, L.si, kHessMaxSlots);
         memcpy(t + kHessMaxSlots, L.sj, kHessMaxSlots);
         e = cudaMemcpyToSymbol(g_hsij, t, sizeof t, (size_t)key * sizeof t);
         if (e != cudaSuccess) return e;
-        g_hsij_ready[device][key] = true;
+        uint8_t* base = nullptr;
+        e = cudaGetSymbolAddress((void**)&base, g_hsij);
+        if (e != cudaSuccess) return e;
+        g_hsij_addr[device][key] = base + (size_t)key * 2 * kHessMaxSlots;
     }
-    uint8_t* base = nullptr;
-    e = cudaGetSymbolAddress((void**)&base, g_hsij);
-    if (e != cudaSuccess) return e;
-    *out = base + (size_t)key * 2 * kHessMaxSlots;
+    *out = g_hsij_addr[device][key];
     return cudaSuccess;
 }
 
 // The slot table of (kind, weighted, W) is built once (recording the assembly is quadratic in
 // the slot count) and copied out on every call.
+// Layouts and their inverse maps (slot of each column pair), built once per (kind, weighted, W).
+namespace {
+std::mutex g_layout_mutex;
+HessLayout g_layout[2][2][2];
+uint16_t g_slot_of[2][2][2][64 * 64];
+signed char g_layout_state[2][2][2];  // 0: not built, 1: built, -1: does not fit
+
+signed char layout_state(int kind, bool weighted, bool want_w2)
+{
+    const int k = kind == kMass1D ? 0 : 1, w = weighted ? 1 : 0, x = want_w2 ? 1 : 0;
+    std::lock_guard<std::mutex> lock(g_layout_mutex);
+    signed char& st = g_layout_state[k][w][x];
+    if (st == 0) {
+        HessLayout& L = g_layout[k][w][x];
+        st = hess_layout_build(kind, weighted, want_w2, &L) ? 1 : -1;
+        if (st > 0) {
+            uint16_t* so = g_slot_of[k][w][x];
+            memset(so, 0xff, sizeof g_slot_of[k][w][x]);
+            for (int s = 0; s < L.nslots; ++s) so[L.si[s] * 64 + L.sj[s]] = (uint16_t)s;
+        }
+    }
+    return st;
+}
+}  // namespace
+
 bool hess_layout(int kind, bool weighted, bool want_w2, HessLayout* L)
 {
-    static std::mutex mu;
-    static HessLayout cache[2][2][2];
-    static signed char state[2][2][2];  // 0: not built, 1: built, -1: does not fit
-    const int k = kind == kMass1D ? 0 : 1, w = weighted ? 1 : 0, x = want_w2 ? 1 : 0;
-    std::lock_guard<std::mutex> lock(mu);
-    if (state[k][w][x] == 0) state[k][w][x] = hess_layout_build(kind, weighted, want_w2, &cache[k][w][x]) ? 1 : -1;
-    if (state[k][w][x] < 0) return false;
-    *L = cache[k][w][x];
+    if (layout_state(kind, weighted, want_w2) < 0) return false;
+    *L = g_layout[kind == kMass1D ? 0 : 1][weighted ? 1 : 0][want_w2 ? 1 : 0];
     return true;
 }
 
 double hess_assemble(int kind, bool weighted, bool want_w2, const Hoist& H, double sum_wdm, const HessLayout& L,
                      const double* sums, double* nll, double* grad, double* hess, double* w2)
 {
-    uint16_t slot_of[64 * 64];
-    memset(slot_of, 0xff, sizeof slot_of);
-    for (int k = 0; k < L.nslots; ++k) slot_of[L.si[k] * 64 + L.sj[k]] = (uint16_t)k;
-    Reader rd{slot_of, sums};
+    if (layout_state(kind, weighted, want_w2) < 0) return NAN;
+    (void)L;  // the cached inverse map of the same layout
+    Reader rd{g_slot_of[kind == kMass1D ? 0 : 1][weighted ? 1 : 0][want_w2 ? 1 : 0], sums};
     double bad = assemble_any(kind, weighted, H, sum_wdm, want_w2, rd, nll, grad, hess, w2);
     return rd.missing ? NAN : bad;
 }
