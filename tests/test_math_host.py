@@ -20,13 +20,21 @@ CSRC = os.path.join(os.path.dirname(HERE), "paper_2505_12414_gb300", "csrc")
 S = 1024.0 / np.log(2.0)  # the kernels pass x * 1024/ln2
 
 
+_BINARY = {}
+
+
 def host_math_binary(tmpdir):
+    """The host build of the special functions, compiled once per session (the first caller's
+    tmpdir holds it)."""
+    if "path" in _BINARY:
+        return _BINARY["path"]
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not found")
     out = os.path.join(str(tmpdir), "math_host")
     subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-I", CSRC,
                            os.path.join(HERE, "host", "math_host.cu"), "-o", out])
+    _BINARY["path"] = out
     return out
 
 
